@@ -1,0 +1,81 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds NO arithmetic of the method (no features, no proxes, no ADMM):
+it only draws data matrices X (n x d, float32) and targets Y (n x m, float32)
+with numpy's PCG64 generator, so that the GPU library, the oracle, the tests and
+the benchmark all see identical inputs.  The random numbers the METHOD draws
+(the Gaussian projection G and the phases b) are not made here: each side
+produces them from the Philox4x32-10 definition.
+
+The paper's data sets (MNIST-8M, TIMIT) are not available; these recipes stand
+in for them with matching shapes and value ranges (Sec. 5, "Datasets"):
+
+* ``ridge``       n=2000, d=16, X ~ U[0,1], y = sin(2 pi x.u) + 0.1 N(0,1),
+                  u ~ N(0, I/d); real-valued single output.
+* ``multiclass``  Gaussian mixture with one class per component (TIMIT-like:
+                  d=440, 147 classes): means ~ N(0, I), within-class N(0, 4 I),
+                  every feature then standardised; +-1 one-hot targets.
+* ``sparse01``    MNIST-like: d=784 values in [0,1], about 20% non-zero; each
+                  of the classes has a random support template (35% of the
+                  coordinates) and a mean intensity pattern, each row keeps its
+                  template entries with probability 0.57 and jitters them;
+                  +-1 one-hot targets.
+* ``binary``      two Gaussians N(+-mu, I), mu ~ 2 N(0, I/d), labels +-1.
+"""
+import numpy as np
+
+
+def _rng(seed):
+    return np.random.default_rng(int(seed))
+
+
+def ridge(n=2000, d=16, seed=0):
+    rng = _rng(seed)
+    X = rng.random((n, d))
+    u = rng.standard_normal(d) / np.sqrt(d)
+    y = np.sin(2.0 * np.pi * (X @ u)) + 0.1 * rng.standard_normal(n)
+    return X.astype(np.float32), y.reshape(n, 1).astype(np.float32)
+
+
+def onehot_pm1(labels, m):
+    Y = -np.ones((labels.shape[0], m), dtype=np.float32)
+    Y[np.arange(labels.shape[0]), labels] = 1.0
+    return Y
+
+
+def multiclass(n=200_000, d=440, m=147, seed=0, chunk=50_000):
+    rng = _rng(seed)
+    means = rng.standard_normal((m, d)).astype(np.float32)
+    labels = rng.integers(0, m, size=n)
+    X = np.empty((n, d), dtype=np.float32)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        X[r0:r1] = means[labels[r0:r1]] + 2.0 * rng.standard_normal((r1 - r0, d), dtype=np.float32)
+    mu = X.mean(axis=0, dtype=np.float64).astype(np.float32)
+    sd = X.std(axis=0, dtype=np.float64).astype(np.float32)
+    X -= mu
+    X /= np.maximum(sd, 1e-6)
+    return X, onehot_pm1(labels, m)
+
+
+def sparse01(n=20_000, d=784, m=10, seed=0, chunk=100_000):
+    rng = _rng(seed)
+    support = rng.random((m, d)) < 0.35
+    level = rng.random((m, d)).astype(np.float32)
+    labels = rng.integers(0, m, size=n)
+    X = np.zeros((n, d), dtype=np.float32)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        lab = labels[r0:r1]
+        keep = support[lab] & (rng.random((r1 - r0, d)) < 0.57)
+        val = level[lab] + 0.25 * rng.standard_normal((r1 - r0, d), dtype=np.float32)
+        X[r0:r1] = np.where(keep, np.clip(val, 0.0, 1.0), 0.0)
+    return X, onehot_pm1(labels, m)
+
+
+def binary(n=10_000, d=128, seed=0):
+    rng = _rng(seed)
+    mu = 2.0 * rng.standard_normal(d) / np.sqrt(d)
+    y = np.where(rng.random(n) < 0.5, 1.0, -1.0)
+    X = y[:, None] * mu[None, :] + rng.standard_normal((n, d))
+    return X.astype(np.float32), y.reshape(n, 1).astype(np.float32)
