@@ -140,6 +140,12 @@ class Problem:
             self._Z = rff.features_block(self.X, self.seed, self.sigma, self.D, 0, self.D)
         return self._Z
 
+    def solvers(self):
+        """Cached factor of every block (eq. (cache)), built on first use."""
+        if getattr(self, "_solvers", None) is None:
+            self._solvers = [[_BlockSolver(self.Zblock(i, j)) for j in range(self.C)] for i in range(self.R)]
+        return self._solvers
+
     def Zblock(self, i, j):
         r0, r1 = self.rows[i], self.rows[i + 1]
         c0, c1 = self.cols[j], self.cols[j + 1]
@@ -162,7 +168,7 @@ def admm(prob, iters, variant="equation", history=False):
     ni = [int(rows[i + 1] - rows[i]) for i in range(R)]
     sj = [int(cols[j + 1] - cols[j]) for j in range(C)]
     Ys = [prob.Y[rows[i]:rows[i + 1]] for i in range(R)]
-    solvers = [[_BlockSolver(prob.Zblock(i, j)) for j in range(C)] for i in range(R)]
+    solvers = prob.solvers()
 
     z = np.zeros
     O = [z((ni[i], m)) for i in range(R)]

@@ -1,0 +1,301 @@
+"""Python binding of librff_admm.so: block-splitting ADMM over implicit random
+Fourier features on a GB300 (sm_103a).
+
+Argument marshalling only.  Every step of the solver runs in the CUDA library;
+this module converts numpy arrays / torch tensors to pointers and sizes, calls
+the C ABI of include/rff_admm.h under the same function names, and turns error
+codes into exceptions.  There is no CPU fallback: importing fails loudly when
+the library has not been built (``paper_1409_0940_gb300.build.build()``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librff_admm.so")
+
+RFF_OK, RFF_EINVAL, RFF_ENOMEM, RFF_ECUDA, RFF_ETIMEOUT, RFF_ENOTREADY, RFF_ENUMERIC = range(7)
+_STATUS = {0: "RFF_OK", 1: "RFF_EINVAL", 2: "RFF_ENOMEM", 3: "RFF_ECUDA", 4: "RFF_ETIMEOUT",
+           5: "RFF_ENOTREADY", 6: "RFF_ENUMERIC"}
+LOSSES = {"squared": 0, "hinge": 1, "logistic": 2, "multinomial": 3}
+REGS = {"l2": 0, "l1": 1}
+PRECS = {"fp32": 0, "split_bf16": 1}
+RHO_SCALES = {"sum": 0, "mean": 1}
+
+
+class RffError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), message))
+        self.status = status
+
+
+class rff_admm_params(ctypes.Structure):
+    _fields_ = [("loss", ctypes.c_int32), ("reg", ctypes.c_int32), ("lambda_", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("rho", ctypes.c_double), ("D", ctypes.c_int64),
+                ("R", ctypes.c_int32), ("C", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("prec", ctypes.c_int32), ("m", ctypes.c_int32), ("rho_scale", ctypes.c_int32),
+                ("newton_iters", ctypes.c_int32)]
+
+
+class rff_admm_stats(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int32), ("primal_res", ctypes.c_double), ("dual_res", ctypes.c_double),
+                ("objective", ctypes.c_double), ("ms_setup", ctypes.c_double), ("ms_iterations", ctypes.c_double)]
+
+
+class rff_admm_profile(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("launches", ctypes.c_int64), ("ms_prox_reg", ctypes.c_double),
+                ("ms_pass1", ctypes.c_double), ("ms_project", ctypes.c_double), ("ms_pass2", ctypes.c_double),
+                ("ms_exchange", ctypes.c_double), ("ms_average", ctypes.c_double)]
+
+
+# every entry point of include/rff_admm.h: name -> (restype, argtypes)
+_P, _I32, _I64, _U64, _D, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, \
+    ctypes.c_size_t
+PROTOTYPES = {
+    "rff_admm_create": (_I32, [ctypes.POINTER(rff_admm_params), _P, ctypes.POINTER(_P)]),
+    "rff_admm_set_data": (_I32, [_P, _P, _P, _I64, _I64, ctypes.c_int]),
+    "rff_admm_solve": (_I32, [_P, _I32, ctypes.POINTER(rff_admm_stats)]),
+    "rff_admm_predict": (_I32, [_P, _P, _I64, _P, ctypes.c_int]),
+    "rff_admm_get_weights": (_I32, [_P, _P, ctypes.c_int]),
+    "rff_admm_get_state": (_I32, [_P, _P, ctypes.POINTER(_SZ)]),
+    "rff_admm_set_state": (_I32, [_P, _P, _SZ]),
+    "rff_admm_set_profiling": (_I32, [_P, ctypes.c_int]),
+    "rff_admm_get_profile": (_I32, [_P, ctypes.POINTER(rff_admm_profile)]),
+    "rff_admm_destroy": (None, [_P]),
+    "rff_admm_last_error": (ctypes.c_char_p, [_P]),
+    "rff_philox4x32_10": (_I32, [_P, _U64, _I64, _P, _P]),
+    "rff_rff_params": (_I32, [_U64, _D, _I64, _I64, _I64, _P, _P, _P]),
+    "rff_features": (_I32, [_P, _I64, _I64, _U64, _D, _I64, _I64, _I64, _I32, _P, _P]),
+    "rff_prox_loss": (_I32, [_I32, _P, _P, _I64, _I32, _D, _I32, _P, _P]),
+    "rff_prox_reg": (_I32, [_I32, _P, _I64, _D, _P, _P]),
+    "rff_cholesky_f64": (_I32, [_P, _I32, _I32, _P, _P]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("librff_admm.so is not built; run paper_1409_0940_gb300.build.build() "
+                          "(needs nvcc) -- there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in PROTOTYPES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+# ----------------------------------------------------------------- marshalling
+def _is_torch_cuda(x):
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+def _ptr(x, dtype=np.float32):
+    """(pointer, is_device) of a contiguous numpy array or torch tensor of `dtype`."""
+    if x is None:
+        return None, 0
+    if _is_torch_cuda(x) or type(x).__module__.startswith("torch"):
+        import torch
+        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.uint32: torch.int32,
+               np.int32: torch.int32}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            raise TypeError("expected a contiguous %s tensor" % tdt)
+        if x.is_cuda:
+            torch.cuda.synchronize(x.device)
+        return ctypes.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous:
+        raise TypeError("expected a C-contiguous numpy array of %s" % np.dtype(dtype))
+    return ctypes.c_void_p(x.ctypes.data), 0
+
+
+def _check(status, h=None, what=""):
+    if status != RFF_OK:
+        msg = lib.rff_admm_last_error(h).decode() if h else what
+        raise RffError(status, msg or what)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def make_params(loss="squared", reg="l2", lam=1e-4, sigma=1.0, rho=1.0, D=512, R=1, C=1, seed=0,
+                prec="fp32", m=1, rho_scale="sum", newton_iters=0):
+    return rff_admm_params(LOSSES[loss], REGS[reg], lam, sigma, rho, D, R, C, seed, PRECS[prec], m,
+                           RHO_SCALES[rho_scale], newton_iters)
+
+
+# ----------------------------------------------------------------- C ABI, same names
+def rff_admm_create(params, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib.rff_admm_create(ctypes.byref(params), _stream(stream), ctypes.byref(h)), None,
+           "rff_admm_create rejected the parameters")
+    return h
+
+
+def rff_admm_set_data(h, X, Y):
+    n, d = X.shape
+    px, dx = _ptr(X)
+    py, dy = _ptr(Y)
+    if dx != dy:
+        raise TypeError("X and Y must both be host or both be device arrays")
+    _check(lib.rff_admm_set_data(h, px, py, n, d, dx), h)
+
+
+def rff_admm_solve(h, iters, stats=True):
+    st = rff_admm_stats() if stats else None
+    _check(lib.rff_admm_solve(h, iters, ctypes.byref(st) if stats else None), h)
+    if not stats:
+        return None
+    return {k: getattr(st, k) for k, _ in rff_admm_stats._fields_}
+
+
+def rff_admm_predict(h, Xq, out):
+    pq, dq = _ptr(Xq)
+    po, do = _ptr(out)
+    if dq != do:
+        raise TypeError("Xq and scores must both be host or both be device arrays")
+    _check(lib.rff_admm_predict(h, pq, Xq.shape[0], po, dq), h)
+    return out
+
+
+def rff_admm_get_weights(h, out):
+    po, do = _ptr(out)
+    _check(lib.rff_admm_get_weights(h, po, do), h)
+    return out
+
+
+def rff_admm_get_state(h):
+    n = ctypes.c_size_t(0)
+    _check(lib.rff_admm_get_state(h, None, ctypes.byref(n)), h)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib.rff_admm_get_state(h, buf, ctypes.byref(n)), h)
+    return buf.raw[:n.value]
+
+
+def rff_admm_set_state(h, state):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(lib.rff_admm_set_state(h, buf, len(state)), h)
+
+
+def rff_admm_set_profiling(h, enable):
+    _check(lib.rff_admm_set_profiling(h, 1 if enable else 0), h)
+
+
+def rff_admm_get_profile(h):
+    p = rff_admm_profile()
+    _check(lib.rff_admm_get_profile(h, ctypes.byref(p)), h)
+    return {k: getattr(p, k) for k, _ in rff_admm_profile._fields_}
+
+
+def rff_admm_destroy(h):
+    lib.rff_admm_destroy(h)
+
+
+def rff_admm_last_error(h):
+    return lib.rff_admm_last_error(h).decode()
+
+
+def rff_philox4x32_10(ctr, seed, out, stream=None):
+    pc, _ = _ptr(ctr, np.uint32)
+    po, _ = _ptr(out, np.uint32)
+    _check(lib.rff_philox4x32_10(pc, seed, ctr.numel() // 4, po, _stream(stream)), None, "rff_philox4x32_10")
+    return out
+
+
+def rff_rff_params(seed, sigma, d, k_lo, k_hi, G, b, stream=None):
+    pg, _ = _ptr(G)
+    pb, _ = _ptr(b)
+    _check(lib.rff_rff_params(seed, sigma, d, k_lo, k_hi, pg, pb, _stream(stream)), None, "rff_rff_params")
+    return G, b
+
+
+def rff_features(X, seed, sigma, D, k_lo, k_hi, prec, Z, stream=None):
+    px, _ = _ptr(X)
+    pz, _ = _ptr(Z)
+    _check(lib.rff_features(px, X.shape[0], X.shape[1], seed, sigma, D, k_lo, k_hi, PRECS.get(prec, prec), pz,
+                            _stream(stream)), None, "rff_features")
+    return Z
+
+
+def rff_prox_loss(loss, V, Y, t, newton_iters, out, stream=None):
+    pv, _ = _ptr(V)
+    py, _ = _ptr(Y)
+    po, _ = _ptr(out)
+    _check(lib.rff_prox_loss(LOSSES.get(loss, loss), pv, py, V.shape[0], V.shape[1], t, newton_iters, po,
+                             _stream(stream)), None, "rff_prox_loss")
+    return out
+
+
+def rff_prox_reg(reg, V, tau, out, stream=None):
+    pv, _ = _ptr(V)
+    po, _ = _ptr(out)
+    _check(lib.rff_prox_reg(REGS.get(reg, reg), pv, V.numel(), tau, po, _stream(stream)), None, "rff_prox_reg")
+    return out
+
+
+def rff_cholesky_f64(A, info, stream=None):
+    pa, _ = _ptr(A, np.float64)
+    pi, _ = _ptr(info, np.int32)
+    _check(lib.rff_cholesky_f64(pa, A.shape[0], A.shape[1], pi, _stream(stream)), None, "rff_cholesky_f64")
+    return A
+
+
+# ----------------------------------------------------------------- convenience
+class Solver:
+    """Owns one rff_admm_t handle."""
+
+    def __init__(self, stream=None, **kw):
+        self.params = make_params(**kw)
+        self.m = self.params.m
+        self.D = self.params.D
+        self.h = rff_admm_create(self.params, stream)
+
+    def set_data(self, X, Y):
+        rff_admm_set_data(self.h, X, Y)
+
+    def solve(self, iters, stats=True):
+        return rff_admm_solve(self.h, iters, stats)
+
+    def predict(self, Xq, out=None):
+        if out is None:
+            out = np.empty((Xq.shape[0], self.m), dtype=np.float32)
+        return rff_admm_predict(self.h, Xq, out)
+
+    def weights(self, out=None):
+        if out is None:
+            out = np.empty((self.D, self.m), dtype=np.float32)
+        return rff_admm_get_weights(self.h, out)
+
+    def get_state(self):
+        return rff_admm_get_state(self.h)
+
+    def set_state(self, state):
+        rff_admm_set_state(self.h, state)
+
+    def profiling(self, enable=True):
+        rff_admm_set_profiling(self.h, enable)
+
+    def profile(self):
+        return rff_admm_get_profile(self.h)
+
+    def close(self):
+        if self.h:
+            rff_admm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,997 @@
+// The C ABI of include/rff_admm.h: handle, device memory, set-up (Philox draw,
+// Gram matrices, FP64 Cholesky, cached inverses) and the iteration schedule of
+// block-splitting ADMM (Sec. 3, update equations around eq. (gp), in the
+// reorganised form: O'_ij kept per block, Z_ij regenerated twice per iteration).
+#include "../../include/rff_admm.h"
+#include "common.cuh"
+#include "internal.h"
+#include "tc.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace rff;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct rff_admm_s {
+  rff_admm_params p{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  // ---- geometry
+  bool has_data = false, factored = false;
+  int64_t n = 0, d = 0, dld = 0, m = 0, mpad = 0, D = 0, nslots = 0, fslots = 0;
+  int R = 1, C = 1, nsplit = 1, iters_done = 0;
+  float t_loss = 0.f, t_reg = 0.f;
+  std::vector<int64_t> row_start, row_size, row_slot, col_start, col_size, col_slot, foff;
+
+  // ---- device memory (owned)
+  std::vector<DevBuf> bufs;
+  int32_t *row_of_slot = nullptr, *feat_of_slot = nullptr, *slot_of_feat = nullptr;
+  int64_t *d_row_slot = nullptr, *d_row_size = nullptr, *d_col_slot = nullptr, *d_col_size = nullptr;
+  int64_t* d_zero = nullptr;  // {0}: row block table of a query batch
+  float *X32 = nullptr, *Gt32 = nullptr, *bias = nullptr, *Y = nullptr;
+  __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr, *Ghi = nullptr, *Glo = nullptr;
+  float *O = nullptr, *Obar = nullptr, *nu = nullptr, *Dl = nullptr, *Op = nullptr, *V32 = nullptr;
+  __nv_bfloat16 *VThi = nullptr, *VTlo = nullptr, *WThi = nullptr, *WTlo = nullptr, *WbThi = nullptr,
+                *WbTlo = nullptr;
+  float *W = nullptr, *Wbar = nullptr, *mu = nullptr, *What = nullptr, *muij = nullptr, *rhs = nullptr,
+        *xtmp = nullptr, *Rpart = nullptr;
+  float *Q32 = nullptr, *H32 = nullptr;
+  GemmDesc* gdesc = nullptr;  // 3 x R*C
+  double* partials = nullptr;
+  int* flag = nullptr;
+  float *nu_old = nullptr, *Obar_old = nullptr, *mu_old = nullptr, *Wbar_old = nullptr, *muij_old = nullptr;
+  // grow-only scratch for queries and staging
+  DevBuf scratch;
+  // profiling: phase events per iteration, accumulated at the end of a solve call
+  bool profiling = false;
+  rff_admm_profile prof{};
+  std::vector<cudaEvent_t> ev;
+  int64_t launches = 0;
+
+  ~rff_admm_s() {
+    for (auto e : ev) cudaEventDestroy(e);
+    free_all();
+    if (scratch.p) cudaFree(scratch.p);
+    if (own_stream && st) cudaStreamDestroy(st);
+  }
+  void free_all() {
+    for (auto& b : bufs)
+      if (b.p) cudaFree(b.p);
+    bufs.clear();
+  }
+  rff_status fail(rff_status s, const std::string& msg) {
+    err = msg;
+    return s;
+  }
+  rff_status cuda_fail(cudaError_t e, const char* what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return RFF_ECUDA;
+  }
+  bool split_path() const { return p.prec == RFF_PREC_SPLIT_BF16; }
+};
+
+namespace rff {
+TcView tc_view(const rff_admm_s& s);
+}
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return h->cuda_fail(e_, #call); \
+  } while (0)
+
+namespace {
+
+rff_status check_params(const rff_admm_params* p, std::string& why) {
+  if (!p) { why = "params is NULL"; return RFF_EINVAL; }
+  if (p->loss < 0 || p->loss > 3) { why = "unknown loss"; return RFF_EINVAL; }
+  if (p->reg < 0 || p->reg > 1) { why = "unknown regulariser"; return RFF_EINVAL; }
+  if (p->prec < 0 || p->prec > 1) { why = "unknown precision"; return RFF_EINVAL; }
+  if (p->rho_scale < 0 || p->rho_scale > 1) { why = "unknown rho scale"; return RFF_EINVAL; }
+  if (!(p->lambda > 0) || !std::isfinite(p->lambda)) { why = "lambda must be > 0"; return RFF_EINVAL; }
+  if (!(p->sigma > 0) || !std::isfinite(p->sigma)) { why = "sigma must be > 0"; return RFF_EINVAL; }
+  if (!(p->rho > 0) || !std::isfinite(p->rho)) { why = "rho must be > 0"; return RFF_EINVAL; }
+  if (p->D < 1 || p->D > (int64_t)1 << 30) { why = "D out of range"; return RFF_EINVAL; }
+  if (p->R < 1 || p->C < 1 || p->C > p->D) { why = "bad block grid"; return RFF_EINVAL; }
+  if (p->m < 1 || p->m > 256) { why = "m must be in [1, 256]"; return RFF_EINVAL; }
+  if (p->loss == RFF_LOSS_LOGISTIC && p->m != 1) { why = "binary logistic loss needs m = 1"; return RFF_EINVAL; }
+  if (p->newton_iters < 0 || p->newton_iters > 100) { why = "newton_iters out of range"; return RFF_EINVAL; }
+  return RFF_OK;
+}
+
+void partition(int64_t total, int parts, std::vector<int64_t>& start, std::vector<int64_t>& size) {
+  start.assign(parts, 0);
+  size.assign(parts, 0);
+  const int64_t q = total / parts, rem = total % parts;
+  int64_t s = 0;
+  for (int i = 0; i < parts; ++i) {
+    size[i] = q + (i < rem ? 1 : 0);
+    start[i] = s;
+    s += size[i];
+  }
+}
+
+template <typename T>
+rff_status dalloc(rff_admm_t h, T*& ptr, size_t count) {
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return h->fail(RFF_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  h->bufs.push_back(DevBuf{p, bytes});
+  ptr = static_cast<T*>(p);
+  return RFF_OK;
+}
+
+rff_status ensure_scratch(rff_admm_t h, size_t bytes) {
+  if (h->scratch.bytes >= bytes) return RFF_OK;
+  if (h->scratch.p) {
+    cudaStreamSynchronize(h->st);
+    cudaFree(h->scratch.p);
+    h->scratch = DevBuf{};
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return h->fail(RFF_ENOMEM, "scratch allocation failed");
+  }
+  h->scratch = DevBuf{p, bytes};
+  return RFF_OK;
+}
+
+// bytes of device memory the working set needs (checked before allocating)
+size_t working_set_bytes(const rff_admm_s& s) {
+  const size_t f = sizeof(float), b2 = 2;
+  size_t t = 0;
+  t += (size_t)s.nslots * 4 + (size_t)s.fslots * 4 * 2;
+  if (s.split_path()) t += (size_t)s.nslots * s.dld * b2 * 2 + (size_t)s.fslots * s.dld * b2 * 2;
+  else t += (size_t)s.nslots * s.dld * f + (size_t)s.fslots * s.dld * f;
+  t += (size_t)s.fslots * f;
+  t += (size_t)s.nslots * s.mpad * f * (5 + 2);                 // Y, O, Obar, nu, Dl, nu_old, Obar_old
+  t += (size_t)s.C * s.nslots * s.mpad * f * 2;                 // Op, V32
+  if (s.split_path()) t += (size_t)s.C * s.nslots * s.mpad * b2 * 2;
+  t += (size_t)s.fslots * s.mpad * f * 5;                       // W, Wbar, mu, mu_old, Wbar_old
+  t += (size_t)s.R * s.fslots * s.mpad * f * (5 + s.nsplit);    // What, muij, rhs, xtmp, muij_old, Rpart
+  if (s.split_path()) t += (size_t)s.R * s.fslots * s.mpad * b2 * 2 + (size_t)s.fslots * s.mpad * b2 * 2;
+  size_t fac = 0;
+  for (int j = 0; j < s.C; ++j) fac += (size_t)s.col_size[j] * s.col_size[j];
+  t += fac * s.R * f * 2;
+  return t + (64u << 20);
+}
+
+}  // namespace
+
+extern "C" {
+
+rff_status rff_admm_create(const rff_admm_params* params, void* stream, rff_admm_t* out) {
+  if (!out) return RFF_EINVAL;
+  *out = nullptr;
+  std::string why;
+  rff_status s = check_params(params, why);
+  if (s != RFF_OK) return s;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return RFF_ECUDA;
+  }
+  rff_admm_t h = new rff_admm_s();
+  h->p = *params;
+  if (h->p.newton_iters == 0) h->p.newton_iters = 8;
+  if (stream) {
+    h->st = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return RFF_ECUDA;
+    }
+    h->own_stream = true;
+  }
+  *out = h;
+  return RFF_OK;
+}
+
+rff_status rff_admm_set_profiling(rff_admm_t h, int enable) {
+  if (!h) return RFF_EINVAL;
+  h->profiling = enable != 0;
+  h->prof = rff_admm_profile{};
+  h->launches = 0;
+  return RFF_OK;
+}
+
+rff_status rff_admm_get_profile(rff_admm_t h, rff_admm_profile* out) {
+  if (!h || !out) return RFF_EINVAL;
+  *out = h->prof;
+  out->launches = h->launches;
+  return RFF_OK;
+}
+
+void rff_admm_destroy(rff_admm_t h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  delete h;
+}
+
+const char* rff_admm_last_error(rff_admm_t h) { return h ? h->err.c_str() : "null handle"; }
+
+rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int64_t n, int64_t d,
+                             int is_device_ptr) {
+  if (!h) return RFF_EINVAL;
+  h->err.clear();
+  if (!X || !Yin) return h->fail(RFF_EINVAL, "X or Y is NULL");
+  if (n < h->p.R || d < 1 || n > ((int64_t)1 << 31) - 1) return h->fail(RFF_EINVAL, "need R <= n < 2^31 and d >= 1");
+  CK(cudaStreamSynchronize(h->st));
+  h->free_all();
+  h->has_data = h->factored = false;
+  h->iters_done = 0;
+
+  auto& s = *h;
+  s.n = n;
+  s.d = d;
+  s.dld = round_up(d, 64);
+  s.m = s.p.m;
+  s.mpad = round_up(s.m, 16);
+  s.D = s.p.D;
+  s.R = s.p.R;
+  s.C = s.p.C;
+  partition(n, s.R, s.row_start, s.row_size);
+  partition(s.D, s.C, s.col_start, s.col_size);
+  s.row_slot.assign(s.R, 0);
+  s.col_slot.assign(s.C, 0);
+  int64_t acc = 0;
+  for (int i = 0; i < s.R; ++i) { s.row_slot[i] = acc; acc += round_up(s.row_size[i], SLOT); }
+  s.nslots = acc;
+  acc = 0;
+  for (int j = 0; j < s.C; ++j) { s.col_slot[j] = acc; acc += round_up(s.col_size[j], SLOT); }
+  s.fslots = acc;
+  s.foff.assign((size_t)s.R * s.C + 1, 0);
+  for (int i = 0; i < s.R; ++i)
+    for (int j = 0; j < s.C; ++j)
+      s.foff[(size_t)i * s.C + j + 1] = s.foff[(size_t)i * s.C + j] + s.col_size[j] * s.col_size[j];
+  const double nn = (double)n;
+  if (s.p.rho_scale == RFF_RHO_SUM) {
+    s.t_loss = (float)(1.0 / s.p.rho);
+    s.t_reg = (float)(nn * s.p.lambda / s.p.rho);
+  } else {
+    s.t_loss = (float)(1.0 / (nn * s.p.rho));
+    s.t_reg = (float)(s.p.lambda / s.p.rho);
+  }
+  // pass-1 row splits: enough CTAs for two waves on the device
+  {
+    int nsm = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tile = s.split_path() ? 128 : 64;
+    const int64_t ftiles = s.fslots / tile;
+    int64_t min_rows = n;
+    for (int i = 0; i < s.R; ++i) min_rows = std::min(min_rows, s.row_size[i]);
+    const int64_t want = ceil_div(2 * (int64_t)nsm, ftiles * s.R);
+    s.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, ceil_div(min_rows, tile), 64}));
+  }
+
+  // memory check before any allocation
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  const size_t need = working_set_bytes(s);
+  if (need > fr) {
+    return h->fail(RFF_ENOMEM, "working set " + std::to_string(need >> 20) + " MiB exceeds free device memory " +
+                                   std::to_string(fr >> 20) + " MiB");
+  }
+
+  rff_status st = RFF_OK;
+#define AL(ptr, cnt) \
+  if ((st = dalloc(h, ptr, (size_t)(cnt))) != RFF_OK) { h->free_all(); return st; }
+  AL(s.row_of_slot, s.nslots);
+  AL(s.feat_of_slot, s.fslots);
+  AL(s.slot_of_feat, s.D);
+  AL(s.d_row_slot, s.R);
+  AL(s.d_row_size, s.R);
+  AL(s.d_col_slot, s.C);
+  AL(s.d_col_size, s.C);
+  AL(s.d_zero, 2);
+  if (s.split_path()) {
+    AL(s.Xhi, s.nslots * s.dld);
+    AL(s.Xlo, s.nslots * s.dld);
+    AL(s.Ghi, s.fslots * s.dld);
+    AL(s.Glo, s.fslots * s.dld);
+    AL(s.VThi, (int64_t)s.C * s.mpad * s.nslots);
+    AL(s.VTlo, (int64_t)s.C * s.mpad * s.nslots);
+    AL(s.WThi, (int64_t)s.R * s.mpad * s.fslots);
+    AL(s.WTlo, (int64_t)s.R * s.mpad * s.fslots);
+    AL(s.WbThi, s.mpad * s.fslots);
+    AL(s.WbTlo, s.mpad * s.fslots);
+  } else {
+    AL(s.X32, s.nslots * s.dld);
+    AL(s.Gt32, s.fslots * s.dld);
+  }
+  AL(s.bias, s.fslots);
+  AL(s.Y, s.nslots * s.mpad);
+  AL(s.O, s.nslots * s.mpad);
+  AL(s.Obar, s.nslots * s.mpad);
+  AL(s.nu, s.nslots * s.mpad);
+  AL(s.Dl, s.nslots * s.mpad);
+  AL(s.nu_old, s.nslots * s.mpad);
+  AL(s.Obar_old, s.nslots * s.mpad);
+  AL(s.Op, (int64_t)s.C * s.nslots * s.mpad);
+  AL(s.V32, (int64_t)s.C * s.nslots * s.mpad);
+  AL(s.W, s.fslots * s.mpad);
+  AL(s.Wbar, s.fslots * s.mpad);
+  AL(s.mu, s.fslots * s.mpad);
+  AL(s.mu_old, s.fslots * s.mpad);
+  AL(s.Wbar_old, s.fslots * s.mpad);
+  AL(s.What, (int64_t)s.R * s.fslots * s.mpad);
+  AL(s.muij, (int64_t)s.R * s.fslots * s.mpad);
+  AL(s.muij_old, (int64_t)s.R * s.fslots * s.mpad);
+  AL(s.rhs, (int64_t)s.R * s.fslots * s.mpad);
+  AL(s.xtmp, (int64_t)s.R * s.fslots * s.mpad);
+  AL(s.Rpart, (int64_t)s.nsplit * s.R * s.fslots * s.mpad);
+  AL(s.Q32, s.foff.back());
+  AL(s.H32, s.foff.back());
+  AL(s.gdesc, 3 * s.R * s.C);
+  AL(s.partials, 1024);
+  AL(s.flag, 4);
+#undef AL
+
+  // slot tables
+  std::vector<int32_t> ros(s.nslots, -1), fos(s.fslots, -1), sof(s.D, 0);
+  for (int i = 0; i < s.R; ++i)
+    for (int64_t r = 0; r < s.row_size[i]; ++r) ros[s.row_slot[i] + r] = (int32_t)(s.row_start[i] + r);
+  for (int j = 0; j < s.C; ++j)
+    for (int64_t k = 0; k < s.col_size[j]; ++k) {
+      fos[s.col_slot[j] + k] = (int32_t)(s.col_start[j] + k);
+      sof[s.col_start[j] + k] = (int32_t)(s.col_slot[j] + k);
+    }
+  CK(cudaMemcpyAsync(s.row_of_slot, ros.data(), ros.size() * 4, cudaMemcpyHostToDevice, s.st));
+  CK(cudaMemcpyAsync(s.feat_of_slot, fos.data(), fos.size() * 4, cudaMemcpyHostToDevice, s.st));
+  CK(cudaMemcpyAsync(s.slot_of_feat, sof.data(), sof.size() * 4, cudaMemcpyHostToDevice, s.st));
+  CK(cudaMemcpyAsync(s.d_row_slot, s.row_slot.data(), s.R * 8, cudaMemcpyHostToDevice, s.st));
+  CK(cudaMemcpyAsync(s.d_row_size, s.row_size.data(), s.R * 8, cudaMemcpyHostToDevice, s.st));
+  CK(cudaMemcpyAsync(s.d_col_slot, s.col_slot.data(), s.C * 8, cudaMemcpyHostToDevice, s.st));
+  CK(cudaMemcpyAsync(s.d_col_size, s.col_size.data(), s.C * 8, cudaMemcpyHostToDevice, s.st));
+  CK(cudaMemsetAsync(s.d_zero, 0, 16, s.st));
+
+  // data: stage (device), validate, scatter into slots
+  const size_t xb = (size_t)n * d * 4, yb = (size_t)n * s.m * 4;
+  if ((st = ensure_scratch(h, xb + yb + 256)) != RFF_OK) { h->free_all(); return st; }
+  float* sx = static_cast<float*>(h->scratch.p);
+  float* sy = sx + round_up((int64_t)n * d, 64);
+  const cudaMemcpyKind kind = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(sx, X, xb, kind, s.st));
+  CK(cudaMemcpyAsync(sy, Yin, yb, kind, s.st));
+  CK(cudaMemsetAsync(s.flag, 0, 16, s.st));
+  CK(launch_finite_check(sx, (int64_t)n * d, 0, s.flag, s.st));
+  const int pm1 = (s.p.loss == RFF_LOSS_HINGE || s.p.loss == RFF_LOSS_LOGISTIC) ? 1 : 0;
+  CK(launch_finite_check(sy, (int64_t)n * s.m, pm1, s.flag + 1, s.st));
+  int fl[2] = {0, 0};
+  CK(cudaMemcpyAsync(fl, s.flag, 8, cudaMemcpyDeviceToHost, s.st));
+  CK(cudaStreamSynchronize(s.st));
+  if (fl[0]) { h->free_all(); return h->fail(RFF_EINVAL, "X contains NaN or Inf"); }
+  if (fl[1] & 1) { h->free_all(); return h->fail(RFF_EINVAL, "Y contains NaN or Inf"); }
+  if (fl[1] & 2) { h->free_all(); return h->fail(RFF_EINVAL, "hinge/logistic targets must be -1 or +1"); }
+
+  float* Xs = s.X32;
+  if (s.split_path()) {
+    // the float32 slot copy lives in scratch only long enough to split it
+    if ((st = ensure_scratch(h, xb + yb + (size_t)s.nslots * s.dld * 4 + 512)) != RFF_OK) { h->free_all(); return st; }
+    sx = static_cast<float*>(h->scratch.p);
+    sy = sx + round_up((int64_t)n * d, 64);
+    CK(cudaMemcpyAsync(sx, X, xb, kind, s.st));
+    CK(cudaMemcpyAsync(sy, Yin, yb, kind, s.st));
+    Xs = sy + round_up((int64_t)n * s.m, 64);
+  }
+  CK(launch_gather_rows(sx, d, d, s.row_of_slot, s.nslots, Xs, s.dld, s.st));
+  CK(launch_gather_rows(sy, s.m, s.m, s.row_of_slot, s.nslots, s.Y, s.mpad, s.st));
+  if (s.split_path()) CK(launch_split_bf16(Xs, s.nslots * s.dld, s.Xhi, s.Xlo, s.st));
+
+  // ADMM state: all zero (Sec. 3: "initialize to zero"), then O = prox(Obar - nu) = prox(0)
+  const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
+  for (float* b : {s.O, s.Obar, s.nu, s.Dl}) CK(cudaMemsetAsync(b, 0, rowb, s.st));
+  CK(cudaMemsetAsync(s.V32, 0, rowb * s.C, s.st));
+  CK(cudaMemsetAsync(s.Op, 0, rowb * s.C, s.st));
+  for (float* b : {s.W, s.Wbar, s.mu}) CK(cudaMemsetAsync(b, 0, colb, s.st));
+  for (float* b : {s.What, s.muij, s.rhs, s.xtmp}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
+  CK(cudaMemsetAsync(s.Rpart, 0, colb * s.R * s.nsplit, s.st));
+  if (s.split_path()) {
+    CK(cudaMemsetAsync(s.VThi, 0, rowb / 2 * s.C, s.st));
+    CK(cudaMemsetAsync(s.VTlo, 0, rowb / 2 * s.C, s.st));
+    CK(cudaMemsetAsync(s.WThi, 0, colb / 2 * s.R, s.st));
+    CK(cudaMemsetAsync(s.WTlo, 0, colb / 2 * s.R, s.st));
+  }
+  CK(launch_prox_loss(s.p.loss, s.O, s.Y, s.nslots, (int)s.m, s.mpad, s.t_loss, s.p.newton_iters, s.O, s.st));
+  // zero O on padding rows (prox(0) with y = 0 is not zero for the squared loss only if y != 0; y = 0 there)
+  CK(cudaStreamSynchronize(s.st));
+  h->has_data = true;
+  return RFF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ set-up
+namespace {
+
+rff_status setup_factors(rff_admm_t h) {
+  auto& s = *h;
+  const float scale = (float)std::sqrt(2.0 / (double)s.D);
+  // random features: G and b from Philox (Sec. 4)
+  CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, s.Ghi, s.Glo, s.bias,
+                         s.st));
+  // Gram matrices H_ij = I + Z_ij^T Z_ij (eq. (cache)), in FP64, batched by memory
+  int64_t smax = 0;
+  for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
+  const int64_t nblocks = (int64_t)s.R * s.C;
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  const size_t per_block = (size_t)smax * smax * 8 * 2;
+  const int64_t chunk_rows = std::min<int64_t>(32768, round_up(*std::max_element(s.row_size.begin(), s.row_size.end()), 64));
+  const size_t zbytes = (size_t)chunk_rows * smax * 4;
+  size_t budget = (size_t)(fr * 0.6);
+  budget = budget > zbytes + (256u << 20) ? budget - zbytes - (256u << 20) : 0;
+  int64_t batch = std::max<int64_t>(1, std::min<int64_t>(nblocks, (int64_t)(budget / std::max<size_t>(per_block + factor_scratch_bytes(1, (int)smax), 1))));
+  const size_t need = (size_t)batch * per_block + zbytes + factor_scratch_bytes((int)batch, (int)smax) + (size_t)batch * 4 + 4096;
+  rff_status rs = ensure_scratch(h, need);
+  if (rs != RFF_OK) return rs;
+  char* base = static_cast<char*>(s.scratch.p);
+  double* H64 = reinterpret_cast<double*>(base);
+  double* Q64 = H64 + batch * smax * smax;
+  float* Zc = reinterpret_cast<float*>(Q64 + batch * smax * smax);
+  int32_t* info = reinterpret_cast<int32_t*>(Zc + chunk_rows * smax);
+  void* fscr = reinterpret_cast<char*>(info) + round_up(batch * 4, 256);
+
+  for (int64_t b0 = 0; b0 < nblocks; b0 += batch) {
+    const int64_t nb = std::min(batch, nblocks - b0);
+    std::vector<MatJob> jobs;
+    CK(cudaMemsetAsync(info, 0, nb * 4, s.st));
+    for (int64_t bb = 0; bb < nb; ++bb) {
+      const int64_t blk = b0 + bb;
+      const int i = (int)(blk / s.C), j = (int)(blk % s.C);
+      const int64_t sj = s.col_size[j];
+      double* Hb = H64 + bb * smax * smax;
+      double* Qb = Q64 + bb * smax * smax;
+      CK(cudaMemsetAsync(Hb, 0, sj * sj * 8, s.st));
+      for (int64_t r = 0; r < s.row_size[i]; r += chunk_rows) {
+        const int64_t nr = std::min(chunk_rows, s.row_size[i] - r);
+        if (s.split_path()) {
+          CK(tc_write_z(tc_view(s), s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj));
+        } else {
+          ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, scale, s.row_of_slot, s.feat_of_slot,
+                   s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj};
+          CK(launch_write_z_simt(za, s.st));
+        }
+        CK(launch_gram_f32_to_f64(Zc, sj, nr, sj, Hb, sj, s.st));
+      }
+      CK(launch_add_identity_and_mirror(Hb, sj, sj, s.st));
+      CK(launch_convert_f64_f32(Hb, s.H32 + s.foff[blk], sj * sj, s.st));
+      CK(cudaMemsetAsync(Qb, 0, sj * sj * 8, s.st));
+      CK(launch_set_diag(Qb, sj, sj, 1.0, s.st));
+      jobs.push_back(MatJob{Hb, sj, (int)sj, Qb, sj, info + bb});
+    }
+    CK(factor_and_invert_f64(jobs, true, fscr, s.st));
+    for (int64_t bb = 0; bb < nb; ++bb) {
+      const int64_t blk = b0 + bb;
+      const int64_t sj = s.col_size[blk % s.C];
+      CK(launch_convert_f64_f32(Q64 + bb * smax * smax, s.Q32 + s.foff[blk], sj * sj, s.st));
+    }
+    std::vector<int32_t> hinfo(nb);
+    CK(cudaMemcpyAsync(hinfo.data(), info, nb * 4, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaStreamSynchronize(s.st));
+    for (int64_t bb = 0; bb < nb; ++bb)
+      if (hinfo[bb] != 0)
+        return h->fail(RFF_ENUMERIC, "Gram matrix of block " + std::to_string(b0 + bb) +
+                                         " not positive definite at column " + std::to_string(hinfo[bb] - 1));
+  }
+  // iteration GEMM descriptors: x = Q rhs; r = rhs - H x; x += Q r
+  std::vector<GemmDesc> g(3 * nblocks);
+  for (int i = 0; i < s.R; ++i)
+    for (int j = 0; j < s.C; ++j) {
+      const int64_t blk = (int64_t)i * s.C + j, sj = s.col_size[j];
+      const int64_t off = ((int64_t)i * s.fslots + s.col_slot[j]) * s.mpad;
+      float* Qb = s.Q32 + s.foff[blk];
+      float* Hb = s.H32 + s.foff[blk];
+      g[blk] = GemmDesc{Qb, s.rhs + off, nullptr, s.What + off, (int)sj, (int)s.mpad, (int)sj, sj, s.mpad, 0, s.mpad};
+      g[nblocks + blk] = GemmDesc{Hb, s.What + off, s.rhs + off, s.xtmp + off, (int)sj, (int)s.mpad, (int)sj, sj,
+                                  s.mpad, s.mpad, s.mpad};
+      g[2 * nblocks + blk] = GemmDesc{Qb, s.xtmp + off, s.What + off, s.What + off, (int)sj, (int)s.mpad, (int)sj, sj,
+                                      s.mpad, s.mpad, s.mpad};
+    }
+  CK(cudaMemcpyAsync(s.gdesc, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, s.st));
+  CK(cudaStreamSynchronize(s.st));
+  s.factored = true;
+  return RFF_OK;
+}
+
+// ------------------------------------------------------------------ iteration
+PassArgs base_pass_args(const rff_admm_s& s) {
+  PassArgs a{};
+  a.X = s.X32;
+  a.ldx = s.dld;
+  a.Gt = s.Gt32;
+  a.ldg = s.dld;
+  a.K = (int)s.dld;
+  a.bias = s.bias;
+  a.scale = (float)std::sqrt(2.0 / (double)s.D);
+  a.row_ok = s.row_of_slot;
+  a.feat_ok = s.feat_of_slot;
+  a.row_slot = s.d_row_slot;
+  a.row_size = s.d_row_size;
+  a.R = s.R;
+  a.col_slot = s.d_col_slot;
+  a.col_size = s.d_col_size;
+  a.C = s.C;
+  a.mpad = (int)s.mpad;
+  a.nsplit = s.nsplit;
+  return a;
+}
+
+// phase boundaries of one iteration; with profiling on, events k*7 .. k*7+6
+rff_status mark(rff_admm_t h, int k, int phase) {
+  if (!h->profiling) return RFF_OK;
+  CK(cudaEventRecord(h->ev[(size_t)k * 7 + phase], h->st));
+  return RFF_OK;
+}
+
+rff_status iterate(rff_admm_t h, int k) {
+  auto& s = *h;
+  const int64_t nfe = s.fslots * s.mpad;
+  const int64_t nblocks = (int64_t)s.R * s.C;
+  int64_t smax = 0;
+  for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
+  rff_status r;
+  if ((r = mark(h, k, 0)) != RFF_OK) return r;
+  // W_j <- prox_{(n lam / rho) r}(Wbar_j - mu_j)
+  CK(launch_prox_reg(s.p.reg, s.Wbar, s.mu, nfe, s.t_reg, s.W, s.st));
+  if ((r = mark(h, k, 1)) != RFF_OK) return r;
+  // pass 1: R_ij = Z_ij^T V_ij,  V_ij = Obar_ij + nu_i
+  PassArgs a = base_pass_args(s);
+  if (s.split_path()) {
+    CK(tc_pass1(tc_view(s), s.Rpart));
+  } else {
+    a.M = s.V32;
+    a.m_block_stride = s.nslots * s.mpad;
+    a.out = s.Rpart;
+    a.out_block_stride = s.fslots * s.mpad;
+    CK(launch_pass1_simt(a, s.fslots, s.st));
+  }
+  if ((r = mark(h, k, 2)) != RFF_OK) return r;
+  // graph projection, eq. (gpWij): W'_ij = Q_ij (Wbar_j - mu'_ij + R_ij), one refinement step with H_ij
+  CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st));
+  CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st));
+  CK(launch_gemm_f32_nn(s.gdesc + nblocks, (int)nblocks, (int)smax, (int)s.mpad, -1.f, 1.f, s.st));
+  CK(launch_gemm_f32_nn(s.gdesc + 2 * nblocks, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 1.f, s.st));
+  if ((r = mark(h, k, 3)) != RFF_OK) return r;
+  // pass 2: O'_ij = Z_ij W'_ij (eq. (gpOij))
+  if (s.split_path()) {
+    CK(launch_transpose_split(s.What, s.fslots, (int)s.mpad, s.R, s.fslots * s.mpad, s.WThi, s.WTlo, s.fslots,
+                              s.mpad * s.fslots, s.st));
+    CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1));
+  } else {
+    a.M = s.What;
+    a.m_block_stride = s.fslots * s.mpad;
+    a.out = s.Op;
+    a.out_block_stride = s.nslots * s.mpad;
+    a.per_block = 1;
+    CK(launch_pass2_simt(a, s.nslots, s.st));
+  }
+  if ((r = mark(h, k, 4)) != RFF_OK) return r;
+  // exchange, nu update, next loss prox, next V_ij
+  RowEpiArgs e{s.Op, s.O, s.Obar, s.nu, s.Dl, s.Y, s.V32, nullptr, nullptr, s.row_of_slot, s.nslots,
+               s.C, (int)s.m, (int)s.mpad, s.p.loss, s.p.newton_iters, s.t_loss};
+  CK(launch_row_epilogue(e, s.st));
+  if (s.split_path())
+    CK(launch_transpose_split(s.V32, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
+                              s.mpad * s.nslots, s.st));
+  if ((r = mark(h, k, 5)) != RFF_OK) return r;
+  // averaging and dual updates
+  CK(launch_avg_dual(s.W, s.What, s.R, nfe, s.Wbar, s.mu, s.muij, s.st));
+  if ((r = mark(h, k, 6)) != RFF_OK) return r;
+  s.launches += s.split_path() ? 11 : 9;
+  return RFF_OK;
+}
+
+rff_status sum_partials(rff_admm_t h, double& out) {
+  std::vector<double> hp(1024);
+  CK(cudaMemcpyAsync(hp.data(), h->partials, 1024 * 8, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  double sacc = 0.0;
+  for (double v : hp) sacc += v;
+  out = sacc;
+  return RFF_OK;
+}
+
+rff_status sqdiff(rff_admm_t h, const float* a, const float* b, int64_t n, double& out) {
+  CK(launch_sqdiff_partials(a, b, n, h->partials, 1024, h->st));
+  return sum_partials(h, out);
+}
+
+// scores S (slots x m_pad) = Z(rows) Wbar, on the handle's training rows or a query batch
+rff_status scores_pass(rff_admm_t h, const float* Xrows32, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl,
+                       int64_t nrows, const int32_t* row_ok, float* out) {
+  auto& s = *h;
+  if (s.split_path()) {
+    CK(launch_transpose_split(s.Wbar, s.fslots, (int)s.mpad, 1, 0, s.WbThi, s.WbTlo, s.fslots, 0, s.st));
+    CK(tc_predict(tc_view(s), Xh, Xl, nrows, s.WbThi, s.WbTlo, out));
+  } else {
+    PassArgs a = base_pass_args(s);
+    a.X = Xrows32;
+    a.row_ok = row_ok;
+    a.row_slot = s.d_zero;
+    a.R = 1;
+    a.M = s.Wbar;
+    a.m_block_stride = 0;
+    a.out = out;
+    a.out_block_stride = 0;
+    a.per_block = 0;
+    CK(launch_pass2_simt(a, nrows, s.st));
+  }
+  return RFF_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ tc.h glue used by tc.cu
+namespace rff {
+TcView tc_view(const rff_admm_s& s) {
+  TcView v{};
+  v.Xhi = s.Xhi; v.Xlo = s.Xlo; v.Ghi = s.Ghi; v.Glo = s.Glo;
+  v.VThi = s.VThi; v.VTlo = s.VTlo;
+  v.bias = s.bias; v.row_ok = s.row_of_slot; v.feat_ok = s.feat_of_slot;
+  v.nslots = s.nslots; v.fslots = s.fslots; v.dld = s.dld; v.mpad = s.mpad;
+  v.R = s.R; v.C = s.C; v.nsplit = s.nsplit;
+  v.row_slot = s.row_slot.data(); v.row_size = s.row_size.data();
+  v.col_slot = s.col_slot.data(); v.col_size = s.col_size.data();
+  v.scale = (float)std::sqrt(2.0 / (double)s.D);
+  v.st = s.st;
+  return v;
+}
+}  // namespace rff
+
+extern "C" {
+
+rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats) {
+  if (!h) return RFF_EINVAL;
+  h->err.clear();
+  if (!h->has_data) return h->fail(RFF_ENOTREADY, "no data: call rff_admm_set_data first");
+  if (iters < 0) return h->fail(RFF_EINVAL, "iters must be >= 0");
+  auto& s = *h;
+  cudaEvent_t e0, e1, e2;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventCreate(&e2));
+  CK(cudaEventRecord(e0, s.st));
+  if (!s.factored) {
+    rff_status r = setup_factors(h);
+    if (r != RFF_OK) return r;
+  }
+  CK(cudaEventRecord(e1, s.st));
+  const int64_t rowb = s.nslots * s.mpad * 4, colb = s.fslots * s.mpad * 4;
+  if (s.profiling && (size_t)iters * 7 > s.ev.size()) {
+    const size_t old = s.ev.size();
+    s.ev.resize((size_t)iters * 7);
+    for (size_t e = old; e < s.ev.size(); ++e) CK(cudaEventCreate(&s.ev[e]));
+  }
+  for (int k = 0; k < iters; ++k) {
+    if (stats && k == iters - 1) {
+      CK(cudaMemcpyAsync(s.nu_old, s.nu, rowb, cudaMemcpyDeviceToDevice, s.st));
+      CK(cudaMemcpyAsync(s.Obar_old, s.Obar, rowb, cudaMemcpyDeviceToDevice, s.st));
+      CK(cudaMemcpyAsync(s.mu_old, s.mu, colb, cudaMemcpyDeviceToDevice, s.st));
+      CK(cudaMemcpyAsync(s.Wbar_old, s.Wbar, colb, cudaMemcpyDeviceToDevice, s.st));
+      CK(cudaMemcpyAsync(s.muij_old, s.muij, colb * s.R, cudaMemcpyDeviceToDevice, s.st));
+    }
+    rff_status r = iterate(h, k);
+    if (r != RFF_OK) return r;
+    s.iters_done++;
+  }
+  CK(cudaEventRecord(e2, s.st));
+  CK(cudaEventSynchronize(e2));
+  if (s.profiling) {
+    double* acc[6] = {&s.prof.ms_prox_reg, &s.prof.ms_pass1, &s.prof.ms_project, &s.prof.ms_pass2,
+                      &s.prof.ms_exchange, &s.prof.ms_average};
+    for (int k = 0; k < iters; ++k)
+      for (int ph = 0; ph < 6; ++ph) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, s.ev[(size_t)k * 7 + ph], s.ev[(size_t)k * 7 + ph + 1]));
+        *acc[ph] += ms;
+      }
+    s.prof.iters += iters;
+  }
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    float ms0 = 0, ms1 = 0;
+    cudaEventElapsedTime(&ms0, e0, e1);
+    cudaEventElapsedTime(&ms1, e1, e2);
+    stats->ms_setup = ms0;
+    stats->ms_iterations = ms1;
+    stats->iters_done = s.iters_done;
+    rff_status r;
+    if (iters > 0) {
+      // primal: |O - Obar| = |nu^k - nu^{k-1}|, |W - Wbar| = |mu^k - mu^{k-1}|, |W'_ij - Wbar| likewise
+      double a1, a2, a3, b1, b2;
+      if ((r = sqdiff(h, s.nu, s.nu_old, s.nslots * s.mpad, a1)) != RFF_OK) return r;
+      if ((r = sqdiff(h, s.mu, s.mu_old, s.fslots * s.mpad, a2)) != RFF_OK) return r;
+      if ((r = sqdiff(h, s.muij, s.muij_old, s.R * s.fslots * s.mpad, a3)) != RFF_OK) return r;
+      if ((r = sqdiff(h, s.Wbar, s.Wbar_old, s.fslots * s.mpad, b1)) != RFF_OK) return r;
+      if ((r = sqdiff(h, s.Obar, s.Obar_old, s.nslots * s.mpad, b2)) != RFF_OK) return r;
+      stats->primal_res = std::sqrt(a1 + a2 + a3);
+      stats->dual_res = s.p.rho * std::sqrt(b1 + b2);
+    }
+    // objective at Wbar: one scoring pass over the training rows into the O' buffer
+    if ((r = scores_pass(h, s.X32, s.Xhi, s.Xlo, s.nslots, s.row_of_slot, s.Op)) != RFF_OK) return r;
+    double loss = 0, reg = 0;
+    CK(launch_loss_partials(s.p.loss, s.Y, s.Op, s.row_of_slot, s.nslots, (int)s.m, (int)s.mpad, s.partials, 1024,
+                            s.st));
+    if ((r = sum_partials(h, loss)) != RFF_OK) return r;
+    CK(launch_reg_partials(s.p.reg, s.Wbar, s.fslots * s.mpad, s.partials, 1024, s.st));
+    if ((r = sum_partials(h, reg)) != RFF_OK) return r;
+    stats->objective = loss + (double)s.n * s.p.lambda * reg;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  return RFF_OK;
+}
+
+rff_status rff_admm_predict(rff_admm_t h, const float* Xq, int64_t q, float* scores, int is_device_ptr) {
+  if (!h) return RFF_EINVAL;
+  h->err.clear();
+  if (!h->has_data || !h->factored) return h->fail(RFF_ENOTREADY, "predict needs a solve first");
+  if (q < 0) return h->fail(RFF_EINVAL, "q < 0");
+  if (q == 0) return RFF_OK;
+  if (!Xq || !scores) return h->fail(RFF_EINVAL, "NULL pointer");
+  auto& s = *h;
+  const int64_t chunk = std::min<int64_t>(round_up(q, SLOT), 65536);
+  const size_t need = (size_t)chunk * s.d * 4 + (size_t)chunk * s.dld * 4 + (size_t)chunk * s.dld * 2 * 2 +
+                      (size_t)chunk * s.mpad * 4 + 4096;
+  rff_status r = ensure_scratch(h, need);
+  if (r != RFF_OK) return r;
+  float* stage = static_cast<float*>(s.scratch.p);
+  float* xq32 = stage + round_up(chunk * s.d, 64);
+  __nv_bfloat16* xh = reinterpret_cast<__nv_bfloat16*>(xq32 + chunk * s.dld);
+  __nv_bfloat16* xl = xh + chunk * s.dld;
+  float* sc = reinterpret_cast<float*>(xl + chunk * s.dld);
+  const cudaMemcpyKind kin = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int64_t q0 = 0; q0 < q; q0 += chunk) {
+    const int64_t nq = std::min(chunk, q - q0), nqp = round_up(nq, SLOT);
+    CK(cudaMemcpyAsync(stage, Xq + q0 * s.d, nq * s.d * 4, kin, s.st));
+    CK(cudaMemsetAsync(s.flag, 0, 4, s.st));
+    CK(launch_finite_check(stage, nq * s.d, 0, s.flag, s.st));
+    int fl = 0;
+    CK(cudaMemcpyAsync(&fl, s.flag, 4, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaStreamSynchronize(s.st));
+    if (fl) return h->fail(RFF_EINVAL, "queries contain NaN or Inf");
+    // rows q0..q0+nq into a slot-padded block (rows beyond nq are zero and discarded)
+    CK(cudaMemsetAsync(xq32, 0, nqp * s.dld * 4, s.st));
+    CK(launch_gather_rows(stage, s.d, s.d, nullptr, nq, xq32, s.dld, s.st));
+    if (s.split_path()) CK(launch_split_bf16(xq32, nqp * s.dld, xh, xl, s.st));
+    if ((r = scores_pass(h, xq32, xh, xl, nqp, nullptr, sc)) != RFF_OK) return r;
+    CK(cudaMemcpy2DAsync(scores + q0 * s.m, s.m * 4, sc, s.mpad * 4, s.m * 4, nq, kout, s.st));
+  }
+  CK(cudaStreamSynchronize(s.st));
+  return RFF_OK;
+}
+
+rff_status rff_admm_get_weights(rff_admm_t h, float* Wout, int is_device_ptr) {
+  if (!h) return RFF_EINVAL;
+  h->err.clear();
+  if (!h->has_data) return h->fail(RFF_ENOTREADY, "no data");
+  if (!Wout) return h->fail(RFF_EINVAL, "NULL pointer");
+  auto& s = *h;
+  rff_status r = ensure_scratch(h, (size_t)s.D * s.m * 4 + 256);
+  if (r != RFF_OK) return r;
+  float* tmp = static_cast<float*>(s.scratch.p);
+  CK(launch_gather_rows(s.Wbar, s.mpad, s.m, s.slot_of_feat, s.D, tmp, s.m, s.st));
+  CK(cudaMemcpyAsync(Wout, tmp, (size_t)s.D * s.m * 4, is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     s.st));
+  CK(cudaStreamSynchronize(s.st));
+  return RFF_OK;
+}
+
+// ---- checkpoint: header + raw slot-layout arrays
+namespace {
+struct StateHeader {
+  char magic[8];
+  uint32_t version, pad;
+  rff_admm_params p;
+  int64_t n, d, m, nslots, fslots;
+  int32_t R, C, iters_done, reserved;
+};
+struct Piece {
+  float* ptr;
+  size_t bytes;
+};
+std::vector<Piece> state_pieces(rff_admm_s& s) {
+  const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
+  return {{s.O, rowb},        {s.Obar, rowb},       {s.nu, rowb},   {s.Dl, rowb},   {s.V32, rowb * s.C},
+          {s.W, colb},        {s.Wbar, colb},       {s.mu, colb},   {s.What, colb * s.R}, {s.muij, colb * s.R}};
+}
+}  // namespace
+
+rff_status rff_admm_get_state(rff_admm_t h, void* buf, size_t* bytes) {
+  if (!h || !bytes) return RFF_EINVAL;
+  h->err.clear();
+  if (!h->has_data) return h->fail(RFF_ENOTREADY, "no data");
+  auto pieces = state_pieces(*h);
+  size_t need = sizeof(StateHeader);
+  for (auto& pc : pieces) need += pc.bytes;
+  if (!buf) {
+    *bytes = need;
+    return RFF_OK;
+  }
+  if (*bytes < need) return h->fail(RFF_EINVAL, "buffer too small");
+  StateHeader hd{};
+  memcpy(hd.magic, "RFFADMM", 8);
+  hd.version = 1;
+  hd.p = h->p;
+  hd.n = h->n; hd.d = h->d; hd.m = h->m; hd.nslots = h->nslots; hd.fslots = h->fslots;
+  hd.R = h->R; hd.C = h->C; hd.iters_done = h->iters_done;
+  char* out = static_cast<char*>(buf);
+  memcpy(out, &hd, sizeof(hd));
+  size_t off = sizeof(hd);
+  for (auto& pc : pieces) {
+    CK(cudaMemcpyAsync(out + off, pc.ptr, pc.bytes, cudaMemcpyDeviceToHost, h->st));
+    off += pc.bytes;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  *bytes = need;
+  return RFF_OK;
+}
+
+rff_status rff_admm_set_state(rff_admm_t h, const void* buf, size_t bytes) {
+  if (!h || !buf) return RFF_EINVAL;
+  h->err.clear();
+  if (!h->has_data) return h->fail(RFF_ENOTREADY, "no data");
+  auto& s = *h;
+  auto pieces = state_pieces(s);
+  size_t need = sizeof(StateHeader);
+  for (auto& pc : pieces) need += pc.bytes;
+  if (bytes != need) return h->fail(RFF_EINVAL, "state size mismatch");
+  StateHeader hd;
+  memcpy(&hd, buf, sizeof(hd));
+  if (memcmp(hd.magic, "RFFADMM", 8) != 0 || hd.version != 1) return h->fail(RFF_EINVAL, "not a state buffer");
+  if (hd.n != s.n || hd.d != s.d || hd.m != s.m || hd.R != s.R || hd.C != s.C || hd.p.D != s.p.D ||
+      hd.p.seed != s.p.seed || hd.p.loss != s.p.loss || hd.p.reg != s.p.reg || hd.p.prec != s.p.prec ||
+      hd.p.lambda != s.p.lambda || hd.p.sigma != s.p.sigma || hd.p.rho != s.p.rho ||
+      hd.p.rho_scale != s.p.rho_scale)
+    return h->fail(RFF_EINVAL, "state was written for other data, parameters or grid");
+  const char* in = static_cast<const char*>(buf);
+  size_t off = sizeof(hd);
+  for (auto& pc : pieces) {
+    CK(cudaMemcpyAsync(pc.ptr, in + off, pc.bytes, cudaMemcpyHostToDevice, s.st));
+    off += pc.bytes;
+  }
+  if (s.split_path())
+    CK(launch_transpose_split(s.V32, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
+                              s.mpad * s.nslots, s.st));
+  CK(cudaStreamSynchronize(s.st));
+  s.iters_done = hd.iters_done;
+  return RFF_OK;
+}
+
+// ------------------------------------------------------------------ step-level entry points
+rff_status rff_philox4x32_10(const uint32_t* ctr, uint64_t seed, int64_t n, uint32_t* out, void* stream) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) return RFF_EINVAL;
+  return launch_philox_raw(ctr, seed, n, out, static_cast<cudaStream_t>(stream)) == cudaSuccess ? RFF_OK
+                                                                                                : RFF_ECUDA;
+}
+
+rff_status rff_rff_params(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t k_hi, float* G, float* b,
+                          void* stream) {
+  if (d < 1 || k_lo < 0 || k_hi < k_lo || !(sigma > 0) || !G) return RFF_EINVAL;
+  return launch_params_rowmajor(seed, sigma, d, k_lo, k_hi - k_lo, G, b, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? RFF_OK
+             : RFF_ECUDA;
+}
+
+rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma, int64_t D, int64_t k_lo,
+                        int64_t k_hi, int32_t prec, float* Z, void* stream) {
+  if (n < 0 || d < 1 || D < 1 || k_lo < 0 || k_hi < k_lo || k_hi > D || !(sigma > 0) || prec < 0 || prec > 1)
+    return RFF_EINVAL;
+  if (n == 0 || k_hi == k_lo) return RFF_OK;
+  if (!X || !Z) return RFF_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t nf = k_hi - k_lo, dld = round_up(d, 64), np = round_up(n, SLOT), fp = round_up(nf, SLOT);
+  const size_t bytes = (size_t)np * dld * 4 + (size_t)fp * dld * 4 + (size_t)fp * 4 + (size_t)np * 4 + (size_t)fp * 4 +
+                       (size_t)(np + fp) * dld * 2 * 2 + 4096;
+  char* base = nullptr;
+  if (cudaMallocAsync((void**)&base, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return RFF_ENOMEM;
+  }
+  float* X32 = reinterpret_cast<float*>(base);
+  float* G32 = X32 + np * dld;
+  float* bias = G32 + fp * dld;
+  int32_t* rok = reinterpret_cast<int32_t*>(bias + fp);
+  int32_t* fok = rok + np;
+  __nv_bfloat16* Xh = reinterpret_cast<__nv_bfloat16*>(fok + fp);
+  __nv_bfloat16* Xl = Xh + np * dld;
+  __nv_bfloat16* Gh = Xl + np * dld;
+  __nv_bfloat16* Gl = Gh + fp * dld;
+  std::vector<int32_t> r(np), f(fp);
+  for (int64_t i = 0; i < np; ++i) r[i] = i < n ? (int32_t)i : -1;
+  for (int64_t i = 0; i < fp; ++i) f[i] = i < nf ? (int32_t)(k_lo + i) : -1;
+  cudaError_t e = cudaMemcpyAsync(rok, r.data(), np * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(fok, f.data(), fp * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_gather_rows(X, d, d, rok, np, X32, dld, st);
+  if (e == cudaSuccess)
+    e = launch_params_slots(seed, sigma, d, dld, fp, fok, G32, prec ? Gh : nullptr, prec ? Gl : nullptr, bias, st);
+  const float scale = (float)std::sqrt(2.0 / (double)D);
+  if (e == cudaSuccess) {
+    if (prec == RFF_PREC_FP32) {
+      ZArgs za{X32, dld, G32, dld, (int)dld, bias, scale, rok, fok, 0, n, 0, nf, Z, nf};
+      e = launch_write_z_simt(za, st);
+    } else {
+      e = launch_split_bf16(X32, np * dld, Xh, Xl, st);
+      if (e == cudaSuccess) {
+        const int64_t zero = 0;
+        TcView v{};
+        v.Xhi = Xh; v.Xlo = Xl; v.Ghi = Gh; v.Glo = Gl;
+        v.bias = bias; v.row_ok = rok; v.feat_ok = fok;
+        v.nslots = np; v.fslots = fp; v.dld = dld; v.mpad = 16; v.R = 1; v.C = 1; v.nsplit = 1;
+        v.row_slot = &zero; v.row_size = &n; v.col_slot = &zero; v.col_size = &nf;
+        v.scale = scale; v.st = st;
+        e = tc_write_z(v, 0, n, 0, nf, Z, nf);
+      }
+    }
+  }
+  cudaFreeAsync(base, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorNotSupported ? RFF_EINVAL : RFF_ECUDA;
+  }
+  return RFF_OK;
+}
+
+rff_status rff_prox_loss(int32_t loss, const float* V, const float* Yv, int64_t n, int32_t m, double t,
+                         int32_t newton_iters, float* out, void* stream) {
+  if (loss < 0 || loss > 3 || n < 0 || m < 1 || m > 256 || !(t >= 0) || (n > 0 && (!V || !Yv || !out)))
+    return RFF_EINVAL;
+  if (loss == RFF_LOSS_LOGISTIC && m != 1) return RFF_EINVAL;
+  return launch_prox_loss(loss, V, Yv, n, m, m, (float)t, newton_iters > 0 ? newton_iters : 8, out,
+                          static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? RFF_OK
+             : RFF_ECUDA;
+}
+
+rff_status rff_prox_reg(int32_t reg, const float* V, int64_t n, double tau, float* out, void* stream) {
+  if (reg < 0 || reg > 1 || n < 0 || !(tau >= 0) || (n > 0 && (!V || !out))) return RFF_EINVAL;
+  return launch_prox_reg(reg, V, nullptr, n, (float)tau, out, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? RFF_OK
+             : RFF_ECUDA;
+}
+
+rff_status rff_cholesky_f64(double* A, int32_t batch, int32_t s, int32_t* info, void* stream) {
+  if (batch < 0 || s < 1 || (batch > 0 && (!A || !info))) return RFF_EINVAL;
+  if (batch == 0) return RFF_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t need = factor_scratch_bytes(batch, s);
+  void* scr = nullptr;
+  if (cudaMallocAsync(&scr, need, st) != cudaSuccess) {
+    cudaGetLastError();
+    return RFF_ENOMEM;
+  }
+  std::vector<MatJob> jobs;
+  for (int b = 0; b < batch; ++b) jobs.push_back(MatJob{A + (size_t)b * s * s, s, s, nullptr, 0, info + b});
+  cudaError_t e = cudaMemsetAsync(info, 0, (size_t)batch * 4, st);
+  if (e == cudaSuccess) e = factor_and_invert_f64(jobs, false, scr, st);
+  cudaFreeAsync(scr, st);
+  return e == cudaSuccess ? RFF_OK : RFF_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// Shared device helpers of the GB300 solver: Philox4x32-10, the range-reduced
+// cosine of the feature map, BF16 hi/lo splitting, and the slot layout that
+// every kernel indexes.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rff {
+
+// Rows and features live in "slot" space: every row block i (Sec. 3, n_i rows)
+// starts at a multiple of SLOT, and so does every column block j (s_j features).
+// Tiles therefore never straddle two blocks, and every tensor-memory copy that
+// starts at a block boundary is 16-byte aligned.  Padding slots hold zeros.
+constexpr int SLOT = 128;
+
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline int64_t ceil_div(int64_t x, int64_t a) { return (x + a - 1) / a; }
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC'11: ten rounds of two 32x32->64-bit multiplies with Weyl-sequence key bumps.
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+  }
+  return c;
+}
+
+// u = ((w >> 8) + 0.5) 2^-24: 2^24 equally spaced points strictly inside (0, 1),
+// exact in float64.
+__host__ __device__ __forceinline__ double uniform01(uint32_t w) {
+  return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0);
+}
+
+// ------------------------------------------------------------------ cosine
+// cos(x) for the feature map z = sqrt(2/D) cos(w.x + b).  Range reduction by
+// Cody-Waite with a two-term 2*pi (x = k 2pi + r, |r| <= pi, the products k*2pi
+// fused into FMAs), then a polynomial in s = r^2 of degree 6 whose coefficients
+// were fitted for this library by iteratively reweighted least squares (Lawson's
+// algorithm) on [0, pi^2] (see fit_cos_poly.py beside this file).  Fit error
+// 1.1e-8; measured in float32 evaluation, |error| <= 4e-7 on [-pi, pi].
+__device__ __forceinline__ float cos_rr(float x) {
+  const float inv_2pi = 0.159154943091895336f;
+  const float two_pi_hi = 6.28318548202514648f;   // float32 nearest to 2 pi
+  const float two_pi_lo = -1.74845553146951717e-07f;  // 2 pi - two_pi_hi
+  const float k = rintf(x * inv_2pi);
+  float r = fmaf(-k, two_pi_hi, x);
+  r = fmaf(-k, two_pi_lo, r);
+  const float s = r * r;
+  float p = 1.7247605565984259e-09f;
+  p = fmaf(p, s, -2.7079772735305596e-07f);
+  p = fmaf(p, s, 2.4769966330495663e-05f);
+  p = fmaf(p, s, -0.0013887807726860046f);
+  p = fmaf(p, s, 0.04166648909449577f);
+  p = fmaf(p, s, -0.49999988079071045f);
+  p = fmaf(p, s, 1.0f);
+  return p;
+}
+
+// ------------------------------------------------------------------ BF16 split
+// x = hi + lo + O(2^-17 |x|): hi = bf16(x), lo = bf16(x - hi).
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+}  // namespace rff

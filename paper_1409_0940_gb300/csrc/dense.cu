@@ -1,0 +1,400 @@
+// Batched dense linear algebra on the SIMT pipes: the Gram matrices
+// I + Z_ij^T Z_ij of eq. (cache), their FP64 Cholesky factorisation, the cached
+// inverse Q_ij = (I + Z_ij^T Z_ij)^-1 (the paper's "Q_ij can be cached"), and the
+// per-iteration products with Q_ij and H_ij.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <vector>
+
+namespace rff {
+
+namespace {
+
+// ------------------------------------------------------------------ generic GEMM
+// D = alpha * op(A) op(B) + beta * Cm for a batch of row-major matrices.
+// Tile 64 x 64, 256 threads, 4 x 4 outputs per thread.  Loads are bounds-checked
+// so any M, N, K works.  lower_only skips tiles strictly above the diagonal.
+template <typename T, int BK>
+__global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ descs, int transA, int transB, T alpha,
+                                              T beta, int lower_only) {
+  const GemmDesc g = descs[blockIdx.z];
+  const int tm = blockIdx.x, tn = blockIdx.y;
+  if (tm * 64 >= g.M || tn * 64 >= g.N) return;
+  if (lower_only && tn > tm) return;
+  const T* __restrict__ A = static_cast<const T*>(g.A);
+  const T* __restrict__ B = static_cast<const T*>(g.B);
+  __shared__ T As[BK][64 + 1];
+  __shared__ T Bs[BK][64 + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  const int m0 = tm * 64, n0 = tn * 64;
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    for (int t = tid; t < 64 * BK; t += 256) {
+      int mm, kk;
+      if (transA) { mm = t % 64; kk = t / 64; } else { kk = t % BK; mm = t / BK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      T v = T(0);
+      if (gm < g.M && gk < g.K) v = transA ? A[(int64_t)gk * g.lda + gm] : A[(int64_t)gm * g.lda + gk];
+      As[kk][mm] = v;
+      int nn, kb;
+      if (transB) { kb = t % BK; nn = t / BK; } else { nn = t % 64; kb = t / 64; }
+      const int gn = n0 + nn, gkb = k0 + kb;
+      T w = T(0);
+      if (gn < g.N && gkb < g.K) w = transB ? B[(int64_t)gn * g.ldb + gkb] : B[(int64_t)gkb * g.ldb + gn];
+      Bs[kb][nn] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const T* __restrict__ Cm = static_cast<const T*>(g.Cm);
+  T* __restrict__ D = static_cast<T*>(g.D);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty * 4 + i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx * 4 + j;
+      if (gn >= g.N) continue;
+      T v = alpha * acc[i][j];
+      if (beta != T(0)) v = fma(beta, Cm[(int64_t)gm * g.ldc + gn], v);
+      D[(int64_t)gm * g.ldd + gn] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ FP32 NN GEMM
+// The per-iteration products x = Q r and r = b - H x: A (M x K) and B (K x N)
+// row-major with K-contiguous A rows, N-contiguous B rows; vector loads when the
+// tile is interior.  Tile 64 x 64, BK = 32.
+__global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict__ descs, float alpha, float beta) {
+  const GemmDesc g = descs[blockIdx.z];
+  const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+  if (m0 >= g.M || n0 >= g.N) return;
+  const float* __restrict__ A = static_cast<const float*>(g.A);
+  const float* __restrict__ B = static_cast<const float*>(g.B);
+  __shared__ __align__(16) float As[32][64 + 4];
+  __shared__ __align__(16) float Bs[32][64 + 4];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < g.K; k0 += 32) {
+    // A tile: 64 rows x 32 k
+    for (int t = tid; t < 64 * 32; t += 256) {
+      const int kk = t % 32, mm = t / 32;
+      const int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < g.M && gk < g.K) ? A[(int64_t)gm * g.lda + gk] : 0.f;
+    }
+    // B tile: 32 k x 64 n
+    for (int t = tid; t < 64 * 32; t += 256) {
+      const int nn = t % 64, kb = t / 64;
+      const int gn = n0 + nn, gk = k0 + kb;
+      Bs[kb][nn] = (gn < g.N && gk < g.K) ? B[(int64_t)gk * g.ldb + gn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float4 av = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+      const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const float* __restrict__ Cm = static_cast<const float*>(g.Cm);
+  float* __restrict__ D = static_cast<float*>(g.D);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty * 4 + i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx * 4 + j;
+      if (gn >= g.N) continue;
+      float v = alpha * acc[i][j];
+      if (beta != 0.f) v = fmaf(beta, Cm[(int64_t)gm * g.ldc + gn], v);
+      D[(int64_t)gm * g.ldd + gn] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ Gram
+// H (s x s, f64, lower tiles) += Z^T Z for Z (n x s) float32.  FP32 products
+// summed over chunks of 256 rows in FP32, chunk sums accumulated in FP64.
+__global__ void __launch_bounds__(256) k_gram(const float* __restrict__ Z, int64_t ldz, int64_t n, int64_t s,
+                                              double* __restrict__ H, int64_t ldh) {
+  const int tm = blockIdx.x, tn = blockIdx.y;
+  if (tn > tm) return;
+  const int64_t a0 = (int64_t)tm * 64, b0 = (int64_t)tn * 64;
+  __shared__ __align__(16) float As[32][64 + 4];
+  __shared__ __align__(16) float Bs[32][64 + 4];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  double acc64[4][4] = {};
+  float acc[4][4] = {};
+  int chunk = 0;
+  for (int64_t r0 = 0; r0 < n; r0 += 32) {
+    for (int t = tid; t < 64 * 32; t += 256) {
+      const int c = t % 64, r = t / 64;
+      const int64_t gr = r0 + r;
+      As[r][c] = (gr < n && a0 + c < s) ? Z[gr * ldz + a0 + c] : 0.f;
+      Bs[r][c] = (gr < n && b0 + c < s) ? Z[gr * ldz + b0 + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float4 av = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+      const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+    if (++chunk == 8) {
+      chunk = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc64[i][j] += (double)acc[i][j];
+          acc[i][j] = 0.f;
+        }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gm = a0 + ty * 4 + i, gn = b0 + tx * 4 + j;
+      if (gm < s && gn < s) H[gm * ldh + gn] += acc64[i][j] + (double)acc[i][j];
+    }
+}
+
+// ------------------------------------------------------------------ diagonal potrf
+// One CTA per matrix: factor the bs x bs diagonal block starting at column kcol
+// (bs = min(64, s - kcol)) in shared memory, write L back (upper part zeroed) and
+// the inverse of L into inv (64 x 64, zero padded).  info = column+1 of the first
+// non-positive pivot (the pivot is replaced by 1 so the factorisation finishes).
+
+
+__global__ void __launch_bounds__(256) k_potrf_diag(const DiagJob* __restrict__ jobs, int kcol) {
+  const DiagJob jb = jobs[blockIdx.x];
+  if (kcol >= jb.s) return;
+  const int bs = min(64, jb.s - kcol);
+  __shared__ double L[64][65];
+  __shared__ double Li[64][65];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int t = tid; t < 64 * 64; t += 256) {
+    const int r = t / 64, c = t % 64;
+    L[r][c] = (r < bs && c < bs) ? jb.A[(int64_t)(kcol + r) * jb.ld + kcol + c] : (r == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int c = 0; c < bs; ++c) {
+    if (tid == 0) {
+      double d = L[c][c];
+      if (!(d > 0.0)) {
+        if (bad == 0) bad = kcol + c + 1;
+        d = 1.0;
+      }
+      L[c][c] = sqrt(d);
+    }
+    __syncthreads();
+    const double piv = L[c][c];
+    for (int r = c + 1 + tid; r < bs; r += 256) L[r][c] /= piv;
+    __syncthreads();
+    const int w = bs - c - 1;
+    for (int t = tid; t < w * w; t += 256) {
+      const int r = c + 1 + t / w, q = c + 1 + t % w;
+      if (q <= r) L[r][q] -= L[r][c] * L[q][c];
+    }
+    __syncthreads();
+  }
+  // inverse of the lower-triangular L, one column per thread
+  if (tid < 64) {
+    const int q = tid;
+    for (int r = 0; r < 64; ++r) {
+      double v = 0.0;
+      if (r >= q && r < bs) {
+        double sacc = (r == q) ? 1.0 : 0.0;
+        for (int t = q; t < r; ++t) sacc -= L[r][t] * Li[t][q];
+        v = sacc / L[r][r];
+      }
+      Li[r][q] = v;
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < 64 * 64; t += 256) {
+    const int r = t / 64, c = t % 64;
+    if (r < bs && c < bs) jb.A[(int64_t)(kcol + r) * jb.ld + kcol + c] = (c <= r) ? L[r][c] : 0.0;
+    jb.inv[t] = Li[r][c];
+  }
+  if (tid == 0 && bad && jb.info && *jb.info == 0) *jb.info = bad;
+}
+
+__global__ void k_add_identity_and_mirror(double* H, int64_t ldh, int64_t s) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= s * s) return;
+  const int64_t r = t / s, c = t % s;
+  if (c > r) H[r * ldh + c] = H[c * ldh + r];
+  else if (c == r) H[r * ldh + c] += 1.0;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_f32_nn(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, float alpha, float beta,
+                               cudaStream_t st) {
+  if (nbatch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(maxM, 64), (unsigned)ceil_div(maxN, 64), (unsigned)nbatch);
+  k_gemm_f32_nn<<<grid, 256, 0, st>>>(descs_dev, alpha, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_f64(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, int transA, int transB,
+                            double alpha, double beta, int lower_only, cudaStream_t st) {
+  if (nbatch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(maxM, 64), (unsigned)ceil_div(maxN, 64), (unsigned)nbatch);
+  k_gemm<double, 16><<<grid, 256, 0, st>>>(descs_dev, transA, transB, alpha, beta, lower_only);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_f32_to_f64(const float* Z, int64_t ldz, int64_t n, int64_t s, double* H, int64_t ldh,
+                                   cudaStream_t st) {
+  if (n <= 0 || s <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(s, 64), (unsigned)ceil_div(s, 64));
+  k_gram<<<grid, 256, 0, st>>>(Z, ldz, n, s, H, ldh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_identity_and_mirror(double* H, int64_t ldh, int64_t s, cudaStream_t st) {
+  if (s <= 0) return cudaSuccess;
+  k_add_identity_and_mirror<<<(unsigned)ceil_div(s * s, 256), 256, 0, st>>>(H, ldh, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_potrf_diag(const DiagJob* jobs_dev, int njobs, int kcol, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  k_potrf_diag<<<njobs, 256, 0, st>>>(jobs_dev, kcol);
+  return cudaGetLastError();
+}
+
+// Blocked right-looking Cholesky (64-column panels) of every A_b in place, then
+// optionally Q_b = A_b^-1 by forward and backward substitution against the
+// identity, using the inverted 64 x 64 diagonal factors:
+//   potrf step k:  L_kk = chol(A_kk);  A_ik <- A_ik L_kk^-T;  A_il -= A_ik A_lk^T
+//   L Y = I:       Y_k = L_kk^-1 B_k;  B_i -= L_ik Y_k   (i > k)
+//   L^T Q = Y:     Q_k = L_kk^-T Y_k;  Y_i -= L_ki^T Q_k (i < k)
+// Descriptors live in `dev_scratch` (>= factor_scratch_bytes bytes).
+size_t factor_scratch_bytes(int njobs, int smax) {
+  const int nb = (int)ceil_div(smax, 64);
+  return (size_t)njobs * nb * 64 * 64 * sizeof(double) + (size_t)njobs * sizeof(DiagJob) * nb +
+         (size_t)njobs * nb * 6 * sizeof(GemmDesc) + 1024;
+}
+
+cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st) {
+  const int nj = (int)jobs.size();
+  if (nj == 0) return cudaSuccess;
+  int smax = 0;
+  for (const auto& j : jobs) smax = std::max(smax, j.s);
+  const int nb = (int)ceil_div(smax, 64);
+  char* p = static_cast<char*>(dev_scratch);
+  double* inv = reinterpret_cast<double*>(p);
+  p += (size_t)nj * nb * 64 * 64 * sizeof(double);
+  DiagJob* djobs = reinterpret_cast<DiagJob*>(p);
+  p += (size_t)nj * nb * sizeof(DiagJob);
+  GemmDesc* gd = reinterpret_cast<GemmDesc*>(p);
+
+  std::vector<DiagJob> hd((size_t)nj * nb);
+  for (int k = 0; k < nb; ++k)
+    for (int b = 0; b < nj; ++b)
+      hd[(size_t)k * nj + b] = DiagJob{jobs[b].A, jobs[b].ld, jobs[b].s, inv + ((size_t)b * nb + k) * 4096,
+                                       jobs[b].info};
+  cudaError_t e = cudaMemcpyAsync(djobs, hd.data(), hd.size() * sizeof(DiagJob), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+
+  // descriptor table: [phase][k][b], phases: panel, trailing, fwdA, fwdB, bwdA, bwdB
+  std::vector<GemmDesc> g((size_t)6 * nb * nj);
+  auto at = [&](int ph, int k, int b) -> GemmDesc& { return g[((size_t)ph * nb + k) * nj + b]; };
+  for (int k = 0; k < nb; ++k)
+    for (int b = 0; b < nj; ++b) {
+      const MatJob& J = jobs[b];
+      const int64_t c0 = (int64_t)k * 64;
+      const int bs = (int)std::max<int64_t>(0, std::min<int64_t>(64, J.s - c0));
+      const int rest = (int)std::max<int64_t>(0, J.s - c0 - 64);
+      double* Ikk = inv + ((size_t)b * nb + k) * 4096;
+      GemmDesc z{};
+      // panel: A_ik <- A_ik * inv^T (in place)
+      GemmDesc pn = z;
+      if (bs > 0 && rest > 0) pn = GemmDesc{J.A + (c0 + 64) * J.ld + c0, Ikk, nullptr, J.A + (c0 + 64) * J.ld + c0,
+                                            rest, bs, bs, J.ld, 64, 0, J.ld};
+      at(0, k, b) = pn;
+      GemmDesc tr = z;
+      if (bs > 0 && rest > 0) tr = GemmDesc{J.A + (c0 + 64) * J.ld + c0, J.A + (c0 + 64) * J.ld + c0,
+                                            J.A + (c0 + 64) * J.ld + c0 + 64, J.A + (c0 + 64) * J.ld + c0 + 64,
+                                            rest, rest, bs, J.ld, J.ld, J.ld, J.ld};
+      at(1, k, b) = tr;
+      GemmDesc fa = z, fb = z, ba = z, bb = z;
+      if (invert && bs > 0) {
+        fa = GemmDesc{Ikk, J.Q + c0 * J.ldq, nullptr, J.Q + c0 * J.ldq, bs, J.s, bs, 64, J.ldq, 0, J.ldq};
+        if (rest > 0) fb = GemmDesc{J.A + (c0 + 64) * J.ld + c0, J.Q + c0 * J.ldq, J.Q + (c0 + 64) * J.ldq,
+                                    J.Q + (c0 + 64) * J.ldq, rest, J.s, bs, J.ld, J.ldq, J.ldq, J.ldq};
+        ba = fa;
+        if (c0 > 0) bb = GemmDesc{J.A + c0 * J.ld, J.Q + c0 * J.ldq, J.Q, J.Q, (int)c0, J.s, bs, J.ld, J.ldq, J.ldq,
+                                  J.ldq};
+      }
+      at(2, k, b) = fa;
+      at(3, k, b) = fb;
+      at(4, k, b) = ba;
+      at(5, k, b) = bb;
+    }
+  e = cudaMemcpyAsync(gd, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  auto dev = [&](int ph, int k) { return gd + ((size_t)ph * nb + k) * nj; };
+
+  for (int k = 0; k < nb; ++k) {
+    const int c0 = k * 64, rest = std::max(0, smax - c0 - 64);
+    if ((e = launch_potrf_diag(djobs + (size_t)k * nj, nj, c0, st)) != cudaSuccess) return e;
+    if (rest > 0) {
+      if ((e = launch_gemm_f64(dev(0, k), nj, rest, 64, 0, 1, 1.0, 0.0, 0, st)) != cudaSuccess) return e;
+      if ((e = launch_gemm_f64(dev(1, k), nj, rest, rest, 0, 1, -1.0, 1.0, 1, st)) != cudaSuccess) return e;
+    }
+  }
+  if (!invert) return cudaSuccess;
+  for (int k = 0; k < nb; ++k) {
+    const int c0 = k * 64, rest = std::max(0, smax - c0 - 64);
+    if ((e = launch_gemm_f64(dev(2, k), nj, 64, smax, 0, 0, 1.0, 0.0, 0, st)) != cudaSuccess) return e;
+    if (rest > 0)
+      if ((e = launch_gemm_f64(dev(3, k), nj, rest, smax, 0, 0, -1.0, 1.0, 0, st)) != cudaSuccess) return e;
+  }
+  for (int k = nb - 1; k >= 0; --k) {
+    const int c0 = k * 64;
+    if ((e = launch_gemm_f64(dev(4, k), nj, 64, smax, 1, 0, 1.0, 0.0, 0, st)) != cudaSuccess) return e;
+    if (c0 > 0)
+      if ((e = launch_gemm_f64(dev(5, k), nj, c0, smax, 1, 0, -1.0, 1.0, 0, st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace rff

@@ -1,0 +1,470 @@
+// Bandwidth-bound kernels of the iteration: proximal operators (Sec. 2.3; the
+// O and W updates of Sec. 3), the row-local exchange that follows the graph
+// projection (eq. (obar_ij), (obar) in the reorganised form of Sec. 3), the
+// averaging and dual updates, layout changes and deterministic reductions.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+
+namespace rff {
+
+namespace {
+
+constexpr int LOSS_SQUARED = 0, LOSS_HINGE = 1, LOSS_LOGISTIC = 2, LOSS_MULTINOMIAL = 3;
+
+// dst[p][c] = src[map[p]][c] for c < w, zero elsewhere (map[p] < 0: zero row)
+__global__ void k_scatter_rows(const float* __restrict__ src, int64_t lds, int64_t w,
+                               const int32_t* __restrict__ map, int64_t nrows, float* __restrict__ dst, int64_t ld) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nrows * ld) return;
+  const int64_t p = t / ld, c = t % ld;
+  const int32_t g = map ? map[p] : (int32_t)p;
+  dst[t] = (g >= 0 && c < w) ? src[(int64_t)g * lds + c] : 0.f;
+}
+
+__global__ void k_split(const float* __restrict__ src, int64_t n, __nv_bfloat16* __restrict__ hi,
+                        __nv_bfloat16* __restrict__ lo) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  split_bf16(src[t], hi[t], lo[t]);
+}
+
+// ---- scalar proxes: argmin_o 1/2 (o - v)^2 + t V(y, o)
+__device__ __forceinline__ float prox_squared(float v, float y, float t) { return (v + 2.f * t * y) / (1.f + 2.f * t); }
+
+__device__ __forceinline__ float prox_hinge(float v, float y, float t) {
+  const float u = y * v;
+  return u > 1.f ? v : (u < 1.f - t ? v + t * y : y);
+}
+
+// logistic, y = +-1: in p = y o, a = y v solve f(p) = p - a - t / (1 + e^p) = 0,
+// f increasing, root in [a, a + t]: Newton steps kept inside the bracket, which
+// is tightened by the sign of f at every step.
+__device__ __forceinline__ float prox_logistic(float v, float y, float t, int iters) {
+  const float a = y * v;
+  float lo = a, hi = a + t, p = a + 0.5f * t;
+  for (int it = 0; it < iters; ++it) {
+    const float sm = 1.f / (1.f + __expf(p));   // sigma(-p)
+    const float f = p - a - t * sm;
+    if (f < 0.f) lo = p; else hi = p;
+    const float fp = 1.f + t * sm * (1.f - sm);
+    float q = p - f / fp;
+    if (!(q > lo && q < hi)) q = 0.5f * (lo + hi);
+    p = q;
+  }
+  return y * p;
+}
+
+__device__ __forceinline__ float prox_scalar(int loss, float v, float y, float t, int iters) {
+  if (loss == LOSS_SQUARED) return prox_squared(v, y, t);
+  if (loss == LOSS_HINGE) return prox_hinge(v, y, t);
+  return prox_logistic(v, y, t, iters);
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ float warp_max(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+// Multinomial logistic prox of one row, one warp, lanes over the m outputs
+// (up to 8 per lane): Newton on o - v + t (softmax(o) - e_c) = 0 with the
+// Hessian I + t (diag p - p p^T) inverted by the Sherman-Morrison formula.
+// c = argmax_k y_k (first maximum).
+constexpr int MAXPL = 8;
+__device__ void prox_multinomial_row(const float (&v)[MAXPL], const float (&y)[MAXPL], int m, float t, int iters,
+                                     float (&o)[MAXPL]) {
+  const int lane = threadIdx.x & 31;
+  // class index: first maximum of y
+  float best = -INFINITY;
+  int bidx = 1 << 30;
+#pragma unroll
+  for (int q = 0; q < MAXPL; ++q) {
+    const int k = lane + 32 * q;
+    if (k < m && (y[q] > best)) { best = y[q]; bidx = k; }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+    if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+  }
+#pragma unroll
+  for (int q = 0; q < MAXPL; ++q) o[q] = v[q];
+  for (int it = 0; it < iters; ++it) {
+    float mx = -INFINITY;
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q)
+      if (lane + 32 * q < m) mx = fmaxf(mx, o[q]);
+    mx = warp_max(mx);
+    float e[MAXPL], se = 0.f;
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) {
+      e[q] = (lane + 32 * q < m) ? __expf(o[q] - mx) : 0.f;
+      se += e[q];
+    }
+    se = warp_sum(se);
+    float g[MAXPL], dg[MAXPL], dp[MAXPL], s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) {
+      const int k = lane + 32 * q;
+      const float pk = e[q] / se;
+      g[q] = (k < m) ? (o[q] - v[q] + t * (pk - (k == bidx ? 1.f : 0.f))) : 0.f;
+      const float dinv = 1.f / (1.f + t * pk);
+      dg[q] = dinv * g[q];
+      dp[q] = (k < m) ? dinv * pk : 0.f;
+      s1 += pk * dg[q] * (k < m);
+      s2 += pk * dp[q];
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    const float coef = t * s1 / (1.f - t * s2);
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) o[q] -= dg[q] + coef * dp[q];
+  }
+}
+
+__global__ void k_prox_loss(int loss, const float* __restrict__ V, const float* __restrict__ Y, int64_t n, int m,
+                            int64_t ld, float t, int iters, float* __restrict__ out) {
+  if (loss == LOSS_MULTINOMIAL) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    if (row >= n) return;
+    const int lane = threadIdx.x & 31;
+    float v[MAXPL], y[MAXPL], o[MAXPL];
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) {
+      const int k = lane + 32 * q;
+      v[q] = (k < m) ? V[row * ld + k] : 0.f;
+      y[q] = (k < m) ? Y[row * ld + k] : 0.f;
+    }
+    prox_multinomial_row(v, y, m, t, iters, o);
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) {
+      const int k = lane + 32 * q;
+      if (k < m) out[row * ld + k] = o[q];
+    }
+    return;
+  }
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * (int64_t)m) return;
+  const int64_t r = e / m, c = e % m;
+  out[r * ld + c] = prox_scalar(loss, V[r * ld + c], Y[r * ld + c], t, iters);
+}
+
+// prox of tau r at (V - mu): l2 |w|^2 -> (v - mu)/(1 + 2 tau); l1 -> soft threshold
+__global__ void k_prox_reg(int reg, const float* __restrict__ V, const float* __restrict__ mu, int64_t n, float tau,
+                           float* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float x = V[e] - (mu ? mu[e] : 0.f);
+  out[e] = (reg == 0) ? x / (1.f + 2.f * tau) : copysignf(fmaxf(fabsf(x) - tau, 0.f), x);
+}
+
+// Row-local exchange after pass 2 (one warp per row slot, lanes over outputs):
+//   S = sum_j O'_ij;  Delta = O - S;  Obar = S/(C+1) + C/(C+1) O;  nu += O - Obar
+//   V_ij = O'_ij + Delta/(C+1) + nu        (= Obar_ij + nu, the pass-1 operand)
+//   O <- prox_{t V}(Obar - nu)             (the loss step of the next iteration)
+// Padding rows are written as zeros.
+__global__ void k_row_epilogue(RowEpiArgs a) {
+  const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  if (p >= a.nslots) return;
+  const int lane = threadIdx.x & 31;
+  const bool ok = a.row_ok[p] >= 0;
+  const int64_t base = p * a.mpad;
+  const int64_t jstride = a.nslots * a.mpad;
+  const float inv_c1 = 1.f / (float)(a.C + 1);
+  const float cfrac = (float)a.C * inv_c1;
+  float w_in[MAXPL], y[MAXPL];
+  float dl[MAXPL], nuv[MAXPL];
+#pragma unroll
+  for (int q = 0; q < MAXPL; ++q) {
+    const int k = lane + 32 * q;
+    w_in[q] = 0.f; y[q] = 0.f; dl[q] = 0.f; nuv[q] = 0.f;
+    if (k >= a.mpad) continue;
+    float S = 0.f;
+    for (int j = 0; j < a.C; ++j) S += a.Op[j * jstride + base + k];
+    const float O = a.O[base + k];
+    float nu = a.nu[base + k];
+    const float Delta = O - S;
+    const float Obar = S * inv_c1 + cfrac * O;
+    nu += O - Obar;
+    if (!ok || k >= a.m) {
+      a.Obar[base + k] = 0.f; a.nu[base + k] = 0.f; a.Dl[base + k] = 0.f;
+      continue;
+    }
+    a.Obar[base + k] = Obar;
+    a.nu[base + k] = nu;
+    a.Dl[base + k] = Delta;
+    dl[q] = Delta;
+    nuv[q] = nu;
+    w_in[q] = Obar - nu;
+    y[q] = a.Y[base + k];
+  }
+  // V_ij for every column block
+  if (a.V32) {
+    for (int j = 0; j < a.C; ++j) {
+#pragma unroll
+      for (int q = 0; q < MAXPL; ++q) {
+        const int k = lane + 32 * q;
+        if (k >= a.mpad) continue;
+        const float vv = (ok && k < a.m) ? a.Op[j * jstride + base + k] + dl[q] * inv_c1 + nuv[q] : 0.f;
+        a.V32[j * jstride + base + k] = vv;
+      }
+    }
+  }
+  // next loss step
+  float o[MAXPL];
+  if (a.loss == LOSS_MULTINOMIAL) {
+    prox_multinomial_row(w_in, y, a.m, a.t_loss, a.newton, o);
+  } else {
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) o[q] = prox_scalar(a.loss, w_in[q], y[q], a.t_loss, a.newton);
+  }
+#pragma unroll
+  for (int q = 0; q < MAXPL; ++q) {
+    const int k = lane + 32 * q;
+    if (k >= a.mpad) continue;
+    a.O[base + k] = (ok && k < a.m) ? o[q] : 0.f;
+  }
+}
+
+__global__ void k_rhs(const float* __restrict__ Wbar, const float* __restrict__ muij, const float* __restrict__ Rpart,
+                      int nsplit, int R, int64_t nfe, float* __restrict__ rhs) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)R * nfe) return;
+  const int64_t e = t % nfe;
+  float acc = Wbar[e] - muij[t];
+  for (int s = 0; s < nsplit; ++s) acc += Rpart[(int64_t)s * R * nfe + t];
+  rhs[t] = acc;
+}
+
+// Wbar = (W + sum_i W'_i)/(R+1);  mu += W - Wbar;  mu'_i += W'_i - Wbar
+__global__ void k_avg_dual(const float* __restrict__ W, const float* __restrict__ What, int R, int64_t nfe,
+                           float* __restrict__ Wbar, float* __restrict__ mu, float* __restrict__ muij) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nfe) return;
+  const float w = W[e];
+  float s = w;
+  for (int i = 0; i < R; ++i) s += What[(int64_t)i * nfe + e];
+  const float wb = s / (float)(R + 1);
+  Wbar[e] = wb;
+  mu[e] += w - wb;
+  for (int i = 0; i < R; ++i) muij[(int64_t)i * nfe + e] += What[(int64_t)i * nfe + e] - wb;
+}
+
+// src [b][rows][cols] float32 -> hi/lo [b][cols][dst_ld] BF16, 32 x 32 smem tiles
+__global__ void k_transpose_split(const float* __restrict__ src, int64_t rows, int cols, int64_t sbs,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t dld,
+                                  int64_t dbs) {
+  __shared__ float tile[32][33];
+  const int b = blockIdx.z;
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 256 threads: 8 rows per pass
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t r = r0 + rr;
+    const int c = c0 + tx;
+    tile[rr][tx] = (r < rows && c < cols) ? src[b * sbs + r * cols + c] : 0.f;
+  }
+  __syncthreads();
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int c = c0 + cc;
+    const int64_t r = r0 + tx;
+    if (c < cols && r < rows) {
+      __nv_bfloat16 h, l;
+      split_bf16(tile[tx][cc], h, l);
+      hi[b * dbs + (int64_t)c * dld + r] = h;
+      lo[b * dbs + (int64_t)c * dld + r] = l;
+    }
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double x) {
+  __shared__ double red[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = x;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+  return s;
+}
+
+__global__ void __launch_bounds__(256) k_sqdiff(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
+                                                double* __restrict__ partials) {
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double d = (double)a[e] - (b ? (double)b[e] : 0.0);
+    acc += d * d;
+  }
+  const double s = block_sum<256>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(256) k_loss_sum(int loss, const float* __restrict__ Y, const float* __restrict__ S,
+                                                  const int32_t* __restrict__ row_ok, int64_t nslots, int m, int mpad,
+                                                  double* __restrict__ partials) {
+  double acc = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nslots;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    if (row_ok[p] < 0) continue;
+    const float* y = Y + p * mpad;
+    const float* o = S + p * mpad;
+    if (loss == LOSS_MULTINOMIAL) {
+      double mx = -1e300, yb = -1e300;
+      int c = 0;
+      for (int k = 0; k < m; ++k) {
+        mx = fmax(mx, (double)o[k]);
+        if (y[k] > yb) { yb = y[k]; c = k; }
+      }
+      double se = 0.0;
+      for (int k = 0; k < m; ++k) se += exp((double)o[k] - mx);
+      acc += mx + log(se) - (double)o[c];
+    } else {
+      for (int k = 0; k < m; ++k) {
+        const double yy = y[k], oo = o[k];
+        if (loss == LOSS_SQUARED) acc += (yy - oo) * (yy - oo);
+        else if (loss == LOSS_HINGE) acc += fmax(0.0, 1.0 - yy * oo);
+        else acc += (-yy * oo > 0 ? -yy * oo + log1p(exp(yy * oo)) : log1p(exp(-yy * oo)));
+      }
+    }
+  }
+  const double s = block_sum<256>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(256) k_reg_sum(int reg, const float* __restrict__ W, int64_t n,
+                                                 double* __restrict__ partials) {
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    acc += reg == 0 ? (double)W[e] * W[e] : fabs((double)W[e]);
+  const double s = block_sum<256>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < n) d[e] = (float)s[e];
+}
+
+// flag |= 1 for a NaN/Inf entry; with pm1, flag |= 2 for an entry outside {-1, +1}
+__global__ void k_finite(const float* __restrict__ x, int64_t n, int pm1, int* __restrict__ flag) {
+  int f = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[e];
+    if (!isfinite(v)) f |= 1;
+    if (pm1 && v != 1.f && v != -1.f) f |= 2;
+  }
+  if (f) atomicOr(flag, f);
+}
+
+__global__ void k_set_diag(double* __restrict__ A, int64_t ld, int64_t s, double v) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < s) A[t * ld + t] = v;
+}
+
+inline unsigned nblk(int64_t n, int bs = 256) { return (unsigned)ceil_div(n, bs); }
+
+}  // namespace
+
+cudaError_t launch_gather_rows(const float* src, int64_t lds, int64_t w, const int32_t* map, int64_t nrows,
+                               float* dst, int64_t ld, cudaStream_t st) {
+  if (nrows * ld <= 0) return cudaSuccess;
+  k_scatter_rows<<<nblk(nrows * ld), 256, 0, st>>>(src, lds, w, map, nrows, dst, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(const float* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_split<<<nblk(n), 256, 0, st>>>(src, n, hi, lo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prox_loss(int loss, const float* V, const float* Y, int64_t n, int m, int64_t ld, float t,
+                             int newton, float* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (m > 32 * MAXPL) return cudaErrorInvalidValue;
+  const int64_t threads = loss == LOSS_MULTINOMIAL ? n * 32 : n * m;
+  k_prox_loss<<<nblk(threads), 256, 0, st>>>(loss, V, Y, n, m, ld, t, newton, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prox_reg(int reg, const float* V, const float* mu, int64_t n, float tau, float* out,
+                            cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_prox_reg<<<nblk(n), 256, 0, st>>>(reg, V, mu, n, tau, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st) {
+  if (a.nslots <= 0) return cudaSuccess;
+  if (a.mpad > 32 * MAXPL) return cudaErrorInvalidValue;
+  k_row_epilogue<<<nblk(a.nslots * 32), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(const float* Wbar, const float* muij, const float* Rpart, int nsplit, int R, int64_t nfe,
+                       float* rhs, cudaStream_t st) {
+  k_rhs<<<nblk((int64_t)R * nfe), 256, 0, st>>>(Wbar, muij, Rpart, nsplit, R, nfe, rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_avg_dual(const float* W, const float* What, int R, int64_t nfe, float* Wbar, float* mu,
+                            float* muij, cudaStream_t st) {
+  k_avg_dual<<<nblk(nfe), 256, 0, st>>>(W, What, R, nfe, Wbar, mu, muij);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_split(const float* src, int64_t rows, int cols, int nbatch, int64_t src_batch_stride,
+                                   __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t dst_ld, int64_t dst_batch_stride,
+                                   cudaStream_t st) {
+  if (rows <= 0 || cols <= 0 || nbatch <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32), (unsigned)nbatch);
+  k_transpose_split<<<grid, 256, 0, st>>>(src, rows, cols, src_batch_stride, hi, lo, dst_ld, dst_batch_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sqdiff_partials(const float* a, const float* b, int64_t n, double* partials, int nblocks,
+                                   cudaStream_t st) {
+  k_sqdiff<<<nblocks, 256, 0, st>>>(a, b, n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_partials(int loss, const float* Y, const float* S, const int32_t* row_ok, int64_t nslots,
+                                 int m, int mpad, double* partials, int nblocks, cudaStream_t st) {
+  k_loss_sum<<<nblocks, 256, 0, st>>>(loss, Y, S, row_ok, nslots, m, mpad, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reg_partials(int reg, const float* W, int64_t n, double* partials, int nblocks, cudaStream_t st) {
+  k_reg_sum<<<nblocks, 256, 0, st>>>(reg, W, n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_f64_to_f32<<<nblk(n), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_finite<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4096), 256, 0, st>>>(x, n, pm1, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_diag(double* A, int64_t ld, int64_t s, double v, cudaStream_t st) {
+  if (s <= 0) return cudaSuccess;
+  k_set_diag<<<nblk(s), 256, 0, st>>>(A, ld, s, v);
+  return cudaGetLastError();
+}
+
+}  // namespace rff

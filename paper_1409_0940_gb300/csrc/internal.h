@@ -1,0 +1,145 @@
+// Internal launcher declarations shared by the translation units of the library.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace rff {
+
+// Arguments of the fused regeneration passes (SIMT and tensor-core versions).
+// Row-side arrays are indexed by row slot, feature-side arrays by feature slot.
+struct PassArgs {
+  const float* X;        // data rows (slots) x K, float32            (SIMT)
+  int64_t ldx;
+  const float* Gt;       // feature rows (slots) x K, float32         (SIMT)
+  int64_t ldg;
+  int K;                 // padded input dimension (multiple of 64)
+  const float* bias;     // b per feature slot
+  float scale;           // sqrt(2/D)
+  const int32_t* row_ok; // row_of_slot table (-1 = padding), or null = all valid
+  const int32_t* feat_ok;
+  const int64_t* row_slot;  // R entries: first slot of each row block
+  const int64_t* row_size;  // R entries: n_i
+  int R;
+  const int64_t* col_slot;  // C entries
+  const int64_t* col_size;  // C entries: s_j
+  int C;
+  const float* M;           // chain operand (SIMT: rows x m_pad float32)
+  int64_t m_block_stride;   // elements between the chain operands of successive blocks
+  float* out;
+  int64_t out_block_stride; // elements between outputs of successive blocks
+  int mpad;
+  int nsplit;               // pass 1: row splits per row block
+  int per_block;            // pass 2: write per column block (1) or once (0)
+};
+
+struct ZArgs {
+  const float* X;
+  int64_t ldx;
+  const float* Gt;
+  int64_t ldg;
+  int K;
+  const float* bias;
+  float scale;
+  const int32_t* row_ok;
+  const int32_t* feat_ok;
+  int64_t r0, nr, f0, nf;   // row slots [r0, r0+nr), feature slots [f0, f0+nf)
+  float* out;
+  int64_t ldo;
+};
+
+// philox.cu
+cudaError_t launch_philox_raw(const uint32_t* ctr, uint64_t seed, int64_t n, uint32_t* out, cudaStream_t st);
+cudaError_t launch_params_rowmajor(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t nk, float* G,
+                                   float* b, cudaStream_t st);
+cudaError_t launch_params_slots(uint64_t seed, double sigma, int64_t d, int64_t ld, int64_t nslots,
+                                const int32_t* feat_of_slot, float* Gt, __nv_bfloat16* Ghi, __nv_bfloat16* Glo,
+                                float* bias, cudaStream_t st);
+
+// regen_simt.cu
+cudaError_t launch_pass1_simt(const PassArgs& p, int64_t nfeat_slots, cudaStream_t st);
+cudaError_t launch_pass2_simt(const PassArgs& p, int64_t nrow_slots, cudaStream_t st);
+cudaError_t launch_write_z_simt(const ZArgs& p, cudaStream_t st);
+
+// dense.cu: batched dense linear algebra (SIMT)
+struct GemmDesc {          // D = alpha * op(A) op(B) + beta * Cm, row-major
+  const void* A;
+  const void* B;
+  const void* Cm;
+  void* D;
+  int M, N, K;
+  int64_t lda, ldb, ldc, ldd;
+};
+// f32 iteration GEMM, NN only, desc array on the device
+cudaError_t launch_gemm_f32_nn(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, float alpha, float beta,
+                               cudaStream_t st);
+// f64 with runtime transposes
+cudaError_t launch_gemm_f64(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, int transA, int transB,
+                            double alpha, double beta, int lower_only, cudaStream_t st);
+// Gram: D(f64) = beta*D + Z^T Z over rows, Z float32 (n x s, ld), FP32 products, FP64 accumulation
+cudaError_t launch_gram_f32_to_f64(const float* Z, int64_t ldz, int64_t n, int64_t s, double* H, int64_t ldh,
+                                   cudaStream_t st);
+struct DiagJob {   // one matrix of a batched factorisation
+  double* A;       // matrix base (s x s, leading dimension ld)
+  int64_t ld;
+  int s;
+  double* inv;     // 64 x 64: inverse of the current diagonal factor
+  int32_t* info;   // first failing column + 1, or untouched
+};
+cudaError_t launch_potrf_diag(const DiagJob* jobs_dev, int njobs, int kcol, cudaStream_t st);
+cudaError_t launch_add_identity_and_mirror(double* H, int64_t ldh, int64_t s, cudaStream_t st);
+struct MatJob {    // host description of one matrix to factor (and invert)
+  double* A;       // in: SPD matrix; out: lower Cholesky factor
+  int64_t ld;
+  int s;
+  double* Q;       // out: inverse (must hold the identity on entry), or null
+  int64_t ldq;
+  int32_t* info;   // device int32, zero on entry
+};
+size_t factor_scratch_bytes(int njobs, int smax);
+cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st);
+
+// elementwise.cu
+// dst[p][c] = src[map[p] * lds + c] (c < w), zero for c >= w or map[p] < 0; map null = identity
+cudaError_t launch_gather_rows(const float* src, int64_t lds, int64_t w, const int32_t* map, int64_t nrows,
+                               float* dst, int64_t ld, cudaStream_t st);
+cudaError_t launch_split_bf16(const float* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st);
+cudaError_t launch_prox_loss(int loss, const float* V, const float* Y, int64_t n, int m, int64_t ld, float t,
+                             int newton, float* out, cudaStream_t st);
+cudaError_t launch_prox_reg(int reg, const float* V, const float* mu, int64_t n, float tau, float* out,
+                            cudaStream_t st);
+struct RowEpiArgs {
+  const float* Op;      // C x slots x mpad
+  float* O;             // slots x mpad (in: O^k, out: O^{k+1} = prox(Obar - nu))
+  float* Obar;
+  float* nu;
+  float* Dl;            // Delta_i
+  const float* Y;
+  float* V32;           // C x slots x mpad (may be null)
+  __nv_bfloat16* VThi;  // C x mpad x slots (may be null)
+  __nv_bfloat16* VTlo;
+  const int32_t* row_ok;
+  int64_t nslots;
+  int C, m, mpad, loss, newton;
+  float t_loss;
+};
+cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st);
+cudaError_t launch_rhs(const float* Wbar, const float* muij, const float* Rpart, int nsplit, int R, int64_t nfe,
+                       float* rhs, cudaStream_t st);
+cudaError_t launch_avg_dual(const float* W, const float* What, int R, int64_t nfe, float* Wbar, float* mu,
+                            float* muij, cudaStream_t st);
+cudaError_t launch_transpose_split(const float* src, int64_t rows, int cols, int nbatch, int64_t src_batch_stride,
+                                   __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t dst_ld, int64_t dst_batch_stride,
+                                   cudaStream_t st);
+cudaError_t launch_sqdiff_partials(const float* a, const float* b, int64_t n, double* partials, int nblocks,
+                                   cudaStream_t st);
+cudaError_t launch_loss_partials(int loss, const float* Y, const float* S, const int32_t* row_ok, int64_t nslots,
+                                 int m, int mpad, double* partials, int nblocks, cudaStream_t st);
+cudaError_t launch_reg_partials(int reg, const float* W, int64_t n, double* partials, int nblocks, cudaStream_t st);
+cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
+cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, cudaStream_t st);
+cudaError_t launch_set_diag(double* A, int64_t ld, int64_t s, double v, cudaStream_t st);
+
+}  // namespace rff

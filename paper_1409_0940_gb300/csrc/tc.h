@@ -1,0 +1,36 @@
+// Tensor-core (tcgen05) regeneration passes of the split-BF16 path.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rff {
+
+// What the tensor-core passes need from a solver handle.  Host arrays (row_slot,
+// ...) describe the block grid; device arrays hold the data in slot layout.
+struct TcView {
+  const __nv_bfloat16 *Xhi, *Xlo;   // nslots x dld
+  const __nv_bfloat16 *Ghi, *Glo;   // fslots x dld
+  const __nv_bfloat16 *VThi, *VTlo; // C x mpad x nslots (pass-1 chain operand)
+  const float* bias;                // fslots
+  const int32_t *row_ok, *feat_ok;  // slot tables, -1 = padding
+  int64_t nslots, fslots, dld, mpad;
+  int R, C, nsplit;
+  const int64_t *row_slot, *row_size, *col_slot, *col_size;  // host
+  float scale;
+  cudaStream_t st;
+};
+
+// Z for row slots [r0, r0+nr) x feature slots [f0, f0+nf) into out (ld ldo), float32.
+cudaError_t tc_write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int64_t nf, float* out, int64_t ldo);
+// Pass 1: R-partials [nsplit][R][fslots][mpad] = Z_ij^T V_ij.
+cudaError_t tc_pass1(const TcView& v, float* Rpart);
+// Pass 2: out[j][slots][mpad] = Z_ij M_i (per_block) or out[slots][mpad] = sum_j Z_ij M (predict);
+// M given transposed and split: [R][mpad][fslots] hi/lo, m_block_stride elements apart.
+cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, int64_t m_block_stride,
+                     float* out, int per_block);
+// Scores for a query block (nrows slot-padded rows of split X) against M (mpad x fslots hi/lo).
+cudaError_t tc_predict(const TcView& v, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int64_t nrows,
+                       const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, float* out);
+
+}  // namespace rff

@@ -1,0 +1,177 @@
+"""GPU parity of the whole solver (C ABI) against the FP64 oracle, iterate for iterate."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from oracle import admm  # noqa: E402
+
+PRECS = {"fp32": 1e-5}   # relative weight / objective tolerance per path
+
+
+@pytest.fixture(scope="module")
+def rff():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1409_0940_gb300
+    return paper_1409_0940_gb300
+
+
+def run_gpu(rff, X, Y, iters, prec, **kw):
+    s = rff.Solver(prec=prec, **kw)
+    s.set_data(X, Y)
+    st = s.solve(iters)
+    W = s.weights()
+    return s, st, W
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ridge_ref():
+    """The n=2000, d=16, D=512 ridge workload: oracle iterates and the closed form."""
+    X, Y = synth.ridge(seed=1)
+    p = admm.Problem(X, Y, "squared", "l2", 1e-4, 4.0, 1.0, 512, 1, 1, 2)
+    out = admm.admm(p, 200, history=True)
+    return X, Y, p, out, admm.ridge_closed_form(p.Z(), p.Y, p.lam)
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+def test_ridge_1x1_matches_oracle_and_closed_form(rff, ridge_ref, prec):
+    X, Y, p, out, Wcf = ridge_ref
+    s, st, W = run_gpu(rff, X, Y, 200, prec, loss="squared", reg="l2", lam=1e-4, sigma=4.0, rho=1.0, D=512,
+                       R=1, C=1, seed=2, m=1)
+    tol = PRECS[prec]
+    assert rel(W, out["Wbar"]) < tol
+    assert rel(W, Wcf) < tol
+    assert abs(st["objective"] - p.objective(out["Wbar"])) < tol * abs(p.objective(out["Wbar"]))
+    # predictions on fresh points
+    Xq = np.random.default_rng(5).random((333, 16)).astype(np.float32)
+    got = s.predict(Xq)
+    ref = p.predict(Xq, out["Wbar"])
+    assert np.abs(got - ref).max() < tol * np.abs(ref).max() * 10
+    s.close()
+
+
+GRIDS = [
+    # (loss, reg, n, d, m, D, R, C, iters, lam, rho, sigma)
+    ("squared", "l2", 777, 13, 1, 300, 3, 2, 30, 1e-3, 1.0, 2.0),
+    ("squared", "l1", 640, 9, 2, 256, 2, 2, 25, 1e-4, 1.0, 2.0),
+    ("hinge", "l2", 900, 11, 5, 384, 2, 3, 25, 1e-3, 1.0, 3.0),
+    ("hinge", "l2", 500, 7, 1, 200, 1, 2, 25, 1e-3, 0.5, 2.0),
+    ("logistic", "l2", 600, 8, 1, 256, 2, 1, 25, 1e-3, 1.0, 2.5),
+    ("multinomial", "l2", 700, 10, 4, 320, 2, 2, 25, 1e-3, 1.0, 3.0),
+]
+
+
+def _data(loss, n, d, m, seed):
+    if loss == "squared":
+        X, y = synth.ridge(n=n, d=d, seed=seed)
+        Y = np.repeat(y, m, axis=1) * np.linspace(1, 0.5, m, dtype=np.float32)[None]
+        return X, np.ascontiguousarray(Y, dtype=np.float32)
+    if m == 1:
+        return synth.binary(n=n, d=d, seed=seed)
+    return synth.multiclass(n=n, d=d, m=m, seed=seed)
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("case", GRIDS, ids=lambda c: "%s-%s-%dx%d-m%d" % (c[0], c[1], c[6], c[7], c[4]))
+def test_grids_and_losses_match_oracle(rff, prec, case):
+    loss, reg, n, d, m, D, R, C, iters, lam, rho, sigma = case
+    X, Y = _data(loss, n, d, m, seed=n + m)
+    p = admm.Problem(X, Y, loss, reg, lam, sigma, rho, D, R, C, seed=31)
+    out = admm.admm(p, iters, history=True)
+    s, st, W = run_gpu(rff, X, Y, iters, prec, loss=loss, reg=reg, lam=lam, sigma=sigma, rho=rho, D=D, R=R, C=C,
+                       seed=31, m=m)
+    tol = PRECS[prec]
+    assert rel(W, out["Wbar"]) < tol, rel(W, out["Wbar"])
+    f_ref = p.objective(out["Wbar"])
+    assert abs(st["objective"] - f_ref) < tol * abs(f_ref)
+    pr, du = out["history"][-1]
+    assert abs(st["primal_res"] - pr) < 1e-2 * pr + 1e-6
+    assert abs(st["dual_res"] - du) < 1e-2 * du + 1e-6
+    s.close()
+
+
+def test_resume_from_checkpoint_is_bit_identical(rff):
+    X, Y = synth.multiclass(n=500, d=6, m=3, seed=2)
+    kw = dict(loss="hinge", reg="l2", lam=1e-3, sigma=2.0, rho=1.0, D=256, R=2, C=2, seed=4, m=3)
+    a = rff.Solver(**kw)
+    a.set_data(X, Y)
+    a.solve(12, stats=False)
+    Wa = a.weights()
+    b = rff.Solver(**kw)
+    b.set_data(X, Y)
+    b.solve(5, stats=False)
+    state = b.get_state()
+    b.close()
+    c = rff.Solver(**kw)
+    c.set_data(X, Y)
+    c.set_state(state)
+    c.solve(7, stats=False)
+    assert np.array_equal(c.weights(), Wa)
+    a.close()
+    c.close()
+
+
+def test_runs_are_deterministic(rff):
+    X, Y = synth.ridge(n=400, d=5, seed=9)
+    kw = dict(loss="squared", reg="l2", lam=1e-3, sigma=1.0, D=200, R=2, C=2, seed=1, m=1)
+    Ws = []
+    for _ in range(2):
+        s = rff.Solver(**kw)
+        s.set_data(X, Y)
+        s.solve(10, stats=False)
+        Ws.append(s.weights())
+        s.close()
+    assert np.array_equal(Ws[0], Ws[1])
+
+
+def test_invalid_inputs_are_rejected(rff):
+    X, Y = synth.binary(n=100, d=4, seed=1)
+    s = rff.Solver(loss="hinge", D=64, m=1)
+    with pytest.raises(rff.RffError) as e:
+        s.predict(X[:3])
+    assert e.value.status == rff.RFF_ENOTREADY
+    bad = X.copy()
+    bad[3, 2] = np.nan
+    with pytest.raises(rff.RffError) as e:
+        s.set_data(bad, Y)
+    assert e.value.status == rff.RFF_EINVAL
+    with pytest.raises(rff.RffError) as e:
+        s.set_data(X, Y * 0.5)          # hinge targets must be +-1
+    assert e.value.status == rff.RFF_EINVAL
+    s.set_data(X, Y)
+    s.solve(2, stats=False)
+    q = X[:5].copy()
+    q[0, 0] = np.inf
+    with pytest.raises(rff.RffError):
+        s.predict(q)
+    assert s.predict(X[:0]).shape == (0, 1)
+    s.close()
+
+
+def test_device_pointers_match_host_pointers(rff):
+    X, Y = synth.ridge(n=300, d=4, seed=3)
+    kw = dict(loss="squared", lam=1e-3, sigma=1.0, D=128, R=1, C=2, seed=8, m=1)
+    a = rff.Solver(**kw)
+    a.set_data(X, Y)
+    a.solve(5, stats=False)
+    b = rff.Solver(**kw)
+    b.set_data(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda())
+    b.solve(5, stats=False)
+    out = torch.empty((128, 1), dtype=torch.float32, device="cuda")
+    b.weights(out)
+    assert np.array_equal(out.cpu().numpy(), a.weights())
+    sq = torch.empty((50, 1), dtype=torch.float32, device="cuda")
+    b.predict(torch.from_numpy(X[:50]).cuda(), sq)
+    assert np.array_equal(sq.cpu().numpy(), a.predict(X[:50]))
+    a.close()
+    b.close()
