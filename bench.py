@@ -112,13 +112,13 @@ def solver_kw(w, prec):
 def flops_per_iter(w, prec):
     """Algorithmic work of one iteration.  Useful FP32-equivalent flops: two
     regenerations of X.G (2 n d D each) and two chained products (2 n D m each),
-    the three s_j x s_j x m projections per block.  Executed BF16 tensor flops of
+    the s_j x s_j x m product with the cached inverse per block.  Executed BF16 tensor flops of
     the split path: 3 products for X.G and 3 for each chained product at m_pad."""
     n, d, D, m, R, C = w["n"], w["d"], w["D"], w["m"], w["R"], w["C"]
     mpad = -(-m // 16) * 16
     dpad = -(-d // 64) * 64
     s = D // C
-    useful = 2 * (2 * n * d * D) + 2 * (2 * n * D * m) + R * C * 3 * 2 * s * s * m
+    useful = 2 * (2 * n * d * D) + 2 * (2 * n * D * m) + R * C * 2 * s * s * m
     pass_tc = 3 * 2 * n * dpad * D + 3 * 2 * n * D * mpad       # one pass, executed on tensor cores
     pass_simt = 2 * n * dpad * D + 2 * n * D * mpad              # one pass, FP32 FMA
     return useful, (pass_tc if prec == "split_bf16" else pass_simt)

@@ -163,7 +163,7 @@ typedef struct {
   int64_t launches;        /* kernels launched by those iterations                           */
   double ms_prox_reg;      /* W <- prox_r(Wbar - mu)                                         */
   double ms_pass1;         /* Z_ij^T V_ij, Z regenerated (fused kernel)                      */
-  double ms_project;       /* right-hand side, Q_ij products and the refinement step         */
+  double ms_project;       /* right-hand side and the products with the cached Q_ij          */
   double ms_pass2;         /* Z_ij W'_ij, Z regenerated (fused kernel)                       */
   double ms_exchange;      /* row exchange, nu update, loss prox, next V_ij                  */
   double ms_average;       /* Wbar, mu, mu'_ij updates                                      */

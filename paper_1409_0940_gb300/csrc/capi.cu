@@ -49,9 +49,9 @@ struct rff_admm_s {
   __nv_bfloat16 *VThi = nullptr, *VTlo = nullptr, *WThi = nullptr, *WTlo = nullptr, *WbThi = nullptr,
                 *WbTlo = nullptr;
   float *W = nullptr, *Wbar = nullptr, *mu = nullptr, *What = nullptr, *muij = nullptr, *rhs = nullptr,
-        *xtmp = nullptr, *Rpart = nullptr;
-  float *Q32 = nullptr, *H32 = nullptr;
-  GemmDesc* gdesc = nullptr;  // 3 x R*C
+        *Rpart = nullptr;
+  float* Q32 = nullptr;       // cached (I + Z_ij^T Z_ij)^-1 per block
+  GemmDesc* gdesc = nullptr;  // R*C
   double* partials = nullptr;
   int* flag = nullptr;
   float *nu_old = nullptr, *Obar_old = nullptr, *mu_old = nullptr, *Wbar_old = nullptr, *muij_old = nullptr;
@@ -168,11 +168,11 @@ size_t working_set_bytes(const rff_admm_s& s) {
   t += (size_t)s.C * s.nslots * s.mpad * f * 2;                 // Op, V32
   if (s.split_path()) t += (size_t)s.C * s.nslots * s.mpad * b2 * 2;
   t += (size_t)s.fslots * s.mpad * f * 5;                       // W, Wbar, mu, mu_old, Wbar_old
-  t += (size_t)s.R * s.fslots * s.mpad * f * (5 + s.nsplit);    // What, muij, rhs, xtmp, muij_old, Rpart
+  t += (size_t)s.R * s.fslots * s.mpad * f * (4 + s.nsplit);    // What, muij, rhs, muij_old, Rpart
   if (s.split_path()) t += (size_t)s.R * s.fslots * s.mpad * b2 * 2 + (size_t)s.fslots * s.mpad * b2 * 2;
   size_t fac = 0;
   for (int j = 0; j < s.C; ++j) fac += (size_t)s.col_size[j] * s.col_size[j];
-  t += fac * s.R * f * 2;
+  t += fac * s.R * f;
   return t + (64u << 20);
 }
 
@@ -340,11 +340,9 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   AL(s.muij, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.muij_old, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.rhs, (int64_t)s.R * s.fslots * s.mpad);
-  AL(s.xtmp, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.Rpart, (int64_t)s.nsplit * s.R * s.fslots * s.mpad);
   AL(s.Q32, s.foff.back());
-  AL(s.H32, s.foff.back());
-  AL(s.gdesc, 3 * s.R * s.C);
+  AL(s.gdesc, s.R * s.C);
   AL(s.partials, 1024);
   AL(s.flag, 4);
 #undef AL
@@ -406,7 +404,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   CK(cudaMemsetAsync(s.V32, 0, rowb * s.C, s.st));
   CK(cudaMemsetAsync(s.Op, 0, rowb * s.C, s.st));
   for (float* b : {s.W, s.Wbar, s.mu}) CK(cudaMemsetAsync(b, 0, colb, s.st));
-  for (float* b : {s.What, s.muij, s.rhs, s.xtmp}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
+  for (float* b : {s.What, s.muij, s.rhs}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
   CK(cudaMemsetAsync(s.Rpart, 0, colb * s.R * s.nsplit, s.st));
   if (s.split_path()) {
     CK(cudaMemsetAsync(s.VThi, 0, rowb / 2 * s.C, s.st));
@@ -439,7 +437,7 @@ rff_status setup_factors(rff_admm_t h) {
   size_t fr = 0, tot = 0;
   CK(cudaMemGetInfo(&fr, &tot));
   const size_t per_block = (size_t)smax * smax * 8 * 2;
-  const int64_t chunk_rows = std::min<int64_t>(32768, round_up(*std::max_element(s.row_size.begin(), s.row_size.end()), 64));
+  const int64_t chunk_rows = std::min<int64_t>(32768, round_up(*std::max_element(s.row_size.begin(), s.row_size.end()), SLOT));
   const size_t zbytes = (size_t)chunk_rows * smax * 4;
   size_t budget = (size_t)(fr * 0.6);
   budget = budget > zbytes + (256u << 20) ? budget - zbytes - (256u << 20) : 0;
@@ -477,7 +475,6 @@ rff_status setup_factors(rff_admm_t h) {
         CK(launch_gram_f32_to_f64(Zc, sj, nr, sj, Hb, sj, s.st));
       }
       CK(launch_add_identity_and_mirror(Hb, sj, sj, s.st));
-      CK(launch_convert_f64_f32(Hb, s.H32 + s.foff[blk], sj * sj, s.st));
       CK(cudaMemsetAsync(Qb, 0, sj * sj * 8, s.st));
       CK(launch_set_diag(Qb, sj, sj, 1.0, s.st));
       jobs.push_back(MatJob{Hb, sj, (int)sj, Qb, sj, info + bb});
@@ -496,19 +493,14 @@ rff_status setup_factors(rff_admm_t h) {
         return h->fail(RFF_ENUMERIC, "Gram matrix of block " + std::to_string(b0 + bb) +
                                          " not positive definite at column " + std::to_string(hinfo[bb] - 1));
   }
-  // iteration GEMM descriptors: x = Q rhs; r = rhs - H x; x += Q r
-  std::vector<GemmDesc> g(3 * nblocks);
+  // iteration GEMM descriptors: x = Q rhs
+  std::vector<GemmDesc> g(nblocks);
   for (int i = 0; i < s.R; ++i)
     for (int j = 0; j < s.C; ++j) {
       const int64_t blk = (int64_t)i * s.C + j, sj = s.col_size[j];
       const int64_t off = ((int64_t)i * s.fslots + s.col_slot[j]) * s.mpad;
       float* Qb = s.Q32 + s.foff[blk];
-      float* Hb = s.H32 + s.foff[blk];
       g[blk] = GemmDesc{Qb, s.rhs + off, nullptr, s.What + off, (int)sj, (int)s.mpad, (int)sj, sj, s.mpad, 0, s.mpad};
-      g[nblocks + blk] = GemmDesc{Hb, s.What + off, s.rhs + off, s.xtmp + off, (int)sj, (int)s.mpad, (int)sj, sj,
-                                  s.mpad, s.mpad, s.mpad};
-      g[2 * nblocks + blk] = GemmDesc{Qb, s.xtmp + off, s.What + off, s.What + off, (int)sj, (int)s.mpad, (int)sj, sj,
-                                      s.mpad, s.mpad, s.mpad};
     }
   CK(cudaMemcpyAsync(s.gdesc, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, s.st));
   CK(cudaStreamSynchronize(s.st));
@@ -569,11 +561,11 @@ rff_status iterate(rff_admm_t h, int k) {
     CK(launch_pass1_simt(a, s.fslots, s.st));
   }
   if ((r = mark(h, k, 2)) != RFF_OK) return r;
-  // graph projection, eq. (gpWij): W'_ij = Q_ij (Wbar_j - mu'_ij + R_ij), one refinement step with H_ij
+  // graph projection, eq. (gpWij): W'_ij = Q_ij (Wbar_j - mu'_ij + R_ij) with the cached inverse.
+  // (A refinement step r = rhs - H x computed in FP32 adds more rounding than it removes, and an
+  // FP64 or compensated residual costs several times the solve on this part's FP64/FP32 pipes.)
   CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st));
   CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st));
-  CK(launch_gemm_f32_nn(s.gdesc + nblocks, (int)nblocks, (int)smax, (int)s.mpad, -1.f, 1.f, s.st));
-  CK(launch_gemm_f32_nn(s.gdesc + 2 * nblocks, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 1.f, s.st));
   if ((r = mark(h, k, 3)) != RFF_OK) return r;
   // pass 2: O'_ij = Z_ij W'_ij (eq. (gpOij))
   if (s.split_path()) {
@@ -600,7 +592,7 @@ rff_status iterate(rff_admm_t h, int k) {
   // averaging and dual updates
   CK(launch_avg_dual(s.W, s.What, s.R, nfe, s.Wbar, s.mu, s.muij, s.st));
   if ((r = mark(h, k, 6)) != RFF_OK) return r;
-  s.launches += s.split_path() ? 11 : 9;
+  s.launches += s.split_path() ? 9 : 7;
   return RFF_OK;
 }
 
@@ -655,6 +647,7 @@ TcView tc_view(const rff_admm_s& s) {
   v.R = s.R; v.C = s.C; v.nsplit = s.nsplit;
   v.row_slot = s.row_slot.data(); v.row_size = s.row_size.data();
   v.col_slot = s.col_slot.data(); v.col_size = s.col_size.data();
+  v.d_row_slot = s.d_row_slot; v.d_row_size = s.d_row_size; v.d_col_slot = s.d_col_slot; v.d_col_size = s.d_col_size;
   v.scale = (float)std::sqrt(2.0 / (double)s.D);
   v.st = s.st;
   return v;
@@ -699,6 +692,8 @@ rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats) {
   }
   CK(cudaEventRecord(e2, s.st));
   CK(cudaEventSynchronize(e2));
+  if (s.split_path() && tc_error_word() != 0)
+    return h->fail(RFF_ETIMEOUT, "a tensor-core pass gave up waiting (device error word set)");
   if (s.profiling) {
     double* acc[6] = {&s.prof.ms_prox_reg, &s.prof.ms_pass1, &s.prof.ms_project, &s.prof.ms_pass2,
                       &s.prof.ms_exchange, &s.prof.ms_average};
@@ -908,7 +903,7 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t nf = k_hi - k_lo, dld = round_up(d, 64), np = round_up(n, SLOT), fp = round_up(nf, SLOT);
   const size_t bytes = (size_t)np * dld * 4 + (size_t)fp * dld * 4 + (size_t)fp * 4 + (size_t)np * 4 + (size_t)fp * 4 +
-                       (size_t)(np + fp) * dld * 2 * 2 + 4096;
+                       (size_t)(np + fp) * dld * 2 * 2 + 64 + 4096;
   char* base = nullptr;
   if (cudaMallocAsync((void**)&base, bytes, st) != cudaSuccess) {
     cudaGetLastError();
@@ -923,10 +918,13 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
   __nv_bfloat16* Xl = Xh + np * dld;
   __nv_bfloat16* Gh = Xl + np * dld;
   __nv_bfloat16* Gl = Gh + fp * dld;
+  int64_t* tabs = reinterpret_cast<int64_t*>(Gl + fp * dld);   // {0, n, 0, nf}
   std::vector<int32_t> r(np), f(fp);
+  const int64_t htab[4] = {0, n, 0, nf};
   for (int64_t i = 0; i < np; ++i) r[i] = i < n ? (int32_t)i : -1;
   for (int64_t i = 0; i < fp; ++i) f[i] = i < nf ? (int32_t)(k_lo + i) : -1;
   cudaError_t e = cudaMemcpyAsync(rok, r.data(), np * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tabs, htab, sizeof(htab), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(fok, f.data(), fp * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = launch_gather_rows(X, d, d, rok, np, X32, dld, st);
   if (e == cudaSuccess)
@@ -945,16 +943,20 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
         v.bias = bias; v.row_ok = rok; v.feat_ok = fok;
         v.nslots = np; v.fslots = fp; v.dld = dld; v.mpad = 16; v.R = 1; v.C = 1; v.nsplit = 1;
         v.row_slot = &zero; v.row_size = &n; v.col_slot = &zero; v.col_size = &nf;
+        v.d_row_slot = tabs; v.d_row_size = tabs + 1; v.d_col_slot = tabs + 2; v.d_col_size = tabs + 3;
         v.scale = scale; v.st = st;
         e = tc_write_z(v, 0, n, 0, nf, Z, nf);
       }
     }
   }
+  // the host vectors above are read by the asynchronous copies: finish before they go
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(base, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorNotSupported ? RFF_EINVAL : RFF_ECUDA;
   }
+  if (prec == RFF_PREC_SPLIT_BF16 && tc_error_word() != 0) return RFF_ETIMEOUT;
   return RFF_OK;
 }
 
@@ -990,6 +992,7 @@ rff_status rff_cholesky_f64(double* A, int32_t batch, int32_t s, int32_t* info, 
   for (int b = 0; b < batch; ++b) jobs.push_back(MatJob{A + (size_t)b * s * s, s, s, nullptr, 0, info + b});
   cudaError_t e = cudaMemsetAsync(info, 0, (size_t)batch * 4, st);
   if (e == cudaSuccess) e = factor_and_invert_f64(jobs, false, scr, st);
+  if (e == cudaSuccess) e = launch_zero_strict_upper(A, s, batch, st);
   cudaFreeAsync(scr, st);
   return e == cudaSuccess ? RFF_OK : RFF_ECUDA;
 }

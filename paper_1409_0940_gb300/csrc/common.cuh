@@ -54,27 +54,27 @@ __host__ __device__ __forceinline__ double uniform01(uint32_t w) {
 
 // ------------------------------------------------------------------ cosine
 // cos(x) for the feature map z = sqrt(2/D) cos(w.x + b).  Range reduction by
-// Cody-Waite with a two-term 2*pi (x = k 2pi + r, |r| <= pi, the products k*2pi
-// fused into FMAs), then a polynomial in s = r^2 of degree 6 whose coefficients
-// were fitted for this library by iteratively reweighted least squares (Lawson's
-// algorithm) on [0, pi^2] (see fit_cos_poly.py beside this file).  Fit error
-// 1.1e-8; measured in float32 evaluation, |error| <= 4e-7 on [-pi, pi].
+// Cody-Waite with a two-term pi (x = k pi + r, |r| <= pi/2, the products k*pi
+// fused into FMAs), cos(x) = (-1)^k cos(r), and cos(r) as a polynomial in
+// s = r^2 of degree 5 whose coefficients were fitted for this library by
+// iteratively reweighted least squares (Lawson's algorithm) on [0, (pi/2)^2]
+// (fit_cos_poly.py beside this file).  Fit error 2.2e-10; float32 evaluation
+// error <= 1.2e-7 on [-pi/2, pi/2].
 __device__ __forceinline__ float cos_rr(float x) {
-  const float inv_2pi = 0.159154943091895336f;
-  const float two_pi_hi = 6.28318548202514648f;   // float32 nearest to 2 pi
-  const float two_pi_lo = -1.74845553146951717e-07f;  // 2 pi - two_pi_hi
-  const float k = rintf(x * inv_2pi);
-  float r = fmaf(-k, two_pi_hi, x);
-  r = fmaf(-k, two_pi_lo, r);
+  const float inv_pi = 0.318309886183790672f;
+  const float pi_hi = 3.14159274101257324f;       // float32 nearest to pi
+  const float pi_lo = -8.74227765734758577e-08f;  // pi - pi_hi
+  const float k = rintf(x * inv_pi);
+  float r = fmaf(-k, pi_hi, x);
+  r = fmaf(-k, pi_lo, r);
   const float s = r * r;
-  float p = 1.7247605565984259e-09f;
-  p = fmaf(p, s, -2.7079772735305596e-07f);
-  p = fmaf(p, s, 2.4769966330495663e-05f);
-  p = fmaf(p, s, -0.0013887807726860046f);
-  p = fmaf(p, s, 0.04166648909449577f);
-  p = fmaf(p, s, -0.49999988079071045f);
+  float p = -2.605149518331018e-07f;
+  p = fmaf(p, s, 2.476016197761055e-05f);
+  p = fmaf(p, s, -0.0013888361863791943f);
+  p = fmaf(p, s, 0.04166663810610771f);
+  p = fmaf(p, s, -0.5f);
   p = fmaf(p, s, 1.0f);
-  return p;
+  return (static_cast<int>(k) & 1) ? -p : p;
 }
 
 // ------------------------------------------------------------------ BF16 split

@@ -139,8 +139,20 @@ __global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict_
 }
 
 // ------------------------------------------------------------------ Gram
-// H (s x s, f64, lower tiles) += Z^T Z for Z (n x s) float32.  FP32 products
-// summed over chunks of 256 rows in FP32, chunk sums accumulated in FP64.
+// H (s x s, f64, lower tiles) += Z^T Z for Z (n x s) float32.  Products and
+// 32-row partial sums in FP32; the partial sums are accumulated in a
+// float-float pair (Knuth's TwoSum), so the sum over all n rows carries about
+// the error of one 32-term FP32 sum.  (An FP32 accumulator over all rows, or
+// over chunks of a few hundred rows, perturbs H enough to move the ADMM fixed
+// point by ~kappa(H) * 1e-7.)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (x - bb);
+  hi = s;
+  lo += e;
+}
+
 __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ Z, int64_t ldz, int64_t n, int64_t s,
                                               double* __restrict__ H, int64_t ldh) {
   const int tm = blockIdx.x, tn = blockIdx.y;
@@ -149,9 +161,7 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ Z, int64
   __shared__ __align__(16) float As[32][64 + 4];
   __shared__ __align__(16) float Bs[32][64 + 4];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  double acc64[4][4] = {};
-  float acc[4][4] = {};
-  int chunk = 0;
+  float hi[4][4] = {}, lo[4][4] = {};
   for (int64_t r0 = 0; r0 < n; r0 += 32) {
     for (int t = tid; t < 64 * 32; t += 256) {
       const int c = t % 64, r = t / 64;
@@ -160,6 +170,7 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ Z, int64
       Bs[r][c] = (gr < n && b0 + c < s) ? Z[gr * ldz + b0 + c] : 0.f;
     }
     __syncthreads();
+    float acc[4][4] = {};
 #pragma unroll 8
     for (int k = 0; k < 32; ++k) {
       const float4 av = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
@@ -171,23 +182,17 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ Z, int64
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
-    if (++chunk == 8) {
-      chunk = 0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          acc64[i][j] += (double)acc[i][j];
-          acc[i][j] = 0.f;
-        }
-    }
+      for (int j = 0; j < 4; ++j) two_sum_acc(hi[i][j], lo[i][j], acc[i][j]);
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int64_t gm = a0 + ty * 4 + i, gn = b0 + tx * 4 + j;
-      if (gm < s && gn < s) H[gm * ldh + gn] += acc64[i][j] + (double)acc[i][j];
+      if (gm < s && gn < s) H[gm * ldh + gn] += (double)hi[i][j] + (double)lo[i][j];
     }
 }
 
@@ -254,6 +259,12 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const DiagJob* __restrict__ 
   if (tid == 0 && bad && jb.info && *jb.info == 0) *jb.info = bad;
 }
 
+__global__ void k_zero_strict_upper(double* A, int64_t s) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= s * s) return;
+  if (t % s > t / s) A[t] = 0.0;
+}
+
 __global__ void k_add_identity_and_mirror(double* H, int64_t ldh, int64_t s) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= s * s) return;
@@ -285,6 +296,13 @@ cudaError_t launch_gram_f32_to_f64(const float* Z, int64_t ldz, int64_t n, int64
   if (n <= 0 || s <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(s, 64), (unsigned)ceil_div(s, 64));
   k_gram<<<grid, 256, 0, st>>>(Z, ldz, n, s, H, ldh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_strict_upper(double* A, int64_t s, int nbatch, cudaStream_t st) {
+  for (int b = 0; b < nbatch; ++b) {
+    k_zero_strict_upper<<<(unsigned)ceil_div(s * s, 256), 256, 0, st>>>(A + (size_t)b * s * s, s);
+  }
   return cudaGetLastError();
 }
 

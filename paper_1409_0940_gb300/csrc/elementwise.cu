@@ -49,8 +49,9 @@ __device__ __forceinline__ float prox_logistic(float v, float y, float t, int it
     const float f = p - a - t * sm;
     if (f < 0.f) lo = p; else hi = p;
     const float fp = 1.f + t * sm * (1.f - sm);
+    if (f == 0.f) break;
     float q = p - f / fp;
-    if (!(q > lo && q < hi)) q = 0.5f * (lo + hi);
+    if (!(q >= lo && q <= hi)) q = 0.5f * (lo + hi);
     p = q;
   }
   return y * p;
@@ -73,14 +74,37 @@ __device__ __forceinline__ float warp_max(float x) {
   return x;
 }
 
-// Multinomial logistic prox of one row, one warp, lanes over the m outputs
-// (up to 8 per lane): Newton on o - v + t (softmax(o) - e_c) = 0 with the
-// Hessian I + t (diag p - p p^T) inverted by the Sherman-Morrison formula.
-// c = argmax_k y_k (first maximum).
+// Multinomial logistic prox of one row, one warp, lanes over the m outputs (up
+// to 8 per lane), c = argmax_k y_k (first maximum).  The optimality condition
+// o = v - t (softmax(o) - e_c) is solved through s = log sum_k exp(o_k): with
+// w = v + t e_c, each p_k = exp(o_k - s) satisfies log p_k + t p_k = w_k - s,
+// a scalar equation solved by Newton from a Lambert-W estimate, and s is the
+// root of F(s) = sum_k p_k(s) - 1, which is convex and decreasing; Newton on s
+// from s0 = max_k w_k - t (where F >= 0) therefore rises monotonically to the
+// root.  Finally o = w - t p.
 constexpr int MAXPL = 8;
+
+__device__ __forceinline__ float solve_logp(float a, float t, float logt) {
+  // q = log p with q + t e^q = a; start from W(t e^a) ~ log1p(z) or L - log L
+  const float L = logt + a;
+  const float W0 = (L < 1.f) ? log1pf(expf(L)) : L - logf(L);
+  float q = logf(fmaxf(W0, 1e-37f)) - logt;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float e = expf(q);
+    q -= (q + t * e - a) / (1.f + t * e);
+  }
+  return q;
+}
+
 __device__ void prox_multinomial_row(const float (&v)[MAXPL], const float (&y)[MAXPL], int m, float t, int iters,
                                      float (&o)[MAXPL]) {
   const int lane = threadIdx.x & 31;
+  if (!(t > 1e-30f)) {
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) o[q] = v[q];
+    return;
+  }
   // class index: first maximum of y
   float best = -INFINITY;
   int bidx = 1 << 30;
@@ -95,38 +119,35 @@ __device__ void prox_multinomial_row(const float (&v)[MAXPL], const float (&y)[M
     const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
     if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
   }
+  float w[MAXPL];
+  float wmax = -INFINITY;
 #pragma unroll
-  for (int q = 0; q < MAXPL; ++q) o[q] = v[q];
+  for (int q = 0; q < MAXPL; ++q) {
+    const int k = lane + 32 * q;
+    w[q] = v[q] + (k == bidx ? t : 0.f);
+    if (k < m) wmax = fmaxf(wmax, w[q]);
+  }
+  wmax = warp_max(wmax);
+  const float logt = logf(t);
+  float s = wmax - t;
   for (int it = 0; it < iters; ++it) {
-    float mx = -INFINITY;
-#pragma unroll
-    for (int q = 0; q < MAXPL; ++q)
-      if (lane + 32 * q < m) mx = fmaxf(mx, o[q]);
-    mx = warp_max(mx);
-    float e[MAXPL], se = 0.f;
+    float F = 0.f, dF = 0.f;
 #pragma unroll
     for (int q = 0; q < MAXPL; ++q) {
-      e[q] = (lane + 32 * q < m) ? __expf(o[q] - mx) : 0.f;
-      se += e[q];
+      if (lane + 32 * q < m) {
+        const float p = expf(solve_logp(w[q] - s, t, logt));
+        F += p;
+        dF += p / (1.f + t * p);
+      }
     }
-    se = warp_sum(se);
-    float g[MAXPL], dg[MAXPL], dp[MAXPL], s1 = 0.f, s2 = 0.f;
+    F = warp_sum(F) - 1.f;
+    dF = warp_sum(dF);
+    s += F / dF;
+  }
 #pragma unroll
-    for (int q = 0; q < MAXPL; ++q) {
-      const int k = lane + 32 * q;
-      const float pk = e[q] / se;
-      g[q] = (k < m) ? (o[q] - v[q] + t * (pk - (k == bidx ? 1.f : 0.f))) : 0.f;
-      const float dinv = 1.f / (1.f + t * pk);
-      dg[q] = dinv * g[q];
-      dp[q] = (k < m) ? dinv * pk : 0.f;
-      s1 += pk * dg[q] * (k < m);
-      s2 += pk * dp[q];
-    }
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    const float coef = t * s1 / (1.f - t * s2);
-#pragma unroll
-    for (int q = 0; q < MAXPL; ++q) o[q] -= dg[q] + coef * dp[q];
+  for (int q = 0; q < MAXPL; ++q) {
+    const int k = lane + 32 * q;
+    o[q] = (k < m) ? w[q] - t * expf(solve_logp(w[q] - s, t, logt)) : 0.f;
   }
 }
 

@@ -1,7 +1,7 @@
 """Fit the polynomial behind cos_rr() in common.cuh (run by hand; not part of the build).
 
-cos(r) for r in [-pi, pi] is written as p(s), s = r^2, a polynomial of degree
-DEG in s.  Lawson's algorithm (iteratively reweighted least squares) drives the
+After the reduction x = k pi + r, cos(x) = (-1)^k cos(r) with |r| <= pi/2, and
+cos(r) is written as p(s), s = r^2, a polynomial of degree DEG in s.  Lawson's algorithm (iteratively reweighted least squares) drives the
 least-squares fit on a dense grid of s towards the minimax one.  Prints the
 float32 coefficients (constant term first), the fit error and the error of a
 float32 Horner evaluation.
@@ -10,15 +10,15 @@ import sys
 
 import numpy as np
 
-DEG = int(sys.argv[1]) if len(sys.argv) > 1 else 6
+DEG = int(sys.argv[1]) if len(sys.argv) > 1 else 5
 
 
 def main():
-    s = np.linspace(0.0, np.pi ** 2, 20001)
+    s = np.linspace(0.0, (np.pi / 2) ** 2, 20001)
     f = np.cos(np.sqrt(s))
     V = np.vander(s, DEG + 1, increasing=True)
     w = np.ones_like(s)
-    for _ in range(200):
+    for _ in range(300):
         c, *_ = np.linalg.lstsq(V * np.sqrt(w)[:, None], f * np.sqrt(w), rcond=None)
         e = np.abs(V @ c - f)
         w = w * e

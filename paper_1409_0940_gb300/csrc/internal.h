@@ -90,6 +90,7 @@ struct DiagJob {   // one matrix of a batched factorisation
 };
 cudaError_t launch_potrf_diag(const DiagJob* jobs_dev, int njobs, int kcol, cudaStream_t st);
 cudaError_t launch_add_identity_and_mirror(double* H, int64_t ldh, int64_t s, cudaStream_t st);
+cudaError_t launch_zero_strict_upper(double* A, int64_t s, int nbatch, cudaStream_t st);
 struct MatJob {    // host description of one matrix to factor (and invert)
   double* A;       // in: SPD matrix; out: lower Cholesky factor
   int64_t ld;

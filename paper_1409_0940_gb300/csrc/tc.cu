@@ -1,14 +1,706 @@
-// Tensor-core regeneration passes (placeholder until the tcgen05 kernels land).
+// Tensor-core regeneration passes of the split-BF16 path (tcgen05 + TMA, sm_103a).
+//
+// One CTA owns a 128-row tile of operand A (data rows in pass 2 / prediction /
+// materialisation; feature rows in pass 1) and walks a run of 128-row tiles of
+// operand B (feature tiles, or data-row tiles).  For every B tile:
+//
+//   acc1 (TMEM, 128 x 128 fp32) = A_hi.B_hi^T + A_hi.B_lo^T + A_lo.B_hi^T     (X G, split BF16)
+//   Z = sqrt(2/D) cos(acc1 + b)  -> Z_hi + Z_lo in shared memory            (the transform, Sec. 4)
+//   acc2 (TMEM, 128 x m_pad fp32) += Z_hi.M_hi + Z_hi.M_lo + Z_lo.M_hi       (chained product)
+//
+// so that Z never reaches global memory (Sec. 3: Z_ij regenerated on the fly).
+// acc2 is written out when a group of B tiles ends: per column block in pass 2
+// (O'_ij = Z_ij W'_ij, eq. (gpOij)), once per split in pass 1 (Z_ij^T V_ij, the
+// right-hand side of eq. (gpWij)), once for prediction.
+//
+// Warp roles (320 threads): warp 0 issues TMA loads, warp 1 owns TMEM and issues
+// the MMAs (one thread), warps 2..9 run the epilogue (cos, split, stores); warps
+// 2..5 take accumulator columns 0..63 and warps 6..9 columns 64..127, each warp
+// the 32 TMEM lanes of its index mod 4.  acc1 is double-buffered so the cosine
+// of tile t overlaps the products of tile t+1.  Every wait is bounded: on a
+// timeout the CTA records an error code, stops issuing work, waits (bounded)
+// for its own copies and products in flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
 #include "tc.h"
 
 namespace rff {
-cudaError_t tc_write_z(const TcView&, int64_t, int64_t, int64_t, int64_t, float*, int64_t) { return cudaErrorNotSupported; }
-cudaError_t tc_pass1(const TcView&, float*) { return cudaErrorNotSupported; }
-cudaError_t tc_pass2(const TcView&, const __nv_bfloat16*, const __nv_bfloat16*, int64_t, float*, int) {
-  return cudaErrorNotSupported;
+
+namespace {
+
+constexpr int MODE_WRITEZ = 0, MODE_PASS1 = 1, MODE_PASS2 = 2, MODE_PREDICT = 3;
+constexpr int NSTAGE = 2;
+constexpr uint32_t STAGE_BYTES = 65536;     // A hi/lo + B hi/lo, 128 x 64 BF16 each
+constexpr uint32_t TILE_BYTES = 16384;      // 128 rows x 128 bytes
+constexpr uint32_t ZBYTES = 65536;          // Z hi (32 KB) + Z lo (32 KB), two 64-column atoms each
+constexpr int NEPI = 8;                     // epilogue warps
+constexpr int NTHREADS = 64 + 32 * NEPI;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACC2_COL = 256;
+constexpr int MAXG = 256;                   // groups (column blocks) per CTA
+constexpr size_t SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + ZBYTES + 2048 + MAXG * 24;
+
+// error codes written to the error word
+constexpr int ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPI = 4;
+
+struct TcArgs {
+  CUtensorMap tA_hi, tA_lo, tB_hi, tB_lo, tM_hi, tM_lo;
+  int mode, nk, mpad, R, C, nsplit;
+  const float* bias;
+  const int32_t* a_ok;
+  const int32_t* b_ok;
+  float scale;
+  const int64_t* row_slot;
+  const int64_t* row_size;
+  const int64_t* col_slot;
+  const int64_t* col_size;
+  int64_t fslots;
+  float* out;
+  int64_t out_block_stride;
+  int64_t wz_r0, wz_nr, wz_f0, wz_nf, ldo;  // materialisation window
+  int* err;
+  long long timeout_cycles;
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-cudaError_t tc_predict(const TcView&, const __nv_bfloat16*, const __nv_bfloat16*, int64_t, const __nv_bfloat16*,
-                       const __nv_bfloat16*, float*) {
-  return cudaErrorNotSupported;
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// K-major operand in the 128-byte swizzled layout written by TMA: rows of 128 bytes,
+// 8-row groups 1024 bytes apart.  Start address advanced by 32 bytes per K step of 16.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
+  d |= (uint64_t)1 << 16;                         // leading byte offset (unused for this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                         // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both operands K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// ------------------------------------------------------------------ shared state
+struct Shared {
+  uint64_t full[NSTAGE], empty[NSTAGE];
+  uint64_t acc1_full[2], acc1_empty[2];
+  uint64_t z_full, z_empty, acc2_full, acc2_empty, mma_done;
+  uint32_t tmem_base;
+  int abort_flag;
+  int ngroups;
+  int m_y;
+  int64_t a_row0;
+  int64_t g_b0[MAXG];
+  int g_nt[MAXG];
+  float* g_out[MAXG];
+};
+
+// bounded wait; one thread polls.  false = the CTA is aborting
+__device__ __forceinline__ bool wait1(uint32_t bar, uint32_t parity, Shared& sh, const TcArgs& a, int code) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*(volatile int*)&sh.abort_flag) return false;
+    if (clock64() - t0 > a.timeout_cycles) {
+      *(volatile int*)&sh.abort_flag = 1;
+      atomicOr(a.err, code);
+      return false;
+    }
+  }
+}
+
+// warp-uniform bounded wait: lane 0 polls, the verdict is broadcast
+__device__ __forceinline__ bool waitw(uint32_t bar, uint32_t parity, Shared& sh, const TcArgs& a, int code) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = wait1(bar, parity, sh, a, code) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant__ TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment of the operand tiles (the swizzle pattern repeats every 1024 bytes)
+  unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  unsigned char* stages = base;
+  unsigned char* zbuf = base + NSTAGE * STAGE_BYTES;
+  Shared& sh = *reinterpret_cast<Shared*>(zbuf + ZBYTES);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const bool chain = a.mode != MODE_WRITEZ;
+
+  // ---------------- plan: A tile, chain-operand row, groups of B tiles
+  int64_t a_row0 = 0;
+  int m_y = 0;
+  if (threadIdx.x == 0) {
+    sh.abort_flag = 0;
+    int ng = 0;
+    if (a.mode == MODE_PASS2 || a.mode == MODE_PREDICT) {
+      a_row0 = (int64_t)blockIdx.x * 128;
+      int i = 0;
+      if (a.mode == MODE_PASS2)
+        while (i + 1 < a.R && a.row_slot[i + 1] <= a_row0) ++i;
+      m_y = i * a.mpad;
+      if (a.mode == MODE_PASS2) {
+        for (int j = 0; j < a.C && ng < MAXG; ++j) {
+          sh.g_b0[ng] = a.col_slot[j];
+          sh.g_nt[ng] = (int)ceil_div(a.col_size[j], 128);
+          sh.g_out[ng] = a.out + j * a.out_block_stride + a_row0 * a.mpad;
+          ++ng;
+        }
+      } else {
+        sh.g_b0[0] = 0;
+        sh.g_nt[0] = (int)(a.fslots / 128);
+        sh.g_out[0] = a.out + a_row0 * a.mpad;
+        ng = 1;
+      }
+    } else if (a.mode == MODE_PASS1) {
+      a_row0 = (int64_t)blockIdx.x * 128;
+      int j = 0;
+      while (j + 1 < a.C && a.col_slot[j + 1] <= a_row0) ++j;
+      const int i = blockIdx.y, split = blockIdx.z;
+      const int64_t nrt = ceil_div(a.row_size[i], 128);
+      const int64_t t0 = split * nrt / a.nsplit, t1 = (split + 1) * nrt / a.nsplit;
+      m_y = j * a.mpad;
+      if (a_row0 - a.col_slot[j] < a.col_size[j] && t1 > t0) {
+        sh.g_b0[0] = a.row_slot[i] + t0 * 128;
+        sh.g_nt[0] = (int)(t1 - t0);
+        sh.g_out[0] = a.out + ((int64_t)split * a.R + i) * a.out_block_stride + a_row0 * a.mpad;
+        ng = 1;
+      }
+    } else {  // materialisation window
+      a_row0 = a.wz_r0 + (int64_t)blockIdx.x * 128;
+      sh.g_b0[0] = a.wz_f0;
+      sh.g_nt[0] = (int)ceil_div(a.wz_nf, 128);
+      sh.g_out[0] = nullptr;
+      ng = 1;
+    }
+    sh.ngroups = ng;
+    sh.a_row0 = a_row0;
+    sh.m_y = m_y;
+  }
+  __syncthreads();
+  const int ngroups = sh.ngroups;
+  if (ngroups == 0) return;      // nothing valid in this tile (uniform across the CTA)
+  a_row0 = sh.a_row0;
+  m_y = sh.m_y;
+
+  const uint32_t bar_full = smem_u32(&sh.full[0]), bar_empty = smem_u32(&sh.empty[0]);
+  const uint32_t bar_a1f = smem_u32(&sh.acc1_full[0]), bar_a1e = smem_u32(&sh.acc1_empty[0]);
+  const uint32_t bar_zf = smem_u32(&sh.z_full), bar_ze = smem_u32(&sh.z_empty);
+  const uint32_t bar_a2f = smem_u32(&sh.acc2_full), bar_a2e = smem_u32(&sh.acc2_empty);
+  const uint32_t bar_done = smem_u32(&sh.mma_done);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar_a1f + 8 * b, 1);
+      mbar_init(bar_a1e + 8 * b, NEPI);
+    }
+    mbar_init(bar_zf, NEPI);
+    mbar_init(bar_ze, 1);
+    mbar_init(bar_a2f, 1);
+    mbar_init(bar_a2e, NEPI);
+    mbar_init(bar_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sh.tmem_base;
+  const int nk = a.nk;
+  const uint32_t mbytes = (uint32_t)a.mpad * 128;   // one chain operand tile (hi or lo), 64 K-columns
+
+  if (warp == 0) {
+    // ================= TMA producer =================
+    if (lane == 0) {
+      tma_prefetch_desc(&a.tA_hi);
+      tma_prefetch_desc(&a.tB_hi);
+      uint32_t it = 0;   // ring uses
+      bool ok = true;
+      int64_t prev_b = -1;
+      auto acquire = [&](uint32_t bytes) -> int {
+        const int s = it % NSTAGE;
+        const uint32_t use = it / NSTAGE;
+        if (use > 0 && !wait1(bar_empty + 8 * s, (use - 1) & 1, sh, a, ERR_TIMEOUT_PRODUCER)) return -1;
+        mbar_expect_tx(bar_full + 8 * s, bytes);
+        ++it;
+        return s;
+      };
+      auto load_chain = [&](int64_t bslot) -> bool {
+        for (int c = 0; c < 2; ++c) {
+          const int s = acquire(2 * mbytes);
+          if (s < 0) return false;
+          const uint32_t dst = smem_u32(stages + s * STAGE_BYTES);
+          const uint32_t fb = bar_full + 8 * s;
+          tma_load_2d(dst, &a.tM_hi, (int)(bslot + 64 * c), m_y, fb);
+          tma_load_2d(dst + mbytes, &a.tM_lo, (int)(bslot + 64 * c), m_y, fb);
+        }
+        return true;
+      };
+      for (int g = 0; g < ngroups && ok; ++g) {
+        for (int lt = 0; lt < sh.g_nt[g] && ok; ++lt) {
+          const int64_t bslot = sh.g_b0[g] + 128 * (int64_t)lt;
+          for (int kc = 0; kc < nk && ok; ++kc) {
+            const int s = acquire(STAGE_BYTES);
+            if (s < 0) { ok = false; break; }
+            const uint32_t dst = smem_u32(stages + s * STAGE_BYTES);
+            const uint32_t fb = bar_full + 8 * s;
+            tma_load_2d(dst, &a.tA_hi, kc * 64, (int)a_row0, fb);
+            tma_load_2d(dst + TILE_BYTES, &a.tA_lo, kc * 64, (int)a_row0, fb);
+            tma_load_2d(dst + 2 * TILE_BYTES, &a.tB_hi, kc * 64, (int)bslot, fb);
+            tma_load_2d(dst + 3 * TILE_BYTES, &a.tB_lo, kc * 64, (int)bslot, fb);
+          }
+          if (ok && chain && prev_b >= 0) ok = load_chain(prev_b);
+          prev_b = bslot;
+        }
+      }
+      if (ok && chain && prev_b >= 0) ok = load_chain(prev_b);
+      // copies in flight finish before the CTA may exit (bounded)
+      for (uint32_t u = (it > NSTAGE ? it - NSTAGE : 0); u < it; ++u) {
+        const int s = u % NSTAGE;
+        if (!mbar_try(bar_full + 8 * s, (u / NSTAGE) & 1)) {
+          const long long t0 = clock64();
+          while (!mbar_try(bar_full + 8 * s, (u / NSTAGE) & 1) && clock64() - t0 < a.timeout_cycles) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ================= MMA issuer =================
+    if (lane == 0) {
+      const uint32_t id1 = idesc_bf16(128, 128);
+      const uint32_t id2 = idesc_bf16(128, a.mpad);
+      uint32_t it = 0;
+      int t = 0;            // B tile index (global)
+      bool ok = true;
+      // chain of tile tc (global index), group g, first/last flags
+      auto do_chain = [&](int tc, int g, bool first, bool last) -> bool {
+        if (!wait1(bar_zf, tc & 1, sh, a, ERR_TIMEOUT_MMA)) return false;
+        if (first && g > 0 && !wait1(bar_a2e, (g - 1) & 1, sh, a, ERR_TIMEOUT_MMA)) return false;
+        fence_after();
+        const uint32_t zhi = smem_u32(zbuf), zlo = zhi + ZBYTES / 2;
+        for (int c = 0; c < 2; ++c) {
+          const int s = it % NSTAGE;
+          if (!wait1(bar_full + 8 * s, (it / NSTAGE) & 1, sh, a, ERR_TIMEOUT_MMA)) return false;
+          fence_after();
+          const uint32_t mhi = smem_u32(stages + s * STAGE_BYTES), mlo = mhi + mbytes;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t zo = c * (ZBYTES / 4) + kk * 32;
+            const uint64_t dzh = sw128_desc(zhi + zo), dzl = sw128_desc(zlo + zo);
+            const uint64_t dmh = sw128_desc(mhi + kk * 32), dml = sw128_desc(mlo + kk * 32);
+            const uint32_t acc = (first && c == 0 && kk == 0) ? 0u : 1u;
+            mma_bf16(tmem + ACC2_COL, dzh, dmh, id2, acc);
+            mma_bf16(tmem + ACC2_COL, dzh, dml, id2, 1u);
+            mma_bf16(tmem + ACC2_COL, dzl, dmh, id2, 1u);
+          }
+          mma_commit(bar_empty + 8 * s);
+          ++it;
+        }
+        mma_commit(bar_ze);
+        if (last) mma_commit(bar_a2f);
+        return true;
+      };
+      int pg = -1, pt = -1;
+      bool pfirst = false, plast = false;
+      for (int g = 0; g < ngroups && ok; ++g) {
+        const int ntg = sh.g_nt[g];
+        for (int lt = 0; lt < ntg && ok; ++lt, ++t) {
+          const int b = t & 1;
+          if (t >= 2 && !wait1(bar_a1e + 8 * b, ((t - 2) >> 1) & 1, sh, a, ERR_TIMEOUT_MMA)) { ok = false; break; }
+          fence_after();
+          const uint32_t d1 = tmem + 128 * b;
+          for (int kc = 0; kc < nk; ++kc) {
+            const int s = it % NSTAGE;
+            if (!wait1(bar_full + 8 * s, (it / NSTAGE) & 1, sh, a, ERR_TIMEOUT_MMA)) { ok = false; break; }
+            fence_after();
+            const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ah = sw128_desc(sa + kk * 32), al = sw128_desc(sa + TILE_BYTES + kk * 32);
+              const uint64_t bh = sw128_desc(sa + 2 * TILE_BYTES + kk * 32),
+                             bl = sw128_desc(sa + 3 * TILE_BYTES + kk * 32);
+              mma_bf16(d1, ah, bh, id1, (kc > 0 || kk > 0) ? 1u : 0u);
+              mma_bf16(d1, ah, bl, id1, 1u);
+              mma_bf16(d1, al, bh, id1, 1u);
+            }
+            mma_commit(bar_empty + 8 * s);
+            ++it;
+          }
+          if (!ok) break;
+          mma_commit(bar_a1f + 8 * b);
+          if (chain && pt >= 0) ok = do_chain(pt, pg, pfirst, plast);
+          pt = t;
+          pg = g;
+          pfirst = lt == 0;
+          plast = lt == ntg - 1;
+        }
+      }
+      if (ok && chain && pt >= 0) ok = do_chain(pt, pg, pfirst, plast);
+      // all products issued by this thread complete before TMEM is released
+      mma_commit(bar_done);
+      wait1(bar_done, 0, sh, a, ERR_TIMEOUT_MMA);
+    }
+  } else {
+    // ================= epilogue =================
+    const int ew = warp - 2;                 // 0..7
+    const int quarter = warp & 3;            // TMEM lane quarter of this warp
+    const int colbase = (ew < 4) ? 0 : 64;   // accumulator columns of this warp
+    const int row = quarter * 32 + lane;     // row of the A tile (TMEM lane)
+    const int64_t arow = a_row0 + row;
+    const bool a_valid = a.a_ok ? (a.a_ok[arow] >= 0) : true;
+    const float bias_a = (a.mode == MODE_PASS1) ? a.bias[arow] : 0.f;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    int t = 0;
+    bool ok = true;
+    for (int g = 0; g < ngroups && ok; ++g) {
+      const int ntg = sh.g_nt[g];
+      for (int lt = 0; lt < ntg && ok; ++lt, ++t) {
+        const int b = t & 1;
+        const int64_t bslot = sh.g_b0[g] + 128 * (int64_t)lt;
+        if (!waitw(bar_a1f + 8 * b, (t >> 1) & 1, sh, a, ERR_TIMEOUT_EPI)) { ok = false; break; }
+        fence_after();
+        uint32_t v0[32], v1[32];
+        tmem_ld32(tmem + lane_addr + 128 * b + colbase, v0);
+        tmem_ld32(tmem + lane_addr + 128 * b + colbase + 32, v1);
+        tmem_wait_ld();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_a1e + 8 * b);
+        // z = scale cos(acc + b), masked to valid rows and features
+        float z[64];
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+          const uint32_t bits = c < 32 ? v0[c] : v1[c - 32];
+          const int64_t bcol = bslot + colbase + c;
+          const bool bv = a.b_ok ? (a.b_ok[bcol] >= 0) : true;
+          const float ph = (a.mode == MODE_PASS1) ? bias_a : a.bias[bcol];
+          z[c] = (a_valid && bv) ? a.scale * cos_rr(__uint_as_float(bits) + ph) : 0.f;
+        }
+        if (!chain) {
+          // materialise Z (float32) inside the window
+          const int64_t r = arow - a.wz_r0;
+          if (r < a.wz_nr) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) {
+              const int64_t f = bslot + colbase + c - a.wz_f0;
+              if (f < a.wz_nf) a.out[r * a.ldo + f] = z[c];
+            }
+          }
+          continue;
+        }
+        // Z tile must be free: the chain of the previous tile has completed
+        if (t >= 1 && !waitw(bar_ze, (t - 1) & 1, sh, a, ERR_TIMEOUT_EPI)) { ok = false; break; }
+        // split into hi/lo BF16 and store in the 128-byte swizzled K-major layout
+        unsigned char* zhi = zbuf + (colbase / 64) * TILE_BYTES;
+        unsigned char* zlo = zhi + ZBYTES / 2;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          uint32_t ph[4], pl[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(z[ch * 8 + 2 * q], h0, l0);
+            split_bf16(z[ch * 8 + 2 * q + 1], h1, l1);
+            ph[q] = pack_bf16(h0, h1);
+            pl[q] = pack_bf16(l0, l1);
+          }
+          const uint32_t off = row * 128 + ((ch ^ (row & 7)) << 4);
+          *reinterpret_cast<uint4*>(zhi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+          *reinterpret_cast<uint4*>(zlo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_zf);
+        if (lt == ntg - 1) {
+          // group finished: write acc2 (rows of this warp, half of the m_pad columns)
+          if (!waitw(bar_a2f, g & 1, sh, a, ERR_TIMEOUT_EPI)) { ok = false; break; }
+          fence_after();
+          const int half = a.mpad / 2;
+          const int c0 = (ew < 4) ? 0 : half;
+          float* orow = sh.g_out[g] + (int64_t)row * a.mpad;
+          for (int c = 0; c < half; c += 8) {
+            uint32_t r8[8];
+            tmem_ld8(tmem + lane_addr + ACC2_COL + c0 + c, r8);
+            tmem_wait_ld();
+            float4* dst = reinterpret_cast<float4*>(orow + c0 + c);
+            dst[0] = make_float4(__uint_as_float(r8[0]), __uint_as_float(r8[1]), __uint_as_float(r8[2]),
+                                 __uint_as_float(r8[3]));
+            dst[1] = make_float4(__uint_as_float(r8[4]), __uint_as_float(r8[5]), __uint_as_float(r8[6]),
+                                 __uint_as_float(r8[7]));
+          }
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar_a2e);
+        }
+      }
+    }
+  }
+  // ---------------- teardown
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D BF16 tensor [rows][cols] (cols contiguous, leading dimension ld elements),
+// box of 64 columns x box_rows rows, 128-byte swizzle
+cudaError_t make_map(CUtensorMap* m, const void* ptr, int64_t cols, int64_t rows, int64_t ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ld * 2) % 16 || box_rows > 256 || box_rows < 1)
+    return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch(TcArgs& a, dim3 grid, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_regen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
+  k_regen_tc<<<grid, NTHREADS, SMEM_BYTES, st>>>(a);
+  return cudaGetLastError();
+}
+
+// device error word shared by all launches (checked by the host after each pass)
+int* err_word() {
+  static int* p = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    if (cudaMalloc(&p, 16) == cudaSuccess) cudaMemset(p, 0, 16);
+    else p = nullptr;
+  });
+  return p;
+}
+
+cudaError_t common_args(const TcView& v, TcArgs& a) {
+  memset(&a, 0, sizeof(a));
+  a.nk = (int)(v.dld / 64);
+  a.mpad = (int)v.mpad;
+  a.R = v.R;
+  a.C = v.C;
+  a.nsplit = v.nsplit;
+  a.bias = v.bias;
+  a.scale = v.scale;
+  a.fslots = v.fslots;
+  a.err = err_word();
+  if (!a.err) return cudaErrorMemoryAllocation;
+  a.timeout_cycles = 4000000000LL;   // about two seconds at the boost clock
+  if (v.mpad > 256 || v.C > MAXG) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+
+}  // namespace
+
+int tc_error_word() {
+  int h = 0;
+  int* p = err_word();
+  if (!p) return -1;
+  if (cudaMemcpy(&h, p, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  if (h) cudaMemset(p, 0, 4);
+  return h;
+}
+
+cudaError_t tc_write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int64_t nf, float* out, int64_t ldo) {
+  if (nr <= 0 || nf <= 0) return cudaSuccess;
+  TcArgs a;
+  cudaError_t e = common_args(v, a);
+  if (e != cudaSuccess) return e;
+  a.mode = MODE_WRITEZ;
+  a.a_ok = v.row_ok;
+  a.b_ok = v.feat_ok;
+  a.wz_r0 = r0; a.wz_nr = nr; a.wz_f0 = f0; a.wz_nf = nf; a.ldo = ldo;
+  a.out = out;
+  if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
+  a.tM_hi = a.tB_hi;
+  a.tM_lo = a.tB_lo;
+  return launch(a, dim3((unsigned)ceil_div(nr, 128)), v.st);
+}
+
+cudaError_t tc_pass1(const TcView& v, float* Rpart) {
+  TcArgs a;
+  cudaError_t e = common_args(v, a);
+  if (e != cudaSuccess) return e;
+  a.mode = MODE_PASS1;
+  a.row_slot = v.d_row_slot; a.row_size = v.d_row_size; a.col_slot = v.d_col_slot; a.col_size = v.d_col_size;
+  a.a_ok = v.feat_ok;
+  a.b_ok = v.row_ok;
+  a.out = Rpart;
+  a.out_block_stride = v.fslots * v.mpad;
+  if ((e = make_map(&a.tA_hi, v.Ghi, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tA_lo, v.Glo, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_hi, v.Xhi, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_lo, v.Xlo, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_hi, v.VThi, v.nslots, (int64_t)v.C * v.mpad, v.nslots, (int)v.mpad)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_lo, v.VTlo, v.nslots, (int64_t)v.C * v.mpad, v.nslots, (int)v.mpad)) != cudaSuccess) return e;
+  return launch(a, dim3((unsigned)(v.fslots / 128), (unsigned)v.R, (unsigned)v.nsplit), v.st);
+}
+
+cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, int64_t m_block_stride,
+                     float* out, int per_block) {
+  (void)m_block_stride;
+  (void)per_block;
+  TcArgs a;
+  cudaError_t e = common_args(v, a);
+  if (e != cudaSuccess) return e;
+  a.mode = MODE_PASS2;
+  a.row_slot = v.d_row_slot; a.row_size = v.d_row_size; a.col_slot = v.d_col_slot; a.col_size = v.d_col_size;
+  a.a_ok = v.row_ok;
+  a.b_ok = v.feat_ok;
+  a.out = out;
+  a.out_block_stride = v.nslots * v.mpad;
+  if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_hi, Mhi, v.fslots, (int64_t)v.R * v.mpad, v.fslots, (int)v.mpad)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_lo, Mlo, v.fslots, (int64_t)v.R * v.mpad, v.fslots, (int)v.mpad)) != cudaSuccess) return e;
+  return launch(a, dim3((unsigned)(v.nslots / 128)), v.st);
+}
+
+cudaError_t tc_predict(const TcView& v, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int64_t nrows,
+                       const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, float* out) {
+  if (nrows <= 0) return cudaSuccess;
+  if (nrows % 128) return cudaErrorInvalidValue;
+  TcArgs a;
+  cudaError_t e = common_args(v, a);
+  if (e != cudaSuccess) return e;
+  a.mode = MODE_PREDICT;
+  a.a_ok = nullptr;
+  a.b_ok = v.feat_ok;
+  a.out = out;
+  if ((e = make_map(&a.tA_hi, Xh, v.dld, nrows, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tA_lo, Xl, v.dld, nrows, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_hi, Mhi, v.fslots, v.mpad, v.fslots, (int)v.mpad)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_lo, Mlo, v.fslots, v.mpad, v.fslots, (int)v.mpad)) != cudaSuccess) return e;
+  return launch(a, dim3((unsigned)(nrows / 128)), v.st);
+}
+
 }  // namespace rff

@@ -17,6 +17,7 @@ struct TcView {
   int64_t nslots, fslots, dld, mpad;
   int R, C, nsplit;
   const int64_t *row_slot, *row_size, *col_slot, *col_size;  // host
+  const int64_t *d_row_slot, *d_row_size, *d_col_slot, *d_col_size;  // device copies
   float scale;
   cudaStream_t st;
 };
@@ -30,6 +31,9 @@ cudaError_t tc_pass1(const TcView& v, float* Rpart);
 cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, int64_t m_block_stride,
                      float* out, int per_block);
 // Scores for a query block (nrows slot-padded rows of split X) against M (mpad x fslots hi/lo).
+// Error word of the tensor-core kernels (bounded waits that gave up); reads and clears it.
+// Synchronises the device.  0 = no error.
+int tc_error_word();
 cudaError_t tc_predict(const TcView& v, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int64_t nrows,
                        const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, float* out);
 

@@ -91,6 +91,22 @@ def test_features_fp32_match_oracle(rff, n, d, D, k_lo, k_hi):
     assert err < 1e-5 * max(1.0, np.sqrt(d / 16)), err
 
 
+@pytest.mark.parametrize("n,d,D,k_lo,k_hi", [(300, 16, 512, 0, 512), (257, 37, 1000, 333, 667),
+                                             (129, 440, 4096, 4000, 4096), (1000, 784, 2048, 0, 2048)])
+def test_features_split_bf16_match_oracle(rff, n, d, D, k_lo, k_hi):
+    """Tensor-core path: X.G as three BF16 products, FP32 accumulate, FP32 cosine."""
+    rng = np.random.default_rng(n + 1)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    seed, sigma = 78, 3.0
+    Z = torch.empty((n, k_hi - k_lo), dtype=torch.float32, device="cuda")
+    rff.rff_features(dev(X), seed, sigma, D, k_lo, k_hi, "split_bf16", Z)
+    torch.cuda.synchronize()
+    ref = orff.features_block(X, seed, sigma, D, k_lo, k_hi)
+    err = np.abs(Z.cpu().numpy() - ref).max() / np.sqrt(2.0 / D)
+    # split products carry ~2^-16 relative error per term of the length-d dot product
+    assert err < 2e-4 * max(1.0, np.sqrt(d / 64)), err
+
+
 def test_features_independent_of_block_split(rff):
     """Sec. 4 block-wise maps: any feature range is the slice of the full map, bit for bit."""
     rng = np.random.default_rng(3)
