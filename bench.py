@@ -130,7 +130,10 @@ def run_ours(args, rank, world):
 
     import paper_1409_0940_gb300 as rff
 
-    w = WORKLOAD
+    w = dict(WORKLOAD)
+    if args.n:
+        w["n"] = args.n
+        w["name"] = w["name"].replace("200k", "%dk" % (args.n // 1000))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     X, Y = make_data(w)
     stream = torch.cuda.Stream()
@@ -158,17 +161,21 @@ def run_ours(args, rank, world):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
+    s.close()
     # end to end through the public API with host buffers: set_data (H2D of X, Y),
     # set-up, K iterations, weights back to the host (D2H)
-    t0 = time.perf_counter()
-    s2 = rff.Solver(stream=stream.cuda_stream, **solver_kw(w, args.prec))
-    s2.set_data(X, Y)
-    s2.solve(args.steps, stats=False)
-    Wh = s2.weights()
-    e2e_s = time.perf_counter() - t0
-    s2.close()
-    h2d = X.nbytes + Y.nbytes
-    d2h = Wh.nbytes
+    e2e = None
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        s2 = rff.Solver(stream=stream.cuda_stream, **solver_kw(w, args.prec))
+        s2.set_data(X, Y)
+        s2.solve(args.steps, stats=False)
+        Wh = s2.weights()
+        e2e_s = time.perf_counter() - t0
+        s2.close()
+        e2e = {"value": args.steps / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": (X.nbytes + Y.nbytes) // args.steps,
+               "d2h_bytes_per_step": Wh.nbytes // args.steps,
+               "note": "set_data + set-up + K iterations + get_weights, host buffers"}
 
     useful, exec_pass = flops_per_iter(w, args.prec)
     hbm, bf16, bf16_sus, src = peaks()
@@ -196,16 +203,13 @@ def run_ours(args, rank, world):
                    "grid": "%dx%d" % (w["R"], w["C"]), "sigma": w["sigma"], "loss": w["loss"], "reg": w["reg"],
                    "lambda": w["lam"], "rho": w["rho"], "prec": args.prec, "parallelism": "replicas",
                    "l2": "inputs larger than L2 (X split 358 MB, V 512 MB, factors 2.1 GB)"},
-        "e2e": {"value": args.steps / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": h2d // args.steps,
-                "d2h_bytes_per_step": d2h // args.steps,
-                "note": "set_data + set-up + K iterations + get_weights, host buffers"},
+        "e2e": e2e,
         "gpu_launches": int(prof["launches"]),
         "phases_ms_per_iter": {k[3:]: prof[k] / max(prof["iters"], 1) for k in prof if k.startswith("ms_")},
         "useful_tflops": useful / (ms / args.steps * 1e-3) / 1e12,
         "roofline": roof,
         "clocks": clk.summary(),
     }
-    s.close()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
@@ -254,6 +258,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="split_bf16", choices=["split_bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--n", type=int, default=0, help="rows of a reduced workload (profiling runs)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -504,6 +504,9 @@ rff_status setup_factors(rff_admm_t h) {
     }
   CK(cudaMemcpyAsync(s.gdesc, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, s.st));
   CK(cudaStreamSynchronize(s.st));
+  // the set-up scratch (FP64 Gram and inverse batches) is released
+  CK(cudaFree(s.scratch.p));
+  s.scratch = DevBuf{};
   s.factored = true;
   return RFF_OK;
 }
