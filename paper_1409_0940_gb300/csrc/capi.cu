@@ -62,8 +62,15 @@ struct rff_admm_s {
   rff_admm_profile prof{};
   std::vector<cudaEvent_t> ev;
   int64_t launches = 0;
+  // one iteration captured as a CUDA graph (after an eager first iteration)
+  cudaGraphExec_t gexec = nullptr;
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
 
   ~rff_admm_s() {
+    drop_graph();
     for (auto e : ev) cudaEventDestroy(e);
     free_all();
     if (scratch.p) cudaFree(scratch.p);
@@ -238,6 +245,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   if (!X || !Yin) return h->fail(RFF_EINVAL, "X or Y is NULL");
   if (n < h->p.R || d < 1 || n > ((int64_t)1 << 31) - 1) return h->fail(RFF_EINVAL, "need R <= n < 2^31 and d >= 1");
   CK(cudaStreamSynchronize(h->st));
+  h->drop_graph();
   h->free_all();
   h->has_data = h->factored = false;
   h->iters_done = 0;
@@ -599,6 +607,29 @@ rff_status iterate(rff_admm_t h, int k) {
   return RFF_OK;
 }
 
+// Capture one iteration (the same launches as iterate()) into an executable graph.
+rff_status capture_iteration(rff_admm_t h) {
+  auto& s = *h;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal));
+  const int64_t saved = s.launches;
+  rff_status r = iterate(h, 0);
+  s.launches = saved;
+  cudaError_t e = cudaStreamEndCapture(s.st, &g);
+  if (r != RFF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return h->cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&s.gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    s.gexec = nullptr;
+    return h->cuda_fail(e, "cudaGraphInstantiate");
+  }
+  return RFF_OK;
+}
+
 rff_status sum_partials(rff_admm_t h, double& out) {
   std::vector<double> hp(1024);
   CK(cudaMemcpyAsync(hp.data(), h->partials, 1024 * 8, cudaMemcpyDeviceToHost, h->st));
@@ -689,7 +720,14 @@ rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats) {
       CK(cudaMemcpyAsync(s.Wbar_old, s.Wbar, colb, cudaMemcpyDeviceToDevice, s.st));
       CK(cudaMemcpyAsync(s.muij_old, s.muij, colb * s.R, cudaMemcpyDeviceToDevice, s.st));
     }
-    rff_status r = iterate(h, k);
+    rff_status r = RFF_OK;
+    if (s.profiling || s.iters_done == 0) {
+      r = iterate(h, k);
+    } else {
+      if (!s.gexec && (r = capture_iteration(h)) != RFF_OK) return r;
+      CK(cudaGraphLaunch(s.gexec, s.st));
+      s.launches += s.split_path() ? 9 : 7;
+    }
     if (r != RFF_OK) return r;
     s.iters_done++;
   }
