@@ -137,6 +137,28 @@ rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats);
  * the first solve, RFF_EINVAL for NaN/Inf queries. */
 rff_status rff_admm_predict(rff_admm_t h, const float* Xq, int64_t q, float* scores, int is_device_ptr);
 
+/* Scores without allocating device memory (the paper has no counterpart: it is an
+ * interface for callers that cannot call cudaMalloc when they score -- code being
+ * captured into a CUDA graph, where allocation is not a capturable operation, and
+ * serving loops whose device memory is owned by another pool or that must not
+ * allocate on the request path).  Same result as rff_admm_predict, same kernels.
+ * Xq (q x d) and scores (q x m) are row-major float32 DEVICE pointers; the call
+ * synchronises the handle's stream before it returns.
+ * Scratch: one fixed 32 MiB array in device global memory, defined by the library
+ * and held by every GPU that loads it until the process exits.  A call needs
+ * q_pad * (4 d_pad + 4 m_pad) bytes on the FP32 path and q_pad * (8 d_pad + 4 m_pad)
+ * on the split-BF16 path (q_pad = q rounded up to 128, d_pad = d rounded up to 64,
+ * m_pad = m rounded up to 16); larger q returns RFF_EINVAL with the limit in the
+ * error text -- score in smaller batches.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the previous call's contents (the call
+ * clears what must start at zero): calls that overlap on the GPU -- two handles
+ * or threads scoring at the same time -- race on it.
+ * Errors: RFF_ENOTREADY before the first solve, RFF_EINVAL for NULL pointers,
+ * NaN/Inf queries or q beyond the scratch, RFF_ECUDA. */
+rff_status rff_admm_predict_noalloc(rff_admm_t h, const float* Xq, int64_t q, float* scores);
+
 /* Copy the consensus weights Wbar (D x m, row-major, rows in global feature
  * order) to W.  Errors: RFF_ENOTREADY without data. */
 rff_status rff_admm_get_weights(rff_admm_t h, float* W, int is_device_ptr);

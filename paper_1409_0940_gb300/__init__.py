@@ -57,6 +57,7 @@ PROTOTYPES = {
     "rff_admm_set_data": (_I32, [_P, _P, _P, _I64, _I64, ctypes.c_int]),
     "rff_admm_solve": (_I32, [_P, _I32, ctypes.POINTER(rff_admm_stats)]),
     "rff_admm_predict": (_I32, [_P, _P, _I64, _P, ctypes.c_int]),
+    "rff_admm_predict_noalloc": (_I32, [_P, _P, _I64, _P]),
     "rff_admm_get_weights": (_I32, [_P, _P, ctypes.c_int]),
     "rff_admm_get_state": (_I32, [_P, _P, ctypes.POINTER(_SZ)]),
     "rff_admm_set_state": (_I32, [_P, _P, _SZ]),
@@ -166,6 +167,16 @@ def rff_admm_predict(h, Xq, out):
     if dq != do:
         raise TypeError("Xq and scores must both be host or both be device arrays")
     _check(lib.rff_admm_predict(h, pq, Xq.shape[0], po, dq), h)
+    return out
+
+
+def rff_admm_predict_noalloc(h, Xq, out):
+    """Scores into `out` without any device allocation (device tensors only)."""
+    pq, dq = _ptr(Xq)
+    po, do = _ptr(out)
+    if not (dq and do):
+        raise TypeError("rff_admm_predict_noalloc takes device tensors")
+    _check(lib.rff_admm_predict_noalloc(h, pq, Xq.shape[0], po), h)
     return out
 
 

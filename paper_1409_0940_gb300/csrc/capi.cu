@@ -919,6 +919,54 @@ rff_status rff_admm_set_state(rff_admm_t h, const void* buf, size_t bytes) {
   return RFF_OK;
 }
 
+}  // extern "C"
+
+// Scoring into caller-provided scratch (used by the allocation-free entry point in
+// noalloc.cu).  Xq and scores are device pointers; scratch holds the slot-padded
+// queries, their BF16 split and the padded scores.
+namespace rff {
+rff_status predict_into_scratch(rff_admm_t h, const float* Xq, int64_t q, float* scores, void* scratch,
+                                size_t scratch_bytes) {
+  if (!h) return RFF_EINVAL;
+  h->err.clear();
+  if (!h->has_data || !h->factored) return h->fail(RFF_ENOTREADY, "predict needs a solve first");
+  if (q < 0) return h->fail(RFF_EINVAL, "q < 0");
+  if (q == 0) return RFF_OK;
+  if (!Xq || !scores || !scratch) return h->fail(RFF_EINVAL, "NULL pointer");
+  auto& s = *h;
+  const int64_t qp = round_up(q, SLOT);
+  const size_t x32 = (size_t)qp * s.dld * 4, xsplit = s.split_path() ? (size_t)qp * s.dld * 2 : 0,
+               scb = (size_t)qp * s.mpad * 4;
+  const size_t need = round_up(x32, 256) + 2 * round_up(xsplit, 256) + scb;
+  if (need > scratch_bytes)
+    return h->fail(RFF_EINVAL, "q = " + std::to_string(q) + " needs " + std::to_string(need) +
+                                   " bytes of the fixed scratch, which holds " + std::to_string(scratch_bytes) +
+                                   ": score the queries in smaller batches");
+  char* base = static_cast<char*>(scratch);
+  float* xq32 = reinterpret_cast<float*>(base);
+  __nv_bfloat16* xh = reinterpret_cast<__nv_bfloat16*>(base + round_up(x32, 256));
+  __nv_bfloat16* xl = reinterpret_cast<__nv_bfloat16*>(base + round_up(x32, 256) + round_up(xsplit, 256));
+  float* sc = reinterpret_cast<float*>(base + round_up(x32, 256) + 2 * round_up(xsplit, 256));
+  CK(cudaMemsetAsync(s.flag, 0, 4, s.st));
+  CK(launch_finite_check(Xq, q * s.d, 0, s.flag, s.st));
+  int fl = 0;
+  CK(cudaMemcpyAsync(&fl, s.flag, 4, cudaMemcpyDeviceToHost, s.st));
+  CK(cudaStreamSynchronize(s.st));
+  if (fl) return h->fail(RFF_EINVAL, "queries contain NaN or Inf");
+  // the scratch keeps the previous call's contents: the padding rows are cleared here
+  CK(cudaMemsetAsync(xq32, 0, x32, s.st));
+  CK(launch_gather_rows(Xq, s.d, s.d, nullptr, q, xq32, s.dld, s.st));
+  if (s.split_path()) CK(launch_split_bf16(xq32, qp * s.dld, xh, xl, s.st));
+  rff_status r = scores_pass(h, xq32, xh, xl, qp, nullptr, sc);
+  if (r != RFF_OK) return r;
+  CK(cudaMemcpy2DAsync(scores, s.m * 4, sc, s.mpad * 4, s.m * 4, q, cudaMemcpyDeviceToDevice, s.st));
+  CK(cudaStreamSynchronize(s.st));
+  return RFF_OK;
+}
+}  // namespace rff
+
+extern "C" {
+
 // ------------------------------------------------------------------ step-level entry points
 rff_status rff_philox4x32_10(const uint32_t* ctr, uint64_t seed, int64_t n, uint32_t* out, void* stream) {
   if (n < 0 || (n > 0 && (!ctr || !out))) return RFF_EINVAL;
