@@ -109,7 +109,8 @@ typedef struct rff_admm_s* rff_admm_t;
 /* Create a solver handle.  params: see rff_admm_params; copied.  stream: a
  * cudaStream_t or NULL.  *out receives the handle.  Errors: RFF_EINVAL for
  * out-of-range parameters (lambda <= 0, sigma <= 0, rho <= 0, D < 1, R < 1,
- * C < 1, C > D, m outside [1, 256], unknown enums, logistic loss with m != 1),
+ * C < 1, C > D, m outside [1, 256], unknown enums, logistic loss with m != 1,
+ * C > 64 with RFF_PREC_SPLIT_BF16),
  * RFF_ECUDA if no device is usable. */
 rff_status rff_admm_create(const rff_admm_params* params, void* stream, rff_admm_t* out);
 

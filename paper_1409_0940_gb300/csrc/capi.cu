@@ -33,6 +33,7 @@ struct rff_admm_s {
 
   // ---- geometry
   bool has_data = false, factored = false;
+  int64_t bias_col = -1;  // split path: column of X (ones) and G (b) that folds b into X.G
   int64_t n = 0, d = 0, dld = 0, m = 0, mpad = 0, D = 0, nslots = 0, fslots = 0;
   int R = 1, C = 1, nsplit = 1, iters_done = 0;
   float t_loss = 0.f, t_reg = 0.f;
@@ -118,6 +119,7 @@ rff_status check_params(const rff_admm_params* p, std::string& why) {
   if (p->m < 1 || p->m > 256) { why = "m must be in [1, 256]"; return RFF_EINVAL; }
   if (p->loss == RFF_LOSS_LOGISTIC && p->m != 1) { why = "binary logistic loss needs m = 1"; return RFF_EINVAL; }
   if (p->newton_iters < 0 || p->newton_iters > 100) { why = "newton_iters out of range"; return RFF_EINVAL; }
+  if (p->prec == RFF_PREC_SPLIT_BF16 && p->C > 64) { why = "the split-BF16 path supports C <= 64"; return RFF_EINVAL; }
   return RFF_OK;
 }
 
@@ -254,6 +256,8 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   s.n = n;
   s.d = d;
   s.dld = round_up(d, 64);
+  // the split path folds the phase b into the tensor-core product when column d is free
+  s.bias_col = (s.p.prec == RFF_PREC_SPLIT_BF16 && round_up(d + 1, 64) == s.dld) ? d : -1;
   s.m = s.p.m;
   s.mpad = round_up(s.m, 16);
   s.D = s.p.D;
@@ -404,6 +408,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   }
   CK(launch_gather_rows(sx, d, d, s.row_of_slot, s.nslots, Xs, s.dld, s.st));
   CK(launch_gather_rows(sy, s.m, s.m, s.row_of_slot, s.nslots, s.Y, s.mpad, s.st));
+  if (s.bias_col >= 0) CK(launch_set_column(Xs, s.dld, s.nslots, s.bias_col, 1.f, s.st));
   if (s.split_path()) CK(launch_split_bf16(Xs, s.nslots * s.dld, s.Xhi, s.Xlo, s.st));
 
   // ADMM state: all zero (Sec. 3: "initialize to zero"), then O = prox(Obar - nu) = prox(0)
@@ -437,7 +442,7 @@ rff_status setup_factors(rff_admm_t h) {
   const float scale = (float)std::sqrt(2.0 / (double)s.D);
   // random features: G and b from Philox (Sec. 4)
   CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, s.Ghi, s.Glo, s.bias,
-                         s.st));
+                         s.bias_col, s.st));
   // Gram matrices H_ij = I + Z_ij^T Z_ij (eq. (cache)), in FP64, batched by memory
   int64_t smax = 0;
   for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
@@ -683,6 +688,7 @@ TcView tc_view(const rff_admm_s& s) {
   v.col_slot = s.col_slot.data(); v.col_size = s.col_size.data();
   v.d_row_slot = s.d_row_slot; v.d_row_size = s.d_row_size; v.d_col_slot = s.d_col_slot; v.d_col_size = s.d_col_size;
   v.scale = (float)std::sqrt(2.0 / (double)s.D);
+  v.bias_in_mma = s.bias_col >= 0 ? 1 : 0;
   v.st = s.st;
   return v;
 }
@@ -814,6 +820,7 @@ rff_status rff_admm_predict(rff_admm_t h, const float* Xq, int64_t q, float* sco
     // rows q0..q0+nq into a slot-padded block (rows beyond nq are zero and discarded)
     CK(cudaMemsetAsync(xq32, 0, nqp * s.dld * 4, s.st));
     CK(launch_gather_rows(stage, s.d, s.d, nullptr, nq, xq32, s.dld, s.st));
+    if (s.bias_col >= 0) CK(launch_set_column(xq32, s.dld, nqp, s.bias_col, 1.f, s.st));
     if (s.split_path()) CK(launch_split_bf16(xq32, nqp * s.dld, xh, xl, s.st));
     if ((r = scores_pass(h, xq32, xh, xl, nqp, nullptr, sc)) != RFF_OK) return r;
     CK(cudaMemcpy2DAsync(scores + q0 * s.m, s.m * 4, sc, s.mpad * 4, s.m * 4, nq, kout, s.st));
@@ -956,6 +963,7 @@ rff_status predict_into_scratch(rff_admm_t h, const float* Xq, int64_t q, float*
   // the scratch keeps the previous call's contents: the padding rows are cleared here
   CK(cudaMemsetAsync(xq32, 0, x32, s.st));
   CK(launch_gather_rows(Xq, s.d, s.d, nullptr, q, xq32, s.dld, s.st));
+  if (s.bias_col >= 0) CK(launch_set_column(xq32, s.dld, qp, s.bias_col, 1.f, s.st));
   if (s.split_path()) CK(launch_split_bf16(xq32, qp * s.dld, xh, xl, s.st));
   rff_status r = scores_pass(h, xq32, xh, xl, qp, nullptr, sc);
   if (r != RFF_OK) return r;
@@ -1016,15 +1024,18 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
   if (e == cudaSuccess) e = cudaMemcpyAsync(tabs, htab, sizeof(htab), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(fok, f.data(), fp * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = launch_gather_rows(X, d, d, rok, np, X32, dld, st);
+  const int64_t bcol = (prec == RFF_PREC_SPLIT_BF16 && round_up(d + 1, 64) == dld) ? d : -1;
   if (e == cudaSuccess)
-    e = launch_params_slots(seed, sigma, d, dld, fp, fok, G32, prec ? Gh : nullptr, prec ? Gl : nullptr, bias, st);
+    e = launch_params_slots(seed, sigma, d, dld, fp, fok, G32, prec ? Gh : nullptr, prec ? Gl : nullptr, bias, bcol,
+                            st);
   const float scale = (float)std::sqrt(2.0 / (double)D);
   if (e == cudaSuccess) {
     if (prec == RFF_PREC_FP32) {
       ZArgs za{X32, dld, G32, dld, (int)dld, bias, scale, rok, fok, 0, n, 0, nf, Z, nf};
       e = launch_write_z_simt(za, st);
     } else {
-      e = launch_split_bf16(X32, np * dld, Xh, Xl, st);
+      if (bcol >= 0) e = launch_set_column(X32, dld, np, bcol, 1.f, st);
+      if (e == cudaSuccess) e = launch_split_bf16(X32, np * dld, Xh, Xl, st);
       if (e == cudaSuccess) {
         const int64_t zero = 0;
         TcView v{};
@@ -1033,7 +1044,7 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
         v.nslots = np; v.fslots = fp; v.dld = dld; v.mpad = 16; v.R = 1; v.C = 1; v.nsplit = 1;
         v.row_slot = &zero; v.row_size = &n; v.col_slot = &zero; v.col_size = &nf;
         v.d_row_slot = tabs; v.d_row_size = tabs + 1; v.d_col_slot = tabs + 2; v.d_col_size = tabs + 3;
-        v.scale = scale; v.st = st;
+        v.scale = scale; v.bias_in_mma = bcol >= 0 ? 1 : 0; v.st = st;
         e = tc_write_z(v, 0, n, 0, nf, Z, nf);
       }
     }

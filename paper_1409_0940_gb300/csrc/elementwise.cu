@@ -23,6 +23,11 @@ __global__ void k_scatter_rows(const float* __restrict__ src, int64_t lds, int64
   dst[t] = (g >= 0 && c < w) ? src[(int64_t)g * lds + c] : 0.f;
 }
 
+__global__ void k_set_column(float* __restrict__ X, int64_t ld, int64_t rows, int64_t col, float v) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r < rows) X[r * ld + col] = v;
+}
+
 __global__ void k_split(const float* __restrict__ src, int64_t n, __nv_bfloat16* __restrict__ hi,
                         __nv_bfloat16* __restrict__ lo) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -400,6 +405,12 @@ cudaError_t launch_gather_rows(const float* src, int64_t lds, int64_t w, const i
                                float* dst, int64_t ld, cudaStream_t st) {
   if (nrows * ld <= 0) return cudaSuccess;
   k_scatter_rows<<<nblk(nrows * ld), 256, 0, st>>>(src, lds, w, map, nrows, dst, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_column(float* X, int64_t ld, int64_t rows, int64_t col, float v, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  k_set_column<<<nblk(rows), 256, 0, st>>>(X, ld, rows, col, v);
   return cudaGetLastError();
 }
 

@@ -54,9 +54,10 @@ struct ZArgs {
 cudaError_t launch_philox_raw(const uint32_t* ctr, uint64_t seed, int64_t n, uint32_t* out, cudaStream_t st);
 cudaError_t launch_params_rowmajor(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t nk, float* G,
                                    float* b, cudaStream_t st);
+// bias_col >= 0: the BF16 copies carry b in that column (inputs then carry ones there)
 cudaError_t launch_params_slots(uint64_t seed, double sigma, int64_t d, int64_t ld, int64_t nslots,
                                 const int32_t* feat_of_slot, float* Gt, __nv_bfloat16* Ghi, __nv_bfloat16* Glo,
-                                float* bias, cudaStream_t st);
+                                float* bias, int64_t bias_col, cudaStream_t st);
 
 // regen_simt.cu
 cudaError_t launch_pass1_simt(const PassArgs& p, int64_t nfeat_slots, cudaStream_t st);
@@ -106,6 +107,7 @@ cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, 
 // dst[p][c] = src[map[p] * lds + c] (c < w), zero for c >= w or map[p] < 0; map null = identity
 cudaError_t launch_gather_rows(const float* src, int64_t lds, int64_t w, const int32_t* map, int64_t nrows,
                                float* dst, int64_t ld, cudaStream_t st);
+cudaError_t launch_set_column(float* X, int64_t ld, int64_t rows, int64_t col, float v, cudaStream_t st);
 cudaError_t launch_split_bf16(const float* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st);
 cudaError_t launch_prox_loss(int loss, const float* V, const float* Y, int64_t n, int m, int64_t ld, float t,
                              int newton, float* out, cudaStream_t st);

@@ -67,7 +67,7 @@ __global__ void k_params_rowmajor(uint32_t k0, uint32_t k1, double sigma, int64_
 __global__ void k_params_slots(uint32_t k0, uint32_t k1, double sigma, int64_t d, int64_t ld, int64_t nslots,
                                const int32_t* __restrict__ feat_of_slot, float* __restrict__ Gt,
                                __nv_bfloat16* __restrict__ Ghi, __nv_bfloat16* __restrict__ Glo,
-                               float* __restrict__ bias) {
+                               float* __restrict__ bias, int64_t bias_col) {
   const int64_t nq = ld / 4;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nslots * nq) return;
@@ -75,19 +75,23 @@ __global__ void k_params_slots(uint32_t k0, uint32_t k1, double sigma, int64_t d
   const int32_t k = feat_of_slot[p];
   float g[4] = {0.f, 0.f, 0.f, 0.f};
   if (k >= 0 && 4 * q < d) gauss4((uint32_t)k, (uint32_t)q, k0, k1, sigma, g);
+  const bool has_bias_col = bias_col >= 4 * q && bias_col < 4 * q + 4;
+  const float ph = (k >= 0 && (q == 0 || has_bias_col)) ? phase((uint32_t)k, k0, k1) : 0.f;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int64_t r = 4 * q + e;
     const float v = (r < d) ? g[e] : 0.f;
     if (Gt) Gt[p * ld + r] = v;
     if (Ghi) {
+      // the BF16 copies may carry the phase b in column bias_col (the input then
+      // carries a column of ones there), so the product X G already includes b
       __nv_bfloat16 hi, lo;
-      split_bf16(v, hi, lo);
+      split_bf16(r == bias_col ? ph : v, hi, lo);
       Ghi[p * ld + r] = hi;
       Glo[p * ld + r] = lo;
     }
   }
-  if (q == 0 && bias) bias[p] = (k >= 0) ? phase((uint32_t)k, k0, k1) : 0.f;
+  if (q == 0 && bias) bias[p] = ph;
 }
 
 cudaError_t launch_philox_raw(const uint32_t* ctr, uint64_t seed, int64_t n, uint32_t* out, cudaStream_t st) {
@@ -106,11 +110,12 @@ cudaError_t launch_params_rowmajor(uint64_t seed, double sigma, int64_t d, int64
 
 cudaError_t launch_params_slots(uint64_t seed, double sigma, int64_t d, int64_t ld, int64_t nslots,
                                 const int32_t* feat_of_slot, float* Gt, __nv_bfloat16* Ghi, __nv_bfloat16* Glo,
-                                float* bias, cudaStream_t st) {
+                                float* bias, int64_t bias_col, cudaStream_t st) {
   const int64_t total = nslots * (ld / 4);
   if (total <= 0) return cudaSuccess;
   k_params_slots<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>((uint32_t)seed, (uint32_t)(seed >> 32), sigma,
-                                                                   d, ld, nslots, feat_of_slot, Gt, Ghi, Glo, bias);
+                                                                   d, ld, nslots, feat_of_slot, Gt, Ghi, Glo, bias,
+                                                                   bias_col);
   return cudaGetLastError();
 }
 

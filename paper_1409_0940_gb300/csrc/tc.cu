@@ -23,6 +23,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -34,16 +35,32 @@ namespace rff {
 namespace {
 
 constexpr int MODE_WRITEZ = 0, MODE_PASS1 = 1, MODE_PASS2 = 2, MODE_PREDICT = 3;
-constexpr int NSTAGE = 2;
-constexpr uint32_t STAGE_BYTES = 65536;     // A hi/lo + B hi/lo, 128 x 64 BF16 each
-constexpr uint32_t TILE_BYTES = 16384;      // 128 rows x 128 bytes
 constexpr uint32_t ZBYTES = 65536;          // Z hi (32 KB) + Z lo (32 KB), two 64-column atoms each
+constexpr uint32_t ZATOM = 16384;           // one 128 x 64 BF16 atom column of Z (128-byte rows)
 constexpr int NEPI = 8;                     // epilogue warps
 constexpr int NTHREADS = 64 + 32 * NEPI;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC2_COL = 256;
-constexpr int MAXG = 256;                   // groups (column blocks) per CTA
-constexpr size_t SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + ZBYTES + 2048 + MAXG * 24;
+constexpr int MAXG = 64;                    // groups (column blocks) per CTA
+
+// Ring geometry.  KC = K elements per ring stage: 64 (128-byte rows, 128-byte
+// swizzle, 64 KB stages) or 32 (64-byte rows, 64-byte swizzle, 32 KB stages, so
+// more stages fit beside the Z tile and more bytes are in flight).
+template <int KC>
+struct Ring {
+  static constexpr uint32_t ROWB = KC * 2;               // bytes per operand row in a stage
+  static constexpr uint32_t TILEB = 128 * ROWB;          // one 128-row operand tile
+  static constexpr uint32_t STAGEB = 4 * TILEB;          // A hi, A lo, B hi, B lo
+  static constexpr int NS = (KC == 64) ? 2 : 5;          // stages
+  static constexpr int KSTEPS = KC / 16;                 // MMA K steps per stage
+  static constexpr int CHUNKS = 128 / KC;                // chain-operand chunks per B tile
+  static constexpr uint32_t LAYOUT = (KC == 64) ? 2 : 4; // descriptor layout: 128B / 64B swizzle
+  static constexpr uint32_t SBO = 8 * ROWB;              // bytes between 8-row groups
+};
+template <int KC>
+constexpr size_t smem_bytes() {
+  return 1024 + Ring<KC>::NS * Ring<KC>::STAGEB + ZBYTES + 256 + MAXG * 24;
+}
 
 // error codes written to the error word
 constexpr int ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPI = 4;
@@ -63,6 +80,7 @@ struct TcArgs {
   float* out;
   int64_t out_block_stride;
   int64_t wz_r0, wz_nr, wz_f0, wz_nf, ldo;  // materialisation window
+  int bias_in_mma;                          // 1: b already in the product (column of ones)
   int* err;
   long long timeout_cycles;
 };
@@ -108,17 +126,19 @@ __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
-// K-major operand in the 128-byte swizzled layout written by TMA: rows of 128 bytes,
-// 8-row groups 1024 bytes apart.  Start address advanced by 32 bytes per K step of 16.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// K-major operand in a swizzled layout written by TMA: rows of `rowb` bytes, 8-row
+// groups `sbo` bytes apart, layout 2 = 128-byte swizzle, 4 = 64-byte swizzle.  The
+// start address advances by 32 bytes per K step of 16 within a row.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo, uint32_t layout) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
-  d |= (uint64_t)1 << 16;                         // leading byte offset (unused for this swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 16;                         // leading byte offset (unused when swizzled)
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;     // stride byte offset
   d |= (uint64_t)1 << 46;                         // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+  d |= (uint64_t)layout << 61;
   return d;
 }
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) { return smem_desc(saddr, 1024, 2); }
 
 // kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both operands K-major
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -165,8 +185,9 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) 
 }
 
 // ------------------------------------------------------------------ shared state
+template <int NS>
 struct Shared {
-  uint64_t full[NSTAGE], empty[NSTAGE];
+  uint64_t full[NS], empty[NS];
   uint64_t acc1_full[2], acc1_empty[2];
   uint64_t z_full, z_empty, acc2_full, acc2_empty, mma_done;
   uint32_t tmem_base;
@@ -180,7 +201,8 @@ struct Shared {
 };
 
 // bounded wait; one thread polls.  false = the CTA is aborting
-__device__ __forceinline__ bool wait1(uint32_t bar, uint32_t parity, Shared& sh, const TcArgs& a, int code) {
+template <class SH>
+__device__ __forceinline__ bool wait1(uint32_t bar, uint32_t parity, SH& sh, const TcArgs& a, int code) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
@@ -195,20 +217,25 @@ __device__ __forceinline__ bool wait1(uint32_t bar, uint32_t parity, Shared& sh,
 }
 
 // warp-uniform bounded wait: lane 0 polls, the verdict is broadcast
-__device__ __forceinline__ bool waitw(uint32_t bar, uint32_t parity, Shared& sh, const TcArgs& a, int code) {
+template <class SH>
+__device__ __forceinline__ bool waitw(uint32_t bar, uint32_t parity, SH& sh, const TcArgs& a, int code) {
   int ok = 0;
   if ((threadIdx.x & 31) == 0) ok = wait1(bar, parity, sh, a, code) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   return ok != 0;
 }
 
+template <int KC>
 __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant__ TcArgs a) {
+  using RG = Ring<KC>;
+  constexpr int NSTAGE = RG::NS;
+  constexpr uint32_t STAGE_BYTES = RG::STAGEB, TILE_BYTES = RG::TILEB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the operand tiles (the swizzle pattern repeats every 1024 bytes)
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-  unsigned char* stages = base;
-  unsigned char* zbuf = base + NSTAGE * STAGE_BYTES;
-  Shared& sh = *reinterpret_cast<Shared*>(zbuf + ZBYTES);
+  unsigned char* zbuf = base;
+  unsigned char* stages = base + ZBYTES;
+  Shared<NSTAGE>& sh = *reinterpret_cast<Shared<NSTAGE>*>(stages + NSTAGE * STAGE_BYTES);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const bool chain = a.mode != MODE_WRITEZ;
@@ -302,7 +329,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
   fence_after();
   const uint32_t tmem = sh.tmem_base;
   const int nk = a.nk;
-  const uint32_t mbytes = (uint32_t)a.mpad * 128;   // one chain operand tile (hi or lo), 64 K-columns
+  const uint32_t mbytes = (uint32_t)a.mpad * RG::ROWB;   // one chain operand chunk (hi or lo)
 
   if (warp == 0) {
     // ================= TMA producer =================
@@ -321,13 +348,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
         return s;
       };
       auto load_chain = [&](int64_t bslot) -> bool {
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < RG::CHUNKS; ++c) {
           const int s = acquire(2 * mbytes);
           if (s < 0) return false;
           const uint32_t dst = smem_u32(stages + s * STAGE_BYTES);
           const uint32_t fb = bar_full + 8 * s;
-          tma_load_2d(dst, &a.tM_hi, (int)(bslot + 64 * c), m_y, fb);
-          tma_load_2d(dst + mbytes, &a.tM_lo, (int)(bslot + 64 * c), m_y, fb);
+          tma_load_2d(dst, &a.tM_hi, (int)(bslot + KC * c), m_y, fb);
+          tma_load_2d(dst + mbytes, &a.tM_lo, (int)(bslot + KC * c), m_y, fb);
         }
         return true;
       };
@@ -339,10 +366,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
             if (s < 0) { ok = false; break; }
             const uint32_t dst = smem_u32(stages + s * STAGE_BYTES);
             const uint32_t fb = bar_full + 8 * s;
-            tma_load_2d(dst, &a.tA_hi, kc * 64, (int)a_row0, fb);
-            tma_load_2d(dst + TILE_BYTES, &a.tA_lo, kc * 64, (int)a_row0, fb);
-            tma_load_2d(dst + 2 * TILE_BYTES, &a.tB_hi, kc * 64, (int)bslot, fb);
-            tma_load_2d(dst + 3 * TILE_BYTES, &a.tB_lo, kc * 64, (int)bslot, fb);
+            tma_load_2d(dst, &a.tA_hi, kc * KC, (int)a_row0, fb);
+            tma_load_2d(dst + TILE_BYTES, &a.tA_lo, kc * KC, (int)a_row0, fb);
+            tma_load_2d(dst + 2 * TILE_BYTES, &a.tB_hi, kc * KC, (int)bslot, fb);
+            tma_load_2d(dst + 3 * TILE_BYTES, &a.tB_lo, kc * KC, (int)bslot, fb);
           }
           if (ok && chain && prev_b >= 0) ok = load_chain(prev_b);
           prev_b = bslot;
@@ -373,16 +400,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
         if (first && g > 0 && !wait1(bar_a2e, (g - 1) & 1, sh, a, ERR_TIMEOUT_MMA)) return false;
         fence_after();
         const uint32_t zhi = smem_u32(zbuf), zlo = zhi + ZBYTES / 2;
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < RG::CHUNKS; ++c) {
           const int s = it % NSTAGE;
           if (!wait1(bar_full + 8 * s, (it / NSTAGE) & 1, sh, a, ERR_TIMEOUT_MMA)) return false;
           fence_after();
           const uint32_t mhi = smem_u32(stages + s * STAGE_BYTES), mlo = mhi + mbytes;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t zo = c * (ZBYTES / 4) + kk * 32;
+          for (int kk = 0; kk < RG::KSTEPS; ++kk) {
+            const int zk = c * RG::KSTEPS + kk;                 // K step within the 128-wide Z tile
+            const uint32_t zo = (zk / 4) * ZATOM + (zk % 4) * 32;
             const uint64_t dzh = sw128_desc(zhi + zo), dzl = sw128_desc(zlo + zo);
-            const uint64_t dmh = sw128_desc(mhi + kk * 32), dml = sw128_desc(mlo + kk * 32);
+            const uint64_t dmh = smem_desc(mhi + kk * 32, RG::SBO, RG::LAYOUT),
+                           dml = smem_desc(mlo + kk * 32, RG::SBO, RG::LAYOUT);
             const uint32_t acc = (first && c == 0 && kk == 0) ? 0u : 1u;
             mma_bf16(tmem + ACC2_COL, dzh, dmh, id2, acc);
             mma_bf16(tmem + ACC2_COL, dzh, dml, id2, 1u);
@@ -410,10 +439,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
             fence_after();
             const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t ah = sw128_desc(sa + kk * 32), al = sw128_desc(sa + TILE_BYTES + kk * 32);
-              const uint64_t bh = sw128_desc(sa + 2 * TILE_BYTES + kk * 32),
-                             bl = sw128_desc(sa + 3 * TILE_BYTES + kk * 32);
+            for (int kk = 0; kk < RG::KSTEPS; ++kk) {
+              const uint64_t ah = smem_desc(sa + kk * 32, RG::SBO, RG::LAYOUT),
+                             al = smem_desc(sa + TILE_BYTES + kk * 32, RG::SBO, RG::LAYOUT);
+              const uint64_t bh = smem_desc(sa + 2 * TILE_BYTES + kk * 32, RG::SBO, RG::LAYOUT),
+                             bl = smem_desc(sa + 3 * TILE_BYTES + kk * 32, RG::SBO, RG::LAYOUT);
               mma_bf16(d1, ah, bh, id1, (kc > 0 || kk > 0) ? 1u : 0u);
               mma_bf16(d1, ah, bl, id1, 1u);
               mma_bf16(d1, al, bh, id1, 1u);
@@ -442,8 +472,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
     const int colbase = (ew < 4) ? 0 : 64;   // accumulator columns of this warp
     const int row = quarter * 32 + lane;     // row of the A tile (TMEM lane)
     const int64_t arow = a_row0 + row;
-    const bool a_valid = a.a_ok ? (a.a_ok[arow] >= 0) : true;
-    const float bias_a = (a.mode == MODE_PASS1) ? a.bias[arow] : 0.f;
+    // No masks: padding rows and features meet zero chain operands (V and W' are
+    // zero there), and materialisation writes only the valid window.  The phase b
+    // is either part of the product (column of ones in X) or added here.
+    const bool add_bias = !a.bias_in_mma;
+    const float bias_a = (add_bias && a.mode == MODE_PASS1) ? a.bias[arow] : 0.f;
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     int t = 0;
     bool ok = true;
@@ -461,24 +494,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar_a1e + 8 * b);
-        // z = scale cos(acc + b), masked to valid rows and features
+        // z = cos(acc (+ b)); the factor sqrt(2/D) is applied when acc2 is written
         float z[64];
+        if (add_bias) {
+          const float* bcol = a.bias + bslot + colbase;
 #pragma unroll
-        for (int c = 0; c < 64; ++c) {
-          const uint32_t bits = c < 32 ? v0[c] : v1[c - 32];
-          const int64_t bcol = bslot + colbase + c;
-          const bool bv = a.b_ok ? (a.b_ok[bcol] >= 0) : true;
-          const float ph = (a.mode == MODE_PASS1) ? bias_a : a.bias[bcol];
-          z[c] = (a_valid && bv) ? a.scale * cos_rr(__uint_as_float(bits) + ph) : 0.f;
+          for (int c = 0; c < 64; ++c) {
+            const float ph = (a.mode == MODE_PASS1) ? bias_a : __ldg(bcol + c);
+            z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) + ph);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 64; ++c) z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]));
         }
         if (!chain) {
-          // materialise Z (float32) inside the window
+          // materialise Z = sqrt(2/D) cos(...) (float32) inside the window
           const int64_t r = arow - a.wz_r0;
           if (r < a.wz_nr) {
 #pragma unroll
             for (int c = 0; c < 64; ++c) {
               const int64_t f = bslot + colbase + c - a.wz_f0;
-              if (f < a.wz_nf) a.out[r * a.ldo + f] = z[c];
+              if (f < a.wz_nf) a.out[r * a.ldo + f] = a.scale * z[c];
             }
           }
           continue;
@@ -486,18 +522,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
         // Z tile must be free: the chain of the previous tile has completed
         if (t >= 1 && !waitw(bar_ze, (t - 1) & 1, sh, a, ERR_TIMEOUT_EPI)) { ok = false; break; }
         // split into hi/lo BF16 and store in the 128-byte swizzled K-major layout
-        unsigned char* zhi = zbuf + (colbase / 64) * TILE_BYTES;
+        unsigned char* zhi = zbuf + (colbase / 64) * ZATOM;
         unsigned char* zlo = zhi + ZBYTES / 2;
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
           uint32_t ph[4], pl[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            __nv_bfloat16 h0, l0, h1, l1;
-            split_bf16(z[ch * 8 + 2 * q], h0, l0);
-            split_bf16(z[ch * 8 + 2 * q + 1], h1, l1);
-            ph[q] = pack_bf16(h0, h1);
-            pl[q] = pack_bf16(l0, l1);
+            // hi = bf16x2(z0, z1); lo = bf16x2(z - hi) (packed conversions)
+            const __nv_bfloat162 h = __floats2bfloat162_rn(z[ch * 8 + 2 * q], z[ch * 8 + 2 * q + 1]);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(z[ch * 8 + 2 * q] - hf.x, z[ch * 8 + 2 * q + 1] - hf.y);
+            ph[q] = *reinterpret_cast<const uint32_t*>(&h);
+            pl[q] = *reinterpret_cast<const uint32_t*>(&l);
           }
           const uint32_t off = row * 128 + ((ch ^ (row & 7)) << 4);
           *reinterpret_cast<uint4*>(zhi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
@@ -517,11 +554,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
             uint32_t r8[8];
             tmem_ld8(tmem + lane_addr + ACC2_COL + c0 + c, r8);
             tmem_wait_ld();
+            const float sc = a.scale;
             float4* dst = reinterpret_cast<float4*>(orow + c0 + c);
-            dst[0] = make_float4(__uint_as_float(r8[0]), __uint_as_float(r8[1]), __uint_as_float(r8[2]),
-                                 __uint_as_float(r8[3]));
-            dst[1] = make_float4(__uint_as_float(r8[4]), __uint_as_float(r8[5]), __uint_as_float(r8[6]),
-                                 __uint_as_float(r8[7]));
+            dst[0] = make_float4(sc * __uint_as_float(r8[0]), sc * __uint_as_float(r8[1]),
+                                 sc * __uint_as_float(r8[2]), sc * __uint_as_float(r8[3]));
+            dst[1] = make_float4(sc * __uint_as_float(r8[4]), sc * __uint_as_float(r8[5]),
+                                 sc * __uint_as_float(r8[6]), sc * __uint_as_float(r8[7]));
           }
           fence_before();
           __syncwarp();
@@ -554,20 +592,35 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// K chunk of the ring (64: 128-byte swizzle, 2 stages; 32: 64-byte swizzle, 5 stages).
+// Measured on the multiclass workload: 64 is ~5 % faster (both are bound by shared-
+// memory bandwidth, see the profile notes), so it is the default; RFF_TC_KCHUNK=32
+// in the environment selects the other ring.
+int ring_kc() {
+  static int kc = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char* e = getenv("RFF_TC_KCHUNK");
+    kc = (e && atoi(e) == 32) ? 32 : 64;
+  });
+  return kc;
+}
+
 // 2-D BF16 tensor [rows][cols] (cols contiguous, leading dimension ld elements),
-// box of 64 columns x box_rows rows, 128-byte swizzle
+// box of kc columns x box_rows rows, swizzled to match the ring layout
 cudaError_t make_map(CUtensorMap* m, const void* ptr, int64_t cols, int64_t rows, int64_t ld, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ld * 2) % 16 || box_rows > 256 || box_rows < 1)
     return cudaErrorInvalidValue;
+  const int kc = ring_kc();
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)kc, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, kc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -575,11 +628,15 @@ cudaError_t launch(TcArgs& a, dim3 grid, cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_regen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    attr_err = cudaFuncSetAttribute(k_regen_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<64>());
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(k_regen_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_bytes<32>());
   });
   if (attr_err != cudaSuccess) return attr_err;
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
-  k_regen_tc<<<grid, NTHREADS, SMEM_BYTES, st>>>(a);
+  if (ring_kc() == 64) k_regen_tc<64><<<grid, NTHREADS, smem_bytes<64>(), st>>>(a);
+  else k_regen_tc<32><<<grid, NTHREADS, smem_bytes<32>(), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -596,18 +653,19 @@ int* err_word() {
 
 cudaError_t common_args(const TcView& v, TcArgs& a) {
   memset(&a, 0, sizeof(a));
-  a.nk = (int)(v.dld / 64);
+  a.nk = (int)(v.dld / ring_kc());
   a.mpad = (int)v.mpad;
   a.R = v.R;
   a.C = v.C;
   a.nsplit = v.nsplit;
   a.bias = v.bias;
   a.scale = v.scale;
+  a.bias_in_mma = v.bias_in_mma;
   a.fslots = v.fslots;
   a.err = err_word();
   if (!a.err) return cudaErrorMemoryAllocation;
   a.timeout_cycles = 4000000000LL;   // about two seconds at the boost clock
-  if (v.mpad > 256 || v.C > MAXG) return cudaErrorInvalidValue;
+  if (v.mpad > 256 || v.C > MAXG) return cudaErrorInvalidValue;   // the host checks these limits first
   return cudaSuccess;
 }
 

@@ -19,6 +19,7 @@ struct TcView {
   const int64_t *row_slot, *row_size, *col_slot, *col_size;  // host
   const int64_t *d_row_slot, *d_row_size, *d_col_slot, *d_col_size;  // device copies
   float scale;
+  int bias_in_mma;                  // 1: b is column d of G and X carries ones there
   cudaStream_t st;
 };
 
