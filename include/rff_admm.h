@@ -54,7 +54,7 @@ typedef enum {
 typedef enum {
   RFF_LOSS_SQUARED = 0,    /* |y - o|^2, real targets                                  */
   RFF_LOSS_HINGE = 1,      /* m = 1: max(0, 1 - y o); m > 1: one-vs-rest, +-1 targets   */
-  RFF_LOSS_LOGISTIC = 2,   /* m = 1: log(1 + exp(-y o)), y = +-1                       */
+  RFF_LOSS_LOGISTIC = 2,   /* log(1 + exp(-y o)) per output column, y = +-1            */
   RFF_LOSS_MULTINOMIAL = 3 /* log sum_k exp(o_k) - o_c, c = argmax_k y_k               */
 } rff_loss;
 
@@ -109,8 +109,8 @@ typedef struct rff_admm_s* rff_admm_t;
 /* Create a solver handle.  params: see rff_admm_params; copied.  stream: a
  * cudaStream_t or NULL.  *out receives the handle.  Errors: RFF_EINVAL for
  * out-of-range parameters (lambda <= 0, sigma <= 0, rho <= 0, D < 1, R < 1,
- * C < 1, C > D, m outside [1, 256], unknown enums, logistic loss with m != 1,
- * C > 64 with RFF_PREC_SPLIT_BF16),
+ * C < 1, C > D, m outside [1, 256], unknown enums, C > 64 with
+ * RFF_PREC_SPLIT_BF16),
  * RFF_ECUDA if no device is usable. */
 rff_status rff_admm_create(const rff_admm_params* params, void* stream, rff_admm_t* out);
 
@@ -131,6 +131,38 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Y, int64
  * pass over the data).  Errors: RFF_ENOTREADY without data, RFF_ENUMERIC if a
  * Gram matrix is not positive definite, RFF_ECUDA. */
 rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats);
+
+/* Device-memory budget of a handle (0 = whatever the device has free).  set_data
+ * refuses a working set beyond it (RFF_ENOMEM, before allocating) and the set-up
+ * sizes its factorisation batches to stay within it.  The GPU analogue of the
+ * memory model of Sec. 3 (eq. (mem)). */
+rff_status rff_admm_set_memory_limit(rff_admm_t h, size_t bytes);
+
+/* Device bytes a solve of n x d data with these parameters holds while it iterates
+ * (*resident: data, state, cached factors) and at its peak during set-up with the
+ * smallest factorisation batch (*peak); either pointer may be NULL.  No device work. */
+rff_status rff_admm_estimate_bytes(const rff_admm_params* params, int64_t n, int64_t d, size_t* resident,
+                                   size_t* peak);
+
+/* One lambda per output column (the columns are then independent solves that
+ * share X, sigma, D, the grid and therefore Z and its cached factor -- the lambda
+ * axis of a model-selection sweep costs one regeneration of Z for all lambdas).
+ * lambdas: m values > 0, copied; NULL restores params.lambda for every column.
+ * Separable losses only give independent columns (squared, hinge, logistic).
+ * Errors: RFF_EINVAL for a wrong count or a non-positive value. */
+rff_status rff_admm_set_lambdas(rff_admm_t h, const double* lambdas, int32_t m);
+
+/* Queue `iters` iterations on the handle's stream and return without waiting
+ * (set-up, when still needed, runs first and synchronously).  rff_admm_wait
+ * blocks until they finished and reports a device-side failure. */
+rff_status rff_admm_enqueue(rff_admm_t h, int32_t iters);
+rff_status rff_admm_wait(rff_admm_t h);
+
+/* Model-selection sweep: runs `iters` iterations of every handle (each created
+ * with its own stream, typically one per sigma with its lambdas as columns), all
+ * queued before any is waited for, so the solves overlap on the device.  Each
+ * iteration after a handle's first runs as one CUDA-graph launch. */
+rff_status rff_sweep_run(rff_admm_t* handles, int32_t n, int32_t iters);
 
 /* Scores f(x) = Wbar^T z(x) for q query rows (Sec. 2.2, H_{k,l}; prediction in
  * Sec. 5).  Xq: q x d, scores: q x m, both row-major float32, both host or both
@@ -190,6 +222,8 @@ typedef struct {
   double ms_pass2;         /* Z_ij W'_ij, Z regenerated (fused kernel)                       */
   double ms_exchange;      /* row exchange, nu update, loss prox, next V_ij                  */
   double ms_average;       /* Wbar, mu, mu'_ij updates                                      */
+  int32_t tc_kchunk;       /* K chunk of the tensor-core ring chosen by the autotuner (0: FP32) */
+  int32_t nsplit;          /* row splits of pass 1 chosen by the autotuner                   */
 } rff_admm_profile;
 
 rff_status rff_admm_set_profiling(rff_admm_t h, int enable);
@@ -243,6 +277,58 @@ rff_status rff_prox_reg(int32_t reg, const float* V, int64_t n, double tau, floa
  * triangle zeroed).  info (device, batch int32): 0, or k+1 for a non-positive
  * pivot at column k. */
 rff_status rff_cholesky_f64(double* A, int32_t batch, int32_t s, int32_t* info, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Serving: solve and scoring requests of different sizes, admitted by a device-
+ * memory budget and run side by side (one CUDA stream per active request); solved
+ * models stay resident for scoring until released.  The paper has no serving
+ * layer; admission uses the memory accounting of rff_admm_estimate_bytes (the GPU
+ * analogue of eq. (mem), Sec. 3).  Thread-safe: any host thread may submit, poll
+ * or release.
+ * ------------------------------------------------------------------------------ */
+typedef struct rff_server_s* rff_server_t;
+
+enum { RFF_REQ_SOLVE = 0, RFF_REQ_SCORE = 1 };
+
+typedef struct {
+  int64_t id;         /* request id returned by the submit call                          */
+  int32_t kind;       /* RFF_REQ_SOLVE or RFF_REQ_SCORE                                  */
+  int32_t status;     /* rff_status of the request                                        */
+  double queue_ms;    /* submit -> start (waiting for a worker and for device memory)     */
+  double run_ms;      /* start -> done                                                    */
+  double latency_ms;  /* submit -> done                                                   */
+} rff_completion;
+
+/* budget_bytes: device memory the server may hand out (0 = 90% of what is free);
+ * max_active: requests that may run at once (worker threads, 1..256). */
+rff_status rff_server_create(size_t budget_bytes, int32_t max_active, rff_server_t* out);
+
+/* Queue a solve of (X, Y) (host, n x d and n x m, copied) for `iters` iterations.
+ * *request_id doubles as the model id for scoring.  RFF_ENOMEM when the solve's
+ * peak memory exceeds the whole budget (it could never be admitted). */
+rff_status rff_server_submit_solve(rff_server_t srv, const rff_admm_params* params, const float* X, const float* Y,
+                                   int64_t n, int64_t d, int32_t iters, int64_t* request_id);
+
+/* Queue scores of q rows Xq (host, copied) against a model; `scores` (host, q x m)
+ * is written before the completion is posted and must stay valid until then.
+ * A model whose solve is still queued or running is waited for. */
+rff_status rff_server_submit_score(rff_server_t srv, int64_t model, const float* Xq, int64_t q, float* scores,
+                                   int64_t* request_id);
+
+/* Up to `max` completions, oldest first; waits up to wait_ms for the first one. */
+rff_status rff_server_poll(rff_server_t srv, rff_completion* out, int32_t max, int32_t* count, int32_t wait_ms);
+
+/* Weights of a solved model (host, D x m), as rff_admm_get_weights. */
+rff_status rff_server_get_weights(rff_server_t srv, int64_t model, float* W);
+
+/* Drop a solved (or failed) model and give its memory back to the budget. */
+rff_status rff_server_release(rff_server_t srv, int64_t model);
+
+/* Bytes currently reserved and the budget. */
+rff_status rff_server_memory(rff_server_t srv, size_t* used, size_t* budget);
+
+/* Stop the workers (running requests finish first) and free every model. */
+void rff_server_destroy(rff_server_t srv);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,16 @@ class rff_admm_stats(ctypes.Structure):
 class rff_admm_profile(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("launches", ctypes.c_int64), ("ms_prox_reg", ctypes.c_double),
                 ("ms_pass1", ctypes.c_double), ("ms_project", ctypes.c_double), ("ms_pass2", ctypes.c_double),
-                ("ms_exchange", ctypes.c_double), ("ms_average", ctypes.c_double)]
+                ("ms_exchange", ctypes.c_double), ("ms_average", ctypes.c_double), ("tc_kchunk", ctypes.c_int32),
+                ("nsplit", ctypes.c_int32)]
+
+
+class rff_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("kind", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+RFF_REQ_SOLVE, RFF_REQ_SCORE = 0, 1
 
 
 # every entry point of include/rff_admm.h: name -> (restype, argtypes)
@@ -63,6 +72,13 @@ PROTOTYPES = {
     "rff_admm_set_state": (_I32, [_P, _P, _SZ]),
     "rff_admm_set_profiling": (_I32, [_P, ctypes.c_int]),
     "rff_admm_get_profile": (_I32, [_P, ctypes.POINTER(rff_admm_profile)]),
+    "rff_admm_set_memory_limit": (_I32, [_P, _SZ]),
+    "rff_admm_estimate_bytes": (_I32, [ctypes.POINTER(rff_admm_params), _I64, _I64, ctypes.POINTER(_SZ),
+                                       ctypes.POINTER(_SZ)]),
+    "rff_admm_set_lambdas": (_I32, [_P, _P, _I32]),
+    "rff_admm_enqueue": (_I32, [_P, _I32]),
+    "rff_admm_wait": (_I32, [_P]),
+    "rff_sweep_run": (_I32, [_P, _I32, _I32]),
     "rff_admm_destroy": (None, [_P]),
     "rff_admm_last_error": (ctypes.c_char_p, [_P]),
     "rff_philox4x32_10": (_I32, [_P, _U64, _I64, _P, _P]),
@@ -71,6 +87,15 @@ PROTOTYPES = {
     "rff_prox_loss": (_I32, [_I32, _P, _P, _I64, _I32, _D, _I32, _P, _P]),
     "rff_prox_reg": (_I32, [_I32, _P, _I64, _D, _P, _P]),
     "rff_cholesky_f64": (_I32, [_P, _I32, _I32, _P, _P]),
+    "rff_server_create": (_I32, [_SZ, _I32, ctypes.POINTER(_P)]),
+    "rff_server_submit_solve": (_I32, [_P, ctypes.POINTER(rff_admm_params), _P, _P, _I64, _I64, _I32,
+                                       ctypes.POINTER(_I64)]),
+    "rff_server_submit_score": (_I32, [_P, _I64, _P, _I64, _P, ctypes.POINTER(_I64)]),
+    "rff_server_poll": (_I32, [_P, ctypes.POINTER(rff_completion), _I32, ctypes.POINTER(_I32), _I32]),
+    "rff_server_get_weights": (_I32, [_P, _I64, _P]),
+    "rff_server_release": (_I32, [_P, _I64]),
+    "rff_server_memory": (_I32, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
+    "rff_server_destroy": (None, [_P]),
 }
 
 
@@ -209,6 +234,42 @@ def rff_admm_get_profile(h):
     return {k: getattr(p, k) for k, _ in rff_admm_profile._fields_}
 
 
+def rff_admm_set_memory_limit(h, nbytes):
+    _check(lib.rff_admm_set_memory_limit(h, nbytes), h)
+
+
+def rff_admm_estimate_bytes(params, n, d):
+    """(resident, peak) device bytes of a solve; no device work."""
+    r, p = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(lib.rff_admm_estimate_bytes(ctypes.byref(params), n, d, ctypes.byref(r), ctypes.byref(p)), None,
+           "rff_admm_estimate_bytes")
+    return r.value, p.value
+
+
+def rff_admm_set_lambdas(h, lambdas):
+    if lambdas is None:
+        _check(lib.rff_admm_set_lambdas(h, None, 0), h)
+        return
+    arr = np.ascontiguousarray(lambdas, dtype=np.float64)
+    _check(lib.rff_admm_set_lambdas(h, ctypes.c_void_p(arr.ctypes.data), arr.size), h)
+
+
+def rff_admm_enqueue(h, iters):
+    _check(lib.rff_admm_enqueue(h, iters), h)
+
+
+def rff_admm_wait(h):
+    _check(lib.rff_admm_wait(h), h)
+
+
+def rff_sweep_run(handles, iters):
+    arr = (ctypes.c_void_p * len(handles))(*[hh.value for hh in handles])
+    st = lib.rff_sweep_run(arr, len(handles), iters)
+    if st != RFF_OK:
+        msgs = [lib.rff_admm_last_error(hh).decode() for hh in handles]
+        raise RffError(st, "; ".join(m for m in msgs if m) or "rff_sweep_run failed")
+
+
 def rff_admm_destroy(h):
     lib.rff_admm_destroy(h)
 
@@ -262,6 +323,57 @@ def rff_cholesky_f64(A, info, stream=None):
     return A
 
 
+def rff_server_create(budget_bytes=0, max_active=4):
+    s = ctypes.c_void_p()
+    _check(lib.rff_server_create(budget_bytes, max_active, ctypes.byref(s)), None, "rff_server_create")
+    return s
+
+
+def rff_server_submit_solve(srv, params, X, Y, iters):
+    px, _ = _ptr(X)
+    py, _ = _ptr(Y)
+    rid = ctypes.c_int64(0)
+    _check(lib.rff_server_submit_solve(srv, ctypes.byref(params), px, py, X.shape[0], X.shape[1], iters,
+                                       ctypes.byref(rid)), None, "rff_server_submit_solve")
+    return rid.value
+
+
+def rff_server_submit_score(srv, model, Xq, out):
+    pq, _ = _ptr(Xq)
+    po, _ = _ptr(out)
+    rid = ctypes.c_int64(0)
+    _check(lib.rff_server_submit_score(srv, model, pq, Xq.shape[0], po, ctypes.byref(rid)), None,
+           "rff_server_submit_score")
+    return rid.value
+
+
+def rff_server_poll(srv, max_count=64, wait_ms=0):
+    buf = (rff_completion * max_count)()
+    n = ctypes.c_int32(0)
+    _check(lib.rff_server_poll(srv, buf, max_count, ctypes.byref(n), wait_ms), None, "rff_server_poll")
+    return [{k: getattr(buf[i], k) for k, _ in rff_completion._fields_} for i in range(n.value)]
+
+
+def rff_server_get_weights(srv, model, out):
+    po, _ = _ptr(out)
+    _check(lib.rff_server_get_weights(srv, model, po), None, "rff_server_get_weights")
+    return out
+
+
+def rff_server_release(srv, model):
+    _check(lib.rff_server_release(srv, model), None, "rff_server_release")
+
+
+def rff_server_memory(srv):
+    u, b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(lib.rff_server_memory(srv, ctypes.byref(u), ctypes.byref(b)), None, "rff_server_memory")
+    return u.value, b.value
+
+
+def rff_server_destroy(srv):
+    lib.rff_server_destroy(srv)
+
+
 # ----------------------------------------------------------------- convenience
 class Solver:
     """Owns one rff_admm_t handle."""
@@ -293,6 +405,15 @@ class Solver:
 
     def set_state(self, state):
         rff_admm_set_state(self.h, state)
+
+    def set_lambdas(self, lambdas):
+        rff_admm_set_lambdas(self.h, lambdas)
+
+    def enqueue(self, iters):
+        rff_admm_enqueue(self.h, iters)
+
+    def wait(self):
+        rff_admm_wait(self.h)
 
     def profiling(self, enable=True):
         rff_admm_set_profiling(self.h, enable)

@@ -34,8 +34,10 @@ struct rff_admm_s {
   // ---- geometry
   bool has_data = false, factored = false;
   int64_t bias_col = -1;  // split path: column of X (ones) and G (b) that folds b into X.G
+  size_t mem_limit = 0;   // device bytes this handle may use (0: whatever is free)
   int64_t n = 0, d = 0, dld = 0, m = 0, mpad = 0, D = 0, nslots = 0, fslots = 0;
-  int R = 1, C = 1, nsplit = 1, iters_done = 0;
+  int R = 1, C = 1, nsplit = 1, nsplit_max = 1, iters_done = 0;
+  int tc_kc = 0;  // ring K chunk of the tensor-core passes, chosen by the autotuner
   float t_loss = 0.f, t_reg = 0.f;
   std::vector<int64_t> row_start, row_size, row_slot, col_start, col_size, col_slot, foff;
 
@@ -52,6 +54,8 @@ struct rff_admm_s {
   float *W = nullptr, *Wbar = nullptr, *mu = nullptr, *What = nullptr, *muij = nullptr, *rhs = nullptr,
         *Rpart = nullptr;
   float* Q32 = nullptr;       // cached (I + Z_ij^T Z_ij)^-1 per block
+  std::vector<double> lam_col;  // lambda of each output column (empty: params.lambda for all)
+  float* lam_dev = nullptr;     // lambda_c / lambda per column (m_pad), or null
   GemmDesc* gdesc = nullptr;  // R*C
   double* partials = nullptr;
   int* flag = nullptr;
@@ -63,6 +67,7 @@ struct rff_admm_s {
   rff_admm_profile prof{};
   std::vector<cudaEvent_t> ev;
   int64_t launches = 0;
+  int pending_profiled = 0;   // profiled iterations enqueued since the last accumulation
   // one iteration captured as a CUDA graph (after an eager first iteration)
   cudaGraphExec_t gexec = nullptr;
   void drop_graph() {
@@ -117,7 +122,6 @@ rff_status check_params(const rff_admm_params* p, std::string& why) {
   if (p->D < 1 || p->D > (int64_t)1 << 30) { why = "D out of range"; return RFF_EINVAL; }
   if (p->R < 1 || p->C < 1 || p->C > p->D) { why = "bad block grid"; return RFF_EINVAL; }
   if (p->m < 1 || p->m > 256) { why = "m must be in [1, 256]"; return RFF_EINVAL; }
-  if (p->loss == RFF_LOSS_LOGISTIC && p->m != 1) { why = "binary logistic loss needs m = 1"; return RFF_EINVAL; }
   if (p->newton_iters < 0 || p->newton_iters > 100) { why = "newton_iters out of range"; return RFF_EINVAL; }
   if (p->prec == RFF_PREC_SPLIT_BF16 && p->C > 64) { why = "the split-BF16 path supports C <= 64"; return RFF_EINVAL; }
   return RFF_OK;
@@ -177,12 +181,85 @@ size_t working_set_bytes(const rff_admm_s& s) {
   t += (size_t)s.C * s.nslots * s.mpad * f * 2;                 // Op, V32
   if (s.split_path()) t += (size_t)s.C * s.nslots * s.mpad * b2 * 2;
   t += (size_t)s.fslots * s.mpad * f * 5;                       // W, Wbar, mu, mu_old, Wbar_old
-  t += (size_t)s.R * s.fslots * s.mpad * f * (4 + s.nsplit);    // What, muij, rhs, muij_old, Rpart
+  t += (size_t)s.R * s.fslots * s.mpad * f * (4 + s.nsplit_max);    // What, muij, rhs, muij_old, Rpart
   if (s.split_path()) t += (size_t)s.R * s.fslots * s.mpad * b2 * 2 + (size_t)s.fslots * s.mpad * b2 * 2;
   size_t fac = 0;
   for (int j = 0; j < s.C; ++j) fac += (size_t)s.col_size[j] * s.col_size[j];
   t += fac * s.R * f;
   return t + (64u << 20);
+}
+
+// relative weights lambda_c / lambda of the output columns (padding columns 0)
+rff_status upload_lambdas(rff_admm_t h) {
+  auto& s = *h;
+  if (!s.lam_dev) return RFF_OK;
+  std::vector<float> w(s.mpad, 0.f);
+  for (int64_t c = 0; c < s.m; ++c)
+    w[c] = s.lam_col.empty() ? 1.f : (float)(s.lam_col[c] / s.p.lambda);
+  CK(cudaMemcpyAsync(s.lam_dev, w.data(), w.size() * 4, cudaMemcpyHostToDevice, s.st));
+  CK(cudaStreamSynchronize(s.st));
+  return RFF_OK;
+}
+
+// Block grid, slot layout and prox steps of a data set of n rows and d inputs.
+void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
+  s.n = n;
+  s.d = d;
+  s.dld = round_up(d, 64);
+  // the split path folds the phase b into the tensor-core product when column d is free
+  s.bias_col = (s.p.prec == RFF_PREC_SPLIT_BF16 && round_up(d + 1, 64) == s.dld) ? d : -1;
+  s.m = s.p.m;
+  s.mpad = round_up(s.m, 16);
+  s.D = s.p.D;
+  s.R = s.p.R;
+  s.C = s.p.C;
+  partition(n, s.R, s.row_start, s.row_size);
+  partition(s.D, s.C, s.col_start, s.col_size);
+  s.row_slot.assign(s.R, 0);
+  s.col_slot.assign(s.C, 0);
+  int64_t acc = 0;
+  for (int i = 0; i < s.R; ++i) { s.row_slot[i] = acc; acc += round_up(s.row_size[i], SLOT); }
+  s.nslots = acc;
+  acc = 0;
+  for (int j = 0; j < s.C; ++j) { s.col_slot[j] = acc; acc += round_up(s.col_size[j], SLOT); }
+  s.fslots = acc;
+  s.foff.assign((size_t)s.R * s.C + 1, 0);
+  for (int i = 0; i < s.R; ++i)
+    for (int j = 0; j < s.C; ++j)
+      s.foff[(size_t)i * s.C + j + 1] = s.foff[(size_t)i * s.C + j] + s.col_size[j] * s.col_size[j];
+  const double nn = (double)n;
+  if (s.p.rho_scale == RFF_RHO_SUM) {
+    s.t_loss = (float)(1.0 / s.p.rho);
+    s.t_reg = (float)(nn * s.p.lambda / s.p.rho);
+  } else {
+    s.t_loss = (float)(1.0 / (nn * s.p.rho));
+    s.t_reg = (float)(s.p.lambda / s.p.rho);
+  }
+  // pass-1 row splits: enough CTAs for two waves on the device
+  {
+    int nsm = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tile = s.split_path() ? 128 : 64;
+    const int64_t ftiles = s.fslots / tile;
+    int64_t min_rows = n;
+    for (int i = 0; i < s.R; ++i) min_rows = std::min(min_rows, s.row_size[i]);
+    const int64_t want = ceil_div(2 * (int64_t)nsm, ftiles * s.R);
+    const int64_t cap = std::min<int64_t>(ceil_div(min_rows, tile), 64);
+    s.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
+    s.nsplit_max = s.nsplit;
+  }
+
+}
+
+// Bytes of set-up scratch for one block batch (FP64 Gram and inverse of `batch`
+// blocks, one materialised row chunk of Z, factorisation scratch).
+size_t setup_bytes(const rff_admm_s& s, int64_t batch) {
+  int64_t smax = 0;
+  for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
+  const int64_t chunk_rows = std::min<int64_t>(32768, round_up(*std::max_element(s.row_size.begin(), s.row_size.end()), SLOT));
+  return (size_t)batch * smax * smax * 8 * 2 + (size_t)chunk_rows * smax * 4 + factor_scratch_bytes((int)batch, (int)smax) +
+         (size_t)batch * 4 + 4096;
 }
 
 }  // namespace
@@ -229,6 +306,8 @@ rff_status rff_admm_get_profile(rff_admm_t h, rff_admm_profile* out) {
   if (!h || !out) return RFF_EINVAL;
   *out = h->prof;
   out->launches = h->launches;
+  out->tc_kchunk = h->split_path() ? (h->tc_kc ? h->tc_kc : 64) : 0;
+  out->nsplit = h->nsplit;
   return RFF_OK;
 }
 
@@ -253,58 +332,16 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   h->iters_done = 0;
 
   auto& s = *h;
-  s.n = n;
-  s.d = d;
-  s.dld = round_up(d, 64);
-  // the split path folds the phase b into the tensor-core product when column d is free
-  s.bias_col = (s.p.prec == RFF_PREC_SPLIT_BF16 && round_up(d + 1, 64) == s.dld) ? d : -1;
-  s.m = s.p.m;
-  s.mpad = round_up(s.m, 16);
-  s.D = s.p.D;
-  s.R = s.p.R;
-  s.C = s.p.C;
-  partition(n, s.R, s.row_start, s.row_size);
-  partition(s.D, s.C, s.col_start, s.col_size);
-  s.row_slot.assign(s.R, 0);
-  s.col_slot.assign(s.C, 0);
-  int64_t acc = 0;
-  for (int i = 0; i < s.R; ++i) { s.row_slot[i] = acc; acc += round_up(s.row_size[i], SLOT); }
-  s.nslots = acc;
-  acc = 0;
-  for (int j = 0; j < s.C; ++j) { s.col_slot[j] = acc; acc += round_up(s.col_size[j], SLOT); }
-  s.fslots = acc;
-  s.foff.assign((size_t)s.R * s.C + 1, 0);
-  for (int i = 0; i < s.R; ++i)
-    for (int j = 0; j < s.C; ++j)
-      s.foff[(size_t)i * s.C + j + 1] = s.foff[(size_t)i * s.C + j] + s.col_size[j] * s.col_size[j];
-  const double nn = (double)n;
-  if (s.p.rho_scale == RFF_RHO_SUM) {
-    s.t_loss = (float)(1.0 / s.p.rho);
-    s.t_reg = (float)(nn * s.p.lambda / s.p.rho);
-  } else {
-    s.t_loss = (float)(1.0 / (nn * s.p.rho));
-    s.t_reg = (float)(s.p.lambda / s.p.rho);
-  }
-  // pass-1 row splits: enough CTAs for two waves on the device
-  {
-    int nsm = 148, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t tile = s.split_path() ? 128 : 64;
-    const int64_t ftiles = s.fslots / tile;
-    int64_t min_rows = n;
-    for (int i = 0; i < s.R; ++i) min_rows = std::min(min_rows, s.row_size[i]);
-    const int64_t want = ceil_div(2 * (int64_t)nsm, ftiles * s.R);
-    s.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, ceil_div(min_rows, tile), 64}));
-  }
+  compute_geometry(s, n, d);
 
   // memory check before any allocation
   size_t fr = 0, tot = 0;
   CK(cudaMemGetInfo(&fr, &tot));
-  const size_t need = working_set_bytes(s);
-  if (need > fr) {
-    return h->fail(RFF_ENOMEM, "working set " + std::to_string(need >> 20) + " MiB exceeds free device memory " +
-                                   std::to_string(fr >> 20) + " MiB");
+  const size_t need = working_set_bytes(s) + setup_bytes(s, 1);
+  const size_t avail = s.mem_limit ? std::min(fr, s.mem_limit) : fr;
+  if (need > avail) {
+    return h->fail(RFF_ENOMEM, "working set " + std::to_string(need >> 20) + " MiB exceeds the " +
+                                   std::to_string(avail >> 20) + " MiB available");
   }
 
   rff_status st = RFF_OK;
@@ -352,9 +389,10 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   AL(s.muij, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.muij_old, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.rhs, (int64_t)s.R * s.fslots * s.mpad);
-  AL(s.Rpart, (int64_t)s.nsplit * s.R * s.fslots * s.mpad);
+  AL(s.Rpart, (int64_t)s.nsplit_max * s.R * s.fslots * s.mpad);
   AL(s.Q32, s.foff.back());
   AL(s.gdesc, s.R * s.C);
+  AL(s.lam_dev, s.mpad);
   AL(s.partials, 1024);
   AL(s.flag, 4);
 #undef AL
@@ -376,6 +414,10 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   CK(cudaMemcpyAsync(s.d_col_slot, s.col_slot.data(), s.C * 8, cudaMemcpyHostToDevice, s.st));
   CK(cudaMemcpyAsync(s.d_col_size, s.col_size.data(), s.C * 8, cudaMemcpyHostToDevice, s.st));
   CK(cudaMemsetAsync(s.d_zero, 0, 16, s.st));
+  {
+    rff_status lr = upload_lambdas(h);
+    if (lr != RFF_OK) { h->free_all(); return lr; }
+  }
 
   // data: stage (device), validate, scatter into slots
   const size_t xb = (size_t)n * d * 4, yb = (size_t)n * s.m * 4;
@@ -418,7 +460,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   CK(cudaMemsetAsync(s.Op, 0, rowb * s.C, s.st));
   for (float* b : {s.W, s.Wbar, s.mu}) CK(cudaMemsetAsync(b, 0, colb, s.st));
   for (float* b : {s.What, s.muij, s.rhs}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
-  CK(cudaMemsetAsync(s.Rpart, 0, colb * s.R * s.nsplit, s.st));
+  CK(cudaMemsetAsync(s.Rpart, 0, colb * s.R * s.nsplit_max, s.st));
   if (s.split_path()) {
     CK(cudaMemsetAsync(s.VThi, 0, rowb / 2 * s.C, s.st));
     CK(cudaMemsetAsync(s.VTlo, 0, rowb / 2 * s.C, s.st));
@@ -437,6 +479,50 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
 // ------------------------------------------------------------------ set-up
 namespace {
 
+// Tile-shape autotuner of the tensor-core passes: times pass 1 + pass 2 for each
+// ring geometry (K chunk 64 or 32) on the handle's own data and keeps the
+// fastest.  Both geometries issue the same MMAs in the same order, so the choice
+// changes speed, never results (a run is reproducible whatever the timing).  The
+// passes only write their scratch outputs (R partials, O'), which every
+// iteration recomputes.
+rff_status autotune(rff_admm_t h) {
+  auto& s = *h;
+  if (!s.split_path()) return RFF_OK;
+  std::vector<int> splits{s.nsplit};
+  if (s.nsplit_max != s.nsplit) splits.push_back(s.nsplit_max);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_kc = 64, best_ns = s.nsplit;
+  for (int kc : {64, 32}) {
+    for (int ns : splits) {
+      s.tc_kc = kc;
+      s.nsplit = ns;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {     // first run warms caches and descriptors
+        CK(cudaEventRecord(e0, s.st));
+        CK(tc_pass1(tc_view(s), s.Rpart));
+        CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1));
+        CK(cudaEventRecord(e1, s.st));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      if (ms < best) {
+        best = ms;
+        best_kc = kc;
+        best_ns = ns;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s.tc_kc = best_kc;
+  s.nsplit = best_ns;
+  if (tc_error_word() != 0) return h->fail(RFF_ETIMEOUT, "a tensor-core pass gave up waiting during tuning");
+  return RFF_OK;
+}
+
 rff_status setup_factors(rff_admm_t h) {
   auto& s = *h;
   const float scale = (float)std::sqrt(2.0 / (double)s.D);
@@ -453,6 +539,10 @@ rff_status setup_factors(rff_admm_t h) {
   const int64_t chunk_rows = std::min<int64_t>(32768, round_up(*std::max_element(s.row_size.begin(), s.row_size.end()), SLOT));
   const size_t zbytes = (size_t)chunk_rows * smax * 4;
   size_t budget = (size_t)(fr * 0.6);
+  if (s.mem_limit) {
+    const size_t ws = working_set_bytes(s);
+    budget = std::min(budget, s.mem_limit > ws ? s.mem_limit - ws : (size_t)0);
+  }
   budget = budget > zbytes + (256u << 20) ? budget - zbytes - (256u << 20) : 0;
   int64_t batch = std::max<int64_t>(1, std::min<int64_t>(nblocks, (int64_t)(budget / std::max<size_t>(per_block + factor_scratch_bytes(1, (int)smax), 1))));
   const size_t need = (size_t)batch * per_block + zbytes + factor_scratch_bytes((int)batch, (int)smax) + (size_t)batch * 4 + 4096;
@@ -521,7 +611,7 @@ rff_status setup_factors(rff_admm_t h) {
   CK(cudaFree(s.scratch.p));
   s.scratch = DevBuf{};
   s.factored = true;
-  return RFF_OK;
+  return autotune(h);
 }
 
 // ------------------------------------------------------------------ iteration
@@ -563,7 +653,7 @@ rff_status iterate(rff_admm_t h, int k) {
   rff_status r;
   if ((r = mark(h, k, 0)) != RFF_OK) return r;
   // W_j <- prox_{(n lam / rho) r}(Wbar_j - mu_j)
-  CK(launch_prox_reg(s.p.reg, s.Wbar, s.mu, nfe, s.t_reg, s.W, s.st));
+  CK(launch_prox_reg(s.p.reg, s.Wbar, s.mu, nfe, s.t_reg, s.W, s.st, s.lam_dev, (int)s.mpad));
   if ((r = mark(h, k, 1)) != RFF_OK) return r;
   // pass 1: R_ij = Z_ij^T V_ij,  V_ij = Obar_ij + nu_i
   PassArgs a = base_pass_args(s);
@@ -635,6 +725,60 @@ rff_status capture_iteration(rff_admm_t h) {
   return RFF_OK;
 }
 
+// Enqueue `iters` iterations on the handle's stream (no host synchronisation).
+// copy_old: keep nu, Obar, mu, Wbar, mu' of the iteration before the last (residuals).
+rff_status enqueue_iterations(rff_admm_t h, int iters, bool copy_old) {
+  auto& s = *h;
+  const int64_t rowb = s.nslots * s.mpad * 4, colb = s.fslots * s.mpad * 4;
+  const int base = s.pending_profiled;   // profiled iterations not yet accumulated
+  if (s.profiling && (size_t)(base + iters) * 7 > s.ev.size()) {
+    const size_t old = s.ev.size();
+    s.ev.resize((size_t)(base + iters) * 7);
+    for (size_t e = old; e < s.ev.size(); ++e) CK(cudaEventCreate(&s.ev[e]));
+  }
+  for (int k = 0; k < iters; ++k) {
+    if (copy_old && k == iters - 1) {
+      CK(cudaMemcpyAsync(s.nu_old, s.nu, rowb, cudaMemcpyDeviceToDevice, s.st));
+      CK(cudaMemcpyAsync(s.Obar_old, s.Obar, rowb, cudaMemcpyDeviceToDevice, s.st));
+      CK(cudaMemcpyAsync(s.mu_old, s.mu, colb, cudaMemcpyDeviceToDevice, s.st));
+      CK(cudaMemcpyAsync(s.Wbar_old, s.Wbar, colb, cudaMemcpyDeviceToDevice, s.st));
+      CK(cudaMemcpyAsync(s.muij_old, s.muij, colb * s.R, cudaMemcpyDeviceToDevice, s.st));
+    }
+    rff_status r = RFF_OK;
+    if (s.profiling || s.iters_done == 0) {
+      r = iterate(h, base + k);
+    } else {
+      if (!s.gexec && (r = capture_iteration(h)) != RFF_OK) return r;
+      CK(cudaGraphLaunch(s.gexec, s.st));
+      s.launches += s.split_path() ? 9 : 7;
+    }
+    if (r != RFF_OK) return r;
+    s.iters_done++;
+  }
+  s.pending_profiled += s.profiling ? iters : 0;
+  return RFF_OK;
+}
+
+// After the stream has drained: tensor-core error word, profiling accumulation.
+rff_status finish_iterations(rff_admm_t h) {
+  auto& s = *h;
+  if (s.split_path() && tc_error_word() != 0)
+    return h->fail(RFF_ETIMEOUT, "a tensor-core pass gave up waiting (device error word set)");
+  if (s.pending_profiled > 0) {
+    double* acc[6] = {&s.prof.ms_prox_reg, &s.prof.ms_pass1, &s.prof.ms_project, &s.prof.ms_pass2,
+                      &s.prof.ms_exchange, &s.prof.ms_average};
+    for (int k = 0; k < s.pending_profiled; ++k)
+      for (int ph = 0; ph < 6; ++ph) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, s.ev[(size_t)k * 7 + ph], s.ev[(size_t)k * 7 + ph + 1]));
+        *acc[ph] += ms;
+      }
+    s.prof.iters += s.pending_profiled;
+    s.pending_profiled = 0;
+  }
+  return RFF_OK;
+}
+
 rff_status sum_partials(rff_admm_t h, double& out) {
   std::vector<double> hp(1024);
   CK(cudaMemcpyAsync(hp.data(), h->partials, 1024 * 8, cudaMemcpyDeviceToHost, h->st));
@@ -689,6 +833,7 @@ TcView tc_view(const rff_admm_s& s) {
   v.d_row_slot = s.d_row_slot; v.d_row_size = s.d_row_size; v.d_col_slot = s.d_col_slot; v.d_col_size = s.d_col_size;
   v.scale = (float)std::sqrt(2.0 / (double)s.D);
   v.bias_in_mma = s.bias_col >= 0 ? 1 : 0;
+  v.kc = s.tc_kc;
   v.st = s.st;
   return v;
 }
@@ -712,45 +857,15 @@ rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats) {
     if (r != RFF_OK) return r;
   }
   CK(cudaEventRecord(e1, s.st));
-  const int64_t rowb = s.nslots * s.mpad * 4, colb = s.fslots * s.mpad * 4;
-  if (s.profiling && (size_t)iters * 7 > s.ev.size()) {
-    const size_t old = s.ev.size();
-    s.ev.resize((size_t)iters * 7);
-    for (size_t e = old; e < s.ev.size(); ++e) CK(cudaEventCreate(&s.ev[e]));
-  }
-  for (int k = 0; k < iters; ++k) {
-    if (stats && k == iters - 1) {
-      CK(cudaMemcpyAsync(s.nu_old, s.nu, rowb, cudaMemcpyDeviceToDevice, s.st));
-      CK(cudaMemcpyAsync(s.Obar_old, s.Obar, rowb, cudaMemcpyDeviceToDevice, s.st));
-      CK(cudaMemcpyAsync(s.mu_old, s.mu, colb, cudaMemcpyDeviceToDevice, s.st));
-      CK(cudaMemcpyAsync(s.Wbar_old, s.Wbar, colb, cudaMemcpyDeviceToDevice, s.st));
-      CK(cudaMemcpyAsync(s.muij_old, s.muij, colb * s.R, cudaMemcpyDeviceToDevice, s.st));
-    }
-    rff_status r = RFF_OK;
-    if (s.profiling || s.iters_done == 0) {
-      r = iterate(h, k);
-    } else {
-      if (!s.gexec && (r = capture_iteration(h)) != RFF_OK) return r;
-      CK(cudaGraphLaunch(s.gexec, s.st));
-      s.launches += s.split_path() ? 9 : 7;
-    }
+  {
+    rff_status r = enqueue_iterations(h, iters, stats != nullptr);
     if (r != RFF_OK) return r;
-    s.iters_done++;
   }
   CK(cudaEventRecord(e2, s.st));
   CK(cudaEventSynchronize(e2));
-  if (s.split_path() && tc_error_word() != 0)
-    return h->fail(RFF_ETIMEOUT, "a tensor-core pass gave up waiting (device error word set)");
-  if (s.profiling) {
-    double* acc[6] = {&s.prof.ms_prox_reg, &s.prof.ms_pass1, &s.prof.ms_project, &s.prof.ms_pass2,
-                      &s.prof.ms_exchange, &s.prof.ms_average};
-    for (int k = 0; k < iters; ++k)
-      for (int ph = 0; ph < 6; ++ph) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, s.ev[(size_t)k * 7 + ph], s.ev[(size_t)k * 7 + ph + 1]));
-        *acc[ph] += ms;
-      }
-    s.prof.iters += iters;
+  {
+    rff_status r = finish_iterations(h);
+    if (r != RFF_OK) return r;
   }
   if (stats) {
     memset(stats, 0, sizeof(*stats));
@@ -778,7 +893,7 @@ rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats) {
     CK(launch_loss_partials(s.p.loss, s.Y, s.Op, s.row_of_slot, s.nslots, (int)s.m, (int)s.mpad, s.partials, 1024,
                             s.st));
     if ((r = sum_partials(h, loss)) != RFF_OK) return r;
-    CK(launch_reg_partials(s.p.reg, s.Wbar, s.fslots * s.mpad, s.partials, 1024, s.st));
+    CK(launch_reg_partials(s.p.reg, s.Wbar, s.fslots * s.mpad, s.partials, 1024, s.st, s.lam_dev, (int)s.mpad));
     if ((r = sum_partials(h, reg)) != RFF_OK) return r;
     stats->objective = loss + (double)s.n * s.p.lambda * reg;
   }
@@ -786,6 +901,82 @@ rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats) {
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
   return RFF_OK;
+}
+
+rff_status rff_admm_set_memory_limit(rff_admm_t h, size_t bytes) {
+  if (!h) return RFF_EINVAL;
+  h->mem_limit = bytes;
+  return RFF_OK;
+}
+
+rff_status rff_admm_estimate_bytes(const rff_admm_params* params, int64_t n, int64_t d, size_t* resident,
+                                   size_t* peak) {
+  std::string why;
+  rff_status st = check_params(params, why);
+  if (st != RFF_OK) return st;
+  if (n < params->R || d < 1 || n > ((int64_t)1 << 31) - 1) return RFF_EINVAL;
+  rff_admm_s s;
+  s.p = *params;
+  compute_geometry(s, n, d);
+  const size_t ws = working_set_bytes(s);
+  if (resident) *resident = ws;
+  if (peak) *peak = ws + setup_bytes(s, 1) + (size_t)n * (d + s.m) * 4 + (size_t)s.nslots * s.dld * 4;
+  return RFF_OK;
+}
+
+rff_status rff_admm_set_lambdas(rff_admm_t h, const double* lambdas, int32_t m) {
+  if (!h) return RFF_EINVAL;
+  h->err.clear();
+  if (!lambdas) {
+    h->lam_col.clear();
+  } else {
+    if (m != h->p.m) return h->fail(RFF_EINVAL, "need one lambda per output column");
+    for (int32_t c = 0; c < m; ++c)
+      if (!(lambdas[c] > 0) || !std::isfinite(lambdas[c])) return h->fail(RFF_EINVAL, "lambdas must be > 0");
+    h->lam_col.assign(lambdas, lambdas + m);
+  }
+  return upload_lambdas(h);
+}
+
+rff_status rff_admm_enqueue(rff_admm_t h, int32_t iters) {
+  if (!h) return RFF_EINVAL;
+  h->err.clear();
+  if (!h->has_data) return h->fail(RFF_ENOTREADY, "no data: call rff_admm_set_data first");
+  if (iters < 0) return h->fail(RFF_EINVAL, "iters must be >= 0");
+  if (!h->factored) {
+    rff_status r = setup_factors(h);
+    if (r != RFF_OK) return r;
+  }
+  return enqueue_iterations(h, iters, false);
+}
+
+rff_status rff_admm_wait(rff_admm_t h) {
+  if (!h) return RFF_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  return finish_iterations(h);
+}
+
+rff_status rff_sweep_run(rff_admm_t* handles, int32_t n, int32_t iters) {
+  if (n < 0 || iters < 0 || (n > 0 && !handles)) return RFF_EINVAL;
+  for (int32_t k = 0; k < n; ++k)
+    if (!handles[k] || !handles[k]->has_data) return RFF_EINVAL;
+  // set-up of every solve first (factors are computed once per handle) ...
+  for (int32_t k = 0; k < n; ++k)
+    if (!handles[k]->factored) {
+      rff_status r = setup_factors(handles[k]);
+      if (r != RFF_OK) return r;
+    }
+  // ... then every solve's iterations are queued on its own stream and run side by side
+  rff_status first = RFF_OK;
+  for (int32_t k = 0; k < n; ++k) {
+    rff_status r = enqueue_iterations(handles[k], iters, false);
+    if (r != RFF_OK && first == RFF_OK) first = r;
+  }
+  for (int32_t k = 0; k < n; ++k) {
+    rff_status r = rff_admm_wait(handles[k]);
+    if (r != RFF_OK && first == RFF_OK) first = r;
+  }
+  return first;
 }
 
 rff_status rff_admm_predict(rff_admm_t h, const float* Xq, int64_t q, float* scores, int is_device_ptr) {

@@ -183,13 +183,15 @@ __global__ void k_prox_loss(int loss, const float* __restrict__ V, const float* 
   out[r * ld + c] = prox_scalar(loss, V[r * ld + c], Y[r * ld + c], t, iters);
 }
 
-// prox of tau r at (V - mu): l2 |w|^2 -> (v - mu)/(1 + 2 tau); l1 -> soft threshold
+// prox of tau r at (V - mu): l2 |w|^2 -> (v - mu)/(1 + 2 tau); l1 -> soft threshold.
+// With tau_col, column c (= e mod ncol) uses tau * tau_col[c] (one lambda per output column).
 __global__ void k_prox_reg(int reg, const float* __restrict__ V, const float* __restrict__ mu, int64_t n, float tau,
-                           float* __restrict__ out) {
+                           const float* __restrict__ tau_col, int ncol, float* __restrict__ out) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
+  const float t = tau_col ? tau * tau_col[e % ncol] : tau;
   const float x = V[e] - (mu ? mu[e] : 0.f);
-  out[e] = (reg == 0) ? x / (1.f + 2.f * tau) : copysignf(fmaxf(fabsf(x) - tau, 0.f), x);
+  out[e] = (reg == 0) ? x / (1.f + 2.f * t) : copysignf(fmaxf(fabsf(x) - t, 0.f), x);
 }
 
 // Row-local exchange after pass 2 (one warp per row slot, lanes over outputs):
@@ -367,11 +369,13 @@ __global__ void __launch_bounds__(256) k_loss_sum(int loss, const float* __restr
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// sum_e w_c r(W_e), c = e mod ncol (w null: all weights 1)
 __global__ void __launch_bounds__(256) k_reg_sum(int reg, const float* __restrict__ W, int64_t n,
+                                                 const float* __restrict__ w, int ncol,
                                                  double* __restrict__ partials) {
   double acc = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    acc += reg == 0 ? (double)W[e] * W[e] : fabs((double)W[e]);
+    acc += (w ? (double)w[e % ncol] : 1.0) * (reg == 0 ? (double)W[e] * W[e] : fabs((double)W[e]));
   const double s = block_sum<256>(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
@@ -430,9 +434,9 @@ cudaError_t launch_prox_loss(int loss, const float* V, const float* Y, int64_t n
 }
 
 cudaError_t launch_prox_reg(int reg, const float* V, const float* mu, int64_t n, float tau, float* out,
-                            cudaStream_t st) {
+                            cudaStream_t st, const float* tau_col, int ncol) {
   if (n <= 0) return cudaSuccess;
-  k_prox_reg<<<nblk(n), 256, 0, st>>>(reg, V, mu, n, tau, out);
+  k_prox_reg<<<nblk(n), 256, 0, st>>>(reg, V, mu, n, tau, tau_col, ncol > 0 ? ncol : 1, out);
   return cudaGetLastError();
 }
 
@@ -476,8 +480,9 @@ cudaError_t launch_loss_partials(int loss, const float* Y, const float* S, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_reg_partials(int reg, const float* W, int64_t n, double* partials, int nblocks, cudaStream_t st) {
-  k_reg_sum<<<nblocks, 256, 0, st>>>(reg, W, n, partials);
+cudaError_t launch_reg_partials(int reg, const float* W, int64_t n, double* partials, int nblocks, cudaStream_t st,
+                                const float* w, int ncol) {
+  k_reg_sum<<<nblocks, 256, 0, st>>>(reg, W, n, w, ncol > 0 ? ncol : 1, partials);
   return cudaGetLastError();
 }
 

@@ -112,7 +112,7 @@ cudaError_t launch_split_bf16(const float* src, int64_t n, __nv_bfloat16* hi, __
 cudaError_t launch_prox_loss(int loss, const float* V, const float* Y, int64_t n, int m, int64_t ld, float t,
                              int newton, float* out, cudaStream_t st);
 cudaError_t launch_prox_reg(int reg, const float* V, const float* mu, int64_t n, float tau, float* out,
-                            cudaStream_t st);
+                            cudaStream_t st, const float* tau_col = nullptr, int ncol = 1);
 struct RowEpiArgs {
   const float* Op;      // C x slots x mpad
   float* O;             // slots x mpad (in: O^k, out: O^{k+1} = prox(Obar - nu))
@@ -140,7 +140,8 @@ cudaError_t launch_sqdiff_partials(const float* a, const float* b, int64_t n, do
                                    cudaStream_t st);
 cudaError_t launch_loss_partials(int loss, const float* Y, const float* S, const int32_t* row_ok, int64_t nslots,
                                  int m, int mpad, double* partials, int nblocks, cudaStream_t st);
-cudaError_t launch_reg_partials(int reg, const float* W, int64_t n, double* partials, int nblocks, cudaStream_t st);
+cudaError_t launch_reg_partials(int reg, const float* W, int64_t n, double* partials, int nblocks, cudaStream_t st,
+                                const float* w = nullptr, int ncol = 1);
 cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
 cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, cudaStream_t st);
 cudaError_t launch_set_diag(double* A, int64_t ld, int64_t s, double v, cudaStream_t st);

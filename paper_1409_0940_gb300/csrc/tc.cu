@@ -608,12 +608,12 @@ int ring_kc() {
 
 // 2-D BF16 tensor [rows][cols] (cols contiguous, leading dimension ld elements),
 // box of kc columns x box_rows rows, swizzled to match the ring layout
-cudaError_t make_map(CUtensorMap* m, const void* ptr, int64_t cols, int64_t rows, int64_t ld, int box_rows) {
+cudaError_t make_map(CUtensorMap* m, const void* ptr, int64_t cols, int64_t rows, int64_t ld, int box_rows,
+                     int kc) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ld * 2) % 16 || box_rows > 256 || box_rows < 1)
     return cudaErrorInvalidValue;
-  const int kc = ring_kc();
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
   const cuuint32_t box[2] = {(cuuint32_t)kc, (cuuint32_t)box_rows};
@@ -624,7 +624,7 @@ cudaError_t make_map(CUtensorMap* m, const void* ptr, int64_t cols, int64_t rows
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch(TcArgs& a, dim3 grid, cudaStream_t st) {
+cudaError_t launch(TcArgs& a, dim3 grid, cudaStream_t st, int kc) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
@@ -635,7 +635,7 @@ cudaError_t launch(TcArgs& a, dim3 grid, cudaStream_t st) {
   });
   if (attr_err != cudaSuccess) return attr_err;
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
-  if (ring_kc() == 64) k_regen_tc<64><<<grid, NTHREADS, smem_bytes<64>(), st>>>(a);
+  if (kc == 64) k_regen_tc<64><<<grid, NTHREADS, smem_bytes<64>(), st>>>(a);
   else k_regen_tc<32><<<grid, NTHREADS, smem_bytes<32>(), st>>>(a);
   return cudaGetLastError();
 }
@@ -651,9 +651,11 @@ int* err_word() {
   return p;
 }
 
+int view_kc(const TcView& v) { return (v.kc == 32 || v.kc == 64) ? v.kc : ring_kc(); }
+
 cudaError_t common_args(const TcView& v, TcArgs& a) {
   memset(&a, 0, sizeof(a));
-  a.nk = (int)(v.dld / ring_kc());
+  a.nk = (int)(v.dld / view_kc(v));
   a.mpad = (int)v.mpad;
   a.R = v.R;
   a.C = v.C;
@@ -691,13 +693,13 @@ cudaError_t tc_write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int6
   a.b_ok = v.feat_ok;
   a.wz_r0 = r0; a.wz_nr = nr; a.wz_f0 = f0; a.wz_nf = nf; a.ldo = ldo;
   a.out = out;
-  if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
+  if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   a.tM_hi = a.tB_hi;
   a.tM_lo = a.tB_lo;
-  return launch(a, dim3((unsigned)ceil_div(nr, 128)), v.st);
+  return launch(a, dim3((unsigned)ceil_div(nr, 128)), v.st, view_kc(v));
 }
 
 cudaError_t tc_pass1(const TcView& v, float* Rpart) {
@@ -710,13 +712,13 @@ cudaError_t tc_pass1(const TcView& v, float* Rpart) {
   a.b_ok = v.row_ok;
   a.out = Rpart;
   a.out_block_stride = v.fslots * v.mpad;
-  if ((e = make_map(&a.tA_hi, v.Ghi, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tA_lo, v.Glo, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tB_hi, v.Xhi, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tB_lo, v.Xlo, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tM_hi, v.VThi, v.nslots, (int64_t)v.C * v.mpad, v.nslots, (int)v.mpad)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tM_lo, v.VTlo, v.nslots, (int64_t)v.C * v.mpad, v.nslots, (int)v.mpad)) != cudaSuccess) return e;
-  return launch(a, dim3((unsigned)(v.fslots / 128), (unsigned)v.R, (unsigned)v.nsplit), v.st);
+  if ((e = make_map(&a.tA_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tA_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_lo, v.Xlo, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_hi, v.VThi, v.nslots, (int64_t)v.C * v.mpad, v.nslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_lo, v.VTlo, v.nslots, (int64_t)v.C * v.mpad, v.nslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
+  return launch(a, dim3((unsigned)(v.fslots / 128), (unsigned)v.R, (unsigned)v.nsplit), v.st, view_kc(v));
 }
 
 cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, int64_t m_block_stride,
@@ -732,13 +734,13 @@ cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloa
   a.b_ok = v.feat_ok;
   a.out = out;
   a.out_block_stride = v.nslots * v.mpad;
-  if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tM_hi, Mhi, v.fslots, (int64_t)v.R * v.mpad, v.fslots, (int)v.mpad)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tM_lo, Mlo, v.fslots, (int64_t)v.R * v.mpad, v.fslots, (int)v.mpad)) != cudaSuccess) return e;
-  return launch(a, dim3((unsigned)(v.nslots / 128)), v.st);
+  if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_hi, Mhi, v.fslots, (int64_t)v.R * v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_lo, Mlo, v.fslots, (int64_t)v.R * v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
+  return launch(a, dim3((unsigned)(v.nslots / 128)), v.st, view_kc(v));
 }
 
 cudaError_t tc_predict(const TcView& v, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int64_t nrows,
@@ -752,13 +754,13 @@ cudaError_t tc_predict(const TcView& v, const __nv_bfloat16* Xh, const __nv_bflo
   a.a_ok = nullptr;
   a.b_ok = v.feat_ok;
   a.out = out;
-  if ((e = make_map(&a.tA_hi, Xh, v.dld, nrows, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tA_lo, Xl, v.dld, nrows, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tM_hi, Mhi, v.fslots, v.mpad, v.fslots, (int)v.mpad)) != cudaSuccess) return e;
-  if ((e = make_map(&a.tM_lo, Mlo, v.fslots, v.mpad, v.fslots, (int)v.mpad)) != cudaSuccess) return e;
-  return launch(a, dim3((unsigned)(nrows / 128)), v.st);
+  if ((e = make_map(&a.tA_hi, Xh, v.dld, nrows, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tA_lo, Xl, v.dld, nrows, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_hi, Mhi, v.fslots, v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
+  if ((e = make_map(&a.tM_lo, Mlo, v.fslots, v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
+  return launch(a, dim3((unsigned)(nrows / 128)), v.st, view_kc(v));
 }
 
 }  // namespace rff

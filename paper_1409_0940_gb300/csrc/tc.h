@@ -20,6 +20,7 @@ struct TcView {
   const int64_t *d_row_slot, *d_row_size, *d_col_slot, *d_col_size;  // device copies
   float scale;
   int bias_in_mma;                  // 1: b is column d of G and X carries ones there
+  int kc;                           // ring K chunk (64 or 32; 0 = library default)
   cudaStream_t st;
 };
 
