@@ -53,7 +53,14 @@ struct rff_admm_s {
                 *WbTlo = nullptr;
   float *W = nullptr, *Wbar = nullptr, *mu = nullptr, *What = nullptr, *muij = nullptr, *rhs = nullptr,
         *Rpart = nullptr;
-  float* Q32 = nullptr;       // cached (I + Z_ij^T Z_ij)^-1 per block
+  float* Q32 = nullptr;       // cached (I + Z_ij^T Z_ij)^-1 per block (float32 path)
+  // split path: the cached inverses split three ways into BF16, blocks stacked by rows
+  // (block b from row qrow[b], rows padded to 128, ldq columns), and the right-hand
+  // side of the projection split the same way, transposed to [R][mpad][fslots]
+  __nv_bfloat16 *Q1 = nullptr, *Q2 = nullptr, *Q3 = nullptr, *rT1 = nullptr, *rT2 = nullptr, *rT3 = nullptr;
+  int64_t ldq = 0, q_rows = 0;
+  std::vector<int64_t> qrow;
+  int32_t* qtab = nullptr;    // per block: Q row, s_j, i*mpad, slot_j, i*fslots + slot_j
   std::vector<double> lam_col;  // lambda of each output column (empty: params.lambda for all)
   float* lam_dev = nullptr;     // lambda_c / lambda per column (m_pad), or null
   GemmDesc* gdesc = nullptr;  // R*C
@@ -181,11 +188,16 @@ size_t working_set_bytes(const rff_admm_s& s) {
   t += (size_t)s.C * s.nslots * s.mpad * f * 2;                 // Op, V32
   if (s.split_path()) t += (size_t)s.C * s.nslots * s.mpad * b2 * 2;
   t += (size_t)s.fslots * s.mpad * f * 5;                       // W, Wbar, mu, mu_old, Wbar_old
-  t += (size_t)s.R * s.fslots * s.mpad * f * (4 + s.nsplit_max);    // What, muij, rhs, muij_old, Rpart
-  if (s.split_path()) t += (size_t)s.R * s.fslots * s.mpad * b2 * 2 + (size_t)s.fslots * s.mpad * b2 * 2;
-  size_t fac = 0;
-  for (int j = 0; j < s.C; ++j) fac += (size_t)s.col_size[j] * s.col_size[j];
-  t += fac * s.R * f;
+  t += (size_t)s.R * s.fslots * s.mpad * f * (3 + s.nsplit_max);    // What, muij, muij_old, Rpart
+  if (s.split_path()) {
+    t += (size_t)s.R * s.fslots * s.mpad * b2 * (2 + 3) + (size_t)s.fslots * s.mpad * b2 * 2;   // WT, rT, WbT
+    t += (size_t)s.q_rows * s.ldq * b2 * 3 + (size_t)s.R * s.C * 5 * 4;                        // Q splits, table
+  } else {
+    t += (size_t)s.R * s.fslots * s.mpad * f;                                                   // rhs
+    size_t fac = 0;
+    for (int j = 0; j < s.C; ++j) fac += (size_t)s.col_size[j] * s.col_size[j];
+    t += fac * s.R * f + (size_t)s.R * s.C * sizeof(GemmDesc);
+  }
   return t + (64u << 20);
 }
 
@@ -227,6 +239,18 @@ void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
   for (int i = 0; i < s.R; ++i)
     for (int j = 0; j < s.C; ++j)
       s.foff[(size_t)i * s.C + j + 1] = s.foff[(size_t)i * s.C + j] + s.col_size[j] * s.col_size[j];
+  s.qrow.assign((size_t)s.R * s.C, 0);
+  s.q_rows = 0;
+  s.ldq = 0;
+  if (s.split_path()) {
+    int64_t smax = 0;
+    for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
+    s.ldq = round_up(smax, 32);
+    for (int64_t b = 0; b < (int64_t)s.R * s.C; ++b) {
+      s.qrow[b] = s.q_rows;
+      s.q_rows += round_up(s.col_size[b % s.C], SLOT);
+    }
+  }
   const double nn = (double)n;
   if (s.p.rho_scale == RFF_RHO_SUM) {
     s.t_loss = (float)(1.0 / s.p.rho);
@@ -388,10 +412,20 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   AL(s.What, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.muij, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.muij_old, (int64_t)s.R * s.fslots * s.mpad);
-  AL(s.rhs, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.Rpart, (int64_t)s.nsplit_max * s.R * s.fslots * s.mpad);
-  AL(s.Q32, s.foff.back());
-  AL(s.gdesc, s.R * s.C);
+  if (s.split_path()) {
+    AL(s.Q1, s.q_rows * s.ldq);
+    AL(s.Q2, s.q_rows * s.ldq);
+    AL(s.Q3, s.q_rows * s.ldq);
+    AL(s.rT1, (int64_t)s.R * s.mpad * s.fslots);
+    AL(s.rT2, (int64_t)s.R * s.mpad * s.fslots);
+    AL(s.rT3, (int64_t)s.R * s.mpad * s.fslots);
+    AL(s.qtab, (int64_t)s.R * s.C * 5);
+  } else {
+    AL(s.rhs, (int64_t)s.R * s.fslots * s.mpad);
+    AL(s.Q32, s.foff.back());
+    AL(s.gdesc, s.R * s.C);
+  }
   AL(s.lam_dev, s.mpad);
   AL(s.partials, 1024);
   AL(s.flag, 4);
@@ -459,13 +493,15 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   CK(cudaMemsetAsync(s.V32, 0, rowb * s.C, s.st));
   CK(cudaMemsetAsync(s.Op, 0, rowb * s.C, s.st));
   for (float* b : {s.W, s.Wbar, s.mu}) CK(cudaMemsetAsync(b, 0, colb, s.st));
-  for (float* b : {s.What, s.muij, s.rhs}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
+  for (float* b : {s.What, s.muij}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
+  if (s.rhs) CK(cudaMemsetAsync(s.rhs, 0, colb * s.R, s.st));
   CK(cudaMemsetAsync(s.Rpart, 0, colb * s.R * s.nsplit_max, s.st));
   if (s.split_path()) {
     CK(cudaMemsetAsync(s.VThi, 0, rowb / 2 * s.C, s.st));
     CK(cudaMemsetAsync(s.VTlo, 0, rowb / 2 * s.C, s.st));
     CK(cudaMemsetAsync(s.WThi, 0, colb / 2 * s.R, s.st));
     CK(cudaMemsetAsync(s.WTlo, 0, colb / 2 * s.R, s.st));
+    for (__nv_bfloat16* b : {s.rT1, s.rT2, s.rT3}) CK(cudaMemsetAsync(b, 0, colb / 2 * s.R, s.st));
   }
   CK(launch_prox_loss(s.p.loss, s.O, s.Y, s.nslots, (int)s.m, s.mpad, s.t_loss, s.p.newton_iters, s.O, s.st));
   // zero O on padding rows (prox(0) with y = 0 is not zero for the squared loss only if y != 0; y = 0 there)
@@ -555,6 +591,8 @@ rff_status setup_factors(rff_admm_t h) {
   int32_t* info = reinterpret_cast<int32_t*>(Zc + chunk_rows * smax);
   void* fscr = reinterpret_cast<char*>(info) + round_up(batch * 4, 256);
 
+  if (s.split_path())   // padding rows and columns of the split inverses stay zero
+    for (__nv_bfloat16* q : {s.Q1, s.Q2, s.Q3}) CK(cudaMemsetAsync(q, 0, (size_t)s.q_rows * s.ldq * 2, s.st));
   for (int64_t b0 = 0; b0 < nblocks; b0 += batch) {
     const int64_t nb = std::min(batch, nblocks - b0);
     std::vector<MatJob> jobs;
@@ -586,7 +624,10 @@ rff_status setup_factors(rff_admm_t h) {
     for (int64_t bb = 0; bb < nb; ++bb) {
       const int64_t blk = b0 + bb;
       const int64_t sj = s.col_size[blk % s.C];
-      CK(launch_convert_f64_f32(Q64 + bb * smax * smax, s.Q32 + s.foff[blk], sj * sj, s.st));
+      if (s.split_path())
+        CK(launch_split3_q(Q64 + bb * smax * smax, (int)sj, s.ldq, s.qrow[blk], s.Q1, s.Q2, s.Q3, s.st));
+      else
+        CK(launch_convert_f64_f32(Q64 + bb * smax * smax, s.Q32 + s.foff[blk], sj * sj, s.st));
     }
     std::vector<int32_t> hinfo(nb);
     CK(cudaMemcpyAsync(hinfo.data(), info, nb * 4, cudaMemcpyDeviceToHost, s.st));
@@ -598,14 +639,23 @@ rff_status setup_factors(rff_admm_t h) {
   }
   // iteration GEMM descriptors: x = Q rhs
   std::vector<GemmDesc> g(nblocks);
+  std::vector<int32_t> qt((size_t)nblocks * 5);
   for (int i = 0; i < s.R; ++i)
     for (int j = 0; j < s.C; ++j) {
       const int64_t blk = (int64_t)i * s.C + j, sj = s.col_size[j];
       const int64_t off = ((int64_t)i * s.fslots + s.col_slot[j]) * s.mpad;
-      float* Qb = s.Q32 + s.foff[blk];
-      g[blk] = GemmDesc{Qb, s.rhs + off, nullptr, s.What + off, (int)sj, (int)s.mpad, (int)sj, sj, s.mpad, 0, s.mpad};
+      if (s.split_path()) {
+        const int64_t v[5] = {s.qrow[blk], sj, (int64_t)i * s.mpad, s.col_slot[j], (int64_t)i * s.fslots + s.col_slot[j]};
+        for (int t = 0; t < 5; ++t) qt[(size_t)blk * 5 + t] = (int32_t)v[t];
+      } else {
+        float* Qb = s.Q32 + s.foff[blk];
+        g[blk] = GemmDesc{Qb, s.rhs + off, nullptr, s.What + off, (int)sj, (int)s.mpad, (int)sj, sj, s.mpad, 0, s.mpad};
+      }
     }
-  CK(cudaMemcpyAsync(s.gdesc, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, s.st));
+  if (s.split_path())
+    CK(cudaMemcpyAsync(s.qtab, qt.data(), qt.size() * 4, cudaMemcpyHostToDevice, s.st));
+  else
+    CK(cudaMemcpyAsync(s.gdesc, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, s.st));
   CK(cudaStreamSynchronize(s.st));
   // the set-up scratch (FP64 Gram and inverse batches) is released
   CK(cudaFree(s.scratch.p));
@@ -635,6 +685,32 @@ PassArgs base_pass_args(const rff_admm_s& s) {
   a.mpad = (int)s.mpad;
   a.nsplit = s.nsplit;
   return a;
+}
+
+QgemmView qgemm_view(const rff_admm_s& s) {
+  QgemmView v{};
+  v.Q1 = s.Q1;
+  v.Q2 = s.Q2;
+  v.Q3 = s.Q3;
+  v.q_rows = s.q_rows;
+  v.ldq = s.ldq;
+  v.R1 = s.rT1;
+  v.R2 = s.rT2;
+  v.R3 = s.rT3;
+  v.r_rows = (int64_t)s.R * s.mpad;
+  v.r_cols = s.fslots;
+  v.tab = s.qtab;
+  v.nblocks = s.R * s.C;
+  int64_t smax = 0;
+  for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
+  v.max_s = (int)smax;
+  v.mpad = (int)s.mpad;
+  v.out = s.What;
+  v.WThi = s.WThi;
+  v.WTlo = s.WTlo;
+  v.fslots = s.fslots;
+  v.st = s.st;
+  return v;
 }
 
 // phase boundaries of one iteration; with profiling on, events k*7 .. k*7+6
@@ -670,13 +746,18 @@ rff_status iterate(rff_admm_t h, int k) {
   // graph projection, eq. (gpWij): W'_ij = Q_ij (Wbar_j - mu'_ij + R_ij) with the cached inverse.
   // (A refinement step r = rhs - H x computed in FP32 adds more rounding than it removes, and an
   // FP64 or compensated residual costs several times the solve on this part's FP64/FP32 pipes.)
-  CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st));
-  CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st));
+  if (s.split_path()) {
+    // six-product split-BF16 GEMM on the tensor cores; also writes W' transposed and split for pass 2
+    CK(launch_rhs_split3T(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, s.fslots, (int)s.mpad, s.feat_of_slot, s.rT1,
+                          s.rT2, s.rT3, s.st));
+    CK(tc_qgemm(qgemm_view(s)));
+  } else {
+    CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st));
+    CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st));
+  }
   if ((r = mark(h, k, 3)) != RFF_OK) return r;
   // pass 2: O'_ij = Z_ij W'_ij (eq. (gpOij))
   if (s.split_path()) {
-    CK(launch_transpose_split(s.What, s.fslots, (int)s.mpad, s.R, s.fslots * s.mpad, s.WThi, s.WTlo, s.fslots,
-                              s.mpad * s.fslots, s.st));
     CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1));
   } else {
     a.M = s.What;
@@ -698,7 +779,7 @@ rff_status iterate(rff_admm_t h, int k) {
   // averaging and dual updates
   CK(launch_avg_dual(s.W, s.What, s.R, nfe, s.Wbar, s.mu, s.muij, s.st));
   if ((r = mark(h, k, 6)) != RFF_OK) return r;
-  s.launches += s.split_path() ? 9 : 7;
+  s.launches += s.split_path() ? 8 : 7;
   return RFF_OK;
 }
 
@@ -750,7 +831,7 @@ rff_status enqueue_iterations(rff_admm_t h, int iters, bool copy_old) {
     } else {
       if (!s.gexec && (r = capture_iteration(h)) != RFF_OK) return r;
       CK(cudaGraphLaunch(s.gexec, s.st));
-      s.launches += s.split_path() ? 9 : 7;
+      s.launches += s.split_path() ? 8 : 7;
     }
     if (r != RFF_OK) return r;
     s.iters_done++;

@@ -1,0 +1,320 @@
+// Cached projection of the split path on tensor cores (eq. (gpWij) with the cached
+// inverse of eq. (cache)):  W'_ij = Q_ij (Wbar_j - mu'_ij + R_ij)  for all blocks.
+//
+// Q_ij and the right-hand side are each split into three BF16 terms
+// (x = x1 + x2 + x3 + O(2^-24 |x|)); the six products whose exponents sum to at
+// most -16 (11, 12, 21, 13, 22, 31) accumulate in TMEM in FP32, which gives the
+// accuracy of an FP32 product.  One CTA computes 128 rows of one block's result
+// (all m_pad columns, one N = m_pad accumulator); a TMA ring of 32-element K
+// chunks (64-byte swizzle) feeds the six A and B tiles of each chunk.  Warp 0
+// issues the copies, one thread of warp 1 the MMAs, warps 2..5 write the result,
+// both row-major in FP32 (for the averaging step) and transposed as a hi/lo BF16
+// pair (the chain operand of pass 2).
+// Waits are bounded as in the regeneration kernel.
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "tc.h"
+#include "tcgen05.cuh"
+
+namespace rff {
+
+namespace {
+
+using namespace tc5;
+
+constexpr int QKC = 32;                      // K elements per ring stage
+constexpr uint32_t QATILE = 128 * QKC * 2;   // 8 KB: 128 rows x 64 bytes
+constexpr int QMAXS = 8;
+constexpr int QNT = 192;
+constexpr int ERR_Q = 8;
+
+struct QArgs {
+  CUtensorMap tQ1, tQ2, tQ3, tR1, tR2, tR3;
+  int mpad, ns;
+  uint32_t stage_bytes, tmem_cols;
+  const int* tab;   // per block: qrow, s, ry, slot, orow
+  int nblocks;
+  float* out;                 // [R*fslots][mpad]
+  __nv_bfloat16 *wthi, *wtlo; // [R*mpad][fslots]
+  int64_t fslots;
+  int* err;
+  long long timeout_cycles;
+};
+
+struct QShared {
+  uint64_t full[QMAXS], empty[QMAXS];
+  uint64_t acc_full, mma_done;
+  uint32_t tmem;
+  int abort_flag;
+};
+
+__device__ __forceinline__ bool qwait(uint32_t bar, uint32_t parity, QShared& sh, const QArgs& a) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*(volatile int*)&sh.abort_flag) return false;
+    if (clock64() - t0 > a.timeout_cycles) {
+      *(volatile int*)&sh.abort_flag = 1;
+      atomicOr(a.err, ERR_Q);
+      return false;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(QNT, 1) k_qgemm(const __grid_constant__ QArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  QShared& sh = *reinterpret_cast<QShared*>(base + a.ns * a.stage_bytes);
+  const int b = blockIdx.y;
+  const int qrow = a.tab[5 * b], s = a.tab[5 * b + 1], ry = a.tab[5 * b + 2], slot = a.tab[5 * b + 3],
+            orow = a.tab[5 * b + 4];
+  const int m0 = blockIdx.x * 128;
+  if (m0 >= s) return;   // uniform across the CTA
+  const int nk = (s + QKC - 1) / QKC;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t bar_full = smem_u32(&sh.full[0]), bar_empty = smem_u32(&sh.empty[0]);
+  const uint32_t bar_acc = smem_u32(&sh.acc_full), bar_done = smem_u32(&sh.mma_done);
+  const uint32_t mb = (uint32_t)a.mpad * (QKC * 2);   // one B tile: m_pad rows x 64 bytes
+  if (threadIdx.x == 0) {
+    sh.abort_flag = 0;
+    for (int i = 0; i < a.ns; ++i) {
+      mbar_init(bar_full + 8 * i, 1);
+      mbar_init(bar_empty + 8 * i, 1);
+    }
+    mbar_init(bar_acc, 1);
+    mbar_init(bar_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sh.tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t issued = 0;
+      for (int kc = 0; kc < nk; ++kc) {
+        const int st = kc % a.ns;
+        const uint32_t use = kc / a.ns;
+        if (use > 0 && !qwait(bar_empty + 8 * st, (use - 1) & 1, sh, a)) break;
+        const uint32_t fb = bar_full + 8 * st;
+        mbar_expect_tx(fb, a.stage_bytes);
+        const uint32_t dst = smem_u32(base + st * a.stage_bytes);
+        tma_load_2d(dst, &a.tQ1, kc * QKC, qrow + m0, fb);
+        tma_load_2d(dst + QATILE, &a.tQ2, kc * QKC, qrow + m0, fb);
+        tma_load_2d(dst + 2 * QATILE, &a.tQ3, kc * QKC, qrow + m0, fb);
+        tma_load_2d(dst + 3 * QATILE, &a.tR1, slot + kc * QKC, ry, fb);
+        tma_load_2d(dst + 3 * QATILE + mb, &a.tR2, slot + kc * QKC, ry, fb);
+        tma_load_2d(dst + 3 * QATILE + 2 * mb, &a.tR3, slot + kc * QKC, ry, fb);
+        ++issued;
+      }
+      // copies in flight finish before the CTA may exit (bounded)
+      for (uint32_t u = issued > (uint32_t)a.ns ? issued - a.ns : 0; u < issued; ++u) {
+        const int st = u % a.ns;
+        const long long t0 = clock64();
+        while (!mbar_try(bar_full + 8 * st, (u / a.ns) & 1) && clock64() - t0 < a.timeout_cycles) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, a.mpad);
+      bool ok = true;
+      for (int kc = 0; kc < nk && ok; ++kc) {
+        const int st = kc % a.ns;
+        if (!qwait(bar_full + 8 * st, (kc / a.ns) & 1, sh, a)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t sa = smem_u32(base + st * a.stage_bytes);
+#pragma unroll
+        for (int kk = 0; kk < QKC / 16; ++kk) {
+          const uint64_t q1 = smem_desc(sa + kk * 32, 512, 4), q2 = smem_desc(sa + QATILE + kk * 32, 512, 4),
+                         q3 = smem_desc(sa + 2 * QATILE + kk * 32, 512, 4);
+          const uint32_t sb = sa + 3 * QATILE + kk * 32;
+          const uint64_t r1 = smem_desc(sb, 512, 4), r2 = smem_desc(sb + mb, 512, 4),
+                         r3 = smem_desc(sb + 2 * mb, 512, 4);
+          mma_bf16(tmem, q1, r1, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(tmem, q1, r2, idesc, 1u);
+          mma_bf16(tmem, q2, r1, idesc, 1u);
+          mma_bf16(tmem, q1, r3, idesc, 1u);
+          mma_bf16(tmem, q2, r2, idesc, 1u);
+          mma_bf16(tmem, q3, r1, idesc, 1u);
+        }
+        mma_commit(bar_empty + 8 * st);
+      }
+      if (ok) mma_commit(bar_acc);
+      mma_commit(bar_done);
+      qwait(bar_done, 0, sh, a);
+    }
+  } else {
+    // epilogue: lanes = rows of the block's result, m_pad columns
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    int ok = 0;
+    if (lane == 0) ok = qwait(bar_acc, 0, sh, a) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) {
+      fence_after();
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+      float* orow_p = a.out + (int64_t)(orow + m0 + row) * a.mpad;
+      const bool valid = m0 + row < s;
+      // transposed copy: column c of block i at row i*mpad + c, this lane's feature slot
+      const int64_t tcol = slot + m0 + row;
+      __nv_bfloat16* th = a.wthi + (int64_t)ry * a.fslots + tcol;
+      __nv_bfloat16* tl = a.wtlo + (int64_t)ry * a.fslots + tcol;
+      for (int c = 0; c < a.mpad; c += 8) {
+        uint32_t r8[8];
+        tmem_ld8(taddr + c, r8);
+        tmem_wait_ld();
+        if (valid) {
+          float x[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) x[t] = __uint_as_float(r8[t]);
+          float4* dst = reinterpret_cast<float4*>(orow_p + c);
+          dst[0] = make_float4(x[0], x[1], x[2], x[3]);
+          dst[1] = make_float4(x[4], x[5], x[6], x[7]);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            __nv_bfloat16 hi, lo;
+            split_bf16(x[t], hi, lo);
+            th[(int64_t)(c + t) * a.fslots] = hi;
+            tl[(int64_t)(c + t) * a.fslots] = lo;
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+}
+
+// ---- the right-hand side, split three ways and transposed: rT_t[i][c][slot]
+__global__ void k_rhs_split3T(const float* __restrict__ Wbar, const float* __restrict__ muij,
+                              const float* __restrict__ Rpart, int nsplit, int R, int64_t fslots, int mpad,
+                              const int32_t* __restrict__ feat_ok, __nv_bfloat16* __restrict__ r1,
+                              __nv_bfloat16* __restrict__ r2, __nv_bfloat16* __restrict__ r3) {
+  __shared__ float tile[32][33];
+  const int i = blockIdx.z;
+  const int64_t p0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 256 threads
+  const int64_t nfe = fslots * mpad;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t p = p0 + rr;
+    const int c = c0 + tx;
+    float v = 0.f;
+    if (p < fslots && c < mpad && feat_ok[p] >= 0) {
+      const int64_t e = p * mpad + c, t = (int64_t)i * nfe + e;
+      v = Wbar[e] - muij[t];
+      for (int sp = 0; sp < nsplit; ++sp) v += Rpart[(int64_t)sp * R * nfe + t];
+    }
+    tile[rr][tx] = v;
+  }
+  __syncthreads();
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int c = c0 + cc;
+    const int64_t p = p0 + tx;
+    if (c < mpad && p < fslots) {
+      const float x = tile[tx][cc];
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      const float rem = x - __bfloat162float(h);
+      const __nv_bfloat16 m = __float2bfloat16_rn(rem);
+      const __nv_bfloat16 l = __float2bfloat16_rn(rem - __bfloat162float(m));
+      const int64_t o = ((int64_t)i * mpad + c) * fslots + p;
+      r1[o] = h;
+      r2[o] = m;
+      r3[o] = l;
+    }
+  }
+}
+
+// ---- one block's Q (s x s, float64) into the three split arrays at row qrow
+__global__ void k_split3_q(const double* __restrict__ Q, int s, int64_t ldq, int64_t qrow,
+                           __nv_bfloat16* __restrict__ q1, __nv_bfloat16* __restrict__ q2,
+                           __nv_bfloat16* __restrict__ q3) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)s * s) return;
+  const int64_t r = t / s, c = t % s;
+  const double x = Q[t];
+  const __nv_bfloat16 h = __double2bfloat16(x);
+  const double rem = x - (double)__bfloat162float(h);
+  const __nv_bfloat16 m = __double2bfloat16(rem);
+  const __nv_bfloat16 l = __double2bfloat16(rem - (double)__bfloat162float(m));
+  const int64_t o = (qrow + r) * ldq + c;
+  q1[o] = h;
+  q2[o] = m;
+  q3[o] = l;
+}
+
+}  // namespace
+
+cudaError_t launch_split3_q(const double* Q, int s, int64_t ldq, int64_t qrow, __nv_bfloat16* q1,
+                            __nv_bfloat16* q2, __nv_bfloat16* q3, cudaStream_t st) {
+  const int64_t n = (int64_t)s * s;
+  if (n <= 0) return cudaSuccess;
+  k_split3_q<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(Q, s, ldq, qrow, q1, q2, q3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_split3T(const float* Wbar, const float* muij, const float* Rpart, int nsplit, int R,
+                               int64_t fslots, int mpad, const int32_t* feat_ok, __nv_bfloat16* r1,
+                               __nv_bfloat16* r2, __nv_bfloat16* r3, cudaStream_t st) {
+  dim3 grid((unsigned)ceil_div(fslots, 32), (unsigned)ceil_div(mpad, 32), (unsigned)R);
+  k_rhs_split3T<<<grid, 256, 0, st>>>(Wbar, muij, Rpart, nsplit, R, fslots, mpad, feat_ok, r1, r2, r3);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_qgemm(const QgemmView& v) {
+  if (v.nblocks <= 0) return cudaSuccess;
+  if (v.mpad > 256 || v.mpad % 16) return cudaErrorInvalidValue;
+  QArgs a;
+  memset(&a, 0, sizeof(a));
+  cudaError_t e;
+  if ((e = tc_make_map_bf16(&a.tQ1, v.Q1, v.ldq, v.q_rows, v.ldq, 128, QKC)) != cudaSuccess) return e;
+  if ((e = tc_make_map_bf16(&a.tQ2, v.Q2, v.ldq, v.q_rows, v.ldq, 128, QKC)) != cudaSuccess) return e;
+  if ((e = tc_make_map_bf16(&a.tQ3, v.Q3, v.ldq, v.q_rows, v.ldq, 128, QKC)) != cudaSuccess) return e;
+  if ((e = tc_make_map_bf16(&a.tR1, v.R1, v.r_cols, v.r_rows, v.r_cols, v.mpad, QKC)) != cudaSuccess) return e;
+  if ((e = tc_make_map_bf16(&a.tR2, v.R2, v.r_cols, v.r_rows, v.r_cols, v.mpad, QKC)) != cudaSuccess) return e;
+  if ((e = tc_make_map_bf16(&a.tR3, v.R3, v.r_cols, v.r_rows, v.r_cols, v.mpad, QKC)) != cudaSuccess) return e;
+  a.mpad = v.mpad;
+  a.stage_bytes = 3 * QATILE + 3 * (uint32_t)v.mpad * QKC * 2;
+  const size_t budget = 216 * 1024;
+  a.ns = (int)std::min<size_t>(QMAXS, budget / a.stage_bytes);
+  a.tmem_cols = v.mpad <= 32 ? 32 : v.mpad <= 64 ? 64 : v.mpad <= 128 ? 128 : 256;
+  a.tab = v.tab;
+  a.nblocks = v.nblocks;
+  a.out = v.out;
+  a.wthi = v.WThi;
+  a.wtlo = v.WTlo;
+  a.fslots = v.fslots;
+  a.err = tc_error_ptr();
+  if (!a.err) return cudaErrorMemoryAllocation;
+  a.timeout_cycles = 4000000000LL;
+  const size_t smem = 1024 + (size_t)a.ns * a.stage_bytes + 256;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_qgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 + 216 * 1024 + 256);
+  });
+  if (attr != cudaSuccess) return attr;
+  dim3 grid((unsigned)ceil_div(v.max_s, 128), (unsigned)v.nblocks);
+  k_qgemm<<<grid, QNT, smem, v.st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace rff

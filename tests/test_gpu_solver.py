@@ -68,6 +68,10 @@ GRIDS = [
     ("hinge", "l2", 500, 7, 1, 200, 1, 2, 25, 1e-3, 0.5, 2.0),
     ("logistic", "l2", 600, 8, 1, 256, 2, 1, 25, 1e-3, 1.0, 2.5),
     ("multinomial", "l2", 700, 10, 4, 320, 2, 2, 25, 1e-3, 1.0, 3.0),
+    # wide outputs: unequal column blocks (301 + 300 features, three 128-row tiles with a
+    # ragged last one) and the widest output block the tensor-core passes take (m_pad = 256)
+    ("squared", "l2", 900, 12, 150, 601, 2, 2, 20, 1e-3, 1.0, 3.0),
+    ("squared", "l1", 500, 8, 250, 384, 1, 2, 15, 1e-3, 1.0, 2.0),
 ]
 
 
