@@ -11,7 +11,7 @@ dual updates.  Set-up (Philox draw, Gram matrices, FP64 Cholesky, inverses) is
 done before the timed region.  Every input of the timed region (X split,
 V_ij, W'_ij, the factors) is larger than the 129 MB L2, so no flush is needed.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split_bf16|fp32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split_bf16|fp32|cached_z]
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
 
 One JSON line on rank 0.  With N > 1 (torchrun), each rank solves its own
@@ -121,7 +121,18 @@ def flops_per_iter(w, prec):
     useful = 2 * (2 * n * d * D) + 2 * (2 * n * D * m) + R * C * 2 * s * s * m
     pass_tc = 3 * 2 * n * dpad * D + 3 * 2 * n * D * mpad       # one pass, executed on tensor cores
     pass_simt = 2 * n * dpad * D + 2 * n * D * mpad              # one pass, FP32 FMA
-    return useful, (pass_tc if prec == "split_bf16" else pass_simt)
+    pass_cached = 3 * 2 * n * D * mpad                           # one streamed pass (Z stored)
+    return useful, {"split_bf16": pass_tc, "fp32": pass_simt, "cached_z": pass_cached}[prec]
+
+
+def bytes_per_cached_pass(w):
+    """Algorithmic HBM bytes of one streamed pass of the cached-Z precision: Z (or Z^T)
+    as a hi/lo BF16 pair (4 n D), the n x m_pad chained operand or result of all C
+    column blocks (4 C n m_pad), and the D x m_pad operand or result of all R row
+    blocks (4 R D m_pad)."""
+    n, D, m, R, C = w["n"], w["D"], w["m"], w["R"], w["C"]
+    mpad = -(-m // 16) * 16
+    return 4 * n * D + 4 * C * n * mpad + 4 * R * D * mpad
 
 
 def run_ours(args, rank, world):
@@ -186,6 +197,13 @@ def run_ours(args, rank, world):
     if args.prec == "split_bf16":
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sus, "unit": "TFLOP/s",
                 "frac": achieved / bf16_sus, "traffic": None, "kernel": ph[3:], "peak_source": src + " sustained bf16"}
+    elif args.prec == "cached_z":
+        # the streamed pass reads Z once: HBM-bound (the tensor work, 3 x 2 n D m_pad, would take
+        # slightly less time at the sustained BF16 peak)
+        gbs = bytes_per_cached_pass(w) / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                "kernel": ph[3:], "peak_source": src + " copy bandwidth", "tensor_tflops": achieved,
+                "tensor_frac": achieved / bf16_sus}
     else:
         # FP32 SIMT: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (max boost)
         alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -198,7 +216,7 @@ def run_ours(args, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3" if args.prec == "split_bf16" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16x3", "data": "synthetic",
         "config": {"workload": w["name"], "n": w["n"], "d": w["d"], "m": w["m"], "D": w["D"],
                    "grid": "%dx%d" % (w["R"], w["C"]), "sigma": w["sigma"], "loss": w["loss"], "reg": w["reg"],
                    "lambda": w["lam"], "rho": w["rho"], "prec": args.prec, "parallelism": "replicas",
@@ -250,19 +268,158 @@ def run_reference(args, rank, world):
             "e2e": {"value": cb["value"], "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ----------------------------------------------------------------- sweep and serving workloads
+SWEEP = dict(name="sweep-8sigma-x-8lambda-logistic-d128", sigmas=[1, 2, 4, 8, 16, 32, 64, 128],
+             lambdas=[1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9], Ds=[1024, 2048, 4096, 8192], d=128,
+             n_lo=10_000, n_hi=400_000, seed=7)
+
+
+def run_sweep(args):
+    """(sigma, lambda) sweep: 64 binary-logistic + l2 solves; per sigma one data set (n log-uniform in
+    [10k, 400k], d = 128), one D (cycled over 1k..8k), one handle whose 8 columns are the 8 lambdas
+    (one factor per sigma); the 8 handles run side by side (rff_sweep_run, CUDA-graph iterations)."""
+    import numpy as np
+    import torch
+
+    import paper_1409_0940_gb300 as rff
+    import synth
+    w = SWEEP
+    rng = np.random.default_rng(w["seed"])
+    ns = np.exp(rng.uniform(np.log(w["n_lo"]), np.log(w["n_hi"]), len(w["sigmas"]))).astype(int)
+    solvers, groups = [], []
+    for k, sigma in enumerate(w["sigmas"]):
+        n, D = int(ns[k]), w["Ds"][k % len(w["Ds"])]
+        X, y = synth.binary(n=n, d=w["d"], seed=100 + k)
+        Y = np.ascontiguousarray(np.repeat(y, len(w["lambdas"]), axis=1))
+        R, C = -(-n // 50_000), D // 1024
+        s = rff.Solver(prec=args.prec, loss="logistic", reg="l2", lam=w["lambdas"][0], sigma=float(sigma), rho=1.0,
+                       D=D, R=R, C=C, seed=k, m=len(w["lambdas"]))
+        s.set_lambdas(w["lambdas"])
+        s.set_data(X, Y)
+        solvers.append(s)
+        groups.append({"sigma": sigma, "n": n, "D": D, "grid": "%dx%d" % (R, C)})
+    rff.rff_sweep_run([s.h for s in solvers], args.warmup)     # set-up (factors) + warm-up
+    torch.cuda.synchronize()
+    with Clocks(torch.cuda.current_device()) as clk:
+        t0 = time.perf_counter()
+        rff.rff_sweep_run([s.h for s in solvers], args.steps)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+    tuned = [s.profile() for s in solvers]
+    for s, g, pr in zip(solvers, groups, tuned):
+        g["tc_kchunk"] = pr["tc_kchunk"]
+        s.close()
+    nsolve = len(w["sigmas"]) * len(w["lambdas"])
+    return {"metric": "sweep solve-iterations/s", "value": nsolve * args.steps / sec, "unit": "solve-iter/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3" if args.prec == "split_bf16" else "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "solves": nsolve, "groups": groups, "prec": args.prec,
+                       "timing": "host wall clock around rff_sweep_run (all streams drained)"},
+            "clocks": clk.summary()}
+
+
+def run_serve(args):
+    """Serving: Poisson arrivals of solve requests (n log-uniform 5k..200k, d in 32..784,
+    D in 1k..8k, loss in {squared, hinge, logistic}, reg in {l2, l1}) and scoring batches of
+    1..4096 queries against resident models; p50/p99 latency per request kind."""
+    import numpy as np
+
+    import paper_1409_0940_gb300 as rff
+    import synth
+    rng = np.random.default_rng(11)
+    n_solve, n_score, rate_solve, rate_score = 24, 400, 2.0, 40.0
+    events = [(t, "solve") for t in np.cumsum(rng.exponential(1 / rate_solve, n_solve))]
+    events += [(t, "score") for t in 1.0 + np.cumsum(rng.exponential(1 / rate_score, n_score))]
+    events.sort()
+    # request contents are drawn before the clock starts
+    losses = ["squared", "hinge", "logistic"]
+    solves, k = [], 0
+    for t, kind in events:
+        if kind != "solve":
+            continue
+        n = int(np.exp(rng.uniform(np.log(5_000), np.log(200_000))))
+        d = int(rng.choice([32, 64, 128, 256, 440, 784]))
+        D = int(rng.choice([1024, 2048, 4096, 8192]))
+        loss, reg = losses[k % 3], ["l2", "l1"][(k // 3) % 2]
+        if loss == "squared":
+            X, Y = synth.ridge(n=n, d=d, seed=k)
+        else:
+            X, Y = synth.binary(n=n, d=d, seed=k)
+        pr = rff.make_params(loss=loss, reg=reg, lam=1e-4, sigma=float(np.sqrt(d)), D=D, R=-(-n // 50_000),
+                             C=max(1, D // 2048), seed=k, m=1, prec=args.prec)
+        solves.append((pr, X, Y, d))
+        k += 1
+    srv = rff.rff_server_create(0, 8)
+    models, kinds, pending, scores = [], {}, set(), []
+    solved = set()          # models whose solve has completed (scores against them hit a resident model)
+    t_start = time.perf_counter()
+    done = []
+    ev, si = 0, 0
+    while ev < len(events) or pending:
+        now = time.perf_counter() - t_start
+        while ev < len(events) and events[ev][0] <= now:
+            kind = events[ev][1]
+            if kind == "solve":
+                pr, X, Y, d = solves[si]
+                si += 1
+                rid = rff.rff_server_submit_solve(srv, pr, X, Y, 30)
+                models.append((rid, d))
+                kinds[rid] = "solve"
+                pending.add(rid)
+            elif models:
+                mid, d = models[int(rng.integers(len(models)))]
+                q = int(np.exp(rng.uniform(0, np.log(4096))))
+                Xq = rng.standard_normal((q, d)).astype(np.float32)
+                out = np.empty((q, 1), dtype=np.float32)
+                scores.append(out)
+                rid = rff.rff_server_submit_score(srv, mid, Xq, out)
+                kinds[rid] = "score" if mid in solved else "score_waiting"
+                pending.add(rid)
+            ev += 1
+        for c in rff.rff_server_poll(srv, 256, 5):
+            pending.discard(c["id"])
+            done.append(c)
+            if kinds[c["id"]] == "solve" and c["status"] == 0:
+                solved.add(c["id"])
+    wall = time.perf_counter() - t_start
+    rff.rff_server_destroy(srv)
+    out = {"metric": "serve p50/p99 ms", "n_gpus": 1, "data": "synthetic", "higher_is_better": False,
+           "config": {"workload": "serve-poisson", "solve_requests": n_solve, "score_requests": n_score,
+                      "rate_solve_per_s": rate_solve, "rate_score_per_s": rate_score, "max_active": 8,
+                      "iterations_per_solve": 30, "prec": args.prec}, "wall_s": wall}
+    for kind in ("solve", "score", "score_waiting"):
+        lat = np.array([c["latency_ms"] for c in done if kinds[c["id"]] == kind and c["status"] == 0])
+        que = np.array([c["queue_ms"] for c in done if kinds[c["id"]] == kind and c["status"] == 0])
+        out[kind] = {"count": int(lat.size), "failed": int(sum(1 for c in done if kinds[c["id"]] == kind
+                                                              and c["status"] != 0)),
+                     "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+                     "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+                     "queue_p50_ms": float(np.percentile(que, 50)) if que.size else None}
+    out["value"] = out["score"]["p99_ms"]
+    out["unit"] = "ms (p99 of scores against resident models)"
+    out["throughput_req_per_s"] = len(done) / wall
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="split_bf16", choices=["split_bf16", "fp32"])
+    ap.add_argument("--prec", default="split_bf16", choices=["split_bf16", "fp32", "cached_z"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--n", type=int, default=0, help="rows of a reduced workload (profiling runs)")
+    ap.add_argument("--workload", default="multiclass", choices=["multiclass", "sweep", "serve"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.workload != "multiclass":
+        line = run_sweep(args) if args.workload == "sweep" else run_serve(args)
+        print(json.dumps(line), flush=True)
+        return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
         if rank == 0:

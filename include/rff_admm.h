@@ -67,9 +67,16 @@ typedef enum {
 /* How Z_ij is regenerated and applied. */
 typedef enum {
   RFF_PREC_FP32 = 0,      /* X.G, cos and both chained products in FP32 on the SIMT pipes  */
-  RFF_PREC_SPLIT_BF16 = 1 /* X.G as three BF16 tensor-core products (hi.hi + hi.lo + lo.hi),
+  RFF_PREC_SPLIT_BF16 = 1, /* X.G as three BF16 tensor-core products (hi.hi + hi.lo + lo.hi),
                              FP32 accumulate in TMEM, FP32 cos, chained products again as
                              three BF16 products of the hi/lo split of both operands       */
+  RFF_PREC_CACHED_Z = 2   /* Z materialised once (set-up, by the split-BF16 regeneration)
+                             and kept in device memory as a hi/lo BF16 pair, with a
+                             transposed copy: n_slots x D_slots x 8 bytes.  Each iteration
+                             streams it through the same three-product chained GEMMs
+                             instead of regenerating it; the comparison mode of the paper's
+                             memory trade-off (Sec. 3: Z is not stored), for data sets
+                             whose Z fits in device memory                                 */
 } rff_precision;
 
 /* Scaling of rho (the paper never fixes it).  RFF_RHO_SUM: rho is the penalty of the

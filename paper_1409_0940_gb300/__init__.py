@@ -20,7 +20,7 @@ _STATUS = {0: "RFF_OK", 1: "RFF_EINVAL", 2: "RFF_ENOMEM", 3: "RFF_ECUDA", 4: "RF
            5: "RFF_ENOTREADY", 6: "RFF_ENUMERIC"}
 LOSSES = {"squared": 0, "hinge": 1, "logistic": 2, "multinomial": 3}
 REGS = {"l2": 0, "l1": 1}
-PRECS = {"fp32": 0, "split_bf16": 1}
+PRECS = {"fp32": 0, "split_bf16": 1, "cached_z": 2}
 RHO_SCALES = {"sum": 0, "mean": 1}
 
 

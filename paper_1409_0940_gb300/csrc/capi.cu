@@ -60,7 +60,13 @@ struct rff_admm_s {
   __nv_bfloat16 *Q1 = nullptr, *Q2 = nullptr, *Q3 = nullptr, *rT1 = nullptr, *rT2 = nullptr, *rT3 = nullptr;
   int64_t ldq = 0, q_rows = 0;
   std::vector<int64_t> qrow;
-  int32_t* qtab = nullptr;    // per block: Q row, s_j, i*mpad, slot_j, i*fslots + slot_j
+  SgJob* qjobs = nullptr;     // projection GEMM jobs (one per 128-row tile of every Q_ij)
+  int nqjobs = 0;
+  // cached-Z precision: Z (n_slots x D_slots) and Z^T as hi/lo pairs, and the jobs of
+  // the two streamed passes
+  __nv_bfloat16 *Zhi = nullptr, *Zlo = nullptr, *ZThi = nullptr, *ZTlo = nullptr;
+  SgJob *p1jobs = nullptr, *p2jobs = nullptr;
+  int np1 = 0, np2 = 0, nsplit_cz = 1;
   std::vector<double> lam_col;  // lambda of each output column (empty: params.lambda for all)
   float* lam_dev = nullptr;     // lambda_c / lambda per column (m_pad), or null
   GemmDesc* gdesc = nullptr;  // R*C
@@ -102,7 +108,9 @@ struct rff_admm_s {
     err = std::string(what) + ": " + cudaGetErrorString(e);
     return RFF_ECUDA;
   }
-  bool split_path() const { return p.prec == RFF_PREC_SPLIT_BF16; }
+  // the split path: tensor-core kernels and BF16 operand copies (cached-Z uses them too)
+  bool split_path() const { return p.prec == RFF_PREC_SPLIT_BF16 || p.prec == RFF_PREC_CACHED_Z; }
+  bool cached_z() const { return p.prec == RFF_PREC_CACHED_Z; }
 };
 
 namespace rff {
@@ -121,7 +129,7 @@ rff_status check_params(const rff_admm_params* p, std::string& why) {
   if (!p) { why = "params is NULL"; return RFF_EINVAL; }
   if (p->loss < 0 || p->loss > 3) { why = "unknown loss"; return RFF_EINVAL; }
   if (p->reg < 0 || p->reg > 1) { why = "unknown regulariser"; return RFF_EINVAL; }
-  if (p->prec < 0 || p->prec > 1) { why = "unknown precision"; return RFF_EINVAL; }
+  if (p->prec < 0 || p->prec > 2) { why = "unknown precision"; return RFF_EINVAL; }
   if (p->rho_scale < 0 || p->rho_scale > 1) { why = "unknown rho scale"; return RFF_EINVAL; }
   if (!(p->lambda > 0) || !std::isfinite(p->lambda)) { why = "lambda must be > 0"; return RFF_EINVAL; }
   if (!(p->sigma > 0) || !std::isfinite(p->sigma)) { why = "sigma must be > 0"; return RFF_EINVAL; }
@@ -130,7 +138,7 @@ rff_status check_params(const rff_admm_params* p, std::string& why) {
   if (p->R < 1 || p->C < 1 || p->C > p->D) { why = "bad block grid"; return RFF_EINVAL; }
   if (p->m < 1 || p->m > 256) { why = "m must be in [1, 256]"; return RFF_EINVAL; }
   if (p->newton_iters < 0 || p->newton_iters > 100) { why = "newton_iters out of range"; return RFF_EINVAL; }
-  if (p->prec == RFF_PREC_SPLIT_BF16 && p->C > 64) { why = "the split-BF16 path supports C <= 64"; return RFF_EINVAL; }
+  if (p->prec != RFF_PREC_FP32 && p->C > 64) { why = "the split-BF16 and cached-Z paths support C <= 64"; return RFF_EINVAL; }
   return RFF_OK;
 }
 
@@ -191,7 +199,12 @@ size_t working_set_bytes(const rff_admm_s& s) {
   t += (size_t)s.R * s.fslots * s.mpad * f * (3 + s.nsplit_max);    // What, muij, muij_old, Rpart
   if (s.split_path()) {
     t += (size_t)s.R * s.fslots * s.mpad * b2 * (2 + 3) + (size_t)s.fslots * s.mpad * b2 * 2;   // WT, rT, WbT
-    t += (size_t)s.q_rows * s.ldq * b2 * 3 + (size_t)s.R * s.C * 5 * 4;                        // Q splits, table
+    t += (size_t)s.q_rows * s.ldq * b2 * 3 + (size_t)s.R * s.C * (s.ldq / 128 + 1) * sizeof(SgJob);   // Q splits
+    if (s.cached_z()) {
+      t += (size_t)s.nslots * s.fslots * b2 * 4;                                                // Z, Z^T hi/lo
+      t += (size_t)(s.nslots / 128 * s.C + s.fslots / 128 * s.R * s.nsplit_cz) * sizeof(SgJob);
+      t += (size_t)s.R * s.fslots * s.mpad * f * (s.nsplit_cz > s.nsplit_max ? s.nsplit_cz - s.nsplit_max : 0);
+    }
   } else {
     t += (size_t)s.R * s.fslots * s.mpad * f;                                                   // rhs
     size_t fac = 0;
@@ -272,6 +285,15 @@ void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
     const int64_t cap = std::min<int64_t>(ceil_div(min_rows, tile), 64);
     s.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
     s.nsplit_max = s.nsplit;
+    // cached-Z pass 1 (one CTA per 128 features x row range, two CTAs per SM): about
+    // twelve waves of jobs, every split at least eight 128-row tiles of every row block
+    s.nsplit_cz = 1;
+    if (s.cached_z()) {
+      const int64_t ft = s.fslots / 128;
+      const int64_t nrt = ceil_div(min_rows, 128);
+      const int64_t want_cz = ceil_div(24 * (int64_t)nsm, ft * s.R);
+      s.nsplit_cz = (int)std::max<int64_t>(1, std::min<int64_t>({want_cz, nrt / 8, (int64_t)64}));
+    }
   }
 
 }
@@ -331,7 +353,7 @@ rff_status rff_admm_get_profile(rff_admm_t h, rff_admm_profile* out) {
   *out = h->prof;
   out->launches = h->launches;
   out->tc_kchunk = h->split_path() ? (h->tc_kc ? h->tc_kc : 64) : 0;
-  out->nsplit = h->nsplit;
+  out->nsplit = h->cached_z() ? h->nsplit_cz : h->nsplit;
   return RFF_OK;
 }
 
@@ -412,7 +434,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   AL(s.What, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.muij, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.muij_old, (int64_t)s.R * s.fslots * s.mpad);
-  AL(s.Rpart, (int64_t)s.nsplit_max * s.R * s.fslots * s.mpad);
+  AL(s.Rpart, (int64_t)std::max(s.nsplit_max, s.nsplit_cz) * s.R * s.fslots * s.mpad);
   if (s.split_path()) {
     AL(s.Q1, s.q_rows * s.ldq);
     AL(s.Q2, s.q_rows * s.ldq);
@@ -420,7 +442,22 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
     AL(s.rT1, (int64_t)s.R * s.mpad * s.fslots);
     AL(s.rT2, (int64_t)s.R * s.mpad * s.fslots);
     AL(s.rT3, (int64_t)s.R * s.mpad * s.fslots);
-    AL(s.qtab, (int64_t)s.R * s.C * 5);
+    {
+      int64_t nq = 0;
+      for (int64_t b = 0; b < (int64_t)s.R * s.C; ++b) nq += ceil_div(s.col_size[b % s.C], 128);
+      s.nqjobs = (int)nq;
+      AL(s.qjobs, nq);
+    }
+    if (s.cached_z()) {
+      AL(s.Zhi, s.nslots * s.fslots);
+      AL(s.Zlo, s.nslots * s.fslots);
+      AL(s.ZThi, s.nslots * s.fslots);
+      AL(s.ZTlo, s.nslots * s.fslots);
+      s.np2 = (int)(s.nslots / 128 * s.C);
+      s.np1 = (int)(s.fslots / 128 * s.R * s.nsplit_cz);
+      AL(s.p1jobs, s.np1);
+      AL(s.p2jobs, s.np2);
+    }
   } else {
     AL(s.rhs, (int64_t)s.R * s.fslots * s.mpad);
     AL(s.Q32, s.foff.back());
@@ -495,7 +532,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   for (float* b : {s.W, s.Wbar, s.mu}) CK(cudaMemsetAsync(b, 0, colb, s.st));
   for (float* b : {s.What, s.muij}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
   if (s.rhs) CK(cudaMemsetAsync(s.rhs, 0, colb * s.R, s.st));
-  CK(cudaMemsetAsync(s.Rpart, 0, colb * s.R * s.nsplit_max, s.st));
+  CK(cudaMemsetAsync(s.Rpart, 0, colb * s.R * std::max(s.nsplit_max, s.nsplit_cz), s.st));
   if (s.split_path()) {
     CK(cudaMemsetAsync(s.VThi, 0, rowb / 2 * s.C, s.st));
     CK(cudaMemsetAsync(s.VTlo, 0, rowb / 2 * s.C, s.st));
@@ -523,7 +560,7 @@ namespace {
 // iteration recomputes.
 rff_status autotune(rff_admm_t h) {
   auto& s = *h;
-  if (!s.split_path()) return RFF_OK;
+  if (!s.split_path() || s.cached_z()) return RFF_OK;
   std::vector<int> splits{s.nsplit};
   if (s.nsplit_max != s.nsplit) splits.push_back(s.nsplit_max);
   cudaEvent_t e0, e1;
@@ -556,6 +593,64 @@ rff_status autotune(rff_admm_t h) {
   s.tc_kc = best_kc;
   s.nsplit = best_ns;
   if (tc_error_word() != 0) return h->fail(RFF_ETIMEOUT, "a tensor-core pass gave up waiting during tuning");
+  return RFF_OK;
+}
+
+// Cached-Z precision: Z (all row slots x all feature slots, padding included) and its
+// transpose as hi/lo BF16 pairs, computed by the split-BF16 regeneration kernel in row
+// chunks staged in FP32, and the job tables of the two streamed passes.
+rff_status materialise_z(rff_admm_t h) {
+  auto& s = *h;
+  const int64_t chunk = std::max<int64_t>(128, ((int64_t)(256u << 20) / (s.fslots * 4)) / 128 * 128);
+  rff_status rs = ensure_scratch(h, (size_t)chunk * s.fslots * 4);
+  if (rs != RFF_OK) return rs;
+  float* zc = static_cast<float*>(s.scratch.p);
+  for (int64_t r0 = 0; r0 < s.nslots; r0 += chunk) {
+    const int64_t nr = std::min(chunk, s.nslots - r0);
+    CK(tc_write_z(tc_view(s), r0, nr, 0, s.fslots, zc, s.fslots));
+    CK(launch_split_bf16(zc, nr * s.fslots, s.Zhi + r0 * s.fslots, s.Zlo + r0 * s.fslots, s.st));
+    CK(launch_transpose_split(zc, nr, (int)s.fslots, 1, 0, s.ZThi + r0, s.ZTlo + r0, s.nslots, 0, s.st));
+  }
+  // pass 2: one job per (128-row tile, column block j), K = the features of block j
+  std::vector<SgJob> j2, j1;
+  for (int64_t rt = 0; rt < s.nslots / 128; ++rt) {
+    int i = 0;
+    while (i + 1 < s.R && s.row_slot[i + 1] <= rt * 128) ++i;
+    for (int j = 0; j < s.C; ++j) {
+      SgJob jb{};
+      jb.a_row = (int32_t)(rt * 128);
+      jb.a_k0 = (int32_t)s.col_slot[j];
+      jb.b_row = (int32_t)(i * s.mpad);
+      jb.b_k0 = (int32_t)s.col_slot[j];
+      jb.nk = (int32_t)ceil_div(s.col_size[j], 32);
+      jb.out = ((int64_t)j * s.nslots + rt * 128) * s.mpad;
+      jb.tout = -1;
+      j2.push_back(jb);
+    }
+  }
+  // pass 1: one job per (128-feature tile, row block i, row split), K = the split's rows
+  for (int sp = 0; sp < s.nsplit_cz; ++sp)
+    for (int i = 0; i < s.R; ++i) {
+      const int64_t nrt = ceil_div(s.row_size[i], 128);
+      const int64_t t0 = sp * nrt / s.nsplit_cz, t1 = (sp + 1) * nrt / s.nsplit_cz;
+      for (int64_t ft = 0; ft < s.fslots / 128; ++ft) {
+        int j = 0;
+        while (j + 1 < s.C && s.col_slot[j + 1] <= ft * 128) ++j;
+        SgJob jb{};
+        jb.a_row = (int32_t)(ft * 128);
+        jb.a_k0 = (int32_t)(s.row_slot[i] + t0 * 128);
+        jb.b_row = (int32_t)(j * s.mpad);
+        jb.b_k0 = jb.a_k0;
+        jb.nk = (int32_t)((t1 - t0) * 4);
+        jb.out = (((int64_t)sp * s.R + i) * s.fslots + ft * 128) * s.mpad;
+        jb.tout = -1;
+        j1.push_back(jb);
+      }
+    }
+  if ((int)j1.size() != s.np1 || (int)j2.size() != s.np2) return h->fail(RFF_ECUDA, "internal: cached-Z job count");
+  CK(cudaMemcpyAsync(s.p1jobs, j1.data(), j1.size() * sizeof(SgJob), cudaMemcpyHostToDevice, s.st));
+  CK(cudaMemcpyAsync(s.p2jobs, j2.data(), j2.size() * sizeof(SgJob), cudaMemcpyHostToDevice, s.st));
+  CK(cudaStreamSynchronize(s.st));
   return RFF_OK;
 }
 
@@ -639,24 +734,39 @@ rff_status setup_factors(rff_admm_t h) {
   }
   // iteration GEMM descriptors: x = Q rhs
   std::vector<GemmDesc> g(nblocks);
-  std::vector<int32_t> qt((size_t)nblocks * 5);
+  std::vector<SgJob> qj;
   for (int i = 0; i < s.R; ++i)
     for (int j = 0; j < s.C; ++j) {
       const int64_t blk = (int64_t)i * s.C + j, sj = s.col_size[j];
       const int64_t off = ((int64_t)i * s.fslots + s.col_slot[j]) * s.mpad;
       if (s.split_path()) {
-        const int64_t v[5] = {s.qrow[blk], sj, (int64_t)i * s.mpad, s.col_slot[j], (int64_t)i * s.fslots + s.col_slot[j]};
-        for (int t = 0; t < 5; ++t) qt[(size_t)blk * 5 + t] = (int32_t)v[t];
+        // one job per 128-row tile of Q_ij: rows of W'_ij, all m_pad columns, K = s_j
+        for (int64_t m0 = 0; m0 < sj; m0 += 128) {
+          SgJob jb{};
+          jb.a_row = (int32_t)(s.qrow[blk] + m0);
+          jb.a_k0 = 0;
+          jb.b_row = (int32_t)(i * s.mpad);
+          jb.b_k0 = (int32_t)s.col_slot[j];
+          jb.nk = (int32_t)ceil_div(sj, 32);
+          jb.out = ((int64_t)i * s.fslots + s.col_slot[j] + m0) * s.mpad;
+          jb.tout = (int64_t)i * s.mpad * s.fslots + s.col_slot[j] + m0;
+          qj.push_back(jb);
+        }
       } else {
         float* Qb = s.Q32 + s.foff[blk];
         g[blk] = GemmDesc{Qb, s.rhs + off, nullptr, s.What + off, (int)sj, (int)s.mpad, (int)sj, sj, s.mpad, 0, s.mpad};
       }
     }
-  if (s.split_path())
-    CK(cudaMemcpyAsync(s.qtab, qt.data(), qt.size() * 4, cudaMemcpyHostToDevice, s.st));
-  else
+  if (s.split_path()) {
+    if ((int)qj.size() != s.nqjobs) return h->fail(RFF_ECUDA, "internal: projection job count");
+    CK(cudaMemcpyAsync(s.qjobs, qj.data(), qj.size() * sizeof(SgJob), cudaMemcpyHostToDevice, s.st));
+  } else
     CK(cudaMemcpyAsync(s.gdesc, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, s.st));
   CK(cudaStreamSynchronize(s.st));
+  if (s.cached_z()) {
+    rff_status zr = materialise_z(h);
+    if (zr != RFF_OK) return zr;
+  }
   // the set-up scratch (FP64 Gram and inverse batches) is released
   CK(cudaFree(s.scratch.p));
   s.scratch = DevBuf{};
@@ -687,28 +797,73 @@ PassArgs base_pass_args(const rff_admm_s& s) {
   return a;
 }
 
-QgemmView qgemm_view(const rff_admm_s& s) {
-  QgemmView v{};
-  v.Q1 = s.Q1;
-  v.Q2 = s.Q2;
-  v.Q3 = s.Q3;
-  v.q_rows = s.q_rows;
-  v.ldq = s.ldq;
-  v.R1 = s.rT1;
-  v.R2 = s.rT2;
-  v.R3 = s.rT3;
-  v.r_rows = (int64_t)s.R * s.mpad;
-  v.r_cols = s.fslots;
-  v.tab = s.qtab;
-  v.nblocks = s.R * s.C;
-  int64_t smax = 0;
-  for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
-  v.max_s = (int)smax;
+// W'_ij = Q_ij rhs_ij for all blocks: Q and rhs split three ways (six products);
+// W' is written row-major and as the transposed hi/lo pair that pass 2 reads
+SgView qgemm_view(const rff_admm_s& s) {
+  SgView v{};
+  v.A[0] = s.Q1;
+  v.A[1] = s.Q2;
+  v.A[2] = s.Q3;
+  v.a_rows = s.q_rows;
+  v.a_cols = s.ldq;
+  v.B[0] = s.rT1;
+  v.B[1] = s.rT2;
+  v.B[2] = s.rT3;
+  v.b_rows = (int64_t)s.R * s.mpad;
+  v.b_cols = s.fslots;
+  v.na = v.nb = 3;
+  v.jobs = s.qjobs;
+  v.njobs = s.nqjobs;
   v.mpad = (int)s.mpad;
   v.out = s.What;
-  v.WThi = s.WThi;
-  v.WTlo = s.WTlo;
-  v.fslots = s.fslots;
+  v.thi = s.WThi;
+  v.tlo = s.WTlo;
+  v.tld = s.fslots;
+  v.st = s.st;
+  return v;
+}
+
+// cached-Z pass 1: R partials [split][i][feature slot][c] = sum over the split's rows of
+// block i of Z^T[f][r] V_ij[r][c]  (A = Z^T hi/lo, B = V^T hi/lo of block j)
+SgView cz_pass1_view(const rff_admm_s& s) {
+  SgView v{};
+  v.A[0] = s.ZThi;
+  v.A[1] = s.ZTlo;
+  v.a_rows = s.fslots;
+  v.a_cols = s.nslots;
+  v.B[0] = s.VThi;
+  v.B[1] = s.VTlo;
+  v.b_rows = (int64_t)s.C * s.mpad;
+  v.b_cols = s.nslots;
+  v.na = v.nb = 2;
+  v.jobs = s.p1jobs;
+  v.njobs = s.np1;
+  v.mpad = (int)s.mpad;
+  v.out = s.Rpart;
+  v.tld = -1;
+  v.smem_budget = 110 * 1024;   // two CTAs per SM: one's epilogue overlaps the other's stream
+  v.st = s.st;
+  return v;
+}
+
+// cached-Z pass 2: O'_ij[r][c] = sum over features of block j of Z[r][f] W'_ij[f][c]
+SgView cz_pass2_view(const rff_admm_s& s) {
+  SgView v{};
+  v.A[0] = s.Zhi;
+  v.A[1] = s.Zlo;
+  v.a_rows = s.nslots;
+  v.a_cols = s.fslots;
+  v.B[0] = s.WThi;
+  v.B[1] = s.WTlo;
+  v.b_rows = (int64_t)s.R * s.mpad;
+  v.b_cols = s.fslots;
+  v.na = v.nb = 2;
+  v.jobs = s.p2jobs;
+  v.njobs = s.np2;
+  v.mpad = (int)s.mpad;
+  v.out = s.Op;
+  v.tld = -1;
+  v.smem_budget = 110 * 1024;
   v.st = s.st;
   return v;
 }
@@ -733,7 +888,9 @@ rff_status iterate(rff_admm_t h, int k) {
   if ((r = mark(h, k, 1)) != RFF_OK) return r;
   // pass 1: R_ij = Z_ij^T V_ij,  V_ij = Obar_ij + nu_i
   PassArgs a = base_pass_args(s);
-  if (s.split_path()) {
+  if (s.cached_z()) {
+    CK(split_gemm(cz_pass1_view(s)));
+  } else if (s.split_path()) {
     CK(tc_pass1(tc_view(s), s.Rpart));
   } else {
     a.M = s.V32;
@@ -748,16 +905,18 @@ rff_status iterate(rff_admm_t h, int k) {
   // FP64 or compensated residual costs several times the solve on this part's FP64/FP32 pipes.)
   if (s.split_path()) {
     // six-product split-BF16 GEMM on the tensor cores; also writes W' transposed and split for pass 2
-    CK(launch_rhs_split3T(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, s.fslots, (int)s.mpad, s.feat_of_slot, s.rT1,
-                          s.rT2, s.rT3, s.st));
-    CK(tc_qgemm(qgemm_view(s)));
+    CK(launch_rhs_split3T(s.Wbar, s.muij, s.Rpart, s.cached_z() ? s.nsplit_cz : s.nsplit, s.R, s.fslots,
+                          (int)s.mpad, s.feat_of_slot, s.rT1, s.rT2, s.rT3, s.st));
+    CK(split_gemm(qgemm_view(s)));
   } else {
     CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st));
     CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st));
   }
   if ((r = mark(h, k, 3)) != RFF_OK) return r;
   // pass 2: O'_ij = Z_ij W'_ij (eq. (gpOij))
-  if (s.split_path()) {
+  if (s.cached_z()) {
+    CK(split_gemm(cz_pass2_view(s)));
+  } else if (s.split_path()) {
     CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1));
   } else {
     a.M = s.What;

@@ -1,16 +1,27 @@
-// Cached projection of the split path on tensor cores (eq. (gpWij) with the cached
-// inverse of eq. (cache)):  W'_ij = Q_ij (Wbar_j - mu'_ij + R_ij)  for all blocks.
+// Split-BF16 streaming GEMM on tensor cores, driven by a job table.
 //
-// Q_ij and the right-hand side are each split into three BF16 terms
-// (x = x1 + x2 + x3 + O(2^-24 |x|)); the six products whose exponents sum to at
-// most -16 (11, 12, 21, 13, 22, 31) accumulate in TMEM in FP32, which gives the
-// accuracy of an FP32 product.  One CTA computes 128 rows of one block's result
-// (all m_pad columns, one N = m_pad accumulator); a TMA ring of 32-element K
-// chunks (64-byte swizzle) feeds the six A and B tiles of each chunk.  Warp 0
-// issues the copies, one thread of warp 1 the MMAs, warps 2..5 write the result,
-// both row-major in FP32 (for the averaging step) and transposed as a hi/lo BF16
-// pair (the chain operand of pass 2).
-// Waits are bounded as in the regeneration kernel.
+// Every job multiplies one 128-row tile of operand A (rows a_row.., K from a_k0)
+// by the m_pad-row operand B (rows b_row.., K from b_k0) over nk chunks of 32:
+//
+//   acc (TMEM, 128 x m_pad fp32) = sum over the split products A_s . B_t^T
+//
+// with A = A1 + A2 (+ A3) and B = B1 + B2 (+ B3) split into BF16 terms.  Three
+// terms each (NA = NB = 3) take the six products whose exponents sum to at most
+// 2^-16 (11, 12, 21, 13, 22, 31): the accuracy of an FP32 product.  Two terms
+// each take 11, 12, 21 (hi.hi + hi.lo + lo.hi).  The accumulator is written
+// row-major to out + job.out (ld m_pad), and optionally transposed and split
+// into a hi/lo BF16 pair (column c of row r at thi + job.tout + c*tld + r).
+//
+// Users: the cached projection of eq. (gpWij) (A = Q_ij split three ways, B = the
+// right-hand side), and the two chained products of the cached-Z precision
+// (pass 1: A = Z^T, B = V^T; pass 2: A = Z, B = W'^T; eq. (gpWij), (gpOij)).
+//
+// A TMA ring of 32-element K chunks (64-byte swizzle) feeds the tiles of each
+// chunk.  Warp 0 issues the copies, one thread of warp 1 the MMAs, warps 2..5
+// write the result.  Waits are bounded as in the regeneration kernel: on a timeout
+// the CTA records an error code, waits (bounded) for its copies and products in
+// flight, frees TMEM and returns.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -31,14 +42,13 @@ constexpr int QNT = 192;
 constexpr int ERR_Q = 8;
 
 struct QArgs {
-  CUtensorMap tQ1, tQ2, tQ3, tR1, tR2, tR3;
+  CUtensorMap tA[3], tB[3];
   int mpad, ns;
   uint32_t stage_bytes, tmem_cols;
-  const int* tab;   // per block: qrow, s, ry, slot, orow
-  int nblocks;
-  float* out;                 // [R*fslots][mpad]
-  __nv_bfloat16 *wthi, *wtlo; // [R*mpad][fslots]
-  int64_t fslots;
+  const SgJob* jobs;
+  float* out;
+  __nv_bfloat16 *thi, *tlo;
+  int64_t tld;
   int* err;
   long long timeout_cycles;
 };
@@ -64,16 +74,18 @@ __device__ __forceinline__ bool qwait(uint32_t bar, uint32_t parity, QShared& sh
   }
 }
 
-__global__ void __launch_bounds__(QNT, 1) k_qgemm(const __grid_constant__ QArgs a) {
+// split-product order (A term, B term): exponents summing to at most 2^-16
+__host__ __device__ constexpr int prod_a(int p) { return p == 2 || p == 4 ? 1 : p == 5 ? 2 : 0; }
+__host__ __device__ constexpr int prod_b(int p) { return p == 1 || p == 4 ? 1 : p == 3 ? 2 : 0; }
+
+template <int NA, int NB>
+__global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArgs a) {
+  constexpr int NPROD = (NA == 3 && NB == 3) ? 6 : 3;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   QShared& sh = *reinterpret_cast<QShared*>(base + a.ns * a.stage_bytes);
-  const int b = blockIdx.y;
-  const int qrow = a.tab[5 * b], s = a.tab[5 * b + 1], ry = a.tab[5 * b + 2], slot = a.tab[5 * b + 3],
-            orow = a.tab[5 * b + 4];
-  const int m0 = blockIdx.x * 128;
-  if (m0 >= s) return;   // uniform across the CTA
-  const int nk = (s + QKC - 1) / QKC;
+  const SgJob job = a.jobs[blockIdx.x];
+  const int nk = job.nk;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const uint32_t bar_full = smem_u32(&sh.full[0]), bar_empty = smem_u32(&sh.empty[0]);
   const uint32_t bar_acc = smem_u32(&sh.acc_full), bar_done = smem_u32(&sh.mma_done);
@@ -109,12 +121,11 @@ __global__ void __launch_bounds__(QNT, 1) k_qgemm(const __grid_constant__ QArgs 
         const uint32_t fb = bar_full + 8 * st;
         mbar_expect_tx(fb, a.stage_bytes);
         const uint32_t dst = smem_u32(base + st * a.stage_bytes);
-        tma_load_2d(dst, &a.tQ1, kc * QKC, qrow + m0, fb);
-        tma_load_2d(dst + QATILE, &a.tQ2, kc * QKC, qrow + m0, fb);
-        tma_load_2d(dst + 2 * QATILE, &a.tQ3, kc * QKC, qrow + m0, fb);
-        tma_load_2d(dst + 3 * QATILE, &a.tR1, slot + kc * QKC, ry, fb);
-        tma_load_2d(dst + 3 * QATILE + mb, &a.tR2, slot + kc * QKC, ry, fb);
-        tma_load_2d(dst + 3 * QATILE + 2 * mb, &a.tR3, slot + kc * QKC, ry, fb);
+#pragma unroll
+        for (int s = 0; s < NA; ++s) tma_load_2d(dst + s * QATILE, &a.tA[s], job.a_k0 + kc * QKC, job.a_row, fb);
+#pragma unroll
+        for (int s = 0; s < NB; ++s)
+          tma_load_2d(dst + NA * QATILE + s * mb, &a.tB[s], job.b_k0 + kc * QKC, job.b_row, fb);
         ++issued;
       }
       // copies in flight finish before the CTA may exit (bounded)
@@ -129,7 +140,7 @@ __global__ void __launch_bounds__(QNT, 1) k_qgemm(const __grid_constant__ QArgs 
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(128, a.mpad);
       bool ok = true;
-      for (int kc = 0; kc < nk && ok; ++kc) {
+      for (int kc = 0; kc < nk; ++kc) {
         const int st = kc % a.ns;
         if (!qwait(bar_full + 8 * st, (kc / a.ns) & 1, sh, a)) {
           ok = false;
@@ -137,59 +148,53 @@ __global__ void __launch_bounds__(QNT, 1) k_qgemm(const __grid_constant__ QArgs 
         }
         fence_after();
         const uint32_t sa = smem_u32(base + st * a.stage_bytes);
+        const uint32_t sb = sa + NA * QATILE;
 #pragma unroll
         for (int kk = 0; kk < QKC / 16; ++kk) {
-          const uint64_t q1 = smem_desc(sa + kk * 32, 512, 4), q2 = smem_desc(sa + QATILE + kk * 32, 512, 4),
-                         q3 = smem_desc(sa + 2 * QATILE + kk * 32, 512, 4);
-          const uint32_t sb = sa + 3 * QATILE + kk * 32;
-          const uint64_t r1 = smem_desc(sb, 512, 4), r2 = smem_desc(sb + mb, 512, 4),
-                         r3 = smem_desc(sb + 2 * mb, 512, 4);
-          mma_bf16(tmem, q1, r1, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-          mma_bf16(tmem, q1, r2, idesc, 1u);
-          mma_bf16(tmem, q2, r1, idesc, 1u);
-          mma_bf16(tmem, q1, r3, idesc, 1u);
-          mma_bf16(tmem, q2, r2, idesc, 1u);
-          mma_bf16(tmem, q3, r1, idesc, 1u);
+#pragma unroll
+          for (int p = 0; p < NPROD; ++p) {
+            const uint64_t da = smem_desc(sa + prod_a(p) * QATILE + kk * 32, 512, 4);
+            const uint64_t db = smem_desc(sb + prod_b(p) * mb + kk * 32, 512, 4);
+            mma_bf16(tmem, da, db, idesc, (kc > 0 || kk > 0 || p > 0) ? 1u : 0u);
+          }
         }
         mma_commit(bar_empty + 8 * st);
       }
-      if (ok) mma_commit(bar_acc);
+      if (ok && nk > 0) mma_commit(bar_acc);
       mma_commit(bar_done);
       qwait(bar_done, 0, sh, a);
     }
   } else {
-    // epilogue: lanes = rows of the block's result, m_pad columns
+    // epilogue: lanes = rows of the A tile, m_pad columns
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
     int ok = 0;
-    if (lane == 0) ok = qwait(bar_acc, 0, sh, a) ? 1 : 0;
+    if (lane == 0) ok = (nk > 0 && qwait(bar_acc, 0, sh, a)) ? 1 : 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (ok) {
       fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
-      float* orow_p = a.out + (int64_t)(orow + m0 + row) * a.mpad;
-      const bool valid = m0 + row < s;
-      // transposed copy: column c of block i at row i*mpad + c, this lane's feature slot
-      const int64_t tcol = slot + m0 + row;
-      __nv_bfloat16* th = a.wthi + (int64_t)ry * a.fslots + tcol;
-      __nv_bfloat16* tl = a.wtlo + (int64_t)ry * a.fslots + tcol;
+      float* orow_p = a.out + job.out + (int64_t)row * a.mpad;
+      const bool transposed = job.tout >= 0;
+      __nv_bfloat16* th = transposed ? a.thi + job.tout + row : nullptr;
+      __nv_bfloat16* tl = transposed ? a.tlo + job.tout + row : nullptr;
       for (int c = 0; c < a.mpad; c += 8) {
         uint32_t r8[8];
         tmem_ld8(taddr + c, r8);
         tmem_wait_ld();
-        if (valid) {
-          float x[8];
+        float x[8];
 #pragma unroll
-          for (int t = 0; t < 8; ++t) x[t] = __uint_as_float(r8[t]);
-          float4* dst = reinterpret_cast<float4*>(orow_p + c);
-          dst[0] = make_float4(x[0], x[1], x[2], x[3]);
-          dst[1] = make_float4(x[4], x[5], x[6], x[7]);
+        for (int t = 0; t < 8; ++t) x[t] = __uint_as_float(r8[t]);
+        float4* dst = reinterpret_cast<float4*>(orow_p + c);
+        dst[0] = make_float4(x[0], x[1], x[2], x[3]);
+        dst[1] = make_float4(x[4], x[5], x[6], x[7]);
+        if (transposed) {
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
             __nv_bfloat16 hi, lo;
             split_bf16(x[t], hi, lo);
-            th[(int64_t)(c + t) * a.fslots] = hi;
-            tl[(int64_t)(c + t) * a.fslots] = lo;
+            th[(int64_t)(c + t) * a.tld] = hi;
+            tl[(int64_t)(c + t) * a.tld] = lo;
           }
         }
       }
@@ -261,6 +266,17 @@ __global__ void k_split3_q(const double* __restrict__ Q, int s, int64_t ldq, int
   q3[o] = l;
 }
 
+template <int NA, int NB>
+cudaError_t set_smem_attr() {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_split_gemm<NA, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                1024 + 216 * 1024 + 256);
+  });
+  return attr;
+}
+
 }  // namespace
 
 cudaError_t launch_split3_q(const double* Q, int s, int64_t ldq, int64_t qrow, __nv_bfloat16* q1,
@@ -279,41 +295,40 @@ cudaError_t launch_rhs_split3T(const float* Wbar, const float* muij, const float
   return cudaGetLastError();
 }
 
-cudaError_t tc_qgemm(const QgemmView& v) {
-  if (v.nblocks <= 0) return cudaSuccess;
-  if (v.mpad > 256 || v.mpad % 16) return cudaErrorInvalidValue;
+cudaError_t split_gemm(const SgView& v) {
+  if (v.njobs <= 0) return cudaSuccess;
+  if (v.mpad > 256 || v.mpad < 16 || v.mpad % 16) return cudaErrorInvalidValue;
+  if (!((v.na == 3 && v.nb == 3) || (v.na == 2 && v.nb == 2))) return cudaErrorInvalidValue;
   QArgs a;
   memset(&a, 0, sizeof(a));
   cudaError_t e;
-  if ((e = tc_make_map_bf16(&a.tQ1, v.Q1, v.ldq, v.q_rows, v.ldq, 128, QKC)) != cudaSuccess) return e;
-  if ((e = tc_make_map_bf16(&a.tQ2, v.Q2, v.ldq, v.q_rows, v.ldq, 128, QKC)) != cudaSuccess) return e;
-  if ((e = tc_make_map_bf16(&a.tQ3, v.Q3, v.ldq, v.q_rows, v.ldq, 128, QKC)) != cudaSuccess) return e;
-  if ((e = tc_make_map_bf16(&a.tR1, v.R1, v.r_cols, v.r_rows, v.r_cols, v.mpad, QKC)) != cudaSuccess) return e;
-  if ((e = tc_make_map_bf16(&a.tR2, v.R2, v.r_cols, v.r_rows, v.r_cols, v.mpad, QKC)) != cudaSuccess) return e;
-  if ((e = tc_make_map_bf16(&a.tR3, v.R3, v.r_cols, v.r_rows, v.r_cols, v.mpad, QKC)) != cudaSuccess) return e;
+  for (int s = 0; s < v.na; ++s)
+    if ((e = tc_make_map_bf16(&a.tA[s], v.A[s], v.a_cols, v.a_rows, v.a_cols, 128, QKC)) != cudaSuccess) return e;
+  for (int s = 0; s < v.nb; ++s)
+    if ((e = tc_make_map_bf16(&a.tB[s], v.B[s], v.b_cols, v.b_rows, v.b_cols, v.mpad, QKC)) != cudaSuccess)
+      return e;
   a.mpad = v.mpad;
-  a.stage_bytes = 3 * QATILE + 3 * (uint32_t)v.mpad * QKC * 2;
-  const size_t budget = 216 * 1024;
+  a.stage_bytes = v.na * QATILE + v.nb * (uint32_t)v.mpad * QKC * 2;
+  const size_t budget = std::min<size_t>(v.smem_budget ? v.smem_budget : 216 * 1024, 216 * 1024);
   a.ns = (int)std::min<size_t>(QMAXS, budget / a.stage_bytes);
+  if (a.ns < 2) a.ns = 2;
   a.tmem_cols = v.mpad <= 32 ? 32 : v.mpad <= 64 ? 64 : v.mpad <= 128 ? 128 : 256;
-  a.tab = v.tab;
-  a.nblocks = v.nblocks;
+  a.jobs = v.jobs;
   a.out = v.out;
-  a.wthi = v.WThi;
-  a.wtlo = v.WTlo;
-  a.fslots = v.fslots;
+  a.thi = v.thi;
+  a.tlo = v.tlo;
+  a.tld = v.tld;
   a.err = tc_error_ptr();
   if (!a.err) return cudaErrorMemoryAllocation;
-  a.timeout_cycles = 4000000000LL;
+  a.timeout_cycles = 4000000000LL;   // about two seconds at the boost clock
   const size_t smem = 1024 + (size_t)a.ns * a.stage_bytes + 256;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_qgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 + 216 * 1024 + 256);
-  });
-  if (attr != cudaSuccess) return attr;
-  dim3 grid((unsigned)ceil_div(v.max_s, 128), (unsigned)v.nblocks);
-  k_qgemm<<<grid, QNT, smem, v.st>>>(a);
+  if (v.na == 3) {
+    if ((e = set_smem_attr<3, 3>()) != cudaSuccess) return e;
+    k_split_gemm<3, 3><<<(unsigned)v.njobs, QNT, smem, v.st>>>(a);
+  } else {
+    if ((e = set_smem_attr<2, 2>()) != cudaSuccess) return e;
+    k_split_gemm<2, 2><<<(unsigned)v.njobs, QNT, smem, v.st>>>(a);
+  }
   return cudaGetLastError();
 }
 

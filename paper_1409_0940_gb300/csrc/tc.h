@@ -41,23 +41,31 @@ cudaError_t tc_predict(const TcView& v, const __nv_bfloat16* Xh, const __nv_bflo
                        const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, float* out);
 
 
-// Cached projection of the split path, eq. (gpWij): for every block (i, j)
-// out[i*fslots + slot_j + r][c] = sum_k Q_ij[r][k] rhs_ij[k][c], with Q_ij and rhs split
-// three ways into BF16 and six tensor-core products accumulated in FP32.  The result
-// is also written transposed and split two ways (WThi/WTlo, [R][mpad][fslots]) for pass 2.
-struct QgemmView {
-  const __nv_bfloat16 *Q1, *Q2, *Q3;   // q_rows x ldq, block b's rows from tab[5b]
-  int64_t q_rows, ldq;
-  const __nv_bfloat16 *R1, *R2, *R3;   // rhs transposed: [R*mpad][fslots]
-  int64_t r_rows, r_cols;
-  const int* tab;                      // device, per block: Q row, s_j, i*mpad, slot_j, i*fslots + slot_j
-  int nblocks, max_s, mpad;
-  float* out;                          // [R*fslots][mpad]
-  __nv_bfloat16 *WThi, *WTlo;          // [R*mpad][fslots]
-  int64_t fslots;
+// Split-BF16 streaming GEMM on the tensor cores, one CTA per job:
+//   out[job.out + r*mpad + c] = sum_k A[job.a_row + r][job.a_k0 + k] B[job.b_row + c][job.b_k0 + k]
+// for r < 128, c < mpad, k < 32*job.nk, with A and B split into na = nb = 3 BF16 terms
+// (six products) or 2 terms (three products).  If job.tout >= 0 the result is also
+// written transposed as a hi/lo pair: thi/tlo[job.tout + c*tld + r].  A is a_rows x
+// a_cols (row-major), B b_rows x b_cols; every job's K range and rows lie inside them.
+struct SgJob {
+  int32_t a_row, a_k0, b_row, b_k0, nk, pad_;
+  int64_t out, tout;
+};
+struct SgView {
+  const __nv_bfloat16* A[3];
+  int64_t a_rows, a_cols;
+  const __nv_bfloat16* B[3];
+  int64_t b_rows, b_cols;
+  int na, nb;
+  const SgJob* jobs;                   // device
+  int njobs, mpad;
+  float* out;
+  __nv_bfloat16 *thi, *tlo;
+  int64_t tld;
+  size_t smem_budget;                  // ring bytes per CTA (0 = the largest; smaller lets 2 CTAs share an SM)
   cudaStream_t st;
 };
-cudaError_t tc_qgemm(const QgemmView& v);
+cudaError_t split_gemm(const SgView& v);
 // Q (s x s, row-major float64) split three ways into rows [qrow, qrow+s) of q1..q3 (ld ldq).
 cudaError_t launch_split3_q(const double* Q, int s, int64_t ldq, int64_t qrow, __nv_bfloat16* q1,
                             __nv_bfloat16* q2, __nv_bfloat16* q3, cudaStream_t st);

@@ -45,7 +45,8 @@ def test_every_declared_symbol_is_exported_and_bound(rff):
 
 def test_parameter_validation_on_host(rff):
     bad = [dict(lam=0.0), dict(sigma=-1.0), dict(rho=0.0), dict(D=0), dict(R=0), dict(C=0),
-           dict(C=10, D=5), dict(m=0), dict(m=300), dict(prec="split_bf16", C=65, D=1000)]
+           dict(C=10, D=5), dict(m=0), dict(m=300), dict(prec="split_bf16", C=65, D=1000),
+           dict(prec="cached_z", C=65, D=1000)]
     for kw in bad:
         p = rff.make_params(**kw)
         h = ctypes.c_void_p()
