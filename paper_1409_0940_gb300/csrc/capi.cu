@@ -48,7 +48,8 @@ struct rff_admm_s {
   int64_t* d_zero = nullptr;  // {0}: row block table of a query batch
   float *X32 = nullptr, *Gt32 = nullptr, *bias = nullptr, *Y = nullptr;
   __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr, *Ghi = nullptr, *Glo = nullptr;
-  float *O = nullptr, *Obar = nullptr, *nu = nullptr, *Dl = nullptr, *Op = nullptr, *V32 = nullptr;
+  float *O = nullptr, *Obar = nullptr, *nu = nullptr, *Op = nullptr;
+  float* V32 = nullptr;       // FP32 path: V_ij = Obar_ij + nu_i, C x slots x mpad (split path: V^T hi/lo only)
   __nv_bfloat16 *VThi = nullptr, *VTlo = nullptr, *WThi = nullptr, *WTlo = nullptr, *WbThi = nullptr,
                 *WbTlo = nullptr;
   float *W = nullptr, *Wbar = nullptr, *mu = nullptr, *What = nullptr, *muij = nullptr, *rhs = nullptr,
@@ -192,8 +193,8 @@ size_t working_set_bytes(const rff_admm_s& s) {
   if (s.split_path()) t += (size_t)s.nslots * s.dld * b2 * 2 + (size_t)s.fslots * s.dld * b2 * 2;
   else t += (size_t)s.nslots * s.dld * f + (size_t)s.fslots * s.dld * f;
   t += (size_t)s.fslots * f;
-  t += (size_t)s.nslots * s.mpad * f * (5 + 2);                 // Y, O, Obar, nu, Dl, nu_old, Obar_old
-  t += (size_t)s.C * s.nslots * s.mpad * f * 2;                 // Op, V32
+  t += (size_t)s.nslots * s.mpad * f * (4 + 2);                 // Y, O, Obar, nu, nu_old, Obar_old
+  t += (size_t)s.C * s.nslots * s.mpad * f * (s.split_path() ? 1 : 2);   // Op (+ V32 on the FP32 path)
   if (s.split_path()) t += (size_t)s.C * s.nslots * s.mpad * b2 * 2;
   t += (size_t)s.fslots * s.mpad * f * 5;                       // W, Wbar, mu, mu_old, Wbar_old
   t += (size_t)s.R * s.fslots * s.mpad * f * (3 + s.nsplit_max);    // What, muij, muij_old, Rpart
@@ -421,11 +422,10 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   AL(s.O, s.nslots * s.mpad);
   AL(s.Obar, s.nslots * s.mpad);
   AL(s.nu, s.nslots * s.mpad);
-  AL(s.Dl, s.nslots * s.mpad);
   AL(s.nu_old, s.nslots * s.mpad);
   AL(s.Obar_old, s.nslots * s.mpad);
   AL(s.Op, (int64_t)s.C * s.nslots * s.mpad);
-  AL(s.V32, (int64_t)s.C * s.nslots * s.mpad);
+  if (!s.split_path()) AL(s.V32, (int64_t)s.C * s.nslots * s.mpad);
   AL(s.W, s.fslots * s.mpad);
   AL(s.Wbar, s.fslots * s.mpad);
   AL(s.mu, s.fslots * s.mpad);
@@ -526,8 +526,8 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
 
   // ADMM state: all zero (Sec. 3: "initialize to zero"), then O = prox(Obar - nu) = prox(0)
   const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
-  for (float* b : {s.O, s.Obar, s.nu, s.Dl}) CK(cudaMemsetAsync(b, 0, rowb, s.st));
-  CK(cudaMemsetAsync(s.V32, 0, rowb * s.C, s.st));
+  for (float* b : {s.O, s.Obar, s.nu}) CK(cudaMemsetAsync(b, 0, rowb, s.st));
+  if (s.V32) CK(cudaMemsetAsync(s.V32, 0, rowb * s.C, s.st));
   CK(cudaMemsetAsync(s.Op, 0, rowb * s.C, s.st));
   for (float* b : {s.W, s.Wbar, s.mu}) CK(cudaMemsetAsync(b, 0, colb, s.st));
   for (float* b : {s.What, s.muij}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
@@ -928,17 +928,16 @@ rff_status iterate(rff_admm_t h, int k) {
   }
   if ((r = mark(h, k, 4)) != RFF_OK) return r;
   // exchange, nu update, next loss prox, next V_ij
-  RowEpiArgs e{s.Op, s.O, s.Obar, s.nu, s.Dl, s.Y, s.V32, nullptr, nullptr, s.row_of_slot, s.nslots,
+  RowEpiArgs e{s.Op, s.O, s.Obar, s.nu, s.Y, s.V32, s.VThi, s.VTlo, s.row_of_slot, s.nslots,
                s.C, (int)s.m, (int)s.mpad, s.p.loss, s.p.newton_iters, s.t_loss};
+  if (s.split_path()) e.V32 = nullptr;   // the split path keeps only V^T (hi/lo)
+  else e.VThi = e.VTlo = nullptr;
   CK(launch_row_epilogue(e, s.st));
-  if (s.split_path())
-    CK(launch_transpose_split(s.V32, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
-                              s.mpad * s.nslots, s.st));
   if ((r = mark(h, k, 5)) != RFF_OK) return r;
   // averaging and dual updates
   CK(launch_avg_dual(s.W, s.What, s.R, nfe, s.Wbar, s.mu, s.muij, s.st));
   if ((r = mark(h, k, 6)) != RFF_OK) return r;
-  s.launches += s.split_path() ? 8 : 7;
+  s.launches += 7;
   return RFF_OK;
 }
 
@@ -990,7 +989,7 @@ rff_status enqueue_iterations(rff_admm_t h, int iters, bool copy_old) {
     } else {
       if (!s.gexec && (r = capture_iteration(h)) != RFF_OK) return r;
       CK(cudaGraphLaunch(s.gexec, s.st));
-      s.launches += s.split_path() ? 8 : 7;
+      s.launches += 7;
     }
     if (r != RFF_OK) return r;
     s.iters_done++;
@@ -1286,13 +1285,24 @@ struct StateHeader {
   int32_t R, C, iters_done, reserved;
 };
 struct Piece {
-  float* ptr;
+  void* ptr;
   size_t bytes;
 };
+// the iteration's state: O, Obar, nu, the pass-1 operand V (FP32, or V^T as the hi/lo
+// pair the tensor-core pass reads), W, Wbar, mu, W'_ij, mu'_ij
 std::vector<Piece> state_pieces(rff_admm_s& s) {
   const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
-  return {{s.O, rowb},        {s.Obar, rowb},       {s.nu, rowb},   {s.Dl, rowb},   {s.V32, rowb * s.C},
-          {s.W, colb},        {s.Wbar, colb},       {s.mu, colb},   {s.What, colb * s.R}, {s.muij, colb * s.R}};
+  std::vector<Piece> v{{s.O, rowb}, {s.Obar, rowb}, {s.nu, rowb}};
+  if (s.split_path()) {
+    v.push_back({s.VThi, rowb / 2 * s.C});
+    v.push_back({s.VTlo, rowb / 2 * s.C});
+  } else {
+    v.push_back({s.V32, rowb * s.C});
+  }
+  for (Piece pc : std::vector<Piece>{{s.W, colb}, {s.Wbar, colb}, {s.mu, colb}, {s.What, colb * s.R},
+                                     {s.muij, colb * s.R}})
+    v.push_back(pc);
+  return v;
 }
 }  // namespace
 
@@ -1349,9 +1359,6 @@ rff_status rff_admm_set_state(rff_admm_t h, const void* buf, size_t bytes) {
     CK(cudaMemcpyAsync(pc.ptr, in + off, pc.bytes, cudaMemcpyHostToDevice, s.st));
     off += pc.bytes;
   }
-  if (s.split_path())
-    CK(launch_transpose_split(s.V32, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
-                              s.mpad * s.nslots, s.st));
   CK(cudaStreamSynchronize(s.st));
   s.iters_done = hd.iters_done;
   return RFF_OK;

@@ -6,6 +6,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <mutex>
 
 namespace rff {
 
@@ -194,71 +195,96 @@ __global__ void k_prox_reg(int reg, const float* __restrict__ V, const float* __
   out[e] = (reg == 0) ? x / (1.f + 2.f * t) : copysignf(fmaxf(fabsf(x) - t, 0.f), x);
 }
 
-// Row-local exchange after pass 2 (one warp per row slot, lanes over outputs):
+// Row-local exchange after pass 2 (one CTA per 32 row slots, 8 warps):
 //   S = sum_j O'_ij;  Delta = O - S;  Obar = S/(C+1) + C/(C+1) O;  nu += O - Obar
-//   V_ij = O'_ij + Delta/(C+1) + nu        (= Obar_ij + nu, the pass-1 operand)
+//   V_ij = O'_ij + (Delta/(C+1) + nu)      (= Obar_ij + nu, the pass-1 operand)
 //   O <- prox_{t V}(Obar - nu)             (the loss step of the next iteration)
-// Padding rows are written as zeros.
-__global__ void k_row_epilogue(RowEpiArgs a) {
-  const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-  if (p >= a.nslots) return;
-  const int lane = threadIdx.x & 31;
-  const bool ok = a.row_ok[p] >= 0;
-  const int64_t base = p * a.mpad;
-  const int64_t jstride = a.nslots * a.mpad;
+// Phase 1 (a warp per row, lanes over outputs) updates Obar, nu and O and keeps
+// Delta/(C+1) + nu of the tile in shared memory; phase 2 forms V_ij tile by tile,
+// either row-major in FP32 (the SIMT path's operand) or transposed and split into
+// hi/lo BF16 (V^T[j][c][slot], the tensor-core operand) through a shared-memory
+// transpose so that both the reads and the writes are coalesced.  Padding rows and
+// columns are written as zeros.
+constexpr int EX_ROWS = 32;
+
+template <int LOSS>
+__global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
+  extern __shared__ float ex_smem[];
+  const int mp = a.mpad;
+  float* term = ex_smem;                         // [32][mpad]
+  float* tile = ex_smem + EX_ROWS * mp;          // [32][mpad + 1]
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int64_t p0 = (int64_t)blockIdx.x * EX_ROWS;
+  const int64_t jstride = a.nslots * mp;
   const float inv_c1 = 1.f / (float)(a.C + 1);
   const float cfrac = (float)a.C * inv_c1;
-  float w_in[MAXPL], y[MAXPL];
-  float dl[MAXPL], nuv[MAXPL];
+  for (int r = warp; r < EX_ROWS; r += 8) {
+    const int64_t p = p0 + r;
+    const bool ok = a.row_ok[p] >= 0;
+    const int64_t base = p * mp;
+    float w_in[MAXPL], y[MAXPL];
 #pragma unroll
-  for (int q = 0; q < MAXPL; ++q) {
-    const int k = lane + 32 * q;
-    w_in[q] = 0.f; y[q] = 0.f; dl[q] = 0.f; nuv[q] = 0.f;
-    if (k >= a.mpad) continue;
-    float S = 0.f;
-    for (int j = 0; j < a.C; ++j) S += a.Op[j * jstride + base + k];
-    const float O = a.O[base + k];
-    float nu = a.nu[base + k];
-    const float Delta = O - S;
-    const float Obar = S * inv_c1 + cfrac * O;
-    nu += O - Obar;
-    if (!ok || k >= a.m) {
-      a.Obar[base + k] = 0.f; a.nu[base + k] = 0.f; a.Dl[base + k] = 0.f;
-      continue;
-    }
-    a.Obar[base + k] = Obar;
-    a.nu[base + k] = nu;
-    a.Dl[base + k] = Delta;
-    dl[q] = Delta;
-    nuv[q] = nu;
-    w_in[q] = Obar - nu;
-    y[q] = a.Y[base + k];
-  }
-  // V_ij for every column block
-  if (a.V32) {
-    for (int j = 0; j < a.C; ++j) {
-#pragma unroll
-      for (int q = 0; q < MAXPL; ++q) {
-        const int k = lane + 32 * q;
-        if (k >= a.mpad) continue;
-        const float vv = (ok && k < a.m) ? a.Op[j * jstride + base + k] + dl[q] * inv_c1 + nuv[q] : 0.f;
-        a.V32[j * jstride + base + k] = vv;
+    for (int q = 0; q < MAXPL; ++q) {
+      const int k = lane + 32 * q;
+      w_in[q] = 0.f;
+      y[q] = 0.f;
+      if (k >= mp) continue;
+      float S = 0.f;
+      for (int j = 0; j < a.C; ++j) S += a.Op[j * jstride + base + k];
+      const float O = a.O[base + k];
+      float nu = a.nu[base + k];
+      const float Delta = O - S;
+      const float Obar = S * inv_c1 + cfrac * O;
+      nu += O - Obar;
+      const bool live = ok && k < a.m;
+      a.Obar[base + k] = live ? Obar : 0.f;
+      a.nu[base + k] = live ? nu : 0.f;
+      term[r * mp + k] = live ? Delta * inv_c1 + nu : 0.f;
+      if (live) {
+        w_in[q] = Obar - nu;
+        y[q] = a.Y[base + k];
       }
     }
-  }
-  // next loss step
-  float o[MAXPL];
-  if (a.loss == LOSS_MULTINOMIAL) {
-    prox_multinomial_row(w_in, y, a.m, a.t_loss, a.newton, o);
-  } else {
+    float o[MAXPL];
+    if (LOSS == LOSS_MULTINOMIAL) {
+      prox_multinomial_row(w_in, y, a.m, a.t_loss, a.newton, o);
+    } else {
 #pragma unroll
-    for (int q = 0; q < MAXPL; ++q) o[q] = prox_scalar(a.loss, w_in[q], y[q], a.t_loss, a.newton);
-  }
+      for (int q = 0; q < MAXPL; ++q) o[q] = prox_scalar(LOSS, w_in[q], y[q], a.t_loss, a.newton);
+    }
 #pragma unroll
-  for (int q = 0; q < MAXPL; ++q) {
-    const int k = lane + 32 * q;
-    if (k >= a.mpad) continue;
-    a.O[base + k] = (ok && k < a.m) ? o[q] : 0.f;
+    for (int q = 0; q < MAXPL; ++q) {
+      const int k = lane + 32 * q;
+      if (k < mp) a.O[base + k] = (ok && k < a.m) ? o[q] : 0.f;
+    }
+  }
+  __syncthreads();
+  // phase 2: V_ij = O'_ij + term, per column block
+  for (int j = 0; j < a.C; ++j) {
+    const float* opj = a.Op + j * jstride + p0 * mp;
+    if (a.V32) {
+      float* vj = a.V32 + j * jstride + p0 * mp;
+      for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
+        const bool live = a.row_ok[p0 + e / mp] >= 0 && e % mp < a.m;
+        vj[e] = live ? opj[e] + term[e] : 0.f;
+      }
+      continue;
+    }
+    for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
+      const int r = e / mp, k = e % mp;
+      const bool live = a.row_ok[p0 + r] >= 0 && k < a.m;
+      tile[r * (mp + 1) + k] = live ? opj[e] + term[e] : 0.f;
+    }
+    __syncthreads();
+    // lanes over the 32 rows, warps over columns: V^T[j][c][p0 + lane]
+    for (int c = warp; c < mp; c += 8) {
+      __nv_bfloat16 hi, lo;
+      split_bf16(tile[lane * (mp + 1) + c], hi, lo);
+      const int64_t o = ((int64_t)j * mp + c) * a.nslots + p0 + lane;
+      a.VThi[o] = hi;
+      a.VTlo[o] = lo;
+    }
+    __syncthreads();
   }
 }
 
@@ -442,8 +468,29 @@ cudaError_t launch_prox_reg(int reg, const float* V, const float* mu, int64_t n,
 
 cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st) {
   if (a.nslots <= 0) return cudaSuccess;
-  if (a.mpad > 32 * MAXPL) return cudaErrorInvalidValue;
-  k_row_epilogue<<<nblk(a.nslots * 32), 256, 0, st>>>(a);
+  if (a.mpad > 32 * MAXPL || a.nslots % EX_ROWS) return cudaErrorInvalidValue;
+  if (!a.V32 && !(a.VThi && a.VTlo)) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)EX_ROWS * (2 * a.mpad + 1) * sizeof(float);
+  const unsigned grid = (unsigned)(a.nslots / EX_ROWS);
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    const int mx = EX_ROWS * (2 * 32 * MAXPL + 1) * (int)sizeof(float);
+    attr = cudaFuncSetAttribute(k_exchange<LOSS_SQUARED>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_exchange<LOSS_HINGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_exchange<LOSS_LOGISTIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_exchange<LOSS_MULTINOMIAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  });
+  if (attr != cudaSuccess) return attr;
+  switch (a.loss) {
+    case LOSS_SQUARED: k_exchange<LOSS_SQUARED><<<grid, 256, smem, st>>>(a); break;
+    case LOSS_HINGE: k_exchange<LOSS_HINGE><<<grid, 256, smem, st>>>(a); break;
+    case LOSS_LOGISTIC: k_exchange<LOSS_LOGISTIC><<<grid, 256, smem, st>>>(a); break;
+    default: k_exchange<LOSS_MULTINOMIAL><<<grid, 256, smem, st>>>(a); break;
+  }
   return cudaGetLastError();
 }
 

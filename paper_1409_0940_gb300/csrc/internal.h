@@ -118,7 +118,6 @@ struct RowEpiArgs {
   float* O;             // slots x mpad (in: O^k, out: O^{k+1} = prox(Obar - nu))
   float* Obar;
   float* nu;
-  float* Dl;            // Delta_i
   const float* Y;
   float* V32;           // C x slots x mpad (may be null)
   __nv_bfloat16* VThi;  // C x mpad x slots (may be null)
