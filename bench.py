@@ -135,6 +135,29 @@ def bytes_per_cached_pass(w):
     return 4 * n * D + 4 * C * n * mpad + 4 * R * D * mpad
 
 
+def measure(rff, w, X, Y, prec, steps, warmup, stream):
+    """warmup untimed iterations (the first call also builds the factors), then steps
+    iterations timed with CUDA events on the solver's stream; returns the device ms,
+    the phase profile, the consensus weights and the clock record."""
+    import torch
+    s = rff.Solver(stream=stream.cuda_stream, **solver_kw(w, prec))
+    s.set_data(X, Y)
+    s.solve(warmup, stats=False)
+    s.profiling(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        s.solve(steps, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    W = s.weights()
+    s.close()
+    return ms, prof, W, clk
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -148,31 +171,17 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     X, Y = make_data(w)
     stream = torch.cuda.Stream()
-    s = rff.Solver(stream=stream.cuda_stream, **solver_kw(w, args.prec))
-    s.set_data(X, Y)
-    s.solve(args.warmup, stats=False)          # set-up + warm-up iterations
-    s.profiling(True)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(torch.cuda.current_device()) as clk:
-        e0.record(stream)
-        s.solve(args.steps, stats=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
+    ms, prof, W_main, clk = measure(rff, w, X, Y, args.prec, args.steps, args.warmup, stream)
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    prof = s.profile()
-    if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
-    s.close()
     # end to end through the public API with host buffers: set_data (H2D of X, Y),
     # set-up, K iterations, weights back to the host (D2H)
     e2e = None
@@ -187,6 +196,27 @@ def run_ours(args, rank, world):
         e2e = {"value": args.steps / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": (X.nbytes + Y.nbytes) // args.steps,
                "d2h_bytes_per_step": Wh.nbytes // args.steps,
                "note": "set_data + set-up + K iterations + get_weights, host buffers"}
+
+    # the other precisions on the same workload and iteration count: speed, and the
+    # relative difference of the consensus weights (all three approximate the same
+    # FP64 iterate; the oracle parity itself is in the tests)
+    compare = None
+    if not args.no_compare and rank == 0:
+        compare = {}
+        Ws = {args.prec: W_main}
+        for prec in ("split_bf16", "cached_z", "fp32"):
+            if prec == args.prec:
+                compare[prec] = {"iter_per_s": args.steps / (ms * 1e-3)}
+                continue
+            k = args.steps if prec != "fp32" else max(1, min(args.steps, 5))
+            # same total iteration count as the main run: the untimed part makes up the rest
+            ms_p, _, W_p, _ = measure(rff, w, X, Y, prec, k, args.warmup + args.steps - k, stream)
+            Ws[prec] = W_p
+            compare[prec] = {"iter_per_s": k / (ms_p * 1e-3)}
+        ref = Ws["fp32"].astype(np.float64)
+        for prec, Wp in Ws.items():
+            compare[prec]["rel_diff_vs_fp32"] = float(np.linalg.norm(Wp - ref) / np.linalg.norm(ref))
+        compare["iterations"] = args.warmup + args.steps
 
     useful, exec_pass = flops_per_iter(w, args.prec)
     hbm, bf16, bf16_sus, src = peaks()
@@ -227,6 +257,7 @@ def run_ours(args, rank, world):
         "useful_tflops": useful / (ms / args.steps * 1e-3) / 1e12,
         "roofline": roof,
         "clocks": clk.summary(),
+        "precisions": compare,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
@@ -411,6 +442,7 @@ def main():
     ap.add_argument("--prec", default="split_bf16", choices=["split_bf16", "fp32", "cached_z"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-compare", action="store_true", help="skip the other precisions (profiling runs)")
     ap.add_argument("--n", type=int, default=0, help="rows of a reduced workload (profiling runs)")
     ap.add_argument("--workload", default="multiclass", choices=["multiclass", "sweep", "serve"])
     args = ap.parse_args()

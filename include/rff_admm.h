@@ -231,6 +231,10 @@ typedef struct {
   double ms_average;       /* Wbar, mu, mu'_ij updates                                      */
   int32_t tc_kchunk;       /* K chunk of the tensor-core ring chosen by the autotuner (0: FP32) */
   int32_t nsplit;          /* row splits of pass 1 chosen by the autotuner                   */
+  int32_t tc_z_tmem;       /* 1: the tensor-core passes keep the Z tile in tensor memory,
+                              0: in shared memory (chosen by the autotuner; the environment
+                              variable RFF_TC_GEOMETRY="kc,zt" fixes both instead)          */
+  int32_t reserved;
 } rff_admm_profile;
 
 rff_status rff_admm_set_profiling(rff_admm_t h, int enable);

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -38,6 +39,7 @@ struct rff_admm_s {
   int64_t n = 0, d = 0, dld = 0, m = 0, mpad = 0, D = 0, nslots = 0, fslots = 0;
   int R = 1, C = 1, nsplit = 1, nsplit_max = 1, iters_done = 0;
   int tc_kc = 0;  // ring K chunk of the tensor-core passes, chosen by the autotuner
+  int tc_zt = 0;  // 1: Z tile of the tensor-core passes in TMEM (autotuned)
   float t_loss = 0.f, t_reg = 0.f;
   std::vector<int64_t> row_start, row_size, row_slot, col_start, col_size, col_slot, foff;
 
@@ -355,6 +357,7 @@ rff_status rff_admm_get_profile(rff_admm_t h, rff_admm_profile* out) {
   out->launches = h->launches;
   out->tc_kchunk = h->split_path() ? (h->tc_kc ? h->tc_kc : 64) : 0;
   out->nsplit = h->cached_z() ? h->nsplit_cz : h->nsplit;
+  out->tc_z_tmem = h->split_path() ? h->tc_zt : 0;
   return RFF_OK;
 }
 
@@ -553,24 +556,37 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
 namespace {
 
 // Tile-shape autotuner of the tensor-core passes: times pass 1 + pass 2 for each
-// ring geometry (K chunk 64 or 32) on the handle's own data and keeps the
-// fastest.  Both geometries issue the same MMAs in the same order, so the choice
+// ring geometry (K chunk 64 or 32, Z tile in shared or tensor memory) on the
+// handle's own data and keeps the fastest.  All geometries issue the same MMAs in
+// the same order, so the choice
 // changes speed, never results (a run is reproducible whatever the timing).  The
 // passes only write their scratch outputs (R partials, O'), which every
 // iteration recomputes.
 rff_status autotune(rff_admm_t h) {
   auto& s = *h;
   if (!s.split_path() || s.cached_z()) return RFF_OK;
+  // RFF_TC_GEOMETRY="kc,zt" (kc 64 or 32, zt 0 or 1) fixes the geometry instead
+  if (const char* g = getenv("RFF_TC_GEOMETRY")) {
+    int kc = 0, zt = -1;
+    if (sscanf(g, "%d,%d", &kc, &zt) == 2 && (kc == 64 || kc == 32) && (zt == 0 || zt == 1)) {
+      s.tc_kc = kc;
+      s.tc_zt = zt;
+      return RFF_OK;
+    }
+    return h->fail(RFF_EINVAL, "RFF_TC_GEOMETRY must be \"64,0\", \"64,1\", \"32,0\" or \"32,1\"");
+  }
   std::vector<int> splits{s.nsplit};
   if (s.nsplit_max != s.nsplit) splits.push_back(s.nsplit_max);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_kc = 64, best_ns = s.nsplit;
+  int best_kc = 64, best_ns = s.nsplit, best_zt = 0;
+  for (int zt : {0, 1})
   for (int kc : {64, 32}) {
     for (int ns : splits) {
       s.tc_kc = kc;
+      s.tc_zt = zt;
       s.nsplit = ns;
       float ms = 0.f;
       for (int rep = 0; rep < 2; ++rep) {     // first run warms caches and descriptors
@@ -585,12 +601,14 @@ rff_status autotune(rff_admm_t h) {
         best = ms;
         best_kc = kc;
         best_ns = ns;
+        best_zt = zt;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   s.tc_kc = best_kc;
+  s.tc_zt = best_zt;
   s.nsplit = best_ns;
   if (tc_error_word() != 0) return h->fail(RFF_ETIMEOUT, "a tensor-core pass gave up waiting during tuning");
   return RFF_OK;
@@ -1073,6 +1091,7 @@ TcView tc_view(const rff_admm_s& s) {
   v.scale = (float)std::sqrt(2.0 / (double)s.D);
   v.bias_in_mma = s.bias_col >= 0 ? 1 : 0;
   v.kc = s.tc_kc;
+  v.zt = s.tc_zt;
   v.st = s.st;
   return v;
 }

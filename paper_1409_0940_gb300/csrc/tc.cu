@@ -47,21 +47,31 @@ constexpr int MAXG = 64;                    // groups (column blocks) per CTA
 // Ring geometry.  KC = K elements per ring stage: 64 (128-byte rows, 128-byte
 // swizzle, 64 KB stages) or 32 (64-byte rows, 64-byte swizzle, 32 KB stages, so
 // more stages fit beside the Z tile and more bytes are in flight).
-template <int KC>
+//
+// ZT selects where the Z tile lives between the cosine and the chained product:
+// 0 = shared memory (128-byte swizzled K-major, the chained MMA reads it by
+// descriptor), 1 = tensor memory (the chained MMA takes A from TMEM).  With Z in
+// TMEM the shared memory it used holds more ring stages, and neither the Z stores
+// nor the chained MMA's A reads use shared-memory bandwidth; acc1 is then single-
+// buffered (TMEM: acc1 128 columns, Z hi 64, Z lo 64, acc2 at 256).  Both issue the
+// same products in the same order.
+template <int KC, int ZT>
 struct Ring {
   static constexpr uint32_t ROWB = KC * 2;               // bytes per operand row in a stage
   static constexpr uint32_t TILEB = 128 * ROWB;          // one 128-row operand tile
   static constexpr uint32_t STAGEB = 4 * TILEB;          // A hi, A lo, B hi, B lo
-  static constexpr int NS = (KC == 64) ? 2 : 5;          // stages
+  static constexpr int NS = ZT ? ((KC == 64) ? 3 : 6) : ((KC == 64) ? 2 : 5);   // stages
   static constexpr int KSTEPS = KC / 16;                 // MMA K steps per stage
   static constexpr int CHUNKS = 128 / KC;                // chain-operand chunks per B tile
   static constexpr uint32_t LAYOUT = (KC == 64) ? 2 : 4; // descriptor layout: 128B / 64B swizzle
   static constexpr uint32_t SBO = 8 * ROWB;              // bytes between 8-row groups
+  static constexpr uint32_t ZSMEM = ZT ? 0 : ZBYTES;     // shared memory of the Z tile
 };
-template <int KC>
+template <int KC, int ZT>
 constexpr size_t smem_bytes() {
-  return 1024 + Ring<KC>::NS * Ring<KC>::STAGEB + ZBYTES + 256 + MAXG * 24;
+  return 1024 + Ring<KC, ZT>::NS * Ring<KC, ZT>::STAGEB + Ring<KC, ZT>::ZSMEM + 256 + MAXG * 24;
 }
+constexpr uint32_t ZH_COL = 128, ZL_COL = 192;   // Z hi / lo in TMEM (ZT = 1), 64 columns each
 
 // error codes written to the error word
 constexpr int ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPI = 4;
@@ -129,16 +139,16 @@ __device__ __forceinline__ bool waitw(uint32_t bar, uint32_t parity, SH& sh, con
   return ok != 0;
 }
 
-template <int KC>
+template <int KC, int ZT>
 __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant__ TcArgs a) {
-  using RG = Ring<KC>;
+  using RG = Ring<KC, ZT>;
   constexpr int NSTAGE = RG::NS;
   constexpr uint32_t STAGE_BYTES = RG::STAGEB, TILE_BYTES = RG::TILEB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the operand tiles (the swizzle pattern repeats every 1024 bytes)
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   unsigned char* zbuf = base;
-  unsigned char* stages = base + ZBYTES;
+  unsigned char* stages = base + RG::ZSMEM;
   Shared<NSTAGE>& sh = *reinterpret_cast<Shared<NSTAGE>*>(stages + NSTAGE * STAGE_BYTES);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -312,14 +322,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
 #pragma unroll
           for (int kk = 0; kk < RG::KSTEPS; ++kk) {
             const int zk = c * RG::KSTEPS + kk;                 // K step within the 128-wide Z tile
-            const uint32_t zo = (zk / 4) * ZATOM + (zk % 4) * 32;
-            const uint64_t dzh = sw128_desc(zhi + zo), dzl = sw128_desc(zlo + zo);
             const uint64_t dmh = smem_desc(mhi + kk * 32, RG::SBO, RG::LAYOUT),
                            dml = smem_desc(mlo + kk * 32, RG::SBO, RG::LAYOUT);
             const uint32_t acc = (first && c == 0 && kk == 0) ? 0u : 1u;
-            mma_bf16(tmem + ACC2_COL, dzh, dmh, id2, acc);
-            mma_bf16(tmem + ACC2_COL, dzh, dml, id2, 1u);
-            mma_bf16(tmem + ACC2_COL, dzl, dmh, id2, 1u);
+            if (ZT) {
+              // A = Z from TMEM: 16 K elements = 8 packed columns per step
+              const uint32_t azh = tmem + ZH_COL + 8 * zk, azl = tmem + ZL_COL + 8 * zk;
+              mma_bf16_ts(tmem + ACC2_COL, azh, dmh, id2, acc);
+              mma_bf16_ts(tmem + ACC2_COL, azh, dml, id2, 1u);
+              mma_bf16_ts(tmem + ACC2_COL, azl, dmh, id2, 1u);
+            } else {
+              const uint32_t zo = (zk / 4) * ZATOM + (zk % 4) * 32;
+              const uint64_t dzh = sw128_desc(zhi + zo), dzl = sw128_desc(zlo + zo);
+              mma_bf16(tmem + ACC2_COL, dzh, dmh, id2, acc);
+              mma_bf16(tmem + ACC2_COL, dzh, dml, id2, 1u);
+              mma_bf16(tmem + ACC2_COL, dzl, dmh, id2, 1u);
+            }
           }
           mma_commit(bar_empty + 8 * s);
           ++it;
@@ -333,8 +351,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
       for (int g = 0; g < ngroups && ok; ++g) {
         const int ntg = sh.g_nt[g];
         for (int lt = 0; lt < ntg && ok; ++lt, ++t) {
-          const int b = t & 1;
-          if (t >= 2 && !wait1(bar_a1e + 8 * b, ((t - 2) >> 1) & 1, sh, a, ERR_TIMEOUT_MMA)) { ok = false; break; }
+          // acc1: double-buffered (ZT = 0) or one buffer (ZT = 1)
+          const int b = ZT ? 0 : (t & 1);
+          const bool reuse = ZT ? (t >= 1) : (t >= 2);
+          const uint32_t par = ZT ? ((t - 1) & 1) : (((t - 2) >> 1) & 1);
+          if (reuse && !wait1(bar_a1e + 8 * b, par, sh, a, ERR_TIMEOUT_MMA)) { ok = false; break; }
           fence_after();
           const uint32_t d1 = tmem + 128 * b;
           for (int kc = 0; kc < nk; ++kc) {
@@ -387,9 +408,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
     for (int g = 0; g < ngroups && ok; ++g) {
       const int ntg = sh.g_nt[g];
       for (int lt = 0; lt < ntg && ok; ++lt, ++t) {
-        const int b = t & 1;
+        const int b = ZT ? 0 : (t & 1);
         const int64_t bslot = sh.g_b0[g] + 128 * (int64_t)lt;
-        if (!waitw(bar_a1f + 8 * b, (t >> 1) & 1, sh, a, ERR_TIMEOUT_EPI)) { ok = false; break; }
+        if (!waitw(bar_a1f + 8 * b, ZT ? (t & 1) : ((t >> 1) & 1), sh, a, ERR_TIMEOUT_EPI)) { ok = false; break; }
         fence_after();
         uint32_t v0[32], v1[32];
         tmem_ld32(tmem + lane_addr + 128 * b + colbase, v0);
@@ -425,26 +446,49 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
         }
         // Z tile must be free: the chain of the previous tile has completed
         if (t >= 1 && !waitw(bar_ze, (t - 1) & 1, sh, a, ERR_TIMEOUT_EPI)) { ok = false; break; }
-        // split into hi/lo BF16 and store in the 128-byte swizzled K-major layout
-        unsigned char* zhi = zbuf + (colbase / 64) * ZATOM;
-        unsigned char* zlo = zhi + ZBYTES / 2;
+        if (ZT) {
+          // split into hi/lo BF16 pairs (two K elements per 32-bit column) and store this
+          // warp's 32 rows x 64 features into the Z columns of TMEM
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
-          uint32_t ph[4], pl[4];
+          for (int hf = 0; hf < 2; ++hf) {
+            uint32_t ph[16], pl[16];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            // hi = bf16x2(z0, z1); lo = bf16x2(z - hi) (packed conversions)
-            const __nv_bfloat162 h = __floats2bfloat162_rn(z[ch * 8 + 2 * q], z[ch * 8 + 2 * q + 1]);
-            const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(z[ch * 8 + 2 * q] - hf.x, z[ch * 8 + 2 * q + 1] - hf.y);
-            ph[q] = *reinterpret_cast<const uint32_t*>(&h);
-            pl[q] = *reinterpret_cast<const uint32_t*>(&l);
+            for (int q = 0; q < 16; ++q) {
+              const float z0 = z[32 * hf + 2 * q], z1 = z[32 * hf + 2 * q + 1];
+              const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
+              const float2 f = __bfloat1622float2(h);
+              const __nv_bfloat162 l = __floats2bfloat162_rn(z0 - f.x, z1 - f.y);
+              ph[q] = *reinterpret_cast<const uint32_t*>(&h);
+              pl[q] = *reinterpret_cast<const uint32_t*>(&l);
+            }
+            const uint32_t col = (uint32_t)(colbase / 2 + 16 * hf);
+            tmem_st16(tmem + lane_addr + ZH_COL + col, ph);
+            tmem_st16(tmem + lane_addr + ZL_COL + col, pl);
           }
-          const uint32_t off = row * 128 + ((ch ^ (row & 7)) << 4);
-          *reinterpret_cast<uint4*>(zhi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-          *reinterpret_cast<uint4*>(zlo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+          tmem_wait_st();
+          fence_before();
+        } else {
+          // split into hi/lo BF16 and store in the 128-byte swizzled K-major layout
+          unsigned char* zhi = zbuf + (colbase / 64) * ZATOM;
+          unsigned char* zlo = zhi + ZBYTES / 2;
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) {
+            uint32_t ph[4], pl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              // hi = bf16x2(z0, z1); lo = bf16x2(z - hi) (packed conversions)
+              const __nv_bfloat162 h = __floats2bfloat162_rn(z[ch * 8 + 2 * q], z[ch * 8 + 2 * q + 1]);
+              const float2 hf = __bfloat1622float2(h);
+              const __nv_bfloat162 l = __floats2bfloat162_rn(z[ch * 8 + 2 * q] - hf.x, z[ch * 8 + 2 * q + 1] - hf.y);
+              ph[q] = *reinterpret_cast<const uint32_t*>(&h);
+              pl[q] = *reinterpret_cast<const uint32_t*>(&l);
+            }
+            const uint32_t off = row * 128 + ((ch ^ (row & 7)) << 4);
+            *reinterpret_cast<uint4*>(zhi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+            *reinterpret_cast<uint4*>(zlo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+          }
+          fence_proxy_async();
         }
-        fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar_zf);
         if (lt == ntg - 1) {
@@ -528,20 +572,23 @@ cudaError_t make_map(CUtensorMap* m, const void* ptr, int64_t cols, int64_t rows
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch(TcArgs& a, dim3 grid, cudaStream_t st, int kc) {
+template <int KC, int ZT>
+cudaError_t launch_geom(TcArgs& a, dim3 grid, cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_regen_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<64>());
-    if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(k_regen_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem_bytes<32>());
+    attr_err = cudaFuncSetAttribute(k_regen_tc<KC, ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_bytes<KC, ZT>());
   });
   if (attr_err != cudaSuccess) return attr_err;
-  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
-  if (kc == 64) k_regen_tc<64><<<grid, NTHREADS, smem_bytes<64>(), st>>>(a);
-  else k_regen_tc<32><<<grid, NTHREADS, smem_bytes<32>(), st>>>(a);
+  k_regen_tc<KC, ZT><<<grid, NTHREADS, smem_bytes<KC, ZT>(), st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch(TcArgs& a, dim3 grid, cudaStream_t st, int kc, int zt) {
+  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
+  if (kc == 64) return zt ? launch_geom<64, 1>(a, grid, st) : launch_geom<64, 0>(a, grid, st);
+  return zt ? launch_geom<32, 1>(a, grid, st) : launch_geom<32, 0>(a, grid, st);
 }
 
 // device error word shared by all launches (checked by the host after each pass)
@@ -556,6 +603,7 @@ int* err_word() {
 }
 
 int view_kc(const TcView& v) { return (v.kc == 32 || v.kc == 64) ? v.kc : ring_kc(); }
+int view_zt(const TcView& v) { return v.zt == 1 ? 1 : 0; }
 
 cudaError_t common_args(const TcView& v, TcArgs& a) {
   memset(&a, 0, sizeof(a));
@@ -610,7 +658,7 @@ cudaError_t tc_write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int6
   if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   a.tM_hi = a.tB_hi;
   a.tM_lo = a.tB_lo;
-  return launch(a, dim3((unsigned)ceil_div(nr, 128)), v.st, view_kc(v));
+  return launch(a, dim3((unsigned)ceil_div(nr, 128)), v.st, view_kc(v), view_zt(v));
 }
 
 cudaError_t tc_pass1(const TcView& v, float* Rpart) {
@@ -629,7 +677,7 @@ cudaError_t tc_pass1(const TcView& v, float* Rpart) {
   if ((e = make_map(&a.tB_lo, v.Xlo, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tM_hi, v.VThi, v.nslots, (int64_t)v.C * v.mpad, v.nslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tM_lo, v.VTlo, v.nslots, (int64_t)v.C * v.mpad, v.nslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
-  return launch(a, dim3((unsigned)(v.fslots / 128), (unsigned)v.R, (unsigned)v.nsplit), v.st, view_kc(v));
+  return launch(a, dim3((unsigned)(v.fslots / 128), (unsigned)v.R, (unsigned)v.nsplit), v.st, view_kc(v), view_zt(v));
 }
 
 cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, int64_t m_block_stride,
@@ -651,7 +699,7 @@ cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloa
   if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tM_hi, Mhi, v.fslots, (int64_t)v.R * v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tM_lo, Mlo, v.fslots, (int64_t)v.R * v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
-  return launch(a, dim3((unsigned)(v.nslots / 128)), v.st, view_kc(v));
+  return launch(a, dim3((unsigned)(v.nslots / 128)), v.st, view_kc(v), view_zt(v));
 }
 
 cudaError_t tc_predict(const TcView& v, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int64_t nrows,
@@ -671,7 +719,7 @@ cudaError_t tc_predict(const TcView& v, const __nv_bfloat16* Xh, const __nv_bflo
   if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tM_hi, Mhi, v.fslots, v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tM_lo, Mlo, v.fslots, v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
-  return launch(a, dim3((unsigned)(nrows / 128)), v.st, view_kc(v));
+  return launch(a, dim3((unsigned)(nrows / 128)), v.st, view_kc(v), view_zt(v));
 }
 
 }  // namespace rff

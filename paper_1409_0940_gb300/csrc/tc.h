@@ -22,6 +22,7 @@ struct TcView {
   float scale;
   int bias_in_mma;                  // 1: b is column d of G and X carries ones there
   int kc;                           // ring K chunk (64 or 32; 0 = library default)
+  int zt;                           // 1: Z tile in tensor memory, 0: in shared memory
   cudaStream_t st;
 };
 

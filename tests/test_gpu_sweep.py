@@ -101,3 +101,23 @@ def test_autotuner_choice_is_reported(rff):
     p = s.profile()
     assert p["tc_kchunk"] in (32, 64) and p["nsplit"] >= 1
     s.close()
+
+
+def test_every_tile_geometry_gives_identical_results(rff, monkeypatch):
+    """The four geometries of the regeneration kernel (ring K chunk 64 or 32, Z tile in shared
+    or tensor memory) issue the same products in the same order: weights and scores agree bitwise."""
+    X, Y = synth.multiclass(n=1500, d=30, m=5, seed=2)
+    kw = dict(prec="split_bf16", loss="hinge", reg="l2", lam=1e-3, sigma=3.0, D=640, R=2, C=2, seed=3, m=5)
+    out = []
+    for g in ("64,0", "64,1", "32,0", "32,1"):
+        monkeypatch.setenv("RFF_TC_GEOMETRY", g)
+        s = rff.Solver(**kw)
+        s.set_data(X, Y)
+        s.solve(8, stats=False)
+        p = s.profile()
+        assert (p["tc_kchunk"], p["tc_z_tmem"]) == tuple(int(x) for x in g.split(","))
+        out.append((s.weights(), s.predict(X[:200])))
+        s.close()
+    for W, P in out[1:]:
+        assert np.array_equal(W, out[0][0])
+        assert np.array_equal(P, out[0][1])
