@@ -67,9 +67,13 @@ typedef enum {
 /* How Z_ij is regenerated and applied. */
 typedef enum {
   RFF_PREC_FP32 = 0,      /* X.G, cos and both chained products in FP32 on the SIMT pipes  */
-  RFF_PREC_SPLIT_BF16 = 1, /* X.G as three BF16 tensor-core products (hi.hi + hi.lo + lo.hi),
-                             FP32 accumulate in TMEM, FP32 cos, chained products again as
-                             three BF16 products of the hi/lo split of both operands       */
+  RFF_PREC_SPLIT_BF16 = 1, /* tensor cores: X.G as three FP16 products (hi.hi + hi.lo +
+                             lo.hi) of the hi/lo splits of X and G, each scaled by a power
+                             of two into |.| <= 2^8 (22 significant bits per operand),
+                             FP32 accumulate in TMEM, FP32 cos; the chained products as
+                             three BF16 products of the hi/lo split of both operands.
+                             Queries beyond 2^15 / (X scale), at least 128 times the
+                             largest training |x|, are refused (RFF_EINVAL)              */
   RFF_PREC_CACHED_Z = 2   /* Z materialised once (set-up, by the split-BF16 regeneration)
                              and kept in device memory as a hi/lo BF16 pair, with a
                              transposed copy: n_slots x D_slots x 8 bytes.  Each iteration
@@ -144,6 +148,12 @@ rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats);
  * sizes its factorisation batches to stay within it.  The GPU analogue of the
  * memory model of Sec. 3 (eq. (mem)). */
 rff_status rff_admm_set_memory_limit(rff_admm_t h, size_t bytes);
+
+/* Moves the handle's work to another CUDA stream (for instance one of higher
+ * priority for scoring a solved model while other solves run).  Waits for the work
+ * already on the current stream; a stream the library created is destroyed, the
+ * new one stays the caller's.  Results do not depend on the stream. */
+rff_status rff_admm_set_stream(rff_admm_t h, void* cuda_stream);
 
 /* Device bytes a solve of n x d data with these parameters holds while it iterates
  * (*resident: data, state, cached factors) and at its peak during set-up with the

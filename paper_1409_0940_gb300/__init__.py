@@ -73,6 +73,7 @@ PROTOTYPES = {
     "rff_admm_set_profiling": (_I32, [_P, ctypes.c_int]),
     "rff_admm_get_profile": (_I32, [_P, ctypes.POINTER(rff_admm_profile)]),
     "rff_admm_set_memory_limit": (_I32, [_P, _SZ]),
+    "rff_admm_set_stream": (_I32, [_P, _P]),
     "rff_admm_estimate_bytes": (_I32, [ctypes.POINTER(rff_admm_params), _I64, _I64, ctypes.POINTER(_SZ),
                                        ctypes.POINTER(_SZ)]),
     "rff_admm_set_lambdas": (_I32, [_P, _P, _I32]),
@@ -236,6 +237,11 @@ def rff_admm_get_profile(h):
 
 def rff_admm_set_memory_limit(h, nbytes):
     _check(lib.rff_admm_set_memory_limit(h, nbytes), h)
+
+
+def rff_admm_set_stream(h, stream):
+    """Move the handle's work to `stream` (a torch.cuda.Stream or a raw cudaStream_t)."""
+    _check(lib.rff_admm_set_stream(h, getattr(stream, "cuda_stream", stream)), h)
 
 
 def rff_admm_estimate_bytes(params, n, d):

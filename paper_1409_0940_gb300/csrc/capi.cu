@@ -49,7 +49,9 @@ struct rff_admm_s {
   int64_t *d_row_slot = nullptr, *d_row_size = nullptr, *d_col_slot = nullptr, *d_col_size = nullptr;
   int64_t* d_zero = nullptr;  // {0}: row block table of a query batch
   float *X32 = nullptr, *Gt32 = nullptr, *bias = nullptr, *Y = nullptr;
-  __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr, *Ghi = nullptr, *Glo = nullptr;
+  // split path: X * xscale and G * gscale as FP16 hi/lo pairs (powers of two, |.| <= 2^8)
+  __half *Xhi = nullptr, *Xlo = nullptr, *Ghi = nullptr, *Glo = nullptr;
+  float xscale = 1.f, gscale = 1.f;
   float *O = nullptr, *Obar = nullptr, *nu = nullptr, *Op = nullptr;
   float* V32 = nullptr;       // FP32 path: V_ij = Obar_ij + nu_i, C x slots x mpad (split path: V^T hi/lo only)
   __nv_bfloat16 *VThi = nullptr, *VTlo = nullptr, *WThi = nullptr, *WTlo = nullptr, *WbThi = nullptr,
@@ -91,16 +93,20 @@ struct rff_admm_s {
     gexec = nullptr;
   }
 
+  // Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the handle's
+  // stream): allocating or releasing it never waits for other handles' work on the
+  // device, which matters when solves and scoring requests share a GPU.
   ~rff_admm_s() {
     drop_graph();
     for (auto e : ev) cudaEventDestroy(e);
     free_all();
-    if (scratch.p) cudaFree(scratch.p);
+    if (scratch.p) cudaFreeAsync(scratch.p, st);
+    cudaStreamSynchronize(st);
     if (own_stream && st) cudaStreamDestroy(st);
   }
   void free_all() {
     for (auto& b : bufs)
-      if (b.p) cudaFree(b.p);
+      if (b.p) cudaFreeAsync(b.p, st);
     bufs.clear();
   }
   rff_status fail(rff_status s, const std::string& msg) {
@@ -127,6 +133,31 @@ TcView tc_view(const rff_admm_s& s);
   } while (0)
 
 namespace {
+
+// Largest power of two s with maxabs * s <= 2^8 (1 when maxabs is 0): the scale of the
+// FP16 split of the X.G operands.
+float pow2_scale(double maxabs) {
+  if (!(maxabs > 0) || !std::isfinite(maxabs)) return 1.f;
+  int e = (int)std::floor(std::log2(256.0 / maxabs));
+  e = std::max(-100, std::min(100, e));
+  return std::ldexp(1.0f, e);
+}
+
+// G ~ N(0, sigma^-2) from Box-Muller with u >= 2^-25 gives |G| <= sqrt(50 ln 2)/sigma
+// < 5.9/sigma; the phase b lies in [0, pi).  Both share the scale of G's copies.
+float g_scale(double sigma) { return pow2_scale(std::max(5.9 / sigma, 3.1415927)); }
+
+// Queries go through the same FP16 scaling as the training rows: |x| xscale must stay
+// below 2^15 (queries up to 2^7 times the largest training |x|).
+rff_status check_query_range(rff_admm_t h, int maxbits) {
+  if (!h->split_path()) return RFF_OK;
+  float qmax = 0.f;
+  memcpy(&qmax, &maxbits, 4);
+  if ((double)qmax * h->xscale < 32768.0) return RFF_OK;
+  return h->fail(RFF_EINVAL, "query values up to " + std::to_string(qmax) +
+                                 " exceed the split path's input range (|x| < " + std::to_string(32768.0 / h->xscale) +
+                                 ", at least 128 times the largest training |x|)");
+}
 
 rff_status check_params(const rff_admm_params* p, std::string& why) {
   if (!p) { why = "params is NULL"; return RFF_EINVAL; }
@@ -161,7 +192,7 @@ template <typename T>
 rff_status dalloc(rff_admm_t h, T*& ptr, size_t count) {
   void* p = nullptr;
   const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = cudaMallocAsync(&p, bytes, h->st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return h->fail(RFF_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
@@ -174,12 +205,11 @@ rff_status dalloc(rff_admm_t h, T*& ptr, size_t count) {
 rff_status ensure_scratch(rff_admm_t h, size_t bytes) {
   if (h->scratch.bytes >= bytes) return RFF_OK;
   if (h->scratch.p) {
-    cudaStreamSynchronize(h->st);
-    cudaFree(h->scratch.p);
+    cudaFreeAsync(h->scratch.p, h->st);
     h->scratch = DevBuf{};
   }
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  if (cudaMallocAsync(&p, bytes, h->st) != cudaSuccess) {
     cudaGetLastError();
     return h->fail(RFF_ENOMEM, "scratch allocation failed");
   }
@@ -378,6 +408,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   CK(cudaStreamSynchronize(h->st));
   h->drop_graph();
   h->free_all();
+  CK(cudaStreamSynchronize(h->st));   // the freed blocks return to the device before it is measured
   h->has_data = h->factored = false;
   h->iters_done = 0;
 
@@ -502,12 +533,18 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   CK(cudaMemcpyAsync(sx, X, xb, kind, s.st));
   CK(cudaMemcpyAsync(sy, Yin, yb, kind, s.st));
   CK(cudaMemsetAsync(s.flag, 0, 16, s.st));
-  CK(launch_finite_check(sx, (int64_t)n * d, 0, s.flag, s.st));
+  CK(launch_finite_check(sx, (int64_t)n * d, 0, s.flag, s.st, reinterpret_cast<unsigned*>(s.flag + 2)));
   const int pm1 = (s.p.loss == RFF_LOSS_HINGE || s.p.loss == RFF_LOSS_LOGISTIC) ? 1 : 0;
   CK(launch_finite_check(sy, (int64_t)n * s.m, pm1, s.flag + 1, s.st));
-  int fl[2] = {0, 0};
-  CK(cudaMemcpyAsync(fl, s.flag, 8, cudaMemcpyDeviceToHost, s.st));
+  int fl[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(fl, s.flag, 12, cudaMemcpyDeviceToHost, s.st));
   CK(cudaStreamSynchronize(s.st));
+  {
+    float xmax = 0.f;
+    memcpy(&xmax, &fl[2], 4);
+    s.xscale = pow2_scale(std::max<double>(xmax, s.bias_col >= 0 ? 1.0 : 0.0));
+    s.gscale = g_scale(s.p.sigma);
+  }
   if (fl[0]) { h->free_all(); return h->fail(RFF_EINVAL, "X contains NaN or Inf"); }
   if (fl[1] & 1) { h->free_all(); return h->fail(RFF_EINVAL, "Y contains NaN or Inf"); }
   if (fl[1] & 2) { h->free_all(); return h->fail(RFF_EINVAL, "hinge/logistic targets must be -1 or +1"); }
@@ -525,7 +562,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   CK(launch_gather_rows(sx, d, d, s.row_of_slot, s.nslots, Xs, s.dld, s.st));
   CK(launch_gather_rows(sy, s.m, s.m, s.row_of_slot, s.nslots, s.Y, s.mpad, s.st));
   if (s.bias_col >= 0) CK(launch_set_column(Xs, s.dld, s.nslots, s.bias_col, 1.f, s.st));
-  if (s.split_path()) CK(launch_split_bf16(Xs, s.nslots * s.dld, s.Xhi, s.Xlo, s.st));
+  if (s.split_path()) CK(launch_split_f16(Xs, s.nslots * s.dld, s.xscale, s.Xhi, s.Xlo, s.st));
 
   // ADMM state: all zero (Sec. 3: "initialize to zero"), then O = prox(Obar - nu) = prox(0)
   const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
@@ -676,7 +713,7 @@ rff_status setup_factors(rff_admm_t h) {
   auto& s = *h;
   const float scale = (float)std::sqrt(2.0 / (double)s.D);
   // random features: G and b from Philox (Sec. 4)
-  CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, s.Ghi, s.Glo, s.bias,
+  CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, s.Ghi, s.Glo, s.gscale, s.bias,
                          s.bias_col, s.st));
   // Gram matrices H_ij = I + Z_ij^T Z_ij (eq. (cache)), in FP64, batched by memory
   int64_t smax = 0;
@@ -786,7 +823,7 @@ rff_status setup_factors(rff_admm_t h) {
     if (zr != RFF_OK) return zr;
   }
   // the set-up scratch (FP64 Gram and inverse batches) is released
-  CK(cudaFree(s.scratch.p));
+  CK(cudaFreeAsync(s.scratch.p, s.st));
   s.scratch = DevBuf{};
   s.factored = true;
   return autotune(h);
@@ -1052,7 +1089,7 @@ rff_status sqdiff(rff_admm_t h, const float* a, const float* b, int64_t n, doubl
 }
 
 // scores S (slots x m_pad) = Z(rows) Wbar, on the handle's training rows or a query batch
-rff_status scores_pass(rff_admm_t h, const float* Xrows32, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl,
+rff_status scores_pass(rff_admm_t h, const float* Xrows32, const __half* Xh, const __half* Xl,
                        int64_t nrows, const int32_t* row_ok, float* out) {
   auto& s = *h;
   if (s.split_path()) {
@@ -1089,6 +1126,7 @@ TcView tc_view(const rff_admm_s& s) {
   v.col_slot = s.col_slot.data(); v.col_size = s.col_size.data();
   v.d_row_slot = s.d_row_slot; v.d_row_size = s.d_row_size; v.d_col_slot = s.d_col_slot; v.d_col_size = s.d_col_size;
   v.scale = (float)std::sqrt(2.0 / (double)s.D);
+  v.inv_xg = 1.f / (s.xscale * s.gscale);
   v.bias_in_mma = s.bias_col >= 0 ? 1 : 0;
   v.kc = s.tc_kc;
   v.zt = s.tc_zt;
@@ -1164,6 +1202,18 @@ rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats) {
 rff_status rff_admm_set_memory_limit(rff_admm_t h, size_t bytes) {
   if (!h) return RFF_EINVAL;
   h->mem_limit = bytes;
+  return RFF_OK;
+}
+
+rff_status rff_admm_set_stream(rff_admm_t h, void* cuda_stream) {
+  if (!h || !cuda_stream) return RFF_EINVAL;
+  h->err.clear();
+  cudaStream_t ns = static_cast<cudaStream_t>(cuda_stream);
+  if (ns == h->st) return RFF_OK;
+  CK(cudaStreamSynchronize(h->st));
+  if (h->own_stream) cudaStreamDestroy(h->st);
+  h->st = ns;
+  h->own_stream = false;
   return RFF_OK;
 }
 
@@ -1252,25 +1302,26 @@ rff_status rff_admm_predict(rff_admm_t h, const float* Xq, int64_t q, float* sco
   if (r != RFF_OK) return r;
   float* stage = static_cast<float*>(s.scratch.p);
   float* xq32 = stage + round_up(chunk * s.d, 64);
-  __nv_bfloat16* xh = reinterpret_cast<__nv_bfloat16*>(xq32 + chunk * s.dld);
-  __nv_bfloat16* xl = xh + chunk * s.dld;
+  __half* xh = reinterpret_cast<__half*>(xq32 + chunk * s.dld);
+  __half* xl = xh + chunk * s.dld;
   float* sc = reinterpret_cast<float*>(xl + chunk * s.dld);
   const cudaMemcpyKind kin = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind kout = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   for (int64_t q0 = 0; q0 < q; q0 += chunk) {
     const int64_t nq = std::min(chunk, q - q0), nqp = round_up(nq, SLOT);
     CK(cudaMemcpyAsync(stage, Xq + q0 * s.d, nq * s.d * 4, kin, s.st));
-    CK(cudaMemsetAsync(s.flag, 0, 4, s.st));
-    CK(launch_finite_check(stage, nq * s.d, 0, s.flag, s.st));
-    int fl = 0;
-    CK(cudaMemcpyAsync(&fl, s.flag, 4, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaMemsetAsync(s.flag, 0, 16, s.st));
+    CK(launch_finite_check(stage, nq * s.d, 0, s.flag, s.st, reinterpret_cast<unsigned*>(s.flag + 2)));
+    int fl[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(fl, s.flag, 12, cudaMemcpyDeviceToHost, s.st));
     CK(cudaStreamSynchronize(s.st));
-    if (fl) return h->fail(RFF_EINVAL, "queries contain NaN or Inf");
+    if (fl[0]) return h->fail(RFF_EINVAL, "queries contain NaN or Inf");
+    if ((r = check_query_range(h, fl[2])) != RFF_OK) return r;
     // rows q0..q0+nq into a slot-padded block (rows beyond nq are zero and discarded)
     CK(cudaMemsetAsync(xq32, 0, nqp * s.dld * 4, s.st));
     CK(launch_gather_rows(stage, s.d, s.d, nullptr, nq, xq32, s.dld, s.st));
     if (s.bias_col >= 0) CK(launch_set_column(xq32, s.dld, nqp, s.bias_col, 1.f, s.st));
-    if (s.split_path()) CK(launch_split_bf16(xq32, nqp * s.dld, xh, xl, s.st));
+    if (s.split_path()) CK(launch_split_f16(xq32, nqp * s.dld, s.xscale, xh, xl, s.st));
     if ((r = scores_pass(h, xq32, xh, xl, nqp, nullptr, sc)) != RFF_OK) return r;
     CK(cudaMemcpy2DAsync(scores + q0 * s.m, s.m * 4, sc, s.mpad * 4, s.m * 4, nq, kout, s.st));
   }
@@ -1408,20 +1459,24 @@ rff_status predict_into_scratch(rff_admm_t h, const float* Xq, int64_t q, float*
                                    ": score the queries in smaller batches");
   char* base = static_cast<char*>(scratch);
   float* xq32 = reinterpret_cast<float*>(base);
-  __nv_bfloat16* xh = reinterpret_cast<__nv_bfloat16*>(base + round_up(x32, 256));
-  __nv_bfloat16* xl = reinterpret_cast<__nv_bfloat16*>(base + round_up(x32, 256) + round_up(xsplit, 256));
+  __half* xh = reinterpret_cast<__half*>(base + round_up(x32, 256));
+  __half* xl = reinterpret_cast<__half*>(base + round_up(x32, 256) + round_up(xsplit, 256));
   float* sc = reinterpret_cast<float*>(base + round_up(x32, 256) + 2 * round_up(xsplit, 256));
-  CK(cudaMemsetAsync(s.flag, 0, 4, s.st));
-  CK(launch_finite_check(Xq, q * s.d, 0, s.flag, s.st));
-  int fl = 0;
-  CK(cudaMemcpyAsync(&fl, s.flag, 4, cudaMemcpyDeviceToHost, s.st));
+  CK(cudaMemsetAsync(s.flag, 0, 16, s.st));
+  CK(launch_finite_check(Xq, q * s.d, 0, s.flag, s.st, reinterpret_cast<unsigned*>(s.flag + 2)));
+  int fl[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(fl, s.flag, 12, cudaMemcpyDeviceToHost, s.st));
   CK(cudaStreamSynchronize(s.st));
-  if (fl) return h->fail(RFF_EINVAL, "queries contain NaN or Inf");
+  if (fl[0]) return h->fail(RFF_EINVAL, "queries contain NaN or Inf");
+  {
+    rff_status rr = check_query_range(h, fl[2]);
+    if (rr != RFF_OK) return rr;
+  }
   // the scratch keeps the previous call's contents: the padding rows are cleared here
   CK(cudaMemsetAsync(xq32, 0, x32, s.st));
   CK(launch_gather_rows(Xq, s.d, s.d, nullptr, q, xq32, s.dld, s.st));
   if (s.bias_col >= 0) CK(launch_set_column(xq32, s.dld, qp, s.bias_col, 1.f, s.st));
-  if (s.split_path()) CK(launch_split_bf16(xq32, qp * s.dld, xh, xl, s.st));
+  if (s.split_path()) CK(launch_split_f16(xq32, qp * s.dld, s.xscale, xh, xl, s.st));
   rff_status r = scores_pass(h, xq32, xh, xl, qp, nullptr, sc);
   if (r != RFF_OK) return r;
   CK(cudaMemcpy2DAsync(scores, s.m * 4, sc, s.mpad * 4, s.m * 4, q, cudaMemcpyDeviceToDevice, s.st));
@@ -1457,7 +1512,7 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t nf = k_hi - k_lo, dld = round_up(d, 64), np = round_up(n, SLOT), fp = round_up(nf, SLOT);
   const size_t bytes = (size_t)np * dld * 4 + (size_t)fp * dld * 4 + (size_t)fp * 4 + (size_t)np * 4 + (size_t)fp * 4 +
-                       (size_t)(np + fp) * dld * 2 * 2 + 64 + 4096;
+                       (size_t)(np + fp) * dld * 2 * 2 + 64 + 64 + 4096;
   char* base = nullptr;
   if (cudaMallocAsync((void**)&base, bytes, st) != cudaSuccess) {
     cudaGetLastError();
@@ -1468,11 +1523,12 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
   float* bias = G32 + fp * dld;
   int32_t* rok = reinterpret_cast<int32_t*>(bias + fp);
   int32_t* fok = rok + np;
-  __nv_bfloat16* Xh = reinterpret_cast<__nv_bfloat16*>(fok + fp);
-  __nv_bfloat16* Xl = Xh + np * dld;
-  __nv_bfloat16* Gh = Xl + np * dld;
-  __nv_bfloat16* Gl = Gh + fp * dld;
+  __half* Xh = reinterpret_cast<__half*>(fok + fp);
+  __half* Xl = Xh + np * dld;
+  __half* Gh = Xl + np * dld;
+  __half* Gl = Gh + fp * dld;
   int64_t* tabs = reinterpret_cast<int64_t*>(Gl + fp * dld);   // {0, n, 0, nf}
+  unsigned* xmaxbits = reinterpret_cast<unsigned*>(tabs + 4);
   std::vector<int32_t> r(np), f(fp);
   const int64_t htab[4] = {0, n, 0, nf};
   for (int64_t i = 0; i < np; ++i) r[i] = i < n ? (int32_t)i : -1;
@@ -1482,9 +1538,23 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
   if (e == cudaSuccess) e = cudaMemcpyAsync(fok, f.data(), fp * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = launch_gather_rows(X, d, d, rok, np, X32, dld, st);
   const int64_t bcol = (prec == RFF_PREC_SPLIT_BF16 && round_up(d + 1, 64) == dld) ? d : -1;
+  // the split path scales X and G by powers of two into the FP16 range (largest |x|, |g| <= 2^8)
+  float xscale = 1.f;
+  const float gscale = g_scale(sigma);
+  if (e == cudaSuccess && prec) {
+    unsigned bits = 0;
+    int* fflag = reinterpret_cast<int*>(xmaxbits + 1);
+    e = cudaMemsetAsync(xmaxbits, 0, 8, st);
+    if (e == cudaSuccess) e = launch_finite_check(X, n * d, 0, fflag, st, xmaxbits);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, xmaxbits, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float xmax = 0.f;
+    memcpy(&xmax, &bits, 4);
+    xscale = pow2_scale(std::max<double>(xmax, bcol >= 0 ? 1.0 : 0.0));
+  }
   if (e == cudaSuccess)
-    e = launch_params_slots(seed, sigma, d, dld, fp, fok, G32, prec ? Gh : nullptr, prec ? Gl : nullptr, bias, bcol,
-                            st);
+    e = launch_params_slots(seed, sigma, d, dld, fp, fok, G32, prec ? Gh : nullptr, prec ? Gl : nullptr, gscale, bias,
+                            bcol, st);
   const float scale = (float)std::sqrt(2.0 / (double)D);
   if (e == cudaSuccess) {
     if (prec == RFF_PREC_FP32) {
@@ -1492,7 +1562,7 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
       e = launch_write_z_simt(za, st);
     } else {
       if (bcol >= 0) e = launch_set_column(X32, dld, np, bcol, 1.f, st);
-      if (e == cudaSuccess) e = launch_split_bf16(X32, np * dld, Xh, Xl, st);
+      if (e == cudaSuccess) e = launch_split_f16(X32, np * dld, xscale, Xh, Xl, st);
       if (e == cudaSuccess) {
         const int64_t zero = 0;
         TcView v{};
@@ -1501,7 +1571,7 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
         v.nslots = np; v.fslots = fp; v.dld = dld; v.mpad = 16; v.R = 1; v.C = 1; v.nsplit = 1;
         v.row_slot = &zero; v.row_size = &n; v.col_slot = &zero; v.col_size = &nf;
         v.d_row_slot = tabs; v.d_row_size = tabs + 1; v.d_col_slot = tabs + 2; v.d_col_size = tabs + 3;
-        v.scale = scale; v.bias_in_mma = bcol >= 0 ? 1 : 0; v.st = st;
+        v.scale = scale; v.inv_xg = 1.f / (xscale * gscale); v.bias_in_mma = bcol >= 0 ? 1 : 0; v.st = st;
         e = tc_write_z(v, 0, n, 0, nf, Z, nf);
       }
     }

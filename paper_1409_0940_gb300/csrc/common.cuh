@@ -3,6 +3,7 @@
 // every kernel indexes.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -82,6 +83,17 @@ __device__ __forceinline__ float cos_rr(float x) {
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   hi = __float2bfloat16_rn(x);
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// ------------------------------------------------------------------ scaled FP16 split
+// The X.G operands: x * scale (scale a power of two, so the product is exact) =
+// hi + lo + O(2^-22 |x * scale|) with hi = fp16(x scale), lo = fp16(x scale - hi).
+// The scale keeps |x scale| <= 2^8 (far from the FP16 maximum, 65504) while values
+// far below the largest keep an absolute error of at most 2^-25 in scaled units.
+__device__ __forceinline__ void split_f16(float x, float scale, __half& hi, __half& lo) {
+  const float xs = x * scale;
+  hi = __float2half_rn(xs);
+  lo = __float2half_rn(xs - __half2float(hi));
 }
 
 }  // namespace rff

@@ -325,6 +325,20 @@ cudaError_t launch_potrf_diag(const DiagJob* jobs_dev, int njobs, int kcol, cuda
 //   L Y = I:       Y_k = L_kk^-1 B_k;  B_i -= L_ik Y_k   (i > k)
 //   L^T Q = Y:     Q_k = L_kk^-T Y_k;  Y_i -= L_ki^T Q_k (i < k)
 // Descriptors live in `dev_scratch` (>= factor_scratch_bytes bytes).
+// Q[r][c] = Q[c][r] for c > r (the upper triangle from the lower)
+__global__ void k_mirror_lower(double* __restrict__ Q, int64_t ld, int64_t s) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= s * s) return;
+  const int64_t r = t / s, c = t % s;
+  if (c > r) Q[r * ld + c] = Q[c * ld + r];
+}
+
+cudaError_t launch_mirror_lower(double* Q, int64_t ld, int64_t s, cudaStream_t st) {
+  if (s <= 1) return cudaSuccess;
+  k_mirror_lower<<<(unsigned)ceil_div(s * s, 256), 256, 0, st>>>(Q, ld, s);
+  return cudaGetLastError();
+}
+
 size_t factor_scratch_bytes(int njobs, int smax) {
   const int nb = (int)ceil_div(smax, 64);
   return (size_t)njobs * nb * 64 * 64 * sizeof(double) + (size_t)njobs * sizeof(DiagJob) * nb +
@@ -373,14 +387,20 @@ cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, 
                                             J.A + (c0 + 64) * J.ld + c0 + 64, J.A + (c0 + 64) * J.ld + c0 + 64,
                                             rest, rest, bs, J.ld, J.ld, J.ld, J.ld};
       at(1, k, b) = tr;
+      // Inverse Q = L^-T L^-1 from Q = I: the forward sweep (L Y = I) touches only the
+      // columns up to the diagonal block of block row k (Y is lower triangular); the
+      // backward sweep (L^T Q = Y) computes the block lower triangle of the symmetric Q,
+      // which needs the same columns; the strict upper triangle is mirrored afterwards.
+      // s^3/3 flops per sweep instead of s^3.
       GemmDesc fa = z, fb = z, ba = z, bb = z;
+      const int ncol = (int)(c0 + bs);
       if (invert && bs > 0) {
-        fa = GemmDesc{Ikk, J.Q + c0 * J.ldq, nullptr, J.Q + c0 * J.ldq, bs, J.s, bs, 64, J.ldq, 0, J.ldq};
+        fa = GemmDesc{Ikk, J.Q + c0 * J.ldq, nullptr, J.Q + c0 * J.ldq, bs, ncol, bs, 64, J.ldq, 0, J.ldq};
         if (rest > 0) fb = GemmDesc{J.A + (c0 + 64) * J.ld + c0, J.Q + c0 * J.ldq, J.Q + (c0 + 64) * J.ldq,
-                                    J.Q + (c0 + 64) * J.ldq, rest, J.s, bs, J.ld, J.ldq, J.ldq, J.ldq};
+                                    J.Q + (c0 + 64) * J.ldq, rest, ncol, bs, J.ld, J.ldq, J.ldq, J.ldq};
         ba = fa;
-        if (c0 > 0) bb = GemmDesc{J.A + c0 * J.ld, J.Q + c0 * J.ldq, J.Q, J.Q, (int)c0, J.s, bs, J.ld, J.ldq, J.ldq,
-                                  J.ldq};
+        if (c0 > 0) bb = GemmDesc{J.A + c0 * J.ld, J.Q + c0 * J.ldq, J.Q, J.Q, (int)c0, (int)c0, bs, J.ld, J.ldq,
+                                  J.ldq, J.ldq};
       }
       at(2, k, b) = fa;
       at(3, k, b) = fb;
@@ -401,17 +421,19 @@ cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, 
   }
   if (!invert) return cudaSuccess;
   for (int k = 0; k < nb; ++k) {
-    const int c0 = k * 64, rest = std::max(0, smax - c0 - 64);
-    if ((e = launch_gemm_f64(dev(2, k), nj, 64, smax, 0, 0, 1.0, 0.0, 0, st)) != cudaSuccess) return e;
+    const int c0 = k * 64, rest = std::max(0, smax - c0 - 64), ncol = std::min(smax, c0 + 64);
+    if ((e = launch_gemm_f64(dev(2, k), nj, 64, ncol, 0, 0, 1.0, 0.0, 0, st)) != cudaSuccess) return e;
     if (rest > 0)
-      if ((e = launch_gemm_f64(dev(3, k), nj, rest, smax, 0, 0, -1.0, 1.0, 0, st)) != cudaSuccess) return e;
+      if ((e = launch_gemm_f64(dev(3, k), nj, rest, ncol, 0, 0, -1.0, 1.0, 0, st)) != cudaSuccess) return e;
   }
   for (int k = nb - 1; k >= 0; --k) {
-    const int c0 = k * 64;
-    if ((e = launch_gemm_f64(dev(4, k), nj, 64, smax, 1, 0, 1.0, 0.0, 0, st)) != cudaSuccess) return e;
+    const int c0 = k * 64, ncol = std::min(smax, c0 + 64);
+    if ((e = launch_gemm_f64(dev(4, k), nj, 64, ncol, 1, 0, 1.0, 0.0, 0, st)) != cudaSuccess) return e;
     if (c0 > 0)
-      if ((e = launch_gemm_f64(dev(5, k), nj, c0, smax, 1, 0, -1.0, 1.0, 0, st)) != cudaSuccess) return e;
+      if ((e = launch_gemm_f64(dev(5, k), nj, c0, c0, 1, 0, -1.0, 1.0, 0, st)) != cudaSuccess) return e;
   }
+  for (const auto& J : jobs)
+    if ((e = launch_mirror_lower(J.Q, J.ldq, J.s, st)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 

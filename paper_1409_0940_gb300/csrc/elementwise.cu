@@ -29,6 +29,13 @@ __global__ void k_set_column(float* __restrict__ X, int64_t ld, int64_t rows, in
   if (r < rows) X[r * ld + col] = v;
 }
 
+__global__ void k_split_f16(const float* __restrict__ src, int64_t n, float scale, __half* __restrict__ hi,
+                            __half* __restrict__ lo) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  split_f16(src[t], scale, hi[t], lo[t]);
+}
+
 __global__ void k_split(const float* __restrict__ src, int64_t n, __nv_bfloat16* __restrict__ hi,
                         __nv_bfloat16* __restrict__ lo) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -412,14 +419,24 @@ __global__ void k_f64_to_f32(const double* __restrict__ s, float* __restrict__ d
 }
 
 // flag |= 1 for a NaN/Inf entry; with pm1, flag |= 2 for an entry outside {-1, +1}
-__global__ void k_finite(const float* __restrict__ x, int64_t n, int pm1, int* __restrict__ flag) {
+// flag |= 1 for NaN/Inf, 2 for a value other than +-1 (pm1); maxbits = max |x| of the
+// finite values as float bits (unsigned order equals float order for x >= 0)
+__global__ void k_finite(const float* __restrict__ x, int64_t n, int pm1, int* __restrict__ flag,
+                         unsigned* __restrict__ maxbits) {
   int f = 0;
+  float mx = 0.f;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const float v = x[e];
     if (!isfinite(v)) f |= 1;
+    else mx = fmaxf(mx, fabsf(v));
     if (pm1 && v != 1.f && v != -1.f) f |= 2;
   }
   if (f) atomicOr(flag, f);
+  if (maxbits) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(maxbits, __float_as_uint(mx));
+  }
 }
 
 __global__ void k_set_diag(double* __restrict__ A, int64_t ld, int64_t s, double v) {
@@ -441,6 +458,12 @@ cudaError_t launch_gather_rows(const float* src, int64_t lds, int64_t w, const i
 cudaError_t launch_set_column(float* X, int64_t ld, int64_t rows, int64_t col, float v, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
   k_set_column<<<nblk(rows), 256, 0, st>>>(X, ld, rows, col, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_f16(const float* src, int64_t n, float scale, __half* hi, __half* lo, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_split_f16<<<nblk(n), 256, 0, st>>>(src, n, scale, hi, lo);
   return cudaGetLastError();
 }
 
@@ -539,9 +562,9 @@ cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, cudaStream_t st) {
+cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, cudaStream_t st, unsigned* maxbits) {
   if (n <= 0) return cudaSuccess;
-  k_finite<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4096), 256, 0, st>>>(x, n, pm1, flag);
+  k_finite<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4096), 256, 0, st>>>(x, n, pm1, flag, maxbits);
   return cudaGetLastError();
 }
 

@@ -54,9 +54,10 @@ struct ZArgs {
 cudaError_t launch_philox_raw(const uint32_t* ctr, uint64_t seed, int64_t n, uint32_t* out, cudaStream_t st);
 cudaError_t launch_params_rowmajor(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t nk, float* G,
                                    float* b, cudaStream_t st);
-// bias_col >= 0: the BF16 copies carry b in that column (inputs then carry ones there)
+// Ghi/Glo: the FP16 split of G * gscale; bias_col >= 0: they carry b * gscale in that
+// column (inputs then carry ones there)
 cudaError_t launch_params_slots(uint64_t seed, double sigma, int64_t d, int64_t ld, int64_t nslots,
-                                const int32_t* feat_of_slot, float* Gt, __nv_bfloat16* Ghi, __nv_bfloat16* Glo,
+                                const int32_t* feat_of_slot, float* Gt, __half* Ghi, __half* Glo, float gscale,
                                 float* bias, int64_t bias_col, cudaStream_t st);
 
 // regen_simt.cu
@@ -109,6 +110,8 @@ cudaError_t launch_gather_rows(const float* src, int64_t lds, int64_t w, const i
                                float* dst, int64_t ld, cudaStream_t st);
 cudaError_t launch_set_column(float* X, int64_t ld, int64_t rows, int64_t col, float v, cudaStream_t st);
 cudaError_t launch_split_bf16(const float* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st);
+// hi/lo FP16 split of src * scale (scale a power of two)
+cudaError_t launch_split_f16(const float* src, int64_t n, float scale, __half* hi, __half* lo, cudaStream_t st);
 cudaError_t launch_prox_loss(int loss, const float* V, const float* Y, int64_t n, int m, int64_t ld, float t,
                              int newton, float* out, cudaStream_t st);
 cudaError_t launch_prox_reg(int reg, const float* V, const float* mu, int64_t n, float tau, float* out,
@@ -142,7 +145,8 @@ cudaError_t launch_loss_partials(int loss, const float* Y, const float* S, const
 cudaError_t launch_reg_partials(int reg, const float* W, int64_t n, double* partials, int nblocks, cudaStream_t st,
                                 const float* w = nullptr, int ncol = 1);
 cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
-cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, cudaStream_t st);
+cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, cudaStream_t st,
+                                unsigned* maxbits = nullptr);
 cudaError_t launch_set_diag(double* A, int64_t ld, int64_t s, double v, cudaStream_t st);
 
 }  // namespace rff

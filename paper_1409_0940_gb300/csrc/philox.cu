@@ -66,7 +66,7 @@ __global__ void k_params_rowmajor(uint32_t k0, uint32_t k1, double sigma, int64_
 // Padding features and the columns d..ld-1 are written as zeros.
 __global__ void k_params_slots(uint32_t k0, uint32_t k1, double sigma, int64_t d, int64_t ld, int64_t nslots,
                                const int32_t* __restrict__ feat_of_slot, float* __restrict__ Gt,
-                               __nv_bfloat16* __restrict__ Ghi, __nv_bfloat16* __restrict__ Glo,
+                               __half* __restrict__ Ghi, __half* __restrict__ Glo, float gscale,
                                float* __restrict__ bias, int64_t bias_col) {
   const int64_t nq = ld / 4;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -83,10 +83,10 @@ __global__ void k_params_slots(uint32_t k0, uint32_t k1, double sigma, int64_t d
     const float v = (r < d) ? g[e] : 0.f;
     if (Gt) Gt[p * ld + r] = v;
     if (Ghi) {
-      // the BF16 copies may carry the phase b in column bias_col (the input then
+      // the FP16 copies may carry the phase b in column bias_col (the input then
       // carries a column of ones there), so the product X G already includes b
-      __nv_bfloat16 hi, lo;
-      split_bf16(r == bias_col ? ph : v, hi, lo);
+      __half hi, lo;
+      split_f16(r == bias_col ? ph : v, gscale, hi, lo);
       Ghi[p * ld + r] = hi;
       Glo[p * ld + r] = lo;
     }
@@ -109,12 +109,12 @@ cudaError_t launch_params_rowmajor(uint64_t seed, double sigma, int64_t d, int64
 }
 
 cudaError_t launch_params_slots(uint64_t seed, double sigma, int64_t d, int64_t ld, int64_t nslots,
-                                const int32_t* feat_of_slot, float* Gt, __nv_bfloat16* Ghi, __nv_bfloat16* Glo,
+                                const int32_t* feat_of_slot, float* Gt, __half* Ghi, __half* Glo, float gscale,
                                 float* bias, int64_t bias_col, cudaStream_t st) {
   const int64_t total = nslots * (ld / 4);
   if (total <= 0) return cudaSuccess;
   k_params_slots<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>((uint32_t)seed, (uint32_t)(seed >> 32), sigma,
-                                                                   d, ld, nslots, feat_of_slot, Gt, Ghi, Glo, bias,
+                                                                   d, ld, nslots, feat_of_slot, Gt, Ghi, Glo, gscale, bias,
                                                                    bias_col);
   return cudaGetLastError();
 }

@@ -39,8 +39,10 @@ struct Model {
   int64_t d = 0;
   int32_t m = 0;
   std::mutex use;   // one request at a time on a handle
+  cudaStream_t score_stream = nullptr;   // highest priority: scoring is not queued behind solves
   ~Model() {
     if (h) rff_admm_destroy(h);
+    if (score_stream) cudaStreamDestroy(score_stream);
   }
 };
 
@@ -129,6 +131,16 @@ struct rff_server_s {
     if (st == RFF_OK) st = rff_admm_set_memory_limit(model->h, r.peak);
     if (st == RFF_OK) st = rff_admm_set_data(model->h, r.X.data(), r.Y.data(), r.n, r.d, 0);
     if (st == RFF_OK) st = rff_admm_solve(model->h, r.iters, nullptr);
+    if (st == RFF_OK) {
+      // a solved model scores on a stream of the highest priority, so the blocks of its
+      // scoring kernels are scheduled ahead of those of solves still running
+      int lo = 0, hi = 0;
+      if (cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+          cudaStreamCreateWithPriority(&model->score_stream, cudaStreamNonBlocking, hi) == cudaSuccess)
+        st = rff_admm_set_stream(model->h, model->score_stream);
+      else
+        cudaGetLastError();
+    }
     std::vector<float>().swap(r.X);
     std::vector<float>().swap(r.Y);
     {

@@ -83,6 +83,7 @@ struct TcArgs {
   const int32_t* a_ok;
   const int32_t* b_ok;
   float scale;
+  float inv_xg;                             // X.G accumulator -> X G (1 / (xscale gscale))
   const int64_t* row_slot;
   const int64_t* row_size;
   const int64_t* col_slot;
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
   } else if (warp == 1) {
     // ================= MMA issuer =================
     if (lane == 0) {
-      const uint32_t id1 = idesc_bf16(128, 128);
+      const uint32_t id1 = idesc_f16(128, 128);    // X.G: scaled FP16 splits
       const uint32_t id2 = idesc_bf16(128, a.mpad);
       uint32_t it = 0;
       int t = 0;            // B tile index (global)
@@ -401,6 +402,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
     // zero there), and materialisation writes only the valid window.  The phase b
     // is either part of the product (column of ones in X) or added here.
     const bool add_bias = !a.bias_in_mma;
+    const float inv_xg = a.inv_xg;            // power of two: the rescaling is exact
     const float bias_a = (add_bias && a.mode == MODE_PASS1) ? a.bias[arow] : 0.f;
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     int t = 0;
@@ -426,11 +428,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
 #pragma unroll
           for (int c = 0; c < 64; ++c) {
             const float ph = (a.mode == MODE_PASS1) ? bias_a : __ldg(bcol + c);
-            z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) + ph);
+            z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg + ph);
           }
         } else {
 #pragma unroll
-          for (int c = 0; c < 64; ++c) z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]));
+          for (int c = 0; c < 64; ++c) z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg);
         }
         if (!chain) {
           // materialise Z = sqrt(2/D) cos(...) (float32) inside the window
@@ -614,6 +616,7 @@ cudaError_t common_args(const TcView& v, TcArgs& a) {
   a.nsplit = v.nsplit;
   a.bias = v.bias;
   a.scale = v.scale;
+  a.inv_xg = v.inv_xg;
   a.bias_in_mma = v.bias_in_mma;
   a.fslots = v.fslots;
   a.err = err_word();
@@ -702,7 +705,7 @@ cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloa
   return launch(a, dim3((unsigned)(v.nslots / 128)), v.st, view_kc(v), view_zt(v));
 }
 
-cudaError_t tc_predict(const TcView& v, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int64_t nrows,
+cudaError_t tc_predict(const TcView& v, const __half* Xh, const __half* Xl, int64_t nrows,
                        const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, float* out) {
   if (nrows <= 0) return cudaSuccess;
   if (nrows % 128) return cudaErrorInvalidValue;

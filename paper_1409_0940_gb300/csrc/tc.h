@@ -10,8 +10,8 @@ namespace rff {
 // What the tensor-core passes need from a solver handle.  Host arrays (row_slot,
 // ...) describe the block grid; device arrays hold the data in slot layout.
 struct TcView {
-  const __nv_bfloat16 *Xhi, *Xlo;   // nslots x dld
-  const __nv_bfloat16 *Ghi, *Glo;   // fslots x dld
+  const __half *Xhi, *Xlo;          // nslots x dld, FP16 split of X * xscale
+  const __half *Ghi, *Glo;          // fslots x dld, FP16 split of G * gscale
   const __nv_bfloat16 *VThi, *VTlo; // C x mpad x nslots (pass-1 chain operand)
   const float* bias;                // fslots
   const int32_t *row_ok, *feat_ok;  // slot tables, -1 = padding
@@ -20,6 +20,7 @@ struct TcView {
   const int64_t *row_slot, *row_size, *col_slot, *col_size;  // host
   const int64_t *d_row_slot, *d_row_size, *d_col_slot, *d_col_size;  // device copies
   float scale;
+  float inv_xg;                     // 1 / (xscale gscale): the X.G accumulator times this is X G
   int bias_in_mma;                  // 1: b is column d of G and X carries ones there
   int kc;                           // ring K chunk (64 or 32; 0 = library default)
   int zt;                           // 1: Z tile in tensor memory, 0: in shared memory
@@ -38,7 +39,7 @@ cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloa
 // Error word of the tensor-core kernels (bounded waits that gave up); reads and clears it.
 // Synchronises the device.  0 = no error.
 int tc_error_word();
-cudaError_t tc_predict(const TcView& v, const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int64_t nrows,
+cudaError_t tc_predict(const TcView& v, const __half* Xh, const __half* Xl, int64_t nrows,
                        const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, float* out);
 
 

@@ -179,3 +179,47 @@ def test_device_pointers_match_host_pointers(rff):
     assert np.array_equal(sq.cpu().numpy(), a.predict(X[:50]))
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "cached_z"])
+def test_split_path_query_range(rff, prec):
+    """The split path scales X into the FP16 range from the training data: queries up to 128x the
+    largest training |x| score (and agree with the FP32 path's features to the split precision);
+    larger ones are refused instead of overflowing.  The FP32 path takes any finite query."""
+    X, y = synth.ridge(n=600, d=7, seed=4)
+    xmax = float(np.abs(X).max())
+    kw = dict(loss="squared", reg="l2", lam=1e-3, sigma=50.0, D=256, R=1, C=2, seed=5, m=1)
+    s = rff.Solver(prec=prec, **kw)
+    s.set_data(X, y)
+    s.solve(5, stats=False)
+    f = rff.Solver(prec="fp32", **kw)
+    f.set_data(X, y)
+    f.solve(5, stats=False)
+    big = (X[:40] / xmax * 100.0 * xmax).astype(np.float32)
+    a, b = s.predict(big), f.predict(big)
+    assert np.isfinite(a).all()
+    assert np.abs(a - b).max() < 1e-3 * max(np.abs(b).max(), 1e-6)
+    with pytest.raises(rff.RffError) as e:
+        s.predict((X[:4] * 1000.0).astype(np.float32))
+    assert e.value.status == rff.RFF_EINVAL
+    assert np.isfinite(f.predict((X[:4] * 1000.0).astype(np.float32))).all()
+    s.close()
+    f.close()
+
+
+def test_set_stream_mid_solve_keeps_results(rff):
+    X, Y = synth.multiclass(n=700, d=9, m=3, seed=6)
+    kw = dict(prec="split_bf16", loss="hinge", reg="l2", lam=1e-3, sigma=2.0, D=256, R=2, C=2, seed=1, m=3)
+    a = rff.Solver(**kw)
+    a.set_data(X, Y)
+    a.solve(10, stats=False)
+    b = rff.Solver(**kw)
+    b.set_data(X, Y)
+    b.solve(4, stats=False)
+    hp = torch.cuda.Stream(priority=-1)
+    rff.rff_admm_set_stream(b.h, hp)
+    b.solve(6, stats=False)
+    assert np.array_equal(a.weights(), b.weights())
+    assert np.array_equal(a.predict(X[:50]), b.predict(X[:50]))
+    a.close()
+    b.close()
