@@ -53,8 +53,11 @@ struct rff_admm_s {
   __half *Xhi = nullptr, *Xlo = nullptr, *Ghi = nullptr, *Glo = nullptr;
   float xscale = 1.f, gscale = 1.f;
   float *O = nullptr, *Obar = nullptr, *nu = nullptr, *Op = nullptr;
-  float* V32 = nullptr;       // FP32 path: V_ij = Obar_ij + nu_i, C x slots x mpad (split path: V^T hi/lo only)
-  __nv_bfloat16 *VThi = nullptr, *VTlo = nullptr, *WThi = nullptr, *WTlo = nullptr, *WbThi = nullptr,
+  float* V32 = nullptr;       // V_ij = Obar_ij + nu_i, C x slots x mpad
+  // split path: the chained operands V^T, W'^T, Wbar^T as FP16 hi/lo pairs, each scaled by
+  // f16_scale(max |.|); the maxima (float bits) live in amax[0..2] = V, W', Wbar
+  unsigned* amax = nullptr;
+  __half *VThi = nullptr, *VTlo = nullptr, *WThi = nullptr, *WTlo = nullptr, *WbThi = nullptr,
                 *WbTlo = nullptr;
   float *W = nullptr, *Wbar = nullptr, *mu = nullptr, *What = nullptr, *muij = nullptr, *rhs = nullptr,
         *Rpart = nullptr;
@@ -69,7 +72,8 @@ struct rff_admm_s {
   int nqjobs = 0;
   // cached-Z precision: Z (n_slots x D_slots) and Z^T as hi/lo pairs, and the jobs of
   // the two streamed passes
-  __nv_bfloat16 *Zhi = nullptr, *Zlo = nullptr, *ZThi = nullptr, *ZTlo = nullptr;
+  __half *Zhi = nullptr, *Zlo = nullptr, *ZThi = nullptr, *ZTlo = nullptr;   // FP16 split of zscale Z
+  float zscale = 1.f;
   SgJob *p1jobs = nullptr, *p2jobs = nullptr;
   int np1 = 0, np2 = 0, nsplit_cz = 1;
   std::vector<double> lam_col;  // lambda of each output column (empty: params.lambda for all)
@@ -223,10 +227,10 @@ size_t working_set_bytes(const rff_admm_s& s) {
   size_t t = 0;
   t += (size_t)s.nslots * 4 + (size_t)s.fslots * 4 * 2;
   if (s.split_path()) t += (size_t)s.nslots * s.dld * b2 * 2 + (size_t)s.fslots * s.dld * b2 * 2;
-  else t += (size_t)s.nslots * s.dld * f + (size_t)s.fslots * s.dld * f;
+  if (!s.split_path() || s.cached_z()) t += (size_t)s.nslots * s.dld * f + (size_t)s.fslots * s.dld * f;
   t += (size_t)s.fslots * f;
   t += (size_t)s.nslots * s.mpad * f * (4 + 2);                 // Y, O, Obar, nu, nu_old, Obar_old
-  t += (size_t)s.C * s.nslots * s.mpad * f * (s.split_path() ? 1 : 2);   // Op (+ V32 on the FP32 path)
+  t += (size_t)s.C * s.nslots * s.mpad * f * 2;                 // Op, V32
   if (s.split_path()) t += (size_t)s.C * s.nslots * s.mpad * b2 * 2;
   t += (size_t)s.fslots * s.mpad * f * 5;                       // W, Wbar, mu, mu_old, Wbar_old
   t += (size_t)s.R * s.fslots * s.mpad * f * (3 + s.nsplit_max);    // What, muij, muij_old, Rpart
@@ -305,7 +309,10 @@ void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
     s.t_loss = (float)(1.0 / (nn * s.p.rho));
     s.t_reg = (float)(s.p.lambda / s.p.rho);
   }
-  // pass-1 row splits: enough CTAs for two waves on the device
+  // pass-1 row splits: enough CTAs for two waves on the device and, on the tensor-core
+  // path, at most ~6400 rows per split: the FP32 accumulator of the tensor cores rounds
+  // toward zero at every accumulation, so its error grows with the chain length; the
+  // partial sums of the splits are added in FP32 with round-to-nearest afterwards
   {
     int nsm = 148, dev = 0;
     cudaGetDevice(&dev);
@@ -314,9 +321,15 @@ void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
     const int64_t ftiles = s.fslots / tile;
     int64_t min_rows = n;
     for (int i = 0; i < s.R; ++i) min_rows = std::min(min_rows, s.row_size[i]);
-    const int64_t want = ceil_div(2 * (int64_t)nsm, ftiles * s.R);
+    int64_t want = ceil_div(2 * (int64_t)nsm, ftiles * s.R);
+    if (s.split_path()) want = std::max<int64_t>(want, ceil_div(min_rows, 6400));
     const int64_t cap = std::min<int64_t>(ceil_div(min_rows, tile), 64);
     s.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
+    // RFF_PASS1_SPLITS=k fixes the row splits of pass 1 (bounded by one 128-row tile each)
+    if (const char* e = getenv("RFF_PASS1_SPLITS")) {
+      const int k = atoi(e);
+      if (k >= 1) s.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(k, ceil_div(min_rows, tile)));
+    }
     s.nsplit_max = s.nsplit;
     // cached-Z pass 1 (one CTA per 128 features x row range, two CTAs per SM): about
     // twelve waves of jobs, every split at least eight 128-row tiles of every row block
@@ -447,7 +460,10 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
     AL(s.WTlo, (int64_t)s.R * s.mpad * s.fslots);
     AL(s.WbThi, s.mpad * s.fslots);
     AL(s.WbTlo, s.mpad * s.fslots);
-  } else {
+  }
+  // FP32 copies of X and G: the SIMT path's operands, and on the cached-Z path the inputs
+  // of its one-time FP32 materialisation of Z (round-to-nearest FMA chains for X.G)
+  if (!s.split_path() || s.cached_z()) {
     AL(s.X32, s.nslots * s.dld);
     AL(s.Gt32, s.fslots * s.dld);
   }
@@ -459,7 +475,8 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   AL(s.nu_old, s.nslots * s.mpad);
   AL(s.Obar_old, s.nslots * s.mpad);
   AL(s.Op, (int64_t)s.C * s.nslots * s.mpad);
-  if (!s.split_path()) AL(s.V32, (int64_t)s.C * s.nslots * s.mpad);
+  AL(s.V32, (int64_t)s.C * s.nslots * s.mpad);
+  AL(s.amax, 4);
   AL(s.W, s.fslots * s.mpad);
   AL(s.Wbar, s.fslots * s.mpad);
   AL(s.mu, s.fslots * s.mpad);
@@ -550,7 +567,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   if (fl[1] & 2) { h->free_all(); return h->fail(RFF_EINVAL, "hinge/logistic targets must be -1 or +1"); }
 
   float* Xs = s.X32;
-  if (s.split_path()) {
+  if (s.split_path() && !s.cached_z()) {
     // the float32 slot copy lives in scratch only long enough to split it
     if ((st = ensure_scratch(h, xb + yb + (size_t)s.nslots * s.dld * 4 + 512)) != RFF_OK) { h->free_all(); return st; }
     sx = static_cast<float*>(h->scratch.p);
@@ -567,7 +584,8 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   // ADMM state: all zero (Sec. 3: "initialize to zero"), then O = prox(Obar - nu) = prox(0)
   const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
   for (float* b : {s.O, s.Obar, s.nu}) CK(cudaMemsetAsync(b, 0, rowb, s.st));
-  if (s.V32) CK(cudaMemsetAsync(s.V32, 0, rowb * s.C, s.st));
+  CK(cudaMemsetAsync(s.V32, 0, rowb * s.C, s.st));
+  CK(cudaMemsetAsync(s.amax, 0, 16, s.st));
   CK(cudaMemsetAsync(s.Op, 0, rowb * s.C, s.st));
   for (float* b : {s.W, s.Wbar, s.mu}) CK(cudaMemsetAsync(b, 0, colb, s.st));
   for (float* b : {s.What, s.muij}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
@@ -629,7 +647,7 @@ rff_status autotune(rff_admm_t h) {
       for (int rep = 0; rep < 2; ++rep) {     // first run warms caches and descriptors
         CK(cudaEventRecord(e0, s.st));
         CK(tc_pass1(tc_view(s), s.Rpart));
-        CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1));
+        CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + 1));
         CK(cudaEventRecord(e1, s.st));
         CK(cudaEventSynchronize(e1));
         CK(cudaEventElapsedTime(&ms, e0, e1));
@@ -651,20 +669,26 @@ rff_status autotune(rff_admm_t h) {
   return RFF_OK;
 }
 
-// Cached-Z precision: Z (all row slots x all feature slots, padding included) and its
-// transpose as hi/lo BF16 pairs, computed by the split-BF16 regeneration kernel in row
-// chunks staged in FP32, and the job tables of the two streamed passes.
+// Cached-Z precision: Z (all row slots x all feature slots) and its transpose as scaled
+// FP16 hi/lo pairs, computed once in FP32 on the SIMT pipes (X.G as round-to-nearest
+// FMA chains: the tensor cores' accumulator rounds toward zero at every step, which
+// for X.G costs accuracy that one-time work need not give up), staged in row chunks,
+// and the job tables of the two streamed passes.
 rff_status materialise_z(rff_admm_t h) {
   auto& s = *h;
   const int64_t chunk = std::max<int64_t>(128, ((int64_t)(256u << 20) / (s.fslots * 4)) / 128 * 128);
   rff_status rs = ensure_scratch(h, (size_t)chunk * s.fslots * 4);
   if (rs != RFF_OK) return rs;
   float* zc = static_cast<float*>(s.scratch.p);
+  s.zscale = pow2_scale(std::sqrt(2.0 / (double)s.D));   // |Z| <= sqrt(2/D)
   for (int64_t r0 = 0; r0 < s.nslots; r0 += chunk) {
     const int64_t nr = std::min(chunk, s.nslots - r0);
-    CK(tc_write_z(tc_view(s), r0, nr, 0, s.fslots, zc, s.fslots));
-    CK(launch_split_bf16(zc, nr * s.fslots, s.Zhi + r0 * s.fslots, s.Zlo + r0 * s.fslots, s.st));
-    CK(launch_transpose_split(zc, nr, (int)s.fslots, 1, 0, s.ZThi + r0, s.ZTlo + r0, s.nslots, 0, s.st));
+    ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, (float)std::sqrt(2.0 / (double)s.D), s.row_of_slot,
+             s.feat_of_slot, r0, nr, 0, s.fslots, zc, s.fslots};
+    CK(launch_write_z_simt(za, s.st));
+    CK(launch_split_f16(zc, nr * s.fslots, s.zscale, s.Zhi + r0 * s.fslots, s.Zlo + r0 * s.fslots, s.st));
+    CK(launch_transpose_split_f16(zc, nr, (int)s.fslots, 1, 0, s.ZThi + r0, s.ZTlo + r0, s.nslots, 0, s.zscale,
+                                  nullptr, s.st));
   }
   // pass 2: one job per (128-row tile, column block j), K = the features of block j
   std::vector<SgJob> j2, j1;
@@ -679,7 +703,6 @@ rff_status materialise_z(rff_admm_t h) {
       jb.b_k0 = (int32_t)s.col_slot[j];
       jb.nk = (int32_t)ceil_div(s.col_size[j], 32);
       jb.out = ((int64_t)j * s.nslots + rt * 128) * s.mpad;
-      jb.tout = -1;
       j2.push_back(jb);
     }
   }
@@ -698,7 +721,6 @@ rff_status materialise_z(rff_admm_t h) {
         jb.b_k0 = jb.a_k0;
         jb.nk = (int32_t)((t1 - t0) * 4);
         jb.out = (((int64_t)sp * s.R + i) * s.fslots + ft * 128) * s.mpad;
-        jb.tout = -1;
         j1.push_back(jb);
       }
     }
@@ -756,7 +778,7 @@ rff_status setup_factors(rff_admm_t h) {
       CK(cudaMemsetAsync(Hb, 0, sj * sj * 8, s.st));
       for (int64_t r = 0; r < s.row_size[i]; r += chunk_rows) {
         const int64_t nr = std::min(chunk_rows, s.row_size[i] - r);
-        if (s.split_path()) {
+        if (s.split_path() && !s.cached_z()) {
           CK(tc_write_z(tc_view(s), s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj));
         } else {
           ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, scale, s.row_of_slot, s.feat_of_slot,
@@ -804,7 +826,6 @@ rff_status setup_factors(rff_admm_t h) {
           jb.b_k0 = (int32_t)s.col_slot[j];
           jb.nk = (int32_t)ceil_div(sj, 32);
           jb.out = ((int64_t)i * s.fslots + s.col_slot[j] + m0) * s.mpad;
-          jb.tout = (int64_t)i * s.mpad * s.fslots + s.col_slot[j] + m0;
           qj.push_back(jb);
         }
       } else {
@@ -852,8 +873,8 @@ PassArgs base_pass_args(const rff_admm_s& s) {
   return a;
 }
 
-// W'_ij = Q_ij rhs_ij for all blocks: Q and rhs split three ways (six products);
-// W' is written row-major and as the transposed hi/lo pair that pass 2 reads
+// W'_ij = Q_ij rhs_ij for all blocks: Q and rhs split three ways into BF16 (six
+// products); W' is written row-major and max |W'| reduced for its FP16 split
 SgView qgemm_view(const rff_admm_s& s) {
   SgView v{};
   v.A[0] = s.Q1;
@@ -871,9 +892,9 @@ SgView qgemm_view(const rff_admm_s& s) {
   v.njobs = s.nqjobs;
   v.mpad = (int)s.mpad;
   v.out = s.What;
-  v.thi = s.WThi;
-  v.tlo = s.WTlo;
-  v.tld = s.fslots;
+  v.out_scale = 1.f;
+  v.amax = s.amax + 1;
+  v.two_acc = 1;
   v.st = s.st;
   return v;
 }
@@ -891,11 +912,13 @@ SgView cz_pass1_view(const rff_admm_s& s) {
   v.b_rows = (int64_t)s.C * s.mpad;
   v.b_cols = s.nslots;
   v.na = v.nb = 2;
+  v.f16 = 1;
   v.jobs = s.p1jobs;
   v.njobs = s.np1;
   v.mpad = (int)s.mpad;
   v.out = s.Rpart;
-  v.tld = -1;
+  v.out_scale = 1.f / s.zscale;
+  v.b_amax = s.amax;
   v.smem_budget = 110 * 1024;   // two CTAs per SM: one's epilogue overlaps the other's stream
   v.st = s.st;
   return v;
@@ -913,11 +936,13 @@ SgView cz_pass2_view(const rff_admm_s& s) {
   v.b_rows = (int64_t)s.R * s.mpad;
   v.b_cols = s.fslots;
   v.na = v.nb = 2;
+  v.f16 = 1;
   v.jobs = s.p2jobs;
   v.njobs = s.np2;
   v.mpad = (int)s.mpad;
   v.out = s.Op;
-  v.tld = -1;
+  v.out_scale = 1.f / s.zscale;
+  v.b_amax = s.amax + 1;
   v.smem_budget = 110 * 1024;
   v.st = s.st;
   return v;
@@ -959,10 +984,14 @@ rff_status iterate(rff_admm_t h, int k) {
   // (A refinement step r = rhs - H x computed in FP32 adds more rounding than it removes, and an
   // FP64 or compensated residual costs several times the solve on this part's FP64/FP32 pipes.)
   if (s.split_path()) {
-    // six-product split-BF16 GEMM on the tensor cores; also writes W' transposed and split for pass 2
+    // six-product split-BF16 GEMM on the tensor cores (reducing max |W'|), then the
+    // transposed FP16 split of W' that pass 2 reads
     CK(launch_rhs_split3T(s.Wbar, s.muij, s.Rpart, s.cached_z() ? s.nsplit_cz : s.nsplit, s.R, s.fslots,
                           (int)s.mpad, s.feat_of_slot, s.rT1, s.rT2, s.rT3, s.st));
+    CK(cudaMemsetAsync(s.amax + 1, 0, 4, s.st));
     CK(split_gemm(qgemm_view(s)));
+    CK(launch_transpose_split_f16(s.What, s.fslots, (int)s.mpad, s.R, s.fslots * s.mpad, s.WThi, s.WTlo, s.fslots,
+                                  s.mpad * s.fslots, 1.f, s.amax + 1, s.st));
   } else {
     CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st));
     CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st));
@@ -972,7 +1001,7 @@ rff_status iterate(rff_admm_t h, int k) {
   if (s.cached_z()) {
     CK(split_gemm(cz_pass2_view(s)));
   } else if (s.split_path()) {
-    CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1));
+    CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + 1));
   } else {
     a.M = s.What;
     a.m_block_stride = s.fslots * s.mpad;
@@ -983,16 +1012,19 @@ rff_status iterate(rff_admm_t h, int k) {
   }
   if ((r = mark(h, k, 4)) != RFF_OK) return r;
   // exchange, nu update, next loss prox, next V_ij
-  RowEpiArgs e{s.Op, s.O, s.Obar, s.nu, s.Y, s.V32, s.VThi, s.VTlo, s.row_of_slot, s.nslots,
+  RowEpiArgs e{s.Op, s.O, s.Obar, s.nu, s.Y, s.V32, s.split_path() ? s.amax : nullptr, s.row_of_slot, s.nslots,
                s.C, (int)s.m, (int)s.mpad, s.p.loss, s.p.newton_iters, s.t_loss};
-  if (s.split_path()) e.V32 = nullptr;   // the split path keeps only V^T (hi/lo)
-  else e.VThi = e.VTlo = nullptr;
+  if (s.split_path()) CK(cudaMemsetAsync(s.amax, 0, 4, s.st));
   CK(launch_row_epilogue(e, s.st));
+  // the tensor-core path reads V^T as a scaled FP16 hi/lo pair
+  if (s.split_path())
+    CK(launch_transpose_split_f16(s.V32, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
+                                  s.mpad * s.nslots, 1.f, s.amax, s.st));
   if ((r = mark(h, k, 5)) != RFF_OK) return r;
   // averaging and dual updates
   CK(launch_avg_dual(s.W, s.What, s.R, nfe, s.Wbar, s.mu, s.muij, s.st));
   if ((r = mark(h, k, 6)) != RFF_OK) return r;
-  s.launches += 7;
+  s.launches += s.split_path() ? 9 : 7;
   return RFF_OK;
 }
 
@@ -1044,7 +1076,7 @@ rff_status enqueue_iterations(rff_admm_t h, int iters, bool copy_old) {
     } else {
       if (!s.gexec && (r = capture_iteration(h)) != RFF_OK) return r;
       CK(cudaGraphLaunch(s.gexec, s.st));
-      s.launches += 7;
+      s.launches += s.split_path() ? 9 : 7;
     }
     if (r != RFF_OK) return r;
     s.iters_done++;
@@ -1093,8 +1125,11 @@ rff_status scores_pass(rff_admm_t h, const float* Xrows32, const __half* Xh, con
                        int64_t nrows, const int32_t* row_ok, float* out) {
   auto& s = *h;
   if (s.split_path()) {
-    CK(launch_transpose_split(s.Wbar, s.fslots, (int)s.mpad, 1, 0, s.WbThi, s.WbTlo, s.fslots, 0, s.st));
-    CK(tc_predict(tc_view(s), Xh, Xl, nrows, s.WbThi, s.WbTlo, out));
+    CK(cudaMemsetAsync(s.amax + 2, 0, 4, s.st));
+    CK(launch_finite_check(s.Wbar, s.fslots * s.mpad, 0, reinterpret_cast<int*>(s.amax + 3), s.st, s.amax + 2));
+    CK(launch_transpose_split_f16(s.Wbar, s.fslots, (int)s.mpad, 1, 0, s.WbThi, s.WbTlo, s.fslots, 0, 1.f,
+                                  s.amax + 2, s.st));
+    CK(tc_predict(tc_view(s), Xh, Xl, nrows, s.WbThi, s.WbTlo, s.amax + 2, out));
   } else {
     PassArgs a = base_pass_args(s);
     a.X = Xrows32;
@@ -1118,7 +1153,7 @@ namespace rff {
 TcView tc_view(const rff_admm_s& s) {
   TcView v{};
   v.Xhi = s.Xhi; v.Xlo = s.Xlo; v.Ghi = s.Ghi; v.Glo = s.Glo;
-  v.VThi = s.VThi; v.VTlo = s.VTlo;
+  v.VThi = s.VThi; v.VTlo = s.VTlo; v.v_amax = s.amax;
   v.bias = s.bias; v.row_ok = s.row_of_slot; v.feat_ok = s.feat_of_slot;
   v.nslots = s.nslots; v.fslots = s.fslots; v.dld = s.dld; v.mpad = s.mpad;
   v.R = s.R; v.C = s.C; v.nsplit = s.nsplit;
@@ -1358,17 +1393,11 @@ struct Piece {
   void* ptr;
   size_t bytes;
 };
-// the iteration's state: O, Obar, nu, the pass-1 operand V (FP32, or V^T as the hi/lo
-// pair the tensor-core pass reads), W, Wbar, mu, W'_ij, mu'_ij
+// the iteration's state: O, Obar, nu, the pass-1 operand V, W, Wbar, mu, W'_ij, mu'_ij
+// (the FP16 split of V^T on the tensor-core path is rebuilt from V)
 std::vector<Piece> state_pieces(rff_admm_s& s) {
   const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
-  std::vector<Piece> v{{s.O, rowb}, {s.Obar, rowb}, {s.nu, rowb}};
-  if (s.split_path()) {
-    v.push_back({s.VThi, rowb / 2 * s.C});
-    v.push_back({s.VTlo, rowb / 2 * s.C});
-  } else {
-    v.push_back({s.V32, rowb * s.C});
-  }
+  std::vector<Piece> v{{s.O, rowb}, {s.Obar, rowb}, {s.nu, rowb}, {s.V32, rowb * s.C}};
   for (Piece pc : std::vector<Piece>{{s.W, colb}, {s.Wbar, colb}, {s.mu, colb}, {s.What, colb * s.R},
                                      {s.muij, colb * s.R}})
     v.push_back(pc);
@@ -1428,6 +1457,12 @@ rff_status rff_admm_set_state(rff_admm_t h, const void* buf, size_t bytes) {
   for (auto& pc : pieces) {
     CK(cudaMemcpyAsync(pc.ptr, in + off, pc.bytes, cudaMemcpyHostToDevice, s.st));
     off += pc.bytes;
+  }
+  if (s.split_path()) {
+    CK(cudaMemsetAsync(s.amax, 0, 16, s.st));
+    CK(launch_finite_check(s.V32, s.C * s.nslots * s.mpad, 0, reinterpret_cast<int*>(s.amax + 3), s.st, s.amax));
+    CK(launch_transpose_split_f16(s.V32, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
+                                  s.mpad * s.nslots, 1.f, s.amax, s.st));
   }
   CK(cudaStreamSynchronize(s.st));
   s.iters_done = hd.iters_done;

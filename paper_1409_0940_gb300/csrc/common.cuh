@@ -96,4 +96,20 @@ __device__ __forceinline__ void split_f16(float x, float scale, __half& hi, __ha
   lo = __float2half_rn(xs - __half2float(hi));
 }
 
+// Scale of the FP16 split of a matrix whose largest |entry| is maxabs: the power of two s
+// with maxabs * s in [128, 256) (1 when maxabs is 0), and its inverse.  Computed on the
+// device from a maximum that an earlier kernel reduced, so producers and consumers of a
+// split agree without a round trip to the host.
+__device__ __forceinline__ int f16_scale_exp(float maxabs) {
+  if (!(maxabs > 0.f)) return 0;
+  int e;
+  frexpf(maxabs, &e);                 // maxabs = f 2^e, f in [0.5, 1)
+  return 8 - max(e, -100);
+}
+__device__ __forceinline__ float f16_scale(float maxabs) { return ldexpf(1.f, f16_scale_exp(maxabs)); }
+__device__ __forceinline__ float f16_inv_scale(float maxabs) { return ldexpf(1.f, -f16_scale_exp(maxabs)); }
+
+// Fixed scale of the FP16 split of cosines (|cos| <= 1) in the chained products
+constexpr float COS_SCALE = 128.f;
+
 }  // namespace rff

@@ -207,11 +207,10 @@ __global__ void k_prox_reg(int reg, const float* __restrict__ V, const float* __
 //   V_ij = O'_ij + (Delta/(C+1) + nu)      (= Obar_ij + nu, the pass-1 operand)
 //   O <- prox_{t V}(Obar - nu)             (the loss step of the next iteration)
 // Phase 1 (a warp per row, lanes over outputs) updates Obar, nu and O and keeps
-// Delta/(C+1) + nu of the tile in shared memory; phase 2 forms V_ij tile by tile,
-// either row-major in FP32 (the SIMT path's operand) or transposed and split into
-// hi/lo BF16 (V^T[j][c][slot], the tensor-core operand) through a shared-memory
-// transpose so that both the reads and the writes are coalesced.  Padding rows and
-// columns are written as zeros.
+// Delta/(C+1) + nu of the tile in shared memory; phase 2 forms V_ij row-major in
+// FP32 and, for the tensor-core path, reduces max |V| (the scale of its FP16
+// split, which k_transpose_split_f16 writes next).  Padding rows and columns are
+// written as zeros.
 constexpr int EX_ROWS = 32;
 
 template <int LOSS>
@@ -219,7 +218,6 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
   extern __shared__ float ex_smem[];
   const int mp = a.mpad;
   float* term = ex_smem;                         // [32][mpad]
-  float* tile = ex_smem + EX_ROWS * mp;          // [32][mpad + 1]
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int64_t p0 = (int64_t)blockIdx.x * EX_ROWS;
   const int64_t jstride = a.nslots * mp;
@@ -267,31 +265,22 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
   }
   __syncthreads();
   // phase 2: V_ij = O'_ij + term, per column block
+  float vmax = 0.f;
   for (int j = 0; j < a.C; ++j) {
     const float* opj = a.Op + j * jstride + p0 * mp;
-    if (a.V32) {
-      float* vj = a.V32 + j * jstride + p0 * mp;
-      for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
-        const bool live = a.row_ok[p0 + e / mp] >= 0 && e % mp < a.m;
-        vj[e] = live ? opj[e] + term[e] : 0.f;
-      }
-      continue;
-    }
+    float* vj = a.V32 + j * jstride + p0 * mp;
     for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
-      const int r = e / mp, k = e % mp;
-      const bool live = a.row_ok[p0 + r] >= 0 && k < a.m;
-      tile[r * (mp + 1) + k] = live ? opj[e] + term[e] : 0.f;
+      const bool live = a.row_ok[p0 + e / mp] >= 0 && e % mp < a.m;
+      const float v = live ? opj[e] + term[e] : 0.f;
+      vj[e] = v;
+      vmax = fmaxf(vmax, fabsf(v));
     }
-    __syncthreads();
-    // lanes over the 32 rows, warps over columns: V^T[j][c][p0 + lane]
-    for (int c = warp; c < mp; c += 8) {
-      __nv_bfloat16 hi, lo;
-      split_bf16(tile[lane * (mp + 1) + c], hi, lo);
-      const int64_t o = ((int64_t)j * mp + c) * a.nslots + p0 + lane;
-      a.VThi[o] = hi;
-      a.VTlo[o] = lo;
-    }
-    __syncthreads();
+  }
+  if (a.vmax) {
+    // largest |V| (the scale of the next FP16 split of V^T)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if (lane == 0 && vmax > 0.f) atomicMax(a.vmax, __float_as_uint(vmax));
   }
 }
 
@@ -320,6 +309,35 @@ __global__ void k_avg_dual(const float* __restrict__ W, const float* __restrict_
 }
 
 // src [b][rows][cols] float32 -> hi/lo [b][cols][dst_ld] BF16, 32 x 32 smem tiles
+// The transposed FP16 split of a row-major FP32 matrix, scaled by a power of two:
+// amax (device, max |src| as float bits) selects it (f16_scale), else scale.
+__global__ void k_transpose_split_f16(const float* __restrict__ src, int64_t rows, int cols, int64_t sbs,
+                                      __half* __restrict__ hi, __half* __restrict__ lo, int64_t dld, int64_t dbs,
+                                      float scale, const unsigned* __restrict__ amax) {
+  __shared__ float tile[32][33];
+  const float sc = amax ? f16_scale(__uint_as_float(*amax)) : scale;
+  const int b = blockIdx.z;
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 256 threads: 8 rows per pass
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t r = r0 + rr;
+    const int c = c0 + tx;
+    tile[rr][tx] = (r < rows && c < cols) ? src[b * sbs + r * cols + c] : 0.f;
+  }
+  __syncthreads();
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int c = c0 + cc;
+    const int64_t r = r0 + tx;
+    if (c < cols && r < rows) {
+      __half h, l;
+      split_f16(tile[tx][cc], sc, h, l);
+      hi[b * dbs + (int64_t)c * dld + r] = h;
+      lo[b * dbs + (int64_t)c * dld + r] = l;
+    }
+  }
+}
+
 __global__ void k_transpose_split(const float* __restrict__ src, int64_t rows, int cols, int64_t sbs,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t dld,
                                   int64_t dbs) {
@@ -492,13 +510,13 @@ cudaError_t launch_prox_reg(int reg, const float* V, const float* mu, int64_t n,
 cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st) {
   if (a.nslots <= 0) return cudaSuccess;
   if (a.mpad > 32 * MAXPL || a.nslots % EX_ROWS) return cudaErrorInvalidValue;
-  if (!a.V32 && !(a.VThi && a.VTlo)) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)EX_ROWS * (2 * a.mpad + 1) * sizeof(float);
+  if (!a.V32) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)EX_ROWS * a.mpad * sizeof(float);
   const unsigned grid = (unsigned)(a.nslots / EX_ROWS);
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    const int mx = EX_ROWS * (2 * 32 * MAXPL + 1) * (int)sizeof(float);
+    const int mx = EX_ROWS * 32 * MAXPL * (int)sizeof(float);
     attr = cudaFuncSetAttribute(k_exchange<LOSS_SQUARED>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_exchange<LOSS_HINGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -526,6 +544,16 @@ cudaError_t launch_rhs(const float* Wbar, const float* muij, const float* Rpart,
 cudaError_t launch_avg_dual(const float* W, const float* What, int R, int64_t nfe, float* Wbar, float* mu,
                             float* muij, cudaStream_t st) {
   k_avg_dual<<<nblk(nfe), 256, 0, st>>>(W, What, R, nfe, Wbar, mu, muij);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_split_f16(const float* src, int64_t rows, int cols, int nbatch, int64_t src_batch_stride,
+                                       __half* hi, __half* lo, int64_t dst_ld, int64_t dst_batch_stride, float scale,
+                                       const unsigned* amax, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0 || nbatch <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32), (unsigned)nbatch);
+  k_transpose_split_f16<<<grid, 256, 0, st>>>(src, rows, cols, src_batch_stride, hi, lo, dst_ld, dst_batch_stride,
+                                              scale, amax);
   return cudaGetLastError();
 }
 

@@ -122,9 +122,8 @@ struct RowEpiArgs {
   float* Obar;
   float* nu;
   const float* Y;
-  float* V32;           // C x slots x mpad (may be null)
-  __nv_bfloat16* VThi;  // C x mpad x slots (may be null)
-  __nv_bfloat16* VTlo;
+  float* V32;           // C x slots x mpad
+  unsigned* vmax;       // max |V| as float bits (atomicMax), or null
   const int32_t* row_ok;
   int64_t nslots;
   int C, m, mpad, loss, newton;
@@ -135,6 +134,10 @@ cudaError_t launch_rhs(const float* Wbar, const float* muij, const float* Rpart,
                        float* rhs, cudaStream_t st);
 cudaError_t launch_avg_dual(const float* W, const float* What, int R, int64_t nfe, float* Wbar, float* mu,
                             float* muij, cudaStream_t st);
+// hi/lo FP16 split of src^T scaled by f16_scale(*amax) (amax non-null) or by scale
+cudaError_t launch_transpose_split_f16(const float* src, int64_t rows, int cols, int nbatch, int64_t src_batch_stride,
+                                       __half* hi, __half* lo, int64_t dst_ld, int64_t dst_batch_stride, float scale,
+                                       const unsigned* amax, cudaStream_t st);
 cudaError_t launch_transpose_split(const float* src, int64_t rows, int cols, int nbatch, int64_t src_batch_stride,
                                    __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t dst_ld, int64_t dst_batch_stride,
                                    cudaStream_t st);

@@ -5,12 +5,13 @@
 //
 //   acc (TMEM, 128 x m_pad fp32) = sum over the split products A_s . B_t^T
 //
-// with A = A1 + A2 (+ A3) and B = B1 + B2 (+ B3) split into BF16 terms.  Three
-// terms each (NA = NB = 3) take the six products whose exponents sum to at most
-// 2^-16 (11, 12, 21, 13, 22, 31): the accuracy of an FP32 product.  Two terms
-// each take 11, 12, 21 (hi.hi + hi.lo + lo.hi).  The accumulator is written
-// row-major to out + job.out (ld m_pad), and optionally transposed and split
-// into a hi/lo BF16 pair (column c of row r at thi + job.tout + c*tld + r).
+// with A = A1 + A2 (+ A3) and B = B1 + B2 (+ B3) split into 16-bit terms.  Three
+// BF16 terms each (NA = NB = 3) take the six products whose exponents sum to at
+// most 2^-16 (11, 12, 21, 13, 22, 31): the accuracy of an FP32 product.  Two
+// terms each (scaled FP16 hi/lo, 22 significant bits) take 11, 12, 21.  The
+// accumulator times out_scale (and the inverse FP16 scale of B, from the device
+// maximum b_amax) is written row-major to out + job.out (ld m_pad); amax, when
+// given, collects max |result| for the FP16 split of the result that follows.
 //
 // Users: the cached projection of eq. (gpWij) (A = Q_ij split three ways, B = the
 // right-hand side), and the two chained products of the cached-Z precision
@@ -45,10 +46,12 @@ struct QArgs {
   CUtensorMap tA[3], tB[3];
   int mpad, ns;
   uint32_t stage_bytes, tmem_cols;
+  uint32_t acc_b;            // column of the second accumulator (the small products), 0 = one accumulator
   const SgJob* jobs;
   float* out;
-  __nv_bfloat16 *thi, *tlo;
-  int64_t tld;
+  float out_scale;
+  const unsigned* b_amax;
+  unsigned* amax;
   int* err;
   long long timeout_cycles;
 };
@@ -78,7 +81,7 @@ __device__ __forceinline__ bool qwait(uint32_t bar, uint32_t parity, QShared& sh
 __host__ __device__ constexpr int prod_a(int p) { return p == 2 || p == 4 ? 1 : p == 5 ? 2 : 0; }
 __host__ __device__ constexpr int prod_b(int p) { return p == 1 || p == 4 ? 1 : p == 3 ? 2 : 0; }
 
-template <int NA, int NB>
+template <int NA, int NB, int F16>
 __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArgs a) {
   constexpr int NPROD = (NA == 3 && NB == 3) ? 6 : 3;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -138,7 +141,7 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(128, a.mpad);
+      const uint32_t idesc = F16 ? idesc_f16(128, a.mpad) : idesc_bf16(128, a.mpad);
       bool ok = true;
       for (int kc = 0; kc < nk; ++kc) {
         const int st = kc % a.ns;
@@ -155,7 +158,13 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
           for (int p = 0; p < NPROD; ++p) {
             const uint64_t da = smem_desc(sa + prod_a(p) * QATILE + kk * 32, 512, 4);
             const uint64_t db = smem_desc(sb + prod_b(p) * mb + kk * 32, 512, 4);
-            mma_bf16(tmem, da, db, idesc, (kc > 0 || kk > 0 || p > 0) ? 1u : 0u);
+            if (a.acc_b) {
+              // hi.hi alone in the first accumulator, the smaller products in the second
+              const uint32_t d = p == 0 ? tmem : tmem + a.acc_b;
+              mma_bf16(d, da, db, idesc, (kc > 0 || kk > 0 || p > 1) ? 1u : 0u);
+            } else {
+              mma_bf16(tmem, da, db, idesc, (kc > 0 || kk > 0 || p > 0) ? 1u : 0u);
+            }
           }
         }
         mma_commit(bar_empty + 8 * st);
@@ -175,28 +184,27 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
       fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
       float* orow_p = a.out + job.out + (int64_t)row * a.mpad;
-      const bool transposed = job.tout >= 0;
-      __nv_bfloat16* th = transposed ? a.thi + job.tout + row : nullptr;
-      __nv_bfloat16* tl = transposed ? a.tlo + job.tout + row : nullptr;
+      const float sc = a.out_scale * (a.b_amax ? f16_inv_scale(__uint_as_float(*a.b_amax)) : 1.f);
+      float mx = 0.f;
       for (int c = 0; c < a.mpad; c += 8) {
-        uint32_t r8[8];
+        uint32_t r8[8], s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         tmem_ld8(taddr + c, r8);
+        if (a.acc_b) tmem_ld8(taddr + a.acc_b + c, s8);
         tmem_wait_ld();
         float x[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) x[t] = __uint_as_float(r8[t]);
+        for (int t = 0; t < 8; ++t) {
+          x[t] = sc * (__uint_as_float(r8[t]) + __uint_as_float(s8[t]));
+          mx = fmaxf(mx, fabsf(x[t]));
+        }
         float4* dst = reinterpret_cast<float4*>(orow_p + c);
         dst[0] = make_float4(x[0], x[1], x[2], x[3]);
         dst[1] = make_float4(x[4], x[5], x[6], x[7]);
-        if (transposed) {
+      }
+      if (a.amax) {
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            __nv_bfloat16 hi, lo;
-            split_bf16(x[t], hi, lo);
-            th[(int64_t)(c + t) * a.tld] = hi;
-            tl[(int64_t)(c + t) * a.tld] = lo;
-          }
-        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && mx > 0.f) atomicMax(a.amax, __float_as_uint(mx));
       }
     }
   }
@@ -266,12 +274,12 @@ __global__ void k_split3_q(const double* __restrict__ Q, int s, int64_t ldq, int
   q3[o] = l;
 }
 
-template <int NA, int NB>
+template <int NA, int NB, int F16>
 cudaError_t set_smem_attr() {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_split_gemm<NA, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr = cudaFuncSetAttribute(k_split_gemm<NA, NB, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 1024 + 216 * 1024 + 256);
   });
   return attr;
@@ -298,7 +306,7 @@ cudaError_t launch_rhs_split3T(const float* Wbar, const float* muij, const float
 cudaError_t split_gemm(const SgView& v) {
   if (v.njobs <= 0) return cudaSuccess;
   if (v.mpad > 256 || v.mpad < 16 || v.mpad % 16) return cudaErrorInvalidValue;
-  if (!((v.na == 3 && v.nb == 3) || (v.na == 2 && v.nb == 2))) return cudaErrorInvalidValue;
+  if (!((v.na == 3 && v.nb == 3 && !v.f16) || (v.na == 2 && v.nb == 2 && v.f16))) return cudaErrorInvalidValue;
   QArgs a;
   memset(&a, 0, sizeof(a));
   cudaError_t e;
@@ -313,21 +321,28 @@ cudaError_t split_gemm(const SgView& v) {
   a.ns = (int)std::min<size_t>(QMAXS, budget / a.stage_bytes);
   if (a.ns < 2) a.ns = 2;
   a.tmem_cols = v.mpad <= 32 ? 32 : v.mpad <= 64 ? 64 : v.mpad <= 128 ? 128 : 256;
+  if (v.two_acc) {
+    // the tensor cores' FP32 accumulator rounds toward zero at every accumulation: the
+    // dominant hi.hi products get an accumulator of their own (K/16 accumulations instead of
+    // NPROD K/16), the small products share the second, and the two are added in FP32
+    a.acc_b = a.tmem_cols;
+    a.tmem_cols *= 2;
+  }
   a.jobs = v.jobs;
   a.out = v.out;
-  a.thi = v.thi;
-  a.tlo = v.tlo;
-  a.tld = v.tld;
+  a.out_scale = v.out_scale;
+  a.b_amax = v.b_amax;
+  a.amax = v.amax;
   a.err = tc_error_ptr();
   if (!a.err) return cudaErrorMemoryAllocation;
   a.timeout_cycles = 4000000000LL;   // about two seconds at the boost clock
   const size_t smem = 1024 + (size_t)a.ns * a.stage_bytes + 256;
   if (v.na == 3) {
-    if ((e = set_smem_attr<3, 3>()) != cudaSuccess) return e;
-    k_split_gemm<3, 3><<<(unsigned)v.njobs, QNT, smem, v.st>>>(a);
+    if ((e = set_smem_attr<3, 3, 0>()) != cudaSuccess) return e;
+    k_split_gemm<3, 3, 0><<<(unsigned)v.njobs, QNT, smem, v.st>>>(a);
   } else {
-    if ((e = set_smem_attr<2, 2>()) != cudaSuccess) return e;
-    k_split_gemm<2, 2><<<(unsigned)v.njobs, QNT, smem, v.st>>>(a);
+    if ((e = set_smem_attr<2, 2, 1>()) != cudaSuccess) return e;
+    k_split_gemm<2, 2, 1><<<(unsigned)v.njobs, QNT, smem, v.st>>>(a);
   }
   return cudaGetLastError();
 }

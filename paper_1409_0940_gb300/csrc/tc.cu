@@ -84,6 +84,7 @@ struct TcArgs {
   const int32_t* b_ok;
   float scale;
   float inv_xg;                             // X.G accumulator -> X G (1 / (xscale gscale))
+  const unsigned* m_amax;                   // max |M| of the chained operand (its FP16 split scale)
   const int64_t* row_slot;
   const int64_t* row_size;
   const int64_t* col_slot;
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
     // ================= MMA issuer =================
     if (lane == 0) {
       const uint32_t id1 = idesc_f16(128, 128);    // X.G: scaled FP16 splits
-      const uint32_t id2 = idesc_bf16(128, a.mpad);
+      const uint32_t id2 = idesc_f16(128, a.mpad);     // chain: scaled FP16 splits of Z and M
       uint32_t it = 0;
       int t = 0;            // B tile index (global)
       bool ok = true;
@@ -449,17 +450,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
         // Z tile must be free: the chain of the previous tile has completed
         if (t >= 1 && !waitw(bar_ze, (t - 1) & 1, sh, a, ERR_TIMEOUT_EPI)) { ok = false; break; }
         if (ZT) {
-          // split into hi/lo BF16 pairs (two K elements per 32-bit column) and store this
-          // warp's 32 rows x 64 features into the Z columns of TMEM
+          // split COS_SCALE z into hi/lo FP16 pairs (two K elements per 32-bit column) and
+          // store this warp's 32 rows x 64 features into the Z columns of TMEM
 #pragma unroll
           for (int hf = 0; hf < 2; ++hf) {
             uint32_t ph[16], pl[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-              const float z0 = z[32 * hf + 2 * q], z1 = z[32 * hf + 2 * q + 1];
-              const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
-              const float2 f = __bfloat1622float2(h);
-              const __nv_bfloat162 l = __floats2bfloat162_rn(z0 - f.x, z1 - f.y);
+              const float z0 = COS_SCALE * z[32 * hf + 2 * q], z1 = COS_SCALE * z[32 * hf + 2 * q + 1];
+              const __half2 h = __floats2half2_rn(z0, z1);
+              const float2 f = __half22float2(h);
+              const __half2 l = __floats2half2_rn(z0 - f.x, z1 - f.y);
               ph[q] = *reinterpret_cast<const uint32_t*>(&h);
               pl[q] = *reinterpret_cast<const uint32_t*>(&l);
             }
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
           tmem_wait_st();
           fence_before();
         } else {
-          // split into hi/lo BF16 and store in the 128-byte swizzled K-major layout
+          // split into hi/lo FP16 and store in the 128-byte swizzled K-major layout
           unsigned char* zhi = zbuf + (colbase / 64) * ZATOM;
           unsigned char* zlo = zhi + ZBYTES / 2;
 #pragma unroll
@@ -478,10 +479,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
             uint32_t ph[4], pl[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              // hi = bf16x2(z0, z1); lo = bf16x2(z - hi) (packed conversions)
-              const __nv_bfloat162 h = __floats2bfloat162_rn(z[ch * 8 + 2 * q], z[ch * 8 + 2 * q + 1]);
-              const float2 hf = __bfloat1622float2(h);
-              const __nv_bfloat162 l = __floats2bfloat162_rn(z[ch * 8 + 2 * q] - hf.x, z[ch * 8 + 2 * q + 1] - hf.y);
+              // hi = fp16x2(s z0, s z1); lo = fp16x2(s z - hi) (packed conversions)
+              const float z0 = COS_SCALE * z[ch * 8 + 2 * q], z1 = COS_SCALE * z[ch * 8 + 2 * q + 1];
+              const __half2 h = __floats2half2_rn(z0, z1);
+              const float2 hf = __half22float2(h);
+              const __half2 l = __floats2half2_rn(z0 - hf.x, z1 - hf.y);
               ph[q] = *reinterpret_cast<const uint32_t*>(&h);
               pl[q] = *reinterpret_cast<const uint32_t*>(&l);
             }
@@ -500,11 +502,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
           const int half = a.mpad / 2;
           const int c0 = (ew < 4) ? 0 : half;
           float* orow = sh.g_out[g] + (int64_t)row * a.mpad;
+          // undo the FP16 scales of Z (COS_SCALE) and of the chained operand, apply sqrt(2/D)
+          const float sc = a.scale / COS_SCALE * (a.m_amax ? f16_inv_scale(__uint_as_float(*a.m_amax)) : 1.f);
           for (int c = 0; c < half; c += 8) {
             uint32_t r8[8];
             tmem_ld8(tmem + lane_addr + ACC2_COL + c0 + c, r8);
             tmem_wait_ld();
-            const float sc = a.scale;
             float4* dst = reinterpret_cast<float4*>(orow + c0 + c);
             dst[0] = make_float4(sc * __uint_as_float(r8[0]), sc * __uint_as_float(r8[1]),
                                  sc * __uint_as_float(r8[2]), sc * __uint_as_float(r8[3]));
@@ -674,6 +677,7 @@ cudaError_t tc_pass1(const TcView& v, float* Rpart) {
   a.b_ok = v.row_ok;
   a.out = Rpart;
   a.out_block_stride = v.fslots * v.mpad;
+  a.m_amax = v.v_amax;
   if ((e = make_map(&a.tA_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tB_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
@@ -683,8 +687,8 @@ cudaError_t tc_pass1(const TcView& v, float* Rpart) {
   return launch(a, dim3((unsigned)(v.fslots / 128), (unsigned)v.R, (unsigned)v.nsplit), v.st, view_kc(v), view_zt(v));
 }
 
-cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, int64_t m_block_stride,
-                     float* out, int per_block) {
+cudaError_t tc_pass2(const TcView& v, const __half* Mhi, const __half* Mlo, int64_t m_block_stride,
+                     float* out, int per_block, const unsigned* m_amax) {
   (void)m_block_stride;
   (void)per_block;
   TcArgs a;
@@ -696,6 +700,7 @@ cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloa
   a.b_ok = v.feat_ok;
   a.out = out;
   a.out_block_stride = v.nslots * v.mpad;
+  a.m_amax = m_amax;
   if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
@@ -706,7 +711,7 @@ cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloa
 }
 
 cudaError_t tc_predict(const TcView& v, const __half* Xh, const __half* Xl, int64_t nrows,
-                       const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, float* out) {
+                       const __half* Mhi, const __half* Mlo, const unsigned* m_amax, float* out) {
   if (nrows <= 0) return cudaSuccess;
   if (nrows % 128) return cudaErrorInvalidValue;
   TcArgs a;
@@ -716,6 +721,7 @@ cudaError_t tc_predict(const TcView& v, const __half* Xh, const __half* Xl, int6
   a.a_ok = nullptr;
   a.b_ok = v.feat_ok;
   a.out = out;
+  a.m_amax = m_amax;
   if ((e = make_map(&a.tA_hi, Xh, v.dld, nrows, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, Xl, v.dld, nrows, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;

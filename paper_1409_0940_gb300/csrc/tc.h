@@ -12,7 +12,8 @@ namespace rff {
 struct TcView {
   const __half *Xhi, *Xlo;          // nslots x dld, FP16 split of X * xscale
   const __half *Ghi, *Glo;          // fslots x dld, FP16 split of G * gscale
-  const __nv_bfloat16 *VThi, *VTlo; // C x mpad x nslots (pass-1 chain operand)
+  const __half *VThi, *VTlo;        // C x mpad x nslots (pass-1 chain operand), FP16 split of V^T
+  const unsigned* v_amax;           // max |V| (float bits): the scale of that split
   const float* bias;                // fslots
   const int32_t *row_ok, *feat_ok;  // slot tables, -1 = padding
   int64_t nslots, fslots, dld, mpad;
@@ -32,39 +33,43 @@ cudaError_t tc_write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int6
 // Pass 1: R-partials [nsplit][R][fslots][mpad] = Z_ij^T V_ij.
 cudaError_t tc_pass1(const TcView& v, float* Rpart);
 // Pass 2: out[j][slots][mpad] = Z_ij M_i (per_block) or out[slots][mpad] = sum_j Z_ij M (predict);
-// M given transposed and split: [R][mpad][fslots] hi/lo, m_block_stride elements apart.
-cudaError_t tc_pass2(const TcView& v, const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, int64_t m_block_stride,
-                     float* out, int per_block);
+// M given transposed and split: [R][mpad][fslots] hi/lo FP16 of M scaled by f16_scale(*m_amax),
+// m_block_stride elements apart.
+cudaError_t tc_pass2(const TcView& v, const __half* Mhi, const __half* Mlo, int64_t m_block_stride,
+                     float* out, int per_block, const unsigned* m_amax);
 // Scores for a query block (nrows slot-padded rows of split X) against M (mpad x fslots hi/lo).
 // Error word of the tensor-core kernels (bounded waits that gave up); reads and clears it.
 // Synchronises the device.  0 = no error.
 int tc_error_word();
 cudaError_t tc_predict(const TcView& v, const __half* Xh, const __half* Xl, int64_t nrows,
-                       const __nv_bfloat16* Mhi, const __nv_bfloat16* Mlo, float* out);
+                       const __half* Mhi, const __half* Mlo, const unsigned* m_amax, float* out);
 
 
-// Split-BF16 streaming GEMM on the tensor cores, one CTA per job:
-//   out[job.out + r*mpad + c] = sum_k A[job.a_row + r][job.a_k0 + k] B[job.b_row + c][job.b_k0 + k]
-// for r < 128, c < mpad, k < 32*job.nk, with A and B split into na = nb = 3 BF16 terms
-// (six products) or 2 terms (three products).  If job.tout >= 0 the result is also
-// written transposed as a hi/lo pair: thi/tlo[job.tout + c*tld + r].  A is a_rows x
-// a_cols (row-major), B b_rows x b_cols; every job's K range and rows lie inside them.
+// Split streaming GEMM on the tensor cores, one CTA per job:
+//   out[job.out + r*mpad + c] = out_scale / s_B sum_k A[job.a_row + r][job.a_k0 + k] B[job.b_row + c][job.b_k0 + k]
+// for r < 128, c < mpad, k < 32*job.nk, with A and B split into three BF16 terms (six
+// products; f16 = 0) or into two scaled FP16 terms (three products; f16 = 1).  s_B is
+// f16_scale(*b_amax) when b_amax is given (the scale B's split was written with), else 1;
+// amax, when given, receives max |out| (atomicMax of float bits).  A is a_rows x a_cols
+// (row-major), B b_rows x b_cols; every job's K range and rows lie inside them.
 struct SgJob {
   int32_t a_row, a_k0, b_row, b_k0, nk, pad_;
-  int64_t out, tout;
+  int64_t out;
 };
 struct SgView {
-  const __nv_bfloat16* A[3];
+  const void* A[3];
   int64_t a_rows, a_cols;
-  const __nv_bfloat16* B[3];
+  const void* B[3];
   int64_t b_rows, b_cols;
-  int na, nb;
+  int na, nb, f16;
   const SgJob* jobs;                   // device
   int njobs, mpad;
   float* out;
-  __nv_bfloat16 *thi, *tlo;
-  int64_t tld;
+  float out_scale;
+  const unsigned* b_amax;
+  unsigned* amax;
   size_t smem_budget;                  // ring bytes per CTA (0 = the largest; smaller lets 2 CTAs share an SM)
+  int two_acc;                         // 1: hi.hi products in their own TMEM accumulator (twice the columns)
   cudaStream_t st;
 };
 cudaError_t split_gemm(const SgView& v);
