@@ -246,7 +246,7 @@ def run_ours(args, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16x3", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f16x3", "data": "synthetic",
         "config": {"workload": w["name"], "n": w["n"], "d": w["d"], "m": w["m"], "D": w["D"],
                    "grid": "%dx%d" % (w["R"], w["C"]), "sigma": w["sigma"], "loss": w["loss"], "reg": w["reg"],
                    "lambda": w["lam"], "rho": w["rho"], "prec": args.prec, "parallelism": "replicas",
@@ -344,7 +344,7 @@ def run_sweep(args):
     return {"metric": "sweep solve-iterations/s", "value": nsolve * args.steps / sec, "unit": "solve-iter/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3" if args.prec == "split_bf16" else "f32", "data": "synthetic",
+            "dtype": "f32" if args.prec == "fp32" else "f16x3", "data": "synthetic",
             "config": {"workload": w["name"], "solves": nsolve, "groups": groups, "prec": args.prec,
                        "timing": "host wall clock around rff_sweep_run (all streams drained)"},
             "clocks": clk.summary()}

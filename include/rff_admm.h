@@ -67,15 +67,18 @@ typedef enum {
 /* How Z_ij is regenerated and applied. */
 typedef enum {
   RFF_PREC_FP32 = 0,      /* X.G, cos and both chained products in FP32 on the SIMT pipes  */
-  RFF_PREC_SPLIT_BF16 = 1, /* tensor cores: X.G as three FP16 products (hi.hi + hi.lo +
-                             lo.hi) of the hi/lo splits of X and G, each scaled by a power
-                             of two into |.| <= 2^8 (22 significant bits per operand),
-                             FP32 accumulate in TMEM, FP32 cos; the chained products as
-                             three BF16 products of the hi/lo split of both operands.
-                             Queries beyond 2^15 / (X scale), at least 128 times the
-                             largest training |x|, are refused (RFF_EINVAL)              */
-  RFF_PREC_CACHED_Z = 2   /* Z materialised once (set-up, by the split-BF16 regeneration)
-                             and kept in device memory as a hi/lo BF16 pair, with a
+  RFF_PREC_SPLIT_BF16 = 1, /* the split tensor-core path: X.G as three FP16 products
+                             (hi.hi + hi.lo + lo.hi) of the hi/lo splits of X and G, each
+                             scaled by a power of two into |.| <= 2^8 (22 significant bits
+                             per operand), FP32 accumulate in TMEM, FP32 cos; the chained
+                             products as three FP16 products of hi/lo splits of 2^7 cos and
+                             of V, W' (scaled from their maxima); the projection with Q and
+                             its right-hand side as three BF16 terms (six products, the
+                             dominant ones in an accumulator of their own).  Queries beyond
+                             2^15 / (X scale), at least 128 times the largest training |x|,
+                             are refused (RFF_EINVAL)                                    */
+  RFF_PREC_CACHED_Z = 2   /* Z materialised once (set-up, FP32 on the SIMT pipes) and kept
+                             in device memory as a scaled FP16 hi/lo pair, with a
                              transposed copy: n_slots x D_slots x 8 bytes.  Each iteration
                              streams it through the same three-product chained GEMMs
                              instead of regenerating it; the comparison mode of the paper's
