@@ -61,7 +61,12 @@ struct rff_admm_s {
                 *WbTlo = nullptr;
   float *W = nullptr, *Wbar = nullptr, *mu = nullptr, *What = nullptr, *muij = nullptr, *rhs = nullptr,
         *Rpart = nullptr;
-  float* Q32 = nullptr;       // cached (I + Z_ij^T Z_ij)^-1 per block (float32 path)
+  float* Q32 = nullptr;       // cached (I + Z_ij^T Z_ij)^-1 per block (float32 path), or the
+                              // (I + Z_ij Z_ij^T)^-1 of the outer form (both paths)
+  // outer form of the graph projection (eq. (graphU) via the identity of Sec. 3 with
+  // (I + Z Z^T)^-1, chosen when every block has fewer rows than features): u = Z rhs
+  bool outer = false;
+  float* U32 = nullptr;       // C x slots x mpad
   // split path: the cached inverses split three ways into BF16, blocks stacked by rows
   // (block b from row qrow[b], rows padded to 128, ldq columns), and the right-hand
   // side of the projection split the same way, transposed to [R][mpad][fslots]
@@ -235,19 +240,22 @@ size_t working_set_bytes(const rff_admm_s& s) {
   t += (size_t)s.fslots * s.mpad * f * 5;                       // W, Wbar, mu, mu_old, Wbar_old
   t += (size_t)s.R * s.fslots * s.mpad * f * (3 + s.nsplit_max);    // What, muij, muij_old, Rpart
   if (s.split_path()) {
-    t += (size_t)s.R * s.fslots * s.mpad * b2 * (2 + 3) + (size_t)s.fslots * s.mpad * b2 * 2;   // WT, rT, WbT
-    t += (size_t)s.q_rows * s.ldq * b2 * 3 + (size_t)s.R * s.C * (s.ldq / 128 + 1) * sizeof(SgJob);   // Q splits
+    t += (size_t)s.R * s.fslots * s.mpad * b2 * 2 + (size_t)s.fslots * s.mpad * b2 * 2;         // WT, WbT
+    if (!s.outer) {
+      t += (size_t)s.R * s.fslots * s.mpad * b2 * 3;                                          // rT
+      t += (size_t)s.q_rows * s.ldq * b2 * 3 + (size_t)s.R * s.C * (s.ldq / 128 + 1) * sizeof(SgJob);   // Q splits
+    }
     if (s.cached_z()) {
       t += (size_t)s.nslots * s.fslots * b2 * 4;                                                // Z, Z^T hi/lo
       t += (size_t)(s.nslots / 128 * s.C + s.fslots / 128 * s.R * s.nsplit_cz) * sizeof(SgJob);
       t += (size_t)s.R * s.fslots * s.mpad * f * (s.nsplit_cz > s.nsplit_max ? s.nsplit_cz - s.nsplit_max : 0);
     }
-  } else {
-    t += (size_t)s.R * s.fslots * s.mpad * f;                                                   // rhs
-    size_t fac = 0;
-    for (int j = 0; j < s.C; ++j) fac += (size_t)s.col_size[j] * s.col_size[j];
-    t += fac * s.R * f + (size_t)s.R * s.C * sizeof(GemmDesc);
   }
+  if (!s.split_path() || s.outer) {
+    t += (size_t)s.R * s.fslots * s.mpad * f;                                                   // rhs
+    t += (size_t)s.foff.back() * f + (size_t)s.R * s.C * sizeof(GemmDesc);                     // factors
+  }
+  if (s.outer) t += (size_t)s.C * s.nslots * s.mpad * f;                                       // u = Z rhs
   return t + (64u << 20);
 }
 
@@ -285,14 +293,24 @@ void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
   acc = 0;
   for (int j = 0; j < s.C; ++j) { s.col_slot[j] = acc; acc += round_up(s.col_size[j], SLOT); }
   s.fslots = acc;
+  // the projection's cached factor per block: (I + Z^T Z)^-1 (s_j x s_j) or, when every
+  // block has fewer rows than features, (I + Z Z^T)^-1 (n_i x n_i); the cached-Z
+  // precision streams Z through the Gram form only
+  {
+    const int64_t nmax = *std::max_element(s.row_size.begin(), s.row_size.end());
+    const int64_t smin = *std::min_element(s.col_size.begin(), s.col_size.end());
+    s.outer = s.p.prec != RFF_PREC_CACHED_Z && nmax < smin;
+  }
   s.foff.assign((size_t)s.R * s.C + 1, 0);
   for (int i = 0; i < s.R; ++i)
-    for (int j = 0; j < s.C; ++j)
-      s.foff[(size_t)i * s.C + j + 1] = s.foff[(size_t)i * s.C + j] + s.col_size[j] * s.col_size[j];
+    for (int j = 0; j < s.C; ++j) {
+      const int64_t fd = s.outer ? s.row_size[i] : s.col_size[j];
+      s.foff[(size_t)i * s.C + j + 1] = s.foff[(size_t)i * s.C + j] + fd * fd;
+    }
   s.qrow.assign((size_t)s.R * s.C, 0);
   s.q_rows = 0;
   s.ldq = 0;
-  if (s.split_path()) {
+  if (s.split_path() && !s.outer) {
     int64_t smax = 0;
     for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
     s.ldq = round_up(smax, 32);
@@ -486,7 +504,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   AL(s.muij, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.muij_old, (int64_t)s.R * s.fslots * s.mpad);
   AL(s.Rpart, (int64_t)std::max(s.nsplit_max, s.nsplit_cz) * s.R * s.fslots * s.mpad);
-  if (s.split_path()) {
+  if (s.split_path() && !s.outer) {
     AL(s.Q1, s.q_rows * s.ldq);
     AL(s.Q2, s.q_rows * s.ldq);
     AL(s.Q3, s.q_rows * s.ldq);
@@ -499,6 +517,8 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
       s.nqjobs = (int)nq;
       AL(s.qjobs, nq);
     }
+  }
+  if (s.split_path()) {
     if (s.cached_z()) {
       AL(s.Zhi, s.nslots * s.fslots);
       AL(s.Zlo, s.nslots * s.fslots);
@@ -509,11 +529,13 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
       AL(s.p1jobs, s.np1);
       AL(s.p2jobs, s.np2);
     }
-  } else {
+  }
+  if (!s.split_path() || s.outer) {
     AL(s.rhs, (int64_t)s.R * s.fslots * s.mpad);
     AL(s.Q32, s.foff.back());
     AL(s.gdesc, s.R * s.C);
   }
+  if (s.outer) AL(s.U32, (int64_t)s.C * s.nslots * s.mpad);
   AL(s.lam_dev, s.mpad);
   AL(s.partials, 1024);
   AL(s.flag, 4);
@@ -590,13 +612,15 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   for (float* b : {s.W, s.Wbar, s.mu}) CK(cudaMemsetAsync(b, 0, colb, s.st));
   for (float* b : {s.What, s.muij}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
   if (s.rhs) CK(cudaMemsetAsync(s.rhs, 0, colb * s.R, s.st));
+  if (s.U32) CK(cudaMemsetAsync(s.U32, 0, rowb * s.C, s.st));
   CK(cudaMemsetAsync(s.Rpart, 0, colb * s.R * std::max(s.nsplit_max, s.nsplit_cz), s.st));
   if (s.split_path()) {
     CK(cudaMemsetAsync(s.VThi, 0, rowb / 2 * s.C, s.st));
     CK(cudaMemsetAsync(s.VTlo, 0, rowb / 2 * s.C, s.st));
     CK(cudaMemsetAsync(s.WThi, 0, colb / 2 * s.R, s.st));
     CK(cudaMemsetAsync(s.WTlo, 0, colb / 2 * s.R, s.st));
-    for (__nv_bfloat16* b : {s.rT1, s.rT2, s.rT3}) CK(cudaMemsetAsync(b, 0, colb / 2 * s.R, s.st));
+    for (__nv_bfloat16* b : {s.rT1, s.rT2, s.rT3})
+      if (b) CK(cudaMemsetAsync(b, 0, colb / 2 * s.R, s.st));
   }
   CK(launch_prox_loss(s.p.loss, s.O, s.Y, s.nslots, (int)s.m, s.mpad, s.t_loss, s.p.newton_iters, s.O, s.st));
   // zero O on padding rows (prox(0) with y = 0 is not zero for the squared loss only if y != 0; y = 0 there)
@@ -737,33 +761,39 @@ rff_status setup_factors(rff_admm_t h) {
   // random features: G and b from Philox (Sec. 4)
   CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, s.Ghi, s.Glo, s.gscale, s.bias,
                          s.bias_col, s.st));
-  // Gram matrices H_ij = I + Z_ij^T Z_ij (eq. (cache)), in FP64, batched by memory
+  // Gram matrices H_ij = I + Z_ij^T Z_ij (eq. (cache)), or I + Z_ij Z_ij^T in the outer
+  // form, in FP64, batched by memory
   int64_t smax = 0;
   for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
+  const int64_t nmax = *std::max_element(s.row_size.begin(), s.row_size.end());
+  const int64_t fmax = s.outer ? nmax : smax;          // factor dimension
   const int64_t nblocks = (int64_t)s.R * s.C;
   size_t fr = 0, tot = 0;
   CK(cudaMemGetInfo(&fr, &tot));
-  const size_t per_block = (size_t)smax * smax * 8 * 2;
-  const int64_t chunk_rows = std::min<int64_t>(32768, round_up(*std::max_element(s.row_size.begin(), s.row_size.end()), SLOT));
-  const size_t zbytes = (size_t)chunk_rows * smax * 4;
+  const size_t per_block = (size_t)fmax * fmax * 8 * 2;
+  const int64_t chunk_rows = std::min<int64_t>(32768, round_up(nmax, SLOT));
+  // outer form: Z_ij in chunks of feature columns, each transposed for the Gram kernel
+  const int64_t chunk_feat = std::min<int64_t>(2048, round_up(smax, SLOT));
+  const size_t zbytes = s.outer ? (size_t)nmax * chunk_feat * 4 * 2 : (size_t)chunk_rows * smax * 4;
   size_t budget = (size_t)(fr * 0.6);
   if (s.mem_limit) {
     const size_t ws = working_set_bytes(s);
     budget = std::min(budget, s.mem_limit > ws ? s.mem_limit - ws : (size_t)0);
   }
   budget = budget > zbytes + (256u << 20) ? budget - zbytes - (256u << 20) : 0;
-  int64_t batch = std::max<int64_t>(1, std::min<int64_t>(nblocks, (int64_t)(budget / std::max<size_t>(per_block + factor_scratch_bytes(1, (int)smax), 1))));
-  const size_t need = (size_t)batch * per_block + zbytes + factor_scratch_bytes((int)batch, (int)smax) + (size_t)batch * 4 + 4096;
+  int64_t batch = std::max<int64_t>(1, std::min<int64_t>(nblocks, (int64_t)(budget / std::max<size_t>(per_block + factor_scratch_bytes(1, (int)fmax), 1))));
+  const size_t need = (size_t)batch * per_block + zbytes + factor_scratch_bytes((int)batch, (int)fmax) + (size_t)batch * 4 + 4096;
   rff_status rs = ensure_scratch(h, need);
   if (rs != RFF_OK) return rs;
   char* base = static_cast<char*>(s.scratch.p);
   double* H64 = reinterpret_cast<double*>(base);
-  double* Q64 = H64 + batch * smax * smax;
-  float* Zc = reinterpret_cast<float*>(Q64 + batch * smax * smax);
-  int32_t* info = reinterpret_cast<int32_t*>(Zc + chunk_rows * smax);
+  double* Q64 = H64 + batch * fmax * fmax;
+  float* Zc = reinterpret_cast<float*>(Q64 + batch * fmax * fmax);
+  float* Zt = Zc + (s.outer ? nmax * chunk_feat : 0);   // transposed chunk (outer form)
+  int32_t* info = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(Zc) + zbytes);
   void* fscr = reinterpret_cast<char*>(info) + round_up(batch * 4, 256);
 
-  if (s.split_path())   // padding rows and columns of the split inverses stay zero
+  if (s.split_path() && !s.outer)   // padding rows and columns of the split inverses stay zero
     for (__nv_bfloat16* q : {s.Q1, s.Q2, s.Q3}) CK(cudaMemsetAsync(q, 0, (size_t)s.q_rows * s.ldq * 2, s.st));
   for (int64_t b0 = 0; b0 < nblocks; b0 += batch) {
     const int64_t nb = std::min(batch, nblocks - b0);
@@ -772,11 +802,25 @@ rff_status setup_factors(rff_admm_t h) {
     for (int64_t bb = 0; bb < nb; ++bb) {
       const int64_t blk = b0 + bb;
       const int i = (int)(blk / s.C), j = (int)(blk % s.C);
-      const int64_t sj = s.col_size[j];
-      double* Hb = H64 + bb * smax * smax;
-      double* Qb = Q64 + bb * smax * smax;
-      CK(cudaMemsetAsync(Hb, 0, sj * sj * 8, s.st));
-      for (int64_t r = 0; r < s.row_size[i]; r += chunk_rows) {
+      const int64_t sj = s.col_size[j], ni = s.row_size[i];
+      const int64_t fd = s.outer ? ni : sj;
+      double* Hb = H64 + bb * fmax * fmax;
+      double* Qb = Q64 + bb * fmax * fmax;
+      CK(cudaMemsetAsync(Hb, 0, fd * fd * 8, s.st));
+      // outer form: H = I + Z Z^T accumulated over feature chunks (the rows of Z^T)
+      for (int64_t f0 = 0; s.outer && f0 < sj; f0 += chunk_feat) {
+        const int64_t nf = std::min(chunk_feat, sj - f0);
+        if (s.split_path()) {
+          CK(tc_write_z(tc_view(s), s.row_slot[i], ni, s.col_slot[j] + f0, nf, Zc, nf));
+        } else {
+          ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, scale, s.row_of_slot, s.feat_of_slot,
+                   s.row_slot[i], ni, s.col_slot[j] + f0, nf, Zc, nf};
+          CK(launch_write_z_simt(za, s.st));
+        }
+        CK(launch_transpose_f32(Zc, ni, nf, Zt, ni, s.st));
+        CK(launch_gram_f32_to_f64(Zt, ni, nf, ni, Hb, ni, s.st));
+      }
+      for (int64_t r = 0; !s.outer && r < s.row_size[i]; r += chunk_rows) {
         const int64_t nr = std::min(chunk_rows, s.row_size[i] - r);
         if (s.split_path() && !s.cached_z()) {
           CK(tc_write_z(tc_view(s), s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj));
@@ -787,19 +831,19 @@ rff_status setup_factors(rff_admm_t h) {
         }
         CK(launch_gram_f32_to_f64(Zc, sj, nr, sj, Hb, sj, s.st));
       }
-      CK(launch_add_identity_and_mirror(Hb, sj, sj, s.st));
-      CK(cudaMemsetAsync(Qb, 0, sj * sj * 8, s.st));
-      CK(launch_set_diag(Qb, sj, sj, 1.0, s.st));
-      jobs.push_back(MatJob{Hb, sj, (int)sj, Qb, sj, info + bb});
+      CK(launch_add_identity_and_mirror(Hb, fd, fd, s.st));
+      CK(cudaMemsetAsync(Qb, 0, fd * fd * 8, s.st));
+      CK(launch_set_diag(Qb, fd, fd, 1.0, s.st));
+      jobs.push_back(MatJob{Hb, fd, (int)fd, Qb, fd, info + bb});
     }
     CK(factor_and_invert_f64(jobs, true, fscr, s.st));
     for (int64_t bb = 0; bb < nb; ++bb) {
       const int64_t blk = b0 + bb;
-      const int64_t sj = s.col_size[blk % s.C];
-      if (s.split_path())
-        CK(launch_split3_q(Q64 + bb * smax * smax, (int)sj, s.ldq, s.qrow[blk], s.Q1, s.Q2, s.Q3, s.st));
+      const int64_t fd = s.outer ? s.row_size[blk / s.C] : s.col_size[blk % s.C];
+      if (s.split_path() && !s.outer)
+        CK(launch_split3_q(Q64 + bb * fmax * fmax, (int)fd, s.ldq, s.qrow[blk], s.Q1, s.Q2, s.Q3, s.st));
       else
-        CK(launch_convert_f64_f32(Q64 + bb * smax * smax, s.Q32 + s.foff[blk], sj * sj, s.st));
+        CK(launch_convert_f64_f32(Q64 + bb * fmax * fmax, s.Q32 + s.foff[blk], fd * fd, s.st));
     }
     std::vector<int32_t> hinfo(nb);
     CK(cudaMemcpyAsync(hinfo.data(), info, nb * 4, cudaMemcpyDeviceToHost, s.st));
@@ -816,7 +860,12 @@ rff_status setup_factors(rff_admm_t h) {
     for (int j = 0; j < s.C; ++j) {
       const int64_t blk = (int64_t)i * s.C + j, sj = s.col_size[j];
       const int64_t off = ((int64_t)i * s.fslots + s.col_slot[j]) * s.mpad;
-      if (s.split_path()) {
+      if (s.outer) {
+        // O'_ij = (I + Z_ij Z_ij^T)^-1 u_ij, rows of block i in column block j
+        const int64_t ni = s.row_size[i], roff = ((int64_t)j * s.nslots + s.row_slot[i]) * s.mpad;
+        g[blk] = GemmDesc{s.Q32 + s.foff[blk], s.U32 + roff, nullptr, s.Op + roff, (int)ni, (int)s.mpad, (int)ni, ni,
+                          s.mpad, 0, s.mpad};
+      } else if (s.split_path()) {
         // one job per 128-row tile of Q_ij: rows of W'_ij, all m_pad columns, K = s_j
         for (int64_t m0 = 0; m0 < sj; m0 += 128) {
           SgJob jb{};
@@ -833,7 +882,7 @@ rff_status setup_factors(rff_admm_t h) {
         g[blk] = GemmDesc{Qb, s.rhs + off, nullptr, s.What + off, (int)sj, (int)s.mpad, (int)sj, sj, s.mpad, 0, s.mpad};
       }
     }
-  if (s.split_path()) {
+  if (s.split_path() && !s.outer) {
     if ((int)qj.size() != s.nqjobs) return h->fail(RFF_ECUDA, "internal: projection job count");
     CK(cudaMemcpyAsync(s.qjobs, qj.data(), qj.size() * sizeof(SgJob), cudaMemcpyHostToDevice, s.st));
   } else
@@ -955,8 +1004,92 @@ rff_status mark(rff_admm_t h, int k, int phase) {
   return RFF_OK;
 }
 
+// The row exchange, the next loss prox, V_ij and (tensor-core path) its FP16 split, then
+// the averaging and dual updates: the end of every iteration (phases 4..6).
+rff_status exchange_and_average(rff_admm_t h, int k) {
+  auto& s = *h;
+  const int64_t nfe = s.fslots * s.mpad;
+  rff_status r;
+  RowEpiArgs e{s.Op, s.O, s.Obar, s.nu, s.Y, s.V32, s.split_path() ? s.amax : nullptr, s.row_of_slot, s.nslots,
+               s.C, (int)s.m, (int)s.mpad, s.p.loss, s.p.newton_iters, s.t_loss};
+  if (s.split_path()) CK(cudaMemsetAsync(s.amax, 0, 4, s.st));
+  CK(launch_row_epilogue(e, s.st));
+  if (s.split_path())
+    CK(launch_transpose_split_f16(s.V32, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
+                                  s.mpad * s.nslots, 1.f, s.amax, s.st));
+  if ((r = mark(h, k, 5)) != RFF_OK) return r;
+  CK(launch_avg_dual(s.W, s.What, s.R, nfe, s.Wbar, s.mu, s.muij, s.st));
+  return mark(h, k, 6);
+}
+
+// One iteration with the outer form of the graph projection (every block has fewer rows
+// than features).  With P_ij = (I + Z_ij Z_ij^T)^-1 the projection of eq. (gpWij) is
+//   rhs = Wbar_j - mu'_ij + Z_ij^T V_ij,  O'_ij = P_ij (Z_ij rhs),  W'_ij = rhs - Z_ij^T O'_ij
+// (Z W' = (I - Z Z^T P) Z rhs = P Z rhs): three regenerations of Z_ij per iteration and
+// an n_i x n_i factor instead of s_j x s_j.  Phases: ms_project covers rhs, Z rhs, P and
+// Z^T O'; ms_pass2 is empty.
+rff_status iterate_outer(rff_admm_t h, int k) {
+  auto& s = *h;
+  const int64_t nfe = s.fslots * s.mpad;
+  const int64_t nmax = *std::max_element(s.row_size.begin(), s.row_size.end());
+  int* scratch_flag = reinterpret_cast<int*>(s.amax + 3);
+  rff_status r;
+  if ((r = mark(h, k, 0)) != RFF_OK) return r;
+  CK(launch_prox_reg(s.p.reg, s.Wbar, s.mu, nfe, s.t_reg, s.W, s.st, s.lam_dev, (int)s.mpad));
+  if ((r = mark(h, k, 1)) != RFF_OK) return r;
+  // R_ij = Z_ij^T V_ij
+  PassArgs a = base_pass_args(s);
+  if (s.split_path()) {
+    CK(tc_pass1(tc_view(s), s.Rpart));
+  } else {
+    a.M = s.V32;
+    a.m_block_stride = s.nslots * s.mpad;
+    a.out = s.Rpart;
+    a.out_block_stride = nfe;
+    CK(launch_pass1_simt(a, s.fslots, s.st));
+  }
+  if ((r = mark(h, k, 2)) != RFF_OK) return r;
+  // rhs, then u_ij = Z_ij rhs_ij into U32
+  CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st, s.feat_of_slot, (int)s.mpad));
+  if (s.split_path()) {
+    CK(cudaMemsetAsync(s.amax + 1, 0, 4, s.st));
+    CK(launch_finite_check(s.rhs, s.R * nfe, 0, scratch_flag, s.st, s.amax + 1));
+    CK(launch_transpose_split_f16(s.rhs, s.fslots, (int)s.mpad, s.R, nfe, s.WThi, s.WTlo, s.fslots,
+                                  s.mpad * s.fslots, 1.f, s.amax + 1, s.st));
+    CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.U32, 1, s.amax + 1));
+  } else {
+    PassArgs b = base_pass_args(s);
+    b.M = s.rhs;
+    b.m_block_stride = nfe;
+    b.out = s.U32;
+    b.out_block_stride = s.nslots * s.mpad;
+    b.per_block = 1;
+    CK(launch_pass2_simt(b, s.nslots, s.st));
+  }
+  // O'_ij = P_ij u_ij
+  CK(launch_gemm_f32_nn(s.gdesc, s.R * s.C, (int)nmax, (int)s.mpad, 1.f, 0.f, s.st));
+  // W'_ij = rhs_ij - Z_ij^T O'_ij (the second pass-1 product reuses the R partials)
+  if (s.split_path()) {
+    CK(cudaMemsetAsync(s.amax, 0, 4, s.st));
+    CK(launch_finite_check(s.Op, s.C * s.nslots * s.mpad, 0, scratch_flag, s.st, s.amax));
+    CK(launch_transpose_split_f16(s.Op, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
+                                  s.mpad * s.nslots, 1.f, s.amax, s.st));
+    CK(tc_pass1(tc_view(s), s.Rpart));
+  } else {
+    a.M = s.Op;
+    CK(launch_pass1_simt(a, s.fslots, s.st));
+  }
+  CK(launch_sub_partials(s.rhs, s.Rpart, s.nsplit, s.R, nfe, s.feat_of_slot, (int)s.mpad, s.What, s.st));
+  if ((r = mark(h, k, 3)) != RFF_OK) return r;
+  if ((r = mark(h, k, 4)) != RFF_OK) return r;
+  if ((r = exchange_and_average(h, k)) != RFF_OK) return r;
+  s.launches += s.split_path() ? 14 : 9;
+  return RFF_OK;
+}
+
 rff_status iterate(rff_admm_t h, int k) {
   auto& s = *h;
+  if (s.outer) return iterate_outer(h, k);
   const int64_t nfe = s.fslots * s.mpad;
   const int64_t nblocks = (int64_t)s.R * s.C;
   int64_t smax = 0;
@@ -1011,19 +1144,9 @@ rff_status iterate(rff_admm_t h, int k) {
     CK(launch_pass2_simt(a, s.nslots, s.st));
   }
   if ((r = mark(h, k, 4)) != RFF_OK) return r;
-  // exchange, nu update, next loss prox, next V_ij
-  RowEpiArgs e{s.Op, s.O, s.Obar, s.nu, s.Y, s.V32, s.split_path() ? s.amax : nullptr, s.row_of_slot, s.nslots,
-               s.C, (int)s.m, (int)s.mpad, s.p.loss, s.p.newton_iters, s.t_loss};
-  if (s.split_path()) CK(cudaMemsetAsync(s.amax, 0, 4, s.st));
-  CK(launch_row_epilogue(e, s.st));
-  // the tensor-core path reads V^T as a scaled FP16 hi/lo pair
-  if (s.split_path())
-    CK(launch_transpose_split_f16(s.V32, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
-                                  s.mpad * s.nslots, 1.f, s.amax, s.st));
-  if ((r = mark(h, k, 5)) != RFF_OK) return r;
-  // averaging and dual updates
-  CK(launch_avg_dual(s.W, s.What, s.R, nfe, s.Wbar, s.mu, s.muij, s.st));
-  if ((r = mark(h, k, 6)) != RFF_OK) return r;
+  // exchange, nu update, next loss prox, next V_ij (the tensor-core path reads V^T as a
+  // scaled FP16 hi/lo pair), averaging and dual updates
+  if ((r = exchange_and_average(h, k)) != RFF_OK) return r;
   s.launches += s.split_path() ? 9 : 7;
   return RFF_OK;
 }
@@ -1076,7 +1199,7 @@ rff_status enqueue_iterations(rff_admm_t h, int iters, bool copy_old) {
     } else {
       if (!s.gexec && (r = capture_iteration(h)) != RFF_OK) return r;
       CK(cudaGraphLaunch(s.gexec, s.st));
-      s.launches += s.split_path() ? 9 : 7;
+      s.launches += s.outer ? (s.split_path() ? 14 : 9) : (s.split_path() ? 9 : 7);
     }
     if (r != RFF_OK) return r;
     s.iters_done++;

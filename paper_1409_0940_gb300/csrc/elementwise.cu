@@ -284,14 +284,53 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
   }
 }
 
+// rhs = Wbar - mu'_ij + sum of the R partials (padding feature slots zero when feat_ok is given)
 __global__ void k_rhs(const float* __restrict__ Wbar, const float* __restrict__ muij, const float* __restrict__ Rpart,
-                      int nsplit, int R, int64_t nfe, float* __restrict__ rhs) {
+                      int nsplit, int R, int64_t nfe, const int32_t* __restrict__ feat_ok, int mpad,
+                      float* __restrict__ rhs) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)R * nfe) return;
   const int64_t e = t % nfe;
+  if (feat_ok && feat_ok[e / mpad] < 0) {
+    rhs[t] = 0.f;
+    return;
+  }
   float acc = Wbar[e] - muij[t];
   for (int s = 0; s < nsplit; ++s) acc += Rpart[(int64_t)s * R * nfe + t];
   rhs[t] = acc;
+}
+
+// W'_ij = rhs_ij - Z_ij^T O'_ij from the R partials of the second pass-1 product (outer
+// form of the projection); padding feature slots zero
+__global__ void k_sub_partials(const float* __restrict__ rhs, const float* __restrict__ Rpart, int nsplit, int R,
+                               int64_t nfe, const int32_t* __restrict__ feat_ok, int mpad, float* __restrict__ What) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)R * nfe) return;
+  const int64_t e = t % nfe;
+  if (feat_ok[e / mpad] < 0) {
+    What[t] = 0.f;
+    return;
+  }
+  float acc = 0.f;
+  for (int s = 0; s < nsplit; ++s) acc += Rpart[(int64_t)s * R * nfe + t];
+  What[t] = rhs[t] - acc;
+}
+
+// dst[c][r] = src[r][c] (src rows x cols, dst ld dld)
+__global__ void k_transpose_f32(const float* __restrict__ src, int64_t rows, int64_t cols, float* __restrict__ dst,
+                                int64_t dld) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t r = r0 + rr, c = c0 + tx;
+    tile[rr][tx] = (r < rows && c < cols) ? src[r * cols + c] : 0.f;
+  }
+  __syncthreads();
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int64_t c = c0 + cc, r = r0 + tx;
+    if (c < cols && r < rows) dst[c * dld + r] = tile[tx][cc];
+  }
 }
 
 // Wbar = (W + sum_i W'_i)/(R+1);  mu += W - Wbar;  mu'_i += W'_i - Wbar
@@ -536,8 +575,22 @@ cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_rhs(const float* Wbar, const float* muij, const float* Rpart, int nsplit, int R, int64_t nfe,
-                       float* rhs, cudaStream_t st) {
-  k_rhs<<<nblk((int64_t)R * nfe), 256, 0, st>>>(Wbar, muij, Rpart, nsplit, R, nfe, rhs);
+                       float* rhs, cudaStream_t st, const int32_t* feat_ok, int mpad) {
+  k_rhs<<<nblk((int64_t)R * nfe), 256, 0, st>>>(Wbar, muij, Rpart, nsplit, R, nfe, feat_ok, mpad > 0 ? mpad : 1, rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub_partials(const float* rhs, const float* Rpart, int nsplit, int R, int64_t nfe,
+                                const int32_t* feat_ok, int mpad, float* What, cudaStream_t st) {
+  k_sub_partials<<<nblk((int64_t)R * nfe), 256, 0, st>>>(rhs, Rpart, nsplit, R, nfe, feat_ok, mpad, What);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_f32(const float* src, int64_t rows, int64_t cols, float* dst, int64_t dld,
+                                 cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32));
+  k_transpose_f32<<<grid, 256, 0, st>>>(src, rows, cols, dst, dld);
   return cudaGetLastError();
 }
 

@@ -131,7 +131,13 @@ struct RowEpiArgs {
 };
 cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st);
 cudaError_t launch_rhs(const float* Wbar, const float* muij, const float* Rpart, int nsplit, int R, int64_t nfe,
-                       float* rhs, cudaStream_t st);
+                       float* rhs, cudaStream_t st, const int32_t* feat_ok = nullptr, int mpad = 0);
+// W' = rhs - sum of the nsplit partials, padding feature slots zero (outer form)
+cudaError_t launch_sub_partials(const float* rhs, const float* Rpart, int nsplit, int R, int64_t nfe,
+                                const int32_t* feat_ok, int mpad, float* What, cudaStream_t st);
+// dst[c][r] = src[r][c]
+cudaError_t launch_transpose_f32(const float* src, int64_t rows, int64_t cols, float* dst, int64_t dld,
+                                 cudaStream_t st);
 cudaError_t launch_avg_dual(const float* W, const float* What, int R, int64_t nfe, float* Wbar, float* mu,
                             float* muij, cudaStream_t st);
 // hi/lo FP16 split of src^T scaled by f16_scale(*amax) (amax non-null) or by scale

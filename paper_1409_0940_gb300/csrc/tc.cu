@@ -43,6 +43,7 @@ constexpr int NTHREADS = 64 + 32 * NEPI;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC2_COL = 256;
 constexpr int MAXG = 64;                    // groups (column blocks) per CTA
+constexpr int PRED_GT = 8;                  // feature tiles per scoring group
 
 // Ring geometry.  KC = K elements per ring stage: 64 (128-byte rows, 128-byte
 // swizzle, 64 KB stages) or 32 (64-byte rows, 64-byte swizzle, 32 KB stages, so
@@ -176,10 +177,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
           ++ng;
         }
       } else {
-        sh.g_b0[0] = 0;
-        sh.g_nt[0] = (int)(a.fslots / 128);
-        sh.g_out[0] = a.out + a_row0 * a.mpad;
-        ng = 1;
+        // scoring: the features in groups of up to PRED_GT tiles, each group accumulated in
+        // a fresh acc2 and added into the output rows in FP32 (the tensor cores' accumulator
+        // rounds toward zero at every accumulation; shorter chains keep its bias small)
+        const int ntiles = (int)(a.fslots / 128);
+        const int gt = max(PRED_GT, (int)ceil_div(ntiles, MAXG));
+        for (int t0 = 0; t0 < ntiles && ng < MAXG; t0 += gt) {
+          sh.g_b0[ng] = (int64_t)t0 * 128;
+          sh.g_nt[ng] = min(gt, ntiles - t0);
+          sh.g_out[ng] = a.out + a_row0 * a.mpad;
+          ++ng;
+        }
       }
     } else if (a.mode == MODE_PASS1) {
       a_row0 = (int64_t)blockIdx.x * 128;
@@ -509,10 +517,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
             tmem_ld8(tmem + lane_addr + ACC2_COL + c0 + c, r8);
             tmem_wait_ld();
             float4* dst = reinterpret_cast<float4*>(orow + c0 + c);
-            dst[0] = make_float4(sc * __uint_as_float(r8[0]), sc * __uint_as_float(r8[1]),
-                                 sc * __uint_as_float(r8[2]), sc * __uint_as_float(r8[3]));
-            dst[1] = make_float4(sc * __uint_as_float(r8[4]), sc * __uint_as_float(r8[5]),
-                                 sc * __uint_as_float(r8[6]), sc * __uint_as_float(r8[7]));
+            float4 v0 = make_float4(sc * __uint_as_float(r8[0]), sc * __uint_as_float(r8[1]),
+                                    sc * __uint_as_float(r8[2]), sc * __uint_as_float(r8[3]));
+            float4 v1 = make_float4(sc * __uint_as_float(r8[4]), sc * __uint_as_float(r8[5]),
+                                    sc * __uint_as_float(r8[6]), sc * __uint_as_float(r8[7]));
+            if (a.mode == MODE_PREDICT && g > 0) {   // this CTA wrote these rows for group g-1
+              const float4 p0 = dst[0], p1 = dst[1];
+              v0 = make_float4(p0.x + v0.x, p0.y + v0.y, p0.z + v0.z, p0.w + v0.w);
+              v1 = make_float4(p1.x + v1.x, p1.y + v1.y, p1.z + v1.z, p1.w + v1.w);
+            }
+            dst[0] = v0;
+            dst[1] = v1;
           }
           fence_before();
           __syncwarp();
