@@ -225,8 +225,12 @@ def run_ours(args, rank, world):
     per_launch_ms = prof[ph] / max(prof["iters"], 1)
     achieved = exec_pass / (per_launch_ms * 1e-3) / 1e12
     if args.prec == "split_bf16":
+        # DRAM bytes per launch from the ncu capture of k_regen_tc<64, 1> at n = 100k, scaled to
+        # the 200k-row workload by rows (profiles/k_regen_tc_multiclass_100k.md)
+        traffic = {"pass1": 1.647e9, "pass2": 1.361e9}.get(ph[3:]) if not args.n else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sus, "unit": "TFLOP/s",
-                "frac": achieved / bf16_sus, "traffic": None, "kernel": ph[3:], "peak_source": src + " sustained bf16"}
+                "frac": achieved / bf16_sus, "traffic": traffic, "kernel": ph[3:],
+                "peak_source": src + " sustained bf16"}
     elif args.prec == "cached_z":
         # the streamed pass reads Z once: HBM-bound (the tensor work, 3 x 2 n D m_pad, would take
         # slightly less time at the sustained BF16 peak)
@@ -303,6 +307,42 @@ def run_reference(args, rank, world):
 SWEEP = dict(name="sweep-8sigma-x-8lambda-logistic-d128", sigmas=[1, 2, 4, 8, 16, 32, 64, 128],
              lambdas=[1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9], Ds=[1024, 2048, 4096, 8192], d=128,
              n_lo=10_000, n_hi=400_000, seed=7)
+
+
+def run_ridge(args):
+    """The small ridge solve (n = 2000, d = 16, D = 512, one 1 x 1 block, squared + l2,
+    lambda = 1e-4, 200 iterations): launch- and latency-bound, so the measure is the time of
+    one iteration replayed as a CUDA graph, and of the whole 200-iteration solve."""
+    import numpy as np
+    import torch
+
+    import paper_1409_0940_gb300 as rff
+    import synth
+    X, y = synth.ridge(n=2000, d=16, seed=0)
+    stream = torch.cuda.Stream()
+    s = rff.Solver(stream=stream.cuda_stream, prec=args.prec, loss="squared", reg="l2", lam=1e-4, sigma=4.0,
+                   rho=1.0, D=512, R=1, C=1, seed=1, m=1)
+    s.set_data(X, y)
+    s.solve(max(args.warmup, 3), stats=False)        # set-up, eager first iteration, graph capture
+    torch.cuda.synchronize()
+    iters = 200
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        s.solve(iters, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    s.close()
+    return {"metric": "ridge iteration latency", "value": 1e3 * ms / iters, "unit": "us/iter", "n_gpus": 1,
+            "steps": iters, "warmup": max(args.warmup, 3), "ms_per_step": ms / iters, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f16x3",
+            "data": "synthetic",
+            "config": {"workload": "ridge-2000-d16-D512-1x1", "iterations": iters, "prec": args.prec,
+                       "timing": "CUDA events around 200 graph-replayed iterations"},
+            "gpu_launches_per_iter": int(prof["launches"]) / (iters + max(args.warmup, 3)),
+            "solve_ms_200_iters": ms, "clocks": clk.summary()}
 
 
 def run_sweep(args):
@@ -444,12 +484,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-compare", action="store_true", help="skip the other precisions (profiling runs)")
     ap.add_argument("--n", type=int, default=0, help="rows of a reduced workload (profiling runs)")
-    ap.add_argument("--workload", default="multiclass", choices=["multiclass", "sweep", "serve"])
+    ap.add_argument("--workload", default="multiclass", choices=["multiclass", "ridge", "sweep", "serve"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.workload != "multiclass":
-        line = run_sweep(args) if args.workload == "sweep" else run_serve(args)
+        line = {"sweep": run_sweep, "serve": run_serve, "ridge": run_ridge}[args.workload](args)
         print(json.dumps(line), flush=True)
         return
     if args.impl == "reference":
