@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(name="multiclass-200k-d440-D16384-m147-4x4", n=200_000, d=440, m=147, sigma=10.0, D=16384, R=4,
                 C=4, loss="squared", reg="l2", lam=1e-5, rho=1.0, data_seed=1, philox_seed=2)
 METRIC = "ADMM iter/s"
+TRAFFIC_200K = {}     # kernel -> DRAM bytes per launch (see run_ours)
 
 
 def peaks():
@@ -225,9 +226,10 @@ def run_ours(args, rank, world):
     per_launch_ms = prof[ph] / max(prof["iters"], 1)
     achieved = exec_pass / (per_launch_ms * 1e-3) / 1e12
     if args.prec == "split_bf16":
-        # DRAM bytes per launch from the ncu capture of k_regen_tc<64, 1> at n = 100k, scaled to
-        # the 200k-row workload by rows (profiles/k_regen_tc_multiclass_100k.md)
-        traffic = {"pass1": 1.647e9, "pass2": 1.361e9}.get(ph[3:]) if not args.n else None
+        # DRAM bytes per launch from an ncu capture of the current k_regen_tc at n = 100k, scaled
+        # to the 200k-row workload by rows (profiles/k_regen_tc_multiclass_100k.md); None while
+        # the kernel has changed since the last capture
+        traffic = TRAFFIC_200K.get(ph[3:]) if not args.n else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sus, "unit": "TFLOP/s",
                 "frac": achieved / bf16_sus, "traffic": traffic, "kernel": ph[3:],
                 "peak_source": src + " sustained bf16"}

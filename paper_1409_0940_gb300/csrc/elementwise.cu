@@ -227,17 +227,33 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
     const int64_t p = p0 + r;
     const bool ok = a.row_ok[p] >= 0;
     const int64_t base = p * mp;
-    float w_in[MAXPL], y[MAXPL];
+    float w_in[MAXPL], y[MAXPL], Ov[MAXPL], nuv[MAXPL], Sv[MAXPL];
+    // all of the row's loads first (independent, so they are in flight together)
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) {
+      const int k = lane + 32 * q;
+      const bool in = k < mp;
+      Ov[q] = in ? a.O[base + k] : 0.f;
+      nuv[q] = in ? a.nu[base + k] : 0.f;
+      y[q] = in ? a.Y[base + k] : 0.f;
+      Sv[q] = 0.f;
+    }
+    for (int j = 0; j < a.C; ++j) {
+      const float* opj = a.Op + j * jstride + base;
+#pragma unroll
+      for (int q = 0; q < MAXPL; ++q) {
+        const int k = lane + 32 * q;
+        if (k < mp) Sv[q] += opj[k];
+      }
+    }
 #pragma unroll
     for (int q = 0; q < MAXPL; ++q) {
       const int k = lane + 32 * q;
       w_in[q] = 0.f;
-      y[q] = 0.f;
       if (k >= mp) continue;
-      float S = 0.f;
-      for (int j = 0; j < a.C; ++j) S += a.Op[j * jstride + base + k];
-      const float O = a.O[base + k];
-      float nu = a.nu[base + k];
+      const float S = Sv[q];
+      const float O = Ov[q];
+      float nu = nuv[q];
       const float Delta = O - S;
       const float Obar = S * inv_c1 + cfrac * O;
       nu += O - Obar;
@@ -245,10 +261,8 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
       a.Obar[base + k] = live ? Obar : 0.f;
       a.nu[base + k] = live ? nu : 0.f;
       term[r * mp + k] = live ? Delta * inv_c1 + nu : 0.f;
-      if (live) {
-        w_in[q] = Obar - nu;
-        y[q] = a.Y[base + k];
-      }
+      if (live) w_in[q] = Obar - nu;
+      else y[q] = 0.f;
     }
     float o[MAXPL];
     if (LOSS == LOSS_MULTINOMIAL) {

@@ -23,6 +23,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -61,7 +62,7 @@ struct Ring {
   static constexpr uint32_t ROWB = KC * 2;               // bytes per operand row in a stage
   static constexpr uint32_t TILEB = 128 * ROWB;          // one 128-row operand tile
   static constexpr uint32_t STAGEB = 4 * TILEB;          // A hi, A lo, B hi, B lo
-  static constexpr int NS = ZT ? ((KC == 64) ? 3 : 6) : ((KC == 64) ? 2 : 5);   // stages
+  static constexpr int NS = ZT ? ((KC == 64) ? 3 : 6) : ((KC == 64) ? 2 : 4);   // stages
   static constexpr int KSTEPS = KC / 16;                 // MMA K steps per stage
   static constexpr int CHUNKS = 128 / KC;                // chain-operand chunks per B tile
   static constexpr uint32_t LAYOUT = (KC == 64) ? 2 : 4; // descriptor layout: 128B / 64B swizzle
@@ -69,9 +70,7 @@ struct Ring {
   static constexpr uint32_t ZSMEM = ZT ? 0 : ZBYTES;     // shared memory of the Z tile
 };
 template <int KC, int ZT>
-constexpr size_t smem_bytes() {
-  return 1024 + Ring<KC, ZT>::NS * Ring<KC, ZT>::STAGEB + Ring<KC, ZT>::ZSMEM + 256 + MAXG * 24;
-}
+constexpr size_t smem_bytes();   // defined after Shared
 constexpr uint32_t ZH_COL = 128, ZL_COL = 192;   // Z hi / lo in TMEM (ZT = 1), 64 columns each
 
 // error codes written to the error word
@@ -84,6 +83,7 @@ struct TcArgs {
   const int32_t* a_ok;
   const int32_t* b_ok;
   float scale;
+  int64_t nrow_tiles;                       // pass 2: 128-row tiles of the data (work items x C)
   float inv_xg;                             // X.G accumulator -> X G (1 / (xscale gscale))
   const unsigned* m_amax;                   // max |M| of the chained operand (its FP16 split scale)
   const int64_t* row_slot;
@@ -115,7 +115,18 @@ struct Shared {
   int64_t g_b0[MAXG];
   int g_nt[MAXG];
   float* g_out[MAXG];
+  int64_t g_arow[MAXG];   // A tile row of the group (pass 2 takes work items of several row tiles)
+  int g_my[MAXG];         // chained-operand row of the group
 };
+
+template <int KC, int ZT>
+constexpr size_t smem_bytes() {
+  // 1024 bytes of alignment slack, the ring, the Z tile, the barriers and the work plan
+  return 1024 + Ring<KC, ZT>::NS * Ring<KC, ZT>::STAGEB + Ring<KC, ZT>::ZSMEM + sizeof(Shared<Ring<KC, ZT>::NS>);
+}
+static_assert(smem_bytes<64, 0>() <= 232448 && smem_bytes<64, 1>() <= 232448 && smem_bytes<32, 0>() <= 232448 &&
+                  smem_bytes<32, 1>() <= 232448,
+              "every ring geometry fits the 227 KB of shared memory a CTA may use");
 
 // bounded wait; one thread polls.  false = the CTA is aborting
 template <class SH>
@@ -163,20 +174,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
   if (threadIdx.x == 0) {
     sh.abort_flag = 0;
     int ng = 0;
-    if (a.mode == MODE_PASS2 || a.mode == MODE_PREDICT) {
+    if (a.mode == MODE_PASS2) {
+      // persistent over work items (row tile rt, column block j), item = rt C + j: CTA c
+      // takes items c, c + G, c + 2G, ... (G = gridDim.x), so the CTAs' loads differ by at
+      // most one item and neighbouring CTAs share row tiles in L2
+      const int64_t nitems = a.nrow_tiles * a.C;
+      for (int64_t it = blockIdx.x; it < nitems && ng < MAXG; it += gridDim.x) {
+        const int64_t arow = (it / a.C) * 128;
+        const int j = (int)(it % a.C);
+        int i = 0;
+        while (i + 1 < a.R && a.row_slot[i + 1] <= arow) ++i;
+        sh.g_b0[ng] = a.col_slot[j];
+        sh.g_nt[ng] = (int)ceil_div(a.col_size[j], 128);
+        sh.g_out[ng] = a.out + j * a.out_block_stride + arow * a.mpad;
+        sh.g_arow[ng] = arow;
+        sh.g_my[ng] = i * a.mpad;
+        ++ng;
+      }
+      if (ng > 0) {
+        a_row0 = sh.g_arow[0];
+        m_y = sh.g_my[0];
+      }
+    } else if (a.mode == MODE_PREDICT) {
       a_row0 = (int64_t)blockIdx.x * 128;
-      int i = 0;
-      if (a.mode == MODE_PASS2)
-        while (i + 1 < a.R && a.row_slot[i + 1] <= a_row0) ++i;
-      m_y = i * a.mpad;
-      if (a.mode == MODE_PASS2) {
-        for (int j = 0; j < a.C && ng < MAXG; ++j) {
-          sh.g_b0[ng] = a.col_slot[j];
-          sh.g_nt[ng] = (int)ceil_div(a.col_size[j], 128);
-          sh.g_out[ng] = a.out + j * a.out_block_stride + a_row0 * a.mpad;
-          ++ng;
-        }
-      } else {
+      m_y = 0;
+      {
         // scoring: the features in groups of up to PRED_GT tiles, each group accumulated in
         // a fresh acc2 and added into the output rows in FP32 (the tensor cores' accumulator
         // rounds toward zero at every accumulation; shorter chains keep its bias small)
@@ -210,6 +232,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
       sh.g_out[0] = nullptr;
       ng = 1;
     }
+    if (a.mode != MODE_PASS2)
+      for (int g = 0; g < ng; ++g) {
+        sh.g_arow[g] = a_row0;
+        sh.g_my[g] = m_y;
+      }
     sh.ngroups = ng;
     sh.a_row0 = a_row0;
     sh.m_y = m_y;
@@ -263,6 +290,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
       uint32_t it = 0;   // ring uses
       bool ok = true;
       int64_t prev_b = -1;
+      int prev_my = 0;
       auto acquire = [&](uint32_t bytes) -> int {
         const int s = it % NSTAGE;
         const uint32_t use = it / NSTAGE;
@@ -277,8 +305,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
           if (s < 0) return false;
           const uint32_t dst = smem_u32(stages + s * STAGE_BYTES);
           const uint32_t fb = bar_full + 8 * s;
-          tma_load_2d(dst, &a.tM_hi, (int)(bslot + KC * c), m_y, fb);
-          tma_load_2d(dst + mbytes, &a.tM_lo, (int)(bslot + KC * c), m_y, fb);
+          tma_load_2d(dst, &a.tM_hi, (int)(bslot + KC * c), prev_my, fb);
+          tma_load_2d(dst + mbytes, &a.tM_lo, (int)(bslot + KC * c), prev_my, fb);
         }
         return true;
       };
@@ -290,13 +318,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
             if (s < 0) { ok = false; break; }
             const uint32_t dst = smem_u32(stages + s * STAGE_BYTES);
             const uint32_t fb = bar_full + 8 * s;
-            tma_load_2d(dst, &a.tA_hi, kc * KC, (int)a_row0, fb);
-            tma_load_2d(dst + TILE_BYTES, &a.tA_lo, kc * KC, (int)a_row0, fb);
+            tma_load_2d(dst, &a.tA_hi, kc * KC, (int)sh.g_arow[g], fb);
+            tma_load_2d(dst + TILE_BYTES, &a.tA_lo, kc * KC, (int)sh.g_arow[g], fb);
             tma_load_2d(dst + 2 * TILE_BYTES, &a.tB_hi, kc * KC, (int)bslot, fb);
             tma_load_2d(dst + 3 * TILE_BYTES, &a.tB_lo, kc * KC, (int)bslot, fb);
           }
           if (ok && chain && prev_b >= 0) ok = load_chain(prev_b);
           prev_b = bslot;
+          prev_my = sh.g_my[g];
         }
       }
       if (ok && chain && prev_b >= 0) ok = load_chain(prev_b);
@@ -560,7 +589,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// K chunk of the ring (64: 128-byte swizzle, 2 stages; 32: 64-byte swizzle, 5 stages).
+// K chunk of the ring (64: 128-byte swizzle, 2 or 3 stages; 32: 64-byte swizzle, 4 or 6 stages).
 // Measured on the multiclass workload: 64 is ~5 % faster (both are bound by shared-
 // memory bandwidth, see the profile notes), so it is the default; RFF_TC_KCHUNK=32
 // in the environment selects the other ring.
@@ -620,6 +649,19 @@ int* err_word() {
     else p = nullptr;
   });
   return p;
+}
+
+int sm_count() {
+  static int n = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      n = 148;
+    }
+  });
+  return n;
 }
 
 int view_kc(const TcView& v) { return (v.kc == 32 || v.kc == 64) ? v.kc : ring_kc(); }
@@ -716,13 +758,18 @@ cudaError_t tc_pass2(const TcView& v, const __half* Mhi, const __half* Mlo, int6
   a.out = out;
   a.out_block_stride = v.nslots * v.mpad;
   a.m_amax = m_amax;
+  a.nrow_tiles = v.nslots / 128;
   if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tB_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tM_hi, Mhi, v.fslots, (int64_t)v.R * v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tM_lo, Mlo, v.fslots, (int64_t)v.R * v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
-  return launch(a, dim3((unsigned)(v.nslots / 128)), v.st, view_kc(v), view_zt(v));
+  // persistent: one CTA per SM (the ring fills most of shared memory), enough CTAs that
+  // none takes more than MAXG work items
+  const int64_t nitems = a.nrow_tiles * v.C;
+  const int64_t grid = std::min<int64_t>(nitems, std::max<int64_t>(sm_count(), ceil_div(nitems, MAXG)));
+  return launch(a, dim3((unsigned)grid), v.st, view_kc(v), view_zt(v));
 }
 
 cudaError_t tc_predict(const TcView& v, const __half* Xh, const __half* Xl, int64_t nrows,
