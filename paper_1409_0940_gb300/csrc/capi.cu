@@ -836,7 +836,7 @@ rff_status setup_factors(rff_admm_t h) {
       CK(launch_set_diag(Qb, fd, fd, 1.0, s.st));
       jobs.push_back(MatJob{Hb, fd, (int)fd, Qb, fd, info + bb});
     }
-    CK(factor_and_invert_f64(jobs, true, fscr, s.st));
+    CK(factor_and_invert_f64(jobs, true, fscr, s.st, true));
     for (int64_t bb = 0; bb < nb; ++bb) {
       const int64_t blk = b0 + bb;
       const int64_t fd = s.outer ? s.row_size[blk / s.C] : s.col_size[blk % s.C];

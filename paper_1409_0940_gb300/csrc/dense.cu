@@ -145,6 +145,102 @@ __global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict_
 // the error of one 32-term FP32 sum.  (An FP32 accumulator over all rows, or
 // over chunks of a few hundred rows, perturbs H enough to move the ADMM fixed
 // point by ~kappa(H) * 1e-7.)
+// ------------------------------------------------------------------ double-float GEMM
+// The FP64 GEMM of the set-up factorisation in double-float arithmetic on the FP32 pipes
+// (this part issues FP32 FMAs at 64 times its FP64 rate).  Each FP64 input is held as a
+// float pair x = hi + lo (48 significant bits); a product a b is formed exactly as
+// p + e by p = a_hi b_hi, e = fma(a_hi, b_hi, -p), plus the cross terms a_hi b_lo and
+// a_lo b_hi (a_lo b_lo, 2^-48 relative, is dropped); the accumulator is a float pair
+// updated by TwoSum (Knuth), the error terms gathered in its low part.  The result is
+// hi + lo in FP64: about 2^-44 relative per K = 64 dot product, enough for a factor whose
+// inverse feeds FP32 and three-term BF16 iterations.  Same tiling and interface as k_gemm.
+constexpr int DF_BK = 16;
+__global__ void __launch_bounds__(256) k_gemm_df(const GemmDesc* __restrict__ descs, int transA, int transB,
+                                                 double alpha, double beta, int lower_only) {
+  const GemmDesc g = descs[blockIdx.z];
+  const int tm = blockIdx.x, tn = blockIdx.y;
+  if (tm * 64 >= g.M || tn * 64 >= g.N) return;
+  if (lower_only && tn > tm) return;
+  const double* __restrict__ A = static_cast<const double*>(g.A);
+  const double* __restrict__ B = static_cast<const double*>(g.B);
+  __shared__ float Ah[DF_BK][64 + 1], Al[DF_BK][64 + 1];
+  __shared__ float Bh[DF_BK][64 + 1], Bl[DF_BK][64 + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  float hi[4][4], lo[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
+  const int m0 = tm * 64, n0 = tn * 64;
+  for (int k0 = 0; k0 < g.K; k0 += DF_BK) {
+    for (int t = tid; t < 64 * DF_BK; t += 256) {
+      int mm, kk;
+      if (transA) { mm = t % 64; kk = t / 64; } else { kk = t % DF_BK; mm = t / DF_BK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      double v = 0.0;
+      if (gm < g.M && gk < g.K) v = transA ? A[(int64_t)gk * g.lda + gm] : A[(int64_t)gm * g.lda + gk];
+      const float vh = __double2float_rn(v);
+      Ah[kk][mm] = vh;
+      Al[kk][mm] = __double2float_rn(v - (double)vh);
+      int nn, kb;
+      if (transB) { kb = t % DF_BK; nn = t / DF_BK; } else { nn = t % 64; kb = t / 64; }
+      const int gn = n0 + nn, gkb = k0 + kb;
+      double w = 0.0;
+      if (gn < g.N && gkb < g.K) w = transB ? B[(int64_t)gn * g.ldb + gkb] : B[(int64_t)gkb * g.ldb + gn];
+      const float wh = __double2float_rn(w);
+      Bh[kb][nn] = wh;
+      Bl[kb][nn] = __double2float_rn(w - (double)wh);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < DF_BK; ++k) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ah[i] = Ah[k][ty * 4 + i];
+        al[i] = Al[k][ty * 4 + i];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        bh[j] = Bh[k][tx * 4 + j];
+        bl[j] = Bl[k][tx * 4 + j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          // the rounded product and the TwoSum steps must not be contracted into FMAs:
+          // the exact-error identities hold only for separately rounded operations
+          const float p = __fmul_rn(ah[i], bh[j]);
+          float e = fmaf(ah[i], bh[j], -p);
+          e = fmaf(ah[i], bl[j], e);
+          e = fmaf(al[i], bh[j], e);
+          const float s = __fadd_rn(hi[i][j], p);
+          const float bb = __fsub_rn(s, hi[i][j]);
+          const float err = __fadd_rn(__fsub_rn(hi[i][j], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+          lo[i][j] += err + e;
+          hi[i][j] = s;
+        }
+    }
+    __syncthreads();
+  }
+  const double* __restrict__ Cm = static_cast<const double*>(g.Cm);
+  double* __restrict__ D = static_cast<double*>(g.D);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty * 4 + i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx * 4 + j;
+      if (gn >= g.N) continue;
+      double v = alpha * ((double)hi[i][j] + (double)lo[i][j]);
+      if (beta != 0.0) v = fma(beta, Cm[(int64_t)gm * g.ldc + gn], v);
+      D[(int64_t)gm * g.ldd + gn] = v;
+    }
+  }
+}
+
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   const float s = hi + x;
   const float bb = s - hi;
@@ -284,10 +380,13 @@ cudaError_t launch_gemm_f32_nn(const GemmDesc* descs_dev, int nbatch, int maxM, 
 }
 
 cudaError_t launch_gemm_f64(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, int transA, int transB,
-                            double alpha, double beta, int lower_only, cudaStream_t st) {
+                            double alpha, double beta, int lower_only, cudaStream_t st, bool double_float) {
   if (nbatch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(maxM, 64), (unsigned)ceil_div(maxN, 64), (unsigned)nbatch);
-  k_gemm<double, 16><<<grid, 256, 0, st>>>(descs_dev, transA, transB, alpha, beta, lower_only);
+  if (double_float)
+    k_gemm_df<<<grid, 256, 0, st>>>(descs_dev, transA, transB, alpha, beta, lower_only);
+  else
+    k_gemm<double, 16><<<grid, 256, 0, st>>>(descs_dev, transA, transB, alpha, beta, lower_only);
   return cudaGetLastError();
 }
 
@@ -345,7 +444,8 @@ size_t factor_scratch_bytes(int njobs, int smax) {
          (size_t)njobs * nb * 6 * sizeof(GemmDesc) + 1024;
 }
 
-cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st) {
+cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st,
+                                  bool double_float) {
   const int nj = (int)jobs.size();
   if (nj == 0) return cudaSuccess;
   int smax = 0;
@@ -415,22 +515,22 @@ cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, 
     const int c0 = k * 64, rest = std::max(0, smax - c0 - 64);
     if ((e = launch_potrf_diag(djobs + (size_t)k * nj, nj, c0, st)) != cudaSuccess) return e;
     if (rest > 0) {
-      if ((e = launch_gemm_f64(dev(0, k), nj, rest, 64, 0, 1, 1.0, 0.0, 0, st)) != cudaSuccess) return e;
-      if ((e = launch_gemm_f64(dev(1, k), nj, rest, rest, 0, 1, -1.0, 1.0, 1, st)) != cudaSuccess) return e;
+      if ((e = launch_gemm_f64(dev(0, k), nj, rest, 64, 0, 1, 1.0, 0.0, 0, st, double_float)) != cudaSuccess) return e;
+      if ((e = launch_gemm_f64(dev(1, k), nj, rest, rest, 0, 1, -1.0, 1.0, 1, st, double_float)) != cudaSuccess) return e;
     }
   }
   if (!invert) return cudaSuccess;
   for (int k = 0; k < nb; ++k) {
     const int c0 = k * 64, rest = std::max(0, smax - c0 - 64), ncol = std::min(smax, c0 + 64);
-    if ((e = launch_gemm_f64(dev(2, k), nj, 64, ncol, 0, 0, 1.0, 0.0, 0, st)) != cudaSuccess) return e;
+    if ((e = launch_gemm_f64(dev(2, k), nj, 64, ncol, 0, 0, 1.0, 0.0, 0, st, double_float)) != cudaSuccess) return e;
     if (rest > 0)
-      if ((e = launch_gemm_f64(dev(3, k), nj, rest, ncol, 0, 0, -1.0, 1.0, 0, st)) != cudaSuccess) return e;
+      if ((e = launch_gemm_f64(dev(3, k), nj, rest, ncol, 0, 0, -1.0, 1.0, 0, st, double_float)) != cudaSuccess) return e;
   }
   for (int k = nb - 1; k >= 0; --k) {
     const int c0 = k * 64, ncol = std::min(smax, c0 + 64);
-    if ((e = launch_gemm_f64(dev(4, k), nj, 64, ncol, 1, 0, 1.0, 0.0, 0, st)) != cudaSuccess) return e;
+    if ((e = launch_gemm_f64(dev(4, k), nj, 64, ncol, 1, 0, 1.0, 0.0, 0, st, double_float)) != cudaSuccess) return e;
     if (c0 > 0)
-      if ((e = launch_gemm_f64(dev(5, k), nj, c0, c0, 1, 0, -1.0, 1.0, 0, st)) != cudaSuccess) return e;
+      if ((e = launch_gemm_f64(dev(5, k), nj, c0, c0, 1, 0, -1.0, 1.0, 0, st, double_float)) != cudaSuccess) return e;
   }
   for (const auto& J : jobs)
     if ((e = launch_mirror_lower(J.Q, J.ldq, J.s, st)) != cudaSuccess) return e;

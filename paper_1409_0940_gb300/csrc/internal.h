@@ -77,9 +77,9 @@ struct GemmDesc {          // D = alpha * op(A) op(B) + beta * Cm, row-major
 // f32 iteration GEMM, NN only, desc array on the device
 cudaError_t launch_gemm_f32_nn(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, float alpha, float beta,
                                cudaStream_t st);
-// f64 with runtime transposes
+// f64 with runtime transposes; double_float: FP64 in and out, double-float arithmetic inside
 cudaError_t launch_gemm_f64(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, int transA, int transB,
-                            double alpha, double beta, int lower_only, cudaStream_t st);
+                            double alpha, double beta, int lower_only, cudaStream_t st, bool double_float = false);
 // Gram: D(f64) = beta*D + Z^T Z over rows, Z float32 (n x s, ld), FP32 products, FP64 accumulation
 cudaError_t launch_gram_f32_to_f64(const float* Z, int64_t ldz, int64_t n, int64_t s, double* H, int64_t ldh,
                                    cudaStream_t st);
@@ -102,7 +102,10 @@ struct MatJob {    // host description of one matrix to factor (and invert)
   int32_t* info;   // device int32, zero on entry
 };
 size_t factor_scratch_bytes(int njobs, int smax);
-cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st);
+// blocked Cholesky (and inverse); double_float selects the double-float GEMM for the block
+// updates (the 64 x 64 diagonal factorisations stay FP64)
+cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st,
+                                  bool double_float = false);
 
 // elementwise.cu
 // dst[p][c] = src[map[p] * lds + c] (c < w), zero for c >= w or map[p] < 0; map null = identity
