@@ -136,6 +136,23 @@ def bytes_per_cached_pass(w):
     return 4 * n * D + 4 * C * n * mpad + 4 * R * D * mpad
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: every rank's timed region ends at the same barrier, so the
+    job's time is the maximum (all_reduce MAX; NCCL on the GPU, gloo in the CPU tests)."""
+    import torch
+    if dist is None:
+        return ms
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps, world, ms):
+    """Whole-job iterations per second: every rank runs `steps` iterations of its own replica
+    of the workload (weak scaling, no data-path collective)."""
+    return steps * world / (ms * 1e-3)
+
+
 def measure(rff, w, X, Y, prec, steps, warmup, stream):
     """warmup untimed iterations (the first call also builds the factors), then steps
     iterations timed with CUDA events on the solver's stream; returns the device ms,
@@ -179,9 +196,7 @@ def run_ours(args, rank, world):
     ms, prof, W_main, clk = measure(rff, w, X, Y, args.prec, args.steps, args.warmup, stream)
     if dist:
         dist.barrier()
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
 
     # end to end through the public API with host buffers: set_data (H2D of X, Y),
     # set-up, K iterations, weights back to the host (D2H)
@@ -247,8 +262,7 @@ def run_ours(args, rank, world):
                 "frac": achieved / alu_peak, "traffic": None, "kernel": ph[3:],
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"}
 
-    iters_total = args.steps * world
-    value = iters_total / (ms * 1e-3)
+    value = job_throughput(args.steps, world, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
