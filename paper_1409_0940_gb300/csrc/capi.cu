@@ -53,9 +53,9 @@ struct rff_admm_s {
   __half *Xhi = nullptr, *Xlo = nullptr, *Ghi = nullptr, *Glo = nullptr;
   float xscale = 1.f, gscale = 1.f;
   float *O = nullptr, *Obar = nullptr, *nu = nullptr, *Op = nullptr;
-  float* V32 = nullptr;       // V_ij = Obar_ij + nu_i, C x slots x mpad
+  float* V32 = nullptr;       // V_ij = Obar_ij + nu_i, C x slots x mpad (FP32 path)
   // split path: the chained operands V^T, W'^T, Wbar^T as FP16 hi/lo pairs, each scaled by
-  // f16_scale(max |.|); the maxima (float bits) live in amax[0..2] = V, W', Wbar
+  // f16_scale of a maximum or bound; the maxima (float bits) live in amax (AMAX_* words)
   unsigned* amax = nullptr;
   __half *VThi = nullptr, *VTlo = nullptr, *WThi = nullptr, *WTlo = nullptr, *WbThi = nullptr,
                 *WbTlo = nullptr;
@@ -235,7 +235,7 @@ size_t working_set_bytes(const rff_admm_s& s) {
   if (!s.split_path() || s.cached_z()) t += (size_t)s.nslots * s.dld * f + (size_t)s.fslots * s.dld * f;
   t += (size_t)s.fslots * f;
   t += (size_t)s.nslots * s.mpad * f * (4 + 2);                 // Y, O, Obar, nu, nu_old, Obar_old
-  t += (size_t)s.C * s.nslots * s.mpad * f * 2;                 // Op, V32
+  t += (size_t)s.C * s.nslots * s.mpad * f * (s.split_path() ? 1 : 2);   // Op (+ V on the FP32 path)
   if (s.split_path()) t += (size_t)s.C * s.nslots * s.mpad * b2 * 2;
   t += (size_t)s.fslots * s.mpad * f * 5;                       // W, Wbar, mu, mu_old, Wbar_old
   t += (size_t)s.R * s.fslots * s.mpad * f * (3 + s.nsplit_max);    // What, muij, muij_old, Rpart
@@ -493,8 +493,8 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   AL(s.nu_old, s.nslots * s.mpad);
   AL(s.Obar_old, s.nslots * s.mpad);
   AL(s.Op, (int64_t)s.C * s.nslots * s.mpad);
-  AL(s.V32, (int64_t)s.C * s.nslots * s.mpad);
-  AL(s.amax, 4);
+  if (!s.split_path()) AL(s.V32, (int64_t)s.C * s.nslots * s.mpad);
+  AL(s.amax, AMAX_WORDS);
   AL(s.W, s.fslots * s.mpad);
   AL(s.Wbar, s.fslots * s.mpad);
   AL(s.mu, s.fslots * s.mpad);
@@ -606,8 +606,8 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   // ADMM state: all zero (Sec. 3: "initialize to zero"), then O = prox(Obar - nu) = prox(0)
   const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
   for (float* b : {s.O, s.Obar, s.nu}) CK(cudaMemsetAsync(b, 0, rowb, s.st));
-  CK(cudaMemsetAsync(s.V32, 0, rowb * s.C, s.st));
-  CK(cudaMemsetAsync(s.amax, 0, 16, s.st));
+  if (s.V32) CK(cudaMemsetAsync(s.V32, 0, rowb * s.C, s.st));
+  CK(cudaMemsetAsync(s.amax, 0, AMAX_WORDS * 4, s.st));
   CK(cudaMemsetAsync(s.Op, 0, rowb * s.C, s.st));
   for (float* b : {s.W, s.Wbar, s.mu}) CK(cudaMemsetAsync(b, 0, colb, s.st));
   for (float* b : {s.What, s.muij}) CK(cudaMemsetAsync(b, 0, colb * s.R, s.st));
@@ -623,6 +623,10 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
       if (b) CK(cudaMemsetAsync(b, 0, colb / 2 * s.R, s.st));
   }
   CK(launch_prox_loss(s.p.loss, s.O, s.Y, s.nslots, (int)s.m, s.mpad, s.t_loss, s.p.newton_iters, s.O, s.st));
+  // max |O| of the initial state (nu = 0, V = 0): the first exchange's bound of |V|
+  if (s.split_path())
+    CK(launch_finite_check(s.O, s.nslots * s.mpad, 0, reinterpret_cast<int*>(s.amax + AMAX_FLAG), s.st,
+                           s.amax + AMAX_O));
   // zero O on padding rows (prox(0) with y = 0 is not zero for the squared loss only if y != 0; y = 0 there)
   CK(cudaStreamSynchronize(s.st));
   h->has_data = true;
@@ -671,7 +675,7 @@ rff_status autotune(rff_admm_t h) {
       for (int rep = 0; rep < 2; ++rep) {     // first run warms caches and descriptors
         CK(cudaEventRecord(e0, s.st));
         CK(tc_pass1(tc_view(s), s.Rpart));
-        CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + 1));
+        CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + AMAX_W));
         CK(cudaEventRecord(e1, s.st));
         CK(cudaEventSynchronize(e1));
         CK(cudaEventElapsedTime(&ms, e0, e1));
@@ -942,7 +946,7 @@ SgView qgemm_view(const rff_admm_s& s) {
   v.mpad = (int)s.mpad;
   v.out = s.What;
   v.out_scale = 1.f;
-  v.amax = s.amax + 1;
+  v.amax = s.amax + AMAX_W;
   v.two_acc = 1;
   v.st = s.st;
   return v;
@@ -991,7 +995,8 @@ SgView cz_pass2_view(const rff_admm_s& s) {
   v.mpad = (int)s.mpad;
   v.out = s.Op;
   v.out_scale = 1.f / s.zscale;
-  v.b_amax = s.amax + 1;
+  v.b_amax = s.amax + AMAX_W;
+  v.amax = s.amax + AMAX_OP;
   v.smem_budget = 110 * 1024;
   v.st = s.st;
   return v;
@@ -1010,13 +1015,19 @@ rff_status exchange_and_average(rff_admm_t h, int k) {
   auto& s = *h;
   const int64_t nfe = s.fslots * s.mpad;
   rff_status r;
-  RowEpiArgs e{s.Op, s.O, s.Obar, s.nu, s.Y, s.V32, s.split_path() ? s.amax : nullptr, s.row_of_slot, s.nslots,
+  RowEpiArgs e{s.Op, s.O, s.Obar, s.nu, s.Y, s.V32, nullptr, nullptr, nullptr, s.row_of_slot, s.nslots,
                s.C, (int)s.m, (int)s.mpad, s.p.loss, s.p.newton_iters, s.t_loss};
-  if (s.split_path()) CK(cudaMemsetAsync(s.amax, 0, 4, s.st));
+  if (s.split_path()) {
+    // V^T as a scaled FP16 pair straight from the exchange (scale from the bound of |V|)
+    e.VThi = s.VThi;
+    e.VTlo = s.VTlo;
+    e.amax = s.amax;
+    CK(cudaMemsetAsync(s.amax + AMAX_V, 0, 4, s.st));
+    CK(cudaMemsetAsync(s.amax + AMAX_O_NEXT, 0, 8, s.st));
+  }
   CK(launch_row_epilogue(e, s.st));
-  if (s.split_path())
-    CK(launch_transpose_split_f16(s.V32, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
-                                  s.mpad * s.nslots, 1.f, s.amax, s.st));
+  if (s.split_path())   // the outputs' maxima become the next exchange's inputs
+    CK(cudaMemcpyAsync(s.amax + AMAX_O, s.amax + AMAX_O_NEXT, 8, cudaMemcpyDeviceToDevice, s.st));
   if ((r = mark(h, k, 5)) != RFF_OK) return r;
   CK(launch_avg_dual(s.W, s.What, s.R, nfe, s.Wbar, s.mu, s.muij, s.st));
   return mark(h, k, 6);
@@ -1032,7 +1043,7 @@ rff_status iterate_outer(rff_admm_t h, int k) {
   auto& s = *h;
   const int64_t nfe = s.fslots * s.mpad;
   const int64_t nmax = *std::max_element(s.row_size.begin(), s.row_size.end());
-  int* scratch_flag = reinterpret_cast<int*>(s.amax + 3);
+  int* scratch_flag = reinterpret_cast<int*>(s.amax + AMAX_FLAG);
   rff_status r;
   if ((r = mark(h, k, 0)) != RFF_OK) return r;
   CK(launch_prox_reg(s.p.reg, s.Wbar, s.mu, nfe, s.t_reg, s.W, s.st, s.lam_dev, (int)s.mpad));
@@ -1052,11 +1063,11 @@ rff_status iterate_outer(rff_admm_t h, int k) {
   // rhs, then u_ij = Z_ij rhs_ij into U32
   CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st, s.feat_of_slot, (int)s.mpad));
   if (s.split_path()) {
-    CK(cudaMemsetAsync(s.amax + 1, 0, 4, s.st));
-    CK(launch_finite_check(s.rhs, s.R * nfe, 0, scratch_flag, s.st, s.amax + 1));
+    CK(cudaMemsetAsync(s.amax + AMAX_W, 0, 4, s.st));
+    CK(launch_finite_check(s.rhs, s.R * nfe, 0, scratch_flag, s.st, s.amax + AMAX_W));
     CK(launch_transpose_split_f16(s.rhs, s.fslots, (int)s.mpad, s.R, nfe, s.WThi, s.WTlo, s.fslots,
-                                  s.mpad * s.fslots, 1.f, s.amax + 1, s.st));
-    CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.U32, 1, s.amax + 1));
+                                  s.mpad * s.fslots, 1.f, s.amax + AMAX_W, s.st));
+    CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.U32, 1, s.amax + AMAX_W));
   } else {
     PassArgs b = base_pass_args(s);
     b.M = s.rhs;
@@ -1070,11 +1081,15 @@ rff_status iterate_outer(rff_admm_t h, int k) {
   CK(launch_gemm_f32_nn(s.gdesc, s.R * s.C, (int)nmax, (int)s.mpad, 1.f, 0.f, s.st));
   // W'_ij = rhs_ij - Z_ij^T O'_ij (the second pass-1 product reuses the R partials)
   if (s.split_path()) {
-    CK(cudaMemsetAsync(s.amax, 0, 4, s.st));
-    CK(launch_finite_check(s.Op, s.C * s.nslots * s.mpad, 0, scratch_flag, s.st, s.amax));
+    // O'^T as a scaled FP16 pair in the V^T buffers (V^T is rewritten by the exchange);
+    // max |O'| is also the exchange's input
+    CK(cudaMemsetAsync(s.amax + AMAX_OP, 0, 4, s.st));
+    CK(launch_finite_check(s.Op, s.C * s.nslots * s.mpad, 0, scratch_flag, s.st, s.amax + AMAX_OP));
     CK(launch_transpose_split_f16(s.Op, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
-                                  s.mpad * s.nslots, 1.f, s.amax, s.st));
-    CK(tc_pass1(tc_view(s), s.Rpart));
+                                  s.mpad * s.nslots, 1.f, s.amax + AMAX_OP, s.st));
+    TcView vo = tc_view(s);
+    vo.v_amax = s.amax + AMAX_OP;
+    CK(tc_pass1(vo, s.Rpart));
   } else {
     a.M = s.Op;
     CK(launch_pass1_simt(a, s.fslots, s.st));
@@ -1083,7 +1098,7 @@ rff_status iterate_outer(rff_admm_t h, int k) {
   if ((r = mark(h, k, 3)) != RFF_OK) return r;
   if ((r = mark(h, k, 4)) != RFF_OK) return r;
   if ((r = exchange_and_average(h, k)) != RFF_OK) return r;
-  s.launches += s.split_path() ? 14 : 9;
+  s.launches += s.split_path() ? 13 : 9;
   return RFF_OK;
 }
 
@@ -1121,20 +1136,21 @@ rff_status iterate(rff_admm_t h, int k) {
     // transposed FP16 split of W' that pass 2 reads
     CK(launch_rhs_split3T(s.Wbar, s.muij, s.Rpart, s.cached_z() ? s.nsplit_cz : s.nsplit, s.R, s.fslots,
                           (int)s.mpad, s.feat_of_slot, s.rT1, s.rT2, s.rT3, s.st));
-    CK(cudaMemsetAsync(s.amax + 1, 0, 4, s.st));
+    CK(cudaMemsetAsync(s.amax + AMAX_W, 0, 4, s.st));
     CK(split_gemm(qgemm_view(s)));
     CK(launch_transpose_split_f16(s.What, s.fslots, (int)s.mpad, s.R, s.fslots * s.mpad, s.WThi, s.WTlo, s.fslots,
-                                  s.mpad * s.fslots, 1.f, s.amax + 1, s.st));
+                                  s.mpad * s.fslots, 1.f, s.amax + AMAX_W, s.st));
   } else {
     CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st));
     CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st));
   }
   if ((r = mark(h, k, 3)) != RFF_OK) return r;
   // pass 2: O'_ij = Z_ij W'_ij (eq. (gpOij))
+  if (s.split_path()) CK(cudaMemsetAsync(s.amax + AMAX_OP, 0, 4, s.st));   // max |O'| for the exchange
   if (s.cached_z()) {
     CK(split_gemm(cz_pass2_view(s)));
   } else if (s.split_path()) {
-    CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + 1));
+    CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + AMAX_W, s.amax + AMAX_OP));
   } else {
     a.M = s.What;
     a.m_block_stride = s.fslots * s.mpad;
@@ -1147,7 +1163,7 @@ rff_status iterate(rff_admm_t h, int k) {
   // exchange, nu update, next loss prox, next V_ij (the tensor-core path reads V^T as a
   // scaled FP16 hi/lo pair), averaging and dual updates
   if ((r = exchange_and_average(h, k)) != RFF_OK) return r;
-  s.launches += s.split_path() ? 9 : 7;
+  s.launches += s.split_path() ? 8 : 7;
   return RFF_OK;
 }
 
@@ -1199,7 +1215,7 @@ rff_status enqueue_iterations(rff_admm_t h, int iters, bool copy_old) {
     } else {
       if (!s.gexec && (r = capture_iteration(h)) != RFF_OK) return r;
       CK(cudaGraphLaunch(s.gexec, s.st));
-      s.launches += s.outer ? (s.split_path() ? 14 : 9) : (s.split_path() ? 9 : 7);
+      s.launches += s.outer ? (s.split_path() ? 13 : 9) : (s.split_path() ? 8 : 7);
     }
     if (r != RFF_OK) return r;
     s.iters_done++;
@@ -1248,11 +1264,11 @@ rff_status scores_pass(rff_admm_t h, const float* Xrows32, const __half* Xh, con
                        int64_t nrows, const int32_t* row_ok, float* out) {
   auto& s = *h;
   if (s.split_path()) {
-    CK(cudaMemsetAsync(s.amax + 2, 0, 4, s.st));
-    CK(launch_finite_check(s.Wbar, s.fslots * s.mpad, 0, reinterpret_cast<int*>(s.amax + 3), s.st, s.amax + 2));
+    CK(cudaMemsetAsync(s.amax + AMAX_WB, 0, 4, s.st));
+    CK(launch_finite_check(s.Wbar, s.fslots * s.mpad, 0, reinterpret_cast<int*>(s.amax + AMAX_FLAG), s.st, s.amax + AMAX_WB));
     CK(launch_transpose_split_f16(s.Wbar, s.fslots, (int)s.mpad, 1, 0, s.WbThi, s.WbTlo, s.fslots, 0, 1.f,
-                                  s.amax + 2, s.st));
-    CK(tc_predict(tc_view(s), Xh, Xl, nrows, s.WbThi, s.WbTlo, s.amax + 2, out));
+                                  s.amax + AMAX_WB, s.st));
+    CK(tc_predict(tc_view(s), Xh, Xl, nrows, s.WbThi, s.WbTlo, s.amax + AMAX_WB, out));
   } else {
     PassArgs a = base_pass_args(s);
     a.X = Xrows32;
@@ -1516,11 +1532,18 @@ struct Piece {
   void* ptr;
   size_t bytes;
 };
-// the iteration's state: O, Obar, nu, the pass-1 operand V, W, Wbar, mu, W'_ij, mu'_ij
-// (the FP16 split of V^T on the tensor-core path is rebuilt from V)
+// the iteration's state: O, Obar, nu, the pass-1 operand (V, or on the tensor-core path the
+// FP16 split of V^T with the maxima that scale it), W, Wbar, mu, W'_ij, mu'_ij
 std::vector<Piece> state_pieces(rff_admm_s& s) {
   const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
-  std::vector<Piece> v{{s.O, rowb}, {s.Obar, rowb}, {s.nu, rowb}, {s.V32, rowb * s.C}};
+  std::vector<Piece> v{{s.O, rowb}, {s.Obar, rowb}, {s.nu, rowb}};
+  if (s.split_path()) {
+    v.push_back({s.VThi, rowb / 2 * s.C});
+    v.push_back({s.VTlo, rowb / 2 * s.C});
+    v.push_back({s.amax, AMAX_WORDS * 4});
+  } else {
+    v.push_back({s.V32, rowb * s.C});
+  }
   for (Piece pc : std::vector<Piece>{{s.W, colb}, {s.Wbar, colb}, {s.mu, colb}, {s.What, colb * s.R},
                                      {s.muij, colb * s.R}})
     v.push_back(pc);
@@ -1580,12 +1603,6 @@ rff_status rff_admm_set_state(rff_admm_t h, const void* buf, size_t bytes) {
   for (auto& pc : pieces) {
     CK(cudaMemcpyAsync(pc.ptr, in + off, pc.bytes, cudaMemcpyHostToDevice, s.st));
     off += pc.bytes;
-  }
-  if (s.split_path()) {
-    CK(cudaMemsetAsync(s.amax, 0, 16, s.st));
-    CK(launch_finite_check(s.V32, s.C * s.nslots * s.mpad, 0, reinterpret_cast<int*>(s.amax + 3), s.st, s.amax));
-    CK(launch_transpose_split_f16(s.V32, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
-                                  s.mpad * s.nslots, 1.f, s.amax, s.st));
   }
   CK(cudaStreamSynchronize(s.st));
   s.iters_done = hd.iters_done;

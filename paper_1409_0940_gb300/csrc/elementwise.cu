@@ -207,10 +207,14 @@ __global__ void k_prox_reg(int reg, const float* __restrict__ V, const float* __
 //   V_ij = O'_ij + (Delta/(C+1) + nu)      (= Obar_ij + nu, the pass-1 operand)
 //   O <- prox_{t V}(Obar - nu)             (the loss step of the next iteration)
 // Phase 1 (a warp per row, lanes over outputs) updates Obar, nu and O and keeps
-// Delta/(C+1) + nu of the tile in shared memory; phase 2 forms V_ij row-major in
-// FP32 and, for the tensor-core path, reduces max |V| (the scale of its FP16
-// split, which k_transpose_split_f16 writes next).  Padding rows and columns are
-// written as zeros.
+// Delta/(C+1) + nu of the tile in shared memory; phase 2 forms V_ij tile by tile,
+// either row-major in FP32 (the SIMT path's operand) or transposed and split into a
+// scaled FP16 hi/lo pair (V^T[j][c][slot], the tensor-core operand) through a
+// shared-memory transpose, so that both the reads and the writes are coalesced.
+// The scale of that split comes before any V exists: V = O'_j + nu + 2 (O - S)/(C+1)
+// with S = sum_j O'_j, so |V| <= B = max|O'| + max|nu| + 2/(C+1) (max|O| + C max|O'|)
+// over this kernel's inputs (widened by 2^-10 for the rounding of the bound itself);
+// every CTA computes the same B.  Padding rows and columns are written as zeros.
 constexpr int EX_ROWS = 32;
 
 template <int LOSS>
@@ -218,6 +222,18 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
   extern __shared__ float ex_smem[];
   const int mp = a.mpad;
   float* term = ex_smem;                         // [32][mpad]
+  float* tile = ex_smem + EX_ROWS * mp;          // [32][mpad + 1] (split path)
+  const bool split = a.VThi != nullptr;
+  float vscale = 1.f;
+  if (split) {
+    const float opm = __uint_as_float(a.amax[AMAX_OP]), om = __uint_as_float(a.amax[AMAX_O]),
+                num = __uint_as_float(a.amax[AMAX_NU]);
+    const float c1 = (float)(a.C + 1);
+    const float bound = (opm + num + 2.f * (om + (float)a.C * opm) / c1) * (1.f + 0x1p-10f);
+    vscale = f16_scale(bound);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && bound > 0.f) atomicMax(&a.amax[AMAX_V], __float_as_uint(bound));
+  }
+  float omax = 0.f, numax = 0.f;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int64_t p0 = (int64_t)blockIdx.x * EX_ROWS;
   const int64_t jstride = a.nslots * mp;
@@ -260,6 +276,7 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
       const bool live = ok && k < a.m;
       a.Obar[base + k] = live ? Obar : 0.f;
       a.nu[base + k] = live ? nu : 0.f;
+      if (live) numax = fmaxf(numax, fabsf(nu));
       term[r * mp + k] = live ? Delta * inv_c1 + nu : 0.f;
       if (live) w_in[q] = Obar - nu;
       else y[q] = 0.f;
@@ -274,27 +291,50 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
 #pragma unroll
     for (int q = 0; q < MAXPL; ++q) {
       const int k = lane + 32 * q;
-      if (k < mp) a.O[base + k] = (ok && k < a.m) ? o[q] : 0.f;
+      const bool live = ok && k < a.m;
+      if (k < mp) a.O[base + k] = live ? o[q] : 0.f;
+      if (live) omax = fmaxf(omax, fabsf(o[q]));
+    }
+  }
+  if (split) {
+    // max |O|, |nu| of the outputs: the bound of the next exchange
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+      omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, sh));
+      numax = fmaxf(numax, __shfl_xor_sync(0xffffffffu, numax, sh));
+    }
+    if (lane == 0) {
+      if (omax > 0.f) atomicMax(&a.amax[AMAX_O_NEXT], __float_as_uint(omax));
+      if (numax > 0.f) atomicMax(&a.amax[AMAX_NU_NEXT], __float_as_uint(numax));
     }
   }
   __syncthreads();
   // phase 2: V_ij = O'_ij + term, per column block
-  float vmax = 0.f;
   for (int j = 0; j < a.C; ++j) {
     const float* opj = a.Op + j * jstride + p0 * mp;
-    float* vj = a.V32 + j * jstride + p0 * mp;
-    for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
-      const bool live = a.row_ok[p0 + e / mp] >= 0 && e % mp < a.m;
-      const float v = live ? opj[e] + term[e] : 0.f;
-      vj[e] = v;
-      vmax = fmaxf(vmax, fabsf(v));
+    if (!split) {
+      float* vj = a.V32 + j * jstride + p0 * mp;
+      for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
+        const bool live = a.row_ok[p0 + e / mp] >= 0 && e % mp < a.m;
+        vj[e] = live ? opj[e] + term[e] : 0.f;
+      }
+      continue;
     }
-  }
-  if (a.vmax) {
-    // largest |V| (the scale of the next FP16 split of V^T)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if (lane == 0 && vmax > 0.f) atomicMax(a.vmax, __float_as_uint(vmax));
+    for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
+      const int r = e / mp, k = e % mp;
+      const bool live = a.row_ok[p0 + r] >= 0 && k < a.m;
+      tile[r * (mp + 1) + k] = live ? opj[e] + term[e] : 0.f;
+    }
+    __syncthreads();
+    // lanes over the 32 rows, warps over columns: V^T[j][c][p0 + lane]
+    for (int c = warp; c < mp; c += 8) {
+      __half hi, lo;
+      split_f16(tile[lane * (mp + 1) + c], vscale, hi, lo);
+      const int64_t o = ((int64_t)j * mp + c) * a.nslots + p0 + lane;
+      a.VThi[o] = hi;
+      a.VTlo[o] = lo;
+    }
+    __syncthreads();
   }
 }
 
@@ -563,13 +603,14 @@ cudaError_t launch_prox_reg(int reg, const float* V, const float* mu, int64_t n,
 cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st) {
   if (a.nslots <= 0) return cudaSuccess;
   if (a.mpad > 32 * MAXPL || a.nslots % EX_ROWS) return cudaErrorInvalidValue;
-  if (!a.V32) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)EX_ROWS * a.mpad * sizeof(float);
+  const bool split = a.VThi && a.VTlo && a.amax;
+  if (!a.V32 && !split) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)EX_ROWS * (split ? 2 * a.mpad + 1 : a.mpad) * sizeof(float);
   const unsigned grid = (unsigned)(a.nslots / EX_ROWS);
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    const int mx = EX_ROWS * 32 * MAXPL * (int)sizeof(float);
+    const int mx = EX_ROWS * (2 * 32 * MAXPL + 1) * (int)sizeof(float);
     attr = cudaFuncSetAttribute(k_exchange<LOSS_SQUARED>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_exchange<LOSS_HINGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

@@ -119,14 +119,25 @@ cudaError_t launch_prox_loss(int loss, const float* V, const float* Y, int64_t n
                              int newton, float* out, cudaStream_t st);
 cudaError_t launch_prox_reg(int reg, const float* V, const float* mu, int64_t n, float tau, float* out,
                             cudaStream_t st, const float* tau_col = nullptr, int ncol = 1);
+// words of the device array of maxima (float bits) that scale the FP16 splits
+constexpr int AMAX_V = 0, AMAX_W = 1, AMAX_WB = 2, AMAX_FLAG = 3, AMAX_OP = 4, AMAX_O = 5, AMAX_NU = 6,
+              AMAX_O_NEXT = 7, AMAX_NU_NEXT = 8, AMAX_WORDS = 16;
+
 struct RowEpiArgs {
   const float* Op;      // C x slots x mpad
   float* O;             // slots x mpad (in: O^k, out: O^{k+1} = prox(Obar - nu))
   float* Obar;
   float* nu;
   const float* Y;
-  float* V32;           // C x slots x mpad
-  unsigned* vmax;       // max |V| as float bits (atomicMax), or null
+  float* V32;           // C x slots x mpad (FP32 path), or null
+  // tensor-core path: V^T written as its scaled FP16 hi/lo split (C x mpad x slots), the scale
+  // from an upper bound of |V| built from the maxima in amax (float bits): amax[AMAX_OP] =
+  // max |O'|, amax[AMAX_O] / amax[AMAX_NU] = max |O|, |nu| of this kernel's inputs; the kernel
+  // stores the bound in amax[AMAX_V] and reduces max |O|, |nu| of its outputs into
+  // amax[AMAX_O_NEXT], amax[AMAX_NU_NEXT]
+  __half* VThi;
+  __half* VTlo;
+  unsigned* amax;
   const int32_t* row_ok;
   int64_t nslots;
   int C, m, mpad, loss, newton;

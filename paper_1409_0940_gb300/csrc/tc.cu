@@ -86,6 +86,7 @@ struct TcArgs {
   int64_t nrow_tiles;                       // pass 2: 128-row tiles of the data (work items x C)
   float inv_xg;                             // X.G accumulator -> X G (1 / (xscale gscale))
   const unsigned* m_amax;                   // max |M| of the chained operand (its FP16 split scale)
+  unsigned* out_amax;                       // pass 2: receives max |out| (float bits), or null
   const int64_t* row_slot;
   const int64_t* row_size;
   const int64_t* col_slot;
@@ -541,6 +542,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
           float* orow = sh.g_out[g] + (int64_t)row * a.mpad;
           // undo the FP16 scales of Z (COS_SCALE) and of the chained operand, apply sqrt(2/D)
           const float sc = a.scale / COS_SCALE * (a.m_amax ? f16_inv_scale(__uint_as_float(*a.m_amax)) : 1.f);
+          float omx = 0.f;
           for (int c = 0; c < half; c += 8) {
             uint32_t r8[8];
             tmem_ld8(tmem + lane_addr + ACC2_COL + c0 + c, r8);
@@ -557,6 +559,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
             }
             dst[0] = v0;
             dst[1] = v1;
+            omx = fmaxf(omx, fmaxf(fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)), fmaxf(fabsf(v0.z), fabsf(v0.w))),
+                                   fmaxf(fmaxf(fabsf(v1.x), fabsf(v1.y)), fmaxf(fabsf(v1.z), fabsf(v1.w)))));
+          }
+          if (a.out_amax) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) omx = fmaxf(omx, __shfl_xor_sync(0xffffffffu, omx, o));
+            if (lane == 0 && omx > 0.f) atomicMax(a.out_amax, __float_as_uint(omx));
           }
           fence_before();
           __syncwarp();
@@ -745,7 +754,7 @@ cudaError_t tc_pass1(const TcView& v, float* Rpart) {
 }
 
 cudaError_t tc_pass2(const TcView& v, const __half* Mhi, const __half* Mlo, int64_t m_block_stride,
-                     float* out, int per_block, const unsigned* m_amax) {
+                     float* out, int per_block, const unsigned* m_amax, unsigned* out_amax) {
   (void)m_block_stride;
   (void)per_block;
   TcArgs a;
@@ -758,6 +767,7 @@ cudaError_t tc_pass2(const TcView& v, const __half* Mhi, const __half* Mlo, int6
   a.out = out;
   a.out_block_stride = v.nslots * v.mpad;
   a.m_amax = m_amax;
+  a.out_amax = out_amax;
   a.nrow_tiles = v.nslots / 128;
   if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;

@@ -36,7 +36,7 @@ cudaError_t tc_pass1(const TcView& v, float* Rpart);
 // M given transposed and split: [R][mpad][fslots] hi/lo FP16 of M scaled by f16_scale(*m_amax),
 // m_block_stride elements apart.
 cudaError_t tc_pass2(const TcView& v, const __half* Mhi, const __half* Mlo, int64_t m_block_stride,
-                     float* out, int per_block, const unsigned* m_amax);
+                     float* out, int per_block, const unsigned* m_amax, unsigned* out_amax = nullptr);
 // Scores for a query block (nrows slot-padded rows of split X) against M (mpad x fslots hi/lo).
 // Error word of the tensor-core kernels (bounded waits that gave up); reads and clears it.
 // Synchronises the device.  0 = no error.
