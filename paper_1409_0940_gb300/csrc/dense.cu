@@ -154,15 +154,30 @@ __global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict_
 // updated by TwoSum (Knuth), the error terms gathered in its low part.  The result is
 // hi + lo in FP64: about 2^-44 relative per K = 64 dot product, enough for a factor whose
 // inverse feeds FP32 and three-term BF16 iterations.  Same tiling and interface as k_gemm.
+// An operand given as float pairs (PA / PB) is read as such; one given in FP64 is split on
+// load (that takes FP64-pipe work, so operands that many CTAs read are split once
+// beforehand by k_to_pairs).
 constexpr int DF_BK = 16;
+
+__device__ __forceinline__ void load_pair(const void* base, int64_t idx, bool paired, float& h, float& l) {
+  if (paired) {
+    const float2 v = static_cast<const float2*>(base)[idx];
+    h = v.x;
+    l = v.y;
+  } else {
+    const double v = static_cast<const double*>(base)[idx];
+    h = __double2float_rn(v);
+    l = __double2float_rn(v - (double)h);
+  }
+}
+
+template <bool PA, bool PB>
 __global__ void __launch_bounds__(256) k_gemm_df(const GemmDesc* __restrict__ descs, int transA, int transB,
                                                  double alpha, double beta, int lower_only) {
   const GemmDesc g = descs[blockIdx.z];
   const int tm = blockIdx.x, tn = blockIdx.y;
   if (tm * 64 >= g.M || tn * 64 >= g.N) return;
   if (lower_only && tn > tm) return;
-  const double* __restrict__ A = static_cast<const double*>(g.A);
-  const double* __restrict__ B = static_cast<const double*>(g.B);
   __shared__ float Ah[DF_BK][64 + 1], Al[DF_BK][64 + 1];
   __shared__ float Bh[DF_BK][64 + 1], Bl[DF_BK][64 + 1];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
@@ -177,19 +192,19 @@ __global__ void __launch_bounds__(256) k_gemm_df(const GemmDesc* __restrict__ de
       int mm, kk;
       if (transA) { mm = t % 64; kk = t / 64; } else { kk = t % DF_BK; mm = t / DF_BK; }
       const int gm = m0 + mm, gk = k0 + kk;
-      double v = 0.0;
-      if (gm < g.M && gk < g.K) v = transA ? A[(int64_t)gk * g.lda + gm] : A[(int64_t)gm * g.lda + gk];
-      const float vh = __double2float_rn(v);
+      float vh = 0.f, vl = 0.f;
+      if (gm < g.M && gk < g.K)
+        load_pair(g.A, transA ? (int64_t)gk * g.lda + gm : (int64_t)gm * g.lda + gk, PA, vh, vl);
       Ah[kk][mm] = vh;
-      Al[kk][mm] = __double2float_rn(v - (double)vh);
+      Al[kk][mm] = vl;
       int nn, kb;
       if (transB) { kb = t % DF_BK; nn = t / DF_BK; } else { nn = t % 64; kb = t / 64; }
       const int gn = n0 + nn, gkb = k0 + kb;
-      double w = 0.0;
-      if (gn < g.N && gkb < g.K) w = transB ? B[(int64_t)gn * g.ldb + gkb] : B[(int64_t)gkb * g.ldb + gn];
-      const float wh = __double2float_rn(w);
+      float wh = 0.f, wl = 0.f;
+      if (gn < g.N && gkb < g.K)
+        load_pair(g.B, transB ? (int64_t)gn * g.ldb + gkb : (int64_t)gkb * g.ldb + gn, PB, wh, wl);
       Bh[kb][nn] = wh;
-      Bl[kb][nn] = __double2float_rn(w - (double)wh);
+      Bl[kb][nn] = wl;
     }
     __syncthreads();
 #pragma unroll 4
@@ -239,6 +254,16 @@ __global__ void __launch_bounds__(256) k_gemm_df(const GemmDesc* __restrict__ de
       D[(int64_t)gm * g.ldd + gn] = v;
     }
   }
+}
+
+// dst (float pairs, ld ldd) = src (FP64, ld lda), M x N per job (desc.A = src, desc.D = dst)
+__global__ void k_to_pairs(const GemmDesc* __restrict__ descs) {
+  const GemmDesc g = descs[blockIdx.z];
+  const int64_t r = (int64_t)blockIdx.x * 8 + threadIdx.y, c = (int64_t)blockIdx.y * 32 + threadIdx.x;
+  if (r >= g.M || c >= g.N) return;
+  const double v = static_cast<const double*>(g.A)[r * g.lda + c];
+  const float h = __double2float_rn(v);
+  static_cast<float2*>(g.D)[r * g.ldd + c] = make_float2(h, __double2float_rn(v - (double)h));
 }
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
@@ -384,9 +409,25 @@ cudaError_t launch_gemm_f64(const GemmDesc* descs_dev, int nbatch, int maxM, int
   if (nbatch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(maxM, 64), (unsigned)ceil_div(maxN, 64), (unsigned)nbatch);
   if (double_float)
-    k_gemm_df<<<grid, 256, 0, st>>>(descs_dev, transA, transB, alpha, beta, lower_only);
+    k_gemm_df<false, false><<<grid, 256, 0, st>>>(descs_dev, transA, transB, alpha, beta, lower_only);
   else
     k_gemm<double, 16><<<grid, 256, 0, st>>>(descs_dev, transA, transB, alpha, beta, lower_only);
+  return cudaGetLastError();
+}
+
+// double-float GEMM with both operands given as float pairs
+cudaError_t launch_gemm_df_pairs(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, int transA, int transB,
+                                 double alpha, double beta, int lower_only, cudaStream_t st) {
+  if (nbatch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(maxM, 64), (unsigned)ceil_div(maxN, 64), (unsigned)nbatch);
+  k_gemm_df<true, true><<<grid, 256, 0, st>>>(descs_dev, transA, transB, alpha, beta, lower_only);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_pairs(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, cudaStream_t st) {
+  if (nbatch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(maxM, 8), (unsigned)ceil_div(maxN, 32), (unsigned)nbatch);
+  k_to_pairs<<<grid, dim3(32, 8), 0, st>>>(descs_dev);
   return cudaGetLastError();
 }
 
@@ -438,10 +479,15 @@ cudaError_t launch_mirror_lower(double* Q, int64_t ld, int64_t s, cudaStream_t s
   return cudaGetLastError();
 }
 
+// descriptor phases of the blocked factorisation: 0 panel, 1 trailing update, 2-3 forward
+// sweep, 4-5 backward sweep, 6-9 conversions to float pairs (double-float mode)
+constexpr int FACTOR_PHASES = 10;
+
 size_t factor_scratch_bytes(int njobs, int smax) {
   const int nb = (int)ceil_div(smax, 64);
-  return (size_t)njobs * nb * 64 * 64 * sizeof(double) + (size_t)njobs * sizeof(DiagJob) * nb +
-         (size_t)njobs * nb * 6 * sizeof(GemmDesc) + 1024;
+  // per job: the diagonal inverses, and two 64 x (nb * 64) float-pair staging buffers
+  return (size_t)njobs * nb * 64 * 64 * sizeof(double) + (size_t)njobs * 2 * 64 * nb * 64 * sizeof(float2) +
+         (size_t)njobs * sizeof(DiagJob) * nb + (size_t)njobs * nb * FACTOR_PHASES * sizeof(GemmDesc) + 1024;
 }
 
 cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st,
@@ -454,6 +500,12 @@ cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, 
   char* p = static_cast<char*>(dev_scratch);
   double* inv = reinterpret_cast<double*>(p);
   p += (size_t)nj * nb * 64 * 64 * sizeof(double);
+  // float-pair copies of the operands that many CTAs of one double-float GEMM read: P2 holds
+  // the L panel below the diagonal block (rest x 64, ld 64) or the L block row (64 x c0,
+  // ld ldp); B2 the block row of Q (64 x ncol, ld ldp)
+  const int64_t ldp = (int64_t)nb * 64;
+  float2* pairs = reinterpret_cast<float2*>(p);
+  p += (size_t)nj * 2 * 64 * ldp * sizeof(float2);
   DiagJob* djobs = reinterpret_cast<DiagJob*>(p);
   p += (size_t)nj * nb * sizeof(DiagJob);
   GemmDesc* gd = reinterpret_cast<GemmDesc*>(p);
@@ -466,8 +518,8 @@ cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, 
   cudaError_t e = cudaMemcpyAsync(djobs, hd.data(), hd.size() * sizeof(DiagJob), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
 
-  // descriptor table: [phase][k][b], phases: panel, trailing, fwdA, fwdB, bwdA, bwdB
-  std::vector<GemmDesc> g((size_t)6 * nb * nj);
+  // descriptor table: [phase][k][b]
+  std::vector<GemmDesc> g((size_t)FACTOR_PHASES * nb * nj);
   auto at = [&](int ph, int k, int b) -> GemmDesc& { return g[((size_t)ph * nb + k) * nj + b]; };
   for (int k = 0; k < nb; ++k)
     for (int b = 0; b < nj; ++b) {
@@ -476,61 +528,102 @@ cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, 
       const int bs = (int)std::max<int64_t>(0, std::min<int64_t>(64, J.s - c0));
       const int rest = (int)std::max<int64_t>(0, J.s - c0 - 64);
       double* Ikk = inv + ((size_t)b * nb + k) * 4096;
+      float2* P2 = pairs + (size_t)b * 2 * 64 * ldp;
+      float2* B2 = P2 + 64 * ldp;
+      double* Lp = J.A + (c0 + 64) * J.ld + c0;   // L panel below the diagonal block
       GemmDesc z{};
       // panel: A_ik <- A_ik * inv^T (in place)
       GemmDesc pn = z;
       if (bs > 0 && rest > 0) pn = GemmDesc{J.A + (c0 + 64) * J.ld + c0, Ikk, nullptr, J.A + (c0 + 64) * J.ld + c0,
                                             rest, bs, bs, J.ld, 64, 0, J.ld};
       at(0, k, b) = pn;
-      GemmDesc tr = z;
-      if (bs > 0 && rest > 0) tr = GemmDesc{J.A + (c0 + 64) * J.ld + c0, J.A + (c0 + 64) * J.ld + c0,
-                                            J.A + (c0 + 64) * J.ld + c0 + 64, J.A + (c0 + 64) * J.ld + c0 + 64,
-                                            rest, rest, bs, J.ld, J.ld, J.ld, J.ld};
+      GemmDesc tr = z, cp = z;
+      if (bs > 0 && rest > 0) {
+        if (double_float) {
+          cp = GemmDesc{Lp, nullptr, nullptr, P2, rest, bs, 0, J.ld, 0, 0, 64};
+          tr = GemmDesc{P2, P2, Lp + 64, Lp + 64, rest, rest, bs, 64, 64, J.ld, J.ld};
+        } else {
+          tr = GemmDesc{Lp, Lp, Lp + 64, Lp + 64, rest, rest, bs, J.ld, J.ld, J.ld, J.ld};
+        }
+      }
       at(1, k, b) = tr;
+      at(6, k, b) = cp;
       // Inverse Q = L^-T L^-1 from Q = I: the forward sweep (L Y = I) touches only the
       // columns up to the diagonal block of block row k (Y is lower triangular); the
       // backward sweep (L^T Q = Y) computes the block lower triangle of the symmetric Q,
       // which needs the same columns; the strict upper triangle is mirrored afterwards.
       // s^3/3 flops per sweep instead of s^3.
-      GemmDesc fa = z, fb = z, ba = z, bb = z;
+      GemmDesc fa = z, fb = z, ba = z, bb = z, cq = z, cl = z, cqb = z;
       const int ncol = (int)(c0 + bs);
+      double* Qk = J.Q + c0 * J.ldq;   // block row k of Q
       if (invert && bs > 0) {
-        fa = GemmDesc{Ikk, J.Q + c0 * J.ldq, nullptr, J.Q + c0 * J.ldq, bs, ncol, bs, 64, J.ldq, 0, J.ldq};
-        if (rest > 0) fb = GemmDesc{J.A + (c0 + 64) * J.ld + c0, J.Q + c0 * J.ldq, J.Q + (c0 + 64) * J.ldq,
-                                    J.Q + (c0 + 64) * J.ldq, rest, ncol, bs, J.ld, J.ldq, J.ldq, J.ldq};
+        fa = GemmDesc{Ikk, Qk, nullptr, Qk, bs, ncol, bs, 64, J.ldq, 0, J.ldq};
         ba = fa;
-        if (c0 > 0) bb = GemmDesc{J.A + c0 * J.ld, J.Q + c0 * J.ldq, J.Q, J.Q, (int)c0, (int)c0, bs, J.ld, J.ldq,
-                                  J.ldq, J.ldq};
+        if (double_float) {
+          // the forward update reads the panel pairs of phase 6 and Q_k converted after fa
+          cq = GemmDesc{Qk, nullptr, nullptr, B2, bs, ncol, 0, J.ldq, 0, 0, ldp};
+          if (rest > 0) fb = GemmDesc{P2, B2, Qk + 64 * J.ldq, Qk + 64 * J.ldq, rest, ncol, bs, 64, ldp, J.ldq,
+                                      J.ldq};
+          if (c0 > 0) {
+            cl = GemmDesc{J.A + c0 * J.ld, nullptr, nullptr, P2, bs, (int)c0, 0, J.ld, 0, 0, ldp};
+            cqb = GemmDesc{Qk, nullptr, nullptr, B2, bs, (int)c0, 0, J.ldq, 0, 0, ldp};
+            bb = GemmDesc{P2, B2, J.Q, J.Q, (int)c0, (int)c0, bs, ldp, ldp, J.ldq, J.ldq};
+          }
+        } else {
+          if (rest > 0) fb = GemmDesc{Lp, Qk, Qk + 64 * J.ldq, Qk + 64 * J.ldq, rest, ncol, bs, J.ld, J.ldq, J.ldq,
+                                      J.ldq};
+          if (c0 > 0) bb = GemmDesc{J.A + c0 * J.ld, Qk, J.Q, J.Q, (int)c0, (int)c0, bs, J.ld, J.ldq, J.ldq, J.ldq};
+        }
       }
       at(2, k, b) = fa;
       at(3, k, b) = fb;
       at(4, k, b) = ba;
       at(5, k, b) = bb;
+      at(7, k, b) = cq;
+      at(8, k, b) = cl;
+      at(9, k, b) = cqb;
     }
   e = cudaMemcpyAsync(gd, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   auto dev = [&](int ph, int k) { return gd + ((size_t)ph * nb + k) * nj; };
 
+  // the GEMMs that many CTAs feed from one panel or block row (trailing update, forward and
+  // backward updates) read float pairs converted once per step in double-float mode; the
+  // 64-row products (panel solve, diagonal-block products) split their FP64 operands on load
+  const bool df = double_float;
+  auto upd = [&](int ph, int k, int M, int N, int tA, int tB, int lower) {
+    return df ? launch_gemm_df_pairs(dev(ph, k), nj, M, N, tA, tB, -1.0, 1.0, lower, st)
+              : launch_gemm_f64(dev(ph, k), nj, M, N, tA, tB, -1.0, 1.0, lower, st);
+  };
   for (int k = 0; k < nb; ++k) {
     const int c0 = k * 64, rest = std::max(0, smax - c0 - 64);
     if ((e = launch_potrf_diag(djobs + (size_t)k * nj, nj, c0, st)) != cudaSuccess) return e;
     if (rest > 0) {
-      if ((e = launch_gemm_f64(dev(0, k), nj, rest, 64, 0, 1, 1.0, 0.0, 0, st, double_float)) != cudaSuccess) return e;
-      if ((e = launch_gemm_f64(dev(1, k), nj, rest, rest, 0, 1, -1.0, 1.0, 1, st, double_float)) != cudaSuccess) return e;
+      if ((e = launch_gemm_f64(dev(0, k), nj, rest, 64, 0, 1, 1.0, 0.0, 0, st, df)) != cudaSuccess) return e;
+      if (df && (e = launch_to_pairs(dev(6, k), nj, rest, 64, st)) != cudaSuccess) return e;
+      if ((e = upd(1, k, rest, rest, 0, 1, 1)) != cudaSuccess) return e;
     }
   }
   if (!invert) return cudaSuccess;
   for (int k = 0; k < nb; ++k) {
     const int c0 = k * 64, rest = std::max(0, smax - c0 - 64), ncol = std::min(smax, c0 + 64);
-    if ((e = launch_gemm_f64(dev(2, k), nj, 64, ncol, 0, 0, 1.0, 0.0, 0, st, double_float)) != cudaSuccess) return e;
-    if (rest > 0)
-      if ((e = launch_gemm_f64(dev(3, k), nj, rest, ncol, 0, 0, -1.0, 1.0, 0, st, double_float)) != cudaSuccess) return e;
+    if ((e = launch_gemm_f64(dev(2, k), nj, 64, ncol, 0, 0, 1.0, 0.0, 0, st, df)) != cudaSuccess) return e;
+    if (rest > 0) {
+      if (df && ((e = launch_to_pairs(dev(6, k), nj, rest, 64, st)) != cudaSuccess ||
+                 (e = launch_to_pairs(dev(7, k), nj, 64, ncol, st)) != cudaSuccess))
+        return e;
+      if ((e = upd(3, k, rest, ncol, 0, 0, 0)) != cudaSuccess) return e;
+    }
   }
   for (int k = nb - 1; k >= 0; --k) {
     const int c0 = k * 64, ncol = std::min(smax, c0 + 64);
-    if ((e = launch_gemm_f64(dev(4, k), nj, 64, ncol, 1, 0, 1.0, 0.0, 0, st, double_float)) != cudaSuccess) return e;
-    if (c0 > 0)
-      if ((e = launch_gemm_f64(dev(5, k), nj, c0, c0, 1, 0, -1.0, 1.0, 0, st, double_float)) != cudaSuccess) return e;
+    if ((e = launch_gemm_f64(dev(4, k), nj, 64, ncol, 1, 0, 1.0, 0.0, 0, st, df)) != cudaSuccess) return e;
+    if (c0 > 0) {
+      if (df && ((e = launch_to_pairs(dev(8, k), nj, 64, c0, st)) != cudaSuccess ||
+                 (e = launch_to_pairs(dev(9, k), nj, 64, c0, st)) != cudaSuccess))
+        return e;
+      if ((e = upd(5, k, c0, c0, 1, 0, 0)) != cudaSuccess) return e;
+    }
   }
   for (const auto& J : jobs)
     if ((e = launch_mirror_lower(J.Q, J.ldq, J.s, st)) != cudaSuccess) return e;

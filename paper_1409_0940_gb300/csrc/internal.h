@@ -80,6 +80,11 @@ cudaError_t launch_gemm_f32_nn(const GemmDesc* descs_dev, int nbatch, int maxM, 
 // f64 with runtime transposes; double_float: FP64 in and out, double-float arithmetic inside
 cudaError_t launch_gemm_f64(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, int transA, int transB,
                             double alpha, double beta, int lower_only, cudaStream_t st, bool double_float = false);
+// double-float GEMM whose A and B are float pairs (hi, lo) and whose C and D are FP64
+cudaError_t launch_gemm_df_pairs(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, int transA, int transB,
+                                 double alpha, double beta, int lower_only, cudaStream_t st);
+// D (float pairs, ld ldd) = A (FP64, ld lda), M x N per descriptor
+cudaError_t launch_to_pairs(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, cudaStream_t st);
 // Gram: D(f64) = beta*D + Z^T Z over rows, Z float32 (n x s, ld), FP32 products, FP64 accumulation
 cudaError_t launch_gram_f32_to_f64(const float* Z, int64_t ldz, int64_t n, int64_t s, double* H, int64_t ldh,
                                    cudaStream_t st);
