@@ -15,19 +15,26 @@ Readings (the paper fixes neither constants nor the multiclass hinge):
   sum_k max(0, 1 - y_k o_k) with +-1 one-hot targets.
 * logistic, m = 1: log(1 + exp(-y o)), y in {-1, +1}.
 * multinomial logistic: log sum_k exp(o_k) - o_c with c = argmax_k y_k (first).
+* l1 loss: |y - o|_1 = sum_k |y_k - o_k| (real targets).
+* multiclass hinge (Crammer and Singer): max_k (Delta_k + o_k - o_c) with
+  Delta_k = 1 - [k = c] and c = argmax_k y_k (first); zero when o_c beats every
+  other output by a margin of 1.
 * l1 regulariser r(W) = sum |W_ij|.
 
-Methods: closed forms where they exist (squared, hinge, l2, l1); the binary
-logistic prox by bisection of its monotone optimality condition to 1e-15; the
-multinomial prox by damped Newton on its strictly convex objective until
-the gradient is below 1e-14 (relative).
+Methods: closed forms where they exist (squared, hinge, l1 loss, l2, l1); the
+binary logistic prox by bisection of its monotone optimality condition to 1e-15;
+the multinomial prox by damped Newton on its strictly convex objective until
+the gradient is below 1e-14 (relative); the multiclass hinge prox through its
+dual, a Euclidean projection onto the probability simplex computed by sorting.
 
 Pins: brute-force minimisation of the prox objective on random tiny inputs,
-the t -> 0 limit (prox -> identity), kink cases of the hinge.
+the t -> 0 limit (prox -> identity), kink cases of the hinge, the optimality
+(subgradient) conditions of the multiclass hinge and its two-class reduction to
+the binary hinge of the output difference.
 """
 import numpy as np
 
-LOSSES = ("squared", "hinge", "logistic", "multinomial")
+LOSSES = ("squared", "hinge", "logistic", "multinomial", "l1", "crammer_singer")
 REGS = ("l2", "l1")
 
 
@@ -47,6 +54,14 @@ def loss_value(loss, Y, O):
         mx = O.max(axis=1)
         lse = mx + np.log(np.exp(O - mx[:, None]).sum(axis=1))
         return float((lse - O[np.arange(O.shape[0]), c]).sum())
+    if loss == "l1":
+        return float(np.abs(Y - O).sum())
+    if loss == "crammer_singer":
+        n, m = O.shape
+        c = np.argmax(Y, axis=1)
+        Delta = np.ones((n, m))
+        Delta[np.arange(n), c] = 0.0
+        return float((Delta + O - O[np.arange(n), c][:, None]).max(axis=1).sum())
     raise ValueError(loss)
 
 
@@ -75,6 +90,12 @@ def prox_loss(loss, V, Y, t):
         return _prox_logistic(V, Y, t)
     if loss == "multinomial":
         return _prox_multinomial(V, Y, t)
+    if loss == "l1":
+        # per entry: argmin_o 1/2 (o - v)^2 + t |y - o| is v - y soft-thresholded by t, about y
+        Dv = V - Y
+        return Y + np.sign(Dv) * np.maximum(np.abs(Dv) - t, 0.0)
+    if loss == "crammer_singer":
+        return _prox_crammer_singer(V, Y, t)
     raise ValueError(loss)
 
 
@@ -137,6 +158,42 @@ def _prox_multinomial(V, Y, t):
             alpha = np.where(bad, 0.5 * alpha, alpha)
         O = O - alpha[:, None] * step
     return O
+
+
+def _project_simplex(U):
+    """Row-wise Euclidean projection onto {a >= 0, sum a = 1}, by sorting.
+
+    With the entries sorted decreasingly, u_(1) >= ... >= u_(m), the projection is
+    max(u - tau, 0) where tau = (sum_{i <= r} u_(i) - 1) / r and r is the largest j
+    with u_(j) > (sum_{i <= j} u_(i) - 1) / j (Held, Wolfe and Crowder 1974; Duchi,
+    Shalev-Shwartz, Singer and Chandra 2008).
+    """
+    n, m = U.shape
+    S = -np.sort(-U, axis=1)
+    cs = np.cumsum(S, axis=1)
+    j = np.arange(1, m + 1)
+    ok = S - (cs - 1.0) / j > 0
+    r = m - np.argmax(ok[:, ::-1], axis=1)          # last j where ok holds (j = 1 always does)
+    tau = (cs[np.arange(n), r - 1] - 1.0) / r
+    return np.maximum(U - tau[:, None], 0.0)
+
+
+def _prox_crammer_singer(V, Y, t):
+    # V(y, o) = max_k (Delta_k + o_k - o_c) = max over the probability simplex of
+    # a^T Delta + (a - e_c)^T o (sum a = 1).  Exchanging min over o and max over a
+    # (the objective is convex in o, concave in a), the inner minimiser of
+    # 1/2 |o - v|^2 + t (a - e_c)^T o is o = v - t (a - e_c); what is left to
+    # maximise over a is, up to constants, -t^2/2 |a - e_c - (Delta + v)/t|^2, so a is
+    # the projection of e_c + (Delta + v)/t onto the simplex.
+    n, m = V.shape
+    if t <= 0.0:
+        return V.copy()
+    c = np.argmax(Y, axis=1)
+    E = np.zeros((n, m))
+    E[np.arange(n), c] = 1.0
+    Delta = 1.0 - E
+    A = _project_simplex(E + (Delta + V) / t)
+    return V - t * (A - E)
 
 
 def prox_reg(reg, V, tau):

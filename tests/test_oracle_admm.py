@@ -89,7 +89,7 @@ def test_graph_projection_is_the_argmin():
 
 
 @pytest.mark.parametrize("loss,reg", [("hinge", "l2"), ("squared", "l1"), ("logistic", "l2"),
-                                      ("multinomial", "l2")])
+                                      ("multinomial", "l2"), ("l1", "l2"), ("crammer_singer", "l2")])
 def test_residuals_go_to_zero(loss, reg):
     if loss == "logistic":
         X, Y = synth.binary(n=400, d=6, seed=8)

@@ -40,6 +40,8 @@ def _loss_mp(loss, y, o):
         return mp.mpf(0) if 1 - y * o < 0 else 1 - y * o
     if loss == "logistic":
         return mp.log(1 + mp.exp(-y * o))
+    if loss == "l1":
+        return abs(y - o)
     raise ValueError(loss)
 
 
@@ -50,7 +52,7 @@ def _brute_scalar(loss, v, y, t):
     return _golden(f, v - span, v + span)
 
 
-@pytest.mark.parametrize("loss", ["squared", "hinge", "logistic"])
+@pytest.mark.parametrize("loss", ["squared", "hinge", "logistic", "l1"])
 def test_scalar_losses_brute_force(loss):
     rng = np.random.default_rng(1)
     for _ in range(150):
@@ -99,7 +101,7 @@ def test_multinomial_brute_force(m):
         assert f(got) <= f(res.x) + 1e-12
 
 
-@pytest.mark.parametrize("loss", ["squared", "hinge", "logistic", "multinomial"])
+@pytest.mark.parametrize("loss", ["squared", "hinge", "logistic", "multinomial", "l1", "crammer_singer"])
 def test_small_step_is_identity(loss):
     rng = np.random.default_rng(4)
     V = rng.normal(size=(5, 3)) * 2
@@ -129,3 +131,85 @@ def test_regulariser_brute_force(reg):
         ref = _golden(f, vm - abs(vm) - 1, vm + abs(vm) + 1)
         got = P.prox_reg(reg, np.array([[v]]), tau)[0, 0]
         assert abs(got - ref) < 1e-12 * max(1.0, abs(ref))
+
+
+def test_l1_loss_kinks():
+    t = 0.5
+    # |v - y| <= t: the output sits on the target; otherwise it moves t towards it
+    V = np.array([[1.2, 0.9, -3.0, 2.0]])
+    Y = np.array([[1.0, 1.5, -1.0, 2.0]])
+    got = P.prox_loss("l1", V, Y, t)
+    assert np.allclose(got, [[1.0, 1.4, -2.5, 2.0]], atol=0, rtol=1e-15)
+
+
+def _cs_problem(rng, m):
+    t = float(10 ** rng.uniform(-2, 1))
+    v = rng.normal(size=m) * rng.choice([0.3, 1.0, 3.0])
+    c = int(rng.integers(m))
+    y = -np.ones(m)
+    y[c] = 1.0
+    return v, y, c, t
+
+
+@pytest.mark.parametrize("m", [2, 3, 5, 10, 147])
+def test_crammer_singer_optimality_conditions(m):
+    """o = prox_{tV}(v) iff (v - o)/t is a subgradient of V at o.
+
+    V(o) = max_k (Delta_k + o_k - o_c) has subdifferential conv{e_k - e_c : k active},
+    active = the maximising k.  So g = (v - o)/t must be a - e_c with a >= 0,
+    sum a = 1 and a_k = 0 off the active set (this reads the definition of the
+    subdifferential, not the projection the oracle uses).
+    """
+    rng = np.random.default_rng(40 + m)
+    for _ in range(200):
+        v, y, c, t = _cs_problem(rng, m)
+        o = P.prox_loss("crammer_singer", v[None], y[None], t)[0]
+        a = (v - o) / t
+        a[c] += 1.0
+        scale = 1e-9 * (1.0 + np.abs(v).max() / t)
+        assert a.min() > -scale
+        assert abs(a.sum() - 1.0) < scale
+        delta = np.ones(m)
+        delta[c] = 0.0
+        margin = delta + o - o[c]
+        active = margin >= margin.max() - 1e-9 * (1.0 + np.abs(o).max())
+        assert np.all(a[~active] < scale), (a, margin)
+
+
+def test_crammer_singer_two_classes_is_binary_hinge_of_difference():
+    """m = 2: V = max(0, 1 - (o_c - o_k)); the mean of o is free and stays at the mean
+    of v, and the difference d = o_c - o_k minimises (d - e)^2/4 + t max(0, 1 - d),
+    e = v_c - v_k: the binary hinge prox with step 2t and y = 1."""
+    rng = np.random.default_rng(7)
+    for _ in range(500):
+        t = float(10 ** rng.uniform(-2, 1))
+        v = rng.normal(size=2) * 2
+        c = int(rng.integers(2))
+        k = 1 - c
+        y = np.array([-1.0, -1.0])
+        y[c] = 1.0
+        o = P.prox_loss("crammer_singer", v[None], y[None], t)[0]
+        e = v[c] - v[k]
+        d = e if e > 1.0 else (e + 2 * t if e < 1.0 - 2 * t else 1.0)
+        assert abs((o[c] - o[k]) - d) < 1e-12 * (1 + abs(d))
+        assert abs(o.sum() - v.sum()) < 1e-12 * (1 + np.abs(v).sum())
+
+
+@pytest.mark.parametrize("m", [3, 4])
+def test_crammer_singer_brute_force(m):
+    """Against a generic constrained minimiser of the epigraph form
+    min 1/2 |o - v|^2 + t s  subject to  s >= Delta_k + o_k - o_c for every k."""
+    rng = np.random.default_rng(60 + m)
+    for _ in range(25):
+        v, y, c, t = _cs_problem(rng, m)
+        delta = np.ones(m)
+        delta[c] = 0.0
+        f = lambda z: 0.5 * np.sum((z[:m] - v) ** 2) + t * z[m]
+        cons = [{"type": "ineq", "fun": (lambda z, k=k: z[m] - (delta[k] + z[k] - z[c]))} for k in range(m)]
+        z0 = np.concatenate([v, [np.max(delta + v - v[c])]])
+        res = optimize.minimize(f, z0, method="SLSQP", constraints=cons,
+                                options=dict(ftol=1e-15, maxiter=1000))
+        got = P.prox_loss("crammer_singer", v[None], y[None], t)[0]
+        obj = lambda o: 0.5 * np.sum((o - v) ** 2) + t * P.loss_value("crammer_singer", y[None], o[None])
+        assert np.max(np.abs(got - res.x[:m])) < 1e-6
+        assert obj(got) <= obj(res.x[:m]) + 1e-12
