@@ -55,7 +55,10 @@ typedef enum {
   RFF_LOSS_SQUARED = 0,    /* |y - o|^2, real targets                                  */
   RFF_LOSS_HINGE = 1,      /* m = 1: max(0, 1 - y o); m > 1: one-vs-rest, +-1 targets   */
   RFF_LOSS_LOGISTIC = 2,   /* log(1 + exp(-y o)) per output column, y = +-1            */
-  RFF_LOSS_MULTINOMIAL = 3 /* log sum_k exp(o_k) - o_c, c = argmax_k y_k               */
+  RFF_LOSS_MULTINOMIAL = 3, /* log sum_k exp(o_k) - o_c, c = argmax_k y_k              */
+  RFF_LOSS_L1 = 4,          /* |y - o|_1, real targets                                  */
+  RFF_LOSS_CRAMMER_SINGER = 5 /* multiclass hinge max_k (Delta_k + o_k - o_c),          */
+                              /* Delta_k = 1 - [k = c], c = argmax_k y_k                */
 } rff_loss;
 
 /* Regularisers r(W), separable over column blocks (Sec. 3, r = sum_j r_j(W_j)). */

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "librff_admm.so")
 RFF_OK, RFF_EINVAL, RFF_ENOMEM, RFF_ECUDA, RFF_ETIMEOUT, RFF_ENOTREADY, RFF_ENUMERIC = range(7)
 _STATUS = {0: "RFF_OK", 1: "RFF_EINVAL", 2: "RFF_ENOMEM", 3: "RFF_ECUDA", 4: "RFF_ETIMEOUT",
            5: "RFF_ENOTREADY", 6: "RFF_ENUMERIC"}
-LOSSES = {"squared": 0, "hinge": 1, "logistic": 2, "multinomial": 3}
+LOSSES = {"squared": 0, "hinge": 1, "logistic": 2, "multinomial": 3, "l1": 4, "crammer_singer": 5}
 REGS = {"l2": 0, "l1": 1}
 PRECS = {"fp32": 0, "split_bf16": 1, "cached_z": 2}
 RHO_SCALES = {"sum": 0, "mean": 1}

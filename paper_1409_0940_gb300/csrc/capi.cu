@@ -170,7 +170,7 @@ rff_status check_query_range(rff_admm_t h, int maxbits) {
 
 rff_status check_params(const rff_admm_params* p, std::string& why) {
   if (!p) { why = "params is NULL"; return RFF_EINVAL; }
-  if (p->loss < 0 || p->loss > 3) { why = "unknown loss"; return RFF_EINVAL; }
+  if (p->loss < 0 || p->loss > 5) { why = "unknown loss"; return RFF_EINVAL; }
   if (p->reg < 0 || p->reg > 1) { why = "unknown regulariser"; return RFF_EINVAL; }
   if (p->prec < 0 || p->prec > 2) { why = "unknown precision"; return RFF_EINVAL; }
   if (p->rho_scale < 0 || p->rho_scale > 1) { why = "unknown rho scale"; return RFF_EINVAL; }
@@ -1764,7 +1764,7 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
 
 rff_status rff_prox_loss(int32_t loss, const float* V, const float* Yv, int64_t n, int32_t m, double t,
                          int32_t newton_iters, float* out, void* stream) {
-  if (loss < 0 || loss > 3 || n < 0 || m < 1 || m > 256 || !(t >= 0) || (n > 0 && (!V || !Yv || !out)))
+  if (loss < 0 || loss > 5 || n < 0 || m < 1 || m > 256 || !(t >= 0) || (n > 0 && (!V || !Yv || !out)))
     return RFF_EINVAL;
   if (loss == RFF_LOSS_LOGISTIC && m != 1) return RFF_EINVAL;
   return launch_prox_loss(loss, V, Yv, n, m, m, (float)t, newton_iters > 0 ? newton_iters : 8, out,

@@ -12,7 +12,12 @@ namespace rff {
 
 namespace {
 
-constexpr int LOSS_SQUARED = 0, LOSS_HINGE = 1, LOSS_LOGISTIC = 2, LOSS_MULTINOMIAL = 3;
+constexpr int LOSS_SQUARED = 0, LOSS_HINGE = 1, LOSS_LOGISTIC = 2, LOSS_MULTINOMIAL = 3, LOSS_L1 = 4,
+              LOSS_CRAMMER_SINGER = 5;
+// losses whose prox couples the outputs of a row (a warp per row); the others act per entry
+__host__ __device__ constexpr bool row_loss(int loss) {
+  return loss == LOSS_MULTINOMIAL || loss == LOSS_CRAMMER_SINGER;
+}
 
 // dst[p][c] = src[map[p]][c] for c < w, zero elsewhere (map[p] < 0: zero row)
 __global__ void k_scatter_rows(const float* __restrict__ src, int64_t lds, int64_t w,
@@ -70,9 +75,16 @@ __device__ __forceinline__ float prox_logistic(float v, float y, float t, int it
   return y * p;
 }
 
+// l1 loss |y - o|: v - y soft-thresholded by t, about y
+__device__ __forceinline__ float prox_l1(float v, float y, float t) {
+  const float d = v - y;
+  return y + copysignf(fmaxf(fabsf(d) - t, 0.f), d);
+}
+
 __device__ __forceinline__ float prox_scalar(int loss, float v, float y, float t, int iters) {
   if (loss == LOSS_SQUARED) return prox_squared(v, y, t);
   if (loss == LOSS_HINGE) return prox_hinge(v, y, t);
+  if (loss == LOSS_L1) return prox_l1(v, y, t);
   return prox_logistic(v, y, t, iters);
 }
 
@@ -110,15 +122,9 @@ __device__ __forceinline__ float solve_logp(float a, float t, float logt) {
   return q;
 }
 
-__device__ void prox_multinomial_row(const float (&v)[MAXPL], const float (&y)[MAXPL], int m, float t, int iters,
-                                     float (&o)[MAXPL]) {
+// class index of a row, the first maximum of y over the m outputs (a warp, lanes over outputs)
+__device__ __forceinline__ int row_class(const float (&y)[MAXPL], int m) {
   const int lane = threadIdx.x & 31;
-  if (!(t > 1e-30f)) {
-#pragma unroll
-    for (int q = 0; q < MAXPL; ++q) o[q] = v[q];
-    return;
-  }
-  // class index: first maximum of y
   float best = -INFINITY;
   int bidx = 1 << 30;
 #pragma unroll
@@ -132,6 +138,18 @@ __device__ void prox_multinomial_row(const float (&v)[MAXPL], const float (&y)[M
     const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
     if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
   }
+  return bidx;
+}
+
+__device__ void prox_multinomial_row(const float (&v)[MAXPL], const float (&y)[MAXPL], int m, float t, int iters,
+                                     float (&o)[MAXPL]) {
+  const int lane = threadIdx.x & 31;
+  if (!(t > 1e-30f)) {
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) o[q] = v[q];
+    return;
+  }
+  const int bidx = row_class(y, m);
   float w[MAXPL];
   float wmax = -INFINITY;
 #pragma unroll
@@ -164,9 +182,75 @@ __device__ void prox_multinomial_row(const float (&v)[MAXPL], const float (&y)[M
   }
 }
 
+// Crammer-Singer multiclass hinge prox of one row (a warp, lanes over the m outputs),
+// V(y, o) = max_k (Delta_k + o_k - o_c), Delta_k = 1 - [k = c], c = argmax_k y_k (first).
+// The dual of the prox is a projection onto the probability simplex; scaled by t it reads:
+// with w_k = v_k + Delta_k + t [k = c], the prox is o_k = min(w_k, tau) - Delta_k where tau
+// solves sum_k max(w_k - tau, 0) = t.  tau by Michelot's finite method (1986): from the set of
+// all outputs, tau = (sum of w over the set - t) / its size, and the entries at or below tau
+// leave the set, until none leaves.  The set shrinks at every round but the last (at most m
+// rounds) and keeps its largest entry, which lies above tau for t > 0.  The sums run over
+// w_k - max_k w_k: the entries of the final set lie within t of the maximum (tau >= max w - t),
+// so tau is formed from values of the size of t rather than of |w|.  The warp sums are
+// butterflies, so every lane holds the same tau and takes the same exit.
+__device__ void prox_crammer_singer_row(const float (&v)[MAXPL], const float (&y)[MAXPL], int m, float t,
+                                        float (&o)[MAXPL]) {
+  const int lane = threadIdx.x & 31;
+  if (!(t > 0.f)) {
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) o[q] = v[q];
+    return;
+  }
+  const int c = row_class(y, m);
+  float w[MAXPL];
+  bool in[MAXPL];
+  float wmax = -INFINITY;
+#pragma unroll
+  for (int q = 0; q < MAXPL; ++q) {
+    const int k = lane + 32 * q;
+    in[q] = k < m;
+    w[q] = v[q] + (k == c ? t : 1.f);
+    if (in[q]) wmax = fmaxf(wmax, w[q]);
+  }
+  wmax = warp_max(wmax);
+  float sum = 0.f;
+#pragma unroll
+  for (int q = 0; q < MAXPL; ++q) {
+    w[q] -= wmax;   // shifted: tau below is relative to the maximum
+    if (in[q]) sum += w[q];
+  }
+  int cnt = m;
+  float tau = (warp_sum(sum) - t) / (float)cnt;
+  for (int round = 0; round < m; ++round) {
+    float s2 = 0.f;
+    int c2 = 0;
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q)
+      if (in[q] && w[q] > tau) { s2 += w[q]; ++c2; }
+    s2 = warp_sum(s2);
+    c2 = __reduce_add_sync(0xffffffffu, c2);
+    if (c2 == cnt || c2 == 0) break;
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) in[q] = in[q] && w[q] > tau;
+    cnt = c2;
+    tau = (s2 - t) / (float)cnt;
+  }
+#pragma unroll
+  for (int q = 0; q < MAXPL; ++q) {
+    const int k = lane + 32 * q;
+    o[q] = (k < m) ? (fminf(w[q], tau) + wmax) - (k == c ? 0.f : 1.f) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void prox_row(int loss, const float (&v)[MAXPL], const float (&y)[MAXPL], int m, float t,
+                                         int iters, float (&o)[MAXPL]) {
+  if (loss == LOSS_MULTINOMIAL) prox_multinomial_row(v, y, m, t, iters, o);
+  else prox_crammer_singer_row(v, y, m, t, o);
+}
+
 __global__ void k_prox_loss(int loss, const float* __restrict__ V, const float* __restrict__ Y, int64_t n, int m,
                             int64_t ld, float t, int iters, float* __restrict__ out) {
-  if (loss == LOSS_MULTINOMIAL) {
+  if (row_loss(loss)) {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
     if (row >= n) return;
     const int lane = threadIdx.x & 31;
@@ -177,7 +261,7 @@ __global__ void k_prox_loss(int loss, const float* __restrict__ V, const float* 
       v[q] = (k < m) ? V[row * ld + k] : 0.f;
       y[q] = (k < m) ? Y[row * ld + k] : 0.f;
     }
-    prox_multinomial_row(v, y, m, t, iters, o);
+    prox_row(loss, v, y, m, t, iters, o);
 #pragma unroll
     for (int q = 0; q < MAXPL; ++q) {
       const int k = lane + 32 * q;
@@ -282,8 +366,8 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
       else y[q] = 0.f;
     }
     float o[MAXPL];
-    if (LOSS == LOSS_MULTINOMIAL) {
-      prox_multinomial_row(w_in, y, a.m, a.t_loss, a.newton, o);
+    if (row_loss(LOSS)) {
+      prox_row(LOSS, w_in, y, a.m, a.t_loss, a.newton, o);
     } else {
 #pragma unroll
       for (int q = 0; q < MAXPL; ++q) o[q] = prox_scalar(LOSS, w_in[q], y[q], a.t_loss, a.newton);
@@ -500,11 +584,21 @@ __global__ void __launch_bounds__(256) k_loss_sum(int loss, const float* __restr
       double se = 0.0;
       for (int k = 0; k < m; ++k) se += exp((double)o[k] - mx);
       acc += mx + log(se) - (double)o[c];
+    } else if (loss == LOSS_CRAMMER_SINGER) {
+      double yb = -1e300;
+      int c = 0;
+      for (int k = 0; k < m; ++k)
+        if (y[k] > yb) { yb = y[k]; c = k; }
+      double mx = 0.0;   // the k = c term
+      for (int k = 0; k < m; ++k)
+        if (k != c) mx = fmax(mx, 1.0 + (double)o[k] - (double)o[c]);
+      acc += mx;
     } else {
       for (int k = 0; k < m; ++k) {
         const double yy = y[k], oo = o[k];
         if (loss == LOSS_SQUARED) acc += (yy - oo) * (yy - oo);
         else if (loss == LOSS_HINGE) acc += fmax(0.0, 1.0 - yy * oo);
+        else if (loss == LOSS_L1) acc += fabs(yy - oo);
         else acc += (-yy * oo > 0 ? -yy * oo + log1p(exp(yy * oo)) : log1p(exp(-yy * oo)));
       }
     }
@@ -588,7 +682,7 @@ cudaError_t launch_prox_loss(int loss, const float* V, const float* Y, int64_t n
                              int newton, float* out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (m > 32 * MAXPL) return cudaErrorInvalidValue;
-  const int64_t threads = loss == LOSS_MULTINOMIAL ? n * 32 : n * m;
+  const int64_t threads = row_loss(loss) ? n * 32 : n * m;
   k_prox_loss<<<nblk(threads), 256, 0, st>>>(loss, V, Y, n, m, ld, t, newton, out);
   return cudaGetLastError();
 }
@@ -618,13 +712,20 @@ cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st) {
       attr = cudaFuncSetAttribute(k_exchange<LOSS_LOGISTIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_exchange<LOSS_MULTINOMIAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_exchange<LOSS_L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_exchange<LOSS_CRAMMER_SINGER>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   });
   if (attr != cudaSuccess) return attr;
   switch (a.loss) {
     case LOSS_SQUARED: k_exchange<LOSS_SQUARED><<<grid, 256, smem, st>>>(a); break;
     case LOSS_HINGE: k_exchange<LOSS_HINGE><<<grid, 256, smem, st>>>(a); break;
     case LOSS_LOGISTIC: k_exchange<LOSS_LOGISTIC><<<grid, 256, smem, st>>>(a); break;
-    default: k_exchange<LOSS_MULTINOMIAL><<<grid, 256, smem, st>>>(a); break;
+    case LOSS_MULTINOMIAL: k_exchange<LOSS_MULTINOMIAL><<<grid, 256, smem, st>>>(a); break;
+    case LOSS_L1: k_exchange<LOSS_L1><<<grid, 256, smem, st>>>(a); break;
+    case LOSS_CRAMMER_SINGER: k_exchange<LOSS_CRAMMER_SINGER><<<grid, 256, smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

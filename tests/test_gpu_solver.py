@@ -68,6 +68,9 @@ GRIDS = [
     ("hinge", "l2", 500, 7, 1, 200, 1, 2, 25, 1e-3, 0.5, 2.0),
     ("logistic", "l2", 600, 8, 1, 256, 2, 1, 25, 1e-3, 1.0, 2.5),
     ("multinomial", "l2", 700, 10, 4, 320, 2, 2, 25, 1e-3, 1.0, 3.0),
+    ("l1", "l2", 640, 9, 2, 256, 2, 2, 25, 1e-4, 1.0, 2.0),
+    ("crammer_singer", "l2", 700, 10, 6, 320, 2, 2, 25, 1e-3, 1.0, 3.0),
+    ("crammer_singer", "l1", 600, 12, 147, 384, 2, 2, 15, 1e-4, 1.0, 3.0),
     # wide outputs: unequal column blocks (301 + 300 features, three 128-row tiles with a
     # ragged last one) and the widest output block the tensor-core passes take (m_pad = 256)
     ("squared", "l2", 900, 12, 150, 601, 2, 2, 20, 1e-3, 1.0, 3.0),
@@ -77,11 +80,13 @@ GRIDS = [
     ("hinge", "l2", 500, 7, 3, 2048, 2, 2, 20, 1e-3, 1.0, 3.0),
     ("logistic", "l1", 500, 12, 1, 1536, 3, 1, 20, 1e-3, 1.0, 2.5),
     ("multinomial", "l2", 400, 9, 4, 1200, 2, 2, 15, 1e-3, 1.0, 3.0),
+    ("crammer_singer", "l2", 400, 9, 5, 1200, 2, 2, 15, 1e-3, 1.0, 3.0),
+    ("l1", "l2", 500, 8, 3, 1536, 3, 1, 15, 1e-4, 1.0, 2.0),
 ]
 
 
 def _data(loss, n, d, m, seed):
-    if loss == "squared":
+    if loss in ("squared", "l1"):
         X, y = synth.ridge(n=n, d=d, seed=seed)
         Y = np.repeat(y, m, axis=1) * np.linspace(1, 0.5, m, dtype=np.float32)[None]
         return X, np.ascontiguousarray(Y, dtype=np.float32)

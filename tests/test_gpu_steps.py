@@ -122,12 +122,14 @@ def test_features_independent_of_block_split(rff):
 
 # ----------------------------------------------------------------- proxes
 @pytest.mark.parametrize("loss,m", [("squared", 3), ("hinge", 1), ("hinge", 7), ("logistic", 1),
-                                    ("multinomial", 5), ("multinomial", 147)])
+                                    ("multinomial", 5), ("multinomial", 147), ("l1", 1), ("l1", 6),
+                                    ("crammer_singer", 2), ("crammer_singer", 10), ("crammer_singer", 147),
+                                    ("crammer_singer", 256)])
 def test_prox_loss_matches_oracle(rff, loss, m):
     rng = np.random.default_rng(m)
     n = 3000
     V = (rng.standard_normal((n, m)) * 2).astype(np.float32)
-    if loss == "squared":
+    if loss in ("squared", "l1"):
         Y = rng.standard_normal((n, m)).astype(np.float32)
     elif loss in ("hinge", "logistic") and m == 1:
         Y = np.where(rng.random((n, 1)) < 0.5, -1.0, 1.0).astype(np.float32)
