@@ -37,6 +37,17 @@ memory-efficient rewrite of Sec. 3 (U_ij = Z_ij^T O_ij, one Delta_i,
 Z_ij^T Obar_ij = U_ij + Z_ij^T Delta_i / (C + 1),
 Obar_i = sum_j O_ij / (C + 1) + C/(C + 1) O_i), with the Z^T nu term restored.
 
+Stochastic block subsets (proposed in Sec. 5 and the conclusion, not specified there):
+with ``block_fraction`` p < 1, iteration k updates only the blocks drawn active.
+Reading: an inactive block (i, j) skips the graph projection and keeps What_ij, O_ij
+(and U_ij); every other update, each dual mu_ij included, runs as usual from the
+blocks' current values.  The duals of every consensus group then keep summing to zero
+(mu_j + sum_i mu_ij = 0 after each averaging step), as in the full method; freezing an
+inactive block's mu_ij breaks that sum and the iterates settle at a point whose residuals
+vanish but which is not the minimiser.  The draw: block b = i C + j is active in iteration k (from 0) iff
+(w >> 8) < floor(p 2^24), w the first word of Philox4x32-10 at counter (b, k, 2, 0)
+under the solve's seed (tags 0 and 1 draw G and b); p = 1 keeps every block active.
+
 Stopping: the paper runs a fixed number of iterations; so does this oracle.
 Residuals (reported, never used to stop):
   primal = |(O - Obar, W - Wbar, {What_ij - Wbar_j})|_F
@@ -48,8 +59,19 @@ graph projection; "equation" == "reorganised" to 1e-12; residuals -> 0.
 import numpy as np
 import scipy.linalg as sla
 
+from . import philox
 from . import prox as P
 from . import rff
+
+
+def block_mask(seed, R, C, k, p):
+    """Active blocks of iteration k (R x C booleans) for the block fraction p."""
+    thr = np.uint64(int(np.floor(float(p) * 2.0 ** 24)))
+    k0, k1 = philox.seed_key(seed)
+    b = np.arange(R * C, dtype=np.uint64)
+    z = np.zeros_like(b)
+    w0, _, _, _ = philox.philox4x32_10(b, z + np.uint64(k), z + np.uint64(2), z, k0, k1)
+    return ((w0 >> np.uint64(8)) < thr).reshape(R, C)
 
 
 # ----------------------------------------------------------------- closed forms
@@ -161,8 +183,10 @@ class Problem:
         return Zq @ W
 
 
-def admm(prob, iters, variant="equation", history=False):
-    """Run `iters` iterations; returns a dict of the final state (+ history)."""
+def admm(prob, iters, variant="equation", history=False, block_fraction=1.0):
+    """Run `iters` iterations; returns a dict of the final state (+ history).
+
+    block_fraction < 1: the stochastic block-subset variant (module header)."""
     R, C, m = prob.R, prob.C, prob.m
     rows, cols = prob.rows, prob.cols
     ni = [int(rows[i + 1] - rows[i]) for i in range(R)]
@@ -185,7 +209,9 @@ def admm(prob, iters, variant="equation", history=False):
     Dbar = [z((ni[i], m)) for i in range(R)]
     hist = []
 
-    for _ in range(iters):
+    for k in range(iters):
+        act = (block_mask(prob.seed, R, C, k, block_fraction) if block_fraction < 1.0
+               else np.ones((R, C), dtype=bool))
         Wbar_old = [w.copy() for w in Wbar]
         Obar_old = [o.copy() for o in Obar]
         for i in range(R):
@@ -196,7 +222,8 @@ def admm(prob, iters, variant="equation", history=False):
         if variant == "equation":
             for i in range(R):
                 for j in range(C):
-                    What[i][j], Oij[i][j] = solvers[i][j].project(Wbar[j] - muij[i][j], Obij[i][j] + nu[i])
+                    if act[i, j]:
+                        What[i][j], Oij[i][j] = solvers[i][j].project(Wbar[j] - muij[i][j], Obij[i][j] + nu[i])
             for j in range(C):
                 Wbar[j] = (W[j] + sum(What[i][j] for i in range(R))) / (R + 1)
             for i in range(R):
@@ -219,6 +246,8 @@ def admm(prob, iters, variant="equation", history=False):
                     # Z^T (Obar_ij + nu_i) = U_ij + Z^T (Delta_i/(C+1) + nu_i); the
                     # projection's right-hand side is assembled from these parts
                     # and solved with the cached factor of block (i, j).
+                    if not act[i, j]:
+                        continue
                     s = solvers[i][j]
                     rhs = Wbar[j] - muij[i][j] + U[i][j] + Zs[j].T @ corr
                     if s.gram:
@@ -242,6 +271,8 @@ def admm(prob, iters, variant="equation", history=False):
         elif variant == "algorithm1_literal":
             # Algorithm 1 exactly as printed: no Z^T nu term, and mu', mu
             # updated with the Wbar of the previous iteration.
+            if block_fraction < 1.0:
+                raise ValueError("the literal Algorithm 1 has no stochastic variant")
             for i in range(R):
                 Zs = [solvers[i][j].Z for j in range(C)]
                 Delta = O[i].copy()

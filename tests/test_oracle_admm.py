@@ -166,3 +166,54 @@ def test_predict_is_features_times_weights():
     Xq = X[:7]
     G, b = philox.rff_params(5, 1.0, 3, 32)
     assert np.allclose(p.predict(Xq, W), rff.features(Xq, G, b, 32) @ W, rtol=0, atol=1e-14)
+
+
+# ----------------------------------------------------------------- stochastic block subsets
+def test_block_mask_frequency_and_full_fraction():
+    """Each block is active with probability p, independently across blocks and iterations
+    (binomial bounds at 6 sigma); p = 1 keeps every block active."""
+    R, C, K = 4, 4, 400
+    for p in (0.25, 0.5, 0.8):
+        M = np.array([admm.block_mask(11, R, C, k, p) for k in range(K)])
+        n = M.size
+        assert abs(M.mean() - p) < 6 * np.sqrt(p * (1 - p) / n)
+        per_block = M.reshape(K, R * C).mean(axis=0)
+        assert np.all(np.abs(per_block - p) < 6 * np.sqrt(p * (1 - p) / K))
+        # successive iterations are not copies of each other
+        assert np.mean([np.array_equal(M[k], M[k + 1]) for k in range(K - 1)]) < 0.2
+    assert all(admm.block_mask(3, 5, 3, k, 1.0).all() for k in range(50))
+
+
+def test_stochastic_equation_equals_reorganised():
+    X, Y = synth.multiclass(n=300, d=5, m=3, seed=12)
+    p = admm.Problem(X, Y, "hinge", "l2", lam=1e-3, sigma=2.0, rho=1.0, D=120, R=3, C=2, seed=5)
+    a = admm.admm(p, 40, variant="equation", block_fraction=0.5)
+    b = admm.admm(p, 40, variant="reorganised", block_fraction=0.5)
+    assert np.abs(a["Wbar"] - b["Wbar"]).max() < 1e-12 * max(1.0, np.abs(a["Wbar"]).max())
+
+
+def test_stochastic_keeps_consensus_duals_summing_to_zero():
+    """mu_j + sum_i mu_ij = 0 after every iteration, as in the full method."""
+    X, Y = synth.ridge(n=240, d=4, seed=13)
+    p = admm.Problem(X, Y, "squared", "l2", lam=1e-3, sigma=2.0, rho=1.0, D=90, R=3, C=3, seed=8)
+    for it in (1, 7, 30):
+        o = admm.admm(p, it, block_fraction=0.4)
+        s = o["mu"] + sum(o["muij"])
+        assert np.abs(s).max() < 1e-12 * max(1.0, np.abs(o["mu"]).max())
+
+
+def test_stochastic_reaches_ridge_closed_form():
+    """With half of the blocks updated per iteration the iterates still reach the
+    minimiser (Sec. 2.2 closed form), at about half the rate of the full method."""
+    X, Y = synth.ridge(n=300, d=5, seed=4)
+    p = admm.Problem(X, Y, "squared", "l2", lam=1e-3, sigma=2.0, rho=1.0, D=96, R=2, C=2, seed=7)
+    W = admm.ridge_closed_form(p.Z(), p.Y, p.lam)
+    o = admm.admm(p, 6000, variant="reorganised", block_fraction=0.5)
+    assert np.linalg.norm(o["Wbar"] - W) / np.linalg.norm(W) < 1e-5
+
+
+def test_stochastic_residuals_go_to_zero():
+    X, Y = synth.multiclass(n=400, d=6, m=3, seed=8)
+    p = admm.Problem(X, Y, "hinge", "l2", lam=1e-3, sigma=3.0, rho=1.0, D=64, R=2, C=2, seed=3)
+    h = admm.admm(p, 1200, variant="reorganised", history=True, block_fraction=0.5)["history"]
+    assert h[-1, 0] < 1e-2 * h[5, 0] and h[-1, 1] < 1e-2 * h[5, 1]
