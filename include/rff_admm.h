@@ -175,6 +175,18 @@ rff_status rff_admm_estimate_bytes(const rff_admm_params* params, int64_t n, int
  * Errors: RFF_EINVAL for a wrong count or a non-positive value. */
 rff_status rff_admm_set_lambdas(rff_admm_t h, const double* lambdas, int32_t m);
 
+/* Stochastic block subsets (proposed in Sec. 5 and the conclusion): from the next
+ * iteration on, each block (i, j) takes part in the graph projection of an iteration
+ * with probability p, independently; the others keep their W'_ij and O'_ij for that
+ * iteration while every prox, the exchange, the averaging and every dual (mu_ij too)
+ * update as usual.  Block b = i C + j is active in iteration k (counted from the
+ * start of the solve, across calls and checkpoints) iff (w >> 8) < floor(p 2^24), w the
+ * first word of Philox4x32-10 at counter (b, k, 2, 0) under params.seed.  p = 1 (the
+ * default) is the deterministic method.  The iteration time of the passes and the
+ * projection falls with the number of active blocks.
+ * Errors: RFF_EINVAL unless 2^-24 <= p <= 1. */
+rff_status rff_admm_set_block_fraction(rff_admm_t h, double p);
+
 /* Queue `iters` iterations on the handle's stream and return without waiting
  * (set-up, when still needed, runs first and synchronously).  rff_admm_wait
  * blocks until they finished and reports a device-side failure. */
@@ -227,8 +239,9 @@ rff_status rff_admm_get_weights(rff_admm_t h, float* W, int is_device_ptr);
 rff_status rff_admm_get_state(rff_admm_t h, void* buf, size_t* bytes);
 
 /* Restore a state written by rff_admm_get_state for the same data, parameters
- * and grid; continuing from it reproduces an uninterrupted run bit for bit.
- * Errors: RFF_EINVAL on a size, version or parameter mismatch. */
+ * and grid; continuing from it reproduces an uninterrupted run bit for bit (with a
+ * block fraction, when the same fraction is set).  Runs the set-up (factors) first
+ * if no solve has yet.  Errors: RFF_EINVAL on a size, version or parameter mismatch. */
 rff_status rff_admm_set_state(rff_admm_t h, const void* buf, size_t bytes);
 
 /* Per-phase device timing of the iterations, for performance work.  enable = 1

@@ -77,6 +77,7 @@ PROTOTYPES = {
     "rff_admm_estimate_bytes": (_I32, [ctypes.POINTER(rff_admm_params), _I64, _I64, ctypes.POINTER(_SZ),
                                        ctypes.POINTER(_SZ)]),
     "rff_admm_set_lambdas": (_I32, [_P, _P, _I32]),
+    "rff_admm_set_block_fraction": (_I32, [_P, _D]),
     "rff_admm_enqueue": (_I32, [_P, _I32]),
     "rff_admm_wait": (_I32, [_P]),
     "rff_sweep_run": (_I32, [_P, _I32, _I32]),
@@ -381,6 +382,10 @@ def rff_server_destroy(srv):
 
 
 # ----------------------------------------------------------------- convenience
+def rff_admm_set_block_fraction(h, p):
+    _check(lib.rff_admm_set_block_fraction(h, float(p)), h)
+
+
 class Solver:
     """Owns one rff_admm_t handle."""
 
@@ -414,6 +419,9 @@ class Solver:
 
     def set_lambdas(self, lambdas):
         rff_admm_set_lambdas(self.h, lambdas)
+
+    def set_block_fraction(self, p):
+        rff_admm_set_block_fraction(self.h, p)
 
     def enqueue(self, iters):
         rff_admm_enqueue(self.h, iters)

@@ -81,6 +81,15 @@ struct rff_admm_s {
   float zscale = 1.f;
   SgJob *p1jobs = nullptr, *p2jobs = nullptr;
   int np1 = 0, np2 = 0, nsplit_cz = 1;
+  // stochastic block subsets: a block is active in an iteration when its Philox word is
+  // below bthr (= floor(p 2^24); 2^24: every block, the deterministic method)
+  double bfrac = 1.0;
+  uint32_t bthr = 1u << 24;
+  uint8_t* bmask = nullptr;   // R x C, this iteration's active blocks (device)
+  int64_t* bctr = nullptr;    // the iteration number the next mask is drawn for (device)
+  int64_t bctr_host = 0;
+  bool stochastic() const { return bthr < (1u << 24); }
+  const uint8_t* act() const { return stochastic() ? bmask : nullptr; }
   std::vector<double> lam_col;  // lambda of each output column (empty: params.lambda for all)
   float* lam_dev = nullptr;     // lambda_c / lambda per column (m_pad), or null
   GemmDesc* gdesc = nullptr;  // R*C
@@ -467,6 +476,8 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   AL(s.d_col_slot, s.C);
   AL(s.d_col_size, s.C);
   AL(s.d_zero, 2);
+  AL(s.bmask, (int64_t)s.R * s.C);
+  AL(s.bctr, 1);
   if (s.split_path()) {
     AL(s.Xhi, s.nslots * s.dld);
     AL(s.Xlo, s.nslots * s.dld);
@@ -693,6 +704,9 @@ rff_status autotune(rff_admm_t h) {
   s.tc_kc = best_kc;
   s.tc_zt = best_zt;
   s.nsplit = best_ns;
+  // the timing runs wrote O'_ij, which starts at zero: a block that sits out the first
+  // iterations of a stochastic solve reads it as it is
+  CK(cudaMemsetAsync(s.Op, 0, (size_t)s.C * s.nslots * s.mpad * sizeof(float), s.st));
   if (tc_error_word() != 0) return h->fail(RFF_ETIMEOUT, "a tensor-core pass gave up waiting during tuning");
   return RFF_OK;
 }
@@ -730,6 +744,7 @@ rff_status materialise_z(rff_admm_t h) {
       jb.b_row = (int32_t)(i * s.mpad);
       jb.b_k0 = (int32_t)s.col_slot[j];
       jb.nk = (int32_t)ceil_div(s.col_size[j], 32);
+      jb.blk = i * s.C + j;
       jb.out = ((int64_t)j * s.nslots + rt * 128) * s.mpad;
       j2.push_back(jb);
     }
@@ -748,6 +763,7 @@ rff_status materialise_z(rff_admm_t h) {
         jb.b_row = (int32_t)(j * s.mpad);
         jb.b_k0 = jb.a_k0;
         jb.nk = (int32_t)((t1 - t0) * 4);
+        jb.blk = i * s.C + j;
         jb.out = (((int64_t)sp * s.R + i) * s.fslots + ft * 128) * s.mpad;
         j1.push_back(jb);
       }
@@ -878,6 +894,7 @@ rff_status setup_factors(rff_admm_t h) {
           jb.b_row = (int32_t)(i * s.mpad);
           jb.b_k0 = (int32_t)s.col_slot[j];
           jb.nk = (int32_t)ceil_div(sj, 32);
+          jb.blk = (int32_t)blk;
           jb.out = ((int64_t)i * s.fslots + s.col_slot[j] + m0) * s.mpad;
           qj.push_back(jb);
         }
@@ -948,6 +965,7 @@ SgView qgemm_view(const rff_admm_s& s) {
   v.out_scale = 1.f;
   v.amax = s.amax + AMAX_W;
   v.two_acc = 1;
+  v.bmask = s.act();
   v.st = s.st;
   return v;
 }
@@ -973,6 +991,7 @@ SgView cz_pass1_view(const rff_admm_s& s) {
   v.out_scale = 1.f / s.zscale;
   v.b_amax = s.amax;
   v.smem_budget = 110 * 1024;   // two CTAs per SM: one's epilogue overlaps the other's stream
+  v.bmask = s.act();
   v.st = s.st;
   return v;
 }
@@ -998,7 +1017,22 @@ SgView cz_pass2_view(const rff_admm_s& s) {
   v.b_amax = s.amax + AMAX_W;
   v.amax = s.amax + AMAX_OP;
   v.smem_budget = 110 * 1024;
+  v.bmask = s.act();
   v.st = s.st;
+  return v;
+}
+
+// kernel launches of one iteration (the count a captured iteration replays)
+int iter_launches(const rff_admm_s& s) {
+  int n = s.outer ? (s.split_path() ? 13 : 9) : (s.split_path() ? 8 : 7);
+  if (s.stochastic()) n += 1 + (s.split_path() && !s.outer ? 1 : 0);   // the mask; max |O'| of all blocks
+  return n;
+}
+
+// the tensor-core view of an iteration's passes: the block mask of a stochastic iteration
+TcView iter_view(const rff_admm_s& s) {
+  TcView v = tc_view(s);
+  v.bmask = s.act();
   return v;
 }
 
@@ -1046,12 +1080,15 @@ rff_status iterate_outer(rff_admm_t h, int k) {
   int* scratch_flag = reinterpret_cast<int*>(s.amax + AMAX_FLAG);
   rff_status r;
   if ((r = mark(h, k, 0)) != RFF_OK) return r;
+  if (s.stochastic()) CK(launch_block_mask(s.p.seed, s.bthr, s.R * s.C, s.bctr, s.bmask, s.st));
   CK(launch_prox_reg(s.p.reg, s.Wbar, s.mu, nfe, s.t_reg, s.W, s.st, s.lam_dev, (int)s.mpad));
   if ((r = mark(h, k, 1)) != RFF_OK) return r;
-  // R_ij = Z_ij^T V_ij
+  // R_ij = Z_ij^T V_ij (inactive blocks of a stochastic iteration are skipped by every
+  // per-block kernel below and keep their W'_ij and O'_ij)
   PassArgs a = base_pass_args(s);
+  a.bmask = s.act();
   if (s.split_path()) {
-    CK(tc_pass1(tc_view(s), s.Rpart));
+    CK(tc_pass1(iter_view(s), s.Rpart));
   } else {
     a.M = s.V32;
     a.m_block_stride = s.nslots * s.mpad;
@@ -1067,9 +1104,10 @@ rff_status iterate_outer(rff_admm_t h, int k) {
     CK(launch_finite_check(s.rhs, s.R * nfe, 0, scratch_flag, s.st, s.amax + AMAX_W));
     CK(launch_transpose_split_f16(s.rhs, s.fslots, (int)s.mpad, s.R, nfe, s.WThi, s.WTlo, s.fslots,
                                   s.mpad * s.fslots, 1.f, s.amax + AMAX_W, s.st));
-    CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.U32, 1, s.amax + AMAX_W));
+    CK(tc_pass2(iter_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.U32, 1, s.amax + AMAX_W));
   } else {
     PassArgs b = base_pass_args(s);
+    b.bmask = s.act();
     b.M = s.rhs;
     b.m_block_stride = nfe;
     b.out = s.U32;
@@ -1078,7 +1116,7 @@ rff_status iterate_outer(rff_admm_t h, int k) {
     CK(launch_pass2_simt(b, s.nslots, s.st));
   }
   // O'_ij = P_ij u_ij
-  CK(launch_gemm_f32_nn(s.gdesc, s.R * s.C, (int)nmax, (int)s.mpad, 1.f, 0.f, s.st));
+  CK(launch_gemm_f32_nn(s.gdesc, s.R * s.C, (int)nmax, (int)s.mpad, 1.f, 0.f, s.st, s.act()));
   // W'_ij = rhs_ij - Z_ij^T O'_ij (the second pass-1 product reuses the R partials)
   if (s.split_path()) {
     // O'^T as a scaled FP16 pair in the V^T buffers (V^T is rewritten by the exchange);
@@ -1087,18 +1125,19 @@ rff_status iterate_outer(rff_admm_t h, int k) {
     CK(launch_finite_check(s.Op, s.C * s.nslots * s.mpad, 0, scratch_flag, s.st, s.amax + AMAX_OP));
     CK(launch_transpose_split_f16(s.Op, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
                                   s.mpad * s.nslots, 1.f, s.amax + AMAX_OP, s.st));
-    TcView vo = tc_view(s);
+    TcView vo = iter_view(s);
     vo.v_amax = s.amax + AMAX_OP;
     CK(tc_pass1(vo, s.Rpart));
   } else {
     a.M = s.Op;
     CK(launch_pass1_simt(a, s.fslots, s.st));
   }
-  CK(launch_sub_partials(s.rhs, s.Rpart, s.nsplit, s.R, nfe, s.feat_of_slot, (int)s.mpad, s.What, s.st));
+  CK(launch_sub_partials(s.rhs, s.Rpart, s.nsplit, s.R, nfe, s.feat_of_slot, (int)s.mpad, s.What, s.st, s.act(),
+                         s.d_col_slot, s.C));
   if ((r = mark(h, k, 3)) != RFF_OK) return r;
   if ((r = mark(h, k, 4)) != RFF_OK) return r;
   if ((r = exchange_and_average(h, k)) != RFF_OK) return r;
-  s.launches += s.split_path() ? 13 : 9;
+  s.launches += iter_launches(s);
   return RFF_OK;
 }
 
@@ -1111,15 +1150,19 @@ rff_status iterate(rff_admm_t h, int k) {
   for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
   rff_status r;
   if ((r = mark(h, k, 0)) != RFF_OK) return r;
+  // stochastic variant: this iteration's active blocks; the per-block kernels below skip the
+  // others, which keep W'_ij and O'_ij (every dual still updates)
+  if (s.stochastic()) CK(launch_block_mask(s.p.seed, s.bthr, s.R * s.C, s.bctr, s.bmask, s.st));
   // W_j <- prox_{(n lam / rho) r}(Wbar_j - mu_j)
   CK(launch_prox_reg(s.p.reg, s.Wbar, s.mu, nfe, s.t_reg, s.W, s.st, s.lam_dev, (int)s.mpad));
   if ((r = mark(h, k, 1)) != RFF_OK) return r;
   // pass 1: R_ij = Z_ij^T V_ij,  V_ij = Obar_ij + nu_i
   PassArgs a = base_pass_args(s);
+  a.bmask = s.act();
   if (s.cached_z()) {
     CK(split_gemm(cz_pass1_view(s)));
   } else if (s.split_path()) {
-    CK(tc_pass1(tc_view(s), s.Rpart));
+    CK(tc_pass1(iter_view(s), s.Rpart));
   } else {
     a.M = s.V32;
     a.m_block_stride = s.nslots * s.mpad;
@@ -1142,7 +1185,7 @@ rff_status iterate(rff_admm_t h, int k) {
                                   s.mpad * s.fslots, 1.f, s.amax + AMAX_W, s.st));
   } else {
     CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st));
-    CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st));
+    CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st, s.act()));
   }
   if ((r = mark(h, k, 3)) != RFF_OK) return r;
   // pass 2: O'_ij = Z_ij W'_ij (eq. (gpOij))
@@ -1150,7 +1193,7 @@ rff_status iterate(rff_admm_t h, int k) {
   if (s.cached_z()) {
     CK(split_gemm(cz_pass2_view(s)));
   } else if (s.split_path()) {
-    CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + AMAX_W, s.amax + AMAX_OP));
+    CK(tc_pass2(iter_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + AMAX_W, s.amax + AMAX_OP));
   } else {
     a.M = s.What;
     a.m_block_stride = s.fslots * s.mpad;
@@ -1159,11 +1202,14 @@ rff_status iterate(rff_admm_t h, int k) {
     a.per_block = 1;
     CK(launch_pass2_simt(a, s.nslots, s.st));
   }
+  if (s.split_path() && s.stochastic())   // max |O'| over every block, the kept ones included
+    CK(launch_finite_check(s.Op, s.C * s.nslots * s.mpad, 0, reinterpret_cast<int*>(s.amax + AMAX_FLAG), s.st,
+                           s.amax + AMAX_OP));
   if ((r = mark(h, k, 4)) != RFF_OK) return r;
   // exchange, nu update, next loss prox, next V_ij (the tensor-core path reads V^T as a
   // scaled FP16 hi/lo pair), averaging and dual updates
   if ((r = exchange_and_average(h, k)) != RFF_OK) return r;
-  s.launches += s.split_path() ? 8 : 7;
+  s.launches += iter_launches(s);
   return RFF_OK;
 }
 
@@ -1201,6 +1247,10 @@ rff_status enqueue_iterations(rff_admm_t h, int iters, bool copy_old) {
     s.ev.resize((size_t)(base + iters) * 7);
     for (size_t e = old; e < s.ev.size(); ++e) CK(cudaEventCreate(&s.ev[e]));
   }
+  if (s.stochastic() && iters > 0) {   // the masks continue from the iteration count
+    s.bctr_host = s.iters_done;
+    CK(cudaMemcpyAsync(s.bctr, &s.bctr_host, sizeof(int64_t), cudaMemcpyHostToDevice, s.st));
+  }
   for (int k = 0; k < iters; ++k) {
     if (copy_old && k == iters - 1) {
       CK(cudaMemcpyAsync(s.nu_old, s.nu, rowb, cudaMemcpyDeviceToDevice, s.st));
@@ -1215,7 +1265,7 @@ rff_status enqueue_iterations(rff_admm_t h, int iters, bool copy_old) {
     } else {
       if (!s.gexec && (r = capture_iteration(h)) != RFF_OK) return r;
       CK(cudaGraphLaunch(s.gexec, s.st));
-      s.launches += s.outer ? (s.split_path() ? 13 : 9) : (s.split_path() ? 8 : 7);
+      s.launches += iter_launches(s);
     }
     if (r != RFF_OK) return r;
     s.iters_done++;
@@ -1406,6 +1456,18 @@ rff_status rff_admm_estimate_bytes(const rff_admm_params* params, int64_t n, int
   return RFF_OK;
 }
 
+rff_status rff_admm_set_block_fraction(rff_admm_t h, double p) {
+  if (!h) return RFF_EINVAL;
+  h->err.clear();
+  if (!(p > 0.0 && p <= 1.0)) return h->fail(RFF_EINVAL, "block fraction must be in (0, 1]");
+  const double thr = std::floor(p * 16777216.0);
+  if (thr < 1.0) return h->fail(RFF_EINVAL, "block fraction below 2^-24");
+  h->bfrac = p;
+  h->bthr = (uint32_t)thr;
+  h->drop_graph();   // the captured iteration has a different launch sequence
+  return RFF_OK;
+}
+
 rff_status rff_admm_set_lambdas(rff_admm_t h, const double* lambdas, int32_t m) {
   if (!h) return RFF_EINVAL;
   h->err.clear();
@@ -1532,11 +1594,13 @@ struct Piece {
   void* ptr;
   size_t bytes;
 };
-// the iteration's state: O, Obar, nu, the pass-1 operand (V, or on the tensor-core path the
-// FP16 split of V^T with the maxima that scale it), W, Wbar, mu, W'_ij, mu'_ij
+// the iteration's state: O, Obar, nu, O'_ij, the pass-1 operand (V, or on the tensor-core
+// path the FP16 split of V^T with the maxima that scale it), W, Wbar, mu, W'_ij, mu'_ij
+// (O'_ij and W'_ij carry over to the next iteration for the blocks a stochastic iteration
+// leaves out)
 std::vector<Piece> state_pieces(rff_admm_s& s) {
   const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
-  std::vector<Piece> v{{s.O, rowb}, {s.Obar, rowb}, {s.nu, rowb}};
+  std::vector<Piece> v{{s.O, rowb}, {s.Obar, rowb}, {s.nu, rowb}, {s.Op, rowb * s.C}};
   if (s.split_path()) {
     v.push_back({s.VThi, rowb / 2 * s.C});
     v.push_back({s.VTlo, rowb / 2 * s.C});
@@ -1565,7 +1629,7 @@ rff_status rff_admm_get_state(rff_admm_t h, void* buf, size_t* bytes) {
   if (*bytes < need) return h->fail(RFF_EINVAL, "buffer too small");
   StateHeader hd{};
   memcpy(hd.magic, "RFFADMM", 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.p = h->p;
   hd.n = h->n; hd.d = h->d; hd.m = h->m; hd.nslots = h->nslots; hd.fslots = h->fslots;
   hd.R = h->R; hd.C = h->C; hd.iters_done = h->iters_done;
@@ -1592,12 +1656,16 @@ rff_status rff_admm_set_state(rff_admm_t h, const void* buf, size_t bytes) {
   if (bytes != need) return h->fail(RFF_EINVAL, "state size mismatch");
   StateHeader hd;
   memcpy(&hd, buf, sizeof(hd));
-  if (memcmp(hd.magic, "RFFADMM", 8) != 0 || hd.version != 1) return h->fail(RFF_EINVAL, "not a state buffer");
+  if (memcmp(hd.magic, "RFFADMM", 8) != 0 || hd.version != 2) return h->fail(RFF_EINVAL, "not a state buffer");
   if (hd.n != s.n || hd.d != s.d || hd.m != s.m || hd.R != s.R || hd.C != s.C || hd.p.D != s.p.D ||
       hd.p.seed != s.p.seed || hd.p.loss != s.p.loss || hd.p.reg != s.p.reg || hd.p.prec != s.p.prec ||
       hd.p.lambda != s.p.lambda || hd.p.sigma != s.p.sigma || hd.p.rho != s.p.rho ||
       hd.p.rho_scale != s.p.rho_scale)
     return h->fail(RFF_EINVAL, "state was written for other data, parameters or grid");
+  if (!s.factored) {   // the set-up writes scratch into state buffers (the tuning passes): run it first
+    rff_status r = setup_factors(h);
+    if (r != RFF_OK) return r;
+  }
   const char* in = static_cast<const char*>(buf);
   size_t off = sizeof(hd);
   for (auto& pc : pieces) {

@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ descs
 // The per-iteration products x = Q r and r = b - H x: A (M x K) and B (K x N)
 // row-major with K-contiguous A rows, N-contiguous B rows; vector loads when the
 // tile is interior.  Tile 64 x 64, BK = 32.
-__global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict__ descs, float alpha, float beta) {
+__global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict__ descs, float alpha, float beta,
+                                                     const uint8_t* __restrict__ bmask) {
+  if (bmask && !bmask[blockIdx.z]) return;
   const GemmDesc g = descs[blockIdx.z];
   const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
   if (m0 >= g.M || n0 >= g.N) return;
@@ -397,10 +399,10 @@ __global__ void k_add_identity_and_mirror(double* H, int64_t ldh, int64_t s) {
 }  // namespace
 
 cudaError_t launch_gemm_f32_nn(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, float alpha, float beta,
-                               cudaStream_t st) {
+                               cudaStream_t st, const uint8_t* bmask) {
   if (nbatch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(maxM, 64), (unsigned)ceil_div(maxN, 64), (unsigned)nbatch);
-  k_gemm_f32_nn<<<grid, 256, 0, st>>>(descs_dev, alpha, beta);
+  k_gemm_f32_nn<<<grid, 256, 0, st>>>(descs_dev, alpha, beta, bmask);
   return cudaGetLastError();
 }
 

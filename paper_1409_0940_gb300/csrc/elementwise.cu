@@ -441,10 +441,17 @@ __global__ void k_rhs(const float* __restrict__ Wbar, const float* __restrict__ 
 // W'_ij = rhs_ij - Z_ij^T O'_ij from the R partials of the second pass-1 product (outer
 // form of the projection); padding feature slots zero
 __global__ void k_sub_partials(const float* __restrict__ rhs, const float* __restrict__ Rpart, int nsplit, int R,
-                               int64_t nfe, const int32_t* __restrict__ feat_ok, int mpad, float* __restrict__ What) {
+                               int64_t nfe, const int32_t* __restrict__ feat_ok, int mpad, float* __restrict__ What,
+                               const uint8_t* __restrict__ bmask, const int64_t* __restrict__ col_slot, int C) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)R * nfe) return;
   const int64_t e = t % nfe;
+  if (bmask) {   // an inactive block keeps its W'_ij
+    const int64_t slot = e / mpad;
+    int j = 0;
+    while (j + 1 < C && col_slot[j + 1] <= slot) ++j;
+    if (!bmask[(t / nfe) * C + j]) return;
+  }
   if (feat_ok[e / mpad] < 0) {
     What[t] = 0.f;
     return;
@@ -737,8 +744,10 @@ cudaError_t launch_rhs(const float* Wbar, const float* muij, const float* Rpart,
 }
 
 cudaError_t launch_sub_partials(const float* rhs, const float* Rpart, int nsplit, int R, int64_t nfe,
-                                const int32_t* feat_ok, int mpad, float* What, cudaStream_t st) {
-  k_sub_partials<<<nblk((int64_t)R * nfe), 256, 0, st>>>(rhs, Rpart, nsplit, R, nfe, feat_ok, mpad, What);
+                                const int32_t* feat_ok, int mpad, float* What, cudaStream_t st, const uint8_t* bmask,
+                                const int64_t* col_slot, int C) {
+  k_sub_partials<<<nblk((int64_t)R * nfe), 256, 0, st>>>(rhs, Rpart, nsplit, R, nfe, feat_ok, mpad, What, bmask,
+                                                          col_slot, C);
   return cudaGetLastError();
 }
 

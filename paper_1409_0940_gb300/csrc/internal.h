@@ -33,6 +33,7 @@ struct PassArgs {
   int mpad;
   int nsplit;               // pass 1: row splits per row block
   int per_block;            // pass 2: write per column block (1) or once (0)
+  const uint8_t* bmask;     // device, R x C: active blocks of a stochastic iteration, or null
 };
 
 struct ZArgs {
@@ -52,6 +53,10 @@ struct ZArgs {
 
 // philox.cu
 cudaError_t launch_philox_raw(const uint32_t* ctr, uint64_t seed, int64_t n, uint32_t* out, cudaStream_t st);
+// Active blocks of a stochastic iteration: mask[b] = 1 iff (w >> 8) < thr, w the first
+// word of Philox4x32-10 at counter (b, k, 2, 0) under seed, k = *ctr; then *ctr = k + 1
+cudaError_t launch_block_mask(uint64_t seed, uint32_t thr, int nblocks, int64_t* ctr, uint8_t* mask,
+                              cudaStream_t st);
 cudaError_t launch_params_rowmajor(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t nk, float* G,
                                    float* b, cudaStream_t st);
 // Ghi/Glo: the FP16 split of G * gscale; bias_col >= 0: they carry b * gscale in that
@@ -74,9 +79,10 @@ struct GemmDesc {          // D = alpha * op(A) op(B) + beta * Cm, row-major
   int M, N, K;
   int64_t lda, ldb, ldc, ldd;
 };
-// f32 iteration GEMM, NN only, desc array on the device
+// f32 iteration GEMM, NN only, desc array on the device; bmask: descriptor b runs only if
+// bmask[b] != 0 (null: all run)
 cudaError_t launch_gemm_f32_nn(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, float alpha, float beta,
-                               cudaStream_t st);
+                               cudaStream_t st, const uint8_t* bmask = nullptr);
 // f64 with runtime transposes; double_float: FP64 in and out, double-float arithmetic inside
 cudaError_t launch_gemm_f64(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, int transA, int transB,
                             double alpha, double beta, int lower_only, cudaStream_t st, bool double_float = false);
@@ -151,9 +157,11 @@ struct RowEpiArgs {
 cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st);
 cudaError_t launch_rhs(const float* Wbar, const float* muij, const float* Rpart, int nsplit, int R, int64_t nfe,
                        float* rhs, cudaStream_t st, const int32_t* feat_ok = nullptr, int mpad = 0);
-// W' = rhs - sum of the nsplit partials, padding feature slots zero (outer form)
+// W' = rhs - sum of the nsplit partials, padding feature slots zero (outer form); with
+// bmask (R x C, col_slot: first slot of each of the C column blocks) only active blocks
 cudaError_t launch_sub_partials(const float* rhs, const float* Rpart, int nsplit, int R, int64_t nfe,
-                                const int32_t* feat_ok, int mpad, float* What, cudaStream_t st);
+                                const int32_t* feat_ok, int mpad, float* What, cudaStream_t st,
+                                const uint8_t* bmask = nullptr, const int64_t* col_slot = nullptr, int C = 1);
 // dst[c][r] = src[r][c]
 cudaError_t launch_transpose_f32(const float* src, int64_t rows, int64_t cols, float* dst, int64_t dld,
                                  cudaStream_t st);

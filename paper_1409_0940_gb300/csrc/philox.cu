@@ -7,6 +7,8 @@
 //   G[r, k]        counter (k, r/4, 0, 0); words 0,1 -> Box-Muller pair for rows
 //                  4q, 4q+1 (cos, sin); words 2,3 -> rows 4q+2, 4q+3
 //   b[k]           counter (k, 0, 1, 0), word 0
+//   block mask     counter (b, k, 2, 0), word 0: block b = i C + j active in iteration k
+//                  of the stochastic variant iff (w >> 8) < floor(p 2^24)
 //   uniform        ((w >> 8) + 0.5) 2^-24 in float64
 //   G = float32(sqrt(-2 ln u1) {cos,sin}(2 pi u2) / sigma), b = float32(pi u)
 #include "common.cuh"
@@ -92,6 +94,26 @@ __global__ void k_params_slots(uint32_t k0, uint32_t k1, double sigma, int64_t d
     }
   }
   if (q == 0 && bias) bias[p] = ph;
+}
+
+// One CTA: the mask of iteration *ctr, then the counter moves on (so a captured iteration
+// replays with the right k)
+__global__ void k_block_mask(uint32_t k0, uint32_t k1, uint32_t thr, int nb, int64_t* __restrict__ ctr,
+                             uint8_t* __restrict__ mask) {
+  const int64_t k = *ctr;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const U4 w = philox4x32_10(U4{(uint32_t)b, (uint32_t)k, 2u, 0u}, k0, k1);
+    mask[b] = (w.x >> 8) < thr ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ctr = k + 1;
+}
+
+cudaError_t launch_block_mask(uint64_t seed, uint32_t thr, int nblocks, int64_t* ctr, uint8_t* mask,
+                              cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  k_block_mask<<<1, 256, 0, st>>>((uint32_t)seed, (uint32_t)(seed >> 32), thr, nblocks, ctr, mask);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_philox_raw(const uint32_t* ctr, uint64_t seed, int64_t n, uint32_t* out, cudaStream_t st) {

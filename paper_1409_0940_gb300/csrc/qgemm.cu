@@ -52,6 +52,7 @@ struct QArgs {
   float out_scale;
   const unsigned* b_amax;
   unsigned* amax;
+  const uint8_t* bmask;      // active blocks of a stochastic iteration, or null
   int* err;
   long long timeout_cycles;
 };
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   QShared& sh = *reinterpret_cast<QShared*>(base + a.ns * a.stage_bytes);
   const SgJob job = a.jobs[blockIdx.x];
+  if (a.bmask && !a.bmask[job.blk]) return;   // inactive block: its outputs keep their values
   const int nk = job.nk;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const uint32_t bar_full = smem_u32(&sh.full[0]), bar_empty = smem_u32(&sh.empty[0]);
@@ -333,6 +335,7 @@ cudaError_t split_gemm(const SgView& v) {
   a.out_scale = v.out_scale;
   a.b_amax = v.b_amax;
   a.amax = v.amax;
+  a.bmask = v.bmask;
   a.err = tc_error_ptr();
   if (!a.err) return cudaErrorMemoryAllocation;
   a.timeout_cycles = 4000000000LL;   // about two seconds at the boost clock

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(NT) k_pass2_simt(PassArgs p) {
   // row block of this tile: the chain operand W'_ij depends on it
   int rb = 0;
   while (rb + 1 < p.R && p.row_slot[rb + 1] <= a0) ++rb;
+  const uint8_t* act = p.bmask ? p.bmask + rb * p.C : nullptr;   // skip inactive blocks (per_block)
   const float* M = p.M + rb * p.m_block_stride;
   float acc2[4][MQ];
 #pragma unroll
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(NT) k_pass2_simt(PassArgs p) {
 #pragma unroll
     for (int q = 0; q < MQ; ++q) acc2[i][q] = 0.f;
   for (int j = 0; j < p.C; ++j) {
+    if (act && !act[j]) continue;
     const int64_t f0 = p.col_slot[j], f1 = f0 + p.col_size[j];
     for (int64_t b0 = f0; b0 < f1; b0 += BN) {
       tile_z(sm, p.X, p.ldx, a0, p.Gt, p.ldg, b0, p.K, p.bias, false, p.scale, p.row_ok, p.feat_ok);
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(NT) k_pass1_simt(PassArgs p) {
   int j = 0;
   while (j + 1 < p.C && p.col_slot[j + 1] <= a0) ++j;
   if (a0 - p.col_slot[j] >= p.col_size[j]) return;
+  if (p.bmask && !p.bmask[i * p.C + j]) return;   // inactive block: its partials are not read
   const int64_t r0 = p.row_slot[i], nrt = ceil_div(p.row_size[i], BM);
   const int64_t t0 = split * nrt / p.nsplit, t1 = (split + 1) * nrt / p.nsplit;
   const float* M = p.M + j * p.m_block_stride;

@@ -96,6 +96,7 @@ struct TcArgs {
   int64_t out_block_stride;
   int64_t wz_r0, wz_nr, wz_f0, wz_nf, ldo;  // materialisation window
   int bias_in_mma;                          // 1: b already in the product (column of ones)
+  const uint8_t* bmask;                     // passes 1 and 2: active blocks (R x C), or null
   int* err;
   long long timeout_cycles;
 };
@@ -178,19 +179,41 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
     if (a.mode == MODE_PASS2) {
       // persistent over work items (row tile rt, column block j), item = rt C + j: CTA c
       // takes items c, c + G, c + 2G, ... (G = gridDim.x), so the CTAs' loads differ by at
-      // most one item and neighbouring CTAs share row tiles in L2
-      const int64_t nitems = a.nrow_tiles * a.C;
-      for (int64_t it = blockIdx.x; it < nitems && ng < MAXG; it += gridDim.x) {
-        const int64_t arow = (it / a.C) * 128;
-        const int j = (int)(it % a.C);
-        int i = 0;
-        while (i + 1 < a.R && a.row_slot[i + 1] <= arow) ++i;
+      // most one item and neighbouring CTAs share row tiles in L2.  With a block mask the
+      // items of the active blocks alone are numbered, in the same order (row block, row
+      // tile, active column block), and dealt out the same way.
+      auto add_item = [&](int64_t arow, int i, int j) {
         sh.g_b0[ng] = a.col_slot[j];
         sh.g_nt[ng] = (int)ceil_div(a.col_size[j], 128);
         sh.g_out[ng] = a.out + j * a.out_block_stride + arow * a.mpad;
         sh.g_arow[ng] = arow;
         sh.g_my[ng] = i * a.mpad;
         ++ng;
+      };
+      if (!a.bmask) {
+        const int64_t nitems = a.nrow_tiles * a.C;
+        for (int64_t it = blockIdx.x; it < nitems && ng < MAXG; it += gridDim.x) {
+          const int64_t arow = (it / a.C) * 128;
+          const int j = (int)(it % a.C);
+          int i = 0;
+          while (i + 1 < a.R && a.row_slot[i + 1] <= arow) ++i;
+          add_item(arow, i, j);
+        }
+      } else {
+        int64_t q = blockIdx.x, first = 0;   // next item of this CTA; first item of row block i
+        for (int i = 0; i < a.R && ng < MAXG; ++i) {
+          int na = 0;
+          for (int j = 0; j < a.C; ++j) na += a.bmask[i * a.C + j] != 0;
+          const int64_t end = (i + 1 < a.R) ? a.row_slot[i + 1] : a.nrow_tiles * 128;
+          const int64_t cnt = (end - a.row_slot[i]) / 128 * na;
+          for (; q < first + cnt && ng < MAXG; q += gridDim.x) {
+            const int64_t local = q - first;
+            int jj = (int)(local % na), j = 0;
+            while (!a.bmask[i * a.C + j] || jj-- > 0) ++j;   // the jj-th active column block
+            add_item(a.row_slot[i] + (local / na) * 128, i, j);
+          }
+          first += cnt;
+        }
       }
       if (ng > 0) {
         a_row0 = sh.g_arow[0];
@@ -220,7 +243,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
       const int64_t nrt = ceil_div(a.row_size[i], 128);
       const int64_t t0 = split * nrt / a.nsplit, t1 = (split + 1) * nrt / a.nsplit;
       m_y = j * a.mpad;
-      if (a_row0 - a.col_slot[j] < a.col_size[j] && t1 > t0) {
+      const bool active = !a.bmask || a.bmask[i * a.C + j];
+      if (active && a_row0 - a.col_slot[j] < a.col_size[j] && t1 > t0) {
         sh.g_b0[0] = a.row_slot[i] + t0 * 128;
         sh.g_nt[0] = (int)(t1 - t0);
         sh.g_out[0] = a.out + ((int64_t)split * a.R + i) * a.out_block_stride + a_row0 * a.mpad;
@@ -744,6 +768,7 @@ cudaError_t tc_pass1(const TcView& v, float* Rpart) {
   a.out = Rpart;
   a.out_block_stride = v.fslots * v.mpad;
   a.m_amax = v.v_amax;
+  a.bmask = v.bmask;
   if ((e = make_map(&a.tA_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tB_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
@@ -768,6 +793,7 @@ cudaError_t tc_pass2(const TcView& v, const __half* Mhi, const __half* Mlo, int6
   a.out_block_stride = v.nslots * v.mpad;
   a.m_amax = m_amax;
   a.out_amax = out_amax;
+  a.bmask = v.bmask;
   a.nrow_tiles = v.nslots / 128;
   if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;

@@ -25,6 +25,7 @@ struct TcView {
   int bias_in_mma;                  // 1: b is column d of G and X carries ones there
   int kc;                           // ring K chunk (64 or 32; 0 = library default)
   int zt;                           // 1: Z tile in tensor memory, 0: in shared memory
+  const uint8_t* bmask;             // device, R x C: active blocks of a stochastic iteration, or null
   cudaStream_t st;
 };
 
@@ -53,7 +54,8 @@ cudaError_t tc_predict(const TcView& v, const __half* Xh, const __half* Xl, int6
 // amax, when given, receives max |out| (atomicMax of float bits).  A is a_rows x a_cols
 // (row-major), B b_rows x b_cols; every job's K range and rows lie inside them.
 struct SgJob {
-  int32_t a_row, a_k0, b_row, b_k0, nk, pad_;
+  int32_t a_row, a_k0, b_row, b_k0, nk;
+  int32_t blk;   // block i C + j the job belongs to (skipped when bmask[blk] == 0)
   int64_t out;
 };
 struct SgView {
@@ -70,6 +72,7 @@ struct SgView {
   unsigned* amax;
   size_t smem_budget;                  // ring bytes per CTA (0 = the largest; smaller lets 2 CTAs share an SM)
   int two_acc;                         // 1: hi.hi products in their own TMEM accumulator (twice the columns)
+  const uint8_t* bmask;                // device, R x C: a job of an inactive block does nothing; or null
   cudaStream_t st;
 };
 cudaError_t split_gemm(const SgView& v);
