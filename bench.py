@@ -12,7 +12,11 @@ done before the timed region.  Every input of the timed region (X split,
 V_ij, W'_ij, the factors) is larger than the 129 MB L2, so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split_bf16|fp32|cached_z]
+                  [--loss squared|hinge|multinomial|crammer_singer|l1] [--block-fraction P]
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
+
+--loss swaps the loss of the same workload; --block-fraction P < 1 runs the stochastic
+variant (each block takes part in an iteration's graph projection with probability P).
 
 One JSON line on rank 0.  With N > 1 (torchrun), each rank solves its own
 replica of the workload (the method keeps every block on one GPU) and the value
@@ -153,12 +157,38 @@ def job_throughput(steps, world, ms):
     return steps * world / (ms * 1e-3)
 
 
+def new_solver(rff, w, prec, stream):
+    s = rff.Solver(stream=stream.cuda_stream, **solver_kw(w, prec))
+    if w.get("block_fraction", 1.0) < 1.0:
+        s.set_block_fraction(w["block_fraction"])
+    return s
+
+
+def active_fraction(rff, w, k0, k1):
+    """Fraction of blocks active over iterations [k0, k1) of the stochastic variant: the
+    library's own Philox words at counters (block, k, 2, 0), thresholded as the solver does."""
+    import numpy as np
+    import torch
+    p = w.get("block_fraction", 1.0)
+    if p >= 1.0:
+        return 1.0
+    nb = w["R"] * w["C"]
+    k = np.repeat(np.arange(k0, k1, dtype=np.uint32), nb)
+    b = np.tile(np.arange(nb, dtype=np.uint32), k1 - k0)
+    ctr = np.stack([b, k, np.full_like(b, 2), np.zeros_like(b)], axis=1)
+    dctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    out = torch.zeros_like(dctr)
+    rff.rff_philox4x32_10(dctr, w["philox_seed"], out)
+    w0 = out.cpu().numpy().view(np.uint32)[:, 0]
+    return float(np.mean((w0 >> 8) < np.uint32(int(np.floor(p * 2.0 ** 24)))))
+
+
 def measure(rff, w, X, Y, prec, steps, warmup, stream):
     """warmup untimed iterations (the first call also builds the factors), then steps
     iterations timed with CUDA events on the solver's stream; returns the device ms,
     the phase profile, the consensus weights and the clock record."""
     import torch
-    s = rff.Solver(stream=stream.cuda_stream, **solver_kw(w, prec))
+    s = new_solver(rff, w, prec, stream)
     s.set_data(X, Y)
     s.solve(warmup, stats=False)
     s.profiling(True)
@@ -182,10 +212,7 @@ def run_ours(args, rank, world):
 
     import paper_1409_0940_gb300 as rff
 
-    w = dict(WORKLOAD)
-    if args.n:
-        w["n"] = args.n
-        w["name"] = w["name"].replace("200k", "%dk" % (args.n // 1000))
+    w = workload(args)
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     X, Y = make_data(w)
     stream = torch.cuda.Stream()
@@ -203,7 +230,7 @@ def run_ours(args, rank, world):
     e2e = None
     if not args.no_e2e:
         t0 = time.perf_counter()
-        s2 = rff.Solver(stream=stream.cuda_stream, **solver_kw(w, args.prec))
+        s2 = new_solver(rff, w, args.prec, stream)
         s2.set_data(X, Y)
         s2.solve(args.steps, stats=False)
         Wh = s2.weights()
@@ -235,6 +262,9 @@ def run_ours(args, rank, world):
         compare["iterations"] = args.warmup + args.steps
 
     useful, exec_pass = flops_per_iter(w, args.prec)
+    # the stochastic variant's passes do the work of its active blocks alone
+    act = active_fraction(rff, w, args.warmup, args.warmup + args.steps)
+    exec_pass *= act
     hbm, bf16, bf16_sus, src = peaks()
     # dominant kernel: the larger of the two fused passes
     ph = "ms_pass2" if prof["ms_pass2"] >= prof["ms_pass1"] else "ms_pass1"
@@ -244,14 +274,14 @@ def run_ours(args, rank, world):
         # DRAM bytes per launch from an ncu capture of the current k_regen_tc at n = 100k, scaled
         # to the 200k-row workload by rows (profiles/k_regen_tc_multiclass_100k.md); None while
         # the kernel has changed since the last capture
-        traffic = TRAFFIC_200K.get(ph[3:]) if not args.n else None
+        traffic = TRAFFIC_200K.get(ph[3:]) if not args.n and act == 1.0 else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sus, "unit": "TFLOP/s",
                 "frac": achieved / bf16_sus, "traffic": traffic, "kernel": ph[3:],
                 "peak_source": src + " sustained bf16"}
     elif args.prec == "cached_z":
         # the streamed pass reads Z once: HBM-bound (the tensor work, 3 x 2 n D m_pad, would take
         # slightly less time at the sustained BF16 peak)
-        gbs = bytes_per_cached_pass(w) / (per_launch_ms * 1e-3) / 1e9
+        gbs = bytes_per_cached_pass(w) * act / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
                 "kernel": ph[3:], "peak_source": src + " copy bandwidth", "tensor_tflops": achieved,
                 "tensor_frac": achieved / bf16_sus}
@@ -270,6 +300,7 @@ def run_ours(args, rank, world):
         "config": {"workload": w["name"], "n": w["n"], "d": w["d"], "m": w["m"], "D": w["D"],
                    "grid": "%dx%d" % (w["R"], w["C"]), "sigma": w["sigma"], "loss": w["loss"], "reg": w["reg"],
                    "lambda": w["lam"], "rho": w["rho"], "prec": args.prec, "parallelism": "replicas",
+                   "block_fraction": w["block_fraction"], "active_fraction": act,
                    "l2": "inputs larger than L2 (X split 358 MB, V 512 MB, factors 2.1 GB)"},
         "e2e": e2e,
         "gpu_launches": int(prof["launches"]),
@@ -284,23 +315,37 @@ def run_ours(args, rank, world):
     return line
 
 
-def oracle_iter_seconds(n_sample, iters):
+def workload(args):
+    """The benchmark workload with the command line's row count, loss and block fraction."""
+    w = dict(WORKLOAD)
+    if args.n:
+        w["n"] = args.n
+        w["name"] = w["name"].replace("200k", "%dk" % (args.n // 1000))
+    w["loss"] = args.loss
+    w["block_fraction"] = args.block_fraction
+    if args.loss != "squared":
+        w["name"] += "-" + args.loss
+    if args.block_fraction < 1.0:
+        w["name"] += "-p%g" % args.block_fraction
+    return w
+
+
+def oracle_iter_seconds(w, n_sample, iters):
     """Seconds per iteration of the FP64 oracle on an n_sample-row slice of the workload
-    (same d, D, m, grid; set-up excluded)."""
+    (same d, D, m, grid, loss and block fraction; set-up excluded)."""
     from oracle import admm
-    w = WORKLOAD
     X, Y = make_data(w, n=n_sample)
     p = admm.Problem(X, Y, w["loss"], w["reg"], w["lam"], w["sigma"], w["rho"], w["D"], w["R"], w["C"],
                      w["philox_seed"])
     admm.admm(p, 1)                       # builds Z and the cached factors (untimed)
     t0 = time.perf_counter()
-    admm.admm(p, iters)
+    admm.admm(p, iters, block_fraction=w["block_fraction"])
     return (time.perf_counter() - t0) / iters
 
 
 def cpu_baseline(args, n_sample=8000, iters=3):
-    w = WORKLOAD
-    sec = oracle_iter_seconds(n_sample, iters)
+    w = workload(args)
+    sec = oracle_iter_seconds(w, n_sample, iters)
     scale = w["n"] / n_sample
     return {"value": 1.0 / (sec * scale), "unit": "iter/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": "%d of %d rows (same d, D, m, 4x4 grid), %d iterations timed, set-up excluded, "
@@ -314,7 +359,7 @@ def run_reference(args, rank, world):
     return {"metric": METRIC, "value": cb["value"], "unit": "iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD["name"], "prec": "f64 oracle (explicit Z)"},
+            "config": {"workload": workload(args)["name"], "prec": "f64 oracle (explicit Z)"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -501,6 +546,10 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the other precisions (profiling runs)")
     ap.add_argument("--n", type=int, default=0, help="rows of a reduced workload (profiling runs)")
     ap.add_argument("--workload", default="multiclass", choices=["multiclass", "ridge", "sweep", "serve"])
+    ap.add_argument("--loss", default="squared", choices=["squared", "hinge", "multinomial", "crammer_singer", "l1"],
+                    help="loss of the multiclass workload")
+    ap.add_argument("--block-fraction", type=float, default=1.0,
+                    help="stochastic variant: probability that a block takes part in an iteration")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
