@@ -133,14 +133,17 @@ class Problem:
     """Data and parameters of one solve (Sec. 1, eq. (basicproblem); Sec. 3 grid)."""
 
     def __init__(self, X, Y, loss="squared", reg="l2", lam=1e-4, sigma=1.0, rho=1.0,
-                 D=512, R=1, C=1, seed=0, rho_scale="sum"):
+                 D=512, R=1, C=1, seed=0, rho_scale="sum", feature_map="fourier"):
         self.X = np.asarray(X, dtype=np.float64)
         Y = np.asarray(Y, dtype=np.float64)
         self.Y = Y.reshape(Y.shape[0], -1)
         self.n, self.d = self.X.shape
         self.m = self.Y.shape[1]
-        if loss not in P.LOSSES or reg not in P.REGS:
-            raise ValueError("unknown loss/regulariser")
+        if loss not in P.LOSSES or reg not in P.REGS or feature_map not in rff.MAPS:
+            raise ValueError("unknown loss/regulariser/feature map")
+        if feature_map == "laplace" and (self.X < 0).any():
+            raise ValueError("random Laplace features take nonnegative inputs")
+        self.feature_map = feature_map
         self.loss, self.reg = loss, reg
         self.lam, self.sigma, self.rho = float(lam), float(sigma), float(rho)
         self.D, self.R, self.C, self.seed = int(D), int(R), int(C), int(seed)
@@ -159,7 +162,7 @@ class Problem:
     def Z(self):
         """The explicit feature matrix, computed once (the oracle stores it)."""
         if self._Z is None:
-            self._Z = rff.features_block(self.X, self.seed, self.sigma, self.D, 0, self.D)
+            self._Z = rff.features_block(self.X, self.seed, self.sigma, self.D, 0, self.D, self.feature_map)
         return self._Z
 
     def solvers(self):
@@ -179,7 +182,8 @@ class Problem:
 
     def predict(self, Xq, W):
         """Scores f(x) = W^T z(x) for the rows of Xq."""
-        Zq = rff.features_block(np.asarray(Xq, dtype=np.float64), self.seed, self.sigma, self.D, 0, self.D)
+        Zq = rff.features_block(np.asarray(Xq, dtype=np.float64), self.seed, self.sigma, self.D, 0, self.D,
+                                self.feature_map)
         return Zq @ W
 
 

@@ -92,6 +92,32 @@ def g_words(seed, d, k_lo, k_hi):
     return np.stack(philox4x32_10(kk, qq, 0, 0, k0, k1))
 
 
+def _gauss(seed, d, k_lo, k_hi):
+    """The float64 standard normals behind G[:, k_lo:k_hi], shape (d, k_hi-k_lo)."""
+    w = g_words(seed, d, k_lo, k_hi)                     # (4, nq, nk)
+    u = uniform_from_word(w)
+    a0, a1 = box_muller(u[0], u[1])                      # rows 4q, 4q+1
+    a2, a3 = box_muller(u[2], u[3])                      # rows 4q+2, 4q+3
+    nq, nk = u.shape[1], u.shape[2]
+    z = np.empty((nq, 4, nk), dtype=np.float64)
+    z[:, 0], z[:, 1], z[:, 2], z[:, 3] = a0, a1, a2, a3
+    return z.reshape(4 * nq, nk)[:d]
+
+
+def laplace_params(seed, sigma, d, D, k_lo=0, k_hi=None):
+    """Random Laplace feature parameters for global features k_lo..k_hi-1.
+
+    W float32 (d, k_hi-k_lo), W[r, k] = 1 / (2 sigma^2 g^2) with g the standard normal
+    the Fourier map would use for G[r, k]: a Levy(0, c) draw with c = 1 / (2 sigma^2)
+    (c / g^2 is Levy-distributed), whose Laplace transform is E[exp(-t W)] =
+    exp(-sqrt(2 c t)) = exp(-sqrt(t) / sigma).
+    """
+    if k_hi is None:
+        k_hi = D
+    g = _gauss(seed, d, k_lo, k_hi)
+    return (1.0 / (2.0 * float(sigma) * float(sigma) * g * g)).astype(np.float32)
+
+
 def rff_params(seed, sigma, d, D, k_lo=0, k_hi=None):
     """Random Fourier feature parameters for global features k_lo..k_hi-1.
 
@@ -102,15 +128,7 @@ def rff_params(seed, sigma, d, D, k_lo=0, k_hi=None):
     """
     if k_hi is None:
         k_hi = D
-    w = g_words(seed, d, k_lo, k_hi)                     # (4, nq, nk)
-    u = uniform_from_word(w)
-    a0, a1 = box_muller(u[0], u[1])                      # rows 4q, 4q+1
-    a2, a3 = box_muller(u[2], u[3])                      # rows 4q+2, 4q+3
-    nq, nk = u.shape[1], u.shape[2]
-    z = np.empty((nq, 4, nk), dtype=np.float64)
-    z[:, 0], z[:, 1], z[:, 2], z[:, 3] = a0, a1, a2, a3
-    z = z.reshape(4 * nq, nk)[:d]
-    G = (z / float(sigma)).astype(np.float32)
+    G = (_gauss(seed, d, k_lo, k_hi) / float(sigma)).astype(np.float32)
     k0, k1 = seed_key(seed)
     kk = np.arange(k_lo, k_hi, dtype=np.uint64)
     wb = philox4x32_10(kk, 0, 1, 0, k0, k1)[0]

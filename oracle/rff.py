@@ -19,10 +19,20 @@ Sec. 3 (partition): n = sum n_i over R row blocks, s = sum s_j over C column
 blocks; sizes may be uneven.  Reading: the leading (n mod R) blocks get one
 extra row, likewise for features, and blocks are contiguous ranges.
 
+Random Laplace features (Sec. 4 lists them among the solver's other maps; Yang,
+Sindhwani, Fan, Avron and Mahoney 2014): for nonnegative inputs (histograms),
+z(x) = exp(-W^T x) / sqrt(D) with W[r, k] i.i.d. Levy(0, 1/(2 sigma^2)), whose
+inner products estimate the exponential semigroup kernel
+k(x, x') = exp(-sum_r sqrt(x_r + x'_r) / sigma).  Same operator T[X_i, j] and
+block structure; only the nonlinearity and the parameter law change.
+
 Pins: Z Z^T against the Gaussian kernel within a Hoeffding bound; the slope of
 the mean kernel error against D; Z block (C = 16) == columns of Z (C = 1),
-bitwise; partition sizes against their definition.
+bitwise; partition sizes against their definition; the Laplace map against the
+semigroup kernel within a Hoeffding bound, its parameters against the Levy CDF.
 """
+
+MAPS = ("fourier", "laplace")
 import numpy as np
 
 from . import philox
@@ -44,10 +54,27 @@ def features(X, G, b, D):
     return np.sqrt(2.0 / D) * np.cos(A)
 
 
-def features_block(X, seed, sigma, D, k_lo, k_hi):
+def laplace_features(X, W, D):
+    """Z = exp(-X W) / sqrt(D) in float64."""
+    A = np.asarray(X, dtype=np.float64) @ np.asarray(W, dtype=np.float64)
+    return np.exp(-A) / np.sqrt(D)
+
+
+def features_block(X, seed, sigma, D, k_lo, k_hi, feature_map="fourier"):
     """Z restricted to global features k_lo..k_hi-1 (the operator T[X_i, j])."""
+    if feature_map == "laplace":
+        return laplace_features(X, philox.laplace_params(seed, sigma, X.shape[1], D, k_lo, k_hi), D)
+    if feature_map != "fourier":
+        raise ValueError(feature_map)
     G, b = philox.rff_params(seed, sigma, X.shape[1], D, k_lo, k_hi)
     return features(X, G, b, D)
+
+
+def semigroup_kernel(X1, X2, sigma):
+    """k(x, x') = exp(-sum_r sqrt(x_r + x'_r) / sigma) for nonnegative x, x'."""
+    X1 = np.asarray(X1, dtype=np.float64)
+    X2 = np.asarray(X2, dtype=np.float64)
+    return np.exp(-np.sqrt(X1[:, None, :] + X2[None, :, :]).sum(-1) / sigma)
 
 
 def gaussian_kernel(X1, X2, sigma):

@@ -21,6 +21,11 @@ in for them with matching shapes and value ranges (Sec. 5, "Datasets"):
                   template entries with probability 0.57 and jitters them;
                   +-1 one-hot targets.
 * ``binary``      two Gaussians N(+-mu, I), mu ~ 2 N(0, I/d), labels +-1.
+* ``histograms``  bag-of-words style histograms for the random Laplace map
+                  (nonnegative rows summing to 1): each class draws a Dirichlet
+                  weight over the d bins with most mass on a random 20% of them;
+                  a row is a normalised Gamma draw around its class weights
+                  (concentration 50); +-1 one-hot targets.
 """
 import numpy as np
 
@@ -79,3 +84,14 @@ def binary(n=10_000, d=128, seed=0):
     y = np.where(rng.random(n) < 0.5, 1.0, -1.0)
     X = y[:, None] * mu[None, :] + rng.standard_normal((n, d))
     return X.astype(np.float32), y.reshape(n, 1).astype(np.float32)
+
+
+def histograms(n=20_000, d=256, m=10, seed=0):
+    rng = _rng(seed)
+    boost = np.where(rng.random((m, d)) < 0.2, 5.0, 0.2)
+    weights = rng.dirichlet(np.ones(d), size=m) * boost
+    weights /= weights.sum(axis=1, keepdims=True)
+    labels = rng.integers(0, m, size=n)
+    X = rng.gamma(50.0 * weights[labels] + 1e-3)
+    X /= X.sum(axis=1, keepdims=True)
+    return X.astype(np.float32), onehot_pm1(labels, m)
