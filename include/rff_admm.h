@@ -96,6 +96,16 @@ typedef enum {
  * rho_mean = rho_sum / n. */
 typedef enum { RFF_RHO_SUM = 0, RFF_RHO_MEAN = 1 } rff_rho_scale;
 
+/* The feature map z(.) behind the operator T[X_i, j] (Sec. 4: the solver treats it as a
+ * black box; the paper lists random Fourier features and, among others, random Laplace
+ * features).  Both are drawn from the same Philox stream of standard normals g:
+ *   RFF_MAP_FOURIER  z(x) = sqrt(2/D) cos(G^T x + b), G = g / sigma, b ~ U[0, pi):
+ *                    the Gaussian kernel exp(-|x - x'|^2 / (2 sigma^2))
+ *   RFF_MAP_LAPLACE  z(x) = exp(-W^T x) / sqrt(D), W = 1 / (2 sigma^2 g^2) (Levy): the
+ *                    exponential semigroup kernel exp(-sum_r sqrt(x_r + x'_r) / sigma) on
+ *                    nonnegative inputs (histograms); FP32 and cached-Z precisions only */
+typedef enum { RFF_MAP_FOURIER = 0, RFF_MAP_LAPLACE = 1 } rff_feature_map;
+
 typedef struct {
   int32_t loss;      /* rff_loss                                                     */
   int32_t reg;       /* rff_reg                                                      */
@@ -110,6 +120,7 @@ typedef struct {
   int32_t m;         /* outputs per example, 1 <= m <= 256                            */
   int32_t rho_scale; /* rff_rho_scale                                                */
   int32_t newton_iters; /* Newton steps of the logistic / multinomial prox (0 = 8) */
+  int32_t feature_map;  /* rff_feature_map (0: random Fourier features)              */
 } rff_admm_params;
 
 typedef struct {
@@ -311,6 +322,16 @@ rff_status rff_prox_loss(int32_t loss, const float* V, const float* Y, int64_t n
 
 /* Entry-wise regulariser prox: out = argmin_w 1/2 |w - v|^2 + tau r(w).  n values. */
 rff_status rff_prox_reg(int32_t reg, const float* V, int64_t n, double tau, float* out, void* stream);
+
+/* The random Laplace map's parameters W (d x (k_hi - k_lo), row-major, device) for
+ * global features k_lo..k_hi-1, from the same counters as rff_rff_params' G. */
+rff_status rff_laplace_params(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t k_hi, float* W,
+                              void* stream);
+
+/* Z = exp(-X W) / sqrt(D) for global features k_lo..k_hi-1 (FP32), X n x d nonnegative,
+ * Z n x (k_hi - k_lo); device pointers.  Errors: RFF_EINVAL for a negative or non-finite x. */
+rff_status rff_laplace_features(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma, int64_t D,
+                                int64_t k_lo, int64_t k_hi, float* Z, void* stream);
 
 /* Batched Cholesky factorisation in FP64 of `batch` SPD matrices (eq. (cache)):
  * A: batch x s x s row-major float64, overwritten by the lower factor L (upper

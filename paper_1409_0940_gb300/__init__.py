@@ -19,6 +19,7 @@ RFF_OK, RFF_EINVAL, RFF_ENOMEM, RFF_ECUDA, RFF_ETIMEOUT, RFF_ENOTREADY, RFF_ENUM
 _STATUS = {0: "RFF_OK", 1: "RFF_EINVAL", 2: "RFF_ENOMEM", 3: "RFF_ECUDA", 4: "RFF_ETIMEOUT",
            5: "RFF_ENOTREADY", 6: "RFF_ENUMERIC"}
 LOSSES = {"squared": 0, "hinge": 1, "logistic": 2, "multinomial": 3, "l1": 4, "crammer_singer": 5}
+FEATURE_MAPS = {"fourier": 0, "laplace": 1}
 REGS = {"l2": 0, "l1": 1}
 PRECS = {"fp32": 0, "split_bf16": 1, "cached_z": 2}
 RHO_SCALES = {"sum": 0, "mean": 1}
@@ -35,7 +36,7 @@ class rff_admm_params(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("rho", ctypes.c_double), ("D", ctypes.c_int64),
                 ("R", ctypes.c_int32), ("C", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("prec", ctypes.c_int32), ("m", ctypes.c_int32), ("rho_scale", ctypes.c_int32),
-                ("newton_iters", ctypes.c_int32)]
+                ("newton_iters", ctypes.c_int32), ("feature_map", ctypes.c_int32)]
 
 
 class rff_admm_stats(ctypes.Structure):
@@ -86,6 +87,8 @@ PROTOTYPES = {
     "rff_philox4x32_10": (_I32, [_P, _U64, _I64, _P, _P]),
     "rff_rff_params": (_I32, [_U64, _D, _I64, _I64, _I64, _P, _P, _P]),
     "rff_features": (_I32, [_P, _I64, _I64, _U64, _D, _I64, _I64, _I64, _I32, _P, _P]),
+    "rff_laplace_params": (_I32, [_U64, _D, _I64, _I64, _I64, _P, _P]),
+    "rff_laplace_features": (_I32, [_P, _I64, _I64, _U64, _D, _I64, _I64, _I64, _P, _P]),
     "rff_prox_loss": (_I32, [_I32, _P, _P, _I64, _I32, _D, _I32, _P, _P]),
     "rff_prox_reg": (_I32, [_I32, _P, _I64, _D, _P, _P]),
     "rff_cholesky_f64": (_I32, [_P, _I32, _I32, _P, _P]),
@@ -158,9 +161,9 @@ def _stream(stream):
 
 
 def make_params(loss="squared", reg="l2", lam=1e-4, sigma=1.0, rho=1.0, D=512, R=1, C=1, seed=0,
-                prec="fp32", m=1, rho_scale="sum", newton_iters=0):
+                prec="fp32", m=1, rho_scale="sum", newton_iters=0, feature_map="fourier"):
     return rff_admm_params(LOSSES[loss], REGS[reg], lam, sigma, rho, D, R, C, seed, PRECS[prec], m,
-                           RHO_SCALES[rho_scale], newton_iters)
+                           RHO_SCALES[rho_scale], newton_iters, FEATURE_MAPS[feature_map])
 
 
 # ----------------------------------------------------------------- C ABI, same names
@@ -304,6 +307,20 @@ def rff_features(X, seed, sigma, D, k_lo, k_hi, prec, Z, stream=None):
     pz, _ = _ptr(Z)
     _check(lib.rff_features(px, X.shape[0], X.shape[1], seed, sigma, D, k_lo, k_hi, PRECS.get(prec, prec), pz,
                             _stream(stream)), None, "rff_features")
+    return Z
+
+
+def rff_laplace_params(seed, sigma, d, k_lo, k_hi, W, stream=None):
+    pw, _ = _ptr(W)
+    _check(lib.rff_laplace_params(seed, sigma, d, k_lo, k_hi, pw, _stream(stream)), None, "rff_laplace_params")
+    return W
+
+
+def rff_laplace_features(X, seed, sigma, D, k_lo, k_hi, Z, stream=None):
+    px, _ = _ptr(X)
+    pz, _ = _ptr(Z)
+    _check(lib.rff_laplace_features(px, X.shape[0], X.shape[1], seed, sigma, D, k_lo, k_hi, pz, _stream(stream)),
+           None, "rff_laplace_features")
     return Z
 
 

@@ -137,6 +137,12 @@ struct rff_admm_s {
   }
   // the split path: tensor-core kernels and BF16 operand copies (cached-Z uses them too)
   bool split_path() const { return p.prec == RFF_PREC_SPLIT_BF16 || p.prec == RFF_PREC_CACHED_Z; }
+  // scoring forms X.G on the tensor cores (split path, random Fourier map)
+  bool tc_scores() const { return split_path() && p.feature_map == RFF_MAP_FOURIER; }
+  // the feature map's scale: max |z| (sqrt(2/D) for cos, 1/sqrt(D) for exp(-T) with T >= 0)
+  float zmap_scale() const {
+    return (float)(p.feature_map == RFF_MAP_LAPLACE ? 1.0 / std::sqrt((double)D) : std::sqrt(2.0 / (double)D));
+  }
   bool cached_z() const { return p.prec == RFF_PREC_CACHED_Z; }
 };
 
@@ -168,7 +174,7 @@ float g_scale(double sigma) { return pow2_scale(std::max(5.9 / sigma, 3.1415927)
 // Queries go through the same FP16 scaling as the training rows: |x| xscale must stay
 // below 2^15 (queries up to 2^7 times the largest training |x|).
 rff_status check_query_range(rff_admm_t h, int maxbits) {
-  if (!h->split_path()) return RFF_OK;
+  if (!h->tc_scores()) return RFF_OK;
   float qmax = 0.f;
   memcpy(&qmax, &maxbits, 4);
   if ((double)qmax * h->xscale < 32768.0) return RFF_OK;
@@ -191,6 +197,12 @@ rff_status check_params(const rff_admm_params* p, std::string& why) {
   if (p->m < 1 || p->m > 256) { why = "m must be in [1, 256]"; return RFF_EINVAL; }
   if (p->newton_iters < 0 || p->newton_iters > 100) { why = "newton_iters out of range"; return RFF_EINVAL; }
   if (p->prec != RFF_PREC_FP32 && p->C > 64) { why = "the split-BF16 and cached-Z paths support C <= 64"; return RFF_EINVAL; }
+  if (p->feature_map < 0 || p->feature_map > 1) { why = "unknown feature map"; return RFF_EINVAL; }
+  if (p->feature_map == RFF_MAP_LAPLACE && p->prec == RFF_PREC_SPLIT_BF16) {
+    // W is Levy-distributed: its range spans far more than the FP16 split's 2^29
+    why = "the random Laplace map runs on the FP32 and cached-Z precisions";
+    return RFF_EINVAL;
+  }
   return RFF_OK;
 }
 
@@ -583,7 +595,8 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   CK(cudaMemcpyAsync(sx, X, xb, kind, s.st));
   CK(cudaMemcpyAsync(sy, Yin, yb, kind, s.st));
   CK(cudaMemsetAsync(s.flag, 0, 16, s.st));
-  CK(launch_finite_check(sx, (int64_t)n * d, 0, s.flag, s.st, reinterpret_cast<unsigned*>(s.flag + 2)));
+  CK(launch_finite_check(sx, (int64_t)n * d, s.p.feature_map == RFF_MAP_LAPLACE ? 2 : 0, s.flag, s.st,
+                         reinterpret_cast<unsigned*>(s.flag + 2)));
   const int pm1 = (s.p.loss == RFF_LOSS_HINGE || s.p.loss == RFF_LOSS_LOGISTIC) ? 1 : 0;
   CK(launch_finite_check(sy, (int64_t)n * s.m, pm1, s.flag + 1, s.st));
   int fl[3] = {0, 0, 0};
@@ -595,7 +608,8 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
     s.xscale = pow2_scale(std::max<double>(xmax, s.bias_col >= 0 ? 1.0 : 0.0));
     s.gscale = g_scale(s.p.sigma);
   }
-  if (fl[0]) { h->free_all(); return h->fail(RFF_EINVAL, "X contains NaN or Inf"); }
+  if (fl[0] & 1) { h->free_all(); return h->fail(RFF_EINVAL, "X contains NaN or Inf"); }
+  if (fl[0] & 4) { h->free_all(); return h->fail(RFF_EINVAL, "the random Laplace map takes nonnegative X"); }
   if (fl[1] & 1) { h->free_all(); return h->fail(RFF_EINVAL, "Y contains NaN or Inf"); }
   if (fl[1] & 2) { h->free_all(); return h->fail(RFF_EINVAL, "hinge/logistic targets must be -1 or +1"); }
 
@@ -722,11 +736,11 @@ rff_status materialise_z(rff_admm_t h) {
   rff_status rs = ensure_scratch(h, (size_t)chunk * s.fslots * 4);
   if (rs != RFF_OK) return rs;
   float* zc = static_cast<float*>(s.scratch.p);
-  s.zscale = pow2_scale(std::sqrt(2.0 / (double)s.D));   // |Z| <= sqrt(2/D)
+  s.zscale = pow2_scale(s.zmap_scale());   // |Z| <= sqrt(2/D) (cos) or 1/sqrt(D) (exp(-T))
   for (int64_t r0 = 0; r0 < s.nslots; r0 += chunk) {
     const int64_t nr = std::min(chunk, s.nslots - r0);
-    ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, (float)std::sqrt(2.0 / (double)s.D), s.row_of_slot,
-             s.feat_of_slot, r0, nr, 0, s.fslots, zc, s.fslots};
+    ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, s.zmap_scale(), s.row_of_slot,
+             s.feat_of_slot, r0, nr, 0, s.fslots, zc, s.fslots, s.p.feature_map};
     CK(launch_write_z_simt(za, s.st));
     CK(launch_split_f16(zc, nr * s.fslots, s.zscale, s.Zhi + r0 * s.fslots, s.Zlo + r0 * s.fslots, s.st));
     CK(launch_transpose_split_f16(zc, nr, (int)s.fslots, 1, 0, s.ZThi + r0, s.ZTlo + r0, s.nslots, 0, s.zscale,
@@ -777,10 +791,12 @@ rff_status materialise_z(rff_admm_t h) {
 
 rff_status setup_factors(rff_admm_t h) {
   auto& s = *h;
-  const float scale = (float)std::sqrt(2.0 / (double)s.D);
-  // random features: G and b from Philox (Sec. 4)
-  CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, s.Ghi, s.Glo, s.gscale, s.bias,
-                         s.bias_col, s.st));
+  const float scale = s.zmap_scale();
+  // random features: G and b (or the Laplace map's W) from Philox (Sec. 4); the FP16 copies
+  // only where the tensor cores form X.G
+  const bool g16 = s.tc_scores();
+  CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, g16 ? s.Ghi : nullptr,
+                         g16 ? s.Glo : nullptr, s.gscale, s.bias, s.bias_col, s.st, s.p.feature_map));
   // Gram matrices H_ij = I + Z_ij^T Z_ij (eq. (cache)), or I + Z_ij Z_ij^T in the outer
   // form, in FP64, batched by memory
   int64_t smax = 0;
@@ -834,7 +850,7 @@ rff_status setup_factors(rff_admm_t h) {
           CK(tc_write_z(tc_view(s), s.row_slot[i], ni, s.col_slot[j] + f0, nf, Zc, nf));
         } else {
           ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, scale, s.row_of_slot, s.feat_of_slot,
-                   s.row_slot[i], ni, s.col_slot[j] + f0, nf, Zc, nf};
+                   s.row_slot[i], ni, s.col_slot[j] + f0, nf, Zc, nf, s.p.feature_map};
           CK(launch_write_z_simt(za, s.st));
         }
         CK(launch_transpose_f32(Zc, ni, nf, Zt, ni, s.st));
@@ -846,7 +862,7 @@ rff_status setup_factors(rff_admm_t h) {
           CK(tc_write_z(tc_view(s), s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj));
         } else {
           ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, scale, s.row_of_slot, s.feat_of_slot,
-                   s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj};
+                   s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj, s.p.feature_map};
           CK(launch_write_z_simt(za, s.st));
         }
         CK(launch_gram_f32_to_f64(Zc, sj, nr, sj, Hb, sj, s.st));
@@ -929,7 +945,8 @@ PassArgs base_pass_args(const rff_admm_s& s) {
   a.ldg = s.dld;
   a.K = (int)s.dld;
   a.bias = s.bias;
-  a.scale = (float)std::sqrt(2.0 / (double)s.D);
+  a.scale = s.zmap_scale();
+  a.map = s.p.feature_map;
   a.row_ok = s.row_of_slot;
   a.feat_ok = s.feat_of_slot;
   a.row_slot = s.d_row_slot;
@@ -1313,7 +1330,7 @@ rff_status sqdiff(rff_admm_t h, const float* a, const float* b, int64_t n, doubl
 rff_status scores_pass(rff_admm_t h, const float* Xrows32, const __half* Xh, const __half* Xl,
                        int64_t nrows, const int32_t* row_ok, float* out) {
   auto& s = *h;
-  if (s.split_path()) {
+  if (s.tc_scores()) {
     CK(cudaMemsetAsync(s.amax + AMAX_WB, 0, 4, s.st));
     CK(launch_finite_check(s.Wbar, s.fslots * s.mpad, 0, reinterpret_cast<int*>(s.amax + AMAX_FLAG), s.st, s.amax + AMAX_WB));
     CK(launch_transpose_split_f16(s.Wbar, s.fslots, (int)s.mpad, 1, 0, s.WbThi, s.WbTlo, s.fslots, 0, 1.f,
@@ -1547,17 +1564,19 @@ rff_status rff_admm_predict(rff_admm_t h, const float* Xq, int64_t q, float* sco
     const int64_t nq = std::min(chunk, q - q0), nqp = round_up(nq, SLOT);
     CK(cudaMemcpyAsync(stage, Xq + q0 * s.d, nq * s.d * 4, kin, s.st));
     CK(cudaMemsetAsync(s.flag, 0, 16, s.st));
-    CK(launch_finite_check(stage, nq * s.d, 0, s.flag, s.st, reinterpret_cast<unsigned*>(s.flag + 2)));
+    CK(launch_finite_check(stage, nq * s.d, s.p.feature_map == RFF_MAP_LAPLACE ? 2 : 0, s.flag, s.st,
+                           reinterpret_cast<unsigned*>(s.flag + 2)));
     int fl[3] = {0, 0, 0};
     CK(cudaMemcpyAsync(fl, s.flag, 12, cudaMemcpyDeviceToHost, s.st));
     CK(cudaStreamSynchronize(s.st));
-    if (fl[0]) return h->fail(RFF_EINVAL, "queries contain NaN or Inf");
+    if (fl[0] & 1) return h->fail(RFF_EINVAL, "queries contain NaN or Inf");
+    if (fl[0] & 4) return h->fail(RFF_EINVAL, "the random Laplace map takes nonnegative queries");
     if ((r = check_query_range(h, fl[2])) != RFF_OK) return r;
     // rows q0..q0+nq into a slot-padded block (rows beyond nq are zero and discarded)
     CK(cudaMemsetAsync(xq32, 0, nqp * s.dld * 4, s.st));
     CK(launch_gather_rows(stage, s.d, s.d, nullptr, nq, xq32, s.dld, s.st));
     if (s.bias_col >= 0) CK(launch_set_column(xq32, s.dld, nqp, s.bias_col, 1.f, s.st));
-    if (s.split_path()) CK(launch_split_f16(xq32, nqp * s.dld, s.xscale, xh, xl, s.st));
+    if (s.tc_scores()) CK(launch_split_f16(xq32, nqp * s.dld, s.xscale, xh, xl, s.st));
     if ((r = scores_pass(h, xq32, xh, xl, nqp, nullptr, sc)) != RFF_OK) return r;
     CK(cudaMemcpy2DAsync(scores + q0 * s.m, s.m * 4, sc, s.mpad * 4, s.m * 4, nq, kout, s.st));
   }
@@ -1660,7 +1679,7 @@ rff_status rff_admm_set_state(rff_admm_t h, const void* buf, size_t bytes) {
   if (hd.n != s.n || hd.d != s.d || hd.m != s.m || hd.R != s.R || hd.C != s.C || hd.p.D != s.p.D ||
       hd.p.seed != s.p.seed || hd.p.loss != s.p.loss || hd.p.reg != s.p.reg || hd.p.prec != s.p.prec ||
       hd.p.lambda != s.p.lambda || hd.p.sigma != s.p.sigma || hd.p.rho != s.p.rho ||
-      hd.p.rho_scale != s.p.rho_scale)
+      hd.p.rho_scale != s.p.rho_scale || hd.p.feature_map != s.p.feature_map)
     return h->fail(RFF_EINVAL, "state was written for other data, parameters or grid");
   if (!s.factored) {   // the set-up writes scratch into state buffers (the tuning passes): run it first
     rff_status r = setup_factors(h);
@@ -1706,11 +1725,13 @@ rff_status predict_into_scratch(rff_admm_t h, const float* Xq, int64_t q, float*
   __half* xl = reinterpret_cast<__half*>(base + round_up(x32, 256) + round_up(xsplit, 256));
   float* sc = reinterpret_cast<float*>(base + round_up(x32, 256) + 2 * round_up(xsplit, 256));
   CK(cudaMemsetAsync(s.flag, 0, 16, s.st));
-  CK(launch_finite_check(Xq, q * s.d, 0, s.flag, s.st, reinterpret_cast<unsigned*>(s.flag + 2)));
+  CK(launch_finite_check(Xq, q * s.d, s.p.feature_map == RFF_MAP_LAPLACE ? 2 : 0, s.flag, s.st,
+                         reinterpret_cast<unsigned*>(s.flag + 2)));
   int fl[3] = {0, 0, 0};
   CK(cudaMemcpyAsync(fl, s.flag, 12, cudaMemcpyDeviceToHost, s.st));
   CK(cudaStreamSynchronize(s.st));
-  if (fl[0]) return h->fail(RFF_EINVAL, "queries contain NaN or Inf");
+  if (fl[0] & 1) return h->fail(RFF_EINVAL, "queries contain NaN or Inf");
+  if (fl[0] & 4) return h->fail(RFF_EINVAL, "the random Laplace map takes nonnegative queries");
   {
     rff_status rr = check_query_range(h, fl[2]);
     if (rr != RFF_OK) return rr;
@@ -1719,7 +1740,7 @@ rff_status predict_into_scratch(rff_admm_t h, const float* Xq, int64_t q, float*
   CK(cudaMemsetAsync(xq32, 0, x32, s.st));
   CK(launch_gather_rows(Xq, s.d, s.d, nullptr, q, xq32, s.dld, s.st));
   if (s.bias_col >= 0) CK(launch_set_column(xq32, s.dld, qp, s.bias_col, 1.f, s.st));
-  if (s.split_path()) CK(launch_split_f16(xq32, qp * s.dld, s.xscale, xh, xl, s.st));
+  if (s.tc_scores()) CK(launch_split_f16(xq32, qp * s.dld, s.xscale, xh, xl, s.st));
   rff_status r = scores_pass(h, xq32, xh, xl, qp, nullptr, sc);
   if (r != RFF_OK) return r;
   CK(cudaMemcpy2DAsync(scores, s.m * 4, sc, s.mpad * 4, s.m * 4, q, cudaMemcpyDeviceToDevice, s.st));
@@ -1746,9 +1767,24 @@ rff_status rff_rff_params(uint64_t seed, double sigma, int64_t d, int64_t k_lo, 
              : RFF_ECUDA;
 }
 
-rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma, int64_t D, int64_t k_lo,
-                        int64_t k_hi, int32_t prec, float* Z, void* stream) {
-  if (n < 0 || d < 1 || D < 1 || k_lo < 0 || k_hi < k_lo || k_hi > D || !(sigma > 0) || prec < 0 || prec > 1)
+rff_status rff_laplace_params(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t k_hi, float* W,
+                              void* stream) {
+  if (d < 1 || k_lo < 0 || k_hi < k_lo || !(sigma > 0) || !W) return RFF_EINVAL;
+  return launch_params_rowmajor(seed, sigma, d, k_lo, k_hi - k_lo, W, nullptr, static_cast<cudaStream_t>(stream),
+                                RFF_MAP_LAPLACE) == cudaSuccess
+             ? RFF_OK
+             : RFF_ECUDA;
+}
+
+}  // extern "C"
+
+namespace {
+// Z for global features k_lo..k_hi-1 through the solver's own kernels: the random Fourier map
+// in FP32 (prec 0) or on the tensor cores (prec 1), or the random Laplace map (map 1, FP32)
+rff_status features_impl(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma, int64_t D, int64_t k_lo,
+                         int64_t k_hi, int32_t prec, int map, float* Z, void* stream) {
+  if (n < 0 || d < 1 || D < 1 || k_lo < 0 || k_hi < k_lo || k_hi > D || !(sigma > 0) || prec < 0 || prec > 1 ||
+      (map && prec))
     return RFF_EINVAL;
   if (n == 0 || k_hi == k_lo) return RFF_OK;
   if (!X || !Z) return RFF_EINVAL;
@@ -1784,24 +1820,26 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
   // the split path scales X and G by powers of two into the FP16 range (largest |x|, |g| <= 2^8)
   float xscale = 1.f;
   const float gscale = g_scale(sigma);
-  if (e == cudaSuccess && prec) {
-    unsigned bits = 0;
+  bool negative = false;
+  if (e == cudaSuccess && (prec || map)) {
+    unsigned bits[2] = {0, 0};
     int* fflag = reinterpret_cast<int*>(xmaxbits + 1);
     e = cudaMemsetAsync(xmaxbits, 0, 8, st);
-    if (e == cudaSuccess) e = launch_finite_check(X, n * d, 0, fflag, st, xmaxbits);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, xmaxbits, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = launch_finite_check(X, n * d, map ? 2 : 0, fflag, st, xmaxbits);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bits, xmaxbits, 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     float xmax = 0.f;
-    memcpy(&xmax, &bits, 4);
+    memcpy(&xmax, &bits[0], 4);
     xscale = pow2_scale(std::max<double>(xmax, bcol >= 0 ? 1.0 : 0.0));
+    negative = map && (bits[1] & 5);
   }
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && !negative)
     e = launch_params_slots(seed, sigma, d, dld, fp, fok, G32, prec ? Gh : nullptr, prec ? Gl : nullptr, gscale, bias,
-                            bcol, st);
-  const float scale = (float)std::sqrt(2.0 / (double)D);
-  if (e == cudaSuccess) {
+                            bcol, st, map);
+  const float scale = (float)(map ? 1.0 / std::sqrt((double)D) : std::sqrt(2.0 / (double)D));
+  if (e == cudaSuccess && !negative) {
     if (prec == RFF_PREC_FP32) {
-      ZArgs za{X32, dld, G32, dld, (int)dld, bias, scale, rok, fok, 0, n, 0, nf, Z, nf};
+      ZArgs za{X32, dld, G32, dld, (int)dld, bias, scale, rok, fok, 0, n, 0, nf, Z, nf, map};
       e = launch_write_z_simt(za, st);
     } else {
       if (bcol >= 0) e = launch_set_column(X32, dld, np, bcol, 1.f, st);
@@ -1826,8 +1864,21 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
     cudaGetLastError();
     return e == cudaErrorNotSupported ? RFF_EINVAL : RFF_ECUDA;
   }
+  if (negative) return RFF_EINVAL;
   if (prec == RFF_PREC_SPLIT_BF16 && tc_error_word() != 0) return RFF_ETIMEOUT;
   return RFF_OK;
+}
+}  // namespace
+
+extern "C" {
+rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma, int64_t D, int64_t k_lo,
+                        int64_t k_hi, int32_t prec, float* Z, void* stream) {
+  return features_impl(X, n, d, seed, sigma, D, k_lo, k_hi, prec, RFF_MAP_FOURIER, Z, stream);
+}
+
+rff_status rff_laplace_features(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma, int64_t D,
+                                int64_t k_lo, int64_t k_hi, float* Z, void* stream) {
+  return features_impl(X, n, d, seed, sigma, D, k_lo, k_hi, RFF_PREC_FP32, RFF_MAP_LAPLACE, Z, stream);
 }
 
 rff_status rff_prox_loss(int32_t loss, const float* V, const float* Yv, int64_t n, int32_t m, double t,

@@ -641,7 +641,8 @@ __global__ void k_finite(const float* __restrict__ x, int64_t n, int pm1, int* _
     const float v = x[e];
     if (!isfinite(v)) f |= 1;
     else mx = fmaxf(mx, fabsf(v));
-    if (pm1 && v != 1.f && v != -1.f) f |= 2;
+    if (pm1 == 1 && v != 1.f && v != -1.f) f |= 2;
+    if (pm1 == 2 && v < 0.f) f |= 4;
   }
   if (f) atomicOr(flag, f);
   if (maxbits) {

@@ -34,6 +34,7 @@ struct PassArgs {
   int nsplit;               // pass 1: row splits per row block
   int per_block;            // pass 2: write per column block (1) or once (0)
   const uint8_t* bmask;     // device, R x C: active blocks of a stochastic iteration, or null
+  int map;                  // feature map: 0 random Fourier (cos(T + b)), 1 random Laplace (exp(-T))
 };
 
 struct ZArgs {
@@ -49,6 +50,7 @@ struct ZArgs {
   int64_t r0, nr, f0, nf;   // row slots [r0, r0+nr), feature slots [f0, f0+nf)
   float* out;
   int64_t ldo;
+  int map;                  // as PassArgs::map
 };
 
 // philox.cu
@@ -57,13 +59,14 @@ cudaError_t launch_philox_raw(const uint32_t* ctr, uint64_t seed, int64_t n, uin
 // word of Philox4x32-10 at counter (b, k, 2, 0) under seed, k = *ctr; then *ctr = k + 1
 cudaError_t launch_block_mask(uint64_t seed, uint32_t thr, int nblocks, int64_t* ctr, uint8_t* mask,
                               cudaStream_t st);
+// map 0: G (random Fourier) and b; map 1: the random Laplace map's W, b = 0
 cudaError_t launch_params_rowmajor(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t nk, float* G,
-                                   float* b, cudaStream_t st);
+                                   float* b, cudaStream_t st, int map = 0);
 // Ghi/Glo: the FP16 split of G * gscale; bias_col >= 0: they carry b * gscale in that
 // column (inputs then carry ones there)
 cudaError_t launch_params_slots(uint64_t seed, double sigma, int64_t d, int64_t ld, int64_t nslots,
                                 const int32_t* feat_of_slot, float* Gt, __half* Ghi, __half* Glo, float gscale,
-                                float* bias, int64_t bias_col, cudaStream_t st);
+                                float* bias, int64_t bias_col, cudaStream_t st, int map = 0);
 
 // regen_simt.cu
 cudaError_t launch_pass1_simt(const PassArgs& p, int64_t nfeat_slots, cudaStream_t st);
@@ -181,6 +184,7 @@ cudaError_t launch_loss_partials(int loss, const float* Y, const float* S, const
 cudaError_t launch_reg_partials(int reg, const float* W, int64_t n, double* partials, int nblocks, cudaStream_t st,
                                 const float* w = nullptr, int ncol = 1);
 cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
+// flag |= 1 for NaN/Inf; pm1 = 1: |= 2 for a value other than +-1; pm1 = 2: |= 4 for a negative value
 cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, cudaStream_t st,
                                 unsigned* maxbits = nullptr);
 cudaError_t launch_set_diag(double* A, int64_t ld, int64_t s, double v, cudaStream_t st);

@@ -11,23 +11,30 @@
 //                  of the stochastic variant iff (w >> 8) < floor(p 2^24)
 //   uniform        ((w >> 8) + 0.5) 2^-24 in float64
 //   G = float32(sqrt(-2 ln u1) {cos,sin}(2 pi u2) / sigma), b = float32(pi u)
+//   random Laplace map: W = float32(1 / (2 sigma^2 g^2)) from the same standard normals
+//   g (a Levy(0, 1/(2 sigma^2)) draw), b = 0
 #include "common.cuh"
 #include "internal.h"
 
 namespace rff {
 
+// map 0 (random Fourier): g / sigma; map 1 (random Laplace): 1 / (2 sigma^2 g^2)
+__device__ __forceinline__ float from_normal(double g, double sigma, int map) {
+  return map ? (float)(1.0 / (2.0 * sigma * sigma * g * g)) : (float)(g / sigma);
+}
+
 __device__ __forceinline__ void gauss4(uint32_t k, uint32_t q, uint32_t k0, uint32_t k1, double sigma,
-                                       float g[4]) {
+                                       float g[4], int map = 0) {
   const U4 w = philox4x32_10(U4{k, q, 0u, 0u}, k0, k1);
   const double two_pi = 6.283185307179586;  // float64 nearest to 2 pi
   const double r0 = sqrt(-2.0 * log(uniform01(w.x)));
   const double t0 = two_pi * uniform01(w.y);
   const double r1 = sqrt(-2.0 * log(uniform01(w.z)));
   const double t1 = two_pi * uniform01(w.w);
-  g[0] = (float)((r0 * cos(t0)) / sigma);
-  g[1] = (float)((r0 * sin(t0)) / sigma);
-  g[2] = (float)((r1 * cos(t1)) / sigma);
-  g[3] = (float)((r1 * sin(t1)) / sigma);
+  g[0] = from_normal(r0 * cos(t0), sigma, map);
+  g[1] = from_normal(r0 * sin(t0), sigma, map);
+  g[2] = from_normal(r1 * cos(t1), sigma, map);
+  g[3] = from_normal(r1 * sin(t1), sigma, map);
 }
 
 __device__ __forceinline__ float phase(uint32_t k, uint32_t k0, uint32_t k1) {
@@ -49,19 +56,19 @@ __global__ void k_philox_raw(const uint32_t* __restrict__ ctr, uint32_t k0, uint
 
 // API layout: G (d x nk row-major), one thread per (row group q, feature).
 __global__ void k_params_rowmajor(uint32_t k0, uint32_t k1, double sigma, int64_t d, int64_t k_lo, int64_t nk,
-                                  float* __restrict__ G, float* __restrict__ b) {
+                                  float* __restrict__ G, float* __restrict__ b, int map) {
   const int64_t kk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t q = blockIdx.y;
   if (kk >= nk) return;
   const uint32_t k = (uint32_t)(k_lo + kk);
   float g[4];
-  gauss4(k, (uint32_t)q, k0, k1, sigma, g);
+  gauss4(k, (uint32_t)q, k0, k1, sigma, g, map);
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int64_t r = 4 * q + e;
     if (r < d) G[r * nk + kk] = g[e];
   }
-  if (q == 0 && b) b[kk] = phase(k, k0, k1);
+  if (q == 0 && b) b[kk] = map ? 0.f : phase(k, k0, k1);
 }
 
 // Slot layout: Gt (D_slots x ld, feature-major) in float32 and/or split BF16.
@@ -69,16 +76,16 @@ __global__ void k_params_rowmajor(uint32_t k0, uint32_t k1, double sigma, int64_
 __global__ void k_params_slots(uint32_t k0, uint32_t k1, double sigma, int64_t d, int64_t ld, int64_t nslots,
                                const int32_t* __restrict__ feat_of_slot, float* __restrict__ Gt,
                                __half* __restrict__ Ghi, __half* __restrict__ Glo, float gscale,
-                               float* __restrict__ bias, int64_t bias_col) {
+                               float* __restrict__ bias, int64_t bias_col, int map) {
   const int64_t nq = ld / 4;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nslots * nq) return;
   const int64_t p = t / nq, q = t % nq;
   const int32_t k = feat_of_slot[p];
   float g[4] = {0.f, 0.f, 0.f, 0.f};
-  if (k >= 0 && 4 * q < d) gauss4((uint32_t)k, (uint32_t)q, k0, k1, sigma, g);
+  if (k >= 0 && 4 * q < d) gauss4((uint32_t)k, (uint32_t)q, k0, k1, sigma, g, map);
   const bool has_bias_col = bias_col >= 4 * q && bias_col < 4 * q + 4;
-  const float ph = (k >= 0 && (q == 0 || has_bias_col)) ? phase((uint32_t)k, k0, k1) : 0.f;
+  const float ph = (!map && k >= 0 && (q == 0 || has_bias_col)) ? phase((uint32_t)k, k0, k1) : 0.f;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int64_t r = 4 * q + e;
@@ -123,21 +130,21 @@ cudaError_t launch_philox_raw(const uint32_t* ctr, uint64_t seed, int64_t n, uin
 }
 
 cudaError_t launch_params_rowmajor(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t nk, float* G,
-                                   float* b, cudaStream_t st) {
+                                   float* b, cudaStream_t st, int map) {
   if (nk <= 0 || d <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(nk, 128), (unsigned)ceil_div(d, 4));
-  k_params_rowmajor<<<grid, 128, 0, st>>>((uint32_t)seed, (uint32_t)(seed >> 32), sigma, d, k_lo, nk, G, b);
+  k_params_rowmajor<<<grid, 128, 0, st>>>((uint32_t)seed, (uint32_t)(seed >> 32), sigma, d, k_lo, nk, G, b, map);
   return cudaGetLastError();
 }
 
 cudaError_t launch_params_slots(uint64_t seed, double sigma, int64_t d, int64_t ld, int64_t nslots,
                                 const int32_t* feat_of_slot, float* Gt, __half* Ghi, __half* Glo, float gscale,
-                                float* bias, int64_t bias_col, cudaStream_t st) {
+                                float* bias, int64_t bias_col, cudaStream_t st, int map) {
   const int64_t total = nslots * (ld / 4);
   if (total <= 0) return cudaSuccess;
   k_params_slots<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>((uint32_t)seed, (uint32_t)(seed >> 32), sigma,
                                                                    d, ld, nslots, feat_of_slot, Gt, Ghi, Glo, gscale, bias,
-                                                                   bias_col);
+                                                                   bias_col, map);
   return cudaGetLastError();
 }
 

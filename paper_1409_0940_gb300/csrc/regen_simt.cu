@@ -4,7 +4,8 @@
 // 64-row panels of the other ("B"), both holding rows of length K (the input
 // dimension d, padded):
 //     T   = A_panel . B_panel^T                       (X_i G_j or its transpose)
-//     Z   = sqrt(2/D) cos(T + b)  masked to valid slots  (the transform T[X_i, j], Sec. 4)
+//     Z   = sqrt(2/D) cos(T + b)  masked to valid slots  (the transform T[X_i, j], Sec. 4;
+//           the random Laplace map: Z = exp(-T) / sqrt(D))
 //     acc += Z . M[B rows]                             (the chained product)
 // and writes acc when a run ends.  With A = feature rows of G^T and B = data rows
 // this is pass 1, R_ij = Z_ij^T V_ij (the Z_ij^T (Obar_ij + nu_i) term of eq. (gpWij));
@@ -32,7 +33,8 @@ struct SimtSmem {
 __device__ __forceinline__ void tile_z(SimtSmem& sm, const float* __restrict__ A, int64_t lda, int64_t a0,
                                        const float* __restrict__ B, int64_t ldb, int64_t b0, int K,
                                        const float* __restrict__ bias, bool bias_on_a, float scale,
-                                       const int32_t* __restrict__ a_ok, const int32_t* __restrict__ b_ok) {
+                                       const int32_t* __restrict__ a_ok, const int32_t* __restrict__ b_ok,
+                                       int map) {
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   float acc[4][4];
 #pragma unroll
@@ -61,7 +63,7 @@ __device__ __forceinline__ void tile_z(SimtSmem& sm, const float* __restrict__ A
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
   }
-  // epilogue: cos with the feature phase, masked to valid rows/features
+  // epilogue: cos with the feature phase (or exp(-T), the Laplace map), masked to valid rows/features
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int64_t ar = a0 + ty * 4 + i;
@@ -71,7 +73,7 @@ __device__ __forceinline__ void tile_z(SimtSmem& sm, const float* __restrict__ A
       const int64_t br = b0 + tx * 4 + j;
       const bool ok = aok && (b_ok ? (b_ok[br] >= 0) : true);
       const float ph = bias_on_a ? bias[ar] : bias[br];
-      sm.Zs[ty * 4 + i][tx * 4 + j] = ok ? scale * cos_rr(acc[i][j] + ph) : 0.f;
+      sm.Zs[ty * 4 + i][tx * 4 + j] = !ok ? 0.f : map ? scale * expf(-acc[i][j]) : scale * cos_rr(acc[i][j] + ph);
     }
   }
 }
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(NT) k_pass2_simt(PassArgs p) {
     if (act && !act[j]) continue;
     const int64_t f0 = p.col_slot[j], f1 = f0 + p.col_size[j];
     for (int64_t b0 = f0; b0 < f1; b0 += BN) {
-      tile_z(sm, p.X, p.ldx, a0, p.Gt, p.ldg, b0, p.K, p.bias, false, p.scale, p.row_ok, p.feat_ok);
+      tile_z(sm, p.X, p.ldx, a0, p.Gt, p.ldg, b0, p.K, p.bias, false, p.scale, p.row_ok, p.feat_ok, p.map);
       __syncthreads();
       load_M(Ms, M, b0, p.mpad);
       __syncthreads();
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(NT) k_pass1_simt(PassArgs p) {
     for (int q = 0; q < MQ; ++q) acc2[ii][q] = 0.f;
   for (int64_t t = t0; t < t1; ++t) {
     const int64_t b0 = r0 + t * BN;
-    tile_z(sm, p.Gt, p.ldg, a0, p.X, p.ldx, b0, p.K, p.bias, true, p.scale, p.feat_ok, p.row_ok);
+    tile_z(sm, p.Gt, p.ldg, a0, p.X, p.ldx, b0, p.K, p.bias, true, p.scale, p.feat_ok, p.row_ok, p.map);
     __syncthreads();
     load_M(Ms, M, b0, p.mpad);
     __syncthreads();
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(NT) k_write_z_simt(ZArgs p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SimtSmem& sm = *reinterpret_cast<SimtSmem*>(smem_raw);
   const int64_t a0 = p.r0 + (int64_t)blockIdx.x * BM, b0 = p.f0 + (int64_t)blockIdx.y * BN;
-  tile_z(sm, p.X, p.ldx, a0, p.Gt, p.ldg, b0, p.K, p.bias, false, p.scale, p.row_ok, p.feat_ok);
+  tile_z(sm, p.X, p.ldx, a0, p.Gt, p.ldg, b0, p.K, p.bias, false, p.scale, p.row_ok, p.feat_ok, p.map);
   __syncthreads();
   for (int t = threadIdx.x; t < BM * BN; t += NT) {
     const int r = t / BN, c = t % BN;
