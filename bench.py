@@ -106,12 +106,14 @@ class Clocks:
 def make_data(w, n=None):
     import synth
     n = n or w["n"]
+    if w.get("feature_map", "fourier") == "laplace":   # the Laplace map takes histograms
+        return synth.histograms(n=n, d=w["d"], m=w["m"], seed=w["data_seed"])
     return synth.multiclass(n=n, d=w["d"], m=w["m"], seed=w["data_seed"])
 
 
 def solver_kw(w, prec):
     return dict(loss=w["loss"], reg=w["reg"], lam=w["lam"], sigma=w["sigma"], rho=w["rho"], D=w["D"], R=w["R"],
-                C=w["C"], seed=w["philox_seed"], m=w["m"], prec=prec)
+                C=w["C"], seed=w["philox_seed"], m=w["m"], prec=prec, feature_map=w.get("feature_map", "fourier"))
 
 
 def flops_per_iter(w, prec):
@@ -248,6 +250,8 @@ def run_ours(args, rank, world):
         compare = {}
         Ws = {args.prec: W_main}
         for prec in ("split_bf16", "cached_z", "fp32"):
+            if prec == "split_bf16" and w["feature_map"] == "laplace":
+                continue                      # the implicit split precision takes the Fourier map only
             if prec == args.prec:
                 compare[prec] = {"iter_per_s": args.steps / (ms * 1e-3)}
                 continue
@@ -300,7 +304,7 @@ def run_ours(args, rank, world):
         "config": {"workload": w["name"], "n": w["n"], "d": w["d"], "m": w["m"], "D": w["D"],
                    "grid": "%dx%d" % (w["R"], w["C"]), "sigma": w["sigma"], "loss": w["loss"], "reg": w["reg"],
                    "lambda": w["lam"], "rho": w["rho"], "prec": args.prec, "parallelism": "replicas",
-                   "block_fraction": w["block_fraction"], "active_fraction": act,
+                   "block_fraction": w["block_fraction"], "active_fraction": act, "feature_map": w["feature_map"],
                    "l2": "inputs larger than L2 (X split 358 MB, V 512 MB, factors 2.1 GB)"},
         "e2e": e2e,
         "gpu_launches": int(prof["launches"]),
@@ -323,6 +327,11 @@ def workload(args):
         w["name"] = w["name"].replace("200k", "%dk" % (args.n // 1000))
     w["loss"] = args.loss
     w["block_fraction"] = args.block_fraction
+    w["feature_map"] = args.feature_map
+    if args.feature_map == "laplace":
+        # histogram inputs (d bins summing to 1) and a bandwidth at the scale of sum_r sqrt(2 x_r)
+        w["name"] = w["name"].replace("multiclass", "histograms") + "-laplace"
+        w["sigma"] = 8.0
     if args.loss != "squared":
         w["name"] += "-" + args.loss
     if args.block_fraction < 1.0:
@@ -336,7 +345,7 @@ def oracle_iter_seconds(w, n_sample, iters):
     from oracle import admm
     X, Y = make_data(w, n=n_sample)
     p = admm.Problem(X, Y, w["loss"], w["reg"], w["lam"], w["sigma"], w["rho"], w["D"], w["R"], w["C"],
-                     w["philox_seed"])
+                     w["philox_seed"], feature_map=w["feature_map"])
     admm.admm(p, 1)                       # builds Z and the cached factors (untimed)
     t0 = time.perf_counter()
     admm.admm(p, iters, block_fraction=w["block_fraction"])
@@ -548,6 +557,8 @@ def main():
     ap.add_argument("--workload", default="multiclass", choices=["multiclass", "ridge", "sweep", "serve"])
     ap.add_argument("--loss", default="squared", choices=["squared", "hinge", "multinomial", "crammer_singer", "l1"],
                     help="loss of the multiclass workload")
+    ap.add_argument("--feature-map", default="fourier", choices=["fourier", "laplace"],
+                    help="laplace: random Laplace features on histogram inputs (fp32 or cached_z precision)")
     ap.add_argument("--block-fraction", type=float, default=1.0,
                     help="stochastic variant: probability that a block takes part in an iteration")
     args = ap.parse_args()
