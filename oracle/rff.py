@@ -32,7 +32,7 @@ bitwise; partition sizes against their definition; the Laplace map against the
 semigroup kernel within a Hoeffding bound, its parameters against the Levy CDF.
 """
 
-MAPS = ("fourier", "laplace")
+MAPS = ("fourier", "laplace", "fastfood")
 import numpy as np
 
 from . import philox
@@ -64,6 +64,10 @@ def features_block(X, seed, sigma, D, k_lo, k_hi, feature_map="fourier"):
     """Z restricted to global features k_lo..k_hi-1 (the operator T[X_i, j])."""
     if feature_map == "laplace":
         return laplace_features(X, philox.laplace_params(seed, sigma, X.shape[1], D, k_lo, k_hi), D)
+    if feature_map == "fastfood":
+        from . import fastfood
+        G, b = fastfood.fastfood_params(seed, sigma, X.shape[1], D, k_lo, k_hi)
+        return features(X, G, b, D)
     if feature_map != "fourier":
         raise ValueError(feature_map)
     G, b = philox.rff_params(seed, sigma, X.shape[1], D, k_lo, k_hi)
