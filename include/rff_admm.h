@@ -103,8 +103,13 @@ typedef enum { RFF_RHO_SUM = 0, RFF_RHO_MEAN = 1 } rff_rho_scale;
  *                    the Gaussian kernel exp(-|x - x'|^2 / (2 sigma^2))
  *   RFF_MAP_LAPLACE  z(x) = exp(-W^T x) / sqrt(D), W = 1 / (2 sigma^2 g^2) (Levy): the
  *                    exponential semigroup kernel exp(-sum_r sqrt(x_r + x'_r) / sigma) on
- *                    nonnegative inputs (histograms); FP32 and cached-Z precisions only */
-typedef enum { RFF_MAP_FOURIER = 0, RFF_MAP_LAPLACE = 1 } rff_feature_map;
+ *                    nonnegative inputs (histograms); FP32 and cached-Z precisions only
+ *   RFF_MAP_FASTFOOD z(x) = sqrt(2/D) cos(V x + b) with the Fastfood matrix (Le, Sarlos and
+ *                    Smola 2013): per block of d' = 2^p >= d features
+ *                    V = S H diag(g) P H diag(B) / (sigma sqrt(d')), H Walsh-Hadamard, B signs,
+ *                    P a permutation, S chi(d') row lengths over |g|; every row of V is
+ *                    N(0, I / sigma^2), so the Gaussian kernel again; d <= 4096 */
+typedef enum { RFF_MAP_FOURIER = 0, RFF_MAP_LAPLACE = 1, RFF_MAP_FASTFOOD = 2 } rff_feature_map;
 
 typedef struct {
   int32_t loss;      /* rff_loss                                                     */
@@ -332,6 +337,12 @@ rff_status rff_laplace_params(uint64_t seed, double sigma, int64_t d, int64_t k_
  * Z n x (k_hi - k_lo); device pointers.  Errors: RFF_EINVAL for a negative or non-finite x. */
 rff_status rff_laplace_features(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma, int64_t D,
                                 int64_t k_lo, int64_t k_hi, float* Z, void* stream);
+
+/* The Fastfood map's projection for global features k_lo..k_hi-1: Vt ((k_hi - k_lo) x d,
+ * row-major: row r is V's row k_lo + r) and b (k_hi - k_lo), device pointers; D sets the
+ * block structure only through d' (features are grouped in blocks of d').  d <= 4096. */
+rff_status rff_fastfood_params(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t k_hi, float* Vt,
+                               float* b, void* stream);
 
 /* Batched Cholesky factorisation in FP64 of `batch` SPD matrices (eq. (cache)):
  * A: batch x s x s row-major float64, overwritten by the lower factor L (upper

@@ -19,7 +19,7 @@ RFF_OK, RFF_EINVAL, RFF_ENOMEM, RFF_ECUDA, RFF_ETIMEOUT, RFF_ENOTREADY, RFF_ENUM
 _STATUS = {0: "RFF_OK", 1: "RFF_EINVAL", 2: "RFF_ENOMEM", 3: "RFF_ECUDA", 4: "RFF_ETIMEOUT",
            5: "RFF_ENOTREADY", 6: "RFF_ENUMERIC"}
 LOSSES = {"squared": 0, "hinge": 1, "logistic": 2, "multinomial": 3, "l1": 4, "crammer_singer": 5}
-FEATURE_MAPS = {"fourier": 0, "laplace": 1}
+FEATURE_MAPS = {"fourier": 0, "laplace": 1, "fastfood": 2}
 REGS = {"l2": 0, "l1": 1}
 PRECS = {"fp32": 0, "split_bf16": 1, "cached_z": 2}
 RHO_SCALES = {"sum": 0, "mean": 1}
@@ -88,6 +88,7 @@ PROTOTYPES = {
     "rff_rff_params": (_I32, [_U64, _D, _I64, _I64, _I64, _P, _P, _P]),
     "rff_features": (_I32, [_P, _I64, _I64, _U64, _D, _I64, _I64, _I64, _I32, _P, _P]),
     "rff_laplace_params": (_I32, [_U64, _D, _I64, _I64, _I64, _P, _P]),
+    "rff_fastfood_params": (_I32, [_U64, _D, _I64, _I64, _I64, _P, _P, _P]),
     "rff_laplace_features": (_I32, [_P, _I64, _I64, _U64, _D, _I64, _I64, _I64, _P, _P]),
     "rff_prox_loss": (_I32, [_I32, _P, _P, _I64, _I32, _D, _I32, _P, _P]),
     "rff_prox_reg": (_I32, [_I32, _P, _I64, _D, _P, _P]),
@@ -314,6 +315,13 @@ def rff_laplace_params(seed, sigma, d, k_lo, k_hi, W, stream=None):
     pw, _ = _ptr(W)
     _check(lib.rff_laplace_params(seed, sigma, d, k_lo, k_hi, pw, _stream(stream)), None, "rff_laplace_params")
     return W
+
+
+def rff_fastfood_params(seed, sigma, d, k_lo, k_hi, Vt, b, stream=None):
+    pv, _ = _ptr(Vt)
+    pb, _ = _ptr(b)
+    _check(lib.rff_fastfood_params(seed, sigma, d, k_lo, k_hi, pv, pb, _stream(stream)), None, "rff_fastfood_params")
+    return Vt, b
 
 
 def rff_laplace_features(X, seed, sigma, D, k_lo, k_hi, Z, stream=None):

@@ -137,8 +137,8 @@ struct rff_admm_s {
   }
   // the split path: tensor-core kernels and BF16 operand copies (cached-Z uses them too)
   bool split_path() const { return p.prec == RFF_PREC_SPLIT_BF16 || p.prec == RFF_PREC_CACHED_Z; }
-  // scoring forms X.G on the tensor cores (split path, random Fourier map)
-  bool tc_scores() const { return split_path() && p.feature_map == RFF_MAP_FOURIER; }
+  // scoring forms X.G on the tensor cores (split path; random Fourier or Fastfood map)
+  bool tc_scores() const { return split_path() && p.feature_map != RFF_MAP_LAPLACE; }
   // the feature map's scale: max |z| (sqrt(2/D) for cos, 1/sqrt(D) for exp(-T) with T >= 0)
   float zmap_scale() const {
     return (float)(p.feature_map == RFF_MAP_LAPLACE ? 1.0 / std::sqrt((double)D) : std::sqrt(2.0 / (double)D));
@@ -197,7 +197,7 @@ rff_status check_params(const rff_admm_params* p, std::string& why) {
   if (p->m < 1 || p->m > 256) { why = "m must be in [1, 256]"; return RFF_EINVAL; }
   if (p->newton_iters < 0 || p->newton_iters > 100) { why = "newton_iters out of range"; return RFF_EINVAL; }
   if (p->prec != RFF_PREC_FP32 && p->C > 64) { why = "the split-BF16 and cached-Z paths support C <= 64"; return RFF_EINVAL; }
-  if (p->feature_map < 0 || p->feature_map > 1) { why = "unknown feature map"; return RFF_EINVAL; }
+  if (p->feature_map < 0 || p->feature_map > 2) { why = "unknown feature map"; return RFF_EINVAL; }
   if (p->feature_map == RFF_MAP_LAPLACE && p->prec == RFF_PREC_SPLIT_BF16) {
     // W is Levy-distributed: its range spans far more than the FP16 split's 2^29
     why = "the random Laplace map runs on the FP32 and cached-Z precisions";
@@ -457,6 +457,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   h->err.clear();
   if (!X || !Yin) return h->fail(RFF_EINVAL, "X or Y is NULL");
   if (n < h->p.R || d < 1 || n > ((int64_t)1 << 31) - 1) return h->fail(RFF_EINVAL, "need R <= n < 2^31 and d >= 1");
+  if (h->p.feature_map == RFF_MAP_FASTFOOD && d > 4096) return h->fail(RFF_EINVAL, "the Fastfood map takes d <= 4096");
   CK(cudaStreamSynchronize(h->st));
   h->drop_graph();
   h->free_all();
@@ -789,14 +790,47 @@ rff_status materialise_z(rff_admm_t h) {
   return RFF_OK;
 }
 
+// Fastfood: V (the projection, in G's place) and b from Philox on the device; its split
+// copies take their scale from the measured max |V| (V has no a-priori bound like
+// Box-Muller's).  Tables and, on the split path, the FP32 V live in the set-up scratch.
+rff_status fastfood_features(rff_admm_t h) {
+  auto& s = *h;
+  const size_t tb = round_up(fastfood_table_bytes(s.D, fastfood_dim(s.d)), 256);
+  const bool keep32 = s.Gt32 != nullptr;
+  const size_t vb = keep32 ? 0 : (size_t)s.fslots * s.dld * 4;
+  rff_status rs = ensure_scratch(h, tb + vb + 256);
+  if (rs != RFF_OK) return rs;
+  char* base = static_cast<char*>(s.scratch.p);
+  float* V = keep32 ? s.Gt32 : reinterpret_cast<float*>(base + tb);
+  unsigned* maxbits = reinterpret_cast<unsigned*>(s.flag + 3);
+  CK(cudaMemsetAsync(maxbits, 0, 4, s.st));
+  CK(launch_fastfood_params(s.p.seed, s.p.sigma, s.d, s.dld, s.D, s.fslots, s.feat_of_slot, V, s.bias, maxbits, base,
+                            s.st));
+  if (s.tc_scores()) {
+    unsigned bits = 0;
+    CK(cudaMemcpyAsync(&bits, maxbits, 4, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaStreamSynchronize(s.st));
+    float vmax = 0.f;
+    memcpy(&vmax, &bits, 4);
+    s.gscale = pow2_scale(std::max<double>(vmax, 3.1415927));   // b in [0, pi) shares the scale
+    CK(launch_split_g_bias(V, s.fslots, s.dld, s.bias, s.bias_col, s.gscale, s.Ghi, s.Glo, s.st));
+  }
+  return RFF_OK;
+}
+
 rff_status setup_factors(rff_admm_t h) {
   auto& s = *h;
   const float scale = s.zmap_scale();
   // random features: G and b (or the Laplace map's W) from Philox (Sec. 4); the FP16 copies
   // only where the tensor cores form X.G
   const bool g16 = s.tc_scores();
-  CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, g16 ? s.Ghi : nullptr,
-                         g16 ? s.Glo : nullptr, s.gscale, s.bias, s.bias_col, s.st, s.p.feature_map));
+  if (s.p.feature_map == RFF_MAP_FASTFOOD) {
+    rff_status r = fastfood_features(h);
+    if (r != RFF_OK) return r;
+  } else {
+    CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, g16 ? s.Ghi : nullptr,
+                           g16 ? s.Glo : nullptr, s.gscale, s.bias, s.bias_col, s.st, s.p.feature_map));
+  }
   // Gram matrices H_ij = I + Z_ij^T Z_ij (eq. (cache)), or I + Z_ij Z_ij^T in the outer
   // form, in FP64, batched by memory
   int64_t smax = 0;
@@ -1765,6 +1799,33 @@ rff_status rff_rff_params(uint64_t seed, double sigma, int64_t d, int64_t k_lo, 
                  cudaSuccess
              ? RFF_OK
              : RFF_ECUDA;
+}
+
+rff_status rff_fastfood_params(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t k_hi, float* Vt,
+                               float* b, void* stream) {
+  if (d < 1 || d > 4096 || k_lo < 0 || k_hi < k_lo || !(sigma > 0) || !Vt || !b) return RFF_EINVAL;
+  if (k_hi == k_lo) return RFF_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t nk = k_hi - k_lo;
+  const size_t tb = round_up(fastfood_table_bytes(k_hi, fastfood_dim(d)), 256);
+  char* base = nullptr;
+  if (cudaMallocAsync((void**)&base, tb + (size_t)nk * 4 + 256, st) != cudaSuccess) {
+    cudaGetLastError();
+    return RFF_ENOMEM;
+  }
+  int32_t* fos = reinterpret_cast<int32_t*>(base + tb);
+  unsigned* mx = reinterpret_cast<unsigned*>(fos + nk);
+  std::vector<int32_t> f(nk);
+  for (int64_t i = 0; i < nk; ++i) f[i] = (int32_t)(k_lo + i);
+  cudaError_t e = cudaMemcpyAsync(fos, f.data(), nk * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_fastfood_params(seed, sigma, d, d, k_hi, nk, fos, Vt, b, mx, base, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // f is read by the asynchronous copy
+  cudaFreeAsync(base, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return RFF_ECUDA;
+  }
+  return RFF_OK;
 }
 
 rff_status rff_laplace_params(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t k_hi, float* W,

@@ -34,7 +34,7 @@ struct PassArgs {
   int nsplit;               // pass 1: row splits per row block
   int per_block;            // pass 2: write per column block (1) or once (0)
   const uint8_t* bmask;     // device, R x C: active blocks of a stochastic iteration, or null
-  int map;                  // feature map: 0 random Fourier (cos(T + b)), 1 random Laplace (exp(-T))
+  int map;                  // feature map: 1 random Laplace (exp(-T)); else cos(T + b) (Fourier, Fastfood)
 };
 
 struct ZArgs {
@@ -55,6 +55,21 @@ struct ZArgs {
 
 // philox.cu
 cudaError_t launch_philox_raw(const uint32_t* ctr, uint64_t seed, int64_t n, uint32_t* out, cudaStream_t st);
+// Fastfood (feature map 2): d' = the smallest power of two >= d (at most 4096)
+inline int fastfood_dim(int64_t d) {
+  int p = 1;
+  while (p < d) p *= 2;
+  return p;
+}
+size_t fastfood_table_bytes(int64_t D, int dp);
+// V rows (feature-major, ld columns, zero beyond d) for the features of the slots, b, and
+// max |V| into maxbits (float bits, atomicMax; zero it first); tables: fastfood_table_bytes
+cudaError_t launch_fastfood_params(uint64_t seed, double sigma, int64_t d, int64_t ld, int64_t D, int64_t nslots,
+                                   const int32_t* feat_of_slot, float* Gt, float* bias, unsigned* maxbits,
+                                   void* tables, cudaStream_t st);
+// hi/lo FP16 split of Gt * gscale (n x ld) with b * gscale in column bias_col (if >= 0)
+cudaError_t launch_split_g_bias(const float* Gt, int64_t n, int64_t ld, const float* bias, int64_t bias_col,
+                                float gscale, __half* hi, __half* lo, cudaStream_t st);
 // Active blocks of a stochastic iteration: mask[b] = 1 iff (w >> 8) < thr, w the first
 // word of Philox4x32-10 at counter (b, k, 2, 0) under seed, k = *ctr; then *ctr = k + 1
 cudaError_t launch_block_mask(uint64_t seed, uint32_t thr, int nblocks, int64_t* ctr, uint8_t* mask,

@@ -73,7 +73,7 @@ __device__ __forceinline__ void tile_z(SimtSmem& sm, const float* __restrict__ A
       const int64_t br = b0 + tx * 4 + j;
       const bool ok = aok && (b_ok ? (b_ok[br] >= 0) : true);
       const float ph = bias_on_a ? bias[ar] : bias[br];
-      sm.Zs[ty * 4 + i][tx * 4 + j] = !ok ? 0.f : map ? scale * expf(-acc[i][j]) : scale * cos_rr(acc[i][j] + ph);
+      sm.Zs[ty * 4 + i][tx * 4 + j] = !ok ? 0.f : map == 1 ? scale * expf(-acc[i][j]) : scale * cos_rr(acc[i][j] + ph);
     }
   }
 }
