@@ -332,6 +332,8 @@ def workload(args):
         # histogram inputs (d bins summing to 1) and a bandwidth at the scale of sum_r sqrt(2 x_r)
         w["name"] = w["name"].replace("multiclass", "histograms") + "-laplace"
         w["sigma"] = 8.0
+    elif args.feature_map == "fastfood":
+        w["name"] += "-fastfood"
     if args.loss != "squared":
         w["name"] += "-" + args.loss
     if args.block_fraction < 1.0:
@@ -460,6 +462,43 @@ def run_sweep(args):
             "clocks": clk.summary()}
 
 
+def run_score(args):
+    """Scoring latency of a resident model that keeps its feature parameters against one that
+    gave them back (rff_admm_release_features: each call draws G again from Philox): the
+    benchmark's d, D, m and grid, a model trained 3 iterations on 20,000 rows, batches of
+    1024 queries from host memory, 30 timed calls each after 3 warm-up calls."""
+    import numpy as np
+    import torch
+
+    import paper_1409_0940_gb300 as rff
+    w = dict(WORKLOAD)
+    w["n"] = 20_000
+    X, Y = make_data(w)
+    Xq = make_data(w, n=1024)[0]
+    stream = torch.cuda.Stream()
+    out = {}
+    for mode in ("resident", "released"):
+        s = new_solver(rff, w, args.prec, stream)
+        s.set_data(X, Y)
+        s.solve(3, stats=False)
+        freed = s.release_features() if mode == "released" else 0
+        for _ in range(3):
+            s.predict(Xq)
+        ts = []
+        for _ in range(30):
+            t0 = time.perf_counter()
+            s.predict(Xq)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        s.close()
+        out[mode] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+                     "bytes_freed": int(freed)}
+    return {"metric": "score latency p50", "value": out["released"]["p50_ms"], "unit": "ms", "n_gpus": 1,
+            "higher_is_better": False, "vs_baseline": None, "dtype": "f16x3" if args.prec != "fp32" else "f32",
+            "data": "synthetic",
+            "config": {"workload": "score-1024q-d440-D16384-m147", "prec": args.prec, "model_rows": w["n"]},
+            "resident": out["resident"], "released": out["released"]}
+
+
 def run_serve(args):
     """Serving: Poisson arrivals of solve requests (n log-uniform 5k..200k, d in 32..784,
     D in 1k..8k, loss in {squared, hinge, logistic}, reg in {l2, l1}) and scoring batches of
@@ -554,18 +593,19 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-compare", action="store_true", help="skip the other precisions (profiling runs)")
     ap.add_argument("--n", type=int, default=0, help="rows of a reduced workload (profiling runs)")
-    ap.add_argument("--workload", default="multiclass", choices=["multiclass", "ridge", "sweep", "serve"])
+    ap.add_argument("--workload", default="multiclass", choices=["multiclass", "ridge", "sweep", "serve", "score"])
     ap.add_argument("--loss", default="squared", choices=["squared", "hinge", "multinomial", "crammer_singer", "l1"],
                     help="loss of the multiclass workload")
-    ap.add_argument("--feature-map", default="fourier", choices=["fourier", "laplace"],
-                    help="laplace: random Laplace features on histogram inputs (fp32 or cached_z precision)")
+    ap.add_argument("--feature-map", default="fourier", choices=["fourier", "laplace", "fastfood"],
+                    help="laplace: random Laplace features on histogram inputs (fp32 or cached_z precision); "
+                         "fastfood: the structured Fastfood projection")
     ap.add_argument("--block-fraction", type=float, default=1.0,
                     help="stochastic variant: probability that a block takes part in an iteration")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.workload != "multiclass":
-        line = {"sweep": run_sweep, "serve": run_serve, "ridge": run_ridge}[args.workload](args)
+        line = {"sweep": run_sweep, "serve": run_serve, "ridge": run_ridge, "score": run_score}[args.workload](args)
         print(json.dumps(line), flush=True)
         return
     if args.impl == "reference":

@@ -191,6 +191,17 @@ rff_status rff_admm_estimate_bytes(const rff_admm_params* params, int64_t n, int
  * Errors: RFF_EINVAL for a wrong count or a non-positive value. */
 rff_status rff_admm_set_lambdas(rff_admm_t h, const double* lambdas, int32_t m);
 
+/* Give back the device copies of the feature parameters (G, or the Laplace W, or the
+ * Fastfood V, and their FP16 split): Sec. 4 keeps omega implicit as the state of the
+ * generator, regenerated on demand.  A resident model then holds no d x D parameters
+ * (2 d_pad D_slots x 2 B on the split path, 4 d_pad D_slots B on the FP32 path); each later
+ * rff_admm_predict draws them again for that call (a few hundred microseconds at
+ * d = 440, D = 16384) and gives them back, and rff_admm_solve keeps them resident again.
+ * The draw is bit-identical, so scores and iterates do not change.  *bytes (may be NULL)
+ * receives the bytes freed.  rff_admm_predict_noalloc refuses a released model
+ * (RFF_ENOTREADY).  Errors: RFF_ENOTREADY before the first solve. */
+rff_status rff_admm_release_features(rff_admm_t h, size_t* bytes);
+
 /* Stochastic block subsets (proposed in Sec. 5 and the conclusion): from the next
  * iteration on, each block (i, j) takes part in the graph projection of an iteration
  * with probability p, independently; the others keep their W'_ij and O'_ij for that

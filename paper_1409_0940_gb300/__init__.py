@@ -79,6 +79,7 @@ PROTOTYPES = {
                                        ctypes.POINTER(_SZ)]),
     "rff_admm_set_lambdas": (_I32, [_P, _P, _I32]),
     "rff_admm_set_block_fraction": (_I32, [_P, _D]),
+    "rff_admm_release_features": (_I32, [_P, ctypes.POINTER(_SZ)]),
     "rff_admm_enqueue": (_I32, [_P, _I32]),
     "rff_admm_wait": (_I32, [_P]),
     "rff_sweep_run": (_I32, [_P, _I32, _I32]),
@@ -411,6 +412,12 @@ def rff_admm_set_block_fraction(h, p):
     _check(lib.rff_admm_set_block_fraction(h, float(p)), h)
 
 
+def rff_admm_release_features(h):
+    n = _SZ(0)
+    _check(lib.rff_admm_release_features(h, ctypes.byref(n)), h)
+    return n.value
+
+
 class Solver:
     """Owns one rff_admm_t handle."""
 
@@ -447,6 +454,9 @@ class Solver:
 
     def set_block_fraction(self, p):
         rff_admm_set_block_fraction(self.h, p)
+
+    def release_features(self):
+        return rff_admm_release_features(self.h)
 
     def enqueue(self, iters):
         rff_admm_enqueue(self.h, iters)

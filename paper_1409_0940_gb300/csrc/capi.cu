@@ -89,6 +89,9 @@ struct rff_admm_s {
   int64_t* bctr = nullptr;    // the iteration number the next mask is drawn for (device)
   int64_t bctr_host = 0;
   bool stochastic() const { return bthr < (1u << 24); }
+  // the feature parameters' device copies (G or V or W, and their FP16 split) were given back:
+  // they are regenerated from Philox when next needed
+  bool features_released = false;
   const uint8_t* act() const { return stochastic() ? bmask : nullptr; }
   std::vector<double> lam_col;  // lambda of each output column (empty: params.lambda for all)
   float* lam_dev = nullptr;     // lambda_c / lambda per column (m_pad), or null
@@ -463,6 +466,7 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   h->free_all();
   CK(cudaStreamSynchronize(h->st));   // the freed blocks return to the device before it is measured
   h->has_data = h->factored = false;
+  h->features_released = false;
   h->iters_done = 0;
 
   auto& s = *h;
@@ -818,18 +822,70 @@ rff_status fastfood_features(rff_admm_t h) {
   return RFF_OK;
 }
 
+// Random features: G and b (or the Laplace map's W, or the Fastfood V) from Philox (Sec. 4),
+// into the handle's copies: FP32 where SIMT kernels read them, the FP16 split where the
+// tensor cores form X.G
+rff_status generate_features(rff_admm_t h) {
+  auto& s = *h;
+  if (s.p.feature_map == RFF_MAP_FASTFOOD) return fastfood_features(h);
+  const bool g16 = s.tc_scores();
+  CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, g16 ? s.Ghi : nullptr,
+                         g16 ? s.Glo : nullptr, s.gscale, s.bias, s.bias_col, s.st, s.p.feature_map));
+  return RFF_OK;
+}
+
+void free_buf(rff_admm_t h, void* p) {
+  for (size_t i = 0; i < h->bufs.size(); ++i)
+    if (h->bufs[i].p == p) {
+      cudaFreeAsync(p, h->st);
+      h->bufs.erase(h->bufs.begin() + (long)i);
+      return;
+    }
+}
+
+// Give back the feature parameters' copies (the paper keeps omega implicit as the state of
+// the generator, Sec. 4); *bytes receives what was freed
+rff_status release_features(rff_admm_t h, size_t* bytes) {
+  auto& s = *h;
+  size_t freed = 0;
+  if (!s.features_released) {
+    for (void* p : {(void*)s.Gt32, (void*)s.Ghi, (void*)s.Glo})
+      if (p) {
+        for (auto& b : s.bufs)
+          if (b.p == p) freed += b.bytes;
+        free_buf(h, p);
+      }
+    s.Gt32 = nullptr;
+    s.Ghi = s.Glo = nullptr;
+    s.features_released = true;
+    s.drop_graph();   // a captured iteration holds the old addresses
+  }
+  if (bytes) *bytes = freed;
+  return RFF_OK;
+}
+
+// Bring them back: allocate and draw again (bit-identical to the first draw)
+rff_status regenerate_features(rff_admm_t h) {
+  auto& s = *h;
+  if (!s.features_released) return RFF_OK;
+  rff_status st = RFF_OK;
+  if (s.split_path()) {
+    if ((st = dalloc(h, s.Ghi, (size_t)(s.fslots * s.dld))) != RFF_OK) return st;
+    if ((st = dalloc(h, s.Glo, (size_t)(s.fslots * s.dld))) != RFF_OK) return st;
+  }
+  if (!s.split_path() || s.cached_z())
+    if ((st = dalloc(h, s.Gt32, (size_t)(s.fslots * s.dld))) != RFF_OK) return st;
+  s.features_released = false;
+  s.drop_graph();
+  return generate_features(h);
+}
+
 rff_status setup_factors(rff_admm_t h) {
   auto& s = *h;
   const float scale = s.zmap_scale();
-  // random features: G and b (or the Laplace map's W) from Philox (Sec. 4); the FP16 copies
-  // only where the tensor cores form X.G
-  const bool g16 = s.tc_scores();
-  if (s.p.feature_map == RFF_MAP_FASTFOOD) {
-    rff_status r = fastfood_features(h);
+  {
+    rff_status r = generate_features(h);
     if (r != RFF_OK) return r;
-  } else {
-    CK(launch_params_slots(s.p.seed, s.p.sigma, s.d, s.dld, s.fslots, s.feat_of_slot, s.Gt32, g16 ? s.Ghi : nullptr,
-                           g16 ? s.Glo : nullptr, s.gscale, s.bias, s.bias_col, s.st, s.p.feature_map));
   }
   // Gram matrices H_ij = I + Z_ij^T Z_ij (eq. (cache)), or I + Z_ij Z_ij^T in the outer
   // form, in FP64, batched by memory
@@ -1291,6 +1347,10 @@ rff_status capture_iteration(rff_admm_t h) {
 // copy_old: keep nu, Obar, mu, Wbar, mu' of the iteration before the last (residuals).
 rff_status enqueue_iterations(rff_admm_t h, int iters, bool copy_old) {
   auto& s = *h;
+  if (s.features_released) {   // a solve keeps them resident again
+    rff_status r = regenerate_features(h);
+    if (r != RFF_OK) return r;
+  }
   const int64_t rowb = s.nslots * s.mpad * 4, colb = s.fslots * s.mpad * 4;
   const int base = s.pending_profiled;   // profiled iterations not yet accumulated
   if (s.profiling && (size_t)(base + iters) * 7 > s.ev.size()) {
@@ -1507,6 +1567,13 @@ rff_status rff_admm_estimate_bytes(const rff_admm_params* params, int64_t n, int
   return RFF_OK;
 }
 
+rff_status rff_admm_release_features(rff_admm_t h, size_t* bytes) {
+  if (!h) return RFF_EINVAL;
+  h->err.clear();
+  if (!h->has_data || !h->factored) return h->fail(RFF_ENOTREADY, "release_features needs a solve first");
+  return release_features(h, bytes);
+}
+
 rff_status rff_admm_set_block_fraction(rff_admm_t h, double p) {
   if (!h) return RFF_EINVAL;
   h->err.clear();
@@ -1582,6 +1649,13 @@ rff_status rff_admm_predict(rff_admm_t h, const float* Xq, int64_t q, float* sco
   if (q == 0) return RFF_OK;
   if (!Xq || !scores) return h->fail(RFF_EINVAL, "NULL pointer");
   auto& s = *h;
+  if (s.features_released) {   // regenerated for this call only, then given back again
+    rff_status r = regenerate_features(h);
+    if (r == RFF_OK) r = rff_admm_predict(h, Xq, q, scores, is_device_ptr);
+    size_t freed = 0;
+    release_features(h, &freed);
+    return r;
+  }
   const int64_t chunk = std::min<int64_t>(round_up(q, SLOT), 65536);
   const size_t need = (size_t)chunk * s.d * 4 + (size_t)chunk * s.dld * 4 + (size_t)chunk * s.dld * 2 * 2 +
                       (size_t)chunk * s.mpad * 4 + 4096;
@@ -1741,6 +1815,8 @@ rff_status predict_into_scratch(rff_admm_t h, const float* Xq, int64_t q, float*
   if (!h) return RFF_EINVAL;
   h->err.clear();
   if (!h->has_data || !h->factored) return h->fail(RFF_ENOTREADY, "predict needs a solve first");
+  if (h->features_released)
+    return h->fail(RFF_ENOTREADY, "the feature parameters were released; regenerating them allocates");
   if (q < 0) return h->fail(RFF_EINVAL, "q < 0");
   if (q == 0) return RFF_OK;
   if (!Xq || !scores || !scratch) return h->fail(RFF_EINVAL, "NULL pointer");
