@@ -155,6 +155,17 @@ rff_status rff_admm_create(const rff_admm_params* params, void* stream, rff_admm
 rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Y, int64_t n, int64_t d,
                              int is_device_ptr);
 
+/* As rff_admm_set_data with X in compressed sparse row form (Sec. 4: sparse inputs enter
+ * only through T): indptr (n + 1, int64, indptr[0] = 0, non-decreasing, indptr[n] = nnz),
+ * indices (nnz column indices in [0, d), int32), values (nnz float32).  Repeated columns
+ * of a row add up.  The rows are expanded into the dense slot layout on the device (the
+ * tensor cores take dense tiles: at the paper's 20 %-dense MNIST rows the dense product
+ * is the faster one), so only the sparse arrays cross from the host.  The same arrays
+ * go host -> device (is_device_ptr = 0) or stay on the device (1).  Errors: those of
+ * rff_admm_set_data, and RFF_EINVAL for a malformed structure. */
+rff_status rff_admm_set_data_csr(rff_admm_t h, const int64_t* indptr, const int32_t* indices, const float* values,
+                                 int64_t nnz, const float* Y, int64_t n, int64_t d, int is_device_ptr);
+
 /* Run `iters` further ADMM iterations (the update equations of Sec. 3 around
  * eq. (gp), all variables starting at zero after set_data).  The first call
  * after set_data first draws G and b (Sec. 4), forms each block's Gram matrix

@@ -65,6 +65,7 @@ _P, _I32, _I64, _U64, _D, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
 PROTOTYPES = {
     "rff_admm_create": (_I32, [ctypes.POINTER(rff_admm_params), _P, ctypes.POINTER(_P)]),
     "rff_admm_set_data": (_I32, [_P, _P, _P, _I64, _I64, ctypes.c_int]),
+    "rff_admm_set_data_csr": (_I32, [_P, _P, _P, _P, _I64, _P, _I64, _I64, ctypes.c_int]),
     "rff_admm_solve": (_I32, [_P, _I32, ctypes.POINTER(rff_admm_stats)]),
     "rff_admm_predict": (_I32, [_P, _P, _I64, _P, ctypes.c_int]),
     "rff_admm_predict_noalloc": (_I32, [_P, _P, _I64, _P]),
@@ -133,7 +134,7 @@ def _ptr(x, dtype=np.float32):
     if _is_torch_cuda(x) or type(x).__module__.startswith("torch"):
         import torch
         tdt = {np.float32: torch.float32, np.float64: torch.float64, np.uint32: torch.int32,
-               np.int32: torch.int32}[dtype]
+               np.int32: torch.int32, np.int64: torch.int64}[dtype]
         if x.dtype != tdt or not x.is_contiguous():
             raise TypeError("expected a contiguous %s tensor" % tdt)
         if x.is_cuda:
@@ -183,6 +184,18 @@ def rff_admm_set_data(h, X, Y):
     if dx != dy:
         raise TypeError("X and Y must both be host or both be device arrays")
     _check(lib.rff_admm_set_data(h, px, py, n, d, dx), h)
+
+
+def rff_admm_set_data_csr(h, indptr, indices, values, Y, d):
+    """X in CSR form: indptr (n + 1, int64), indices (int32), values (float32)."""
+    n = Y.shape[0]
+    pp, dp = _ptr(indptr, np.int64)
+    pi, di = _ptr(indices, np.int32)
+    pv, dv = _ptr(values, np.float32)
+    py, dy = _ptr(Y)
+    if len({dp, di, dv, dy}) != 1:
+        raise TypeError("the CSR arrays and Y must all be host or all be device arrays")
+    _check(lib.rff_admm_set_data_csr(h, pp, pi, pv, values.shape[0], py, n, d, dy), h)
 
 
 def rff_admm_solve(h, iters, stats=True):
@@ -429,6 +442,9 @@ class Solver:
 
     def set_data(self, X, Y):
         rff_admm_set_data(self.h, X, Y)
+
+    def set_data_csr(self, indptr, indices, values, Y, d):
+        rff_admm_set_data_csr(self.h, indptr, indices, values, Y, d)
 
     def solve(self, iters, stats=True):
         return rff_admm_solve(self.h, iters, stats)

@@ -454,11 +454,26 @@ void rff_admm_destroy(rff_admm_t h) {
 
 const char* rff_admm_last_error(rff_admm_t h) { return h ? h->err.c_str() : "null handle"; }
 
-rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int64_t n, int64_t d,
-                             int is_device_ptr) {
+}  // extern "C"
+
+namespace {
+// X as given by the caller: dense row-major n x d, or CSR (indptr n + 1, indices and values nnz)
+struct XInput {
+  const float* dense = nullptr;
+  const int64_t* indptr = nullptr;
+  const int32_t* indices = nullptr;
+  const float* values = nullptr;
+  int64_t nnz = 0;
+};
+
+rff_status set_data_impl(rff_admm_t h, const XInput& xin, const float* Yin, int64_t n, int64_t d,
+                         int is_device_ptr) {
   if (!h) return RFF_EINVAL;
   h->err.clear();
-  if (!X || !Yin) return h->fail(RFF_EINVAL, "X or Y is NULL");
+  const bool csr = xin.dense == nullptr;
+  if ((!csr && !xin.dense) || (csr && (!xin.indptr || (xin.nnz > 0 && (!xin.indices || !xin.values)))) || !Yin)
+    return h->fail(RFF_EINVAL, "X or Y is NULL");
+  if (csr && xin.nnz < 0) return h->fail(RFF_EINVAL, "nnz < 0");
   if (n < h->p.R || d < 1 || n > ((int64_t)1 << 31) - 1) return h->fail(RFF_EINVAL, "need R <= n < 2^31 and d >= 1");
   if (h->p.feature_map == RFF_MAP_FASTFOOD && d > 4096) return h->fail(RFF_EINVAL, "the Fastfood map takes d <= 4096");
   CK(cudaStreamSynchronize(h->st));
@@ -591,22 +606,39 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
     if (lr != RFF_OK) { h->free_all(); return lr; }
   }
 
-  // data: stage (device), validate, scatter into slots
-  const size_t xb = (size_t)n * d * 4, yb = (size_t)n * s.m * 4;
-  if ((st = ensure_scratch(h, xb + yb + 256)) != RFF_OK) { h->free_all(); return st; }
+  // data: stage (device), validate, scatter into slots.  Dense X is staged as n x d; CSR X as
+  // its three arrays (values first, so that the value checks run on one contiguous range)
+  const int64_t xcount = csr ? xin.nnz : (int64_t)n * d;   // the staged X values
+  const size_t xb = (size_t)xcount * 4, yb = (size_t)n * s.m * 4;
+  const size_t csrb = csr ? round_up((n + 1) * 8, 256) + round_up(xin.nnz * 4, 256) : 0;
+  const size_t slotb = (s.split_path() && !s.cached_z()) ? (size_t)s.nslots * s.dld * 4 : 0;
+  if ((st = ensure_scratch(h, round_up(xcount, 64) * 4 + round_up((int64_t)n * s.m, 64) * 4 + csrb + slotb + 1024)) !=
+      RFF_OK) {
+    h->free_all();
+    return st;
+  }
   float* sx = static_cast<float*>(h->scratch.p);
-  float* sy = sx + round_up((int64_t)n * d, 64);
+  float* sy = sx + round_up(xcount, 64);
+  char* cbase = reinterpret_cast<char*>(sy + round_up((int64_t)n * s.m, 64));
+  int64_t* sindptr = reinterpret_cast<int64_t*>(cbase);
+  int32_t* sindices = reinterpret_cast<int32_t*>(cbase + (csr ? round_up((n + 1) * 8, 256) : 0));
   const cudaMemcpyKind kind = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CK(cudaMemcpyAsync(sx, X, xb, kind, s.st));
+  if (xb) CK(cudaMemcpyAsync(sx, csr ? xin.values : xin.dense, xb, kind, s.st));
   CK(cudaMemcpyAsync(sy, Yin, yb, kind, s.st));
   CK(cudaMemsetAsync(s.flag, 0, 16, s.st));
-  CK(launch_finite_check(sx, (int64_t)n * d, s.p.feature_map == RFF_MAP_LAPLACE ? 2 : 0, s.flag, s.st,
+  if (csr) {
+    CK(cudaMemcpyAsync(sindptr, xin.indptr, (n + 1) * 8, kind, s.st));
+    if (xin.nnz) CK(cudaMemcpyAsync(sindices, xin.indices, xin.nnz * 4, kind, s.st));
+    CK(launch_csr_check(sindptr, sindices, n, d, xin.nnz, s.flag + 3, s.st));
+  }
+  CK(launch_finite_check(sx, xcount, s.p.feature_map == RFF_MAP_LAPLACE ? 2 : 0, s.flag, s.st,
                          reinterpret_cast<unsigned*>(s.flag + 2)));
   const int pm1 = (s.p.loss == RFF_LOSS_HINGE || s.p.loss == RFF_LOSS_LOGISTIC) ? 1 : 0;
   CK(launch_finite_check(sy, (int64_t)n * s.m, pm1, s.flag + 1, s.st));
-  int fl[3] = {0, 0, 0};
-  CK(cudaMemcpyAsync(fl, s.flag, 12, cudaMemcpyDeviceToHost, s.st));
+  int fl[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(fl, s.flag, 16, cudaMemcpyDeviceToHost, s.st));
   CK(cudaStreamSynchronize(s.st));
+  if (fl[3]) { h->free_all(); return h->fail(RFF_EINVAL, "CSR X: indptr not non-decreasing from 0 to nnz, or a column index outside [0, d)"); }
   {
     float xmax = 0.f;
     memcpy(&xmax, &fl[2], 4);
@@ -619,16 +651,12 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   if (fl[1] & 2) { h->free_all(); return h->fail(RFF_EINVAL, "hinge/logistic targets must be -1 or +1"); }
 
   float* Xs = s.X32;
-  if (s.split_path() && !s.cached_z()) {
-    // the float32 slot copy lives in scratch only long enough to split it
-    if ((st = ensure_scratch(h, xb + yb + (size_t)s.nslots * s.dld * 4 + 512)) != RFF_OK) { h->free_all(); return st; }
-    sx = static_cast<float*>(h->scratch.p);
-    sy = sx + round_up((int64_t)n * d, 64);
-    CK(cudaMemcpyAsync(sx, X, xb, kind, s.st));
-    CK(cudaMemcpyAsync(sy, Yin, yb, kind, s.st));
-    Xs = sy + round_up((int64_t)n * s.m, 64);
-  }
-  CK(launch_gather_rows(sx, d, d, s.row_of_slot, s.nslots, Xs, s.dld, s.st));
+  if (s.split_path() && !s.cached_z())   // the float32 slot copy lives in scratch only long enough to split it
+    Xs = reinterpret_cast<float*>(cbase + round_up(csrb, 256));
+  if (csr)
+    CK(launch_scatter_csr(sindptr, sindices, sx, s.row_of_slot, s.nslots, Xs, s.dld, s.st));
+  else
+    CK(launch_gather_rows(sx, d, d, s.row_of_slot, s.nslots, Xs, s.dld, s.st));
   CK(launch_gather_rows(sy, s.m, s.m, s.row_of_slot, s.nslots, s.Y, s.mpad, s.st));
   if (s.bias_col >= 0) CK(launch_set_column(Xs, s.dld, s.nslots, s.bias_col, 1.f, s.st));
   if (s.split_path()) CK(launch_split_f16(Xs, s.nslots * s.dld, s.xscale, s.Xhi, s.Xlo, s.st));
@@ -661,6 +689,26 @@ rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int
   CK(cudaStreamSynchronize(s.st));
   h->has_data = true;
   return RFF_OK;
+}
+}  // namespace
+
+extern "C" {
+rff_status rff_admm_set_data(rff_admm_t h, const float* X, const float* Yin, int64_t n, int64_t d,
+                             int is_device_ptr) {
+  XInput xin;
+  xin.dense = X;
+  if (!X) return h ? h->fail(RFF_EINVAL, "X or Y is NULL") : RFF_EINVAL;
+  return set_data_impl(h, xin, Yin, n, d, is_device_ptr);
+}
+
+rff_status rff_admm_set_data_csr(rff_admm_t h, const int64_t* indptr, const int32_t* indices, const float* values,
+                                 int64_t nnz, const float* Y, int64_t n, int64_t d, int is_device_ptr) {
+  XInput xin;
+  xin.indptr = indptr;
+  xin.indices = indices;
+  xin.values = values;
+  xin.nnz = nnz;
+  return set_data_impl(h, xin, Y, n, d, is_device_ptr);
 }
 
 }  // extern "C"

@@ -29,6 +29,29 @@ __global__ void k_scatter_rows(const float* __restrict__ src, int64_t lds, int64
   dst[t] = (g >= 0 && c < w) ? src[(int64_t)g * lds + c] : 0.f;
 }
 
+__global__ void k_csr_check(const int64_t* __restrict__ indptr, const int32_t* __restrict__ indices, int64_t n,
+                            int64_t d, int64_t nnz, int* __restrict__ flag) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int64_t a = indptr[r], b = indptr[r + 1];
+  bool bad = a < 0 || b < a || b > nnz || (r == 0 && a != 0) || (r == n - 1 && b != nnz);
+  if (!bad)
+    for (int64_t e = a; e < b; ++e)
+      if (indices[e] < 0 || indices[e] >= d) { bad = true; break; }
+  if (bad) atomicOr(flag, 1);
+}
+
+// one thread per slot row: its entries in order, so repeated columns add up deterministically
+__global__ void k_scatter_csr(const int64_t* __restrict__ indptr, const int32_t* __restrict__ indices,
+                              const float* __restrict__ values, const int32_t* __restrict__ map, int64_t nrows,
+                              float* __restrict__ dst, int64_t ld) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nrows) return;
+  const int32_t r = map[p];
+  if (r < 0) return;
+  for (int64_t e = indptr[r]; e < indptr[r + 1]; ++e) dst[p * ld + indices[e]] += values[e];
+}
+
 __global__ void k_set_column(float* __restrict__ X, int64_t ld, int64_t rows, int64_t col, float v) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r < rows) X[r * ld + col] = v;
@@ -683,6 +706,22 @@ cudaError_t launch_split_f16(const float* src, int64_t n, float scale, __half* h
 cudaError_t launch_split_bf16(const float* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_split<<<nblk(n), 256, 0, st>>>(src, n, hi, lo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_check(const int64_t* indptr, const int32_t* indices, int64_t n, int64_t d, int64_t nnz,
+                             int* flag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_csr_check<<<nblk(n), 256, 0, st>>>(indptr, indices, n, d, nnz, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_csr(const int64_t* indptr, const int32_t* indices, const float* values,
+                               const int32_t* map, int64_t nrows, float* dst, int64_t ld, cudaStream_t st) {
+  if (nrows <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(dst, 0, (size_t)nrows * ld * sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  k_scatter_csr<<<nblk(nrows), 256, 0, st>>>(indptr, indices, values, map, nrows, dst, ld);
   return cudaGetLastError();
 }
 

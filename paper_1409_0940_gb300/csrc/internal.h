@@ -141,6 +141,13 @@ cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, 
 cudaError_t launch_gather_rows(const float* src, int64_t lds, int64_t w, const int32_t* map, int64_t nrows,
                                float* dst, int64_t ld, cudaStream_t st);
 cudaError_t launch_set_column(float* X, int64_t ld, int64_t rows, int64_t col, float v, cudaStream_t st);
+// CSR structure check: *flag |= 1 unless indptr[0] = 0, indptr[n] = nnz, indptr non-decreasing
+// and every column index of a well-formed row in [0, d) (indices are read only for such rows)
+cudaError_t launch_csr_check(const int64_t* indptr, const int32_t* indices, int64_t n, int64_t d, int64_t nnz,
+                             int* flag, cudaStream_t st);
+// dst[p][c] = sum of the values of row map[p] in column c (CSR; map[p] < 0: zero row), ld >= d
+cudaError_t launch_scatter_csr(const int64_t* indptr, const int32_t* indices, const float* values,
+                               const int32_t* map, int64_t nrows, float* dst, int64_t ld, cudaStream_t st);
 cudaError_t launch_split_bf16(const float* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st);
 // hi/lo FP16 split of src * scale (scale a power of two)
 cudaError_t launch_split_f16(const float* src, int64_t n, float scale, __half* hi, __half* lo, cudaStream_t st);
