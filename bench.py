@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(name="multiclass-200k-d440-D16384-m147-4x4", n=200_000, d=440, m=147, sigma=10.0, D=16384, R=4,
                 C=4, loss="squared", reg="l2", lam=1e-5, rho=1.0, data_seed=1, philox_seed=2)
 METRIC = "ADMM iter/s"
-TRAFFIC_200K = {}     # kernel -> DRAM bytes per launch (see run_ours)
+TRAFFIC_200K = {"pass1": 1.646e9, "pass2": 1.187e9}     # kernel -> DRAM bytes per launch (see run_ours)
 
 
 def peaks():
