@@ -290,11 +290,12 @@ def run_ours(args, rank, world):
                 "kernel": ph[3:], "peak_source": src + " copy bandwidth", "tensor_tflops": achieved,
                 "tensor_frac": achieved / bf16_sus}
     else:
-        # FP32 SIMT: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (max boost)
-        alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        # FP32 SIMT: the measured FFMA throughput of this GPU (independent chains, one launch)
+        alu_peak, _ = rff.rff_measure_fma_peaks(stream.cuda_stream)
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": None, "kernel": ph[3:],
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"}
+                "peak_source": "measured FFMA chains (rff_measure_fma_peaks)",
+                "peak_derived": 152 * 128 * 2 * 2.07e9 / 1e12}
 
     value = job_throughput(args.steps, world, ms)
     line = {

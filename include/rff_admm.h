@@ -366,6 +366,11 @@ rff_status rff_laplace_features(const float* X, int64_t n, int64_t d, uint64_t s
 rff_status rff_fastfood_params(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t k_hi, float* Vt,
                                float* b, void* stream);
 
+/* Measured FMA throughput of this GPU's SIMT pipes in TFLOP/s (2 flop per FMA): FP32 and
+ * FP64, each from one timed launch of independent multiply-add chains (about 20 ms), the
+ * roofline denominators of the FP32 path and the set-up kernels.  Runs on stream. */
+rff_status rff_measure_fma_peaks(double* fp32_tflops, double* fp64_tflops, void* stream);
+
 /* Batched Cholesky factorisation in FP64 of `batch` SPD matrices (eq. (cache)):
  * A: batch x s x s row-major float64, overwritten by the lower factor L (upper
  * triangle zeroed).  info (device, batch int32): 0, or k+1 for a non-positive

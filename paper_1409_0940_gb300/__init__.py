@@ -81,6 +81,7 @@ PROTOTYPES = {
     "rff_admm_set_lambdas": (_I32, [_P, _P, _I32]),
     "rff_admm_set_block_fraction": (_I32, [_P, _D]),
     "rff_admm_release_features": (_I32, [_P, ctypes.POINTER(_SZ)]),
+    "rff_measure_fma_peaks": (_I32, [ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "rff_admm_enqueue": (_I32, [_P, _I32]),
     "rff_admm_wait": (_I32, [_P]),
     "rff_sweep_run": (_I32, [_P, _I32, _I32]),
@@ -423,6 +424,14 @@ def rff_server_destroy(srv):
 # ----------------------------------------------------------------- convenience
 def rff_admm_set_block_fraction(h, p):
     _check(lib.rff_admm_set_block_fraction(h, float(p)), h)
+
+
+def rff_measure_fma_peaks(stream=None):
+    """(FP32, FP64) FMA throughput of the GPU's SIMT pipes in TFLOP/s, measured."""
+    a, b = _D(0), _D(0)
+    _check(lib.rff_measure_fma_peaks(ctypes.byref(a), ctypes.byref(b), _stream(stream)), None,
+           "rff_measure_fma_peaks")
+    return a.value, b.value
 
 
 def rff_admm_release_features(h):

@@ -13,7 +13,11 @@ oracle.admm.admm runs the iterations.  About 10 minutes and 40 GB of host memory
 the whole Wbar (`fro`); the relative error on the sample estimates the relative error of
 the whole matrix.
 
-    python tests/golden/make_multiclass_reference.py
+With --stochastic the same workload runs the stochastic block-subset variant with half of
+the blocks active per iteration (block fraction 0.5, masks from Philox as oracle.admm
+draws them) and writes multiclass_200k_p05_wbar23_sample.npz.
+
+    python tests/golden/make_multiclass_reference.py [--stochastic]
 """
 import os
 import sys
@@ -29,7 +33,9 @@ from oracle import admm, philox, rff  # noqa: E402
 
 N, DIN, M, SIGMA, D, R, C, LAM, RHO, ITERS = 200_000, 440, 147, 10.0, 16384, 4, 4, 1e-5, 1.0, 23
 DATA_SEED, PHILOX_SEED = 1, 2
-OUT = os.path.join(HERE, "multiclass_200k_wbar23_sample.npz")
+FRACTION = 0.5 if "--stochastic" in sys.argv[1:] else 1.0
+OUT = os.path.join(HERE, "multiclass_200k_p05_wbar23_sample.npz" if FRACTION < 1.0 else
+                   "multiclass_200k_wbar23_sample.npz")
 SAMPLE, SAMPLE_SEED = 32768, 0
 
 
@@ -43,7 +49,7 @@ def main():
     print("Z %.0f s" % (time.time() - t0), flush=True)
     p = admm.Problem(X, Y, "squared", "l2", LAM, SIGMA, RHO, D, R, C, seed=PHILOX_SEED)
     p._Z = Z                       # the same matrix Problem.Z() would form, built in chunks
-    W = admm.admm(p, ITERS)["Wbar"]
+    W = admm.admm(p, ITERS, block_fraction=FRACTION)["Wbar"]
     idx = np.sort(np.random.default_rng(SAMPLE_SEED).choice(W.size, SAMPLE, replace=False)).astype(np.int64)
     np.savez(OUT, idx=idx, w=W.ravel()[idx], fro=np.linalg.norm(W))
     print("wrote %s (%.0f s)" % (OUT, time.time() - t0), flush=True)

@@ -50,3 +50,26 @@ def test_full_workload_matches_fp64_oracle(rff, data, prec):
     # the sample stands for the whole matrix: its norm scales with the sampled fraction
     frac = np.sqrt(ref["idx"].size / W.size)
     assert abs(np.linalg.norm(ref["w"]) / (float(ref["fro"]) * frac) - 1.0) < 0.1
+
+
+REF_P05 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "multiclass_200k_p05_wbar23_sample.npz")
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "cached_z"])
+def test_full_workload_stochastic_matches_fp64_oracle(rff, data, prec):
+    """The stochastic block-subset variant (half of the 16 blocks active per iteration) at the
+    full size, against the oracle's stochastic iterate (make_multiclass_reference.py
+    --stochastic): the same Philox masks on both sides."""
+    ref = np.load(REF_P05)
+    X, Y = data
+    s = rff.Solver(prec=prec, **KW)
+    s.set_block_fraction(0.5)
+    s.set_data(X, Y)
+    s.solve(23, stats=False)
+    W = s.weights().astype(np.float64).ravel()
+    s.close()
+    err = np.linalg.norm(W[ref["idx"]] - ref["w"]) / np.linalg.norm(ref["w"])
+    assert err < 1e-4, (prec, err)
+    # and it is a different iterate from the full method's
+    full = np.load(REF)
+    assert np.linalg.norm(ref["w"] - full["w"]) / np.linalg.norm(full["w"]) > 1e-2

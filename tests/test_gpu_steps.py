@@ -183,3 +183,13 @@ def test_cholesky_reports_non_positive_pivot(rff):
     info = torch.zeros(2, dtype=torch.int32, device="cuda")
     rff.rff_cholesky_f64(At, info)
     assert info.cpu().numpy().tolist() == [0, 71]
+
+
+# ----------------------------------------------------------------- measured SIMT peaks
+def test_fma_peaks_are_plausible(rff):
+    """FFMA and DFMA throughput from the library's own chains: FP32 between a quarter of and
+    just above the derived peak (152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s), FP64
+    far below FP32 on this part."""
+    fp32, fp64 = rff.rff_measure_fma_peaks()
+    assert 20.0 < fp32 < 1.1 * 80.5, fp32
+    assert 0.05 < fp64 < fp32 / 2, (fp32, fp64)
