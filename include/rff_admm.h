@@ -366,6 +366,13 @@ rff_status rff_laplace_features(const float* X, int64_t n, int64_t d, uint64_t s
 rff_status rff_fastfood_params(uint64_t seed, double sigma, int64_t d, int64_t k_lo, int64_t k_hi, float* Vt,
                                float* b, void* stream);
 
+/* Failure-path self test: launches a one-thread probe that waits, through the tensor-core
+ * passes' bounded wait, on an mbarrier nothing arrives on.  The wait gives up after about a
+ * millisecond, sets the device error word and returns, so the call returns RFF_ETIMEOUT (the
+ * status a timed-out pass reports) and clears the word; the context stays usable.  RFF_OK
+ * would mean the bound did not fire. */
+rff_status rff_selftest_wait_timeout(void* stream);
+
 /* Measured FMA throughput of this GPU's SIMT pipes in TFLOP/s (2 flop per FMA): FP32 and
  * FP64, each from one timed launch of independent multiply-add chains (about 20 ms), the
  * roofline denominators of the FP32 path and the set-up kernels.  Runs on stream. */

@@ -82,6 +82,7 @@ PROTOTYPES = {
     "rff_admm_set_block_fraction": (_I32, [_P, _D]),
     "rff_admm_release_features": (_I32, [_P, ctypes.POINTER(_SZ)]),
     "rff_measure_fma_peaks": (_I32, [ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
+    "rff_selftest_wait_timeout": (_I32, [_P]),
     "rff_admm_enqueue": (_I32, [_P, _I32]),
     "rff_admm_wait": (_I32, [_P]),
     "rff_sweep_run": (_I32, [_P, _I32, _I32]),
@@ -424,6 +425,11 @@ def rff_server_destroy(srv):
 # ----------------------------------------------------------------- convenience
 def rff_admm_set_block_fraction(h, p):
     _check(lib.rff_admm_set_block_fraction(h, float(p)), h)
+
+
+def rff_selftest_wait_timeout(stream=None):
+    """Status of the bounded-wait probe: RFF_ETIMEOUT when the bound fired (the expected outcome)."""
+    return lib.rff_selftest_wait_timeout(_stream(stream))
 
 
 def rff_measure_fma_peaks(stream=None):

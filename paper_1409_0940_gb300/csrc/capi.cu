@@ -1615,6 +1615,14 @@ rff_status rff_admm_estimate_bytes(const rff_admm_params* params, int64_t n, int
   return RFF_OK;
 }
 
+rff_status rff_selftest_wait_timeout(void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (tc_error_word() != 0) return RFF_ECUDA;   // a failure nobody has collected yet
+  if (tc_wait_probe(2000000, st) != cudaSuccess) return RFF_ECUDA;   // ~1 ms at the boost clock
+  if (cudaStreamSynchronize(st) != cudaSuccess) return RFF_ECUDA;
+  return tc_error_word() != 0 ? RFF_ETIMEOUT : RFF_OK;
+}
+
 rff_status rff_admm_release_features(rff_admm_t h, size_t* bytes) {
   if (!h) return RFF_EINVAL;
   h->err.clear();

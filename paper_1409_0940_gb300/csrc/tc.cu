@@ -155,6 +155,24 @@ __device__ __forceinline__ bool waitw(uint32_t bar, uint32_t parity, SH& sh, con
   return ok != 0;
 }
 
+// Failure-path probe: one thread waits, through the passes' own bounded wait, on an mbarrier
+// that nothing arrives on; the wait gives up after a.timeout_cycles, sets the error word and
+// the kernel returns (the context stays usable)
+struct ProbeShared {
+  uint64_t bar;
+  int abort_flag;
+};
+
+__global__ void k_wait_probe(const __grid_constant__ TcArgs a) {
+  __shared__ ProbeShared sh;
+  if (threadIdx.x == 0) {
+    sh.abort_flag = 0;
+    mbar_init(smem_u32(&sh.bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    wait1(smem_u32(&sh.bar), 0, sh, a, ERR_TIMEOUT_MMA);
+  }
+}
+
 template <int KC, int ZT>
 __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant__ TcArgs a) {
   using RG = Ring<KC, ZT>;
@@ -728,6 +746,16 @@ cudaError_t tc_make_map_bf16(CUtensorMap* m, const void* ptr, int64_t cols, int6
 }
 
 int* tc_error_ptr() { return err_word(); }
+
+cudaError_t tc_wait_probe(long long cycles, cudaStream_t st) {
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  a.err = err_word();
+  if (!a.err) return cudaErrorMemoryAllocation;
+  a.timeout_cycles = cycles;
+  k_wait_probe<<<1, 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
 
 int tc_error_word() {
   int h = 0;

@@ -89,5 +89,7 @@ cudaError_t launch_rhs_split3T(const float* Wbar, const float* muij, const float
 cudaError_t tc_make_map_bf16(CUtensorMap* m, const void* ptr, int64_t cols, int64_t rows, int64_t ld, int box_rows,
                              int kc);
 int* tc_error_ptr();
+// launch a probe whose bounded wait on a barrier nothing arrives on runs out after `cycles`
+cudaError_t tc_wait_probe(long long cycles, cudaStream_t st);
 
 }  // namespace rff

@@ -193,3 +193,18 @@ def test_fma_peaks_are_plausible(rff):
     fp32, fp64 = rff.rff_measure_fma_peaks()
     assert 20.0 < fp32 < 1.1 * 80.5, fp32
     assert 0.05 < fp64 < fp32 / 2, (fp32, fp64)
+
+
+# ----------------------------------------------------------------- failure path
+def test_bounded_wait_times_out_and_the_context_survives(rff):
+    """A wait that nothing ends (a probe on an mbarrier nobody arrives on) runs out after its
+    bound, reports RFF_ETIMEOUT through the device error word, and the GPU stays usable: the
+    tensor-core passes run and report success right after."""
+    assert rff.rff_selftest_wait_timeout() == rff.RFF_ETIMEOUT
+    X, Y = synth.ridge(n=600, d=6, seed=2)
+    s = rff.Solver(prec="split_bf16", loss="squared", reg="l2", lam=1e-3, sigma=2.0, D=256, R=2, C=2, seed=3, m=1)
+    s.set_data(X, Y)
+    st = s.solve(4)
+    assert np.isfinite(st["objective"])
+    s.close()
+    assert rff.rff_selftest_wait_timeout() == rff.RFF_ETIMEOUT   # and again
