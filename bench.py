@@ -457,12 +457,28 @@ def run_sweep(args):
         g["tc_kchunk"] = pr["tc_kchunk"]
         s.close()
     nsolve = len(w["sigmas"]) * len(w["lambdas"])
+    # executed tensor work of the two regeneration passes of every group per iteration:
+    # 3 x 2 n d_pad D (X.G, FP16 x3) + 3 x 2 n D m_pad (chained product), slot-padded sizes
+    mpad = -(-len(w["lambdas"]) // 16) * 16
+    dpad = -(-w["d"] // 64) * 64
+    flops = 0.0
+    for g in groups:
+        R = int(g["grid"].split("x")[0])
+        nslots = sum(-(-(g["n"] // R + (1 if i < g["n"] % R else 0)) // 128) * 128 for i in range(R))
+        flops += 2 * (3 * 2 * nslots * dpad * g["D"] + 3 * 2 * nslots * g["D"] * mpad)
+    tc_tflops = flops * args.steps / sec / 1e12
+    _, _, bf16_sus, src = peaks()
     return {"metric": "sweep solve-iterations/s", "value": nsolve * args.steps / sec, "unit": "solve-iter/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.prec == "fp32" else "f16x3", "data": "synthetic",
             "config": {"workload": w["name"], "solves": nsolve, "groups": groups, "prec": args.prec,
                        "timing": "host wall clock around rff_sweep_run (all streams drained)"},
+            "roofline": {"bound": "tensor", "achieved": tc_tflops, "peak": bf16_sus, "unit": "TFLOP/s",
+                         "frac": tc_tflops / bf16_sus, "traffic": None, "kernel": "k_regen_tc (all groups)",
+                         "peak_source": src + " sustained bf16",
+                         "note": "executed passes' tensor work over the whole sweep iteration (the other kernels "
+                                 "and the groups' overlap included in the time)"},
             "clocks": clk.summary()}
 
 
