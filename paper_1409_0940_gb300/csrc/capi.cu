@@ -359,8 +359,8 @@ void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
     int nsm = 148, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t tile = s.split_path() ? 128 : 64;
-    const int64_t ftiles = s.fslots / tile;
+    const int64_t tile = s.split_path() ? 128 : 64;   // pass-1 row step of a split
+    const int64_t ftiles = s.fslots / 128;             // pass-1 CTAs per row block and split
     int64_t min_rows = n;
     for (int i = 0; i < s.R; ++i) min_rows = std::min(min_rows, s.row_size[i]);
     int64_t want = ceil_div(2 * (int64_t)nsm, ftiles * s.R);
