@@ -243,6 +243,12 @@ rff_status rff_sweep_run(rff_admm_t* handles, int32_t n, int32_t iters);
  * the first solve, RFF_EINVAL for NaN/Inf queries. */
 rff_status rff_admm_predict(rff_admm_t h, const float* Xq, int64_t q, float* scores, int is_device_ptr);
 
+/* Class labels of q query rows (test accuracy, Sec. 5): m = 1: +1 where the score is >= 0,
+ * else -1; m > 1: the index of the largest score (the lowest index among equal scores).
+ * labels: q int32, host (is_device_ptr = 0, Xq host too) or device (1).  Errors: those of
+ * rff_admm_predict. */
+rff_status rff_admm_predict_labels(rff_admm_t h, const float* Xq, int64_t q, int32_t* labels, int is_device_ptr);
+
 /* Scores without allocating device memory (the paper has no counterpart: it is an
  * interface for callers that cannot call cudaMalloc when they score -- code being
  * captured into a CUDA graph, where allocation is not a capturable operation, and

@@ -69,6 +69,7 @@ PROTOTYPES = {
     "rff_admm_solve": (_I32, [_P, _I32, ctypes.POINTER(rff_admm_stats)]),
     "rff_admm_predict": (_I32, [_P, _P, _I64, _P, ctypes.c_int]),
     "rff_admm_predict_noalloc": (_I32, [_P, _P, _I64, _P]),
+    "rff_admm_predict_labels": (_I32, [_P, _P, _I64, _P, ctypes.c_int]),
     "rff_admm_get_weights": (_I32, [_P, _P, ctypes.c_int]),
     "rff_admm_get_state": (_I32, [_P, _P, ctypes.POINTER(_SZ)]),
     "rff_admm_set_state": (_I32, [_P, _P, _SZ]),
@@ -214,6 +215,15 @@ def rff_admm_predict(h, Xq, out):
     if dq != do:
         raise TypeError("Xq and scores must both be host or both be device arrays")
     _check(lib.rff_admm_predict(h, pq, Xq.shape[0], po, dq), h)
+    return out
+
+
+def rff_admm_predict_labels(h, Xq, out):
+    px, dx = _ptr(Xq)
+    po, do = _ptr(out, np.int32)
+    if dx != do:
+        raise TypeError("Xq and the labels must both be host or both be device arrays")
+    _check(lib.rff_admm_predict_labels(h, px, Xq.shape[0], po, dx), h)
     return out
 
 
@@ -468,6 +478,11 @@ class Solver:
         if out is None:
             out = np.empty((Xq.shape[0], self.m), dtype=np.float32)
         return rff_admm_predict(self.h, Xq, out)
+
+    def predict_labels(self, Xq, out=None):
+        if out is None:
+            out = np.empty(Xq.shape[0], dtype=np.int32)
+        return rff_admm_predict_labels(self.h, Xq, out)
 
     def weights(self, out=None):
         if out is None:

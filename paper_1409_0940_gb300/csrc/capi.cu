@@ -1615,6 +1615,41 @@ rff_status rff_admm_estimate_bytes(const rff_admm_params* params, int64_t n, int
   return RFF_OK;
 }
 
+rff_status rff_admm_predict_labels(rff_admm_t h, const float* Xq, int64_t q, int32_t* labels, int is_device_ptr) {
+  if (!h) return RFF_EINVAL;
+  h->err.clear();
+  if (q < 0) return h->fail(RFF_EINVAL, "q < 0");
+  if (q == 0) return RFF_OK;
+  if (!Xq || !labels) return h->fail(RFF_EINVAL, "NULL pointer");
+  auto& s = *h;
+  // scores into a stream-ordered temporary (device queries are read in place), then the labels
+  const size_t sb = round_up((size_t)q * s.m * 4, 256), lb = (size_t)q * 4;
+  char* tmp = nullptr;
+  if (cudaMallocAsync((void**)&tmp, sb + lb + (is_device_ptr ? 0 : (size_t)q * s.d * 4), s.st) != cudaSuccess) {
+    cudaGetLastError();
+    return h->fail(RFF_ENOMEM, "label scratch");
+  }
+  float* sc = reinterpret_cast<float*>(tmp);
+  int32_t* lab = reinterpret_cast<int32_t*>(tmp + sb);
+  const float* xq = Xq;
+  rff_status r = RFF_OK;
+  cudaError_t e = cudaSuccess;
+  if (!is_device_ptr) {
+    float* xd = reinterpret_cast<float*>(tmp + sb + lb);
+    e = cudaMemcpyAsync(xd, Xq, (size_t)q * s.d * 4, cudaMemcpyHostToDevice, s.st);
+    xq = xd;
+  }
+  if (e == cudaSuccess) r = rff_admm_predict(h, xq, q, sc, 1);
+  if (e == cudaSuccess && r == RFF_OK) e = launch_argmax_rows(sc, q, (int)s.m, s.m, lab, s.st);
+  if (e == cudaSuccess && r == RFF_OK)
+    e = cudaMemcpyAsync(labels, lab, lb, is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s.st);
+  cudaFreeAsync(tmp, s.st);
+  if (r != RFF_OK) return r;
+  if (e != cudaSuccess) return h->cuda_fail(e, "predict_labels");
+  return RFF_OK;
+}
+
 rff_status rff_selftest_wait_timeout(void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (tc_error_word() != 0) return RFF_ECUDA;   // a failure nobody has collected yet

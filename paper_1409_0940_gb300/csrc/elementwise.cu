@@ -129,7 +129,9 @@ __device__ __forceinline__ float warp_max(float x) {
 // a scalar equation solved by Newton from a Lambert-W estimate, and s is the
 // root of F(s) = sum_k p_k(s) - 1, which is convex and decreasing; Newton on s
 // from s0 = max_k w_k - t (where F >= 0) therefore rises monotonically to the
-// root.  Finally o = w - t p.
+// root.  Finally o = w - t p.  Only the first solve for each log p_k starts from the
+// estimate (four Newton steps); after each step ds of s it restarts from the first-order
+// update q - ds / (1 + t p) and takes two Newton steps.
 constexpr int MAXPL = 8;
 
 __device__ __forceinline__ float solve_logp(float a, float t, float logt) {
@@ -184,24 +186,50 @@ __device__ void prox_multinomial_row(const float (&v)[MAXPL], const float (&y)[M
   wmax = warp_max(wmax);
   const float logt = logf(t);
   float s = wmax - t;
+  float lq[MAXPL], pv[MAXPL];   // log p_k and p_k at the current s
+#pragma unroll
+  for (int q = 0; q < MAXPL; ++q) {
+    lq[q] = 0.f;
+    pv[q] = 0.f;
+    if (lane + 32 * q < m) {
+      lq[q] = solve_logp(w[q] - s, t, logt);
+      pv[q] = expf(lq[q]);
+    }
+  }
   for (int it = 0; it < iters; ++it) {
     float F = 0.f, dF = 0.f;
+    float rinv[MAXPL];
 #pragma unroll
     for (int q = 0; q < MAXPL; ++q) {
+      rinv[q] = 1.f / (1.f + t * pv[q]);
       if (lane + 32 * q < m) {
-        const float p = expf(solve_logp(w[q] - s, t, logt));
-        F += p;
-        dF += p / (1.f + t * p);
+        F += pv[q];
+        dF += pv[q] * rinv[q];
       }
     }
     F = warp_sum(F) - 1.f;
     dF = warp_sum(dF);
-    s += F / dF;
+    const float ds = F / dF;
+    s += ds;
+#pragma unroll
+    for (int q = 0; q < MAXPL; ++q) {
+      if (lane + 32 * q < m) {
+        const float a = w[q] - s;
+        float x = lq[q] - ds * rinv[q];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const float e = expf(x);
+          x -= (x + t * e - a) / (1.f + t * e);
+        }
+        lq[q] = x;
+        pv[q] = expf(x);
+      }
+    }
   }
 #pragma unroll
   for (int q = 0; q < MAXPL; ++q) {
     const int k = lane + 32 * q;
-    o[q] = (k < m) ? w[q] - t * expf(solve_logp(w[q] - s, t, logt)) : 0.f;
+    o[q] = (k < m) ? w[q] - t * pv[q] : 0.f;
   }
 }
 
@@ -851,6 +879,35 @@ cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cud
 cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, cudaStream_t st, unsigned* maxbits) {
   if (n <= 0) return cudaSuccess;
   k_finite<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4096), 256, 0, st>>>(x, n, pm1, flag, maxbits);
+  return cudaGetLastError();
+}
+
+// one warp per row: lane-strided maximum, then a butterfly keeping the lowest index on ties
+__global__ void k_argmax_rows(const float* __restrict__ S, int64_t q, int m, int64_t ld, int32_t* __restrict__ labels) {
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= q) return;
+  const float* s = S + row * ld;
+  if (m == 1) {
+    if (lane == 0) labels[row] = s[0] >= 0.f ? 1 : -1;
+    return;
+  }
+  float best = -INFINITY;
+  int bi = 1 << 30;
+  for (int k = lane; k < m; k += 32)
+    if (s[k] > best) { best = s[k]; bi = k; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (lane == 0) labels[row] = bi;
+}
+
+cudaError_t launch_argmax_rows(const float* scores, int64_t q, int m, int64_t ld, int32_t* labels, cudaStream_t st) {
+  if (q <= 0) return cudaSuccess;
+  k_argmax_rows<<<nblk(q * 32), 256, 0, st>>>(scores, q, m, ld, labels);
   return cudaGetLastError();
 }
 

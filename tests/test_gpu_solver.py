@@ -259,3 +259,27 @@ def test_outer_form_config3_shape(rff, config3_shape, prec):
     f_at_W = p.objective(np.asarray(W, np.float64))
     assert abs(st["objective"] - f_at_W) < PRECS[prec] * abs(f_at_W)
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_predict_labels(rff, prec):
+    """Labels decide on the GPU's own float32 scores: argmax with the lowest index among equal
+    scores (numpy's argmax returns the first maximum), or the sign for one output."""
+    X, Y = synth.multiclass(n=800, d=9, m=5, seed=6)
+    s = rff.Solver(prec=prec, loss="hinge", reg="l2", lam=1e-3, sigma=3.0, D=256, R=2, C=2, seed=4, m=5)
+    s.set_data(X, Y)
+    s.solve(10, stats=False)
+    Xq = np.random.default_rng(1).standard_normal((333, 9)).astype(np.float32)
+    scores = s.predict(Xq)
+    assert np.array_equal(s.predict_labels(Xq), np.argmax(scores, axis=1).astype(np.int32))
+    out = torch.zeros(333, dtype=torch.int32, device="cuda")
+    s.predict_labels(torch.from_numpy(Xq).cuda(), out)
+    assert np.array_equal(out.cpu().numpy(), np.argmax(scores, axis=1))
+    s.close()
+    Xb, yb = synth.binary(n=600, d=7, seed=2)
+    b = rff.Solver(prec=prec, loss="logistic", reg="l2", lam=1e-3, sigma=2.0, D=128, R=1, C=1, seed=1, m=1)
+    b.set_data(Xb, yb)
+    b.solve(8, stats=False)
+    sb = b.predict(Xb[:100])[:, 0]
+    assert np.array_equal(b.predict_labels(Xb[:100]), np.where(sb >= 0, 1, -1).astype(np.int32))
+    b.close()
