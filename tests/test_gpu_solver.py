@@ -283,3 +283,27 @@ def test_predict_labels(rff, prec):
     sb = b.predict(Xb[:100])[:, 0]
     assert np.array_equal(b.predict_labels(Xb[:100]), np.where(sb >= 0, 1, -1).astype(np.int32))
     b.close()
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("shape", [
+    # (n, d, m, D, R, C): one row per row block, one feature per column block, d = 1
+    (3, 1, 1, 2, 3, 2),
+    # a single feature, a single input dimension, many rows
+    (300, 1, 2, 1, 2, 1),
+    # blocks of 129 rows and 129 features: one full 128-slot tile plus one live row/feature
+    (258, 5, 3, 258, 2, 2),
+])
+def test_degenerate_shapes_match_oracle(rff, prec, shape):
+    n, d, m, D, R, C = shape
+    if prec == "cached_z" and D // C > n // R:
+        pytest.skip("the cached-Z precision takes the Gram form only")
+    rng = np.random.default_rng(n + D)
+    X = rng.random((n, d)).astype(np.float32)
+    Y = rng.standard_normal((n, m)).astype(np.float32)
+    p = admm.Problem(X, Y, "squared", "l2", 1e-3, 1.5, 1.0, D, R, C, seed=13)
+    out = admm.admm(p, 12)
+    s, st, W = run_gpu(rff, X, Y, 12, prec, loss="squared", reg="l2", lam=1e-3, sigma=1.5, rho=1.0, D=D, R=R, C=C,
+                       seed=13, m=m)
+    assert rel(W, out["Wbar"]) < PRECS[prec], rel(W, out["Wbar"])
+    s.close()
