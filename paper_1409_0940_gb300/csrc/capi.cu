@@ -388,12 +388,36 @@ void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
 
 // Bytes of set-up scratch for one block batch (FP64 Gram and inverse of `batch`
 // blocks, one materialised row chunk of Z, factorisation scratch).
+// Split-path Gram on the tensor cores (Gram form): per row chunk of Z, Z^T as a scaled FP16
+// hi/lo pair and 128 x 256 tiles of Z^T Z over 512-row pieces of K, GRAM_GROUP pieces per
+// launch, their partial tiles summed into H in FP64.
+constexpr int GRAM_KCH = 512, GRAM_GROUP = 8;
+
+int64_t tc_gram_tiles(int64_t smax, std::vector<int2>* out = nullptr) {
+  const int64_t spad = round_up(smax, 256);
+  int64_t n = 0;
+  for (int64_t a = 0; a < spad / 128; ++a)
+    for (int64_t b = 0; b * 256 <= a * 128 + 127 && b < spad / 256; ++b) {
+      if (out) out->push_back(make_int2((int)(a * 128), (int)(b * 256)));
+      ++n;
+    }
+  return n;
+}
+
+size_t tc_gram_bytes(int64_t chunk_rows, int64_t smax) {
+  const int64_t spad = round_up(smax, 256), kpad = round_up(chunk_rows, GRAM_KCH), nt = tc_gram_tiles(smax);
+  return round_up((size_t)spad * kpad * 2, 256) * 2 + (size_t)GRAM_GROUP * nt * 128 * 256 * 4 +
+         round_up((size_t)nt * sizeof(int2), 256) + round_up((size_t)GRAM_GROUP * nt * sizeof(SgJob), 256) + 1024;
+}
+
+bool tc_gram(const rff_admm_s& s) { return s.split_path() && !s.outer; }
+
 size_t setup_bytes(const rff_admm_s& s, int64_t batch) {
   int64_t smax = 0;
   for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
   const int64_t chunk_rows = std::min<int64_t>(32768, round_up(*std::max_element(s.row_size.begin(), s.row_size.end()), SLOT));
   return (size_t)batch * smax * smax * 8 * 2 + (size_t)chunk_rows * smax * 4 + factor_scratch_bytes((int)batch, (int)smax) +
-         (size_t)batch * 4 + 4096;
+         (size_t)batch * 4 + 4096 + (tc_gram(s) ? tc_gram_bytes(chunk_rows, smax) : 0);
 }
 
 }  // namespace
@@ -872,6 +896,72 @@ rff_status fastfood_features(rff_admm_t h) {
   return RFF_OK;
 }
 
+// H (s x s FP64, ld s) += Z^T Z for one row chunk Z (nr x s FP32, ld s) on the tensor cores:
+// Z^T split into scaled FP16 hi/lo (three products, the hi.hi ones in an accumulator of their
+// own), 128 x 256 tiles of the lower triangle over 512-row pieces of K (32 accumulations of
+// the dominant products per tile: the accumulator's round-toward-zero bias stays ~2e-6 of a
+// piece's sum), the pieces' tiles added in FP64 in order.  buf: tc_gram_bytes(chunk, smax).
+rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t sj, double* H, char* buf,
+                              int64_t chunk_rows, int64_t smax) {
+  auto& s = *h;
+  const int64_t spad = round_up(smax, 256), kpad = round_up(chunk_rows, GRAM_KCH);
+  std::vector<int2> tiles;
+  const int64_t nt = tc_gram_tiles(sj, &tiles);
+  const float zs = pow2_scale(std::sqrt(2.0 / (double)s.D));   // |Z| <= sqrt(2/D)
+  __half* hi = reinterpret_cast<__half*>(buf);
+  __half* lo = reinterpret_cast<__half*>(buf + round_up((size_t)spad * kpad * 2, 256));
+  float* P = reinterpret_cast<float*>(buf + 2 * round_up((size_t)spad * kpad * 2, 256));
+  int2* dtiles = reinterpret_cast<int2*>(reinterpret_cast<char*>(P) + (size_t)GRAM_GROUP * tc_gram_tiles(smax) * 128 * 256 * 4);
+  SgJob* djobs = reinterpret_cast<SgJob*>(reinterpret_cast<char*>(dtiles) + round_up((size_t)tc_gram_tiles(smax) * sizeof(int2), 256));
+  const int64_t kn = round_up(nr, GRAM_KCH);   // this chunk's K, zero-padded
+  CK(cudaMemsetAsync(hi, 0, (size_t)spad * kn * 2, s.st));
+  CK(cudaMemsetAsync(lo, 0, (size_t)spad * kn * 2, s.st));
+  CK(launch_transpose_split_f16(Zc, nr, (int)sj, 1, 0, hi, lo, kn, 0, zs, nullptr, s.st));
+  CK(cudaMemcpyAsync(dtiles, tiles.data(), nt * sizeof(int2), cudaMemcpyHostToDevice, s.st));
+  const int64_t npieces = kn / GRAM_KCH;
+  std::vector<SgJob> jobs;
+  for (int64_t g0 = 0; g0 < npieces; g0 += GRAM_GROUP) {
+    const int64_t g1 = std::min<int64_t>(npieces, g0 + GRAM_GROUP);
+    jobs.clear();
+    for (int64_t k = g0; k < g1; ++k)
+      for (int64_t t = 0; t < nt; ++t) {
+        SgJob jb{};
+        jb.a_row = tiles[t].x;
+        jb.a_k0 = (int32_t)(k * GRAM_KCH);
+        jb.b_row = tiles[t].y;
+        jb.b_k0 = jb.a_k0;
+        jb.nk = GRAM_KCH / 32;
+        jb.blk = 0;
+        jb.out = ((k - g0) * nt + t) * 128 * 256;
+        jobs.push_back(jb);
+      }
+    // the host vector is read by the copy: pageable memory is staged before the call returns
+    CK(cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(SgJob), cudaMemcpyHostToDevice, s.st));
+    SgView v{};
+    v.A[0] = hi;
+    v.A[1] = lo;
+    v.a_rows = spad;
+    v.a_cols = kn;
+    v.B[0] = hi;
+    v.B[1] = lo;
+    v.b_rows = spad;
+    v.b_cols = kn;
+    v.na = v.nb = 2;
+    v.f16 = 1;
+    v.jobs = djobs;
+    v.njobs = (int)jobs.size();
+    v.mpad = 256;
+    v.out = P;
+    v.out_scale = 1.f / (zs * zs);
+    v.two_acc = 1;
+    v.st = s.st;
+    CK(split_gemm(v));
+    CK(launch_gram_reduce(P, (int)(g1 - g0), (int)nt, dtiles, sj, H, sj, s.st));
+    CK(cudaStreamSynchronize(s.st));   // jobs and P are reused by the next group
+  }
+  return RFF_OK;
+}
+
 // Random features: G and b (or the Laplace map's W, or the Fastfood V) from Philox (Sec. 4),
 // into the handle's copies: FP32 where SIMT kernels read them, the FP16 split where the
 // tensor cores form X.G
@@ -950,7 +1040,8 @@ rff_status setup_factors(rff_admm_t h) {
   const int64_t chunk_rows = std::min<int64_t>(32768, round_up(nmax, SLOT));
   // outer form: Z_ij in chunks of feature columns, each transposed for the Gram kernel
   const int64_t chunk_feat = std::min<int64_t>(2048, round_up(smax, SLOT));
-  const size_t zbytes = s.outer ? (size_t)nmax * chunk_feat * 4 * 2 : (size_t)chunk_rows * smax * 4;
+  const size_t zbytes = (s.outer ? (size_t)nmax * chunk_feat * 4 * 2 : (size_t)chunk_rows * smax * 4) +
+                        (tc_gram(s) ? tc_gram_bytes(chunk_rows, smax) : 0);
   size_t budget = (size_t)(fr * 0.6);
   if (s.mem_limit) {
     const size_t ws = working_set_bytes(s);
@@ -966,6 +1057,9 @@ rff_status setup_factors(rff_admm_t h) {
   double* Q64 = H64 + batch * fmax * fmax;
   float* Zc = reinterpret_cast<float*>(Q64 + batch * fmax * fmax);
   float* Zt = Zc + (s.outer ? nmax * chunk_feat : 0);   // transposed chunk (outer form)
+  // tensor-core Gram buffers after the row chunk, on a 256-byte boundary (tc_gram_bytes keeps 1 KB of slack)
+  char* gbase = reinterpret_cast<char*>(
+      round_up((uintptr_t)(reinterpret_cast<char*>(Zc) + (size_t)chunk_rows * smax * 4), (uintptr_t)256));
   int32_t* info = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(Zc) + zbytes);
   void* fscr = reinterpret_cast<char*>(info) + round_up(batch * 4, 256);
 
@@ -1005,7 +1099,12 @@ rff_status setup_factors(rff_admm_t h) {
                    s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj, s.p.feature_map};
           CK(launch_write_z_simt(za, s.st));
         }
-        CK(launch_gram_f32_to_f64(Zc, sj, nr, sj, Hb, sj, s.st));
+        if (tc_gram(s)) {
+          rff_status gr = tc_gram_accumulate(h, Zc, nr, sj, Hb, gbase, chunk_rows, smax);
+          if (gr != RFF_OK) return gr;
+        } else {
+          CK(launch_gram_f32_to_f64(Zc, sj, nr, sj, Hb, sj, s.st));
+        }
       }
       CK(launch_add_identity_and_mirror(Hb, fd, fd, s.st));
       CK(cudaMemsetAsync(Qb, 0, fd * fd * 8, s.st));

@@ -882,6 +882,25 @@ cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, c
   return cudaGetLastError();
 }
 
+__global__ void k_gram_reduce(const float* __restrict__ P, int nchunk, int ntiles, const int2* __restrict__ tiles,
+                              int64_t s, double* __restrict__ H, int64_t ldh) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ntiles * 128 * 256) return;
+  const int tile = (int)(t / (128 * 256)), e = (int)(t % (128 * 256));
+  const int64_t row = tiles[tile].x + e / 256, col = tiles[tile].y + e % 256;
+  if (row >= s || col > row) return;
+  double v = 0.0;
+  for (int c = 0; c < nchunk; ++c) v += (double)P[((int64_t)c * ntiles + tile) * (128 * 256) + e];
+  H[row * ldh + col] += v;
+}
+
+cudaError_t launch_gram_reduce(const float* P, int nchunk, int ntiles, const int2* tiles, int64_t s, double* H,
+                               int64_t ldh, cudaStream_t st) {
+  if (ntiles <= 0 || nchunk <= 0) return cudaSuccess;
+  k_gram_reduce<<<nblk((int64_t)ntiles * 128 * 256), 256, 0, st>>>(P, nchunk, ntiles, tiles, s, H, ldh);
+  return cudaGetLastError();
+}
+
 // one warp per row: lane-strided maximum, then a butterfly keeping the lowest index on ties
 __global__ void k_argmax_rows(const float* __restrict__ S, int64_t q, int m, int64_t ld, int32_t* __restrict__ labels) {
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;

@@ -210,6 +210,11 @@ cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cud
 cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, cudaStream_t st,
                                 unsigned* maxbits = nullptr);
 cudaError_t launch_set_diag(double* A, int64_t ld, int64_t s, double v, cudaStream_t st);
+// H (FP64, ld ldh) += the sum over nchunk partial tiles (FP32, 128 x 256 each, chunk-major)
+// of the 128 x 256 tiles listed in tiles (first row, first column); entries at or below the
+// diagonal of the s x s matrix only; the chunks are added in order in FP64
+cudaError_t launch_gram_reduce(const float* P, int nchunk, int ntiles, const int2* tiles, int64_t s, double* H,
+                               int64_t ldh, cudaStream_t st);
 // labels of q rows of scores (ld columns, m used): m = 1: +1 if score >= 0 else -1;
 // m > 1: the index of the largest score, the lowest index among equal ones
 cudaError_t launch_argmax_rows(const float* scores, int64_t q, int m, int64_t ld, int32_t* labels, cudaStream_t st);
