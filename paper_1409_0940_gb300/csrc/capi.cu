@@ -1810,21 +1810,127 @@ rff_status rff_admm_wait(rff_admm_t h) {
   return finish_iterations(h);
 }
 
+}  // extern "C"
+
+namespace {
+// One iteration of every solve of a sweep as a single executable graph: from a fork on the
+// master stream each solve's iteration is captured on its own stream (its kernels form a branch
+// of the graph), and the branches join back on the master stream.  One graph launch then runs
+// one iteration of all solves, the branches side by side on the device.
+rff_status capture_sweep(rff_admm_t* hs, int32_t n, cudaStream_t master, cudaGraphExec_t* out) {
+  std::vector<cudaEvent_t> evs;
+  auto cleanup = [&]() {
+    for (auto e : evs) cudaEventDestroy(e);
+  };
+  cudaEvent_t fork = nullptr;
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return RFF_ECUDA;
+  evs.push_back(fork);
+  if (cudaStreamBeginCapture(master, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cleanup();
+    return RFF_ECUDA;
+  }
+  rff_status r = RFF_OK;
+  cudaError_t e = cudaEventRecord(fork, master);
+  for (int32_t k = 0; k < n && r == RFF_OK && e == cudaSuccess; ++k) {
+    rff_admm_t h = hs[k];
+    e = cudaStreamWaitEvent(h->st, fork, 0);
+    if (e != cudaSuccess) break;
+    const int64_t saved = h->launches;
+    r = iterate(h, 0);
+    h->launches = saved;
+    cudaEvent_t join = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (join) evs.push_back(join);
+    if (e == cudaSuccess) e = cudaEventRecord(join, h->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(master, join, 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(master, &g);
+  if (r == RFF_OK && (e != cudaSuccess || ee != cudaSuccess)) r = RFF_ECUDA;
+  if (r == RFF_OK && cudaGraphInstantiate(out, g, 0) != cudaSuccess) r = RFF_ECUDA;
+  if (g) cudaGraphDestroy(g);
+  cleanup();
+  cudaGetLastError();
+  return r;
+}
+}  // namespace
+
+extern "C" {
 rff_status rff_sweep_run(rff_admm_t* handles, int32_t n, int32_t iters) {
   if (n < 0 || iters < 0 || (n > 0 && !handles)) return RFF_EINVAL;
   for (int32_t k = 0; k < n; ++k)
     if (!handles[k] || !handles[k]->has_data) return RFF_EINVAL;
+  if (n == 0 || iters == 0) return RFF_OK;
   // set-up of every solve first (factors are computed once per handle) ...
   for (int32_t k = 0; k < n; ++k)
     if (!handles[k]->factored) {
       rff_status r = setup_factors(handles[k]);
       if (r != RFF_OK) return r;
     }
-  // ... then every solve's iterations are queued on its own stream and run side by side
+  // ... a first, eager iteration of the solves that have none (it also brings back released
+  // feature parameters and points the stochastic masks at the right iteration) ...
+  int32_t left = iters;
+  bool eager = false;
+  for (int32_t k = 0; k < n; ++k) eager = eager || handles[k]->iters_done == 0 || handles[k]->profiling ||
+                                          handles[k]->features_released;
   rff_status first = RFF_OK;
-  for (int32_t k = 0; k < n; ++k) {
-    rff_status r = enqueue_iterations(handles[k], iters, false);
-    if (r != RFF_OK && first == RFF_OK) first = r;
+  if (eager) {
+    for (int32_t k = 0; k < n; ++k) {
+      rff_status r = enqueue_iterations(handles[k], 1, false);
+      if (r != RFF_OK && first == RFF_OK) first = r;
+    }
+    --left;
+  }
+  // ... then the rest as one graph launch per iteration for all solves together
+  if (left > 0 && first == RFF_OK) {
+    bool profiling = false;
+    for (int32_t k = 0; k < n; ++k) profiling = profiling || handles[k]->profiling;
+    cudaStream_t master = nullptr;
+    cudaGraphExec_t gx = nullptr;
+    if (profiling || cudaStreamCreateWithFlags(&master, cudaStreamNonBlocking) != cudaSuccess) {
+      // per-phase events need eager launches: each solve on its own stream, side by side
+      cudaGetLastError();
+      for (int32_t k = 0; k < n; ++k) {
+        rff_status r = enqueue_iterations(handles[k], left, false);
+        if (r != RFF_OK && first == RFF_OK) first = r;
+      }
+    } else {
+      // every solve's pending work is ordered before the graph, and its stochastic masks
+      // continue from its own iteration count
+      cudaEvent_t ready = nullptr;
+      rff_status r = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess ? RFF_OK : RFF_ECUDA;
+      for (int32_t k = 0; k < n && r == RFF_OK; ++k) {
+        rff_admm_t h = handles[k];
+        if (h->stochastic()) {
+          h->bctr_host = h->iters_done;
+          if (cudaMemcpyAsync(h->bctr, &h->bctr_host, sizeof(int64_t), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            r = RFF_ECUDA;
+        }
+        if (r == RFF_OK && (cudaEventRecord(ready, h->st) != cudaSuccess ||
+                            cudaStreamWaitEvent(master, ready, 0) != cudaSuccess))
+          r = RFF_ECUDA;
+      }
+      if (ready) cudaEventDestroy(ready);
+      if (r == RFF_OK) r = capture_sweep(handles, n, master, &gx);
+      for (int32_t it = 0; it < left && r == RFF_OK; ++it)
+        if (cudaGraphLaunch(gx, master) != cudaSuccess) r = RFF_ECUDA;
+      // the solves' streams wait for the graph before their next work
+      cudaEvent_t done = nullptr;
+      if (r == RFF_OK && cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(done, master);
+        for (int32_t k = 0; k < n; ++k) cudaStreamWaitEvent(handles[k]->st, done, 0);
+        cudaEventDestroy(done);
+      }
+      if (r == RFF_OK)
+        for (int32_t k = 0; k < n; ++k) {
+          handles[k]->iters_done += left;
+          handles[k]->launches += (int64_t)left * iter_launches(*handles[k]);
+        }
+      cudaStreamSynchronize(master);
+      if (gx) cudaGraphExecDestroy(gx);
+      cudaStreamDestroy(master);
+      if (r != RFF_OK && first == RFF_OK) first = r;
+    }
   }
   for (int32_t k = 0; k < n; ++k) {
     rff_status r = rff_admm_wait(handles[k]);

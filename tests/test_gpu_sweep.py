@@ -121,3 +121,31 @@ def test_every_tile_geometry_gives_identical_results(rff, monkeypatch):
     for W, P in out[1:]:
         assert np.array_equal(W, out[0][0])
         assert np.array_equal(P, out[0][1])
+
+
+def test_sweep_graph_continues_and_keeps_masks(rff):
+    """Repeated sweep calls replay one graph for all solves (no eager iteration after the
+    first); a stochastic solve in the mix keeps drawing the masks of its own iterations."""
+    X, y = synth.binary(n=700, d=10, seed=5)
+    Y = np.ascontiguousarray(np.repeat(y, 2, axis=1))
+    specs = [dict(prec="split_bf16", sigma=2.0, D=256, R=2, C=2, seed=1, frac=None),
+             dict(prec="split_bf16", sigma=4.0, D=384, R=1, C=3, seed=2, frac=0.5),
+             dict(prec="fp32", sigma=1.0, D=128, R=2, C=1, seed=3, frac=None)]
+    alone, mixed = [], []
+    for sp in specs:
+        for bucket in (alone, mixed):
+            s = rff.Solver(prec=sp["prec"], loss="logistic", reg="l2", lam=1e-3, rho=1.0, sigma=sp["sigma"],
+                           D=sp["D"], R=sp["R"], C=sp["C"], seed=sp["seed"], m=2)
+            if sp["frac"]:
+                s.set_block_fraction(sp["frac"])
+            s.set_data(X, Y)
+            bucket.append(s)
+    for s in alone:
+        s.solve(6, stats=False)
+        s.solve(7, stats=False)
+    rff.rff_sweep_run([s.h for s in mixed], 6)
+    rff.rff_sweep_run([s.h for s in mixed], 7)
+    for a, b in zip(alone, mixed):
+        assert np.array_equal(a.weights(), b.weights())
+        a.close()
+        b.close()
