@@ -217,3 +217,29 @@ def test_stochastic_residuals_go_to_zero():
     p = admm.Problem(X, Y, "hinge", "l2", lam=1e-3, sigma=3.0, rho=1.0, D=64, R=2, C=2, seed=3)
     h = admm.admm(p, 1200, variant="reorganised", history=True, block_fraction=0.5)["history"]
     assert h[-1, 0] < 1e-2 * h[5, 0] and h[-1, 1] < 1e-2 * h[5, 1]
+
+
+def test_random_feature_ridge_tends_to_kernel_ridge():
+    """Sec. 2.2: with the exact kernel the minimiser is f(x) = sum_i alpha_i k(x, x_i),
+    (K + n lam I) alpha = Y (eq. (krr)); the random-feature ridge solution's predictions
+    approach it as D grows (error falling roughly like D^-1/2)."""
+    rng = np.random.default_rng(21)
+    X = rng.random((80, 3))
+    Y = np.sin(3 * X.sum(1, keepdims=True))
+    Xq = rng.random((40, 3))
+    sigma, lam, n = 0.7, 1e-3, 80
+    alpha = np.linalg.solve(rff.gaussian_kernel(X, X, sigma) + n * lam * np.eye(n), Y)
+    f_krr = rff.gaussian_kernel(Xq, X, sigma) @ alpha
+    errs = []
+    Ds = [256, 1024, 4096, 16384]
+    for D in Ds:
+        e = []
+        for seed in range(3):
+            Z = rff.features_block(X, 40 + seed, sigma, D, 0, D)
+            # (Z^T Z + n lam I)^-1 Z^T Y = Z^T (Z Z^T + n lam I)^-1 Y: the n x n form, same W
+            W = Z.T @ np.linalg.solve(Z @ Z.T + n * lam * np.eye(n), Y)
+            e.append(np.abs(rff.features_block(Xq, 40 + seed, sigma, D, 0, D) @ W - f_krr).mean())
+        errs.append(np.mean(e))
+    slope = np.polyfit(np.log(Ds), np.log(errs), 1)[0]
+    assert errs[-1] < 0.25 * errs[0]
+    assert -0.8 < slope < -0.25, (slope, errs)
