@@ -47,7 +47,8 @@ typedef enum {
   RFF_ECUDA = 3,     /* a CUDA runtime call failed                                  */
   RFF_ETIMEOUT = 4,  /* a device-side bounded wait gave up                          */
   RFF_ENOTREADY = 5, /* no data set, or no solve yet                                */
-  RFF_ENUMERIC = 6   /* a factorisation met a non-positive pivot                    */
+  RFF_ENUMERIC = 6,  /* a factorisation met a non-positive pivot                    */
+  RFF_ECANCELLED = 7 /* a serving request cancelled before it started               */
 } rff_status;
 
 /* Losses V(y, o), used only through their proximal operators (Sec. 3 "Modularity"). */
@@ -432,6 +433,11 @@ rff_status rff_server_poll(rff_server_t srv, rff_completion* out, int32_t max, i
 
 /* Weights of a solved model (host, D x m), as rff_admm_get_weights. */
 rff_status rff_server_get_weights(rff_server_t srv, int64_t model, float* W);
+
+/* Cancel a request that has not started: it leaves the queue and completes at once with
+ * status RFF_ECANCELLED (a score waiting for a cancelled solve then fails with RFF_EINVAL).
+ * Returns RFF_ENOTREADY for a request that is running or done, RFF_EINVAL for an unknown id. */
+rff_status rff_server_cancel(rff_server_t srv, int64_t request_id);
 
 /* Drop a solved (or failed) model and give its memory back to the budget. */
 rff_status rff_server_release(rff_server_t srv, int64_t model);

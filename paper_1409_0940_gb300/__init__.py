@@ -15,9 +15,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librff_admm.so")
 
-RFF_OK, RFF_EINVAL, RFF_ENOMEM, RFF_ECUDA, RFF_ETIMEOUT, RFF_ENOTREADY, RFF_ENUMERIC = range(7)
+RFF_OK, RFF_EINVAL, RFF_ENOMEM, RFF_ECUDA, RFF_ETIMEOUT, RFF_ENOTREADY, RFF_ENUMERIC, RFF_ECANCELLED = range(8)
 _STATUS = {0: "RFF_OK", 1: "RFF_EINVAL", 2: "RFF_ENOMEM", 3: "RFF_ECUDA", 4: "RFF_ETIMEOUT",
-           5: "RFF_ENOTREADY", 6: "RFF_ENUMERIC"}
+           5: "RFF_ENOTREADY", 6: "RFF_ENUMERIC", 7: "RFF_ECANCELLED"}
 LOSSES = {"squared": 0, "hinge": 1, "logistic": 2, "multinomial": 3, "l1": 4, "crammer_singer": 5}
 FEATURE_MAPS = {"fourier": 0, "laplace": 1, "fastfood": 2}
 REGS = {"l2": 0, "l1": 1}
@@ -105,6 +105,7 @@ PROTOTYPES = {
     "rff_server_poll": (_I32, [_P, ctypes.POINTER(rff_completion), _I32, ctypes.POINTER(_I32), _I32]),
     "rff_server_get_weights": (_I32, [_P, _I64, _P]),
     "rff_server_release": (_I32, [_P, _I64]),
+    "rff_server_cancel": (_I32, [_P, _I64]),
     "rff_server_memory": (_I32, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
     "rff_server_destroy": (None, [_P]),
 }
@@ -420,6 +421,16 @@ def rff_server_get_weights(srv, model, out):
 
 def rff_server_release(srv, model):
     _check(lib.rff_server_release(srv, model), None, "rff_server_release")
+
+
+def rff_server_cancel(srv, request_id):
+    """True if the request left the queue (it completes with RFF_ECANCELLED), False if it had
+    already started or finished."""
+    st = lib.rff_server_cancel(srv, request_id)
+    if st == RFF_ENOTREADY:
+        return False
+    _check(st, None, "rff_server_cancel")
+    return True
 
 
 def rff_server_memory(srv):

@@ -221,6 +221,24 @@ rff_status rff_server_create(size_t budget_bytes, int32_t max_active, rff_server
   return RFF_OK;
 }
 
+rff_status rff_server_cancel(rff_server_t srv, int64_t request_id) {
+  if (!srv) return RFF_EINVAL;
+  std::unique_ptr<Request> r;
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    for (auto it = srv->queue.begin(); it != srv->queue.end(); ++it)
+      if ((*it)->id == request_id) {
+        r = std::move(*it);
+        srv->queue.erase(it);
+        break;
+      }
+    if (!r) return (request_id >= 1 && request_id < srv->next_id) ? RFF_ENOTREADY : RFF_EINVAL;
+    srv->cv_work.notify_all();   // a score that waited on this solve can now be taken (and fail)
+  }
+  srv->complete(*r, RFF_ECANCELLED, Clock::now());
+  return RFF_OK;
+}
+
 rff_status rff_server_submit_solve(rff_server_t srv, const rff_admm_params* params, const float* X, const float* Y,
                                    int64_t n, int64_t d, int32_t iters, int64_t* request_id) {
   if (!srv || !params || !X || !Y || iters < 0) return RFF_EINVAL;

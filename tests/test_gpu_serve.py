@@ -122,3 +122,31 @@ def test_refusals(rff):
     with pytest.raises(rff.RffError):
         rff.rff_server_submit_score(srv, 12345, X[:3], np.empty((3, 10), np.float32))
     rff.rff_server_destroy(srv)
+
+
+def test_cancel_queued_request(rff):
+    """With one worker busy on a long solve, a queued solve and the score waiting for it can be
+    cancelled: the solve completes at once with RFF_ECANCELLED, the score then fails, and the
+    running solve cannot be cancelled and finishes normally."""
+    srv = rff.rff_server_create(0, 1)
+    XA, YA = synth.multiclass(n=20000, d=32, m=3, seed=3)
+    XB, YB = synth.binary(n=2000, d=16, seed=4)
+    a = rff.rff_server_submit_solve(srv, rff.make_params(loss="hinge", prec="fp32", D=4096, R=2, C=2, m=3,
+                                                         sigma=3.0, lam=1e-3), XA, YA, 300)
+    b = rff.rff_server_submit_solve(srv, rff.make_params(loss="hinge", D=256, R=1, C=1, m=1, sigma=3.0,
+                                                         lam=1e-3), XB, YB, 5)
+    out = np.full((7, 1), np.nan, dtype=np.float32)
+    sc = rff.rff_server_submit_score(srv, b, XB[:7], out)
+    assert rff.rff_server_cancel(srv, b)
+    assert not rff.rff_server_cancel(srv, b)          # already completed (cancelled)
+    with pytest.raises(rff.RffError) as e:
+        rff.rff_server_cancel(srv, 10 ** 9)
+    assert e.value.status == rff.RFF_EINVAL
+    got = _wait_all(rff, srv, [a, b, sc])
+    assert got[b]["status"] == rff.RFF_ECANCELLED
+    assert got[sc]["status"] == rff.RFF_EINVAL and np.isnan(out).all()
+    assert got[a]["status"] == rff.RFF_OK
+    assert not rff.rff_server_cancel(srv, a)          # done
+    with pytest.raises(rff.RffError):
+        rff.rff_server_get_weights(srv, b, np.empty((256, 1), np.float32))
+    rff.rff_server_destroy(srv)
