@@ -380,6 +380,23 @@ rff_status rff_fastfood_params(uint64_t seed, double sigma, int64_t d, int64_t k
  * would mean the bound did not fire. */
 rff_status rff_selftest_wait_timeout(void* stream);
 
+/* Bounds-checked build.  The library is also built with device-side bounds checks
+ * (librff_admm_check.so, compiled with -DRFF_CHECK): the kernels of the iteration and of
+ * scoring test, at their global accesses, that every element index lies inside the layout
+ * the operation defines (the regeneration passes' X, G, chained-operand and output tiles, the
+ * tensor-core epilogues' output rows, the exchange's row tiles, the sparse scatter's column
+ * indices) and that every TMA box starts on a 16-byte boundary; a failed test skips the
+ * access and is counted.  rff_check_enabled() is 1 in that build and 0 in the ordinary one.
+ * rff_check_report synchronises the device and reads and clears the counts into out[5]:
+ *   out[0]  failed tests since the last report (0 in the ordinary build),
+ *   out[1]  source unit of the first failure: 1 elementwise.cu, 2 qgemm.cu, 3 regen_simt.cu,
+ *           4 tc.cu,
+ *   out[2]  its source line, out[3] the index tested, out[4] the bound it broke.
+ * A skipped TMA copy leaves its barrier incomplete: the bounded wait on it gives up and the
+ * pass returns RFF_ETIMEOUT.  Returns RFF_ECUDA if the device reports an error. */
+int32_t rff_check_enabled(void);
+rff_status rff_check_report(int64_t* out);
+
 /* Measured FMA throughput of this GPU's SIMT pipes in TFLOP/s (2 flop per FMA): FP32 and
  * FP64, each from one timed launch of independent multiply-add chains (about 20 ms), the
  * roofline denominators of the FP32 path and the set-up kernels.  Runs on stream. */

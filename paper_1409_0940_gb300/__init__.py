@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librff_admm.so")
+# RFF_ADMM_CHECK=1 loads the bounds-checked build of the library (built by build(check=True))
+CHECKED = os.environ.get("RFF_ADMM_CHECK") == "1"
+LIB_PATH = os.path.join(_HERE, "librff_admm_check.so" if CHECKED else "librff_admm.so")
 
 RFF_OK, RFF_EINVAL, RFF_ENOMEM, RFF_ECUDA, RFF_ETIMEOUT, RFF_ENOTREADY, RFF_ENUMERIC, RFF_ECANCELLED = range(8)
 _STATUS = {0: "RFF_OK", 1: "RFF_EINVAL", 2: "RFF_ENOMEM", 3: "RFF_ECUDA", 4: "RFF_ETIMEOUT",
@@ -106,6 +108,8 @@ PROTOTYPES = {
     "rff_server_get_weights": (_I32, [_P, _I64, _P]),
     "rff_server_release": (_I32, [_P, _I64]),
     "rff_server_cancel": (_I32, [_P, _I64]),
+    "rff_check_enabled": (_I32, []),
+    "rff_check_report": (_I32, [_P]),
     "rff_server_memory": (_I32, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
     "rff_server_destroy": (None, [_P]),
 }
@@ -113,8 +117,9 @@ PROTOTYPES = {
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError("librff_admm.so is not built; run paper_1409_0940_gb300.build.build() "
-                          "(needs nvcc) -- there is no CPU fallback")
+        raise ImportError("%s is not built; run paper_1409_0940_gb300.build.build(%s) "
+                          "(needs nvcc) -- there is no CPU fallback"
+                          % (os.path.basename(LIB_PATH), "check=True" if CHECKED else ""))
     lib = ctypes.CDLL(LIB_PATH)
     for name, (res, args) in PROTOTYPES.items():
         fn = getattr(lib, name)
@@ -431,6 +436,17 @@ def rff_server_cancel(srv, request_id):
         return False
     _check(st, None, "rff_server_cancel")
     return True
+
+
+def rff_check_enabled():
+    return bool(lib.rff_check_enabled())
+
+
+def rff_check_report():
+    """Failed bounds checks since the last report: dict(count, unit, line, index, bound)."""
+    out = (ctypes.c_int64 * 5)()
+    _check(lib.rff_check_report(out), None, "rff_check_report")
+    return dict(zip(("count", "unit", "line", "index", "bound"), list(out)))
 
 
 def rff_server_memory(srv):

@@ -2,7 +2,8 @@
 
 Each translation unit under csrc/ is compiled in parallel with nvcc into
 _build/, then linked into librff_admm.so beside this file.  Objects are reused
-while they are newer than every source and header.
+while they are newer than every source and header.  build(check=True) builds the
+bounds-checked variant instead (-DRFF_CHECK: _build_check/, librff_admm_check.so).
 """
 import concurrent.futures as cf
 import glob
@@ -34,19 +35,23 @@ def _newest_dep():
     return max((os.path.getmtime(p) for p in deps), default=0.0)
 
 
-def build(verbose=False, force=False):
-    """Compile every .cu under csrc/ and link librff_admm.so; returns its path."""
+def build(verbose=False, force=False, check=False):
+    """Compile every .cu under csrc/ and link librff_admm.so (librff_admm_check.so with the
+    device-side bounds checks); returns its path."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD + "_check" if check else BUILD
+    lib = LIB[:-3] + "_check.so" if check else LIB
+    flags = NVFLAGS + (["-DRFF_CHECK"] if check else [])
+    os.makedirs(build_dir, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_time = _newest_dep()
     jobs = []
     objs = []
     for src in sources:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_time):
-            jobs.append([nvcc] + NVFLAGS + ["-c", src, "-o", obj])
+            jobs.append([nvcc] + flags + ["-c", src, "-o", obj])
 
     def run(cmd):
         if verbose:
@@ -59,9 +64,9 @@ def build(verbose=False, force=False):
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        run([nvcc] + ARCH + ["-shared", "-o", LIB] + objs)
-    return LIB
+    if jobs or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        run([nvcc] + ARCH + ["-shared", "-o", lib] + objs)
+    return lib
 
 
 if __name__ == "__main__":

@@ -147,6 +147,7 @@ struct rff_admm_s {
     return (float)(p.feature_map == RFF_MAP_LAPLACE ? 1.0 / std::sqrt((double)D) : std::sqrt(2.0 / (double)D));
   }
   bool cached_z() const { return p.prec == RFF_PREC_CACHED_Z; }
+  int64_t rpart_elems() const { return (int64_t)std::max(nsplit_max, nsplit_cz) * R * fslots * mpad; }
 };
 
 namespace rff {
@@ -742,7 +743,8 @@ namespace {
 
 // Tile-shape autotuner of the tensor-core passes: times pass 1 + pass 2 for each
 // ring geometry (K chunk 64 or 32, Z tile in shared or tensor memory) on the
-// handle's own data and keeps the fastest.  All geometries issue the same MMAs in
+// handle's own data, restricted to the first row block (a quarter of the work on a
+// 4 x 4 grid: still several waves of both passes), and keeps the fastest.  All geometries issue the same MMAs in
 // the same order, so the choice
 // changes speed, never results (a run is reproducible whatever the timing).  The
 // passes only write their scratch outputs (R partials, O'), which every
@@ -775,10 +777,13 @@ rff_status autotune(rff_admm_t h) {
       s.tc_zt = zt;
       s.nsplit = ns;
       float ms = 0.f;
+      TcView tv = tc_view(s);
+      tv.R = 1;
+      tv.row_tiles = ceil_div(s.row_size[0], 128);
       for (int rep = warm ? 1 : 0; rep < 2; ++rep) {   // one untimed run warms caches and descriptors
         CK(cudaEventRecord(e0, s.st));
-        CK(tc_pass1(tc_view(s), s.Rpart));
-        CK(tc_pass2(tc_view(s), s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + AMAX_W));
+        CK(tc_pass1(tv, s.Rpart));
+        CK(tc_pass2(tv, s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + AMAX_W));
         CK(cudaEventRecord(e1, s.st));
         CK(cudaEventSynchronize(e1));
         CK(cudaEventElapsedTime(&ms, e0, e1));
@@ -901,8 +906,11 @@ rff_status fastfood_features(rff_admm_t h) {
 // own), 128 x 256 tiles of the lower triangle over 512-row pieces of K (32 accumulations of
 // the dominant products per tile: the accumulator's round-toward-zero bias stays ~2e-6 of a
 // piece's sum), the pieces' tiles added in FP64 in order.  buf: tc_gram_bytes(chunk, smax).
+// With Zc null the chunk is regenerated straight into that split by the tensor-core write mode
+// (rows zr0.., features zf0.. of the view zv), with the same roundings as splitting the FP32 Z.
 rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t sj, double* H, char* buf,
-                              int64_t chunk_rows, int64_t smax) {
+                              int64_t chunk_rows, int64_t smax, const TcView* zv = nullptr, int64_t zr0 = 0,
+                              int64_t zf0 = 0) {
   auto& s = *h;
   const int64_t spad = round_up(smax, 256), kpad = round_up(chunk_rows, GRAM_KCH);
   std::vector<int2> tiles;
@@ -916,7 +924,10 @@ rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t
   const int64_t kn = round_up(nr, GRAM_KCH);   // this chunk's K, zero-padded
   CK(cudaMemsetAsync(hi, 0, (size_t)spad * kn * 2, s.st));
   CK(cudaMemsetAsync(lo, 0, (size_t)spad * kn * 2, s.st));
-  CK(launch_transpose_split_f16(Zc, nr, (int)sj, 1, 0, hi, lo, kn, 0, zs, nullptr, s.st));
+  if (Zc)
+    CK(launch_transpose_split_f16(Zc, nr, (int)sj, 1, 0, hi, lo, kn, 0, zs, nullptr, s.st));
+  else
+    CK(tc_write_zt_split(*zv, zr0, nr, zf0, sj, zs, hi, lo, kn));
   CK(cudaMemcpyAsync(dtiles, tiles.data(), nt * sizeof(int2), cudaMemcpyHostToDevice, s.st));
   const int64_t npieces = kn / GRAM_KCH;
   std::vector<SgJob> jobs;
@@ -952,6 +963,7 @@ rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t
     v.njobs = (int)jobs.size();
     v.mpad = 256;
     v.out = P;
+    v.out_elems = (int64_t)GRAM_GROUP * tc_gram_tiles(smax) * 128 * 256;
     v.out_scale = 1.f / (zs * zs);
     v.two_acc = 1;
     v.st = s.st;
@@ -1092,6 +1104,13 @@ rff_status setup_factors(rff_admm_t h) {
       }
       for (int64_t r = 0; !s.outer && r < s.row_size[i]; r += chunk_rows) {
         const int64_t nr = std::min(chunk_rows, s.row_size[i] - r);
+        if (tc_gram(s) && !s.cached_z()) {   // Z^T's split written by the regeneration itself
+          const TcView zv = tc_view(s);
+          rff_status gr = tc_gram_accumulate(h, nullptr, nr, sj, Hb, gbase, chunk_rows, smax, &zv,
+                                             s.row_slot[i] + r, s.col_slot[j]);
+          if (gr != RFF_OK) return gr;
+          continue;
+        }
         if (s.split_path() && !s.cached_z()) {
           CK(tc_write_z(tc_view(s), s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj));
         } else {
@@ -1196,6 +1215,8 @@ PassArgs base_pass_args(const rff_admm_s& s) {
   a.C = s.C;
   a.mpad = (int)s.mpad;
   a.nsplit = s.nsplit;
+  a.x_rows = s.nslots;
+  a.g_rows = s.fslots;
   return a;
 }
 
@@ -1218,6 +1239,7 @@ SgView qgemm_view(const rff_admm_s& s) {
   v.njobs = s.nqjobs;
   v.mpad = (int)s.mpad;
   v.out = s.What;
+  v.out_elems = (int64_t)s.R * s.fslots * s.mpad;
   v.out_scale = 1.f;
   v.amax = s.amax + AMAX_W;
   v.two_acc = 1;
@@ -1244,6 +1266,7 @@ SgView cz_pass1_view(const rff_admm_s& s) {
   v.njobs = s.np1;
   v.mpad = (int)s.mpad;
   v.out = s.Rpart;
+  v.out_elems = s.rpart_elems();
   v.out_scale = 1.f / s.zscale;
   v.b_amax = s.amax;
   v.smem_budget = 110 * 1024;   // two CTAs per SM: one's epilogue overlaps the other's stream
@@ -1269,6 +1292,7 @@ SgView cz_pass2_view(const rff_admm_s& s) {
   v.njobs = s.np2;
   v.mpad = (int)s.mpad;
   v.out = s.Op;
+  v.out_elems = (int64_t)s.C * s.nslots * s.mpad;
   v.out_scale = 1.f / s.zscale;
   v.b_amax = s.amax + AMAX_W;
   v.amax = s.amax + AMAX_OP;
@@ -1348,8 +1372,10 @@ rff_status iterate_outer(rff_admm_t h, int k) {
   } else {
     a.M = s.V32;
     a.m_block_stride = s.nslots * s.mpad;
+    a.m_elems = (int64_t)s.C * s.nslots * s.mpad;
     a.out = s.Rpart;
     a.out_block_stride = nfe;
+    a.out_elems = s.rpart_elems();
     CK(launch_pass1_simt(a, s.fslots, s.st));
   }
   if ((r = mark(h, k, 2)) != RFF_OK) return r;
@@ -1366,8 +1392,10 @@ rff_status iterate_outer(rff_admm_t h, int k) {
     b.bmask = s.act();
     b.M = s.rhs;
     b.m_block_stride = nfe;
+    b.m_elems = (int64_t)s.R * nfe;
     b.out = s.U32;
     b.out_block_stride = s.nslots * s.mpad;
+    b.out_elems = (int64_t)s.C * s.nslots * s.mpad;
     b.per_block = 1;
     CK(launch_pass2_simt(b, s.nslots, s.st));
   }
@@ -1386,6 +1414,7 @@ rff_status iterate_outer(rff_admm_t h, int k) {
     CK(tc_pass1(vo, s.Rpart));
   } else {
     a.M = s.Op;
+    a.m_elems = (int64_t)s.C * s.nslots * s.mpad;
     CK(launch_pass1_simt(a, s.fslots, s.st));
   }
   CK(launch_sub_partials(s.rhs, s.Rpart, s.nsplit, s.R, nfe, s.feat_of_slot, (int)s.mpad, s.What, s.st, s.act(),
@@ -1422,8 +1451,10 @@ rff_status iterate(rff_admm_t h, int k) {
   } else {
     a.M = s.V32;
     a.m_block_stride = s.nslots * s.mpad;
+    a.m_elems = (int64_t)s.C * s.nslots * s.mpad;
     a.out = s.Rpart;
     a.out_block_stride = s.fslots * s.mpad;
+    a.out_elems = s.rpart_elems();
     CK(launch_pass1_simt(a, s.fslots, s.st));
   }
   if ((r = mark(h, k, 2)) != RFF_OK) return r;
@@ -1453,8 +1484,10 @@ rff_status iterate(rff_admm_t h, int k) {
   } else {
     a.M = s.What;
     a.m_block_stride = s.fslots * s.mpad;
+    a.m_elems = (int64_t)s.R * s.fslots * s.mpad;
     a.out = s.Op;
     a.out_block_stride = s.nslots * s.mpad;
+    a.out_elems = (int64_t)s.C * s.nslots * s.mpad;
     a.per_block = 1;
     CK(launch_pass2_simt(a, s.nslots, s.st));
   }
@@ -1587,8 +1620,11 @@ rff_status scores_pass(rff_admm_t h, const float* Xrows32, const __half* Xh, con
     a.R = 1;
     a.M = s.Wbar;
     a.m_block_stride = 0;
+    a.m_elems = s.fslots * s.mpad;
+    a.x_rows = nrows;
     a.out = out;
     a.out_block_stride = 0;
+    a.out_elems = nrows * s.mpad;
     a.per_block = 0;
     CK(launch_pass2_simt(a, nrows, s.st));
   }
@@ -1748,6 +1784,42 @@ rff_status rff_admm_predict_labels(rff_admm_t h, const float* Xq, int64_t q, int
   cudaFreeAsync(tmp, s.st);
   if (r != RFF_OK) return r;
   if (e != cudaSuccess) return h->cuda_fail(e, "predict_labels");
+  return RFF_OK;
+}
+
+int32_t rff_check_enabled(void) {
+#ifdef RFF_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+rff_status rff_check_report(int64_t* out) {
+  if (!out) return RFF_EINVAL;
+  for (int k = 0; k < 5; ++k) out[k] = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return RFF_ECUDA;
+  }
+  // the units in the order of their numbers in the report
+  cudaError_t (*const units[])(CheckHit*) = {check_collect_elementwise, check_collect_qgemm,
+                                             check_collect_regen_simt, check_collect_tc};
+  for (int u = 0; u < 4; ++u) {
+    CheckHit hit{};
+    if (units[u](&hit) != cudaSuccess) {
+      cudaGetLastError();
+      return RFF_ECUDA;
+    }
+    if (hit.count == 0) continue;
+    if (out[0] == 0) {
+      out[1] = u + 1;
+      out[2] = hit.line;
+      out[3] = hit.index;
+      out[4] = hit.bound;
+    }
+    out[0] += (int64_t)hit.count;
+  }
   return RFF_OK;
 }
 

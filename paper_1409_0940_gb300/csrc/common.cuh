@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "check.cuh"
+
 namespace rff {
 
 // Rows and features live in "slot" space: every row block i (Sec. 3, n_i rows)

@@ -49,7 +49,8 @@ __global__ void k_scatter_csr(const int64_t* __restrict__ indptr, const int32_t*
   if (p >= nrows) return;
   const int32_t r = map[p];
   if (r < 0) return;
-  for (int64_t e = indptr[r]; e < indptr[r + 1]; ++e) dst[p * ld + indices[e]] += values[e];
+  for (int64_t e = indptr[r]; e < indptr[r + 1]; ++e)
+    if (RFF_IN(indices[e], ld)) dst[p * ld + indices[e]] += values[e];
 }
 
 __global__ void k_set_column(float* __restrict__ X, int64_t ld, int64_t rows, int64_t col, float v) {
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
   float omax = 0.f, numax = 0.f;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int64_t p0 = (int64_t)blockIdx.x * EX_ROWS;
+  if (!RFF_SPAN(p0, EX_ROWS, a.nslots)) return;
   const int64_t jstride = a.nslots * mp;
   const float inv_c1 = 1.f / (float)(a.C + 1);
   const float cfrac = (float)a.C * inv_c1;
@@ -882,22 +884,53 @@ cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, c
   return cudaGetLastError();
 }
 
+// Four consecutive columns per thread: the pieces' float4 loads are all issued before the
+// sums (which keep the pieces' order), and H is updated by two double2 read-modify-writes
+// where the row's address allows it.
+constexpr int GRAM_PIECES_MAX = 8;
+
 __global__ void k_gram_reduce(const float* __restrict__ P, int nchunk, int ntiles, const int2* __restrict__ tiles,
                               int64_t s, double* __restrict__ H, int64_t ldh) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)ntiles * 128 * 256) return;
-  const int tile = (int)(t / (128 * 256)), e = (int)(t % (128 * 256));
+  if (t >= (int64_t)ntiles * 128 * 64) return;
+  const int tile = (int)(t / (128 * 64)), e = (int)(t % (128 * 64)) * 4;
   const int64_t row = tiles[tile].x + e / 256, col = tiles[tile].y + e % 256;
   if (row >= s || col > row) return;
-  double v = 0.0;
-  for (int c = 0; c < nchunk; ++c) v += (double)P[((int64_t)c * ntiles + tile) * (128 * 256) + e];
-  H[row * ldh + col] += v;
+  float4 p[GRAM_PIECES_MAX];
+#pragma unroll
+  for (int c = 0; c < GRAM_PIECES_MAX; ++c)
+    if (c < nchunk) p[c] = *reinterpret_cast<const float4*>(P + ((int64_t)c * ntiles + tile) * (128 * 256) + e);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int c = 0; c < GRAM_PIECES_MAX; ++c)
+    if (c < nchunk) {
+      v[0] += (double)p[c].x;
+      v[1] += (double)p[c].y;
+      v[2] += (double)p[c].z;
+      v[3] += (double)p[c].w;
+    }
+  double* h = H + row * ldh + col;
+  if (col + 3 <= row && ((row * ldh + col) & 1) == 0) {
+    double2* h2 = reinterpret_cast<double2*>(h);
+    double2 a = h2[0], b = h2[1];
+    a.x += v[0];
+    a.y += v[1];
+    b.x += v[2];
+    b.y += v[3];
+    h2[0] = a;
+    h2[1] = b;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (col + q <= row) h[q] += v[q];
+  }
 }
 
 cudaError_t launch_gram_reduce(const float* P, int nchunk, int ntiles, const int2* tiles, int64_t s, double* H,
                                int64_t ldh, cudaStream_t st) {
   if (ntiles <= 0 || nchunk <= 0) return cudaSuccess;
-  k_gram_reduce<<<nblk((int64_t)ntiles * 128 * 256), 256, 0, st>>>(P, nchunk, ntiles, tiles, s, H, ldh);
+  if (nchunk > GRAM_PIECES_MAX) return cudaErrorInvalidValue;
+  k_gram_reduce<<<nblk((int64_t)ntiles * 128 * 64), 256, 0, st>>>(P, nchunk, ntiles, tiles, s, H, ldh);
   return cudaGetLastError();
 }
 
@@ -935,5 +968,7 @@ cudaError_t launch_set_diag(double* A, int64_t ld, int64_t s, double v, cudaStre
   k_set_diag<<<nblk(s), 256, 0, st>>>(A, ld, s, v);
   return cudaGetLastError();
 }
+
+RFF_CHECK_UNIT(elementwise)
 
 }  // namespace rff

@@ -10,6 +10,13 @@ namespace rff {
 
 // Arguments of the fused regeneration passes (SIMT and tensor-core versions).
 // Row-side arrays are indexed by row slot, feature-side arrays by feature slot.
+// read and clear the bounds-check record of each checked translation unit (zeros in the
+// ordinary build)
+cudaError_t check_collect_elementwise(CheckHit* h);
+cudaError_t check_collect_qgemm(CheckHit* h);
+cudaError_t check_collect_regen_simt(CheckHit* h);
+cudaError_t check_collect_tc(CheckHit* h);
+
 struct PassArgs {
   const float* X;        // data rows (slots) x K, float32            (SIMT)
   int64_t ldx;
@@ -35,6 +42,8 @@ struct PassArgs {
   int per_block;            // pass 2: write per column block (1) or once (0)
   const uint8_t* bmask;     // device, R x C: active blocks of a stochastic iteration, or null
   int map;                  // feature map: 1 random Laplace (exp(-T)); else cos(T + b) (Fourier, Fastfood)
+  // extents, tested by the bounds-checked build: rows of X and of Gt, elements of M and of out
+  int64_t x_rows, g_rows, m_elems, out_elems;
 };
 
 struct ZArgs {
@@ -212,7 +221,7 @@ cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, c
 cudaError_t launch_set_diag(double* A, int64_t ld, int64_t s, double v, cudaStream_t st);
 // H (FP64, ld ldh) += the sum over nchunk partial tiles (FP32, 128 x 256 each, chunk-major)
 // of the 128 x 256 tiles listed in tiles (first row, first column); entries at or below the
-// diagonal of the s x s matrix only; the chunks are added in order in FP64
+// diagonal of the s x s matrix only; the chunks (at most 8) are added in order in FP64
 cudaError_t launch_gram_reduce(const float* P, int nchunk, int ntiles, const int2* tiles, int64_t s, double* H,
                                int64_t ldh, cudaStream_t st);
 // labels of q rows of scores (ld columns, m used): m = 1: +1 if score >= 0 else -1;

@@ -49,6 +49,7 @@ struct QArgs {
   uint32_t acc_b;            // column of the second accumulator (the small products), 0 = one accumulator
   const SgJob* jobs;
   float* out;
+  int64_t out_elems;
   float out_scale;
   const unsigned* b_amax;
   unsigned* amax;
@@ -200,8 +201,10 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
           mx = fmaxf(mx, fabsf(x[t]));
         }
         float4* dst = reinterpret_cast<float4*>(orow_p + c);
-        dst[0] = make_float4(x[0], x[1], x[2], x[3]);
-        dst[1] = make_float4(x[4], x[5], x[6], x[7]);
+        if (RFF_SPAN(job.out + (int64_t)row * a.mpad + c, 8, a.out_elems)) {
+          dst[0] = make_float4(x[0], x[1], x[2], x[3]);
+          dst[1] = make_float4(x[4], x[5], x[6], x[7]);
+        }
       }
       if (a.amax) {
 #pragma unroll
@@ -236,7 +239,8 @@ __global__ void k_rhs_split3T(const float* __restrict__ Wbar, const float* __res
     if (p < fslots && c < mpad && feat_ok[p] >= 0) {
       const int64_t e = p * mpad + c, t = (int64_t)i * nfe + e;
       v = Wbar[e] - muij[t];
-      for (int sp = 0; sp < nsplit; ++sp) v += Rpart[(int64_t)sp * R * nfe + t];
+      for (int sp = 0; sp < nsplit; ++sp)
+        if (RFF_IN((int64_t)sp * R * nfe + t, (int64_t)nsplit * R * nfe)) v += Rpart[(int64_t)sp * R * nfe + t];
     }
     tile[rr][tx] = v;
   }
@@ -251,6 +255,7 @@ __global__ void k_rhs_split3T(const float* __restrict__ Wbar, const float* __res
       const __nv_bfloat16 m = __float2bfloat16_rn(rem);
       const __nv_bfloat16 l = __float2bfloat16_rn(rem - __bfloat162float(m));
       const int64_t o = ((int64_t)i * mpad + c) * fslots + p;
+      if (!RFF_IN(o, (int64_t)R * mpad * fslots)) continue;
       r1[o] = h;
       r2[o] = m;
       r3[o] = l;
@@ -332,6 +337,7 @@ cudaError_t split_gemm(const SgView& v) {
   }
   a.jobs = v.jobs;
   a.out = v.out;
+  a.out_elems = v.out_elems;
   a.out_scale = v.out_scale;
   a.b_amax = v.b_amax;
   a.amax = v.amax;
@@ -349,5 +355,7 @@ cudaError_t split_gemm(const SgView& v) {
   }
   return cudaGetLastError();
 }
+
+RFF_CHECK_UNIT(qgemm)
 
 }  // namespace rff

@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(NT, 1) k_pass2_simt(PassArgs p) {
   while (rb + 1 < p.R && p.row_slot[rb + 1] <= a0) ++rb;
   const uint8_t* act = p.bmask ? p.bmask + rb * p.C : nullptr;   // skip inactive blocks (per_block)
   const float* M = p.M + rb * p.m_block_stride;
+  if (!RFF_SPAN(a0, BM, p.x_rows)) return;
   float acc2[8][MQ];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -187,14 +188,17 @@ __global__ void __launch_bounds__(NT, 1) k_pass2_simt(PassArgs p) {
     if (act && !act[j]) continue;
     const int64_t f0 = p.col_slot[j], f1 = f0 + p.col_size[j];
     for (int64_t b0 = f0; b0 < f1; b0 += BN) {
+      if (!RFF_SPAN(b0, BN, p.g_rows) || !RFF_SPAN(rb * p.m_block_stride + b0 * p.mpad, BN * p.mpad, p.m_elems))
+        return;
       tile_z(sm, p.X, p.ldx, a0, p.Gt, p.ldg, b0, p.K, p.bias, false, p.scale, p.row_ok, p.feat_ok, p.map);
       load_M(Ms, M, b0, p.mpad);
       __syncthreads();
       chain<MQ>(sm, Ms, p.mpad, acc2);
     }
-    if (p.per_block) store_acc<MQ>(acc2, p.out + j * p.out_block_stride, a0, p.mpad);
+    if (p.per_block && RFF_SPAN(j * p.out_block_stride + a0 * p.mpad, BM * p.mpad, p.out_elems))
+      store_acc<MQ>(acc2, p.out + j * p.out_block_stride, a0, p.mpad);
   }
-  if (!p.per_block) store_acc<MQ>(acc2, p.out, a0, p.mpad);
+  if (!p.per_block && RFF_SPAN(a0 * p.mpad, BM * p.mpad, p.out_elems)) store_acc<MQ>(acc2, p.out, a0, p.mpad);
 }
 
 // Pass 1: one CTA per (128 feature slots, row block i, row split); runs over the
@@ -214,6 +218,7 @@ __global__ void __launch_bounds__(NT, 1) k_pass1_simt(PassArgs p) {
   const int64_t r0 = p.row_slot[i], nsteps = ceil_div(p.row_size[i], BN);
   const int64_t t0 = split * nsteps / p.nsplit, t1 = (split + 1) * nsteps / p.nsplit;
   const float* M = p.M + j * p.m_block_stride;
+  if (!RFF_SPAN(a0, BM, p.g_rows)) return;
   float acc2[8][MQ];
 #pragma unroll
   for (int ii = 0; ii < 8; ++ii)
@@ -221,12 +226,15 @@ __global__ void __launch_bounds__(NT, 1) k_pass1_simt(PassArgs p) {
     for (int q = 0; q < MQ; ++q) acc2[ii][q] = 0.f;
   for (int64_t t = t0; t < t1; ++t) {
     const int64_t b0 = r0 + t * BN;
+    if (!RFF_SPAN(b0, BN, p.x_rows) || !RFF_SPAN(j * p.m_block_stride + b0 * p.mpad, BN * p.mpad, p.m_elems))
+      return;
     tile_z(sm, p.Gt, p.ldg, a0, p.X, p.ldx, b0, p.K, p.bias, true, p.scale, p.feat_ok, p.row_ok, p.map);
     load_M(Ms, M, b0, p.mpad);
     __syncthreads();
     chain<MQ>(sm, Ms, p.mpad, acc2);
   }
-  store_acc<MQ>(acc2, p.out + ((int64_t)split * p.R + i) * p.out_block_stride, a0, p.mpad);
+  const int64_t o = ((int64_t)split * p.R + i) * p.out_block_stride;
+  if (RFF_SPAN(o + a0 * p.mpad, BM * p.mpad, p.out_elems)) store_acc<MQ>(acc2, p.out + o, a0, p.mpad);
 }
 
 // Materialise Z for rows [r0, r0 + nr) and feature slots [f0, f0 + nf) into
@@ -291,5 +299,7 @@ cudaError_t launch_write_z_simt(const ZArgs& p, cudaStream_t st) {
   k_write_z_simt<<<grid, NT, smem, st>>>(p);
   return cudaGetLastError();
 }
+
+RFF_CHECK_UNIT(regen_simt)
 
 }  // namespace rff

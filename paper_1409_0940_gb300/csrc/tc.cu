@@ -93,8 +93,11 @@ struct TcArgs {
   const int64_t* col_size;
   int64_t fslots;
   float* out;
+  int64_t out_elems;                        // elements of out's layout (checked in bounds-checked builds)
   int64_t out_block_stride;
   int64_t wz_r0, wz_nr, wz_f0, wz_nf, ldo;  // materialisation window
+  __half *zt_hi, *zt_lo;                    // write mode: Z^T as an FP16 hi/lo split (ld ldo), or null
+  float zt_scale;                           // its power-of-two scale
   int bias_in_mma;                          // 1: b already in the product (column of ones)
   const uint8_t* bmask;                     // passes 1 and 2: active blocks (R x C), or null
   int* err;
@@ -508,7 +511,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
           const float* bcol = a.bias + bslot + colbase;
 #pragma unroll
           for (int c = 0; c < 64; ++c) {
-            const float ph = (a.mode == MODE_PASS1) ? bias_a : __ldg(bcol + c);
+            const float ph = (a.mode == MODE_PASS1)                             ? bias_a
+                             : RFF_IN(bslot + colbase + c, a.fslots) ? __ldg(bcol + c)
+                                                                     : 0.f;
             z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg + ph);
           }
         } else {
@@ -518,11 +523,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
         if (!chain) {
           // materialise Z = sqrt(2/D) cos(...) (float32) inside the window
           const int64_t r = arow - a.wz_r0;
-          if (r < a.wz_nr) {
+          if (r < a.wz_nr && a.zt_hi) {
+            // transposed FP16 hi/lo split of zt_scale Z: the lanes hold consecutive rows, so
+            // every store of the warp fills 32 consecutive elements of one row of Z^T
 #pragma unroll
             for (int c = 0; c < 64; ++c) {
               const int64_t f = bslot + colbase + c - a.wz_f0;
-              if (f < a.wz_nf) a.out[r * a.ldo + f] = a.scale * z[c];
+              if (f < a.wz_nf && RFF_IN(f * a.ldo + r, a.out_elems)) {
+                const float xs = a.scale * z[c] * a.zt_scale;
+                const __half h = __float2half_rn(xs);
+                a.zt_hi[f * a.ldo + r] = h;
+                a.zt_lo[f * a.ldo + r] = __float2half_rn(xs - __half2float(h));
+              }
+            }
+          } else if (r < a.wz_nr) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) {
+              const int64_t f = bslot + colbase + c - a.wz_f0;
+              if (f < a.wz_nf && RFF_IN(r * a.ldo + f, a.out_elems)) a.out[r * a.ldo + f] = a.scale * z[c];
             }
           }
           continue;
@@ -594,13 +612,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_tc(const __grid_constant_
                                     sc * __uint_as_float(r8[2]), sc * __uint_as_float(r8[3]));
             float4 v1 = make_float4(sc * __uint_as_float(r8[4]), sc * __uint_as_float(r8[5]),
                                     sc * __uint_as_float(r8[6]), sc * __uint_as_float(r8[7]));
-            if (a.mode == MODE_PREDICT && g > 0) {   // this CTA wrote these rows for group g-1
+            const bool in = RFF_SPAN(orow + c0 + c - a.out, 8, a.out_elems);
+            if (in && a.mode == MODE_PREDICT && g > 0) {   // this CTA wrote these rows for group g-1
               const float4 p0 = dst[0], p1 = dst[1];
               v0 = make_float4(p0.x + v0.x, p0.y + v0.y, p0.z + v0.z, p0.w + v0.w);
               v1 = make_float4(p1.x + v1.x, p1.y + v1.y, p1.z + v1.z, p1.w + v1.w);
             }
-            dst[0] = v0;
-            dst[1] = v1;
+            if (in) {
+              dst[0] = v0;
+              dst[1] = v1;
+            }
             omx = fmaxf(omx, fmaxf(fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)), fmaxf(fabsf(v0.z), fabsf(v0.w))),
                                    fmaxf(fmaxf(fabsf(v1.x), fabsf(v1.y)), fmaxf(fabsf(v1.z), fabsf(v1.w)))));
           }
@@ -766,7 +787,9 @@ int tc_error_word() {
   return h;
 }
 
-cudaError_t tc_write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int64_t nf, float* out, int64_t ldo) {
+namespace {
+cudaError_t write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int64_t nf, float* out, __half* zt_hi,
+                    __half* zt_lo, float zt_scale, int64_t ldo) {
   if (nr <= 0 || nf <= 0) return cudaSuccess;
   TcArgs a;
   cudaError_t e = common_args(v, a);
@@ -776,6 +799,10 @@ cudaError_t tc_write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int6
   a.b_ok = v.feat_ok;
   a.wz_r0 = r0; a.wz_nr = nr; a.wz_f0 = f0; a.wz_nf = nf; a.ldo = ldo;
   a.out = out;
+  a.zt_hi = zt_hi;
+  a.zt_lo = zt_lo;
+  a.zt_scale = zt_scale;
+  a.out_elems = zt_hi ? (nf - 1) * ldo + nr : (nr - 1) * ldo + nf;
   if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
@@ -783,6 +810,16 @@ cudaError_t tc_write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int6
   a.tM_hi = a.tB_hi;
   a.tM_lo = a.tB_lo;
   return launch(a, dim3((unsigned)ceil_div(nr, 128)), v.st, view_kc(v), view_zt(v));
+}
+}  // namespace
+
+cudaError_t tc_write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int64_t nf, float* out, int64_t ldo) {
+  return write_z(v, r0, nr, f0, nf, out, nullptr, nullptr, 0.f, ldo);
+}
+
+cudaError_t tc_write_zt_split(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int64_t nf, float scale,
+                              __half* hi, __half* lo, int64_t ldt) {
+  return write_z(v, r0, nr, f0, nf, nullptr, hi, lo, scale, ldt);
 }
 
 cudaError_t tc_pass1(const TcView& v, float* Rpart) {
@@ -794,6 +831,7 @@ cudaError_t tc_pass1(const TcView& v, float* Rpart) {
   a.a_ok = v.feat_ok;
   a.b_ok = v.row_ok;
   a.out = Rpart;
+  a.out_elems = (int64_t)v.nsplit * v.R * v.fslots * v.mpad;
   a.out_block_stride = v.fslots * v.mpad;
   a.m_amax = v.v_amax;
   a.bmask = v.bmask;
@@ -818,11 +856,12 @@ cudaError_t tc_pass2(const TcView& v, const __half* Mhi, const __half* Mlo, int6
   a.a_ok = v.row_ok;
   a.b_ok = v.feat_ok;
   a.out = out;
+  a.out_elems = (int64_t)v.C * v.nslots * v.mpad;
   a.out_block_stride = v.nslots * v.mpad;
   a.m_amax = m_amax;
   a.out_amax = out_amax;
   a.bmask = v.bmask;
-  a.nrow_tiles = v.nslots / 128;
+  a.nrow_tiles = v.row_tiles > 0 ? std::min<int64_t>(v.row_tiles, v.nslots / 128) : v.nslots / 128;
   if ((e = make_map(&a.tA_hi, v.Xhi, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, v.Xlo, v.dld, v.nslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tB_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
@@ -847,6 +886,7 @@ cudaError_t tc_predict(const TcView& v, const __half* Xh, const __half* Xl, int6
   a.a_ok = nullptr;
   a.b_ok = v.feat_ok;
   a.out = out;
+  a.out_elems = nrows * v.mpad;
   a.m_amax = m_amax;
   if ((e = make_map(&a.tA_hi, Xh, v.dld, nrows, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, Xl, v.dld, nrows, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
@@ -856,5 +896,7 @@ cudaError_t tc_predict(const TcView& v, const __half* Xh, const __half* Xl, int6
   if ((e = make_map(&a.tM_lo, Mlo, v.fslots, v.mpad, v.fslots, (int)v.mpad, view_kc(v))) != cudaSuccess) return e;
   return launch(a, dim3((unsigned)(nrows / 128)), v.st, view_kc(v), view_zt(v));
 }
+
+RFF_CHECK_UNIT(tc)
 
 }  // namespace rff

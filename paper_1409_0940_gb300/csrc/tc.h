@@ -26,11 +26,16 @@ struct TcView {
   int kc;                           // ring K chunk (64 or 32; 0 = library default)
   int zt;                           // 1: Z tile in tensor memory, 0: in shared memory
   const uint8_t* bmask;             // device, R x C: active blocks of a stochastic iteration, or null
+  int64_t row_tiles;                // pass 2: 128-row tiles taken from the first (0 = all of them)
   cudaStream_t st;
 };
 
 // Z for row slots [r0, r0+nr) x feature slots [f0, f0+nf) into out (ld ldo), float32.
 cudaError_t tc_write_z(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int64_t nf, float* out, int64_t ldo);
+// The same window as Z^T split into FP16 hi/lo of scale * Z: hi[f][r], lo[f][r] (ld ldt) for
+// f < nf, r < nr; the elements outside the window are left as they are.
+cudaError_t tc_write_zt_split(const TcView& v, int64_t r0, int64_t nr, int64_t f0, int64_t nf, float scale,
+                              __half* hi, __half* lo, int64_t ldt);
 // Pass 1: R-partials [nsplit][R][fslots][mpad] = Z_ij^T V_ij.
 cudaError_t tc_pass1(const TcView& v, float* Rpart);
 // Pass 2: out[j][slots][mpad] = Z_ij M_i (per_block) or out[slots][mpad] = sum_j Z_ij M (predict);
@@ -67,6 +72,7 @@ struct SgView {
   const SgJob* jobs;                   // device
   int njobs, mpad;
   float* out;
+  int64_t out_elems;                   // elements of out (every job's 128 x mpad tile lies inside)
   float out_scale;
   const unsigned* b_amax;
   unsigned* amax;

@@ -1,0 +1,54 @@
+"""The bounds-checked build (-DRFF_CHECK): on small solves over every path (FP32, split
+tensor-core and cached-Z precisions; Gram and outer forms; stochastic subsets; CSR input;
+Fastfood) no bounds check fails, and the iterates and scores are bit-identical to those of
+the ordinary build (the checks only guard accesses; the arithmetic is the same)."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+@pytest.fixture(scope="module")
+def builds():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sys.path.insert(0, ROOT)
+    from paper_1409_0940_gb300 import build
+    build.build()
+    build.build(check=True)
+
+
+def run_cases(path, checked):
+    env = dict(os.environ)
+    env["RFF_ADMM_CHECK"] = "1" if checked else "0"
+    # the same pass-1 row splits in both builds (the autotuner times kernels, and the checked
+    # ones are slower): the sum order of the R partials is then the same
+    env["RFF_PASS1_SPLITS"] = "2"
+    env["RFF_TC_GEOMETRY"] = "64,0"
+    res = subprocess.run([sys.executable, os.path.join(HERE, "checked_cases.py"), str(path)], env=env,
+                         capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-4000:]
+    return dict(np.load(path))
+
+
+def test_checked_build_matches_and_reports_nothing(builds, tmp_path):
+    plain = run_cases(tmp_path / "plain.npz", False)
+    checked = run_cases(tmp_path / "checked.npz", True)
+    assert int(plain["enabled"]) == 0 and int(checked["enabled"]) == 1
+    assert plain["report"][0] == 0
+    assert checked["report"][0] == 0, "bounds check failed: unit %d line %d index %d bound %d" % tuple(
+        checked["report"][1:])
+    keys = sorted(k for k in plain if k.endswith(("_W", "_S")))
+    assert len(keys) == 16
+    for k in keys:
+        assert np.isfinite(plain[k]).all(), k
+        assert np.array_equal(plain[k], checked[k]), k
