@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(name="multiclass-200k-d440-D16384-m147-4x4", n=200_000, d=440, m=147, sigma=10.0, D=16384, R=4,
                 C=4, loss="squared", reg="l2", lam=1e-5, rho=1.0, data_seed=1, philox_seed=2)
 METRIC = "ADMM iter/s"
-TRAFFIC_200K = {"pass1": 1.646e9, "pass2": 1.187e9}     # kernel -> DRAM bytes per launch (see run_ours)
+TRAFFIC_200K = {"pass1": 1.654e9, "pass2": 1.219e9}     # kernel -> DRAM bytes per launch (see run_ours)
 
 
 def peaks():
@@ -113,7 +113,8 @@ def make_data(w, n=None):
 
 def solver_kw(w, prec):
     return dict(loss=w["loss"], reg=w["reg"], lam=w["lam"], sigma=w["sigma"], rho=w["rho"], D=w["D"], R=w["R"],
-                C=w["C"], seed=w["philox_seed"], m=w["m"], prec=prec, feature_map=w.get("feature_map", "fourier"))
+                C=w["C"], seed=w["philox_seed"], m=w["m"], prec=prec, feature_map=w.get("feature_map", "fourier"),
+                degree=w.get("degree", 2), coef0=w.get("coef0", 1.0))
 
 
 def flops_per_iter(w, prec):
@@ -255,6 +256,8 @@ def run_ours(args, rank, world):
         for prec in ("split_bf16", "cached_z", "fp32"):
             if prec == "split_bf16" and w["feature_map"] == "laplace":
                 continue                      # the implicit split precision takes the Fourier map only
+            if prec != "cached_z" and w["feature_map"] == "tensorsketch":
+                continue                      # sketches are formed once: cached-Z precision only
             if prec == args.prec:
                 compare[prec] = {"iter_per_s": args.steps / (ms * 1e-3)}
                 continue
@@ -338,6 +341,10 @@ def workload(args):
         w["sigma"] = 8.0
     elif args.feature_map == "fastfood":
         w["name"] += "-fastfood"
+    elif args.feature_map == "tensorsketch":
+        # the polynomial kernel (<x, y> / sigma^2 + 1)^2
+        w["degree"], w["coef0"] = 2, 1.0
+        w["name"] += "-tensorsketch-q2"
     if args.loss != "squared":
         w["name"] += "-" + args.loss
     if args.block_fraction < 1.0:
@@ -351,7 +358,8 @@ def oracle_iter_seconds(w, n_sample, iters):
     from oracle import admm
     X, Y = make_data(w, n=n_sample)
     p = admm.Problem(X, Y, w["loss"], w["reg"], w["lam"], w["sigma"], w["rho"], w["D"], w["R"], w["C"],
-                     w["philox_seed"], feature_map=w["feature_map"])
+                     w["philox_seed"], feature_map=w["feature_map"], degree=w.get("degree", 2),
+                     coef0=w.get("coef0", 1.0))
     admm.admm(p, 1)                       # builds Z and the cached factors (untimed)
     t0 = time.perf_counter()
     admm.admm(p, iters, block_fraction=w["block_fraction"])
@@ -616,12 +624,15 @@ def main():
     ap.add_argument("--workload", default="multiclass", choices=["multiclass", "ridge", "sweep", "serve", "score"])
     ap.add_argument("--loss", default="squared", choices=["squared", "hinge", "multinomial", "crammer_singer", "l1"],
                     help="loss of the multiclass workload")
-    ap.add_argument("--feature-map", default="fourier", choices=["fourier", "laplace", "fastfood"],
+    ap.add_argument("--feature-map", default="fourier", choices=["fourier", "laplace", "fastfood", "tensorsketch"],
                     help="laplace: random Laplace features on histogram inputs (fp32 or cached_z precision); "
-                         "fastfood: the structured Fastfood projection")
+                         "fastfood: the structured Fastfood projection; tensorsketch: the polynomial "
+                         "kernel's sketches (cached_z precision)")
     ap.add_argument("--block-fraction", type=float, default=1.0,
                     help="stochastic variant: probability that a block takes part in an iteration")
     args = ap.parse_args()
+    if args.feature_map == "tensorsketch" and args.prec != "cached_z":
+        ap.error("--feature-map tensorsketch runs on --prec cached_z")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.workload != "multiclass":

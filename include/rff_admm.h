@@ -109,8 +109,22 @@ typedef enum { RFF_RHO_SUM = 0, RFF_RHO_MEAN = 1 } rff_rho_scale;
  *                    Smola 2013): per block of d' = 2^p >= d features
  *                    V = S H diag(g) P H diag(B) / (sigma sqrt(d')), H Walsh-Hadamard, B signs,
  *                    P a permutation, S chi(d') row lengths over |g|; every row of V is
- *                    N(0, I / sigma^2), so the Gaussian kernel again; d <= 4096 */
-typedef enum { RFF_MAP_FOURIER = 0, RFF_MAP_LAPLACE = 1, RFF_MAP_FASTFOOD = 2 } rff_feature_map;
+ *                    N(0, I / sigma^2), so the Gaussian kernel again; d <= 4096
+ *   RFF_MAP_TENSORSKETCH  TensorSketch (Pham and Pagh 2013) of the polynomial kernel
+ *                    (<x, x'> / sigma^2 + coef0)^degree: with x~ = (x / sigma, sqrt(coef0)),
+ *                    column block j (s_j features) is its own sketch, the circular
+ *                    convolution of `degree` CountSketches of x~ of length s_j, scaled by
+ *                    sqrt(s_j / D) (Sec. 4 assembles maps that need their whole vector from
+ *                    independent per-block maps), so Z depends on the column partition.
+ *                    Hashes and signs: Philox counter (j, p (d + 1) + i, 7, 0), h = (w0 s_j)
+ *                    >> 32, sign -1 iff the top bit of w1 is set.  Cached-Z precision only (Z
+ *                    is formed once); degree 1..8, s_j <= 8192 */
+typedef enum {
+  RFF_MAP_FOURIER = 0,
+  RFF_MAP_LAPLACE = 1,
+  RFF_MAP_FASTFOOD = 2,
+  RFF_MAP_TENSORSKETCH = 3
+} rff_feature_map;
 
 typedef struct {
   int32_t loss;      /* rff_loss                                                     */
@@ -127,6 +141,8 @@ typedef struct {
   int32_t rho_scale; /* rff_rho_scale                                                */
   int32_t newton_iters; /* Newton steps of the logistic / multinomial prox (0 = 8) */
   int32_t feature_map;  /* rff_feature_map (0: random Fourier features)              */
+  int32_t degree;       /* TensorSketch: polynomial degree (1..8); other maps ignore it */
+  double coef0;         /* TensorSketch: the kernel's offset >= 0; other maps ignore it */
 } rff_admm_params;
 
 typedef struct {
@@ -367,6 +383,14 @@ rff_status rff_laplace_params(uint64_t seed, double sigma, int64_t d, int64_t k_
 rff_status rff_laplace_features(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma, int64_t D,
                                 int64_t k_lo, int64_t k_hi, float* Z, void* stream);
 
+/* TensorSketch features (RFF_MAP_TENSORSKETCH) of the rows of X (n x d, device, row-major)
+ * for D features in C column blocks partitioned as the solver does (the leading D mod C
+ * blocks one larger): Z (n x D, device, row-major), block j in its columns, scaled by
+ * sqrt(s_j / D).  Errors: RFF_EINVAL for a degree outside 1..8, coef0 < 0, blocks over 8192
+ * features or a shared-memory footprint (degree, d, block size) the kernel cannot hold. */
+rff_status rff_tensorsketch_features(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma,
+                                     double coef0, int32_t degree, int64_t D, int32_t C, float* Z, void* stream);
+
 /* The Fastfood map's projection for global features k_lo..k_hi-1: Vt ((k_hi - k_lo) x d,
  * row-major: row r is V's row k_lo + r) and b (k_hi - k_lo), device pointers; D sets the
  * block structure only through d' (features are grouped in blocks of d').  d <= 4096. */
@@ -385,12 +409,12 @@ rff_status rff_selftest_wait_timeout(void* stream);
  * scoring test, at their global accesses, that every element index lies inside the layout
  * the operation defines (the regeneration passes' X, G, chained-operand and output tiles, the
  * tensor-core epilogues' output rows, the exchange's row tiles, the sparse scatter's column
- * indices) and that every TMA box starts on a 16-byte boundary; a failed test skips the
+ * indices, the TensorSketch output rows) and that every TMA box starts on a 16-byte boundary; a failed test skips the
  * access and is counted.  rff_check_enabled() is 1 in that build and 0 in the ordinary one.
  * rff_check_report synchronises the device and reads and clears the counts into out[5]:
  *   out[0]  failed tests since the last report (0 in the ordinary build),
  *   out[1]  source unit of the first failure: 1 elementwise.cu, 2 qgemm.cu, 3 regen_simt.cu,
- *           4 tc.cu,
+ *           4 tc.cu, 5 sketch.cu,
  *   out[2]  its source line, out[3] the index tested, out[4] the bound it broke.
  * A skipped TMA copy leaves its barrier incomplete: the bounded wait on it gives up and the
  * pass returns RFF_ETIMEOUT.  Returns RFF_ECUDA if the device reports an error. */

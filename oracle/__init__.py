@@ -22,6 +22,9 @@ Optimization and Randomization", arXiv:1409.0940):
                  graph projection (eq. (graphU), (graphV)), the ridge closed form
                  (Sec. 2.2), residuals, objective and prediction.
 * ``memory``  -- the per-node memory model, eq. (mem).
+* ``fastfood`` -- Fastfood's structured projection (Sec. 4 lists the map).
+* ``tensorsketch`` -- TensorSketch features of the polynomial kernel, one independent
+                 sketch per column block (Sec. 4 lists the map and the block assembly).
 
 Parity status of every function is stated in its module header; all functions
 here are pinned by the CPU tests (closed forms, brute force, published known-

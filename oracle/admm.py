@@ -133,7 +133,7 @@ class Problem:
     """Data and parameters of one solve (Sec. 1, eq. (basicproblem); Sec. 3 grid)."""
 
     def __init__(self, X, Y, loss="squared", reg="l2", lam=1e-4, sigma=1.0, rho=1.0,
-                 D=512, R=1, C=1, seed=0, rho_scale="sum", feature_map="fourier"):
+                 D=512, R=1, C=1, seed=0, rho_scale="sum", feature_map="fourier", degree=2, coef0=1.0):
         self.X = np.asarray(X, dtype=np.float64)
         Y = np.asarray(Y, dtype=np.float64)
         self.Y = Y.reshape(Y.shape[0], -1)
@@ -144,6 +144,7 @@ class Problem:
         if feature_map == "laplace" and (self.X < 0).any():
             raise ValueError("random Laplace features take nonnegative inputs")
         self.feature_map = feature_map
+        self.degree, self.coef0 = int(degree), float(coef0)   # TensorSketch: (<x,y>/sigma^2 + coef0)^degree
         self.loss, self.reg = loss, reg
         self.lam, self.sigma, self.rho = float(lam), float(sigma), float(rho)
         self.D, self.R, self.C, self.seed = int(D), int(R), int(C), int(seed)
@@ -162,8 +163,14 @@ class Problem:
     def Z(self):
         """The explicit feature matrix, computed once (the oracle stores it)."""
         if self._Z is None:
-            self._Z = rff.features_block(self.X, self.seed, self.sigma, self.D, 0, self.D, self.feature_map)
+            self._Z = self._features(self.X)
         return self._Z
+
+    def _features(self, X):
+        if self.feature_map == "tensorsketch":   # per-column-block sketches (oracle/tensorsketch.py)
+            from . import tensorsketch
+            return tensorsketch.features(X, self.seed, self.sigma, self.coef0, self.degree, self.cols)
+        return rff.features_block(X, self.seed, self.sigma, self.D, 0, self.D, self.feature_map)
 
     def solvers(self):
         """Cached factor of every block (eq. (cache)), built on first use."""
@@ -182,9 +189,7 @@ class Problem:
 
     def predict(self, Xq, W):
         """Scores f(x) = W^T z(x) for the rows of Xq."""
-        Zq = rff.features_block(np.asarray(Xq, dtype=np.float64), self.seed, self.sigma, self.D, 0, self.D,
-                                self.feature_map)
-        return Zq @ W
+        return self._features(np.asarray(Xq, dtype=np.float64)) @ W
 
 
 def admm(prob, iters, variant="equation", history=False, block_fraction=1.0):

@@ -32,7 +32,7 @@ bitwise; partition sizes against their definition; the Laplace map against the
 semigroup kernel within a Hoeffding bound, its parameters against the Levy CDF.
 """
 
-MAPS = ("fourier", "laplace", "fastfood")
+MAPS = ("fourier", "laplace", "fastfood", "tensorsketch")
 import numpy as np
 
 from . import philox

@@ -21,7 +21,7 @@ RFF_OK, RFF_EINVAL, RFF_ENOMEM, RFF_ECUDA, RFF_ETIMEOUT, RFF_ENOTREADY, RFF_ENUM
 _STATUS = {0: "RFF_OK", 1: "RFF_EINVAL", 2: "RFF_ENOMEM", 3: "RFF_ECUDA", 4: "RFF_ETIMEOUT",
            5: "RFF_ENOTREADY", 6: "RFF_ENUMERIC", 7: "RFF_ECANCELLED"}
 LOSSES = {"squared": 0, "hinge": 1, "logistic": 2, "multinomial": 3, "l1": 4, "crammer_singer": 5}
-FEATURE_MAPS = {"fourier": 0, "laplace": 1, "fastfood": 2}
+FEATURE_MAPS = {"fourier": 0, "laplace": 1, "fastfood": 2, "tensorsketch": 3}
 REGS = {"l2": 0, "l1": 1}
 PRECS = {"fp32": 0, "split_bf16": 1, "cached_z": 2}
 RHO_SCALES = {"sum": 0, "mean": 1}
@@ -38,7 +38,8 @@ class rff_admm_params(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("rho", ctypes.c_double), ("D", ctypes.c_int64),
                 ("R", ctypes.c_int32), ("C", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("prec", ctypes.c_int32), ("m", ctypes.c_int32), ("rho_scale", ctypes.c_int32),
-                ("newton_iters", ctypes.c_int32), ("feature_map", ctypes.c_int32)]
+                ("newton_iters", ctypes.c_int32), ("feature_map", ctypes.c_int32), ("degree", ctypes.c_int32),
+                ("coef0", ctypes.c_double)]
 
 
 class rff_admm_stats(ctypes.Structure):
@@ -97,6 +98,7 @@ PROTOTYPES = {
     "rff_laplace_params": (_I32, [_U64, _D, _I64, _I64, _I64, _P, _P]),
     "rff_fastfood_params": (_I32, [_U64, _D, _I64, _I64, _I64, _P, _P, _P]),
     "rff_laplace_features": (_I32, [_P, _I64, _I64, _U64, _D, _I64, _I64, _I64, _P, _P]),
+    "rff_tensorsketch_features": (_I32, [_P, _I64, _I64, _U64, _D, _D, _I32, _I64, _I32, _P, _P]),
     "rff_prox_loss": (_I32, [_I32, _P, _P, _I64, _I32, _D, _I32, _P, _P]),
     "rff_prox_reg": (_I32, [_I32, _P, _I64, _D, _P, _P]),
     "rff_cholesky_f64": (_I32, [_P, _I32, _I32, _P, _P]),
@@ -173,9 +175,9 @@ def _stream(stream):
 
 
 def make_params(loss="squared", reg="l2", lam=1e-4, sigma=1.0, rho=1.0, D=512, R=1, C=1, seed=0,
-                prec="fp32", m=1, rho_scale="sum", newton_iters=0, feature_map="fourier"):
+                prec="fp32", m=1, rho_scale="sum", newton_iters=0, feature_map="fourier", degree=2, coef0=1.0):
     return rff_admm_params(LOSSES[loss], REGS[reg], lam, sigma, rho, D, R, C, seed, PRECS[prec], m,
-                           RHO_SCALES[rho_scale], newton_iters, FEATURE_MAPS[feature_map])
+                           RHO_SCALES[rho_scale], newton_iters, FEATURE_MAPS[feature_map], degree, coef0)
 
 
 # ----------------------------------------------------------------- C ABI, same names
@@ -361,6 +363,14 @@ def rff_laplace_features(X, seed, sigma, D, k_lo, k_hi, Z, stream=None):
     pz, _ = _ptr(Z)
     _check(lib.rff_laplace_features(px, X.shape[0], X.shape[1], seed, sigma, D, k_lo, k_hi, pz, _stream(stream)),
            None, "rff_laplace_features")
+    return Z
+
+
+def rff_tensorsketch_features(X, seed, sigma, coef0, degree, D, C, Z, stream=None):
+    px, _ = _ptr(X)
+    pz, _ = _ptr(Z)
+    _check(lib.rff_tensorsketch_features(px, X.shape[0], X.shape[1], seed, sigma, coef0, degree, D, C, pz,
+                                         _stream(stream)), None, "rff_tensorsketch_features")
     return Z
 
 

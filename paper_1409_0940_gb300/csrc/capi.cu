@@ -24,6 +24,8 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+constexpr int64_t TS_SCORE_ROWS = 2048;   // TensorSketch scoring: rows sketched per product
+
 }  // namespace
 
 struct rff_admm_s {
@@ -79,6 +81,9 @@ struct rff_admm_s {
   // the two streamed passes
   __half *Zhi = nullptr, *Zlo = nullptr, *ZThi = nullptr, *ZTlo = nullptr;   // FP16 split of zscale Z
   float zscale = 1.f;
+  float ts_zmax = 0.f;           // TensorSketch: max |z| over the training rows (the split's scale)
+  float* ts_buf = nullptr;       // TensorSketch scoring: TS_SCORE_ROWS rows of features
+  GemmDesc* ts_desc = nullptr;   // and the descriptor of their product with Wbar
   SgJob *p1jobs = nullptr, *p2jobs = nullptr;
   int np1 = 0, np2 = 0, nsplit_cz = 1;
   // stochastic block subsets: a block is active in an iteration when its Philox word is
@@ -141,9 +146,13 @@ struct rff_admm_s {
   // the split path: tensor-core kernels and BF16 operand copies (cached-Z uses them too)
   bool split_path() const { return p.prec == RFF_PREC_SPLIT_BF16 || p.prec == RFF_PREC_CACHED_Z; }
   // scoring forms X.G on the tensor cores (split path; random Fourier or Fastfood map)
-  bool tc_scores() const { return split_path() && p.feature_map != RFF_MAP_LAPLACE; }
+  bool tc_scores() const {
+    return split_path() && p.feature_map != RFF_MAP_LAPLACE && p.feature_map != RFF_MAP_TENSORSKETCH;
+  }
+  bool tensorsketch() const { return p.feature_map == RFF_MAP_TENSORSKETCH; }
   // the feature map's scale: max |z| (sqrt(2/D) for cos, 1/sqrt(D) for exp(-T) with T >= 0)
   float zmap_scale() const {
+    if (p.feature_map == RFF_MAP_TENSORSKETCH) return ts_zmax > 0.f ? ts_zmax : 1.f;   // measured, no a-priori bound
     return (float)(p.feature_map == RFF_MAP_LAPLACE ? 1.0 / std::sqrt((double)D) : std::sqrt(2.0 / (double)D));
   }
   bool cached_z() const { return p.prec == RFF_PREC_CACHED_Z; }
@@ -201,7 +210,20 @@ rff_status check_params(const rff_admm_params* p, std::string& why) {
   if (p->m < 1 || p->m > 256) { why = "m must be in [1, 256]"; return RFF_EINVAL; }
   if (p->newton_iters < 0 || p->newton_iters > 100) { why = "newton_iters out of range"; return RFF_EINVAL; }
   if (p->prec != RFF_PREC_FP32 && p->C > 64) { why = "the split-BF16 and cached-Z paths support C <= 64"; return RFF_EINVAL; }
-  if (p->feature_map < 0 || p->feature_map > 2) { why = "unknown feature map"; return RFF_EINVAL; }
+  if (p->feature_map < 0 || p->feature_map > 3) { why = "unknown feature map"; return RFF_EINVAL; }
+  if (p->feature_map == RFF_MAP_TENSORSKETCH) {
+    if (p->prec != RFF_PREC_CACHED_Z) {
+      // a sketch is a whole vector per block, not a tile function: Z is formed once and kept
+      why = "TensorSketch features run on the cached-Z precision";
+      return RFF_EINVAL;
+    }
+    if (p->degree < 1 || p->degree > TS_MAX_DEGREE) { why = "TensorSketch degree must be in [1, 8]"; return RFF_EINVAL; }
+    if (!(p->coef0 >= 0) || !std::isfinite(p->coef0)) { why = "TensorSketch coef0 must be >= 0"; return RFF_EINVAL; }
+    if ((p->D + p->C - 1) / p->C > TS_MAX_BLOCK) {
+      why = "TensorSketch column blocks hold at most 8192 features";
+      return RFF_EINVAL;
+    }
+  }
   if (p->feature_map == RFF_MAP_LAPLACE && p->prec == RFF_PREC_SPLIT_BF16) {
     // W is Levy-distributed: its range spans far more than the FP16 split's 2^29
     why = "the random Laplace map runs on the FP32 and cached-Z precisions";
@@ -281,6 +303,7 @@ size_t working_set_bytes(const rff_admm_s& s) {
     t += (size_t)s.foff.back() * f + (size_t)s.R * s.C * sizeof(GemmDesc);                     // factors
   }
   if (s.outer) t += (size_t)s.C * s.nslots * s.mpad * f;                                       // u = Z rhs
+  if (s.tensorsketch()) t += (size_t)TS_SCORE_ROWS * s.fslots * f + sizeof(GemmDesc) + 512;   // scoring rows
   return t + (64u << 20);
 }
 
@@ -501,6 +524,9 @@ rff_status set_data_impl(rff_admm_t h, const XInput& xin, const float* Yin, int6
   if (csr && xin.nnz < 0) return h->fail(RFF_EINVAL, "nnz < 0");
   if (n < h->p.R || d < 1 || n > ((int64_t)1 << 31) - 1) return h->fail(RFF_EINVAL, "need R <= n < 2^31 and d >= 1");
   if (h->p.feature_map == RFF_MAP_FASTFOOD && d > 4096) return h->fail(RFF_EINVAL, "the Fastfood map takes d <= 4096");
+  if (h->tensorsketch() &&
+      tensorsketch_smem_bytes(h->p.degree, d, (h->p.D + h->p.C - 1) / h->p.C) > TS_MAX_SMEM)
+    return h->fail(RFF_EINVAL, "TensorSketch: degree x d and the block size exceed the kernel's shared memory");
   CK(cudaStreamSynchronize(h->st));
   h->drop_graph();
   h->free_all();
@@ -533,6 +559,10 @@ rff_status set_data_impl(rff_admm_t h, const XInput& xin, const float* Yin, int6
   AL(s.d_col_slot, s.C);
   AL(s.d_col_size, s.C);
   AL(s.d_zero, 2);
+  if (s.tensorsketch()) {
+    AL(s.ts_buf, (int64_t)TS_SCORE_ROWS * s.fslots);
+    AL(s.ts_desc, 1);
+  }
   AL(s.bmask, (int64_t)s.R * s.C);
   AL(s.bctr, 1);
   if (s.split_path()) {
@@ -814,6 +844,29 @@ rff_status autotune(rff_admm_t h) {
 // FMA chains: the tensor cores' accumulator rounds toward zero at every step, which
 // for X.G costs accuracy that one-time work need not give up), staged in row chunks,
 // and the job tables of the two streamed passes.
+// TensorSketch over rows [r0, r0 + nr) of X (ld ldx, slot layout) for every column block of
+// the handle; the caller sets the output (or the maximum) and the block range
+TsArgs ts_args(const rff_admm_s& s, const float* X, int64_t ldx, const int32_t* row_ok, int64_t r0, int64_t nr) {
+  TsArgs a{};
+  a.X = X;
+  a.ldx = ldx;
+  a.d = (int)s.d;
+  a.row_ok = row_ok;
+  a.r0 = r0;
+  a.nr = nr;
+  a.q = s.p.degree;
+  a.inv_sigma = (float)(1.0 / s.p.sigma);
+  a.sqrt_c = (float)std::sqrt(s.p.coef0);
+  a.k0 = (uint32_t)s.p.seed;
+  a.k1 = (uint32_t)(s.p.seed >> 32);
+  a.col_slot = s.d_col_slot;
+  a.col_size = s.d_col_size;
+  a.D = s.D;
+  return a;
+}
+
+int64_t ts_block_max(const rff_admm_s& s) { return *std::max_element(s.col_size.begin(), s.col_size.end()); }
+
 rff_status materialise_z(rff_admm_t h) {
   auto& s = *h;
   const int64_t chunk = std::max<int64_t>(128, ((int64_t)(256u << 20) / (s.fslots * 4)) / 128 * 128);
@@ -823,9 +876,18 @@ rff_status materialise_z(rff_admm_t h) {
   s.zscale = pow2_scale(s.zmap_scale());   // |Z| <= sqrt(2/D) (cos) or 1/sqrt(D) (exp(-T))
   for (int64_t r0 = 0; r0 < s.nslots; r0 += chunk) {
     const int64_t nr = std::min(chunk, s.nslots - r0);
-    ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, s.zmap_scale(), s.row_of_slot,
-             s.feat_of_slot, r0, nr, 0, s.fslots, zc, s.fslots, s.p.feature_map};
-    CK(launch_write_z_simt(za, s.st));
+    if (s.tensorsketch()) {
+      TsArgs ta = ts_args(s, s.X32, s.dld, s.row_of_slot, r0, nr);
+      ta.out = zc;
+      ta.ldo = s.fslots;
+      ta.out_elems = nr * s.fslots;
+      ta.pad = 1;
+      CK(launch_tensorsketch(ta, s.C, ts_block_max(s), s.st));
+    } else {
+      ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, s.zmap_scale(), s.row_of_slot,
+               s.feat_of_slot, r0, nr, 0, s.fslots, zc, s.fslots, s.p.feature_map};
+      CK(launch_write_z_simt(za, s.st));
+    }
     CK(launch_split_f16(zc, nr * s.fslots, s.zscale, s.Zhi + r0 * s.fslots, s.Zlo + r0 * s.fslots, s.st));
     CK(launch_transpose_split_f16(zc, nr, (int)s.fslots, 1, 0, s.ZThi + r0, s.ZTlo + r0, s.nslots, 0, s.zscale,
                                   nullptr, s.st));
@@ -915,7 +977,9 @@ rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t
   const int64_t spad = round_up(smax, 256), kpad = round_up(chunk_rows, GRAM_KCH);
   std::vector<int2> tiles;
   const int64_t nt = tc_gram_tiles(sj, &tiles);
-  const float zs = pow2_scale(std::sqrt(2.0 / (double)s.D));   // |Z| <= sqrt(2/D)
+  // |Z| <= sqrt(2/D) (random Fourier and Fastfood maps; the Laplace map's 1/sqrt(D) is below
+  // it), TensorSketch: its measured maximum
+  const float zs = pow2_scale(s.tensorsketch() ? (double)s.ts_zmax : std::sqrt(2.0 / (double)s.D));
   __half* hi = reinterpret_cast<__half*>(buf);
   __half* lo = reinterpret_cast<__half*>(buf + round_up((size_t)spad * kpad * 2, 256));
   float* P = reinterpret_cast<float*>(buf + 2 * round_up((size_t)spad * kpad * 2, 256));
@@ -1034,11 +1098,24 @@ rff_status regenerate_features(rff_admm_t h) {
 
 rff_status setup_factors(rff_admm_t h) {
   auto& s = *h;
-  const float scale = s.zmap_scale();
   {
     rff_status r = generate_features(h);
     if (r != RFF_OK) return r;
   }
+  if (s.tensorsketch()) {
+    // the sketches have no a-priori bound: one pass over the training rows measures max |z|,
+    // the scale of Z's FP16 split (and of the Gram's)
+    unsigned* bits = reinterpret_cast<unsigned*>(s.flag + 3);
+    CK(cudaMemsetAsync(bits, 0, 4, s.st));
+    TsArgs ta = ts_args(s, s.X32, s.dld, s.row_of_slot, 0, s.nslots);
+    ta.amax = bits;
+    CK(launch_tensorsketch(ta, s.C, ts_block_max(s), s.st));
+    unsigned hb = 0;
+    CK(cudaMemcpyAsync(&hb, bits, 4, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaStreamSynchronize(s.st));
+    memcpy(&s.ts_zmax, &hb, 4);
+  }
+  const float scale = s.zmap_scale();
   // Gram matrices H_ij = I + Z_ij^T Z_ij (eq. (cache)), or I + Z_ij Z_ij^T in the outer
   // form, in FP64, batched by memory
   int64_t smax = 0;
@@ -1111,7 +1188,15 @@ rff_status setup_factors(rff_admm_t h) {
           if (gr != RFF_OK) return gr;
           continue;
         }
-        if (s.split_path() && !s.cached_z()) {
+        if (s.tensorsketch()) {
+          TsArgs ta = ts_args(s, s.X32, s.dld, s.row_of_slot, s.row_slot[i] + r, nr);
+          ta.j0 = j;
+          ta.out = Zc;
+          ta.ldo = sj;
+          ta.f_base = s.col_slot[j];
+          ta.out_elems = nr * sj;
+          CK(launch_tensorsketch(ta, 1, sj, s.st));
+        } else if (s.split_path() && !s.cached_z()) {
           CK(tc_write_z(tc_view(s), s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj));
         } else {
           ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, scale, s.row_of_slot, s.feat_of_slot,
@@ -1612,6 +1697,21 @@ rff_status scores_pass(rff_admm_t h, const float* Xrows32, const __half* Xh, con
     CK(launch_transpose_split_f16(s.Wbar, s.fslots, (int)s.mpad, 1, 0, s.WbThi, s.WbTlo, s.fslots, 0, 1.f,
                                   s.amax + AMAX_WB, s.st));
     CK(tc_predict(tc_view(s), Xh, Xl, nrows, s.WbThi, s.WbTlo, s.amax + AMAX_WB, out));
+  } else if (s.tensorsketch()) {
+    // the rows' sketches, TS_SCORE_ROWS at a time, then their product with Wbar in FP32
+    for (int64_t r0 = 0; r0 < nrows; r0 += TS_SCORE_ROWS) {
+      const int64_t nr = std::min<int64_t>(TS_SCORE_ROWS, nrows - r0);
+      TsArgs ta = ts_args(s, Xrows32, s.dld, row_ok, r0, nr);
+      ta.out = s.ts_buf;
+      ta.ldo = s.fslots;
+      ta.out_elems = nr * s.fslots;
+      ta.pad = 1;
+      CK(launch_tensorsketch(ta, s.C, ts_block_max(s), s.st));
+      const GemmDesc g{s.ts_buf, s.Wbar, nullptr, out + r0 * s.mpad, (int)nr, (int)s.mpad, (int)s.fslots,
+                       s.fslots, s.mpad, s.mpad, s.mpad};
+      CK(cudaMemcpyAsync(s.ts_desc, &g, sizeof(g), cudaMemcpyHostToDevice, s.st));
+      CK(launch_gemm_f32_nn(s.ts_desc, 1, (int)nr, (int)s.mpad, 1.f, 0.f, s.st));
+    }
   } else {
     PassArgs a = base_pass_args(s);
     a.X = Xrows32;
@@ -1804,8 +1904,8 @@ rff_status rff_check_report(int64_t* out) {
   }
   // the units in the order of their numbers in the report
   cudaError_t (*const units[])(CheckHit*) = {check_collect_elementwise, check_collect_qgemm,
-                                             check_collect_regen_simt, check_collect_tc};
-  for (int u = 0; u < 4; ++u) {
+                                             check_collect_regen_simt, check_collect_tc, check_collect_sketch};
+  for (int u = 0; u < 5; ++u) {
     CheckHit hit{};
     if (units[u](&hit) != cudaSuccess) {
       cudaGetLastError();
@@ -2386,6 +2486,53 @@ rff_status rff_features(const float* X, int64_t n, int64_t d, uint64_t seed, dou
 rff_status rff_laplace_features(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma, int64_t D,
                                 int64_t k_lo, int64_t k_hi, float* Z, void* stream) {
   return features_impl(X, n, d, seed, sigma, D, k_lo, k_hi, RFF_PREC_FP32, RFF_MAP_LAPLACE, Z, stream);
+}
+
+rff_status rff_tensorsketch_features(const float* X, int64_t n, int64_t d, uint64_t seed, double sigma,
+                                     double coef0, int32_t degree, int64_t D, int32_t C, float* Z, void* stream) {
+  if (!X || !Z || n < 0 || d < 1 || d > (1 << 20) || D < 1 || C < 1 || C > D || C > 65535) return RFF_EINVAL;
+  if (degree < 1 || degree > TS_MAX_DEGREE || !(coef0 >= 0) || !std::isfinite(coef0) || !(sigma > 0)) return RFF_EINVAL;
+  std::vector<int64_t> start, size;
+  partition(D, C, start, size);
+  const int64_t smax = size[0];
+  if (smax > TS_MAX_BLOCK || tensorsketch_smem_bytes(degree, d, smax) > TS_MAX_SMEM) return RFF_EINVAL;
+  if (n == 0) return RFF_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int64_t* dcol = nullptr;
+  if (cudaMallocAsync(&dcol, (size_t)C * 16, st) != cudaSuccess) {
+    cudaGetLastError();
+    return RFF_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(dcol, start.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dcol + C, size.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    TsArgs a{};
+    a.X = X;
+    a.ldx = d;
+    a.d = (int)d;
+    a.nr = n;
+    a.q = degree;
+    a.inv_sigma = (float)(1.0 / sigma);
+    a.sqrt_c = (float)std::sqrt(coef0);
+    a.k0 = (uint32_t)seed;
+    a.k1 = (uint32_t)(seed >> 32);
+    a.col_slot = dcol;
+    a.col_size = dcol + C;
+    a.out = Z;
+    a.ldo = D;
+    a.out_elems = n * D;
+    a.D = D;
+    e = launch_tensorsketch(a, C, smax, st);
+  }
+  // the host vectors are read by the copies: pageable memory is staged before they return
+  cudaError_t f = cudaFreeAsync(dcol, st);
+  if (e == cudaSuccess) e = f;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorInvalidValue ? RFF_EINVAL : RFF_ECUDA;
+  }
+  return RFF_OK;
 }
 
 rff_status rff_prox_loss(int32_t loss, const float* V, const float* Yv, int64_t n, int32_t m, double t,

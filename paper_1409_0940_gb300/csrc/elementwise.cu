@@ -886,7 +886,7 @@ cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, c
 
 // Four consecutive columns per thread: the pieces' float4 loads are all issued before the
 // sums (which keep the pieces' order), and H is updated by two double2 read-modify-writes
-// where the row's address allows it.
+// where the address is 16-byte aligned (H itself may start on an 8-byte boundary).
 constexpr int GRAM_PIECES_MAX = 8;
 
 __global__ void k_gram_reduce(const float* __restrict__ P, int nchunk, int ntiles, const int2* __restrict__ tiles,
@@ -910,7 +910,7 @@ __global__ void k_gram_reduce(const float* __restrict__ P, int nchunk, int ntile
       v[3] += (double)p[c].w;
     }
   double* h = H + row * ldh + col;
-  if (col + 3 <= row && ((row * ldh + col) & 1) == 0) {
+  if (col + 3 <= row && (reinterpret_cast<uintptr_t>(h) & 15) == 0) {
     double2* h2 = reinterpret_cast<double2*>(h);
     double2 a = h2[0], b = h2[1];
     a.x += v[0];

@@ -10,12 +10,43 @@ namespace rff {
 
 // Arguments of the fused regeneration passes (SIMT and tensor-core versions).
 // Row-side arrays are indexed by row slot, feature-side arrays by feature slot.
+// TensorSketch features (the polynomial kernel's map): rows [r0, r0 + nr) of X (slot layout,
+// ld ldx, first d columns used; row_ok: slot -> row, -1 = padding, or null) for the column
+// blocks j = j0 .. j0 + nblocks - 1 (S = col_size[j] features each, at column col_slot[j] - f_base
+// of out, scaled by sqrt(S / D)); pad: also write zeros up to the block's slot boundary;
+// amax: max |z| (float bits, atomicMax; zero it first), or null; out may be null.
+constexpr int TS_MAX_DEGREE = 8;
+constexpr int64_t TS_MAX_BLOCK = 8192;          // features per column block
+constexpr size_t TS_MAX_SMEM = 200 * 1024;
+struct TsArgs {
+  const float* X;
+  int64_t ldx;
+  int d;
+  const int32_t* row_ok;
+  int64_t r0, nr;
+  int q;
+  float inv_sigma, sqrt_c;
+  uint32_t k0, k1;                              // Philox key
+  int j0;                                       // first column block of the launch
+  const int64_t* col_slot;                      // device, one per block
+  const int64_t* col_size;                      // device
+  float* out;
+  int64_t ldo, f_base, out_elems;
+  int pad;
+  int64_t D;
+  unsigned* amax;
+};
+size_t tensorsketch_smem_bytes(int q, int64_t d, int64_t S);
+// nblocks column blocks (grid y), smax = the largest of their sizes
+cudaError_t launch_tensorsketch(const TsArgs& a, int nblocks, int64_t smax, cudaStream_t st);
+
 // read and clear the bounds-check record of each checked translation unit (zeros in the
 // ordinary build)
 cudaError_t check_collect_elementwise(CheckHit* h);
 cudaError_t check_collect_qgemm(CheckHit* h);
 cudaError_t check_collect_regen_simt(CheckHit* h);
 cudaError_t check_collect_tc(CheckHit* h);
+cudaError_t check_collect_sketch(CheckHit* h);
 
 struct PassArgs {
   const float* X;        // data rows (slots) x K, float32            (SIMT)

@@ -26,6 +26,8 @@ CASES = [
     ("fp32_csr", dict(prec="fp32", loss="l1", D=256, R=2, C=2, m=2), "sparse", 700, 1.0, True),
     ("fastfood_split", dict(prec="split_bf16", loss="squared", D=512, R=2, C=2, m=1, feature_map="fastfood"),
      "ridge", 1500, 1.0, False),
+    ("tensorsketch_cz", dict(prec="cached_z", loss="hinge", D=640, R=2, C=3, m=1, feature_map="tensorsketch"),
+     "binary", 2000, 1.0, False),
 ]
 
 

@@ -1,6 +1,6 @@
 """The bounds-checked build (-DRFF_CHECK): on small solves over every path (FP32, split
 tensor-core and cached-Z precisions; Gram and outer forms; stochastic subsets; CSR input;
-Fastfood) no bounds check fails, and the iterates and scores are bit-identical to those of
+Fastfood; TensorSketch) no bounds check fails, and the iterates and scores are bit-identical to those of
 the ordinary build (the checks only guard accesses; the arithmetic is the same)."""
 import os
 import subprocess
@@ -48,7 +48,7 @@ def test_checked_build_matches_and_reports_nothing(builds, tmp_path):
     assert checked["report"][0] == 0, "bounds check failed: unit %d line %d index %d bound %d" % tuple(
         checked["report"][1:])
     keys = sorted(k for k in plain if k.endswith(("_W", "_S")))
-    assert len(keys) == 16
+    assert len(keys) == 18
     for k in keys:
         assert np.isfinite(plain[k]).all(), k
         assert np.array_equal(plain[k], checked[k]), k
