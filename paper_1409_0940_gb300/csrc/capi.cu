@@ -436,12 +436,20 @@ size_t tc_gram_bytes(int64_t chunk_rows, int64_t smax) {
 
 bool tc_gram(const rff_admm_s& s) { return s.split_path() && !s.outer; }
 
+// rows of Z formed per chunk on the cached-Z precision (about 256 MB of FP32)
+int64_t materialise_chunk(const rff_admm_s& s) {
+  return std::max<int64_t>(128, ((int64_t)(256u << 20) / (s.fslots * 4)) / 128 * 128);
+}
+
 size_t setup_bytes(const rff_admm_s& s, int64_t batch) {
   int64_t smax = 0;
   for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
   const int64_t chunk_rows = std::min<int64_t>(32768, round_up(*std::max_element(s.row_size.begin(), s.row_size.end()), SLOT));
-  return (size_t)batch * smax * smax * 8 * 2 + (size_t)chunk_rows * smax * 4 + factor_scratch_bytes((int)batch, (int)smax) +
-         (size_t)batch * 4 + 4096 + (tc_gram(s) ? tc_gram_bytes(chunk_rows, smax) : 0);
+  const size_t t = (size_t)batch * smax * smax * 8 * 2 + (size_t)chunk_rows * smax * 4 +
+                   factor_scratch_bytes((int)batch, (int)smax) + (size_t)batch * 4 + 4096 +
+                   (tc_gram(s) ? tc_gram_bytes(chunk_rows, smax) : 0);
+  // the cached-Z precision forms Z in the same scratch first, in row chunks of ~256 MB
+  return s.cached_z() ? std::max(t, (size_t)materialise_chunk(s) * s.fslots * 4) : t;
 }
 
 }  // namespace
@@ -869,7 +877,7 @@ int64_t ts_block_max(const rff_admm_s& s) { return *std::max_element(s.col_size.
 
 rff_status materialise_z(rff_admm_t h) {
   auto& s = *h;
-  const int64_t chunk = std::max<int64_t>(128, ((int64_t)(256u << 20) / (s.fslots * 4)) / 128 * 128);
+  const int64_t chunk = materialise_chunk(s);
   rff_status rs = ensure_scratch(h, (size_t)chunk * s.fslots * 4);
   if (rs != RFF_OK) return rs;
   float* zc = static_cast<float*>(s.scratch.p);
@@ -969,7 +977,8 @@ rff_status fastfood_features(rff_admm_t h) {
 // the dominant products per tile: the accumulator's round-toward-zero bias stays ~2e-6 of a
 // piece's sum), the pieces' tiles added in FP64 in order.  buf: tc_gram_bytes(chunk, smax).
 // With Zc null the chunk is regenerated straight into that split by the tensor-core write mode
-// (rows zr0.., features zf0.. of the view zv), with the same roundings as splitting the FP32 Z.
+// (rows zr0.., features zf0.. of the view zv), with the same roundings as splitting the FP32 Z;
+// on the cached-Z precision (zv null too) it is copied from the stored split of Z^T.
 rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t sj, double* H, char* buf,
                               int64_t chunk_rows, int64_t smax, const TcView* zv = nullptr, int64_t zr0 = 0,
                               int64_t zf0 = 0) {
@@ -977,9 +986,8 @@ rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t
   const int64_t spad = round_up(smax, 256), kpad = round_up(chunk_rows, GRAM_KCH);
   std::vector<int2> tiles;
   const int64_t nt = tc_gram_tiles(sj, &tiles);
-  // |Z| <= sqrt(2/D) (random Fourier and Fastfood maps; the Laplace map's 1/sqrt(D) is below
-  // it), TensorSketch: its measured maximum
-  const float zs = pow2_scale(s.tensorsketch() ? (double)s.ts_zmax : std::sqrt(2.0 / (double)s.D));
+  // the split's scale: the stored Z's on the cached-Z precision, else that of |Z| <= sqrt(2/D)
+  const float zs = s.cached_z() ? s.zscale : pow2_scale(std::sqrt(2.0 / (double)s.D));
   __half* hi = reinterpret_cast<__half*>(buf);
   __half* lo = reinterpret_cast<__half*>(buf + round_up((size_t)spad * kpad * 2, 256));
   float* P = reinterpret_cast<float*>(buf + 2 * round_up((size_t)spad * kpad * 2, 256));
@@ -988,10 +996,16 @@ rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t
   const int64_t kn = round_up(nr, GRAM_KCH);   // this chunk's K, zero-padded
   CK(cudaMemsetAsync(hi, 0, (size_t)spad * kn * 2, s.st));
   CK(cudaMemsetAsync(lo, 0, (size_t)spad * kn * 2, s.st));
-  if (Zc)
+  if (Zc) {
     CK(launch_transpose_split_f16(Zc, nr, (int)sj, 1, 0, hi, lo, kn, 0, zs, nullptr, s.st));
-  else
+  } else if (zv) {
     CK(tc_write_zt_split(*zv, zr0, nr, zf0, sj, zs, hi, lo, kn));
+  } else {   // features zf0.. and rows zr0.. of the stored Z^T split (ld nslots)
+    CK(cudaMemcpy2DAsync(hi, kn * 2, s.ZThi + zf0 * s.nslots + zr0, s.nslots * 2, nr * 2, sj,
+                         cudaMemcpyDeviceToDevice, s.st));
+    CK(cudaMemcpy2DAsync(lo, kn * 2, s.ZTlo + zf0 * s.nslots + zr0, s.nslots * 2, nr * 2, sj,
+                         cudaMemcpyDeviceToDevice, s.st));
+  }
   CK(cudaMemcpyAsync(dtiles, tiles.data(), nt * sizeof(int2), cudaMemcpyHostToDevice, s.st));
   const int64_t npieces = kn / GRAM_KCH;
   std::vector<SgJob> jobs;
@@ -1138,9 +1152,14 @@ rff_status setup_factors(rff_admm_t h) {
   }
   budget = budget > zbytes + (256u << 20) ? budget - zbytes - (256u << 20) : 0;
   int64_t batch = std::max<int64_t>(1, std::min<int64_t>(nblocks, (int64_t)(budget / std::max<size_t>(per_block + factor_scratch_bytes(1, (int)fmax), 1))));
-  const size_t need = (size_t)batch * per_block + zbytes + factor_scratch_bytes((int)batch, (int)fmax) + (size_t)batch * 4 + 4096;
+  size_t need = (size_t)batch * per_block + zbytes + factor_scratch_bytes((int)batch, (int)fmax) + (size_t)batch * 4 + 4096;
+  if (s.cached_z()) need = std::max(need, (size_t)materialise_chunk(s) * s.fslots * 4);
   rff_status rs = ensure_scratch(h, need);
   if (rs != RFF_OK) return rs;
+  if (s.cached_z()) {   // Z and Z^T's splits first: the Gram below reads the stored Z^T
+    rff_status zr = materialise_z(h);
+    if (zr != RFF_OK) return zr;
+  }
   char* base = static_cast<char*>(s.scratch.p);
   double* H64 = reinterpret_cast<double*>(base);
   double* Q64 = H64 + batch * fmax * fmax;
@@ -1181,34 +1200,18 @@ rff_status setup_factors(rff_admm_t h) {
       }
       for (int64_t r = 0; !s.outer && r < s.row_size[i]; r += chunk_rows) {
         const int64_t nr = std::min(chunk_rows, s.row_size[i] - r);
-        if (tc_gram(s) && !s.cached_z()) {   // Z^T's split written by the regeneration itself
+        if (tc_gram(s)) {   // Z^T's split written by the regeneration itself, or the stored one
           const TcView zv = tc_view(s);
-          rff_status gr = tc_gram_accumulate(h, nullptr, nr, sj, Hb, gbase, chunk_rows, smax, &zv,
-                                             s.row_slot[i] + r, s.col_slot[j]);
+          rff_status gr = tc_gram_accumulate(h, nullptr, nr, sj, Hb, gbase, chunk_rows, smax,
+                                             s.cached_z() ? nullptr : &zv, s.row_slot[i] + r, s.col_slot[j]);
           if (gr != RFF_OK) return gr;
           continue;
         }
-        if (s.tensorsketch()) {
-          TsArgs ta = ts_args(s, s.X32, s.dld, s.row_of_slot, s.row_slot[i] + r, nr);
-          ta.j0 = j;
-          ta.out = Zc;
-          ta.ldo = sj;
-          ta.f_base = s.col_slot[j];
-          ta.out_elems = nr * sj;
-          CK(launch_tensorsketch(ta, 1, sj, s.st));
-        } else if (s.split_path() && !s.cached_z()) {
-          CK(tc_write_z(tc_view(s), s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj));
-        } else {
-          ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, scale, s.row_of_slot, s.feat_of_slot,
-                   s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj, s.p.feature_map};
-          CK(launch_write_z_simt(za, s.st));
-        }
-        if (tc_gram(s)) {
-          rff_status gr = tc_gram_accumulate(h, Zc, nr, sj, Hb, gbase, chunk_rows, smax);
-          if (gr != RFF_OK) return gr;
-        } else {
-          CK(launch_gram_f32_to_f64(Zc, sj, nr, sj, Hb, sj, s.st));
-        }
+        // FP32 precision: Z on the SIMT pipes, its Gram from FP32 products with float-float sums
+        ZArgs za{s.X32, s.dld, s.Gt32, s.dld, (int)s.dld, s.bias, scale, s.row_of_slot, s.feat_of_slot,
+                 s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj, s.p.feature_map};
+        CK(launch_write_z_simt(za, s.st));
+        CK(launch_gram_f32_to_f64(Zc, sj, nr, sj, Hb, sj, s.st));
       }
       CK(launch_add_identity_and_mirror(Hb, fd, fd, s.st));
       CK(cudaMemsetAsync(Qb, 0, fd * fd * 8, s.st));
@@ -1268,10 +1271,6 @@ rff_status setup_factors(rff_admm_t h) {
   } else
     CK(cudaMemcpyAsync(s.gdesc, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, s.st));
   CK(cudaStreamSynchronize(s.st));
-  if (s.cached_z()) {
-    rff_status zr = materialise_z(h);
-    if (zr != RFF_OK) return zr;
-  }
   // the set-up scratch (FP64 Gram and inverse batches) is released
   CK(cudaFreeAsync(s.scratch.p, s.st));
   s.scratch = DevBuf{};

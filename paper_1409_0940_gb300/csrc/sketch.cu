@@ -16,7 +16,10 @@
 // degree is one circular convolution with a sparse CountSketch, computed in pull form
 //   next[t] = sum over i (increasing) of g_p(i) x'_i acc[(t - h_p(i)) mod S],
 // so that every output is one FP32 chain in a fixed order: the result does not depend on the
-// launch geometry, and no atomics touch the values.
+// launch geometry, and no atomics touch the values.  The running sketch is kept twice in a row
+// (acc[t] = acc[t + S]), so acc[(t - h) mod S] = acc[t - h + S] needs no wrap test: for each
+// entry i a thread forms one address and reads its outputs' operands at fixed offsets from it,
+// one shared-memory load and one FMA per multiply-add.
 #include "common.cuh"
 #include "internal.h"
 
@@ -32,8 +35,8 @@ struct TsSmem {
   float* xs;       // d+1
   int32_t* bptr;   // S+1: bucket starts of the first CountSketch
   int32_t* bitem;  // d+1: its entries, bucket by bucket, increasing i
-  float* acc;      // S
-  float* nxt;      // S
+  float* acc;      // 2 S: the running sketch, twice
+  float* nxt;      // 2 S
 };
 
 __device__ __forceinline__ TsSmem ts_carve(unsigned char* raw, int q, int d1, int S) {
@@ -44,7 +47,7 @@ __device__ __forceinline__ TsSmem ts_carve(unsigned char* raw, int q, int d1, in
   m.bptr = reinterpret_cast<int32_t*>(m.xs + d1);
   m.bitem = m.bptr + (S + 1);
   m.acc = reinterpret_cast<float*>(m.bitem + d1);
-  m.nxt = m.acc + S;
+  m.nxt = m.acc + 2 * S;
   return m;
 }
 
@@ -95,6 +98,7 @@ __global__ void __launch_bounds__(TS_NT) k_tensorsketch(TsArgs a) {
         float v = 0.f;
         for (int k = m.bptr[t]; k < m.bptr[t + 1]; ++k) v = fmaf(m.sgn[m.bitem[k]], m.xs[m.bitem[k]], v);
         m.acc[t] = v;
+        m.acc[t + S] = v;
       }
       __syncthreads();
       for (int p = 1; p < q; ++p) {
@@ -104,21 +108,18 @@ __global__ void __launch_bounds__(TS_NT) k_tensorsketch(TsArgs a) {
         for (int i = 0; i < d1; ++i) {
           const float w = m.sgn[p * d1 + i] * m.xs[i];
           if (w == 0.f) continue;   // the same for every thread (sparse rows skip their zeros)
-          const int hh = m.hsh[p * d1 + i];
+          const float* src = m.acc + (S - m.hsh[p * d1 + i]) + tid;   // acc[t - h + S] for t = tid
 #pragma unroll
-          for (int k = 0; k < KT; ++k) {
-            const int t = tid + TS_NT * k;
-            if (t < S) {
-              int idx = t - hh;
-              idx += idx < 0 ? S : 0;
-              acc[k] = fmaf(w, m.acc[idx], acc[k]);
-            }
-          }
+          for (int k = 0; k < KT; ++k)
+            if (tid + TS_NT * k < S) acc[k] = fmaf(w, src[TS_NT * k], acc[k]);
         }
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
           const int t = tid + TS_NT * k;
-          if (t < S) m.nxt[t] = acc[k];
+          if (t < S) {
+            m.nxt[t] = acc[k];
+            m.nxt[t + S] = acc[k];
+          }
         }
         __syncthreads();
         float* sw = m.acc;
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(TS_NT) k_tensorsketch(TsArgs a) {
 
 size_t tensorsketch_smem_bytes(int q, int64_t d, int64_t S) {
   const int64_t d1 = d + 1;
-  return (size_t)(q * d1 * 8 + d1 * 4 + (S + 1) * 4 + d1 * 4 + 2 * S * 4);
+  return (size_t)(q * d1 * 8 + d1 * 4 + (S + 1) * 4 + d1 * 4 + 4 * S * 4);
 }
 
 cudaError_t launch_tensorsketch(const TsArgs& a, int nblocks, int64_t smax, cudaStream_t st) {
@@ -159,8 +160,8 @@ cudaError_t launch_tensorsketch(const TsArgs& a, int nblocks, int64_t smax, cuda
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
-  // about two CTAs per SM in all, each over a strided set of rows of one block
-  const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(a.nr, ceil_div(2 * (int64_t)nsm, nblocks)));
+  // about four CTAs per SM in all, each over a strided set of rows of one block
+  const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(a.nr, ceil_div(4 * (int64_t)nsm, nblocks)));
   const dim3 grid((unsigned)gx, (unsigned)nblocks);
   const int kt = (int)ceil_div(smax, TS_NT);
 #define RFF_TS(K)                                                                                      \
