@@ -112,3 +112,29 @@ def test_solver_matches_oracle(rff, case):
     assert np.array_equal(s2.weights(), W)
     s.close()
     s2.close()
+
+
+def test_largest_block_and_degree(rff):
+    """The largest column block (8192 features) at degree 4, and degree 8 on a small block:
+    the shared-memory layouts at their limits, still equal to the oracle."""
+    rng = np.random.default_rng(11)
+    for q, D, C, d in ((4, 8192, 1, 300), (8, 96, 1, 5)):
+        X = (rng.standard_normal((64, d)) * 0.3).astype(np.float32)
+        Z = torch.zeros((64, D), dtype=torch.float32, device="cuda")
+        rff.rff_tensorsketch_features(dev(X), 2, 3.0, 0.7, q, D, C, Z)
+        ref = ots.features(X.astype(np.float64), 2, 3.0, 0.7, q, orff.partition(D, C))
+        got = Z.cpu().numpy()
+        assert np.abs(got - ref).max() <= 5e-5 * np.abs(ref).max(), (q, np.abs(got - ref).max() / np.abs(ref).max())
+
+
+def test_shared_memory_limit_is_refused(rff):
+    """Degree x (d + 1) hash tables plus a block of 8192 features beyond the kernel's shared
+    memory: refused before any launch, by the step call and by set_data."""
+    X = torch.zeros((4, 5000), dtype=torch.float32, device="cuda")
+    Z = torch.zeros((4, 8192), dtype=torch.float32, device="cuda")
+    with pytest.raises(rff.RffError):
+        rff.rff_tensorsketch_features(X, 1, 1.0, 1.0, 8, 8192, 1, Z)
+    s = rff.Solver(prec="cached_z", feature_map="tensorsketch", degree=8, D=8192, C=1, m=1, loss="squared")
+    with pytest.raises(rff.RffError):
+        s.set_data(np.zeros((300, 5000), np.float32), np.zeros((300, 1), np.float32))
+    s.close()
