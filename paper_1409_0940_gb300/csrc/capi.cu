@@ -83,7 +83,6 @@ struct rff_admm_s {
   float zscale = 1.f;
   float ts_zmax = 0.f;           // TensorSketch: max |z| over the training rows (the split's scale)
   float* ts_buf = nullptr;       // TensorSketch scoring: TS_SCORE_ROWS rows of features
-  GemmDesc* ts_desc = nullptr;   // and the descriptor of their product with Wbar
   SgJob *p1jobs = nullptr, *p2jobs = nullptr;
   int np1 = 0, np2 = 0, nsplit_cz = 1;
   // stochastic block subsets: a block is active in an iteration when its Philox word is
@@ -303,7 +302,7 @@ size_t working_set_bytes(const rff_admm_s& s) {
     t += (size_t)s.foff.back() * f + (size_t)s.R * s.C * sizeof(GemmDesc);                     // factors
   }
   if (s.outer) t += (size_t)s.C * s.nslots * s.mpad * f;                                       // u = Z rhs
-  if (s.tensorsketch()) t += (size_t)TS_SCORE_ROWS * s.fslots * f + sizeof(GemmDesc) + 512;   // scoring rows
+  if (s.tensorsketch()) t += (size_t)TS_SCORE_ROWS * s.fslots * f + 256;   // scoring rows
   return t + (64u << 20);
 }
 
@@ -567,10 +566,7 @@ rff_status set_data_impl(rff_admm_t h, const XInput& xin, const float* Yin, int6
   AL(s.d_col_slot, s.C);
   AL(s.d_col_size, s.C);
   AL(s.d_zero, 2);
-  if (s.tensorsketch()) {
-    AL(s.ts_buf, (int64_t)TS_SCORE_ROWS * s.fslots);
-    AL(s.ts_desc, 1);
-  }
+  if (s.tensorsketch()) AL(s.ts_buf, (int64_t)TS_SCORE_ROWS * s.fslots);
   AL(s.bmask, (int64_t)s.R * s.C);
   AL(s.bctr, 1);
   if (s.split_path()) {
@@ -1708,8 +1704,7 @@ rff_status scores_pass(rff_admm_t h, const float* Xrows32, const __half* Xh, con
       CK(launch_tensorsketch(ta, s.C, ts_block_max(s), s.st));
       const GemmDesc g{s.ts_buf, s.Wbar, nullptr, out + r0 * s.mpad, (int)nr, (int)s.mpad, (int)s.fslots,
                        s.fslots, s.mpad, s.mpad, s.mpad};
-      CK(cudaMemcpyAsync(s.ts_desc, &g, sizeof(g), cudaMemcpyHostToDevice, s.st));
-      CK(launch_gemm_f32_nn(s.ts_desc, 1, (int)nr, (int)s.mpad, 1.f, 0.f, s.st));
+      CK(launch_gemm_f32_nn_one(g, 1.f, 0.f, s.st));
     }
   } else {
     PassArgs a = base_pass_args(s);

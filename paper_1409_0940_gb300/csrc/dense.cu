@@ -84,11 +84,11 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ descs
 // ------------------------------------------------------------------ FP32 NN GEMM
 // The per-iteration products x = Q r and r = b - H x: A (M x K) and B (K x N)
 // row-major with K-contiguous A rows, N-contiguous B rows; vector loads when the
-// tile is interior.  Tile 64 x 64, BK = 32.
-__global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict__ descs, float alpha, float beta,
-                                                     const uint8_t* __restrict__ bmask) {
+// tile is interior.  Tile 64 x 64, BK = 32.  descs null: the one product given by value.
+__global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict__ descs, const GemmDesc one,
+                                                     float alpha, float beta, const uint8_t* __restrict__ bmask) {
   if (bmask && !bmask[blockIdx.z]) return;
-  const GemmDesc g = descs[blockIdx.z];
+  const GemmDesc g = descs ? descs[blockIdx.z] : one;
   const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
   if (m0 >= g.M || n0 >= g.N) return;
   const float* __restrict__ A = static_cast<const float*>(g.A);
@@ -451,7 +451,14 @@ cudaError_t launch_gemm_f32_nn(const GemmDesc* descs_dev, int nbatch, int maxM, 
                                cudaStream_t st, const uint8_t* bmask) {
   if (nbatch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(maxM, 64), (unsigned)ceil_div(maxN, 64), (unsigned)nbatch);
-  k_gemm_f32_nn<<<grid, 256, 0, st>>>(descs_dev, alpha, beta, bmask);
+  k_gemm_f32_nn<<<grid, 256, 0, st>>>(descs_dev, GemmDesc{}, alpha, beta, bmask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_f32_nn_one(const GemmDesc& g, float alpha, float beta, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(g.M, 64), (unsigned)ceil_div(g.N, 64), 1);
+  k_gemm_f32_nn<<<grid, 256, 0, st>>>(nullptr, g, alpha, beta, nullptr);
   return cudaGetLastError();
 }
 

@@ -141,6 +141,8 @@ struct GemmDesc {          // D = alpha * op(A) op(B) + beta * Cm, row-major
 // bmask[b] != 0 (null: all run)
 cudaError_t launch_gemm_f32_nn(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, float alpha, float beta,
                                cudaStream_t st, const uint8_t* bmask = nullptr);
+// the same for one product whose descriptor is passed by value (no device copy of it)
+cudaError_t launch_gemm_f32_nn_one(const GemmDesc& g, float alpha, float beta, cudaStream_t st);
 // f64 with runtime transposes; double_float: FP64 in and out, double-float arithmetic inside
 cudaError_t launch_gemm_f64(const GemmDesc* descs_dev, int nbatch, int maxM, int maxN, int transA, int transB,
                             double alpha, double beta, int lower_only, cudaStream_t st, bool double_float = false);

@@ -138,3 +138,17 @@ def test_shared_memory_limit_is_refused(rff):
     with pytest.raises(rff.RffError):
         s.set_data(np.zeros((300, 5000), np.float32), np.zeros((300, 1), np.float32))
     s.close()
+
+
+def test_full_size_sampled_rows(rff):
+    """At the benchmark's size (200,000 x 440 rows, D = 16384 in 4 blocks: Z has 3.3e9 entries,
+    past 32-bit indexing), sampled rows of the device sketches equal the oracle's."""
+    n, d, D, C = 200_000, 440, 16384, 4
+    X = np.random.default_rng(8).standard_normal((n, d)).astype(np.float32)
+    Z = torch.empty((n, D), dtype=torch.float32, device="cuda")
+    rff.rff_tensorsketch_features(dev(X), 17, 10.0, 1.0, 2, D, C, Z)
+    rows = np.array([0, 1, 4097, 65535, 131071, 131072, 150000, 199998, 199999])
+    got = Z[torch.from_numpy(rows).cuda()].cpu().numpy()
+    del Z
+    ref = ots.features(X[rows].astype(np.float64), 17, 10.0, 1.0, 2, orff.partition(D, C))
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()

@@ -82,3 +82,43 @@ def test_blocks_are_independent_and_scaled():
     Z2 = ts.features(X, 3, 1.0, 1.0, 2, rff.partition(32, 2))
     assert np.allclose(Z2[:, :16], np.sqrt(0.5) * ts.sketch_block(X, 3, 1.0, 1.0, 2, 16, 0), atol=1e-14)
     assert not np.allclose(Z2[:, :16], Z2[:, 16:])
+
+
+def test_admm_with_sketches_reaches_ridge_closed_form():
+    """The solver over TensorSketch features (Z assembled from per-block sketches) converges to
+    the ridge minimiser (Z^T Z + n lam I)^-1 Z^T Y of that Z (Sec. 2.2); the sketches' larger
+    scale slows the linear rate at rho = 1, so 6000 iterations reach 1e-6."""
+    import synth
+    from oracle import admm
+    X, Y = synth.ridge(n=300, d=5, seed=4)
+    p = admm.Problem(X, Y, "squared", "l2", lam=1e-3, sigma=2.0, rho=1.0, D=96, R=2, C=3, seed=7,
+                     feature_map="tensorsketch", degree=2, coef0=1.0)
+    out = admm.admm(p, 6000)
+    W = admm.ridge_closed_form(p.Z(), p.Y, p.lam)
+    assert np.linalg.norm(out["Wbar"] - W) / np.linalg.norm(W) < 1e-6
+
+
+def test_sketch_ridge_tends_to_polynomial_kernel_ridge():
+    """With the exact polynomial kernel the ridge minimiser predicts f = K(Xq, X) (K + n lam I)^-1 Y
+    (eq. (krr)); the sketched ridge's predictions approach it as D grows (d = 30: the tensor
+    square has 961 entries, so the sketches keep colliding over this range of D)."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((60, 30)) / np.sqrt(30)
+    Y = np.tanh(X[:, :1] * X[:, 1:2])
+    Xq = rng.standard_normal((30, 30)) / np.sqrt(30)
+    sigma, c, q, lam, n = 1.0, 1.0, 2, 1e-3, 60
+    K = ts.polynomial_kernel(X, X, sigma, c, q)
+    f = ts.polynomial_kernel(Xq, X, sigma, c, q) @ np.linalg.solve(K + n * lam * np.eye(n), Y)
+    errs = []
+    Ds = [64, 256, 1024, 4096]
+    for D in Ds:
+        e = []
+        for seed in range(3):
+            cols = rff.partition(D, 2)
+            Z = ts.features(X, 60 + seed, sigma, c, q, cols)
+            W = Z.T @ np.linalg.solve(Z @ Z.T + n * lam * np.eye(n), Y)
+            e.append(np.abs(ts.features(Xq, 60 + seed, sigma, c, q, cols) @ W - f).mean())
+        errs.append(np.mean(e))
+    slope = np.polyfit(np.log(Ds), np.log(errs), 1)[0]
+    assert errs[-1] < 0.25 * errs[0], errs
+    assert -0.8 < slope < -0.25, (slope, errs)
