@@ -429,6 +429,48 @@ def run_ridge(args):
             "solve_ms_200_iters": ms, "clocks": clk.summary()}
 
 
+def run_columns(args):
+    """Column partitions (the paper's Sec. 5 experiment on C, at this workload's shape): the
+    multiclass workload (n from --n, default 200k) solved with C = 4, 8, 16, 32, 64 column
+    blocks on the command line's precision; per C the cached factors' bytes, the set-up time,
+    the device time per iteration, and the objective after 30 iterations relative to C = 4's."""
+    import torch
+
+    import paper_1409_0940_gb300 as rff
+    w = workload(args)
+    X, Y = make_data(w)
+    stream = torch.cuda.Stream()
+    rows, iters = [], 30
+    for C in (4, 8, 16, 32, 64):
+        wc = dict(w, C=C)
+        s = new_solver(rff, wc, args.prec, stream)
+        s.set_data(X, Y)
+        t0 = time.perf_counter()
+        s.solve(1, stats=False)                    # set-up and the first iteration
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        s.solve(2, stats=False)                    # graph capture
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.solve(iters - 3, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (iters - 3)
+        obj = s.solve(0)["objective"]
+        sj = -(-wc["D"] // C)
+        rows.append({"C": C, "features_per_block": sj, "factor_bytes": 2 * 3 * wc["R"] * C * sj * sj,
+                     "setup_s": setup_s, "ms_per_iter": ms, "objective_30": obj})
+        s.close()
+    for r in rows:
+        r["objective_vs_C4"] = r["objective_30"] / rows[0]["objective_30"]
+    return {"metric": "ADMM iter/s by column blocks", "value": 1e3 / rows[0]["ms_per_iter"], "unit": "iter/s",
+            "n_gpus": 1, "steps": iters, "warmup": 3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f16x3", "data": "synthetic",
+            "config": {"workload": w["name"] + "-columns", "prec": args.prec,
+                       "factor_bytes": "R C s_j^2 x 3 BF16 terms (the cached Q_ij)"},
+            "columns": rows}
+
+
 def run_sweep(args):
     """(sigma, lambda) sweep: 64 binary-logistic + l2 solves; per sigma one data set (n log-uniform in
     [10k, 400k], d = 128), one D (cycled over 1k..8k), one handle whose 8 columns are the 8 lambdas
@@ -621,7 +663,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-compare", action="store_true", help="skip the other precisions (profiling runs)")
     ap.add_argument("--n", type=int, default=0, help="rows of a reduced workload (profiling runs)")
-    ap.add_argument("--workload", default="multiclass", choices=["multiclass", "ridge", "sweep", "serve", "score"])
+    ap.add_argument("--workload", default="multiclass",
+                    choices=["multiclass", "ridge", "sweep", "serve", "score", "columns"])
     ap.add_argument("--loss", default="squared", choices=["squared", "hinge", "multinomial", "crammer_singer", "l1"],
                     help="loss of the multiclass workload")
     ap.add_argument("--feature-map", default="fourier", choices=["fourier", "laplace", "fastfood", "tensorsketch"],
@@ -636,7 +679,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.workload != "multiclass":
-        line = {"sweep": run_sweep, "serve": run_serve, "ridge": run_ridge, "score": run_score}[args.workload](args)
+        line = {"sweep": run_sweep, "serve": run_serve, "ridge": run_ridge, "score": run_score,
+                "columns": run_columns}[args.workload](args)
         print(json.dumps(line), flush=True)
         return
     if args.impl == "reference":
