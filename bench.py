@@ -471,6 +471,44 @@ def run_columns(args):
             "columns": rows}
 
 
+def run_rows(args):
+    """Scaling the rows at fixed D (the single-GPU analogue of the paper's weak scaling, Sec. 5):
+    the multiclass workload with n = 50k, 100k, 200k, 400k, 800k rows on the 4 x 4 grid; per n
+    the set-up time, the device time per iteration and the rows processed per second."""
+    import torch
+
+    import paper_1409_0940_gb300 as rff
+    w = workload(args)
+    stream = torch.cuda.Stream()
+    rows, iters = [], 20
+    for n in (50_000, 100_000, 200_000, 400_000, 800_000):
+        wn = dict(w, n=n)
+        X, Y = make_data(wn)
+        s = new_solver(rff, wn, args.prec, stream)
+        s.set_data(X, Y)
+        t0 = time.perf_counter()
+        s.solve(1, stats=False)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        s.solve(2, stats=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.solve(iters, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / iters
+        rows.append({"n": n, "setup_s": setup_s, "ms_per_iter": ms, "iter_per_s": 1e3 / ms,
+                     "rows_per_s": n * 1e3 / ms})
+        s.close()
+        del X, Y
+    return {"metric": "ADMM rows/s by n", "value": rows[2]["rows_per_s"], "unit": "rows/s", "n_gpus": 1,
+            "steps": iters, "warmup": 3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.prec == "fp32" else "f16x3", "data": "synthetic",
+            "config": {"workload": w["name"].replace("200k", "n") + "-rows", "prec": args.prec,
+                       "value": "rows per second at n = 200k"},
+            "rows": rows}
+
+
 def run_sweep(args):
     """(sigma, lambda) sweep: 64 binary-logistic + l2 solves; per sigma one data set (n log-uniform in
     [10k, 400k], d = 128), one D (cycled over 1k..8k), one handle whose 8 columns are the 8 lambdas
@@ -664,7 +702,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the other precisions (profiling runs)")
     ap.add_argument("--n", type=int, default=0, help="rows of a reduced workload (profiling runs)")
     ap.add_argument("--workload", default="multiclass",
-                    choices=["multiclass", "ridge", "sweep", "serve", "score", "columns"])
+                    choices=["multiclass", "ridge", "sweep", "serve", "score", "columns", "rows"])
     ap.add_argument("--loss", default="squared", choices=["squared", "hinge", "multinomial", "crammer_singer", "l1"],
                     help="loss of the multiclass workload")
     ap.add_argument("--feature-map", default="fourier", choices=["fourier", "laplace", "fastfood", "tensorsketch"],
@@ -680,7 +718,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.workload != "multiclass":
         line = {"sweep": run_sweep, "serve": run_serve, "ridge": run_ridge, "score": run_score,
-                "columns": run_columns}[args.workload](args)
+                "columns": run_columns, "rows": run_rows}[args.workload](args)
         print(json.dumps(line), flush=True)
         return
     if args.impl == "reference":
