@@ -38,6 +38,7 @@ WORKLOAD = dict(name="multiclass-200k-d440-D16384-m147-4x4", n=200_000, d=440, m
                 C=4, loss="squared", reg="l2", lam=1e-5, rho=1.0, data_seed=1, philox_seed=2)
 METRIC = "ADMM iter/s"
 TRAFFIC_200K = {"pass1": 1.654e9, "pass2": 1.219e9}     # kernel -> DRAM bytes per launch (see run_ours)
+TRAFFIC_CZ_200K = {"pass1": 14.35e9, "pass2": 14.08e9}   # the cached-Z streamed passes, likewise
 
 
 def peaks():
@@ -292,7 +293,10 @@ def run_ours(args, rank, world):
         # the streamed pass reads Z once: HBM-bound (the tensor work, 3 x 2 n D m_pad, would take
         # slightly less time at the sustained BF16 peak)
         gbs = bytes_per_cached_pass(w) * act / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+        # DRAM bytes per launch from an ncu capture at n = 100k scaled by rows
+        # (profiles/k_split_gemm_cached_z_multiclass_100k.md); None off that workload
+        traffic = TRAFFIC_CZ_200K.get(ph[3:]) if not args.n and act == 1.0 else None
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
                 "kernel": ph[3:], "peak_source": src + " copy bandwidth", "tensor_tflops": achieved,
                 "tensor_frac": achieved / bf16_sus}
     else:
