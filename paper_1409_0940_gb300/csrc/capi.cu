@@ -7,6 +7,8 @@
 #include "internal.h"
 #include "tc.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -25,6 +27,15 @@ struct DevBuf {
 };
 
 constexpr int64_t TS_SCORE_ROWS = 2048;   // TensorSketch scoring: rows sketched per product
+
+// A named host range for profilers (NVTX; nothing happens unless a tool is attached): the
+// set-up stages, the iterations and scoring show up by name on a timeline.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace
 
@@ -784,6 +795,7 @@ namespace {
 // passes only write their scratch outputs (R partials, O'), which every
 // iteration recomputes.
 rff_status autotune(rff_admm_t h) {
+  NvtxRange range("rff set-up: autotune");
   auto& s = *h;
   if (!s.split_path() || s.cached_z()) return RFF_OK;
   // RFF_TC_GEOMETRY="kc,zt" (kc 64 or 32, zt 0 or 1) fixes the geometry instead
@@ -872,6 +884,7 @@ TsArgs ts_args(const rff_admm_s& s, const float* X, int64_t ldx, const int32_t* 
 int64_t ts_block_max(const rff_admm_s& s) { return *std::max_element(s.col_size.begin(), s.col_size.end()); }
 
 rff_status materialise_z(rff_admm_t h) {
+  NvtxRange range("rff set-up: materialise Z");
   auto& s = *h;
   const int64_t chunk = materialise_chunk(s);
   rff_status rs = ensure_scratch(h, (size_t)chunk * s.fslots * 4);
@@ -1107,6 +1120,7 @@ rff_status regenerate_features(rff_admm_t h) {
 }
 
 rff_status setup_factors(rff_admm_t h) {
+  NvtxRange range("rff set-up: features, Gram, factors");
   auto& s = *h;
   {
     rff_status r = generate_features(h);
@@ -1608,6 +1622,7 @@ rff_status capture_iteration(rff_admm_t h) {
 // Enqueue `iters` iterations on the handle's stream (no host synchronisation).
 // copy_old: keep nu, Obar, mu, Wbar, mu' of the iteration before the last (residuals).
 rff_status enqueue_iterations(rff_admm_t h, int iters, bool copy_old) {
+  NvtxRange range("rff iterations");
   auto& s = *h;
   if (s.features_released) {   // a solve keeps them resident again
     rff_status r = regenerate_features(h);
@@ -2107,6 +2122,7 @@ rff_status rff_sweep_run(rff_admm_t* handles, int32_t n, int32_t iters) {
 
 rff_status rff_admm_predict(rff_admm_t h, const float* Xq, int64_t q, float* scores, int is_device_ptr) {
   if (!h) return RFF_EINVAL;
+  NvtxRange range("rff predict");
   h->err.clear();
   if (!h->has_data || !h->factored) return h->fail(RFF_ENOTREADY, "predict needs a solve first");
   if (q < 0) return h->fail(RFF_EINVAL, "q < 0");
