@@ -149,7 +149,7 @@ __device__ __forceinline__ bool wait1(uint32_t bar, uint32_t parity, SH& sh, con
   }
 }
 
-// warp-uniform bounded wait: lane 0 polls, the verdict is broadcast
+// warp-uniform bounded wait: lane 0 polls, the outcome is broadcast
 template <class SH>
 __device__ __forceinline__ bool waitw(uint32_t bar, uint32_t parity, SH& sh, const TcArgs& a, int code) {
   int ok = 0;
