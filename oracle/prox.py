@@ -30,7 +30,13 @@ dual, a Euclidean projection onto the probability simplex computed by sorting.
 Pins: brute-force minimisation of the prox objective on random tiny inputs,
 the t -> 0 limit (prox -> identity), kink cases of the hinge, the optimality
 (subgradient) conditions of the multiclass hinge and its two-class reduction to
-the binary hinge of the output difference.
+the binary hinge of the output difference (tests/test_oracle_prox.py).  The values
+(loss_value, reg_value): every loss and regulariser written from its definition in
+40-digit arithmetic, special values (log 2, log m, unit margins), the two-class
+reductions of the multinomial and multiclass hinge losses to the binary ones, shift
+invariance, the logistic asymptotes, the Moreau-envelope gradient identity that ties
+each value to its prox, and the converged ADMM iterate minimising the objective they
+compose (tests/test_oracle_values.py).
 """
 import numpy as np
 

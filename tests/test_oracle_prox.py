@@ -8,6 +8,7 @@ from oracle import prox as P
 
 mp = pytest.importorskip("mpmath").mp
 mp.dps = 40
+from loss_definitions import row_loss_mp  # noqa: E402  (the losses from their definitions)
 
 
 def _golden(f, a, b, tol=1e-25):
@@ -93,7 +94,8 @@ def test_multinomial_brute_force(m):
         c = int(rng.integers(m))
         y = -np.ones(m)
         y[c] = 1.0
-        f = lambda o: 0.5 * np.sum((o - v) ** 2) + t * P.loss_value("multinomial", y[None], o[None])
+        # the objective from the loss's own definition, not from the oracle's loss_value
+        f = lambda o: 0.5 * np.sum((o - v) ** 2) + t * float(row_loss_mp("multinomial", y, o))
         res = optimize.minimize(f, v, method="BFGS", options=dict(gtol=1e-13, maxiter=5000))
         got = P.prox_loss("multinomial", v[None], y[None], t)[0]
         assert np.max(np.abs(got - res.x)) < 1e-6
@@ -210,6 +212,6 @@ def test_crammer_singer_brute_force(m):
         res = optimize.minimize(f, z0, method="SLSQP", constraints=cons,
                                 options=dict(ftol=1e-15, maxiter=1000))
         got = P.prox_loss("crammer_singer", v[None], y[None], t)[0]
-        obj = lambda o: 0.5 * np.sum((o - v) ** 2) + t * P.loss_value("crammer_singer", y[None], o[None])
+        obj = lambda o: 0.5 * np.sum((o - v) ** 2) + t * float(row_loss_mp("crammer_singer", y, o))
         assert np.max(np.abs(got - res.x[:m])) < 1e-6
         assert obj(got) <= obj(res.x[:m]) + 1e-12
