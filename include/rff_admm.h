@@ -267,25 +267,29 @@ rff_status rff_admm_predict(rff_admm_t h, const float* Xq, int64_t q, float* sco
 rff_status rff_admm_predict_labels(rff_admm_t h, const float* Xq, int64_t q, int32_t* labels, int is_device_ptr);
 
 /* Scores without allocating device memory (the paper has no counterpart: it is an
- * interface for callers that cannot call cudaMalloc when they score -- code being
- * captured into a CUDA graph, where allocation is not a capturable operation, and
- * serving loops whose device memory is owned by another pool or that must not
- * allocate on the request path).  Same result as rff_admm_predict, same kernels.
- * Xq (q x d) and scores (q x m) are row-major float32 DEVICE pointers; the call
- * synchronises the handle's stream before it returns.
- * Scratch: one fixed 32 MiB array in device global memory, defined by the library
- * and held by every GPU that loads it until the process exits.  A call needs
- * q_pad * (4 d_pad + 4 m_pad) bytes on the FP32 path and q_pad * (8 d_pad + 4 m_pad)
- * on the split-BF16 path (q_pad = q rounded up to 128, d_pad = d rounded up to 64,
- * m_pad = m rounded up to 16); larger q returns RFF_EINVAL with the limit in the
- * error text -- score in smaller batches.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array and it keeps the previous call's contents (the call
- * clears what must start at zero): calls that overlap on the GPU -- two handles
- * or threads scoring at the same time -- race on it.
- * Errors: RFF_ENOTREADY before the first solve, RFF_EINVAL for NULL pointers,
- * NaN/Inf queries or q beyond the scratch, RFF_ECUDA. */
+ * interface for callers that cannot call cudaMalloc when they score -- a serving loop
+ * whose device memory is handed out entirely by another allocator's pool, so that a
+ * cudaMalloc of its own would fail or fragment that pool, or one that must not take the
+ * device-wide synchronisation an allocation or a free can cost in the middle of a
+ * request).  Same result as rff_admm_predict with device pointers, bit for bit: the
+ * same kernels on the same padded layout.  Xq (q x d) and scores (q x m) are row-major
+ * float32 DEVICE pointers.  The call synchronises the handle's stream twice (after the
+ * finite-value check of the queries and before it returns).
+ * Scratch: one fixed 32 MiB array in device global memory, defined by the library and
+ * held by every GPU that loads it until the process exits.  With q_pad = q rounded up to
+ * 128, d_pad = d rounded up to 64, m_pad = m rounded up to 16 and up() rounding up to a
+ * multiple of 256 bytes, a call needs up(4 q_pad d_pad) + 4 q_pad m_pad bytes on the
+ * FP32 path and up(4 q_pad d_pad) + 2 up(2 q_pad d_pad) + 4 q_pad m_pad bytes on the
+ * split path (the queries in FP32, their FP16 hi/lo split, the padded scores); a larger
+ * q returns RFF_EINVAL with the limit in the error text -- score in smaller batches.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * once per device, that device current); make that first call before any stream
+ * capture begins.
+ * All calls share the array and it keeps the previous call's contents (the call clears
+ * what must start at zero): calls that overlap on the GPU -- two handles or threads
+ * scoring at the same time -- race on it.
+ * Errors: RFF_ENOTREADY before the first solve or after rff_admm_release_features,
+ * RFF_EINVAL for NULL pointers, NaN/Inf queries or q beyond the scratch, RFF_ECUDA. */
 rff_status rff_admm_predict_noalloc(rff_admm_t h, const float* Xq, int64_t q, float* scores);
 
 /* Copy the consensus weights Wbar (D x m, row-major, rows in global feature

@@ -181,10 +181,16 @@ def make_params(loss="squared", reg="l2", lam=1e-4, sigma=1.0, rho=1.0, D=512, R
 
 
 # ----------------------------------------------------------------- C ABI, same names
+# (m, d) of every handle this binding created, for the shape checks of the calls that take
+# bare device pointers (the library cannot see how large a caller's buffer is)
+_dims = {}
+
+
 def rff_admm_create(params, stream=None):
     h = ctypes.c_void_p()
     _check(lib.rff_admm_create(ctypes.byref(params), _stream(stream), ctypes.byref(h)), None,
            "rff_admm_create rejected the parameters")
+    _dims[h.value] = [int(params.m), None]
     return h
 
 
@@ -195,6 +201,8 @@ def rff_admm_set_data(h, X, Y):
     if dx != dy:
         raise TypeError("X and Y must both be host or both be device arrays")
     _check(lib.rff_admm_set_data(h, px, py, n, d, dx), h)
+    if h.value in _dims:
+        _dims[h.value][1] = int(d)
 
 
 def rff_admm_set_data_csr(h, indptr, indices, values, Y, d):
@@ -207,6 +215,8 @@ def rff_admm_set_data_csr(h, indptr, indices, values, Y, d):
     if len({dp, di, dv, dy}) != 1:
         raise TypeError("the CSR arrays and Y must all be host or all be device arrays")
     _check(lib.rff_admm_set_data_csr(h, pp, pi, pv, values.shape[0], py, n, d, dy), h)
+    if h.value in _dims:
+        _dims[h.value][1] = int(d)
 
 
 def rff_admm_solve(h, iters, stats=True):
@@ -236,7 +246,18 @@ def rff_admm_predict_labels(h, Xq, out):
 
 
 def rff_admm_predict_noalloc(h, Xq, out):
-    """Scores into `out` without any device allocation (device tensors only)."""
+    """Scores into `out` without any device allocation (device tensors only).  The
+    shapes are checked against the handle first: the library reads q x d queries and
+    writes q x m scores through bare device pointers."""
+    m, d = _dims.get(getattr(h, "value", h), (None, None))
+    if m is None or d is None:
+        raise TypeError("rff_admm_predict_noalloc: the handle has no data set through this binding")
+    if len(Xq.shape) != 2 or Xq.shape[1] != d:
+        raise TypeError("rff_admm_predict_noalloc: queries of shape %s, the model takes (q, %d)"
+                        % (tuple(Xq.shape), d))
+    if tuple(out.shape) != (Xq.shape[0], m):
+        raise TypeError("rff_admm_predict_noalloc: scores of shape %s, expected (%d, %d)"
+                        % (tuple(out.shape), Xq.shape[0], m))
     pq, dq = _ptr(Xq)
     po, do = _ptr(out)
     if not (dq and do):
@@ -316,6 +337,7 @@ def rff_sweep_run(handles, iters):
 
 
 def rff_admm_destroy(h):
+    _dims.pop(getattr(h, "value", h), None)
     lib.rff_admm_destroy(h)
 
 

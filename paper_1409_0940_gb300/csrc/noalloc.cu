@@ -1,16 +1,16 @@
 // Scoring that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc at the moment they need scores: code that
-// is being captured into a CUDA graph (allocation is not a capturable
-// operation), and serving loops whose device memory belongs to a pool owned by
-// someone else or that must not allocate on the request path (an allocation can
-// synchronise the device and fragments the pool).  rff_admm_predict_noalloc serves
-// them: it runs the same kernels as rff_admm_predict, but its scratch (the
-// slot-padded queries, their BF16 split and the padded scores) lives in one
-// fixed array in device global memory that the library defines once, so a call
-// allocates nothing.  The price: every GPU that loads the library holds the array
-// (32 MiB) until the process exits, a call can score at most as many queries as
-// fit in it, and all calls share it.
+// Some callers cannot call cudaMalloc at the moment they need scores: serving loops
+// whose device memory is handed out entirely by another allocator's pool (a cudaMalloc
+// of their own fails, or fragments that pool), and loops that must not take the
+// device-wide synchronisation an allocation or a free can cost in the middle of a
+// request.  rff_admm_predict_noalloc serves them: it runs the same kernels as
+// rff_admm_predict, but its scratch (the slot-padded queries in FP32, their FP16 hi/lo
+// split and the padded scores) lives in one fixed array in device global memory that
+// the library defines once, so a call allocates nothing.  The price: every GPU that
+// loads the library holds the array (32 MiB) until the process exits, a call can score
+// at most as many queries as fit in it, and all calls share it (calls that overlap on
+// the GPU race on it).  A call synchronises the handle's stream.
 #include <mutex>
 #include <string>
 

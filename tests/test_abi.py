@@ -73,3 +73,26 @@ def test_step_entry_points_validate_sizes(rff):
     assert rff.lib.rff_prox_loss(7, None, None, 1, 1, 1.0, 8, None, None) == rff.RFF_EINVAL
     assert rff.lib.rff_prox_reg(5, None, 1, 1.0, None, None) == rff.RFF_EINVAL
     assert rff.lib.rff_cholesky_f64(None, 1, 0, None, None) == rff.RFF_EINVAL
+
+
+def test_noalloc_binding_checks_shapes_before_any_call(rff):
+    """rff_admm_predict_noalloc takes bare device pointers, so the binding checks the
+    buffers' shapes against the handle's (q, d) and (q, m) before marshalling anything;
+    a handle it did not create (or without data) is refused the same way."""
+    import numpy as np
+    fake = ctypes.c_void_p(0x1000)
+    with pytest.raises(TypeError, match="no data"):
+        rff.rff_admm_predict_noalloc(fake, np.zeros((4, 3), np.float32), np.zeros((4, 2), np.float32))
+    rff._dims[fake.value] = [2, 3]
+    try:
+        with pytest.raises(TypeError, match="queries of shape"):
+            rff.rff_admm_predict_noalloc(fake, np.zeros((4, 5), np.float32), np.zeros((4, 2), np.float32))
+        with pytest.raises(TypeError, match="scores of shape"):
+            rff.rff_admm_predict_noalloc(fake, np.zeros((4, 3), np.float32), np.zeros((4, 3), np.float32))
+        with pytest.raises(TypeError, match="scores of shape"):
+            rff.rff_admm_predict_noalloc(fake, np.zeros((4, 3), np.float32), np.zeros((5, 2), np.float32))
+        # right shapes on host arrays: refused for not being device memory, still before the call
+        with pytest.raises(TypeError, match="device tensors"):
+            rff.rff_admm_predict_noalloc(fake, np.zeros((4, 3), np.float32), np.zeros((4, 2), np.float32))
+    finally:
+        rff._dims.pop(fake.value, None)
