@@ -11,8 +11,17 @@ dual updates.  Set-up (Philox draw, Gram matrices, FP64 Cholesky, inverses) is
 done before the timed region.  Every input of the timed region (X split,
 V_ij, W'_ij, the factors) is larger than the 129 MB L2, so no flush is needed.
 
+The same JSON line carries, at one GPU, two more workloads as sub-objects:
+  "large"  the MNIST-8M-shaped implicit solve: n = 8.1M, d = 784 (~20 % non-zero,
+           stored dense), m = 10, sigma = 9, D = 65,536 in 32 x 16 blocks, one-vs-rest
+           hinge + l2, lambda = 1e-6, split precision; Z (2 TB in FP32) is never stored;
+  "serve"  the serving loop: Poisson arrivals of solve requests (n 5k-500k, d 32-784,
+           D 1k-32k, three losses, two regularisers) and scoring batches of 1-4096
+           queries, the solve rate at 70 % of the measured isolated capacity.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split_bf16|fp32|cached_z]
                   [--loss squared|hinge|multinomial|crammer_singer|l1] [--block-fraction P]
+                  [--workload multiclass|large|serve|ridge|sweep|score] [--no-large] [--no-serve]
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
 
 --loss swaps the loss of the same workload; --block-fraction P < 1 runs the stochastic
@@ -20,7 +29,8 @@ variant (each block takes part in an iteration's graph projection with probabili
 
 One JSON line on rank 0.  With N > 1 (torchrun), each rank solves its own
 replica of the workload (the method keeps every block on one GPU) and the value
-is the total iterations per second of all ranks ("replicas only", weak scaling).
+is the total iterations per second of all ranks ("replicas only", weak scaling);
+the "large" and "serve" sub-objects run at N = 1 only.
 """
 import argparse
 import json
@@ -35,9 +45,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="multiclass-200k-d440-D16384-m147-4x4", n=200_000, d=440, m=147, sigma=10.0, D=16384, R=4,
-                C=4, loss="squared", reg="l2", lam=1e-5, rho=1.0, data_seed=1, philox_seed=2)
+                C=4, loss="squared", reg="l2", lam=1e-5, rho=1.0, data_seed=1, philox_seed=2, data="multiclass")
+# the MNIST-8M-shaped implicit solve (its Z would be 8.1M x 65,536 floats, 2 TB in FP32)
+LARGE = dict(name="mnist8m-shaped-8.1M-d784-D65536-m10-32x16-hinge", n=8_100_000, d=784, m=10, sigma=9.0,
+             D=65536, R=32, C=16, loss="hinge", reg="l2", lam=1e-6, rho=1.0, data_seed=3, philox_seed=4,
+             data="sparse01", feature_map="fourier", block_fraction=1.0)
 METRIC = "ADMM iter/s"
-TRAFFIC_200K = {"pass1": 1.654e9, "pass2": 1.219e9}     # kernel -> DRAM bytes per launch (see run_ours)
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+# DRAM bytes per launch of the fused passes, from an ncu capture of the current kernel at
+# n = 100k scaled to 200k rows (X, V, O' grow with n); None once the kernel has changed
+TRAFFIC_200K = {"pass1": 1.654e9, "pass2": 1.219e9}
 TRAFFIC_CZ_200K = {"pass1": 14.35e9, "pass2": 14.08e9}   # the cached-Z streamed passes, likewise
 
 
@@ -109,6 +126,8 @@ def make_data(w, n=None):
     n = n or w["n"]
     if w.get("feature_map", "fourier") == "laplace":   # the Laplace map takes histograms
         return synth.histograms(n=n, d=w["d"], m=w["m"], seed=w["data_seed"])
+    if w.get("data") == "sparse01":
+        return synth.sparse01(n=n, d=w["d"], m=w["m"], seed=w["data_seed"])
     return synth.multiclass(n=n, d=w["d"], m=w["m"], seed=w["data_seed"])
 
 
@@ -118,14 +137,27 @@ def solver_kw(w, prec):
                 degree=w.get("degree", 2), coef0=w.get("coef0", 1.0))
 
 
+def pads(w):
+    return -(-w["m"] // 16) * 16, -(-w["d"] // 64) * 64   # m_pad, d_pad (the slot layout's padding)
+
+
+def survey_flops_per_pass(w):
+    """Algorithmic tensor work of one regeneration pass, as the roofline counts it: the
+    three split products of X.G at the data's own d (3 x 2 n d D) and one chained product
+    at m_pad (2 n D m_pad)."""
+    mpad, _ = pads(w)
+    return 3 * 2 * w["n"] * w["d"] * w["D"] + 2 * w["n"] * w["D"] * mpad
+
+
 def flops_per_iter(w, prec):
-    """Algorithmic work of one iteration.  Useful FP32-equivalent flops: two
-    regenerations of X.G (2 n d D each) and two chained products (2 n D m each),
-    the s_j x s_j x m product with the cached inverse per block.  Executed BF16 tensor flops of
-    the split path: 3 products for X.G and 3 for each chained product at m_pad."""
+    """Useful FP32-equivalent flops of one iteration (two regenerations of X.G, 2 n d D each,
+    two chained products, 2 n D m each, and the s_j x s_j x m product with the cached inverse
+    per block), and the flops one pass executes on its precision's units: on the split path
+    3 products for X.G at d_pad (the phase folded into a padding column of ones where one is
+    free) and 3 for the chained
+    product at m_pad."""
     n, d, D, m, R, C = w["n"], w["d"], w["D"], w["m"], w["R"], w["C"]
-    mpad = -(-m // 16) * 16
-    dpad = -(-d // 64) * 64
+    mpad, dpad = pads(w)
     s = D // C
     useful = 2 * (2 * n * d * D) + 2 * (2 * n * D * m) + R * C * 2 * s * s * m
     pass_tc = 3 * 2 * n * dpad * D + 3 * 2 * n * D * mpad       # one pass, executed on tensor cores
@@ -139,8 +171,8 @@ def bytes_per_cached_pass(w):
     as a hi/lo BF16 pair (4 n D), the n x m_pad chained operand or result of all C
     column blocks (4 C n m_pad), and the D x m_pad operand or result of all R row
     blocks (4 R D m_pad)."""
-    n, D, m, R, C = w["n"], w["D"], w["m"], w["R"], w["C"]
-    mpad = -(-m // 16) * 16
+    n, D, R, C = w["n"], w["D"], w["R"], w["C"]
+    mpad, _ = pads(w)
     return 4 * n * D + 4 * C * n * mpad + 4 * R * D * mpad
 
 
@@ -187,10 +219,11 @@ def active_fraction(rff, w, k0, k1):
     return float(np.mean((w0 >> 8) < np.uint32(int(np.floor(p * 2.0 ** 24)))))
 
 
-def measure(rff, w, X, Y, prec, steps, warmup, stream):
+def measure(rff, w, X, Y, prec, steps, warmup, stream, objective=False):
     """warmup untimed iterations (the first call also builds the factors), then steps
     iterations timed with CUDA events on the solver's stream; returns the device ms,
-    the phase profile, the consensus weights and the clock record."""
+    the phase profile, the consensus weights, the clock record and (objective=True) the
+    objective at the final consensus weights."""
     import torch
     s = new_solver(rff, w, prec, stream)
     s.set_data(X, Y)
@@ -206,12 +239,47 @@ def measure(rff, w, X, Y, prec, steps, warmup, stream):
     ms = e0.elapsed_time(e1)
     prof = s.profile()
     W = s.weights()
+    obj = s.solve(0)["objective"] if objective else None
     s.close()
-    return ms, prof, W, clk
+    return ms, prof, W, clk, obj
+
+
+def oracle_errors(W, ref):
+    """Relative Frobenius error of W on the stored sample of the FP64 oracle's Wbar."""
+    import numpy as np
+    Wf = W.astype(np.float64).ravel()
+    return float(np.linalg.norm(Wf[ref["idx"]] - ref["w"]) / np.linalg.norm(ref["w"]))
+
+
+def compare_precisions(rff, w, X, Y, main_prec, stream):
+    """The three precisions on the same workload, each for the 23 iterations of the stored
+    FP64 oracle iterate (tests/golden/multiclass_200k_wbar23_sample.npz, written by a script
+    that calls only the oracle): speed over the last 20, and the relative error of the
+    consensus weights and of the objective against the oracle's."""
+    import numpy as np
+    path = os.path.join(GOLDEN, "multiclass_200k_wbar23_sample.npz")
+    default = all(w[k] == WORKLOAD[k] for k in ("n", "d", "m", "D", "R", "C", "loss", "reg", "lam", "sigma"))
+    ref = np.load(path) if default and w["block_fraction"] == 1.0 and w["feature_map"] == "fourier" else None
+    out = {}
+    for prec in ("split_bf16", "cached_z", "fp32"):
+        if prec == "split_bf16" and w["feature_map"] == "laplace":
+            continue                      # the implicit split precision takes the Fourier map only
+        if prec != "cached_z" and w["feature_map"] == "tensorsketch":
+            continue                      # sketches are formed once: cached-Z precision only
+        k = 20 if prec != "fp32" else 5
+        ms_p, _, W_p, _, obj = measure(rff, w, X, Y, prec, k, 23 - k, stream, objective=True)
+        out[prec] = {"iter_per_s": k / (ms_p * 1e-3), "iterations": 23, "objective": obj}
+        if ref is not None:
+            out[prec]["rel_err_vs_fp64_oracle"] = oracle_errors(W_p, ref)
+            if "objective" in ref.files:
+                oo = float(ref["objective"])
+                out[prec]["objective_rel_err_vs_fp64_oracle"] = abs(obj - oo) / abs(oo)
+    if ref is not None:
+        out["oracle"] = "FP64 oracle iterate after 23 iterations, sample of %d Wbar entries" % ref["idx"].size
+    return out
 
 
 def run_ours(args, rank, world):
-    import numpy as np
     import torch
 
     import paper_1409_0940_gb300 as rff
@@ -224,7 +292,7 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    ms, prof, W_main, clk = measure(rff, w, X, Y, args.prec, args.steps, args.warmup, stream)
+    ms, prof, W_main, clk, _ = measure(rff, w, X, Y, args.prec, args.steps, args.warmup, stream)
     if dist:
         dist.barrier()
         ms = max_over_ranks(ms, dist, "cuda")
@@ -247,30 +315,9 @@ def run_ours(args, rank, world):
                "d2h_bytes_per_step": Wh.numel() * 4 // args.steps,
                "note": "set_data + set-up + K iterations + get_weights, pinned host buffers"}
 
-    # the other precisions on the same workload and iteration count: speed, and the
-    # relative difference of the consensus weights (all three approximate the same
-    # FP64 iterate; the oracle parity itself is in the tests)
     compare = None
     if not args.no_compare and rank == 0:
-        compare = {}
-        Ws = {args.prec: W_main}
-        for prec in ("split_bf16", "cached_z", "fp32"):
-            if prec == "split_bf16" and w["feature_map"] == "laplace":
-                continue                      # the implicit split precision takes the Fourier map only
-            if prec != "cached_z" and w["feature_map"] == "tensorsketch":
-                continue                      # sketches are formed once: cached-Z precision only
-            if prec == args.prec:
-                compare[prec] = {"iter_per_s": args.steps / (ms * 1e-3)}
-                continue
-            k = args.steps if prec != "fp32" else max(1, min(args.steps, 5))
-            # same total iteration count as the main run: the untimed part makes up the rest
-            ms_p, _, W_p, _ = measure(rff, w, X, Y, prec, k, args.warmup + args.steps - k, stream)
-            Ws[prec] = W_p
-            compare[prec] = {"iter_per_s": k / (ms_p * 1e-3)}
-        ref = Ws["fp32"].astype(np.float64)
-        for prec, Wp in Ws.items():
-            compare[prec]["rel_diff_vs_fp32"] = float(np.linalg.norm(Wp - ref) / np.linalg.norm(ref))
-        compare["iterations"] = args.warmup + args.steps
+        compare = compare_precisions(rff, w, X, Y, args.prec, stream)
 
     useful, exec_pass = flops_per_iter(w, args.prec)
     # the stochastic variant's passes do the work of its active blocks alone
@@ -280,30 +327,30 @@ def run_ours(args, rank, world):
     # dominant kernel: the larger of the two fused passes
     ph = "ms_pass2" if prof["ms_pass2"] >= prof["ms_pass1"] else "ms_pass1"
     per_launch_ms = prof[ph] / max(prof["iters"], 1)
-    achieved = exec_pass / (per_launch_ms * 1e-3) / 1e12
+    executed = exec_pass / (per_launch_ms * 1e-3) / 1e12
     if args.prec == "split_bf16":
-        # DRAM bytes per launch from an ncu capture of the current k_regen_tc at n = 100k, scaled
-        # to the 200k-row workload by rows (profiles/k_regen_tc_multiclass_100k.md); None while
-        # the kernel has changed since the last capture
+        achieved = survey_flops_per_pass(w) * act / (per_launch_ms * 1e-3) / 1e12
         traffic = TRAFFIC_200K.get(ph[3:]) if not args.n and act == 1.0 else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sus, "unit": "TFLOP/s",
-                "frac": achieved / bf16_sus, "traffic": traffic, "kernel": ph[3:],
-                "peak_source": src + " sustained bf16"}
+                "frac": achieved / bf16_sus, "traffic": traffic, "kernel": "k_regen_tc " + ph[3:],
+                "peak_source": src + " sustained bf16",
+                "count": "3 x 2 n d D (X.G, three split products at d) + 2 n D m_pad (one chained product) "
+                         "per launch",
+                "executed_tflops": executed, "executed_frac": executed / bf16_sus,
+                "executed_count": "3 x 2 n d_pad D + 3 x 2 n D m_pad (every product the kernel issues)"}
     elif args.prec == "cached_z":
         # the streamed pass reads Z once: HBM-bound (the tensor work, 3 x 2 n D m_pad, would take
         # slightly less time at the sustained BF16 peak)
         gbs = bytes_per_cached_pass(w) * act / (per_launch_ms * 1e-3) / 1e9
-        # DRAM bytes per launch from an ncu capture at n = 100k scaled by rows
-        # (profiles/k_split_gemm_cached_z_multiclass_100k.md); None off that workload
         traffic = TRAFFIC_CZ_200K.get(ph[3:]) if not args.n and act == 1.0 else None
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
-                "kernel": ph[3:], "peak_source": src + " copy bandwidth", "tensor_tflops": achieved,
-                "tensor_frac": achieved / bf16_sus}
+                "kernel": "k_split_gemm " + ph[3:], "peak_source": src + " copy bandwidth",
+                "tensor_tflops": executed, "tensor_frac": executed / bf16_sus}
     else:
         # FP32 SIMT: the measured FFMA throughput of this GPU (independent chains, one launch)
         alu_peak, _ = rff.rff_measure_fma_peaks(stream.cuda_stream)
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None, "kernel": ph[3:],
+        roof = {"bound": "alu", "achieved": executed, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": executed / alu_peak, "traffic": None, "kernel": "k_pass_simt " + ph[3:],
                 "peak_source": "measured FFMA chains (rff_measure_fma_peaks)",
                 "peak_derived": 152 * 128 * 2 * 2.07e9 / 1e12}
 
@@ -327,6 +374,10 @@ def run_ours(args, rank, world):
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
+    if world == 1 and not args.no_large:
+        line["large"] = run_large(args)
+    if world == 1 and not args.no_serve:
+        line["serve"] = run_serve(args)
     return line
 
 
@@ -356,6 +407,7 @@ def workload(args):
     return w
 
 
+# ----------------------------------------------------------------- the oracle on the host cores
 def oracle_iter_seconds(w, n_sample, iters):
     """Seconds per iteration of the FP64 oracle on an n_sample-row slice of the workload
     (same d, D, m, grid, loss and block fraction; set-up excluded)."""
@@ -370,25 +422,156 @@ def oracle_iter_seconds(w, n_sample, iters):
     return (time.perf_counter() - t0) / iters
 
 
-def cpu_baseline(args, n_sample=8000, iters=3):
-    w = workload(args)
-    sec = oracle_iter_seconds(w, n_sample, iters)
-    scale = w["n"] / n_sample
-    return {"value": 1.0 / (sec * scale), "unit": "iter/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d of %d rows (same d, D, m, 4x4 grid), %d iterations timed, set-up excluded, "
-                      "per-iteration time extrapolated linearly in n (x%.0f)" % (n_sample, w["n"], iters, scale)}
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def oracle_rate(w, iters=2):
+    """The FP64 oracle's iterations per second on the whole workload, from two slices that
+    keep its projection form: every row block at least as tall as a column block is wide
+    (n_i >= s_j, the Gram form I + Z_ij^T Z_ij, as at the full size).  The time per
+    iteration is fitted as t(n) = a + b n through the two slices (a: the solves with the
+    cached factors, whose cost does not depend on n; b n: the passes over Z and the row
+    updates) and evaluated at the workload's n.  The one helper behind cpu_baseline and
+    the reference arm, so both report the same rate."""
+    smax = -(-w["D"] // w["C"])
+    n1 = max(w["R"] * smax, 4096)
+    n2 = n1 + n1 // 2
+    if n2 >= w["n"]:
+        n1, n2 = w["n"], None
+    t1 = oracle_iter_seconds(w, n1, iters)
+    if n2 is None:
+        t, fit = t1, "the whole workload (%d rows)" % n1
+    else:
+        t2 = oracle_iter_seconds(w, n2, iters)
+        b = (t2 - t1) / (n2 - n1)
+        a = t1 - b * n1
+        t = a + b * w["n"]
+        fit = ("slices of %d and %d of %d rows (same d, D, m, %dx%d grid, every row block at least as tall as "
+               "a column block is wide: the Gram form of the full size), %d iterations each, set-up excluded; "
+               "t(n) = a + b n fitted through them: a = %.3g s, b = %.3g s/row, t(%d) = %.3g s"
+               % (n1, n2, w["n"], w["R"], w["C"], iters, a, b, w["n"], t))
+    return {"value": 1.0 / t, "unit": "iter/s", "cores": blas_threads(), "kind": "oracle", "sample": fit}
+
+
+def cpu_baseline(args):
+    return oracle_rate(workload(args))
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    cb = cpu_baseline(args, n_sample=4000, iters=max(1, min(args.steps, 3)))
+    w = workload(args)
+    cb = oracle_rate(w)
     return {"metric": METRIC, "value": cb["value"], "unit": "iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload(args)["name"], "prec": "f64 oracle (explicit Z)"},
+            "config": {"workload": w["name"], "prec": "f64 oracle (explicit Z)"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_large(args, steps=3):
+    """The MNIST-8M-shaped implicit solve at full size on one GPU (LARGE): data drawn into
+    pinned host memory, then end to end through the public API -- set_data (host to device),
+    set-up (Philox, Gram matrices on the tensor cores, FP64-class factorisation of the 512
+    blocks' 4096 x 4096 Gram matrices), the first iteration, `steps` iterations timed with
+    CUDA events on the solver's stream, the weights back to host memory.  Beside it, the
+    seeded 20,000-row sample of the same workload at the same 32 x 16 grid against the FP64
+    oracle's iterate after 50 iterations (tests/golden/large_20k_32x16_wbar50.npz)."""
+    import numpy as np
+    import torch
+
+    import paper_1409_0940_gb300 as rff
+    import synth
+    w = dict(LARGE)
+    n, d, m = w["n"], w["d"], w["m"]
+    t0 = time.perf_counter()
+    Xp = torch.empty((n, d), dtype=torch.float32, pin_memory=True)
+    _, Y = synth.sparse01(n=n, d=d, m=m, seed=w["data_seed"], out=Xp.numpy())
+    Yp = torch.from_numpy(Y).pin_memory()
+    Wh = torch.empty((w["D"], m), dtype=torch.float32).pin_memory()
+    data_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = new_solver(rff, w, "split_bf16", stream)
+    s.set_data(Xp, Yp)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter()
+    s.solve(1, stats=False)              # set-up and the first iteration
+    torch.cuda.synchronize()
+    t_first = time.perf_counter()
+    s.profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        s.solve(steps, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    s.weights(Wh)
+    e2e_s = time.perf_counter() - t0
+    s.close()
+    del Xp, Yp
+    _, _, bf16_sus, src = peaks()
+    ph = "ms_pass2" if prof["ms_pass2"] >= prof["ms_pass1"] else "ms_pass1"
+    per_launch_ms = prof[ph] / max(prof["iters"], 1)
+    achieved = survey_flops_per_pass(w) / (per_launch_ms * 1e-3) / 1e12
+    _, exec_pass = flops_per_iter(w, "split_bf16")
+    executed = exec_pass / (per_launch_ms * 1e-3) / 1e12
+    out = {"metric": METRIC, "value": steps / (ms * 1e-3), "unit": "iter/s", "steps": steps, "warmup": 1,
+           "ms_per_step": ms / steps, "dtype": "f16x3",
+           "config": {"workload": w["name"], "n": n, "d": d, "m": m, "D": w["D"], "grid": "32x16",
+                      "sigma": w["sigma"], "loss": "hinge (one-vs-rest)", "reg": "l2", "lambda": w["lam"],
+                      "rho": w["rho"], "prec": "split_bf16", "data": "synth.sparse01 (MNIST-8M stand-in, "
+                      "%.1f %% non-zero, stored dense)" % 20.0,
+                      "l2": "inputs larger than L2 (X split 27 GB)"},
+           "set_data_s": t_data - t0, "setup_and_first_iteration_s": t_first - t_data, "data_gen_s": data_s,
+           "e2e": {"value": (1 + steps) / e2e_s, "unit": "iter/s",
+                   "h2d_bytes_per_step": (n * d + n * m) * 4 // (1 + steps),
+                   "d2h_bytes_per_step": w["D"] * m * 4 // (1 + steps),
+                   "note": "set_data from pinned host memory + set-up + %d iterations + get_weights" % (1 + steps)},
+           "gpu_launches": int(prof["launches"]),
+           "phases_ms_per_iter": {k[3:]: prof[k] / max(prof["iters"], 1) for k in prof if k.startswith("ms_")},
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_sus, "unit": "TFLOP/s",
+                        "frac": achieved / bf16_sus, "traffic": None, "kernel": "k_regen_tc " + ph[3:],
+                        "peak_source": src + " sustained bf16",
+                        "count": "3 x 2 n d D + 2 n D m_pad per launch",
+                        "executed_tflops": executed, "executed_frac": executed / bf16_sus},
+           "clocks": clk.summary(),
+           "iterations_of_the_workload": 50,
+           "seconds_for_50_iterations": (t_first - t0) + 49 * ms / steps / 1e3}
+    out["sample_vs_fp64_oracle"] = large_sample_errors(rff, stream)
+    return out
+
+
+def large_sample_errors(rff, stream):
+    """The seeded 20,000-row sample of the large workload at its 32 x 16 grid (625-row blocks:
+    the outer form I + Z_ij Z_ij^T) against the FP64 oracle after 50 iterations."""
+    import numpy as np
+    path = os.path.join(GOLDEN, "large_20k_32x16_wbar50.npz")
+    if not os.path.exists(path):
+        return None
+    ref = np.load(path)
+    w = dict(LARGE, n=int(ref["n"]))
+    X, Y = make_data(w)
+    s = new_solver(rff, w, "split_bf16", stream)
+    s.set_data(X, Y)
+    st = s.solve(50, stats=True)
+    W = s.weights()
+    s.close()
+    return {"rows": w["n"], "grid": "32x16", "iterations": 50, "rel_err_wbar": oracle_errors(W, ref),
+            "objective_rel_err": abs(st["objective"] - float(ref["objective"])) / abs(float(ref["objective"])),
+            "tolerance": 1e-4}
 
 
 # ----------------------------------------------------------------- sweep and serving workloads
@@ -431,86 +614,6 @@ def run_ridge(args):
                        "timing": "CUDA events around 200 graph-replayed iterations"},
             "gpu_launches_per_iter": int(prof["launches"]) / (iters + max(args.warmup, 3)),
             "solve_ms_200_iters": ms, "clocks": clk.summary()}
-
-
-def run_columns(args):
-    """Column partitions (the paper's Sec. 5 experiment on C, at this workload's shape): the
-    multiclass workload (n from --n, default 200k) solved with C = 4, 8, 16, 32, 64 column
-    blocks on the command line's precision; per C the cached factors' bytes, the set-up time,
-    the device time per iteration, and the objective after 30 iterations relative to C = 4's."""
-    import torch
-
-    import paper_1409_0940_gb300 as rff
-    w = workload(args)
-    X, Y = make_data(w)
-    stream = torch.cuda.Stream()
-    rows, iters = [], 30
-    for C in (4, 8, 16, 32, 64):
-        wc = dict(w, C=C)
-        s = new_solver(rff, wc, args.prec, stream)
-        s.set_data(X, Y)
-        t0 = time.perf_counter()
-        s.solve(1, stats=False)                    # set-up and the first iteration
-        torch.cuda.synchronize()
-        setup_s = time.perf_counter() - t0
-        s.solve(2, stats=False)                    # graph capture
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.solve(iters - 3, stats=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / (iters - 3)
-        obj = s.solve(0)["objective"]
-        sj = -(-wc["D"] // C)
-        rows.append({"C": C, "features_per_block": sj, "factor_bytes": 2 * 3 * wc["R"] * C * sj * sj,
-                     "setup_s": setup_s, "ms_per_iter": ms, "objective_30": obj})
-        s.close()
-    for r in rows:
-        r["objective_vs_C4"] = r["objective_30"] / rows[0]["objective_30"]
-    return {"metric": "ADMM iter/s by column blocks", "value": 1e3 / rows[0]["ms_per_iter"], "unit": "iter/s",
-            "n_gpus": 1, "steps": iters, "warmup": 3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f16x3", "data": "synthetic",
-            "config": {"workload": w["name"] + "-columns", "prec": args.prec,
-                       "factor_bytes": "R C s_j^2 x 3 BF16 terms (the cached Q_ij)"},
-            "columns": rows}
-
-
-def run_rows(args):
-    """Scaling the rows at fixed D (the single-GPU analogue of the paper's weak scaling, Sec. 5):
-    the multiclass workload with n = 50k, 100k, 200k, 400k, 800k rows on the 4 x 4 grid; per n
-    the set-up time, the device time per iteration and the rows processed per second."""
-    import torch
-
-    import paper_1409_0940_gb300 as rff
-    w = workload(args)
-    stream = torch.cuda.Stream()
-    rows, iters = [], 20
-    for n in (50_000, 100_000, 200_000, 400_000, 800_000):
-        wn = dict(w, n=n)
-        X, Y = make_data(wn)
-        s = new_solver(rff, wn, args.prec, stream)
-        s.set_data(X, Y)
-        t0 = time.perf_counter()
-        s.solve(1, stats=False)
-        torch.cuda.synchronize()
-        setup_s = time.perf_counter() - t0
-        s.solve(2, stats=False)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.solve(iters, stats=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / iters
-        rows.append({"n": n, "setup_s": setup_s, "ms_per_iter": ms, "iter_per_s": 1e3 / ms,
-                     "rows_per_s": n * 1e3 / ms})
-        s.close()
-        del X, Y
-    return {"metric": "ADMM rows/s by n", "value": rows[2]["rows_per_s"], "unit": "rows/s", "n_gpus": 1,
-            "steps": iters, "warmup": 3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.prec == "fp32" else "f16x3", "data": "synthetic",
-            "config": {"workload": w["name"].replace("200k", "n") + "-rows", "prec": args.prec,
-                       "value": "rows per second at n = 200k"},
-            "rows": rows}
 
 
 def run_sweep(args):
@@ -611,86 +714,133 @@ def run_score(args):
             "resident": out["resident"], "released": out["released"]}
 
 
-def run_serve(args):
-    """Serving: Poisson arrivals of solve requests (n log-uniform 5k..200k, d in 32..784,
-    D in 1k..8k, loss in {squared, hinge, logistic}, reg in {l2, l1}) and scoring batches of
-    1..4096 queries against resident models; p50/p99 latency per request kind."""
+SERVE = dict(n_solve=24, n_score=400, rate_score=40.0, iters=30, load=0.7, max_active=8, seed=11,
+             n_lo=5_000, n_hi=500_000, ds=[32, 64, 128, 256, 440, 784], Ds=[1024, 2048, 4096, 8192, 16384, 32768])
+
+
+def serve_requests(cfg, prec):
+    """The solve requests of the serving workload, drawn before any clock starts: n
+    log-uniform in [5k, 500k], d and D from the configured ranges, losses and regularisers
+    cycled, FP32 data from seeded Gaussian mixtures."""
     import numpy as np
 
     import paper_1409_0940_gb300 as rff
     import synth
-    rng = np.random.default_rng(11)
-    n_solve, n_score, rate_solve, rate_score = 24, 400, 2.0, 40.0
-    events = [(t, "solve") for t in np.cumsum(rng.exponential(1 / rate_solve, n_solve))]
-    events += [(t, "score") for t in 1.0 + np.cumsum(rng.exponential(1 / rate_score, n_score))]
-    events.sort()
-    # request contents are drawn before the clock starts
+    rng = np.random.default_rng(cfg["seed"])
     losses = ["squared", "hinge", "logistic"]
-    solves, k = [], 0
-    for t, kind in events:
-        if kind != "solve":
-            continue
-        n = int(np.exp(rng.uniform(np.log(5_000), np.log(200_000))))
-        d = int(rng.choice([32, 64, 128, 256, 440, 784]))
-        D = int(rng.choice([1024, 2048, 4096, 8192]))
+    reqs = []
+    for k in range(cfg["n_solve"]):
+        n = int(np.exp(rng.uniform(np.log(cfg["n_lo"]), np.log(cfg["n_hi"]))))
+        d = int(rng.choice(cfg["ds"]))
+        D = int(rng.choice(cfg["Ds"]))
         loss, reg = losses[k % 3], ["l2", "l1"][(k // 3) % 2]
-        if loss == "squared":
-            X, Y = synth.ridge(n=n, d=d, seed=k)
-        else:
-            X, Y = synth.binary(n=n, d=d, seed=k)
-        pr = rff.make_params(loss=loss, reg=reg, lam=1e-4, sigma=float(np.sqrt(d)), D=D, R=-(-n // 50_000),
-                             C=max(1, D // 2048), seed=k, m=1, prec=args.prec)
-        solves.append((pr, X, Y, d))
-        k += 1
-    srv = rff.rff_server_create(0, 8)
-    models, kinds, pending, scores = [], {}, set(), []
-    solved = set()          # models whose solve has completed (scores against them hit a resident model)
-    t_start = time.perf_counter()
+        X, Y = synth.ridge(n=n, d=d, seed=k) if loss == "squared" else synth.binary(n=n, d=d, seed=k)
+        R, C = -(-n // 50_000), max(1, D // 2048)
+        pr = rff.make_params(loss=loss, reg=reg, lam=1e-4, sigma=float(np.sqrt(d)), D=D, R=R, C=C, seed=k, m=1,
+                             prec=prec)
+        dpad = -(-d // 64) * 64
+        # tensor work of the request: the regeneration passes of every iteration and the
+        # set-up's Z^T and Gram matrices (the fit below turns it into seconds)
+        work = 2 * 3 * 2 * n * dpad * D * (cfg["iters"] + 1) + 3 * 2 * n * D * (D // C)
+        reqs.append({"params": pr, "X": X, "Y": Y, "d": d, "n": n, "D": D, "loss": loss, "reg": reg,
+                     "work": float(work)})
+    return reqs
+
+
+def run_one_alone(rff, srv, req, iters):
+    rid = rff.rff_server_submit_solve(srv, req["params"], req["X"], req["Y"], iters)
+    while True:
+        for c in rff.rff_server_poll(srv, 16, 50):
+            if c["id"] == rid:
+                rff.rff_server_release(srv, rid)
+                return c["run_ms"]
+
+
+def run_serve(args):
+    """Serving: Poisson arrivals of solve requests and scoring batches of 1..4096 queries
+    against resident models, side by side on the device.  The solve rate is set to 70 % of
+    the isolated capacity measured first: three requests (the smallest, median and largest
+    by work) run alone, a line a + b work through their run times predicts every request's
+    isolated service time, and capacity is one over their mean.  Reported: p50/p99 latency
+    per request kind (scores against resident models, scores that waited for their model's
+    solve, solves) and the throughput."""
+    import numpy as np
+
+    import paper_1409_0940_gb300 as rff
+    cfg = SERVE
+    reqs = serve_requests(cfg, args.prec)
+    srv = rff.rff_server_create(0, cfg["max_active"])
+    order = np.argsort([r["work"] for r in reqs])
+    cal = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    run_ms = [run_one_alone(rff, srv, reqs[i], cfg["iters"]) for i in cal]
+    b, a = np.polyfit([reqs[i]["work"] for i in cal], run_ms, 1)
+    service_ms = np.maximum(a + b * np.array([r["work"] for r in reqs]), min(run_ms))
+    capacity = 1e3 / float(np.mean(service_ms))
+    rate_solve = cfg["load"] * capacity
+    rng = np.random.default_rng(cfg["seed"] + 1)
+    events = [(t, "solve") for t in np.cumsum(rng.exponential(1 / rate_solve, cfg["n_solve"]))]
+    t_first = events[0][0]
+    events += [(t_first + t, "score") for t in np.cumsum(rng.exponential(1 / cfg["rate_score"], cfg["n_score"]))]
+    events.sort()
+    # score request contents are drawn before the clock starts too
+    score_q = [int(np.exp(rng.uniform(0, np.log(4096)))) for _ in range(cfg["n_score"])]
+    score_model = [int(rng.integers(1 << 30)) for _ in range(cfg["n_score"])]
+    models, kinds, pending = [], {}, set()
+    solved = set()
     done = []
-    ev, si = 0, 0
+    ev = si = sc = 0
+    t_start = time.perf_counter()
     while ev < len(events) or pending:
         now = time.perf_counter() - t_start
         while ev < len(events) and events[ev][0] <= now:
-            kind = events[ev][1]
-            if kind == "solve":
-                pr, X, Y, d = solves[si]
+            if events[ev][1] == "solve":
+                r = reqs[si]
                 si += 1
-                rid = rff.rff_server_submit_solve(srv, pr, X, Y, 30)
-                models.append((rid, d))
+                rid = rff.rff_server_submit_solve(srv, r["params"], r["X"], r["Y"], cfg["iters"])
+                models.append((rid, r["d"]))
                 kinds[rid] = "solve"
                 pending.add(rid)
-            elif models:
-                mid, d = models[int(rng.integers(len(models)))]
-                q = int(np.exp(rng.uniform(0, np.log(4096))))
+            else:
+                mid, d = models[score_model[sc] % len(models)]
+                q = score_q[sc]
+                sc += 1
                 Xq = rng.standard_normal((q, d)).astype(np.float32)
                 out = np.empty((q, 1), dtype=np.float32)
-                scores.append(out)
                 rid = rff.rff_server_submit_score(srv, mid, Xq, out)
-                kinds[rid] = "score" if mid in solved else "score_waiting"
+                kinds[rid] = ("score", out) if mid in solved else ("score_waiting", out)
                 pending.add(rid)
             ev += 1
-        for c in rff.rff_server_poll(srv, 256, 5):
+        for c in rff.rff_server_poll(srv, 256, 2):
             pending.discard(c["id"])
             done.append(c)
             if kinds[c["id"]] == "solve" and c["status"] == 0:
                 solved.add(c["id"])
     wall = time.perf_counter() - t_start
     rff.rff_server_destroy(srv)
-    out = {"metric": "serve p50/p99 ms", "n_gpus": 1, "data": "synthetic", "higher_is_better": False,
-           "config": {"workload": "serve-poisson", "solve_requests": n_solve, "score_requests": n_score,
-                      "rate_solve_per_s": rate_solve, "rate_score_per_s": rate_score, "max_active": 8,
-                      "iterations_per_solve": 30, "prec": args.prec}, "wall_s": wall}
+    kind_of = {rid: (k if isinstance(k, str) else k[0]) for rid, k in kinds.items()}
+    out = {"metric": "serve p50/p99 ms", "unit": "ms", "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": "serve-poisson", "solve_requests": cfg["n_solve"], "score_requests": cfg["n_score"],
+                      "n": "log-uniform %d..%d" % (cfg["n_lo"], cfg["n_hi"]), "d": cfg["ds"], "D": cfg["Ds"],
+                      "losses": ["squared", "hinge", "logistic"], "regs": ["l2", "l1"],
+                      "score_queries": "log-uniform 1..4096", "iterations_per_solve": cfg["iters"],
+                      "max_active": cfg["max_active"], "prec": args.prec,
+                      "solve_rate_per_s": rate_solve, "score_rate_per_s": cfg["rate_score"],
+                      "load": "solve arrivals at %.0f %% of the isolated capacity %.2f solves/s (fit through "
+                              "%d requests run alone: %s ms)" % (100 * cfg["load"], capacity, len(cal),
+                                                                 ", ".join("%.0f" % x for x in run_ms))},
+           "wall_s": wall}
     for kind in ("solve", "score", "score_waiting"):
-        lat = np.array([c["latency_ms"] for c in done if kinds[c["id"]] == kind and c["status"] == 0])
-        que = np.array([c["queue_ms"] for c in done if kinds[c["id"]] == kind and c["status"] == 0])
-        out[kind] = {"count": int(lat.size), "failed": int(sum(1 for c in done if kinds[c["id"]] == kind
-                                                              and c["status"] != 0)),
+        ok = [c for c in done if kind_of[c["id"]] == kind and c["status"] == 0]
+        lat = np.array([c["latency_ms"] for c in ok])
+        que = np.array([c["queue_ms"] for c in ok])
+        out[kind] = {"count": len(ok), "failed": sum(1 for c in done if kind_of[c["id"]] == kind and c["status"] != 0),
                      "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
                      "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
                      "queue_p50_ms": float(np.percentile(que, 50)) if que.size else None}
     out["value"] = out["score"]["p99_ms"]
-    out["unit"] = "ms (p99 of scores against resident models)"
+    out["value_is"] = "p99 of scores against resident models"
     out["throughput_req_per_s"] = len(done) / wall
+    out["throughput_solves_per_s"] = out["solve"]["count"] / wall
     return out
 
 
@@ -704,9 +854,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-compare", action="store_true", help="skip the other precisions (profiling runs)")
+    ap.add_argument("--no-large", action="store_true", help="skip the large implicit solve")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving loop")
     ap.add_argument("--n", type=int, default=0, help="rows of a reduced workload (profiling runs)")
-    ap.add_argument("--workload", default="multiclass",
-                    choices=["multiclass", "ridge", "sweep", "serve", "score", "columns", "rows"])
+    ap.add_argument("--workload", default="multiclass", choices=["multiclass", "large", "serve", "ridge", "sweep", "score"])
     ap.add_argument("--loss", default="squared", choices=["squared", "hinge", "multinomial", "crammer_singer", "l1"],
                     help="loss of the multiclass workload")
     ap.add_argument("--feature-map", default="fourier", choices=["fourier", "laplace", "fastfood", "tensorsketch"],
@@ -721,8 +872,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.workload != "multiclass":
-        line = {"sweep": run_sweep, "serve": run_serve, "ridge": run_ridge, "score": run_score,
-                "columns": run_columns, "rows": run_rows}[args.workload](args)
+        if args.workload == "large":
+            line = run_large(args, steps=max(1, min(args.steps, 10)))
+        else:
+            line = {"sweep": run_sweep, "serve": run_serve, "ridge": run_ridge, "score": run_score}[args.workload](args)
         print(json.dumps(line), flush=True)
         return
     if args.impl == "reference":

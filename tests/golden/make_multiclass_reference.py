@@ -9,9 +9,9 @@ Only oracle/ computes: Z is formed in row chunks by oracle.rff.features (an expl
 n x D float64 matrix, 26 GB) so that no temporary of that size is needed beside it, and
 oracle.admm.admm runs the iterations.  About 10 minutes and 40 GB of host memory on an
 8-core machine.  Output: multiclass_200k_wbar23_sample.npz, a seeded random sample of
-32,768 entries of Wbar (flat indices `idx`, float64 values `w`) and the Frobenius norm of
-the whole Wbar (`fro`); the relative error on the sample estimates the relative error of
-the whole matrix.
+32,768 entries of Wbar (flat indices `idx`, float64 values `w`), the Frobenius norm of
+the whole Wbar (`fro`) and the objective at Wbar (`objective`); the relative error on the
+sample estimates the relative error of the whole matrix.
 
 With --stochastic the same workload runs the stochastic block-subset variant with half of
 the blocks active per iteration (block fraction 0.5, masks from Philox as oracle.admm
@@ -51,7 +51,8 @@ def main():
     p._Z = Z                       # the same matrix Problem.Z() would form, built in chunks
     W = admm.admm(p, ITERS, block_fraction=FRACTION)["Wbar"]
     idx = np.sort(np.random.default_rng(SAMPLE_SEED).choice(W.size, SAMPLE, replace=False)).astype(np.int64)
-    np.savez(OUT, idx=idx, w=W.ravel()[idx], fro=np.linalg.norm(W))
+    # the objective sum_i V(y_i, (Z Wbar)_i) + n lambda r(Wbar) at the stored iterate
+    np.savez(OUT, idx=idx, w=W.ravel()[idx], fro=np.linalg.norm(W), objective=p.objective(W))
     print("wrote %s (%.0f s)" % (OUT, time.time() - t0), flush=True)
 
 

@@ -243,23 +243,3 @@ def test_random_feature_ridge_tends_to_kernel_ridge():
     slope = np.polyfit(np.log(Ds), np.log(errs), 1)[0]
     assert errs[-1] < 0.25 * errs[0]
     assert -0.8 < slope < -0.25, (slope, errs)
-
-
-def test_column_partitions_trade_memory_for_progress():
-    """Sec. 5 (effect of column partitions): more column blocks shrink the cached factors
-    (sum_j s_j^2 = D^2 / C) and the graph projections, at the cost of progress per iteration
-    once C is large; moderate C perform alike.  After 150 iterations the objective gap at
-    C = 1, 4, 16 stays within a factor 4 of one another, and at C = 64 (four features per
-    block) it is more than ten times the worst of them."""
-    X, Y = synth.ridge(n=600, d=8, seed=4)
-    gaps, factor_floats = {}, {}
-    for C in (1, 4, 16, 64):
-        p = admm.Problem(X, Y, "squared", "l2", lam=1e-3, sigma=2.0, rho=1.0, D=256, R=2, C=C, seed=7)
-        W = admm.ridge_closed_form(p.Z(), p.Y, p.lam)
-        out = admm.admm(p, 150)
-        gaps[C] = p.objective(out["Wbar"]) / p.objective(W) - 1.0
-        factor_floats[C] = sum(int(p.cols[j + 1] - p.cols[j]) ** 2 for j in range(C))
-    moderate = [gaps[C] for C in (1, 4, 16)]
-    assert min(moderate) > 0 and max(moderate) < 4 * min(moderate), gaps
-    assert gaps[64] > 10 * max(moderate), gaps
-    assert all(factor_floats[C] == 256 * 256 // C for C in factor_floats)
