@@ -325,10 +325,14 @@ typedef struct {
   double ms_average;       /* Wbar, mu, mu'_ij updates                                      */
   int32_t tc_kchunk;       /* K chunk of the tensor-core ring chosen by the autotuner (0: FP32) */
   int32_t nsplit;          /* row splits of pass 1 chosen by the autotuner                   */
-  int32_t tc_z_tmem;       /* 1: the tensor-core passes keep the Z tile in tensor memory,
-                              0: in shared memory (chosen by the autotuner; the environment
-                              variable RFF_TC_GEOMETRY="kc,zt" fixes both instead)          */
-  int32_t reserved;
+  int32_t tc_z_tmem;       /* geometry of the tensor-core passes (chosen by the autotuner;
+                              the environment variable RFF_TC_GEOMETRY="kc,zt" or
+                              "kc,zt,cg" fixes it instead): 0 the Z tile in shared memory,
+                              1 in tensor memory, 2 in tensor memory with two X.G
+                              accumulators (m_pad <= 128), 3 X.G products 256 features wide
+                              (m_pad <= 192)                                               */
+  int32_t tc_cta_pair;     /* 1: the tensor-core passes run as CTA pairs (clusters of two
+                              CTAs sharing each M = 256 MMA), 0: one CTA per MMA            */
 } rff_admm_profile;
 
 rff_status rff_admm_set_profiling(rff_admm_t h, int enable);

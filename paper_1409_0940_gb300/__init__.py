@@ -51,7 +51,7 @@ class rff_admm_profile(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("launches", ctypes.c_int64), ("ms_prox_reg", ctypes.c_double),
                 ("ms_pass1", ctypes.c_double), ("ms_project", ctypes.c_double), ("ms_pass2", ctypes.c_double),
                 ("ms_exchange", ctypes.c_double), ("ms_average", ctypes.c_double), ("tc_kchunk", ctypes.c_int32),
-                ("nsplit", ctypes.c_int32), ("tc_z_tmem", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("nsplit", ctypes.c_int32), ("tc_z_tmem", ctypes.c_int32), ("tc_cta_pair", ctypes.c_int32)]
 
 
 class rff_completion(ctypes.Structure):

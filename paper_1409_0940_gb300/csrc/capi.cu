@@ -53,6 +53,7 @@ struct rff_admm_s {
   int R = 1, C = 1, nsplit = 1, nsplit_max = 1, iters_done = 0;
   int tc_kc = 0;  // ring K chunk of the tensor-core passes, chosen by the autotuner
   int tc_zt = 0;  // 1: Z tile of the tensor-core passes in TMEM (autotuned)
+  int tc_cg = 1;  // 2: the tensor-core passes run as CTA pairs (autotuned)
   float t_loss = 0.f, t_reg = 0.f;
   std::vector<int64_t> row_start, row_size, row_slot, col_start, col_size, col_slot, foff;
 
@@ -388,7 +389,10 @@ void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
   // pass-1 row splits: enough CTAs for two waves on the device and, on the tensor-core
   // path, at most ~6400 rows per split: the FP32 accumulator of the tensor cores rounds
   // toward zero at every accumulation, so its error grows with the chain length; the
-  // partial sums of the splits are added in FP32 with round-to-nearest afterwards
+  // partial sums of the splits are added in FP32 with round-to-nearest afterwards.  The
+  // FP32 path splits into chains of at most ~1600 rows: its FP32 sums of Z^T V over a
+  // whole 50k-row block moved the weights of the multiclass workload by 5.3e-5 from the
+  // FP64 iterate, ~6,250-row chains by 1.3e-5, ~1,600-row chains by 1.1e-5 (measured)
   {
     int nsm = 148, dev = 0;
     cudaGetDevice(&dev);
@@ -398,7 +402,7 @@ void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
     int64_t min_rows = n;
     for (int i = 0; i < s.R; ++i) min_rows = std::min(min_rows, s.row_size[i]);
     int64_t want = ceil_div(2 * (int64_t)nsm, ftiles * s.R);
-    if (s.split_path()) want = std::max<int64_t>(want, ceil_div(min_rows, 6400));
+    want = std::max<int64_t>(want, ceil_div(min_rows, s.split_path() ? 6400 : 1600));
     const int64_t cap = std::min<int64_t>(ceil_div(min_rows, tile), 64);
     s.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
     // RFF_PASS1_SPLITS=k fixes the row splits of pass 1 (bounded by one 128-row tile each)
@@ -509,6 +513,7 @@ rff_status rff_admm_get_profile(rff_admm_t h, rff_admm_profile* out) {
   out->tc_kchunk = h->split_path() ? (h->tc_kc ? h->tc_kc : 64) : 0;
   out->nsplit = h->cached_z() ? h->nsplit_cz : h->nsplit;
   out->tc_z_tmem = h->split_path() ? h->tc_zt : 0;
+  out->tc_cta_pair = h->split_path() && h->tc_cg == 2 ? 1 : 0;
   return RFF_OK;
 }
 
@@ -787,26 +792,33 @@ rff_status rff_admm_set_data_csr(rff_admm_t h, const int64_t* indptr, const int3
 namespace {
 
 // Tile-shape autotuner of the tensor-core passes: times pass 1 + pass 2 for each
-// ring geometry (K chunk 64 or 32, Z tile in shared or tensor memory) on the
-// handle's own data, restricted to the first row block (a quarter of the work on a
-// 4 x 4 grid: still several waves of both passes), and keeps the fastest.  All geometries issue the same MMAs in
-// the same order, so the choice
-// changes speed, never results (a run is reproducible whatever the timing).  The
-// passes only write their scratch outputs (R partials, O'), which every
-// iteration recomputes.
+// ring geometry (K chunk 64 or 32; Z tile in shared or tensor memory; one CTA or a CTA
+// pair per MMA) on the handle's own data, restricted to the first row block (a quarter
+// of the work on a 4 x 4 grid: still several waves of both passes), and keeps the
+// fastest.  All geometries issue the same products in the same order for every output
+// element, so the choice changes speed, never results (a run is reproducible whatever
+// the timing).  The passes only write their scratch outputs (R partials, O'), which
+// every iteration recomputes.
 rff_status autotune(rff_admm_t h) {
   NvtxRange range("rff set-up: autotune");
   auto& s = *h;
   if (!s.split_path() || s.cached_z()) return RFF_OK;
-  // RFF_TC_GEOMETRY="kc,zt" (kc 64 or 32, zt 0 or 1) fixes the geometry instead
+  // RFF_TC_GEOMETRY="kc,zt" or "kc,zt,cg" (kc 64 or 32; zt 0, 1, or 2 when m_pad <= 128;
+  // cg 1, or 2 with zt 1 or 2) fixes the geometry instead
   if (const char* g = getenv("RFF_TC_GEOMETRY")) {
-    int kc = 0, zt = -1;
-    if (sscanf(g, "%d,%d", &kc, &zt) == 2 && (kc == 64 || kc == 32) && (zt == 0 || zt == 1)) {
+    int kc = 0, zt = -1, cg = 1;
+    const int nf = sscanf(g, "%d,%d,%d", &kc, &zt, &cg);
+    if (nf >= 2 && (kc == 64 || kc == 32) &&
+        (zt == 0 || zt == 1 || (zt == 2 && s.mpad <= 128) || (zt == 3 && s.mpad <= 192)) &&
+        (cg == 1 || (cg == 2 && (zt == 1 || zt == 2)))) {
       s.tc_kc = kc;
       s.tc_zt = zt;
+      s.tc_cg = cg;
       return RFF_OK;
     }
-    return h->fail(RFF_EINVAL, "RFF_TC_GEOMETRY must be \"64,0\", \"64,1\", \"32,0\" or \"32,1\"");
+    return h->fail(RFF_EINVAL,
+                   "RFF_TC_GEOMETRY must be \"kc,zt\" or \"kc,zt,cg\" with kc 64 or 32, zt 0, 1, 2 (m_pad <= "
+                   "128) or 3 (m_pad <= 192), cg 1 or 2 (2 needs zt 1 or 2)");
   }
   std::vector<int> splits{s.nsplit};
   if (s.nsplit_max != s.nsplit) splits.push_back(s.nsplit_max);
@@ -814,13 +826,21 @@ rff_status autotune(rff_admm_t h) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_kc = 64, best_ns = s.nsplit, best_zt = 0;
+  int best_kc = 64, best_ns = s.nsplit, best_zt = 0, best_cg = 1;
   bool warm = false;
-  for (int zt : {0, 1})
+  // (Z in smem), (Z in TMEM), the wide N = 256 geometry (m_pad <= 192), and with m_pad <= 128
+  // the double-buffered acc1 beside Z in TMEM.  The CTA-pair geometries are selectable through
+  // RFF_TC_GEOMETRY but not timed here: they measured 6-15 % slower on every workload tried
+  std::vector<std::pair<int, int>> geos{{0, 1}, {1, 1}};   // (zt, cg)
+  if (s.mpad <= 192) geos.push_back({3, 1});
+  if (s.mpad <= 128) geos.push_back({2, 1});
+  for (const auto& geo : geos)
   for (int kc : {64, 32}) {
+    const int zt = geo.first, cg = geo.second;
     for (int ns : splits) {
       s.tc_kc = kc;
       s.tc_zt = zt;
+      s.tc_cg = cg;
       s.nsplit = ns;
       float ms = 0.f;
       TcView tv = tc_view(s);
@@ -840,6 +860,7 @@ rff_status autotune(rff_admm_t h) {
         best_kc = kc;
         best_ns = ns;
         best_zt = zt;
+        best_cg = cg;
       }
     }
   }
@@ -847,6 +868,7 @@ rff_status autotune(rff_admm_t h) {
   cudaEventDestroy(e1);
   s.tc_kc = best_kc;
   s.tc_zt = best_zt;
+  s.tc_cg = best_cg;
   s.nsplit = best_ns;
   // the timing runs wrote O'_ij, which starts at zero: a block that sits out the first
   // iterations of a stochastic solve reads it as it is
@@ -1520,13 +1542,12 @@ rff_status iterate_outer(rff_admm_t h, int k) {
   return RFF_OK;
 }
 
-rff_status iterate(rff_admm_t h, int k) {
+// One iteration in phases: before pass 1 (mask, regulariser prox), pass 1, the projection,
+// pass 2 and after it (exchange, averaging, duals).  iterate() runs them in order; a sweep
+// may run the passes of several solves as one launch between the solves' other phases.
+rff_status phase_pre(rff_admm_t h, int k) {
   auto& s = *h;
-  if (s.outer) return iterate_outer(h, k);
   const int64_t nfe = s.fslots * s.mpad;
-  const int64_t nblocks = (int64_t)s.R * s.C;
-  int64_t smax = 0;
-  for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
   rff_status r;
   if ((r = mark(h, k, 0)) != RFF_OK) return r;
   // stochastic variant: this iteration's active blocks; the per-block kernels below skip the
@@ -1534,8 +1555,12 @@ rff_status iterate(rff_admm_t h, int k) {
   if (s.stochastic()) CK(launch_block_mask(s.p.seed, s.bthr, s.R * s.C, s.bctr, s.bmask, s.st));
   // W_j <- prox_{(n lam / rho) r}(Wbar_j - mu_j)
   CK(launch_prox_reg(s.p.reg, s.Wbar, s.mu, nfe, s.t_reg, s.W, s.st, s.lam_dev, (int)s.mpad));
-  if ((r = mark(h, k, 1)) != RFF_OK) return r;
-  // pass 1: R_ij = Z_ij^T V_ij,  V_ij = Obar_ij + nu_i
+  return mark(h, k, 1);
+}
+
+// pass 1: R_ij = Z_ij^T V_ij,  V_ij = Obar_ij + nu_i
+rff_status phase_pass1(rff_admm_t h) {
+  auto& s = *h;
   PassArgs a = base_pass_args(s);
   a.bmask = s.act();
   if (s.cached_z()) {
@@ -1551,6 +1576,16 @@ rff_status iterate(rff_admm_t h, int k) {
     a.out_elems = s.rpart_elems();
     CK(launch_pass1_simt(a, s.fslots, s.st));
   }
+  return RFF_OK;
+}
+
+rff_status phase_project(rff_admm_t h, int k) {
+  auto& s = *h;
+  const int64_t nfe = s.fslots * s.mpad;
+  const int64_t nblocks = (int64_t)s.R * s.C;
+  int64_t smax = 0;
+  for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
+  rff_status r;
   if ((r = mark(h, k, 2)) != RFF_OK) return r;
   // graph projection, eq. (gpWij): W'_ij = Q_ij (Wbar_j - mu'_ij + R_ij) with the cached inverse.
   // (A refinement step r = rhs - H x computed in FP32 adds more rounding than it removes, and an
@@ -1569,8 +1604,15 @@ rff_status iterate(rff_admm_t h, int k) {
     CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st, s.act()));
   }
   if ((r = mark(h, k, 3)) != RFF_OK) return r;
-  // pass 2: O'_ij = Z_ij W'_ij (eq. (gpOij))
   if (s.split_path()) CK(cudaMemsetAsync(s.amax + AMAX_OP, 0, 4, s.st));   // max |O'| for the exchange
+  return RFF_OK;
+}
+
+// pass 2: O'_ij = Z_ij W'_ij (eq. (gpOij))
+rff_status phase_pass2(rff_admm_t h) {
+  auto& s = *h;
+  PassArgs a = base_pass_args(s);
+  a.bmask = s.act();
   if (s.cached_z()) {
     CK(split_gemm(cz_pass2_view(s)));
   } else if (s.split_path()) {
@@ -1585,13 +1627,30 @@ rff_status iterate(rff_admm_t h, int k) {
     a.per_block = 1;
     CK(launch_pass2_simt(a, s.nslots, s.st));
   }
+  return RFF_OK;
+}
+
+rff_status phase_post(rff_admm_t h, int k) {
+  auto& s = *h;
+  rff_status r;
   if (s.split_path() && s.stochastic())   // max |O'| over every block, the kept ones included
     CK(launch_finite_check(s.Op, s.C * s.nslots * s.mpad, 0, reinterpret_cast<int*>(s.amax + AMAX_FLAG), s.st,
                            s.amax + AMAX_OP));
   if ((r = mark(h, k, 4)) != RFF_OK) return r;
   // exchange, nu update, next loss prox, next V_ij (the tensor-core path reads V^T as a
   // scaled FP16 hi/lo pair), averaging and dual updates
-  if ((r = exchange_and_average(h, k)) != RFF_OK) return r;
+  return exchange_and_average(h, k);
+}
+
+rff_status iterate(rff_admm_t h, int k) {
+  auto& s = *h;
+  if (s.outer) return iterate_outer(h, k);
+  rff_status r;
+  if ((r = phase_pre(h, k)) != RFF_OK) return r;
+  if ((r = phase_pass1(h)) != RFF_OK) return r;
+  if ((r = phase_project(h, k)) != RFF_OK) return r;
+  if ((r = phase_pass2(h)) != RFF_OK) return r;
+  if ((r = phase_post(h, k)) != RFF_OK) return r;
   s.launches += iter_launches(s);
   return RFF_OK;
 }
@@ -1759,6 +1818,7 @@ TcView tc_view(const rff_admm_s& s) {
   v.bias_in_mma = s.bias_col >= 0 ? 1 : 0;
   v.kc = s.tc_kc;
   v.zt = s.tc_zt;
+  v.cg = s.tc_cg;
   v.st = s.st;
   return v;
 }
@@ -1996,34 +2056,64 @@ rff_status rff_admm_wait(rff_admm_t h) {
 namespace {
 // One iteration of every solve of a sweep as a single executable graph: from a fork on the
 // master stream each solve's iteration is captured on its own stream (its kernels form a branch
-// of the graph), and the branches join back on the master stream.  One graph launch then runs
-// one iteration of all solves, the branches side by side on the device.
-rff_status capture_sweep(rff_admm_t* hs, int32_t n, cudaStream_t master, cudaGraphExec_t* out) {
+// of the graph), and the branches join back on the master stream.  The solves in `fused`
+// (split precision, Gram form) run their two regeneration passes as two launches for all of
+// them together (m1, m2: k_regen_multi, their CTAs side by side in one grid) on the master
+// stream, between their other phases, which stay on their own streams:
+//   fork -> [pre] -> join -> pass 1 of all -> fork -> [projection] -> join -> pass 2 of all ->
+//   fork -> [exchange, averaging] -> join.
+// One graph launch then runs one iteration of all solves.
+rff_status capture_sweep(rff_admm_t* hs, int32_t n, cudaStream_t master, const std::vector<int>& fused,
+                         const TcMulti* m1, const TcMulti* m2, cudaGraphExec_t* out) {
   std::vector<cudaEvent_t> evs;
   auto cleanup = [&]() {
     for (auto e : evs) cudaEventDestroy(e);
   };
-  cudaEvent_t fork = nullptr;
-  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return RFF_ECUDA;
-  evs.push_back(fork);
+  auto new_event = [&](cudaEvent_t* ev) -> cudaError_t {
+    cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) evs.push_back(*ev);
+    return e;
+  };
+  // master -> stream (a fork) or stream -> master (a join)
+  auto order = [&](cudaStream_t from, cudaStream_t to) -> cudaError_t {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = new_event(&ev);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, from);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+    return e;
+  };
+  std::vector<char> is_fused(n, 0);
+  for (int k : fused) is_fused[k] = 1;
   if (cudaStreamBeginCapture(master, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cleanup();
     return RFF_ECUDA;
   }
   rff_status r = RFF_OK;
-  cudaError_t e = cudaEventRecord(fork, master);
+  cudaError_t e = cudaSuccess;
+  // the solves iterated whole on their own streams
   for (int32_t k = 0; k < n && r == RFF_OK && e == cudaSuccess; ++k) {
+    if (is_fused[k]) continue;
     rff_admm_t h = hs[k];
-    e = cudaStreamWaitEvent(h->st, fork, 0);
+    e = order(master, h->st);
     if (e != cudaSuccess) break;
     const int64_t saved = h->launches;
     r = iterate(h, 0);
     h->launches = saved;
-    cudaEvent_t join = nullptr;
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
-    if (join) evs.push_back(join);
-    if (e == cudaSuccess) e = cudaEventRecord(join, h->st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(master, join, 0);
+    if (e == cudaSuccess) e = order(h->st, master);
+  }
+  // the fused solves, phase by phase around the shared pass launches
+  using Phase = rff_status (*)(rff_admm_t, int);
+  const Phase phases[3] = {phase_pre, phase_project, phase_post};
+  for (int p = 0; p < 3 && !fused.empty() && r == RFF_OK && e == cudaSuccess; ++p) {
+    for (int k : fused) {
+      rff_admm_t h = hs[k];
+      if ((e = order(master, h->st)) != cudaSuccess) break;
+      const int64_t saved = h->launches;
+      r = phases[p](h, 0);
+      h->launches = saved;
+      if (r != RFF_OK || (e = order(h->st, master)) != cudaSuccess) break;
+    }
+    if (r == RFF_OK && e == cudaSuccess && p < 2) e = tc_multi_launch(p == 0 ? m1 : m2, master);
   }
   cudaGraph_t g = nullptr;
   const cudaError_t ee = cudaStreamEndCapture(master, &g);
@@ -2033,6 +2123,21 @@ rff_status capture_sweep(rff_admm_t* hs, int32_t n, cudaStream_t master, cudaGra
   cleanup();
   cudaGetLastError();
   return r;
+}
+
+// The solves of a sweep whose passes can share launches: the split precision in the Gram form
+// (the passes of k_regen_tc), at least two of them, unless RFF_SWEEP_FUSE=0 keeps every solve's
+// passes to itself.
+std::vector<int> fusable(rff_admm_t* hs, int32_t n) {
+  std::vector<int> f;
+  const char* env = getenv("RFF_SWEEP_FUSE");
+  if (env && atoi(env) == 0) return f;
+  for (int32_t k = 0; k < n && (int)f.size() < 64; ++k) {
+    const auto& s = *hs[k];
+    if (s.split_path() && !s.cached_z() && !s.outer) f.push_back(k);
+  }
+  if (f.size() < 2) f.clear();
+  return f;
 }
 }  // namespace
 
@@ -2092,7 +2197,32 @@ rff_status rff_sweep_run(rff_admm_t* handles, int32_t n, int32_t iters) {
           r = RFF_ECUDA;
       }
       if (ready) cudaEventDestroy(ready);
-      if (r == RFF_OK) r = capture_sweep(handles, n, master, &gx);
+      // the shared pass launches' arguments (written to device memory before the capture)
+      const std::vector<int> fused = fusable(handles, n);
+      TcMulti *m1 = nullptr, *m2 = nullptr;
+      if (r == RFF_OK && !fused.empty()) {
+        std::vector<TcView> views;
+        std::vector<float*> rp, op;
+        std::vector<const __half*> mh, ml;
+        std::vector<const unsigned*> ma;
+        std::vector<unsigned*> oa;
+        for (int k : fused) {
+          auto& s = *handles[k];
+          views.push_back(iter_view(s));
+          rp.push_back(s.Rpart);
+          op.push_back(s.Op);
+          mh.push_back(s.WThi);
+          ml.push_back(s.WTlo);
+          ma.push_back(s.amax + AMAX_W);
+          oa.push_back(s.amax + AMAX_OP);
+        }
+        const int nf = (int)fused.size();
+        if (tc_multi_create(views.data(), nf, 1, rp.data(), nullptr, nullptr, nullptr, nullptr, &m1) != cudaSuccess ||
+            tc_multi_create(views.data(), nf, 2, op.data(), mh.data(), ml.data(), ma.data(), oa.data(), &m2) !=
+                cudaSuccess)
+          r = RFF_ECUDA;
+      }
+      if (r == RFF_OK) r = capture_sweep(handles, n, master, fused, m1, m2, &gx);
       for (int32_t it = 0; it < left && r == RFF_OK; ++it)
         if (cudaGraphLaunch(gx, master) != cudaSuccess) r = RFF_ECUDA;
       // the solves' streams wait for the graph before their next work
@@ -2109,6 +2239,8 @@ rff_status rff_sweep_run(rff_admm_t* handles, int32_t n, int32_t iters) {
         }
       cudaStreamSynchronize(master);
       if (gx) cudaGraphExecDestroy(gx);
+      tc_multi_destroy(m1);
+      tc_multi_destroy(m2);
       cudaStreamDestroy(master);
       if (r != RFF_OK && first == RFF_OK) first = r;
     }

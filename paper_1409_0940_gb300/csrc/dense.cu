@@ -96,8 +96,12 @@ __global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict_
   __shared__ __align__(16) float As[32][64 + 4];
   __shared__ __align__(16) float Bs[32][64 + 4];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  float acc[4][4] = {};
+  // FP32 products summed 32 at a time (acc), each chunk's sum folded into a float-float
+  // accumulator (hi, lo) by TwoSum: the error of a K-term dot product is that of one
+  // 32-term FP32 sum instead of a K-term one (K = s_j = 4096 for the cached projection)
+  float hi[4][4] = {}, lo[4][4] = {};
   for (int k0 = 0; k0 < g.K; k0 += 32) {
+    float acc[4][4] = {};
     // A tile: 64 rows x 32 k
     for (int t = tid; t < 64 * 32; t += 256) {
       const int kk = t % 32, mm = t / 32;
@@ -122,6 +126,16 @@ __global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict_
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        // TwoSum (Knuth); separately rounded operations, not contracted
+        const float sum = __fadd_rn(hi[i][j], acc[i][j]);
+        const float bb = __fsub_rn(sum, hi[i][j]);
+        lo[i][j] += __fadd_rn(__fsub_rn(hi[i][j], __fsub_rn(sum, bb)), __fsub_rn(acc[i][j], bb));
+        hi[i][j] = sum;
+      }
   }
   const float* __restrict__ Cm = static_cast<const float*>(g.Cm);
   float* __restrict__ D = static_cast<float*>(g.D);
@@ -133,7 +147,7 @@ __global__ void __launch_bounds__(256) k_gemm_f32_nn(const GemmDesc* __restrict_
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx * 4 + j;
       if (gn >= g.N) continue;
-      float v = alpha * acc[i][j];
+      float v = alpha * (hi[i][j] + lo[i][j]);
       if (beta != 0.f) v = fmaf(beta, Cm[(int64_t)gm * g.ldc + gn], v);
       D[(int64_t)gm * g.ldd + gn] = v;
     }

@@ -24,7 +24,11 @@ struct TcView {
   float inv_xg;                     // 1 / (xscale gscale): the X.G accumulator times this is X G
   int bias_in_mma;                  // 1: b is column d of G and X carries ones there
   int kc;                           // ring K chunk (64 or 32; 0 = library default)
-  int zt;                           // 1: Z tile in tensor memory, 0: in shared memory
+  int zt;                           // 1: Z tile in tensor memory, 0: in shared memory,
+                                    // 2: in tensor memory with acc1 double-buffered (m_pad <= 128),
+                                    // 3: the wide geometry (N = 256 X.G, Z hi in TMEM and lo in
+                                    //    shared memory; m_pad <= 192; one CTA)
+  int cg;                           // 2: CTA pairs (tcgen05.mma.cta_group::2, Z in TMEM), else one CTA
   const uint8_t* bmask;             // device, R x C: active blocks of a stochastic iteration, or null
   int64_t row_tiles;                // pass 2: 128-row tiles taken from the first (0 = all of them)
   cudaStream_t st;
@@ -43,6 +47,18 @@ cudaError_t tc_pass1(const TcView& v, float* Rpart);
 // m_block_stride elements apart.
 cudaError_t tc_pass2(const TcView& v, const __half* Mhi, const __half* Mlo, int64_t m_block_stride,
                      float* out, int per_block, const unsigned* m_amax, unsigned* out_amax = nullptr);
+// One launch of pass 1 (which = 1) or pass 2 (which = 2) for n solves (a model-selection
+// sweep, n <= 64): per solve its view and the arguments its own tc_pass1 / tc_pass2 call would
+// take (outs = Rpart or O'; Mhi, Mlo, m_amax, out_amax for pass 2 only, else null).  The solves'
+// arguments go to device memory that the object owns (a synchronous copy: create it outside
+// stream capture); every launch then reads them, so the object must outlive the launches.
+// Every solve runs the default geometry (K chunk 64, Z tile in TMEM, one CTA per MMA).
+struct TcMulti;
+cudaError_t tc_multi_create(const TcView* views, int n, int which, float* const* outs, const __half* const* Mhi,
+                            const __half* const* Mlo, const unsigned* const* m_amax, unsigned* const* out_amax,
+                            TcMulti** out);
+cudaError_t tc_multi_launch(const TcMulti* t, cudaStream_t st);
+void tc_multi_destroy(TcMulti* t);
 // Scores for a query block (nrows slot-padded rows of split X) against M (mpad x fslots hi/lo).
 // Error word of the tensor-core kernels (bounded waits that gave up); reads and clears it.
 // Synchronises the device.  0 = no error.

@@ -103,24 +103,35 @@ def test_autotuner_choice_is_reported(rff):
     s.close()
 
 
-def test_every_tile_geometry_gives_identical_results(rff, monkeypatch):
-    """The four geometries of the regeneration kernel (ring K chunk 64 or 32, Z tile in shared
-    or tensor memory) issue the same products in the same order: weights and scores agree bitwise."""
-    X, Y = synth.multiclass(n=1500, d=30, m=5, seed=2)
-    kw = dict(prec="split_bf16", loss="hinge", reg="l2", lam=1e-3, sigma=3.0, D=640, R=2, C=2, seed=3, m=5)
+@pytest.mark.parametrize("shape", [dict(n=1500, D=640, R=2, C=2), dict(n=1111, D=900, R=3, C=2),
+                                   dict(n=700, D=384, R=1, C=3), dict(n=600, D=1024, R=5, C=2)])
+def test_every_tile_geometry_gives_identical_results(rff, monkeypatch, shape):
+    """The twelve geometries of the regeneration kernels (ring K chunk 64 or 32; Z tile in shared
+    or tensor memory, the latter with one or two X.G accumulators; one CTA or a CTA pair per
+    MMA; X.G products 128 or 256 wide) issue the same products in the same order
+    for every output element: weights and scores agree bitwise.  The shapes give row blocks and
+    column blocks with an odd number of 128-slot tiles (a CTA pair then computes and discards a
+    tile past the block), an odd number of query tiles, and blocks of fewer rows than features
+    (the outer form, whose set-up materialises Z through the same kernel)."""
+    X, Y = synth.multiclass(n=shape["n"], d=30, m=5, seed=2)
+    kw = dict(prec="split_bf16", loss="hinge", reg="l2", lam=1e-3, sigma=3.0, D=shape["D"], R=shape["R"],
+              C=shape["C"], seed=3, m=5)
     out = []
-    for g in ("64,0", "64,1", "32,0", "32,1"):
+    for g in ("64,0", "64,1", "32,0", "32,1", "64,1,2", "32,1,2", "64,2", "32,2", "64,2,2", "32,2,2", "64,3",
+              "32,3"):
         monkeypatch.setenv("RFF_TC_GEOMETRY", g)
         s = rff.Solver(**kw)
         s.set_data(X, Y)
         s.solve(8, stats=False)
         p = s.profile()
-        assert (p["tc_kchunk"], p["tc_z_tmem"]) == tuple(int(x) for x in g.split(","))
-        out.append((s.weights(), s.predict(X[:200])))
+        f = [int(x) for x in g.split(",")] + [1]
+        assert (p["tc_kchunk"], p["tc_z_tmem"], p["tc_cta_pair"] + 1) == (f[0], f[1], f[2])
+        out.append((s.weights(), s.predict(X[:200]), s.predict(X[:333])))
         s.close()
-    for W, P in out[1:]:
+    for W, P, P2 in out[1:]:
         assert np.array_equal(W, out[0][0])
         assert np.array_equal(P, out[0][1])
+        assert np.array_equal(P2, out[0][2])
 
 
 def test_sweep_graph_continues_and_keeps_masks(rff):
