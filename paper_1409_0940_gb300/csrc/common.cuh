@@ -80,6 +80,34 @@ __device__ __forceinline__ float cos_rr(float x) {
   return (static_cast<int>(k) & 1) ? -p : p;
 }
 
+// 2^E cos(x), bit for bit 2^E cos_rr(x), with fewer instructions for the tensor-core
+// epilogues (where the cosine's instruction count, not the tensor pipe, bounds the small-d
+// workloads): k = rint(x / pi) by adding and subtracting 1.5 2^23 to the rounded quotient
+// (exact for |x / pi| < 2^22) instead of a rounding and a float-to-integer conversion on the
+// transcendental unit, the parity of k read from the low mantissa bit of the biased sum, the
+// sign applied by flipping the sign bit, and 2^E folded into the polynomial's coefficients
+// (scaling by a power of two commutes with every rounding of the evaluation).
+template <int E>
+__device__ __forceinline__ float cos_rr_pow2(float x) {
+  constexpr float S = (float)(1u << E);
+  const float inv_pi = 0.318309886183790672f;
+  const float pi_hi = 3.14159274101257324f;
+  const float pi_lo = -8.74227765734758577e-08f;
+  const float magic = 12582912.f;   // 1.5 2^23
+  const float biased = __fadd_rn(__fmul_rn(x, inv_pi), magic);   // not contracted: rint of the rounded quotient
+  const float k = __fsub_rn(biased, magic);
+  float r = fmaf(-k, pi_hi, x);
+  r = fmaf(-k, pi_lo, r);
+  const float s = r * r;
+  float p = -2.605149518331018e-07f * S;
+  p = fmaf(p, s, 2.476016197761055e-05f * S);
+  p = fmaf(p, s, -0.0013888361863791943f * S);
+  p = fmaf(p, s, 0.04166663810610771f * S);
+  p = fmaf(p, s, -0.5f * S);
+  p = fmaf(p, s, 1.0f * S);
+  return __int_as_float(__float_as_int(p) ^ (__float_as_int(biased) << 31));
+}
+
 // ------------------------------------------------------------------ BF16 split
 // x = hi + lo + O(2^-17 |x|): hi = bf16(x), lo = bf16(x - hi).
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {

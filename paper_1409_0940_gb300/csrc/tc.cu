@@ -60,6 +60,7 @@ constexpr int NTHREADS = 64 + 32 * NEPI;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC2_COL = 256;         // acc2 with a single acc1 (ZT 0, 1)
 constexpr int MAXG = 64;                    // groups (column blocks) per CTA
+static_assert(COS_SCALE == 128.f, "the epilogues form COS_SCALE cos(.) as cos_rr_pow2<7>");
 constexpr int PRED_GT = 8;                  // feature tiles per scoring group
 
 // Ring geometry.  KC = K elements per ring stage: 64 (128-byte rows, 128-byte
@@ -596,7 +597,8 @@ __device__ __forceinline__ void regen_body(const TcArgs& a, const CtaPos& pos) {
         fence_before();
         __syncwarp();
         if (lane == 0) arrive_mma_side<CG>(bar_a1e + 8 * b);
-        // z = cos(acc (+ b)); the factor sqrt(2/D) is applied when acc2 is written
+        // z = cos(acc (+ b)), times COS_SCALE when it feeds the chained product; the factor
+        // sqrt(2/D) is applied when acc2 (or the materialised Z) is written
         float z[64];
         if (add_bias) {
           const float* bcol = a.bias + bslot + colbase;
@@ -605,11 +607,26 @@ __device__ __forceinline__ void regen_body(const TcArgs& a, const CtaPos& pos) {
             const float ph = (a.mode == MODE_PASS1)                             ? bias_a
                              : RFF_IN(bslot + colbase + c, a.fslots) ? __ldg(bcol + c)
                                                                      : 0.f;
-            z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg + ph);
+            z[c] = __uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg + ph;
+          }
+          // one loop per branch: a per-element choice would evaluate both cosines
+          if (chain) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) z[c] = cos_rr_pow2<7>(z[c]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) z[c] = cos_rr(z[c]);
           }
         } else {
 #pragma unroll
-          for (int c = 0; c < 64; ++c) z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg);
+          for (int c = 0; c < 64; ++c) z[c] = __uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg;
+          if (chain) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) z[c] = cos_rr_pow2<7>(z[c]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) z[c] = cos_rr(z[c]);
+          }
         }
         if (!chain) {
           // materialise Z = sqrt(2/D) cos(...) (float32) inside the window
@@ -646,7 +663,7 @@ __device__ __forceinline__ void regen_body(const TcArgs& a, const CtaPos& pos) {
             uint32_t ph[16], pl[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-              const float z0 = COS_SCALE * z[32 * hf + 2 * q], z1 = COS_SCALE * z[32 * hf + 2 * q + 1];
+              const float z0 = z[32 * hf + 2 * q], z1 = z[32 * hf + 2 * q + 1];   // COS_SCALE z
               const __half2 h = __floats2half2_rn(z0, z1);
               const float2 f = __half22float2(h);
               const __half2 l = __floats2half2_rn(z0 - f.x, z1 - f.y);
@@ -669,7 +686,7 @@ __device__ __forceinline__ void regen_body(const TcArgs& a, const CtaPos& pos) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               // hi = fp16x2(s z0, s z1); lo = fp16x2(s z - hi) (packed conversions)
-              const float z0 = COS_SCALE * z[ch * 8 + 2 * q], z1 = COS_SCALE * z[ch * 8 + 2 * q + 1];
+              const float z0 = z[ch * 8 + 2 * q], z1 = z[ch * 8 + 2 * q + 1];   // COS_SCALE z
               const __half2 h = __floats2half2_rn(z0, z1);
               const float2 hf = __half22float2(h);
               const __half2 l = __floats2half2_rn(z0 - hf.x, z1 - hf.y);
@@ -1031,11 +1048,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_wide(const __grid_constan
               const float ph = (a.mode == MODE_PASS1)                             ? bias_a
                                : RFF_IN(bslot + colbase + c, a.fslots) ? __ldg(bcol + c)
                                                                        : 0.f;
-              z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg + ph);
+              z[c] = __uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg + ph;
             }
           } else {
 #pragma unroll
-            for (int c = 0; c < 64; ++c) z[c] = cos_rr(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg);
+            for (int c = 0; c < 64; ++c) z[c] = __uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv_xg;
+          }
+          // one loop per branch: a per-element choice would evaluate both cosines
+          if (chain) {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) z[c] = cos_rr_pow2<7>(z[c]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) z[c] = cos_rr(z[c]);
           }
           if (!chain) {
             const int64_t r = arow - a.wz_r0;
@@ -1069,7 +1094,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_regen_wide(const __grid_constan
               uint32_t ph[16], pl[16];
 #pragma unroll
               for (int q = 0; q < 16; ++q) {
-                const float z0 = COS_SCALE * z[32 * hf + 2 * q], z1 = COS_SCALE * z[32 * hf + 2 * q + 1];
+                const float z0 = z[32 * hf + 2 * q], z1 = z[32 * hf + 2 * q + 1];   // COS_SCALE z
                 const __half2 hh = __floats2half2_rn(z0, z1);
                 const float2 f = __half22float2(hh);
                 const __half2 l = __floats2half2_rn(z0 - f.x, z1 - f.y);
