@@ -417,12 +417,12 @@ rff_status rff_selftest_wait_timeout(void* stream);
  * scoring test, at their global accesses, that every element index lies inside the layout
  * the operation defines (the regeneration passes' X, G, chained-operand and output tiles, the
  * tensor-core epilogues' output rows, the exchange's row tiles, the sparse scatter's column
- * indices, the TensorSketch output rows) and that every TMA box starts on a 16-byte boundary; a failed test skips the
- * access and is counted.  rff_check_enabled() is 1 in that build and 0 in the ordinary one.
+ * indices, the TensorSketch output rows, the factorisation's operand slices) and that every
+ * TMA box starts on a 16-byte boundary; a failed test skips the access and is counted.  rff_check_enabled() is 1 in that build and 0 in the ordinary one.
  * rff_check_report synchronises the device and reads and clears the counts into out[5]:
  *   out[0]  failed tests since the last report (0 in the ordinary build),
  *   out[1]  source unit of the first failure: 1 elementwise.cu, 2 qgemm.cu, 3 regen_simt.cu,
- *           4 tc.cu, 5 sketch.cu,
+ *           4 tc.cu, 5 sketch.cu, 6 ozaki.cu,
  *   out[2]  its source line, out[3] the index tested, out[4] the bound it broke.
  * A skipped TMA copy leaves its barrier incomplete: the bounded wait on it gives up and the
  * pass returns RFF_ETIMEOUT.  Returns RFF_ECUDA if the device reports an error. */

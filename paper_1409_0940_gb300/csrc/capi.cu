@@ -1973,8 +1973,9 @@ rff_status rff_check_report(int64_t* out) {
   }
   // the units in the order of their numbers in the report
   cudaError_t (*const units[])(CheckHit*) = {check_collect_elementwise, check_collect_qgemm,
-                                             check_collect_regen_simt, check_collect_tc, check_collect_sketch};
-  for (int u = 0; u < 5; ++u) {
+                                             check_collect_regen_simt,  check_collect_tc,
+                                             check_collect_sketch,      check_collect_ozaki};
+  for (int u = 0; u < 6; ++u) {
     CheckHit hit{};
     if (units[u](&hit) != cudaSuccess) {
       cudaGetLastError();

@@ -142,4 +142,29 @@ __device__ __forceinline__ float f16_inv_scale(float maxabs) { return ldexpf(1.f
 // Fixed scale of the FP16 split of cosines (|cos| <= 1) in the chained products
 constexpr float COS_SCALE = 128.f;
 
+// f * 2^k as an FP64 number, built from the exponent and significand fields with integer
+// instructions and selects, no branches (this part's FP64 pipe, conversions included, runs at
+// 1/64 of the FP32 rate).  Exact for zero and normal f when the result is a normal double;
+// subnormal f and results below the normal range give a signed zero, results above it a
+// signed infinity.
+__device__ __forceinline__ double f32_to_f64_scaled(float f, int k) {
+  const uint32_t b = __float_as_uint(f);
+  const int e = (int)((b >> 23) & 0xffu);
+  const int ed = e + (1023 - 127) + k;
+  const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+  uint64_t bits = sign | ((uint64_t)(uint32_t)ed << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
+  bits = (e == 0 || ed <= 0) ? sign : bits;
+  bits = ed >= 2047 ? (sign | 0x7ff0000000000000ull) : bits;
+  return __longlong_as_double((long long)bits);
+}
+
+// hi + lo += x with the rounding error of the addition kept in lo (Knuth's TwoSum, every
+// operation rounded separately: no contraction into FMAs)
+__device__ __forceinline__ void two_sum_into(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb)));
+  hi = s;
+}
+
 }  // namespace rff

@@ -6,6 +6,8 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
 namespace rff {
@@ -555,17 +557,30 @@ cudaError_t launch_mirror_lower(double* Q, int64_t ld, int64_t s, cudaStream_t s
 // sweep, 4-5 backward sweep, 6-9 conversions to float pairs (double-float mode)
 constexpr int FACTOR_PHASES = 10;
 
+// RFF_FACTOR=df selects the double-float block updates below instead of the tensor-core ones
+// of ozaki.cu (read once)
+static bool use_double_float_updates() {
+  static const bool df = [] {
+    const char* e = getenv("RFF_FACTOR");
+    return e && strcmp(e, "df") == 0;
+  }();
+  return df;
+}
+
 size_t factor_scratch_bytes(int njobs, int smax) {
   const int nb = (int)ceil_div(smax, 64);
   // per job: the diagonal inverses, and two 64 x (nb * 64) float-pair staging buffers
-  return (size_t)njobs * nb * 64 * 64 * sizeof(double) + (size_t)njobs * 2 * 64 * nb * 64 * sizeof(float2) +
-         (size_t)njobs * sizeof(DiagJob) * nb + (size_t)njobs * nb * FACTOR_PHASES * sizeof(GemmDesc) + 1024;
+  const size_t df = (size_t)njobs * nb * 64 * 64 * sizeof(double) +
+                    (size_t)njobs * 2 * 64 * nb * 64 * sizeof(float2) + (size_t)njobs * sizeof(DiagJob) * nb +
+                    (size_t)njobs * nb * FACTOR_PHASES * sizeof(GemmDesc) + 1024;
+  return std::max(df, oz_factor_scratch_bytes(njobs, smax));
 }
 
 cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st,
                                   bool double_float) {
   const int nj = (int)jobs.size();
   if (nj == 0) return cudaSuccess;
+  if (!use_double_float_updates()) return factor_and_invert_oz(jobs, invert, dev_scratch, st);
   int smax = 0;
   for (const auto& j : jobs) smax = std::max(smax, j.s);
   const int nb = (int)ceil_div(smax, 64);

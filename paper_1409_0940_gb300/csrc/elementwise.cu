@@ -900,15 +900,20 @@ __global__ void k_gram_reduce(const float* __restrict__ P, int nchunk, int ntile
 #pragma unroll
   for (int c = 0; c < GRAM_PIECES_MAX; ++c)
     if (c < nchunk) p[c] = *reinterpret_cast<const float4*>(P + ((int64_t)c * ntiles + tile) * (128 * 256) + e);
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  // the pieces' sum as a float pair (TwoSum: exact but for the pair's own rounding, ~2^-48),
+  // turned into FP64 by integer instructions: two FP64 additions per element, not 2 nchunk
+  float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int c = 0; c < GRAM_PIECES_MAX; ++c)
     if (c < nchunk) {
-      v[0] += (double)p[c].x;
-      v[1] += (double)p[c].y;
-      v[2] += (double)p[c].z;
-      v[3] += (double)p[c].w;
+      two_sum_into(hi[0], lo[0], p[c].x);
+      two_sum_into(hi[1], lo[1], p[c].y);
+      two_sum_into(hi[2], lo[2], p[c].z);
+      two_sum_into(hi[3], lo[3], p[c].w);
     }
+  double v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = f32_to_f64_scaled(hi[q], 0) + f32_to_f64_scaled(lo[q], 0);
   double* h = H + row * ldh + col;
   if (col + 3 <= row && (reinterpret_cast<uintptr_t>(h) & 15) == 0) {
     double2* h2 = reinterpret_cast<double2*>(h);

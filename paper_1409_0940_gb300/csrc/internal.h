@@ -47,6 +47,7 @@ cudaError_t check_collect_qgemm(CheckHit* h);
 cudaError_t check_collect_regen_simt(CheckHit* h);
 cudaError_t check_collect_tc(CheckHit* h);
 cudaError_t check_collect_sketch(CheckHit* h);
+cudaError_t check_collect_ozaki(CheckHit* h);
 
 struct PassArgs {
   const float* X;        // data rows (slots) x K, float32            (SIMT)
@@ -177,6 +178,12 @@ size_t factor_scratch_bytes(int njobs, int smax);
 // updates (the 64 x 64 diagonal factorisations stay FP64)
 cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st,
                                   bool double_float = false);
+cudaError_t launch_mirror_lower(double* Q, int64_t ld, int64_t s, cudaStream_t st);
+
+// ozaki.cu: the same factorisation with the block updates on the tensor cores (error-free
+// slices of the FP64 operands); factor_and_invert_f64 calls it unless RFF_FACTOR=df
+size_t oz_factor_scratch_bytes(int njobs, int smax);
+cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st);
 
 // elementwise.cu
 // dst[p][c] = src[map[p] * lds + c] (c < w), zero for c >= w or map[p] < 0; map null = identity
