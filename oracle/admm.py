@@ -35,7 +35,12 @@ Readings (the paper is silent or inconsistent; each is stated here once):
 Variants: "equation" keeps every Obar_ij as printed; "reorganised" follows the
 memory-efficient rewrite of Sec. 3 (U_ij = Z_ij^T O_ij, one Delta_i,
 Z_ij^T Obar_ij = U_ij + Z_ij^T Delta_i / (C + 1),
-Obar_i = sum_j O_ij / (C + 1) + C/(C + 1) O_i), with the Z^T nu term restored.
+Obar_i = sum_j O_ij / (C + 1) + C/(C + 1) O_i), with the Z^T nu term restored;
+"incremental" is the equation form with each graph projection taken from the block's
+previous (What_ij, O_ij): the projection is linear and fixes every point of the graph
+(O_ij = Z_ij What_ij), so proj[Obar_ij + nu_i, Wbar_j - mu_ij] = (O_ij, What_ij) +
+proj[Obar_ij + nu_i - O_ij, Wbar_j - mu_ij - What_ij]; the same iterates, with a
+right-hand side that holds only what changed.
 
 Stochastic block subsets (proposed in Sec. 5 and the conclusion, not specified there):
 with ``block_fraction`` p < 1, iteration k updates only the blocks drawn active.
@@ -54,7 +59,7 @@ Residuals (reported, never used to stop):
   dual   = rho |(Wbar^k - Wbar^{k-1}, Obar^k - Obar^{k-1})|_F
 
 Pins: ridge closed form for squared loss + l2 (Sec. 2.2); the KKT system of the
-graph projection; "equation" == "reorganised" to 1e-12; residuals -> 0.
+graph projection; "equation" == "reorganised" == "incremental" to 1e-12; residuals -> 0.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -228,11 +233,17 @@ def admm(prob, iters, variant="equation", history=False, block_fraction=1.0):
         for j in range(C):
             W[j] = P.prox_reg(prob.reg, Wbar[j] - mu[j], prob.t_reg)
 
-        if variant == "equation":
+        if variant in ("equation", "incremental"):
             for i in range(R):
                 for j in range(C):
-                    if act[i, j]:
+                    if not act[i, j]:
+                        continue
+                    if variant == "equation":
                         What[i][j], Oij[i][j] = solvers[i][j].project(Wbar[j] - muij[i][j], Obij[i][j] + nu[i])
+                    else:
+                        dW, dO = solvers[i][j].project(Wbar[j] - muij[i][j] - What[i][j],
+                                                       Obij[i][j] + nu[i] - Oij[i][j])
+                        What[i][j], Oij[i][j] = What[i][j] + dW, Oij[i][j] + dO
             for j in range(C):
                 Wbar[j] = (W[j] + sum(What[i][j] for i in range(R))) / (R + 1)
             for i in range(R):

@@ -167,6 +167,9 @@ struct rff_admm_s {
     return (float)(p.feature_map == RFF_MAP_LAPLACE ? 1.0 / std::sqrt((double)D) : std::sqrt(2.0 / (double)D));
   }
   bool cached_z() const { return p.prec == RFF_PREC_CACHED_Z; }
+  // Gram form: the projection is taken incrementally (phase_project), and pass 1 reads one
+  // operand U_i for every column block
+  bool incremental() const { return !outer; }
   int64_t rpart_elems() const { return (int64_t)std::max(nsplit_max, nsplit_cz) * R * fslots * mpad; }
 };
 
@@ -293,7 +296,7 @@ size_t working_set_bytes(const rff_admm_s& s) {
   if (!s.split_path() || s.cached_z()) t += (size_t)s.nslots * s.dld * f + (size_t)s.fslots * s.dld * f;
   t += (size_t)s.fslots * f;
   t += (size_t)s.nslots * s.mpad * f * (4 + 2);                 // Y, O, Obar, nu, nu_old, Obar_old
-  t += (size_t)s.C * s.nslots * s.mpad * f * (s.split_path() ? 1 : 2);   // Op (+ V on the FP32 path)
+  t += (size_t)s.C * s.nslots * s.mpad * f * (s.split_path() && !s.outer ? 1 : 2);   // Op (+ FP32 V)
   if (s.split_path()) t += (size_t)s.C * s.nslots * s.mpad * b2 * 2;
   t += (size_t)s.fslots * s.mpad * f * 5;                       // W, Wbar, mu, mu_old, Wbar_old
   t += (size_t)s.R * s.fslots * s.mpad * f * (3 + s.nsplit_max);    // What, muij, muij_old, Rpart
@@ -313,7 +316,7 @@ size_t working_set_bytes(const rff_admm_s& s) {
     t += (size_t)s.R * s.fslots * s.mpad * f;                                                   // rhs
     t += (size_t)s.foff.back() * f + (size_t)s.R * s.C * sizeof(GemmDesc);                     // factors
   }
-  if (s.outer) t += (size_t)s.C * s.nslots * s.mpad * f;                                       // u = Z rhs
+  if (s.outer) t += (size_t)s.C * s.nslots * s.mpad * f * 2;                                   // e = V - Z c, y
   if (s.tensorsketch()) t += (size_t)TS_SCORE_ROWS * s.fslots * f + 256;   // scoring rows
   return t + (64u << 20);
 }
@@ -611,7 +614,7 @@ rff_status set_data_impl(rff_admm_t h, const XInput& xin, const float* Yin, int6
   AL(s.nu_old, s.nslots * s.mpad);
   AL(s.Obar_old, s.nslots * s.mpad);
   AL(s.Op, (int64_t)s.C * s.nslots * s.mpad);
-  if (!s.split_path()) AL(s.V32, (int64_t)s.C * s.nslots * s.mpad);
+  if (!s.split_path() || s.outer) AL(s.V32, (int64_t)s.C * s.nslots * s.mpad);   // FP32 V (outer form: U_i)
   AL(s.amax, AMAX_WORDS);
   AL(s.W, s.fslots * s.mpad);
   AL(s.Wbar, s.fslots * s.mpad);
@@ -653,7 +656,7 @@ rff_status set_data_impl(rff_admm_t h, const XInput& xin, const float* Yin, int6
     AL(s.Q32, s.foff.back());
     AL(s.gdesc, s.R * s.C);
   }
-  if (s.outer) AL(s.U32, (int64_t)s.C * s.nslots * s.mpad);
+  if (s.outer) AL(s.U32, 2 * (int64_t)s.C * s.nslots * s.mpad);   // Z c and V - Z c, then -P (V - Z c)
   AL(s.lam_dev, s.mpad);
   AL(s.partials, 1024);
   AL(s.flag, 4);
@@ -959,7 +962,7 @@ rff_status materialise_z(rff_admm_t h) {
         SgJob jb{};
         jb.a_row = (int32_t)(ft * 128);
         jb.a_k0 = (int32_t)(s.row_slot[i] + t0 * 128);
-        jb.b_row = (int32_t)(j * s.mpad);
+        jb.b_row = (int32_t)(s.incremental() ? 0 : j * s.mpad);   // the shared U_i, or V_ij
         jb.b_k0 = jb.a_k0;
         jb.nk = (int32_t)((t1 - t0) * 4);
         jb.blk = i * s.C + j;
@@ -1232,6 +1235,11 @@ rff_status setup_factors(rff_admm_t h) {
       }
       for (int64_t r = 0; !s.outer && r < s.row_size[i]; r += chunk_rows) {
         const int64_t nr = std::min(chunk_rows, s.row_size[i] - r);
+        if (s.split_path() && getenv("RFF_DIAG_SIMT_GRAM")) {
+          CK(tc_write_z(tc_view(s), s.row_slot[i] + r, nr, s.col_slot[j], sj, Zc, sj));
+          CK(launch_gram_f32_to_f64(Zc, sj, nr, sj, Hb, sj, s.st));
+          continue;
+        }
         if (tc_gram(s)) {   // Z^T's split written by the regeneration itself, or the stored one
           const TcView zv = tc_view(s);
           rff_status gr = tc_gram_accumulate(h, nullptr, nr, sj, Hb, gbase, chunk_rows, smax,
@@ -1277,7 +1285,8 @@ rff_status setup_factors(rff_admm_t h) {
       if (s.outer) {
         // O'_ij = (I + Z_ij Z_ij^T)^-1 u_ij, rows of block i in column block j
         const int64_t ni = s.row_size[i], roff = ((int64_t)j * s.nslots + s.row_slot[i]) * s.mpad;
-        g[blk] = GemmDesc{s.Q32 + s.foff[blk], s.U32 + roff, nullptr, s.Op + roff, (int)ni, (int)s.mpad, (int)ni, ni,
+        float* yb = s.U32 + (int64_t)s.C * s.nslots * s.mpad;   // y_ij = -P_ij e_ij (alpha = -1)
+        g[blk] = GemmDesc{s.Q32 + s.foff[blk], s.U32 + roff, nullptr, yb + roff, (int)ni, (int)s.mpad, (int)ni, ni,
                           s.mpad, 0, s.mpad};
       } else if (s.split_path()) {
         // one job per 128-row tile of Q_ij: rows of W'_ij, all m_pad columns, K = s_j
@@ -1293,8 +1302,9 @@ rff_status setup_factors(rff_admm_t h) {
           qj.push_back(jb);
         }
       } else {
-        float* Qb = s.Q32 + s.foff[blk];
-        g[blk] = GemmDesc{Qb, s.rhs + off, nullptr, s.What + off, (int)sj, (int)s.mpad, (int)sj, sj, s.mpad, 0, s.mpad};
+        float* Qb = s.Q32 + s.foff[blk];   // W'_ij += Q_ij rhs_ij (the incremental projection)
+        g[blk] = GemmDesc{Qb, s.rhs + off, s.What + off, s.What + off, (int)sj, (int)s.mpad, (int)sj, sj, s.mpad,
+                          s.mpad, s.mpad};
       }
     }
   if (s.split_path() && !s.outer) {
@@ -1360,6 +1370,7 @@ SgView qgemm_view(const rff_admm_s& s) {
   v.amax = s.amax + AMAX_W;
   v.two_acc = 1;
   v.bmask = s.act();
+  v.accumulate = 1;   // W'_ij += Q_ij rhs_ij (the incremental projection)
   v.st = s.st;
   return v;
 }
@@ -1420,7 +1431,7 @@ SgView cz_pass2_view(const rff_admm_s& s) {
 
 // kernel launches of one iteration (the count a captured iteration replays)
 int iter_launches(const rff_admm_s& s) {
-  int n = s.outer ? (s.split_path() ? 13 : 9) : (s.split_path() ? 8 : 7);
+  int n = s.outer ? (s.split_path() ? 14 : 10) : (s.split_path() ? 8 : 7);
   if (s.stochastic()) n += 1 + (s.split_path() && !s.outer ? 1 : 0);   // the mask; max |O'| of all blocks
   return n;
 }
@@ -1447,8 +1458,10 @@ rff_status exchange_and_average(rff_admm_t h, int k) {
   rff_status r;
   RowEpiArgs e{s.Op, s.O, s.Obar, s.nu, s.Y, s.V32, nullptr, nullptr, nullptr, s.row_of_slot, s.nslots,
                s.C, (int)s.m, (int)s.mpad, s.p.loss, s.p.newton_iters, s.t_loss};
-  if (s.split_path()) {
-    // V^T as a scaled FP16 pair straight from the exchange (scale from the bound of |V|)
+  const bool vsplit = s.split_path() && !s.outer;   // the outer form reads U_i in FP32
+  if (vsplit) {
+    // U^T as a scaled FP16 pair straight from the exchange (scale from the bound of |U|)
+    e.V32 = nullptr;
     e.VThi = s.VThi;
     e.VTlo = s.VTlo;
     e.amax = s.amax;
@@ -1456,7 +1469,7 @@ rff_status exchange_and_average(rff_admm_t h, int k) {
     CK(cudaMemsetAsync(s.amax + AMAX_O_NEXT, 0, 8, s.st));
   }
   CK(launch_row_epilogue(e, s.st));
-  if (s.split_path())   // the outputs' maxima become the next exchange's inputs
+  if (vsplit)   // the outputs' maxima become the next exchange's inputs
     CK(cudaMemcpyAsync(s.amax + AMAX_O, s.amax + AMAX_O_NEXT, 8, cudaMemcpyDeviceToDevice, s.st));
   if ((r = mark(h, k, 5)) != RFF_OK) return r;
   CK(launch_avg_dual(s.W, s.What, s.R, nfe, s.Wbar, s.mu, s.muij, s.st));
@@ -1464,39 +1477,29 @@ rff_status exchange_and_average(rff_admm_t h, int k) {
 }
 
 // One iteration with the outer form of the graph projection (every block has fewer rows
-// than features).  With P_ij = (I + Z_ij Z_ij^T)^-1 the projection of eq. (gpWij) is
-//   rhs = Wbar_j - mu'_ij + Z_ij^T V_ij,  O'_ij = P_ij (Z_ij rhs),  W'_ij = rhs - Z_ij^T O'_ij
-// (Z W' = (I - Z Z^T P) Z rhs = P Z rhs): three regenerations of Z_ij per iteration and
-// an n_i x n_i factor instead of s_j x s_j.  Phases: ms_project covers rhs, Z rhs, P and
-// Z^T O'; ms_pass2 is empty.
+// than features): with c_ij = Wbar_j - mu'_ij, V_ij = Obar_ij + nu_i = O'_ij + U_i and
+// P_ij = (I + Z_ij Z_ij^T)^-1 (n_i x n_i), eq. (gpWij) and (gpOij) read
+//   W'_ij = (I + Z^T Z)^-1 (c + Z^T V) = c + Z^T P (V - Z c),   O'_ij = Z W'_ij = V - P (V - Z c)
+// ((I + Z^T Z)^-1 Z^T = Z^T P and Z Z^T P = I - P): two regenerations of Z_ij per iteration
+// (Z c and Z^T y), and no cancellation between two terms of the size of c.  In order:
+// c; u = Z c (pass 2); e = V - u; y = -P e (GEMM); W' = c - Z^T y (pass 1); O' += U + y.
+// Phases: ms_project covers c, Z c, P and Z^T y; ms_pass2 is empty.
 rff_status iterate_outer(rff_admm_t h, int k) {
   auto& s = *h;
   const int64_t nfe = s.fslots * s.mpad;
   const int64_t nmax = *std::max_element(s.row_size.begin(), s.row_size.end());
+  const int64_t nop = (int64_t)s.C * s.nslots * s.mpad;
+  float* y = s.U32 + nop;
   int* scratch_flag = reinterpret_cast<int*>(s.amax + AMAX_FLAG);
   rff_status r;
   if ((r = mark(h, k, 0)) != RFF_OK) return r;
   if (s.stochastic()) CK(launch_block_mask(s.p.seed, s.bthr, s.R * s.C, s.bctr, s.bmask, s.st));
   CK(launch_prox_reg(s.p.reg, s.Wbar, s.mu, nfe, s.t_reg, s.W, s.st, s.lam_dev, (int)s.mpad));
   if ((r = mark(h, k, 1)) != RFF_OK) return r;
-  // R_ij = Z_ij^T V_ij (inactive blocks of a stochastic iteration are skipped by every
-  // per-block kernel below and keep their W'_ij and O'_ij)
-  PassArgs a = base_pass_args(s);
-  a.bmask = s.act();
-  if (s.split_path()) {
-    CK(tc_pass1(iter_view(s), s.Rpart));
-  } else {
-    a.M = s.V32;
-    a.m_block_stride = s.nslots * s.mpad;
-    a.m_elems = (int64_t)s.C * s.nslots * s.mpad;
-    a.out = s.Rpart;
-    a.out_block_stride = nfe;
-    a.out_elems = s.rpart_elems();
-    CK(launch_pass1_simt(a, s.fslots, s.st));
-  }
   if ((r = mark(h, k, 2)) != RFF_OK) return r;
-  // rhs, then u_ij = Z_ij rhs_ij into U32
-  CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st, s.feat_of_slot, (int)s.mpad));
+  // c_ij, then u_ij = Z_ij c_ij into U32 (inactive blocks of a stochastic iteration are
+  // skipped by every per-block kernel below and keep their W'_ij and O'_ij)
+  CK(launch_rhs(s.Wbar, s.muij, s.Rpart, 0, s.R, nfe, s.rhs, s.st, s.feat_of_slot, (int)s.mpad));
   if (s.split_path()) {
     CK(cudaMemsetAsync(s.amax + AMAX_W, 0, 4, s.st));
     CK(launch_finite_check(s.rhs, s.R * nfe, 0, scratch_flag, s.st, s.amax + AMAX_W));
@@ -1511,30 +1514,38 @@ rff_status iterate_outer(rff_admm_t h, int k) {
     b.m_elems = (int64_t)s.R * nfe;
     b.out = s.U32;
     b.out_block_stride = s.nslots * s.mpad;
-    b.out_elems = (int64_t)s.C * s.nslots * s.mpad;
+    b.out_elems = nop;
     b.per_block = 1;
     CK(launch_pass2_simt(b, s.nslots, s.st));
   }
-  // O'_ij = P_ij u_ij
-  CK(launch_gemm_f32_nn(s.gdesc, s.R * s.C, (int)nmax, (int)s.mpad, 1.f, 0.f, s.st, s.act()));
-  // W'_ij = rhs_ij - Z_ij^T O'_ij (the second pass-1 product reuses the R partials)
+  // e_ij = V_ij - u_ij (in place), y_ij = -P_ij e_ij
+  CK(launch_outer_residual(s.U32, s.Op, s.V32, s.nslots, (int)s.mpad, s.C, s.st));
+  CK(launch_gemm_f32_nn(s.gdesc, s.R * s.C, (int)nmax, (int)s.mpad, -1.f, 0.f, s.st, s.act()));
+  // W'_ij = c_ij - Z_ij^T y_ij (operand per block)
+  PassArgs a = base_pass_args(s);
+  a.bmask = s.act();
   if (s.split_path()) {
-    // O'^T as a scaled FP16 pair in the V^T buffers (V^T is rewritten by the exchange);
-    // max |O'| is also the exchange's input
-    CK(cudaMemsetAsync(s.amax + AMAX_OP, 0, 4, s.st));
-    CK(launch_finite_check(s.Op, s.C * s.nslots * s.mpad, 0, scratch_flag, s.st, s.amax + AMAX_OP));
-    CK(launch_transpose_split_f16(s.Op, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
-                                  s.mpad * s.nslots, 1.f, s.amax + AMAX_OP, s.st));
+    // y^T as a scaled FP16 pair in the V^T buffers
+    CK(cudaMemsetAsync(s.amax + AMAX_OINC, 0, 4, s.st));
+    CK(launch_finite_check(y, nop, 0, scratch_flag, s.st, s.amax + AMAX_OINC));
+    CK(launch_transpose_split_f16(y, s.nslots, (int)s.mpad, s.C, s.nslots * s.mpad, s.VThi, s.VTlo, s.nslots,
+                                  s.mpad * s.nslots, 1.f, s.amax + AMAX_OINC, s.st));
     TcView vo = iter_view(s);
-    vo.v_amax = s.amax + AMAX_OP;
+    vo.v_amax = s.amax + AMAX_OINC;
     CK(tc_pass1(vo, s.Rpart));
   } else {
-    a.M = s.Op;
-    a.m_elems = (int64_t)s.C * s.nslots * s.mpad;
+    a.M = y;
+    a.m_block_stride = s.nslots * s.mpad;
+    a.m_elems = nop;
+    a.out = s.Rpart;
+    a.out_block_stride = nfe;
+    a.out_elems = s.rpart_elems();
     CK(launch_pass1_simt(a, s.fslots, s.st));
   }
   CK(launch_sub_partials(s.rhs, s.Rpart, s.nsplit, s.R, nfe, s.feat_of_slot, (int)s.mpad, s.What, s.st, s.act(),
                          s.d_col_slot, s.C));
+  // O'_ij = V_ij - P_ij e_ij = O'_ij + U_i + y_ij
+  CK(launch_outer_update(s.Op, s.V32, y, s.nslots, (int)s.mpad, s.R, s.C, s.d_row_slot, s.act(), s.st));
   if ((r = mark(h, k, 3)) != RFF_OK) return r;
   if ((r = mark(h, k, 4)) != RFF_OK) return r;
   if ((r = exchange_and_average(h, k)) != RFF_OK) return r;
@@ -1558,7 +1569,8 @@ rff_status phase_pre(rff_admm_t h, int k) {
   return mark(h, k, 1);
 }
 
-// pass 1: R_ij = Z_ij^T V_ij,  V_ij = Obar_ij + nu_i
+// pass 1: R_ij = Z_ij^T U_i with U_i = Delta_i/(C+1) + nu_i = Obar_ij + nu_i - O'_ij, one
+// operand for every column block (the incremental projection below)
 rff_status phase_pass1(rff_admm_t h) {
   auto& s = *h;
   PassArgs a = base_pass_args(s);
@@ -1569,7 +1581,7 @@ rff_status phase_pass1(rff_admm_t h) {
     CK(tc_pass1(iter_view(s), s.Rpart));
   } else {
     a.M = s.V32;
-    a.m_block_stride = s.nslots * s.mpad;
+    a.m_block_stride = 0;   // the shared U_i
     a.m_elems = (int64_t)s.C * s.nslots * s.mpad;
     a.out = s.Rpart;
     a.out_block_stride = s.fslots * s.mpad;
@@ -1587,21 +1599,27 @@ rff_status phase_project(rff_admm_t h, int k) {
   for (int j = 0; j < s.C; ++j) smax = std::max(smax, s.col_size[j]);
   rff_status r;
   if ((r = mark(h, k, 2)) != RFF_OK) return r;
-  // graph projection, eq. (gpWij): W'_ij = Q_ij (Wbar_j - mu'_ij + R_ij) with the cached inverse.
-  // (A refinement step r = rhs - H x computed in FP32 adds more rounding than it removes, and an
-  // FP64 or compensated residual costs several times the solve on this part's FP64/FP32 pipes.)
+  // graph projection, eq. (gpWij): W'_ij = Q_ij (Wbar_j - mu'_ij + Z_ij^T (Obar_ij + nu_i)) with
+  // the cached inverse Q_ij = (I + Z_ij^T Z_ij)^-1, taken incrementally from the previous
+  // W'_ij and O'_ij = Z_ij W'_ij (Q_ij (I + Z_ij^T Z_ij) = I makes it the same map):
+  //   W'_ij <- W'_ij + Q_ij (Wbar_j - mu'_ij - W'_ij + Z_ij^T U_i),  U_i = Obar_ij + nu_i - O'_ij.
+  // Q_ij has gain up to 1 where I + Z_ij^T Z_ij has its small eigenvalues while it shrinks the
+  // right-hand side by the largest ones (about 2e3 for correlated kernels), so a rounding of the
+  // right-hand side reaches W'_ij amplified by up to that condition number: the increment's
+  // right-hand side, and with it that rounding, is the smaller, and U_i is smaller than
+  // Obar_ij + nu_i by O'_ij.
   if (s.split_path()) {
-    // six-product split-BF16 GEMM on the tensor cores (reducing max |W'|), then the
-    // transposed FP16 split of W' that pass 2 reads
+    // six-product split-BF16 GEMM on the tensor cores added into W' (reducing max |W'|), then
+    // the transposed FP16 split of W' that pass 2 reads
     CK(launch_rhs_split3T(s.Wbar, s.muij, s.Rpart, s.cached_z() ? s.nsplit_cz : s.nsplit, s.R, s.fslots,
-                          (int)s.mpad, s.feat_of_slot, s.rT1, s.rT2, s.rT3, s.st));
+                          (int)s.mpad, s.feat_of_slot, s.rT1, s.rT2, s.rT3, s.st, s.What));
     CK(cudaMemsetAsync(s.amax + AMAX_W, 0, 4, s.st));
     CK(split_gemm(qgemm_view(s)));
     CK(launch_transpose_split_f16(s.What, s.fslots, (int)s.mpad, s.R, s.fslots * s.mpad, s.WThi, s.WTlo, s.fslots,
                                   s.mpad * s.fslots, 1.f, s.amax + AMAX_W, s.st));
   } else {
-    CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st));
-    CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 0.f, s.st, s.act()));
+    CK(launch_rhs(s.Wbar, s.muij, s.Rpart, s.nsplit, s.R, nfe, s.rhs, s.st, nullptr, 0, s.What));
+    CK(launch_gemm_f32_nn(s.gdesc, (int)nblocks, (int)smax, (int)s.mpad, 1.f, 1.f, s.st, s.act()));
   }
   if ((r = mark(h, k, 3)) != RFF_OK) return r;
   if (s.split_path()) CK(cudaMemsetAsync(s.amax + AMAX_OP, 0, 4, s.st));   // max |O'| for the exchange
@@ -1819,6 +1837,7 @@ TcView tc_view(const rff_admm_s& s) {
   v.kc = s.tc_kc;
   v.zt = s.tc_zt;
   v.cg = s.tc_cg;
+  v.v_shared = s.incremental() ? 1 : 0;
   v.st = s.st;
   return v;
 }
@@ -1872,12 +1891,24 @@ rff_status rff_admm_solve(rff_admm_t h, int32_t iters, rff_admm_stats* stats) {
       stats->primal_res = std::sqrt(a1 + a2 + a3);
       stats->dual_res = s.p.rho * std::sqrt(b1 + b2);
     }
-    // objective at Wbar: one scoring pass over the training rows into the O' buffer
-    if ((r = scores_pass(h, s.X32, s.Xhi, s.Xlo, s.nslots, s.row_of_slot, s.Op)) != RFF_OK) return r;
+    // objective at Wbar: the training rows scored in chunks into a buffer that no iteration
+    // carries over (O'_ij is: the outer form updates it, and a stochastic iteration's inactive
+    // blocks keep it): the outer form's product scratch, else the pass-1 partials
     double loss = 0, reg = 0;
-    CK(launch_loss_partials(s.p.loss, s.Y, s.Op, s.row_of_slot, s.nslots, (int)s.m, (int)s.mpad, s.partials, 1024,
-                            s.st));
-    if ((r = sum_partials(h, loss)) != RFF_OK) return r;
+    float* sc = s.outer ? s.U32 : s.Rpart;
+    const int64_t chunk = s.outer ? s.nslots
+                                  : std::min<int64_t>(s.nslots, std::max<int64_t>(SLOT, s.rpart_elems() / s.mpad / SLOT * SLOT));
+    for (int64_t r0 = 0; r0 < s.nslots; r0 += chunk) {
+      const int64_t nr = std::min(chunk, s.nslots - r0);
+      if ((r = scores_pass(h, s.X32 ? s.X32 + r0 * s.dld : nullptr, s.Xhi ? s.Xhi + r0 * s.dld : nullptr,
+                           s.Xlo ? s.Xlo + r0 * s.dld : nullptr, nr, s.row_of_slot + r0, sc)) != RFF_OK)
+        return r;
+      CK(launch_loss_partials(s.p.loss, s.Y + r0 * s.mpad, sc, s.row_of_slot + r0, nr, (int)s.m, (int)s.mpad,
+                              s.partials, 1024, s.st));
+      double part = 0;
+      if ((r = sum_partials(h, part)) != RFF_OK) return r;
+      loss += part;
+    }
     CK(launch_reg_partials(s.p.reg, s.Wbar, s.fslots * s.mpad, s.partials, 1024, s.st, s.lam_dev, (int)s.mpad));
     if ((r = sum_partials(h, reg)) != RFF_OK) return r;
     stats->objective = loss + (double)s.n * s.p.lambda * reg;
@@ -2341,7 +2372,7 @@ struct Piece {
 std::vector<Piece> state_pieces(rff_admm_s& s) {
   const size_t rowb = (size_t)s.nslots * s.mpad * 4, colb = (size_t)s.fslots * s.mpad * 4;
   std::vector<Piece> v{{s.O, rowb}, {s.Obar, rowb}, {s.nu, rowb}, {s.Op, rowb * s.C}};
-  if (s.split_path()) {
+  if (s.split_path() && !s.outer) {
     v.push_back({s.VThi, rowb / 2 * s.C});
     v.push_back({s.VTlo, rowb / 2 * s.C});
     v.push_back({s.amax, AMAX_WORDS * 4});

@@ -340,17 +340,18 @@ __global__ void k_prox_reg(int reg, const float* __restrict__ V, const float* __
 
 // Row-local exchange after pass 2 (one CTA per 32 row slots, 8 warps):
 //   S = sum_j O'_ij;  Delta = O - S;  Obar = S/(C+1) + C/(C+1) O;  nu += O - Obar
-//   V_ij = O'_ij + (Delta/(C+1) + nu)      (= Obar_ij + nu, the pass-1 operand)
+//   U_i = Delta/(C+1) + nu                 (Obar_ij + nu_i = O'_ij + U_i: the projections'
+//                                           operand, one for every column block)
 //   O <- prox_{t V}(Obar - nu)             (the loss step of the next iteration)
 // Phase 1 (a warp per row, lanes over outputs) updates Obar, nu and O and keeps
-// Delta/(C+1) + nu of the tile in shared memory; phase 2 forms V_ij tile by tile,
-// either row-major in FP32 (the SIMT path's operand) or transposed and split into a
-// scaled FP16 hi/lo pair (V^T[j][c][slot], the tensor-core operand) through a
-// shared-memory transpose, so that both the reads and the writes are coalesced.
-// The scale of that split comes before any V exists: V = O'_j + nu + 2 (O - S)/(C+1)
-// with S = sum_j O'_j, so |V| <= B = max|O'| + max|nu| + 2/(C+1) (max|O| + C max|O'|)
-// over this kernel's inputs (widened by 2^-10 for the rounding of the bound itself);
-// every CTA computes the same B.  Padding rows and columns are written as zeros.
+// Delta/(C+1) + nu of the tile in shared memory; phase 2 writes U_i, either row-major in
+// FP32 (the SIMT path's and the outer form's operand) or transposed and split into a scaled
+// FP16 hi/lo pair (U^T[c][slot], the tensor-core operand) through a shared-memory
+// transpose, so that both the reads and the writes are coalesced.  The scale of that split
+// comes before any U exists: U = nu + 2 (O - S)/(C+1) with S = sum_j O'_j, so
+// |U| <= B = max|nu| + 2/(C+1) (max|O| + C max|O'|) over this kernel's inputs (widened by
+// 2^-10 for the rounding of the bound itself); every CTA computes the same B.  Padding rows
+// and columns are written as zeros.
 constexpr int EX_ROWS = 32;
 
 template <int LOSS>
@@ -365,7 +366,8 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
     const float opm = __uint_as_float(a.amax[AMAX_OP]), om = __uint_as_float(a.amax[AMAX_O]),
                 num = __uint_as_float(a.amax[AMAX_NU]);
     const float c1 = (float)(a.C + 1);
-    const float bound = (opm + num + 2.f * (om + (float)a.C * opm) / c1) * (1.f + 0x1p-10f);
+    // U = nu^new + Delta/(C+1) = nu + 2 (O - S)/(C+1): |U| <= max|nu| + 2 (max|O| + C max|O'|)/(C+1)
+    const float bound = (num + 2.f * (om + (float)a.C * opm) / c1) * (1.f + 0x1p-10f);
     vscale = f16_scale(bound);
     if (blockIdx.x == 0 && threadIdx.x == 0 && bound > 0.f) atomicMax(&a.amax[AMAX_V], __float_as_uint(bound));
   }
@@ -446,39 +448,36 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
     }
   }
   __syncthreads();
-  // phase 2: V_ij = O'_ij + term, per column block
-  for (int j = 0; j < a.C; ++j) {
-    const float* opj = a.Op + j * jstride + p0 * mp;
-    if (!split) {
-      float* vj = a.V32 + j * jstride + p0 * mp;
-      for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
-        const bool live = a.row_ok[p0 + e / mp] >= 0 && e % mp < a.m;
-        vj[e] = live ? opj[e] + term[e] : 0.f;
-      }
-      continue;
-    }
+  // phase 2: U_i = term, once (block 0 of the V buffers): row-major FP32, or transposed and
+  // split into the scaled FP16 pair through the shared-memory tile
+  if (!split) {
+    float* v = a.V32 + p0 * mp;
     for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
-      const int r = e / mp, k = e % mp;
-      const bool live = a.row_ok[p0 + r] >= 0 && k < a.m;
-      tile[r * (mp + 1) + k] = live ? opj[e] + term[e] : 0.f;
+      const bool live = a.row_ok[p0 + e / mp] >= 0 && e % mp < a.m;
+      v[e] = live ? term[e] : 0.f;
     }
-    __syncthreads();
-    // lanes over the 32 rows, warps over columns: V^T[j][c][p0 + lane]
-    for (int c = warp; c < mp; c += 8) {
-      __half hi, lo;
-      split_f16(tile[lane * (mp + 1) + c], vscale, hi, lo);
-      const int64_t o = ((int64_t)j * mp + c) * a.nslots + p0 + lane;
-      a.VThi[o] = hi;
-      a.VTlo[o] = lo;
-    }
-    __syncthreads();
+    return;
+  }
+  for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
+    const int r = e / mp, k = e % mp;
+    const bool live = a.row_ok[p0 + r] >= 0 && k < a.m;
+    tile[r * (mp + 1) + k] = live ? term[e] : 0.f;
+  }
+  __syncthreads();
+  // lanes over the 32 rows, warps over columns: U^T[c][p0 + lane]
+  for (int c = warp; c < mp; c += 8) {
+    __half hi, lo;
+    split_f16(tile[lane * (mp + 1) + c], vscale, hi, lo);
+    const int64_t o = (int64_t)c * a.nslots + p0 + lane;
+    a.VThi[o] = hi;
+    a.VTlo[o] = lo;
   }
 }
 
 // rhs = Wbar - mu'_ij + sum of the R partials (padding feature slots zero when feat_ok is given)
 __global__ void k_rhs(const float* __restrict__ Wbar, const float* __restrict__ muij, const float* __restrict__ Rpart,
                       int nsplit, int R, int64_t nfe, const int32_t* __restrict__ feat_ok, int mpad,
-                      float* __restrict__ rhs) {
+                      const float* __restrict__ What, float* __restrict__ rhs) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)R * nfe) return;
   const int64_t e = t % nfe;
@@ -487,15 +486,18 @@ __global__ void k_rhs(const float* __restrict__ Wbar, const float* __restrict__ 
     return;
   }
   float acc = Wbar[e] - muij[t];
+  if (What) acc -= What[t];
   for (int s = 0; s < nsplit; ++s) acc += Rpart[(int64_t)s * R * nfe + t];
   rhs[t] = acc;
 }
 
-// W'_ij = rhs_ij - Z_ij^T O'_ij from the R partials of the second pass-1 product (outer
-// form of the projection); padding feature slots zero
+// W'_ij (+)= rhs_ij - Z_ij^T O'_ij from the R partials of the second pass-1 product (outer
+// form of the projection; accumulate: the incremental projection adds the increment to
+// W'_ij); padding feature slots zero
 __global__ void k_sub_partials(const float* __restrict__ rhs, const float* __restrict__ Rpart, int nsplit, int R,
                                int64_t nfe, const int32_t* __restrict__ feat_ok, int mpad, float* __restrict__ What,
-                               const uint8_t* __restrict__ bmask, const int64_t* __restrict__ col_slot, int C) {
+                               const uint8_t* __restrict__ bmask, const int64_t* __restrict__ col_slot, int C,
+                               int accumulate) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)R * nfe) return;
   const int64_t e = t % nfe;
@@ -511,7 +513,32 @@ __global__ void k_sub_partials(const float* __restrict__ rhs, const float* __res
   }
   float acc = 0.f;
   for (int s = 0; s < nsplit; ++s) acc += Rpart[(int64_t)s * R * nfe + t];
-  What[t] = rhs[t] - acc;
+  What[t] = (accumulate ? What[t] : 0.f) + (rhs[t] - acc);
+}
+
+// outer form: e_ij = O'_ij + U_i - u_ij, written over u (every block j of the same rows)
+__global__ void k_outer_residual(float* __restrict__ u, const float* __restrict__ Op, const float* __restrict__ U,
+                                 int64_t nrow_elems, int C) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nrow_elems * C) return;
+  u[t] = (Op[t] + U[t % nrow_elems]) - u[t];
+}
+
+// outer form: O'_ij += U_i + y_ij, blocks of inactive (i, j) untouched
+__global__ void k_outer_update(float* __restrict__ Op, const float* __restrict__ U, const float* __restrict__ y,
+                               int64_t nslots, int mpad, int R, int C, const int64_t* __restrict__ row_slot,
+                               const uint8_t* __restrict__ bmask) {
+  const int64_t nre = nslots * mpad;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nre * C) return;
+  const int64_t e = t % nre;
+  if (bmask) {
+    const int64_t slot = e / mpad;
+    int i = 0;
+    while (i + 1 < R && row_slot[i + 1] <= slot) ++i;
+    if (!bmask[i * C + (int)(t / nre)]) return;
+  }
+  Op[t] += U[e] + y[t];
 }
 
 // dst[c][r] = src[r][c] (src rows x cols, dst ld dld)
@@ -532,17 +559,24 @@ __global__ void k_transpose_f32(const float* __restrict__ src, int64_t rows, int
 }
 
 // Wbar = (W + sum_i W'_i)/(R+1);  mu += W - Wbar;  mu'_i += W'_i - Wbar
+// Wbar = (W + sum_i W'_ij)/(R+1), mu += W - Wbar, mu'_ij += W'_ij - Wbar.  The average and
+// the dual updates are formed in FP64 from the FP32 operands (converted exactly), and each
+// result is rounded once: the duals add up W - Wbar over the iterations, and an FP32 average
+// would hand them its rounding every time (an error that grows with the iteration count).
 __global__ void k_avg_dual(const float* __restrict__ W, const float* __restrict__ What, int R, int64_t nfe,
                            float* __restrict__ Wbar, float* __restrict__ mu, float* __restrict__ muij) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= nfe) return;
-  const float w = W[e];
-  float s = w;
-  for (int i = 0; i < R; ++i) s += What[(int64_t)i * nfe + e];
-  const float wb = s / (float)(R + 1);
-  Wbar[e] = wb;
-  mu[e] += w - wb;
-  for (int i = 0; i < R; ++i) muij[(int64_t)i * nfe + e] += What[(int64_t)i * nfe + e] - wb;
+  const double w = f32_to_f64_scaled(W[e], 0);
+  double s = w;
+  for (int i = 0; i < R; ++i) s += f32_to_f64_scaled(What[(int64_t)i * nfe + e], 0);
+  const double wb = s * (1.0 / (double)(R + 1));
+  Wbar[e] = (float)wb;
+  mu[e] = (float)(f32_to_f64_scaled(mu[e], 0) + (w - wb));
+  for (int i = 0; i < R; ++i) {
+    const int64_t t = (int64_t)i * nfe + e;
+    muij[t] = (float)(f32_to_f64_scaled(muij[t], 0) + (f32_to_f64_scaled(What[t], 0) - wb));
+  }
 }
 
 // src [b][rows][cols] float32 -> hi/lo [b][cols][dst_ld] BF16, 32 x 32 smem tiles
@@ -808,16 +842,33 @@ cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_rhs(const float* Wbar, const float* muij, const float* Rpart, int nsplit, int R, int64_t nfe,
-                       float* rhs, cudaStream_t st, const int32_t* feat_ok, int mpad) {
-  k_rhs<<<nblk((int64_t)R * nfe), 256, 0, st>>>(Wbar, muij, Rpart, nsplit, R, nfe, feat_ok, mpad > 0 ? mpad : 1, rhs);
+                       float* rhs, cudaStream_t st, const int32_t* feat_ok, int mpad, const float* What) {
+  k_rhs<<<nblk((int64_t)R * nfe), 256, 0, st>>>(Wbar, muij, Rpart, nsplit, R, nfe, feat_ok, mpad > 0 ? mpad : 1,
+                                                What, rhs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sub_partials(const float* rhs, const float* Rpart, int nsplit, int R, int64_t nfe,
                                 const int32_t* feat_ok, int mpad, float* What, cudaStream_t st, const uint8_t* bmask,
-                                const int64_t* col_slot, int C) {
+                                const int64_t* col_slot, int C, int accumulate) {
   k_sub_partials<<<nblk((int64_t)R * nfe), 256, 0, st>>>(rhs, Rpart, nsplit, R, nfe, feat_ok, mpad, What, bmask,
-                                                          col_slot, C);
+                                                          col_slot, C, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer_residual(float* u, const float* Op, const float* U, int64_t nslots, int mpad, int C,
+                                  cudaStream_t st) {
+  const int64_t n = nslots * mpad * C;
+  if (n <= 0) return cudaSuccess;
+  k_outer_residual<<<nblk(n), 256, 0, st>>>(u, Op, U, nslots * mpad, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer_update(float* Op, const float* U, const float* y, int64_t nslots, int mpad, int R, int C,
+                                const int64_t* d_row_slot, const uint8_t* bmask, cudaStream_t st) {
+  const int64_t n = nslots * mpad * C;
+  if (n <= 0) return cudaSuccess;
+  k_outer_update<<<nblk(n), 256, 0, st>>>(Op, U, y, nslots, mpad, R, C, d_row_slot, bmask);
   return cudaGetLastError();
 }
 

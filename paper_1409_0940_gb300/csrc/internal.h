@@ -206,7 +206,7 @@ cudaError_t launch_prox_reg(int reg, const float* V, const float* mu, int64_t n,
                             cudaStream_t st, const float* tau_col = nullptr, int ncol = 1);
 // words of the device array of maxima (float bits) that scale the FP16 splits
 constexpr int AMAX_V = 0, AMAX_W = 1, AMAX_WB = 2, AMAX_FLAG = 3, AMAX_OP = 4, AMAX_O = 5, AMAX_NU = 6,
-              AMAX_O_NEXT = 7, AMAX_NU_NEXT = 8, AMAX_WORDS = 16;
+              AMAX_O_NEXT = 7, AMAX_NU_NEXT = 8, AMAX_OINC = 9, AMAX_WORDS = 16;
 
 struct RowEpiArgs {
   const float* Op;      // C x slots x mpad
@@ -214,9 +214,11 @@ struct RowEpiArgs {
   float* Obar;
   float* nu;
   const float* Y;
-  float* V32;           // C x slots x mpad (FP32 path), or null
-  // tensor-core path: V^T written as its scaled FP16 hi/lo split (C x mpad x slots), the scale
-  // from an upper bound of |V| built from the maxima in amax (float bits): amax[AMAX_OP] =
+  // U_i = Delta_i/(C+1) + nu_i (Obar_ij + nu_i = O'_ij + U_i), one operand for every column
+  // block: into V32 (slots x mpad, FP32) when given, else as the tensor-core operand below
+  float* V32;
+  // U^T written as its scaled FP16 hi/lo split (mpad x slots), the scale from an upper bound
+  // of |U| built from the maxima in amax (float bits): amax[AMAX_OP] =
   // max |O'|, amax[AMAX_O] / amax[AMAX_NU] = max |O|, |nu| of this kernel's inputs; the kernel
   // stores the bound in amax[AMAX_V] and reduces max |O|, |nu| of its outputs into
   // amax[AMAX_O_NEXT], amax[AMAX_NU_NEXT]
@@ -229,13 +231,26 @@ struct RowEpiArgs {
   float t_loss;
 };
 cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st);
+// rhs_ij = Wbar_j - mu'_ij (- W'_ij when What is given: the incremental projection) + sum
+// of the R partials
 cudaError_t launch_rhs(const float* Wbar, const float* muij, const float* Rpart, int nsplit, int R, int64_t nfe,
-                       float* rhs, cudaStream_t st, const int32_t* feat_ok = nullptr, int mpad = 0);
+                       float* rhs, cudaStream_t st, const int32_t* feat_ok = nullptr, int mpad = 0,
+                       const float* What = nullptr);
 // W' = rhs - sum of the nsplit partials, padding feature slots zero (outer form); with
 // bmask (R x C, col_slot: first slot of each of the C column blocks) only active blocks
+// W'_ij (+)= rhs_ij - sum of the R partials (accumulate: added to W'_ij, the incremental
+// projection); an inactive block of a stochastic iteration keeps its W'_ij
 cudaError_t launch_sub_partials(const float* rhs, const float* Rpart, int nsplit, int R, int64_t nfe,
                                 const int32_t* feat_ok, int mpad, float* What, cudaStream_t st,
-                                const uint8_t* bmask = nullptr, const int64_t* col_slot = nullptr, int C = 1);
+                                const uint8_t* bmask = nullptr, const int64_t* col_slot = nullptr, int C = 1,
+                                int accumulate = 0);
+// Outer form of the projection (C x slots x mpad blocks, U_i = block 0 of U):
+//   e_ij = O'_ij + U_i - u_ij (into u, in place);
+cudaError_t launch_outer_residual(float* u, const float* Op, const float* U, int64_t nslots, int mpad, int C,
+                                  cudaStream_t st);
+//   O'_ij += U_i + y_ij for the active blocks (bmask per row block i, column block j; null: all)
+cudaError_t launch_outer_update(float* Op, const float* U, const float* y, int64_t nslots, int mpad, int R, int C,
+                                const int64_t* d_row_slot, const uint8_t* bmask, cudaStream_t st);
 // dst[c][r] = src[r][c]
 cudaError_t launch_transpose_f32(const float* src, int64_t rows, int64_t cols, float* dst, int64_t dld,
                                  cudaStream_t st);

@@ -54,6 +54,7 @@ struct QArgs {
   const unsigned* b_amax;
   unsigned* amax;
   const uint8_t* bmask;      // active blocks of a stochastic iteration, or null
+  int accumulate;            // 1: out += result (amax of the sum)
   int* err;
   long long timeout_cycles;
 };
@@ -196,12 +197,17 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
         tmem_wait_ld();
         float x[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          x[t] = sc * (__uint_as_float(r8[t]) + __uint_as_float(s8[t]));
-          mx = fmaxf(mx, fabsf(x[t]));
-        }
+        for (int t = 0; t < 8; ++t) x[t] = sc * (__uint_as_float(r8[t]) + __uint_as_float(s8[t]));
         float4* dst = reinterpret_cast<float4*>(orow_p + c);
-        if (RFF_SPAN(job.out + (int64_t)row * a.mpad + c, 8, a.out_elems)) {
+        const bool in = RFF_SPAN(job.out + (int64_t)row * a.mpad + c, 8, a.out_elems);
+        if (a.accumulate && in) {
+          const float4 p0 = dst[0], p1 = dst[1];
+          x[0] += p0.x; x[1] += p0.y; x[2] += p0.z; x[3] += p0.w;
+          x[4] += p1.x; x[5] += p1.y; x[6] += p1.z; x[7] += p1.w;
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) mx = fmaxf(mx, fabsf(x[t]));
+        if (in) {
           dst[0] = make_float4(x[0], x[1], x[2], x[3]);
           dst[1] = make_float4(x[4], x[5], x[6], x[7]);
         }
@@ -224,8 +230,9 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
 // ---- the right-hand side, split three ways and transposed: rT_t[i][c][slot]
 __global__ void k_rhs_split3T(const float* __restrict__ Wbar, const float* __restrict__ muij,
                               const float* __restrict__ Rpart, int nsplit, int R, int64_t fslots, int mpad,
-                              const int32_t* __restrict__ feat_ok, __nv_bfloat16* __restrict__ r1,
-                              __nv_bfloat16* __restrict__ r2, __nv_bfloat16* __restrict__ r3) {
+                              const int32_t* __restrict__ feat_ok, const float* __restrict__ What,
+                              __nv_bfloat16* __restrict__ r1, __nv_bfloat16* __restrict__ r2,
+                              __nv_bfloat16* __restrict__ r3) {
   __shared__ float tile[32][33];
   const int i = blockIdx.z;
   const int64_t p0 = (int64_t)blockIdx.x * 32;
@@ -239,6 +246,7 @@ __global__ void k_rhs_split3T(const float* __restrict__ Wbar, const float* __res
     if (p < fslots && c < mpad && feat_ok[p] >= 0) {
       const int64_t e = p * mpad + c, t = (int64_t)i * nfe + e;
       v = Wbar[e] - muij[t];
+      if (What) v -= What[t];
       for (int sp = 0; sp < nsplit; ++sp)
         if (RFF_IN((int64_t)sp * R * nfe + t, (int64_t)nsplit * R * nfe)) v += Rpart[(int64_t)sp * R * nfe + t];
     }
@@ -304,9 +312,9 @@ cudaError_t launch_split3_q(const double* Q, int s, int64_t ldq, int64_t qrow, _
 
 cudaError_t launch_rhs_split3T(const float* Wbar, const float* muij, const float* Rpart, int nsplit, int R,
                                int64_t fslots, int mpad, const int32_t* feat_ok, __nv_bfloat16* r1,
-                               __nv_bfloat16* r2, __nv_bfloat16* r3, cudaStream_t st) {
+                               __nv_bfloat16* r2, __nv_bfloat16* r3, cudaStream_t st, const float* What) {
   dim3 grid((unsigned)ceil_div(fslots, 32), (unsigned)ceil_div(mpad, 32), (unsigned)R);
-  k_rhs_split3T<<<grid, 256, 0, st>>>(Wbar, muij, Rpart, nsplit, R, fslots, mpad, feat_ok, r1, r2, r3);
+  k_rhs_split3T<<<grid, 256, 0, st>>>(Wbar, muij, Rpart, nsplit, R, fslots, mpad, feat_ok, What, r1, r2, r3);
   return cudaGetLastError();
 }
 
@@ -342,6 +350,7 @@ cudaError_t split_gemm(const SgView& v) {
   a.b_amax = v.b_amax;
   a.amax = v.amax;
   a.bmask = v.bmask;
+  a.accumulate = v.accumulate;
   a.err = tc_error_ptr();
   if (!a.err) return cudaErrorMemoryAllocation;
   a.timeout_cycles = 4000000000LL;   // about two seconds at the boost clock

@@ -167,8 +167,13 @@ __device__ __forceinline__ void store_acc(float (&acc2)[8][MQ], float* __restric
 // Pass 2 / predict: one CTA per 128 data rows; runs over the feature slots of
 // every column block.  per_block: write O'_ij at the end of each block j (to
 // out + j * out_block_stride); else accumulate over all blocks and write once.
+// For m_pad <= 64 each 64-feature tile's FP32 sum is folded into a float-float
+// accumulator (TwoSum): a 4096-feature block then carries the error of one 64-term
+// sum, not of a 4096-term one (the outer form's W' = c + Z^T P (V - Z c) takes the
+// rounding of Z c with gain ~1 relative to |Z c|, which exceeds |W'|).
 template <int MQ>
 __global__ void __launch_bounds__(NT, 1) k_pass2_simt(PassArgs p) {
+  constexpr bool COMP = MQ <= 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SimtSmem& sm = *reinterpret_cast<SimtSmem*>(smem_raw);
   float* Ms = reinterpret_cast<float*>(smem_raw + sizeof(SimtSmem));
@@ -180,10 +185,17 @@ __global__ void __launch_bounds__(NT, 1) k_pass2_simt(PassArgs p) {
   const float* M = p.M + rb * p.m_block_stride;
   if (!RFF_SPAN(a0, BM, p.x_rows)) return;
   float acc2[8][MQ];
+  float shi[COMP ? 8 : 1][COMP ? MQ : 1], slo[COMP ? 8 : 1][COMP ? MQ : 1];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int q = 0; q < MQ; ++q) acc2[i][q] = 0.f;
+  if (COMP) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int q = 0; q < MQ; ++q) shi[COMP ? i : 0][COMP ? q : 0] = slo[COMP ? i : 0][COMP ? q : 0] = 0.f;
+  }
   for (int j = 0; j < p.C; ++j) {
     if (act && !act[j]) continue;
     const int64_t f0 = p.col_slot[j], f1 = f0 + p.col_size[j];
@@ -194,9 +206,39 @@ __global__ void __launch_bounds__(NT, 1) k_pass2_simt(PassArgs p) {
       load_M(Ms, M, b0, p.mpad);
       __syncthreads();
       chain<MQ>(sm, Ms, p.mpad, acc2);
+      if (COMP) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int q = 0; q < MQ; ++q) {
+            float& h = shi[COMP ? i : 0][COMP ? q : 0];
+            float& l = slo[COMP ? i : 0][COMP ? q : 0];
+            two_sum_into(h, l, acc2[i][q]);
+            acc2[i][q] = 0.f;
+          }
+      }
+    }
+    if (COMP) {   // the block's sum back into acc2 for the store (or the next block)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int q = 0; q < MQ; ++q) {
+          float& h = shi[COMP ? i : 0][COMP ? q : 0];
+          float& l = slo[COMP ? i : 0][COMP ? q : 0];
+          if (p.per_block) {
+            acc2[i][q] = h + l;
+            h = l = 0.f;
+          }
+        }
     }
     if (p.per_block && RFF_SPAN(j * p.out_block_stride + a0 * p.mpad, BM * p.mpad, p.out_elems))
       store_acc<MQ>(acc2, p.out + j * p.out_block_stride, a0, p.mpad);
+  }
+  if (COMP && !p.per_block) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int q = 0; q < MQ; ++q) acc2[i][q] = shi[COMP ? i : 0][COMP ? q : 0] + slo[COMP ? i : 0][COMP ? q : 0];
   }
   if (!p.per_block && RFF_SPAN(a0 * p.mpad, BM * p.mpad, p.out_elems)) store_acc<MQ>(acc2, p.out, a0, p.mpad);
 }

@@ -129,6 +129,7 @@ struct TcArgs {
   float zt_scale;                           // its power-of-two scale
   int bias_in_mma;                          // 1: b already in the product (column of ones)
   const uint8_t* bmask;                     // passes 1 and 2: active blocks (R x C), or null
+  int m_shared;                             // pass 1: the chained operand's rows 0..m_pad serve every block
   int* err;
   long long timeout_cycles;
 };
@@ -325,7 +326,7 @@ __device__ void plan_work(const TcArgs& a, SH& sh, uint32_t rank, const CtaPos& 
     const int i = pos.y, split = pos.z;
     const int64_t nrt = ceil_div(a.row_size[i], 128);
     const int64_t t0 = split * nrt / a.nsplit, t1 = (split + 1) * nrt / a.nsplit;
-    m_y = j * a.mpad;
+    m_y = a.m_shared ? 0 : j * a.mpad;
     const bool active = !a.bmask || a.bmask[i * a.C + j];
     // a pair works whenever its first tile is real; a lone phantom CTA has nothing to do
     if (active && (CG == 2 || !phantom) && t1 > t0) {
@@ -1413,6 +1414,7 @@ cudaError_t args_pass1(const TcView& v, float* Rpart, TcArgs& a, dim3& grid) {
   a.out_block_stride = v.fslots * v.mpad;
   a.m_amax = v.v_amax;
   a.bmask = v.bmask;
+  a.m_shared = v.v_shared;
   const int cg = view_cg(v), brows = view_brows(v), mrows = view_mrows(v);
   if ((e = make_map(&a.tA_hi, v.Ghi, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;
   if ((e = make_map(&a.tA_lo, v.Glo, v.dld, v.fslots, v.dld, 128, view_kc(v))) != cudaSuccess) return e;

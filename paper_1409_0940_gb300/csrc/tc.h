@@ -30,6 +30,7 @@ struct TcView {
                                     //    shared memory; m_pad <= 192; one CTA)
   int cg;                           // 2: CTA pairs (tcgen05.mma.cta_group::2, Z in TMEM), else one CTA
   const uint8_t* bmask;             // device, R x C: active blocks of a stochastic iteration, or null
+  int v_shared;                     // pass 1: one chained operand for every column block (rows 0..m_pad)
   int64_t row_tiles;                // pass 2: 128-row tiles taken from the first (0 = all of them)
   cudaStream_t st;
 };
@@ -95,17 +96,18 @@ struct SgView {
   size_t smem_budget;                  // ring bytes per CTA (0 = the largest; smaller lets 2 CTAs share an SM)
   int two_acc;                         // 1: hi.hi products in their own TMEM accumulator (twice the columns)
   const uint8_t* bmask;                // device, R x C: a job of an inactive block does nothing; or null
+  int accumulate;                      // 1: out += the product (amax of the sum)
   cudaStream_t st;
 };
 cudaError_t split_gemm(const SgView& v);
 // Q (s x s, row-major float64) split three ways into rows [qrow, qrow+s) of q1..q3 (ld ldq).
 cudaError_t launch_split3_q(const double* Q, int s, int64_t ldq, int64_t qrow, __nv_bfloat16* q1,
                             __nv_bfloat16* q2, __nv_bfloat16* q3, cudaStream_t st);
-// rhs_ij = Wbar_j - mu'_ij + sum of the R partials, split three ways and transposed
-// to [R][mpad][fslots]; padding feature slots are written as zero.
+// rhs_ij = Wbar_j - mu'_ij (- W'_ij when What is given) + sum of the R partials, split three
+// ways and transposed to [R][mpad][fslots]; padding feature slots are written as zero.
 cudaError_t launch_rhs_split3T(const float* Wbar, const float* muij, const float* Rpart, int nsplit, int R,
                                int64_t fslots, int mpad, const int32_t* feat_ok, __nv_bfloat16* r1,
-                               __nv_bfloat16* r2, __nv_bfloat16* r3, cudaStream_t st);
+                               __nv_bfloat16* r2, __nv_bfloat16* r3, cudaStream_t st, const float* What = nullptr);
 
 // helpers shared by the tensor-core kernels
 cudaError_t tc_make_map_bf16(CUtensorMap* m, const void* ptr, int64_t cols, int64_t rows, int64_t ld, int box_rows,

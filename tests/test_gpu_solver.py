@@ -217,6 +217,32 @@ def test_split_path_query_range(rff, prec):
     f.close()
 
 
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("shape", ["gram", "outer", "stochastic"])
+def test_solve_in_pieces_with_statistics_is_one_solve(rff, prec, shape):
+    """The statistics a solve call reports (residuals, the objective's scoring pass) leave the
+    iterates alone: 10 iterations in calls of 3, 3 and 4 are those of one call, bit for bit,
+    in the Gram form, in the outer form (whose O'_ij carries over from one iteration to the
+    next) and in a stochastic solve (whose inactive blocks keep O'_ij)."""
+    if prec == "cached_z" and shape == "outer":
+        pytest.skip("the cached-Z precision takes the Gram form only")
+    X, Y = synth.multiclass(n=640, d=9, m=3, seed=6)
+    D = 2048 if shape == "outer" else 256
+    kw = dict(prec=prec, loss="hinge", reg="l2", lam=1e-3, sigma=2.0, D=D, R=2, C=2, seed=1, m=3)
+    a = rff.Solver(**kw)
+    b = rff.Solver(**kw)
+    for s in (a, b):
+        s.set_data(X, Y)
+        if shape == "stochastic":
+            s.set_block_fraction(0.5)
+    a.solve(10)
+    for k in (3, 3, 4):
+        b.solve(k)
+    assert np.array_equal(a.weights(), b.weights())
+    a.close()
+    b.close()
+
+
 def test_set_stream_mid_solve_keeps_results(rff):
     X, Y = synth.multiclass(n=700, d=9, m=3, seed=6)
     kw = dict(prec="split_bf16", loss="hinge", reg="l2", lam=1e-3, sigma=2.0, D=256, R=2, C=2, seed=1, m=3)

@@ -48,6 +48,20 @@ def test_reorganised_equals_equation_form():
             assert np.abs(a[key] - b[key]).max() < 1e-12 * scale, (loss, key)
 
 
+def test_incremental_equals_equation_form():
+    """The projection taken from the previous (What_ij, O_ij) gives the same iterates, in the
+    Gram form (s_j <= n_i) and in the outer form (n_i < s_j)."""
+    X, Y = synth.multiclass(n=600, d=7, m=4, seed=5)
+    for D, R, C in [(80, 3, 4), (600, 3, 2)]:
+        for loss in ["squared", "hinge", "multinomial"]:
+            p = admm.Problem(X, Y, loss, "l2", lam=1e-3, sigma=3.0, rho=0.5, D=D, R=R, C=C, seed=9)
+            a = admm.admm(p, 25, variant="equation")
+            b = admm.admm(p, 25, variant="incremental")
+            for key in ["Wbar", "O", "Obar", "nu", "mu"]:
+                scale = max(1.0, np.abs(a[key]).max())
+                assert np.abs(a[key] - b[key]).max() < 1e-12 * scale, (D, loss, key)
+
+
 def test_algorithm1_as_printed_stalls(ridge_problem):
     """Reading 1: the printed pseudo-code (no Z^T nu, stale Wbar) does not reach the minimiser."""
     X, Y = ridge_problem
@@ -189,6 +203,15 @@ def test_stochastic_equation_equals_reorganised():
     p = admm.Problem(X, Y, "hinge", "l2", lam=1e-3, sigma=2.0, rho=1.0, D=120, R=3, C=2, seed=5)
     a = admm.admm(p, 40, variant="equation", block_fraction=0.5)
     b = admm.admm(p, 40, variant="reorganised", block_fraction=0.5)
+    assert np.abs(a["Wbar"] - b["Wbar"]).max() < 1e-12 * max(1.0, np.abs(a["Wbar"]).max())
+
+
+def test_stochastic_equation_equals_incremental():
+    """An inactive block keeps What_ij and O_ij, from which its next projection starts."""
+    X, Y = synth.multiclass(n=300, d=5, m=3, seed=12)
+    p = admm.Problem(X, Y, "hinge", "l2", lam=1e-3, sigma=2.0, rho=1.0, D=120, R=3, C=2, seed=5)
+    a = admm.admm(p, 40, variant="equation", block_fraction=0.5)
+    b = admm.admm(p, 40, variant="incremental", block_fraction=0.5)
     assert np.abs(a["Wbar"] - b["Wbar"]).max() < 1e-12 * max(1.0, np.abs(a["Wbar"]).max())
 
 
