@@ -43,6 +43,7 @@ constexpr int OZ_BITS = 7;                 // bits per slice
 constexpr int OZ_K = 64;                   // K of every update
 constexpr int OZ_BM = 128, OZ_BN = 32;     // output tile (rows of A, columns of B)
 constexpr int OZ_ITEM_COLS = 512;          // columns of one work item (16 tiles)
+constexpr int OZ_ITEMS_PER_CTA = 2;        // work items a CTA takes in turn (at least one CTA per SM)
 constexpr uint32_t OZ_ATILE = OZ_BM * OZ_K * 2;                // 16 KB: one slice of a 128-row block
 constexpr uint32_t OZ_BTILE = OZ_BN * OZ_K * 2;                // 4 KB: one slice of a 32-column tile
 constexpr uint32_t OZ_ACOLS = OZ_S * OZ_BN;                    // TMEM columns of one accumulator set
@@ -191,7 +192,7 @@ __device__ __forceinline__ void oz_combine(const uint32_t (&g)[OZ_S][4], int j, 
   hi = s;
 }
 
-// Persistent: one CTA per SM takes work items in turn.  Per item warp 0 copies the seven A
+// Each CTA (one per SM at a time: the slices fill shared memory) takes a few work items in turn.  Per item warp 0 copies the seven A
 // slices of the row block once and the seven B slices of each 32-column tile into a double
 // buffer (TMA, 128-byte swizzle); one thread of warp 1 issues the 28 x 4 products of a tile
 // into one of two TMEM accumulator sets (seven 128 x 32 accumulators each); warps 2..17 read a
@@ -655,7 +656,11 @@ cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, v
     a.neg = neg;
     a.beta = beta;
     a.lower = lower;
-    k_oz_rows<<<(unsigned)std::min<int64_t>(i1 - i0, nsm), OZ_THREADS, OZ_SMEM_BYTES, st>>>(a);
+    // at most OZ_ITEMS_PER_CTA items per CTA: a CTA fills its SM's shared memory, so other
+    // kernels (a server's scoring on a high-priority stream) start only when one finishes
+    const int64_t ni = i1 - i0;
+    const int64_t grid = std::min<int64_t>(ni, std::max<int64_t>(nsm, ceil_div(ni, OZ_ITEMS_PER_CTA)));
+    k_oz_rows<<<(unsigned)grid, OZ_THREADS, OZ_SMEM_BYTES, st>>>(a);
     return cudaGetLastError();
   };
   for (int k = 0; k < nb; ++k) {
