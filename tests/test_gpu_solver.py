@@ -56,7 +56,7 @@ def test_ridge_1x1_matches_oracle_and_closed_form(rff, ridge_ref, prec):
     Xq = np.random.default_rng(5).random((333, 16)).astype(np.float32)
     got = s.predict(Xq)
     ref = p.predict(Xq, out["Wbar"])
-    assert np.abs(got - ref).max() < tol * np.abs(ref).max() * 10
+    assert np.abs(got - ref).max() < tol * np.abs(ref).max()
     s.close()
 
 
@@ -279,11 +279,11 @@ def test_outer_form_config3_shape(rff, config3_shape, prec):
     X, Y, kw, W_ref, p = config3_shape
     s, st, W = run_gpu(rff, X, Y, 10, prec, seed=7, m=10, **kw)
     assert rel(W, W_ref) < PRECS[prec], rel(W, W_ref)
-    # ten iterations from zero with lambda = 1e-6 leave the hinge objective far from its
-    # minimum and first-order sensitive to the weights, so the reported objective is checked
-    # against the oracle's objective at the GPU's own weights
+    # the reported objective against the oracle's at the GPU's own weights and at the oracle's
     f_at_W = p.objective(np.asarray(W, np.float64))
     assert abs(st["objective"] - f_at_W) < PRECS[prec] * abs(f_at_W)
+    f_ref = p.objective(W_ref)
+    assert abs(st["objective"] - f_ref) < PRECS[prec] * abs(f_ref), abs(st["objective"] - f_ref) / abs(f_ref)
     s.close()
 
 
