@@ -794,11 +794,11 @@ rff_status rff_admm_set_data_csr(rff_admm_t h, const int64_t* indptr, const int3
 // ------------------------------------------------------------------ set-up
 namespace {
 
-// Tile-shape autotuner of the tensor-core passes: times pass 1 + pass 2 for each
-// ring geometry (K chunk 64 or 32; Z tile in shared or tensor memory; one CTA or a CTA
-// pair per MMA) on the handle's own data, restricted to the first row block (a quarter
-// of the work on a 4 x 4 grid: still several waves of both passes), and keeps the
-// fastest.  All geometries issue the same products in the same order for every output
+// Tile-shape autotuner of the tensor-core passes: times pass 2 for each ring geometry
+// (K chunk 64 or 32; Z tile in shared or tensor memory; the wide products) on the handle's
+// own data, over the first 128-row tiles of the first row block (about two waves of work
+// items; pass 1 runs the same X.G tiles and chained products and ranks the geometries the
+// same way), and keeps the fastest.  All geometries issue the same products in the same order for every output
 // element, so the choice changes speed, never results (a run is reproducible whatever
 // the timing).  The passes only write their scratch outputs (R partials, O'), which
 // every iteration recomputes.
@@ -823,14 +823,16 @@ rff_status autotune(rff_admm_t h) {
                    "RFF_TC_GEOMETRY must be \"kc,zt\" or \"kc,zt,cg\" with kc 64 or 32, zt 0, 1, 2 (m_pad <= "
                    "128) or 3 (m_pad <= 192), cg 1 or 2 (2 needs zt 1 or 2)");
   }
-  std::vector<int> splits{s.nsplit};
-  if (s.nsplit_max != s.nsplit) splits.push_back(s.nsplit_max);
+  std::vector<int> splits{s.nsplit};   // pass 1's row splits are not timed: kept as chosen
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_kc = 64, best_ns = s.nsplit, best_zt = 0, best_cg = 1;
   bool warm = false;
+  int nsm = 148, dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   // (Z in smem), (Z in TMEM), the wide N = 256 geometry (m_pad <= 192), and with m_pad <= 128
   // the double-buffered acc1 beside Z in TMEM.  The CTA-pair geometries are selectable through
   // RFF_TC_GEOMETRY but not timed here: they measured 6-15 % slower on every workload tried
@@ -848,10 +850,9 @@ rff_status autotune(rff_admm_t h) {
       float ms = 0.f;
       TcView tv = tc_view(s);
       tv.R = 1;
-      tv.row_tiles = ceil_div(s.row_size[0], 128);
+      tv.row_tiles = std::min<int64_t>(ceil_div(s.row_size[0], 128), std::max<int64_t>(16, ceil_div(2 * nsm, s.C)));
       for (int rep = warm ? 1 : 0; rep < 2; ++rep) {   // one untimed run warms caches and descriptors
         CK(cudaEventRecord(e0, s.st));
-        CK(tc_pass1(tv, s.Rpart));
         CK(tc_pass2(tv, s.WThi, s.WTlo, s.mpad * s.fslots, s.Op, 1, s.amax + AMAX_W));
         CK(cudaEventRecord(e1, s.st));
         CK(cudaEventSynchronize(e1));
