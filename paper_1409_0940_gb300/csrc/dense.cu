@@ -397,6 +397,8 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const DiagJob* __restrict__ 
   const int bs = min(64, jb.s - kcol);
   __shared__ double L[64][65];
   __shared__ double Li[64][65];
+  __shared__ double rinv[64];   // reciprocals of the pivots (one FP64 division each: this part's
+                                // FP64 division is a long sequence on its 1/64-rate pipe)
   __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
@@ -413,10 +415,11 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const DiagJob* __restrict__ 
         d = 1.0;
       }
       L[c][c] = sqrt(d);
+      rinv[c] = 1.0 / L[c][c];
     }
     __syncthreads();
-    const double piv = L[c][c];
-    for (int r = c + 1 + tid; r < bs; r += 256) L[r][c] /= piv;
+    const double ri = rinv[c];
+    for (int r = c + 1 + tid; r < bs; r += 256) L[r][c] *= ri;
     __syncthreads();
     const int w = bs - c - 1;
     for (int t = tid; t < w * w; t += 256) {
@@ -433,7 +436,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const DiagJob* __restrict__ 
       if (r >= q && r < bs) {
         double sacc = (r == q) ? 1.0 : 0.0;
         for (int t = q; t < r; ++t) sacc -= L[r][t] * Li[t][q];
-        v = sacc / L[r][r];
+        v = sacc * rinv[r];
       }
       Li[r][q] = v;
     }
