@@ -448,7 +448,7 @@ int64_t tc_gram_tiles(int64_t smax, std::vector<int2>* out = nullptr) {
 size_t tc_gram_bytes(int64_t chunk_rows, int64_t smax) {
   const int64_t spad = round_up(smax, 256), kpad = round_up(chunk_rows, GRAM_KCH), nt = tc_gram_tiles(smax);
   return round_up((size_t)spad * kpad * 2, 256) * 2 + (size_t)GRAM_GROUP * nt * 128 * 256 * 4 +
-         round_up((size_t)nt * sizeof(int2), 256) + round_up((size_t)GRAM_GROUP * nt * sizeof(SgJob), 256) + 1024;
+         round_up((size_t)nt * sizeof(int2), 256) + round_up((size_t)(kpad / GRAM_KCH) * nt * sizeof(SgJob), 256) + 1024;
 }
 
 bool tc_gram(const rff_admm_s& s) { return s.split_path() && !s.outer; }
@@ -1043,24 +1043,26 @@ rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t
   }
   CK(cudaMemcpyAsync(dtiles, tiles.data(), nt * sizeof(int2), cudaMemcpyHostToDevice, s.st));
   const int64_t npieces = kn / GRAM_KCH;
+  // every group's job table in one copy: stream order alone keeps P and the tables of one
+  // group from being overwritten before its reduction has read them
   std::vector<SgJob> jobs;
+  jobs.reserve((size_t)npieces * nt);
+  for (int64_t k = 0; k < npieces; ++k)
+    for (int64_t t = 0; t < nt; ++t) {
+      SgJob jb{};
+      jb.a_row = tiles[t].x;
+      jb.a_k0 = (int32_t)(k * GRAM_KCH);
+      jb.b_row = tiles[t].y;
+      jb.b_k0 = jb.a_k0;
+      jb.nk = GRAM_KCH / 32;
+      jb.blk = 0;
+      jb.out = ((k % GRAM_GROUP) * nt + t) * 128 * 256;
+      jobs.push_back(jb);
+    }
+  // the host vector is read by the copy: pageable memory is staged before the call returns
+  CK(cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(SgJob), cudaMemcpyHostToDevice, s.st));
   for (int64_t g0 = 0; g0 < npieces; g0 += GRAM_GROUP) {
     const int64_t g1 = std::min<int64_t>(npieces, g0 + GRAM_GROUP);
-    jobs.clear();
-    for (int64_t k = g0; k < g1; ++k)
-      for (int64_t t = 0; t < nt; ++t) {
-        SgJob jb{};
-        jb.a_row = tiles[t].x;
-        jb.a_k0 = (int32_t)(k * GRAM_KCH);
-        jb.b_row = tiles[t].y;
-        jb.b_k0 = jb.a_k0;
-        jb.nk = GRAM_KCH / 32;
-        jb.blk = 0;
-        jb.out = ((k - g0) * nt + t) * 128 * 256;
-        jobs.push_back(jb);
-      }
-    // the host vector is read by the copy: pageable memory is staged before the call returns
-    CK(cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(SgJob), cudaMemcpyHostToDevice, s.st));
     SgView v{};
     v.A[0] = hi;
     v.A[1] = lo;
@@ -1072,8 +1074,8 @@ rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t
     v.b_cols = kn;
     v.na = v.nb = 2;
     v.f16 = 1;
-    v.jobs = djobs;
-    v.njobs = (int)jobs.size();
+    v.jobs = djobs + g0 * nt;
+    v.njobs = (int)((g1 - g0) * nt);
     v.mpad = 256;
     v.out = P;
     v.out_elems = (int64_t)GRAM_GROUP * tc_gram_tiles(smax) * 128 * 256;
@@ -1082,7 +1084,6 @@ rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t
     v.st = s.st;
     CK(split_gemm(v));
     CK(launch_gram_reduce(P, (int)(g1 - g0), (int)nt, dtiles, sj, H, sj, s.st));
-    CK(cudaStreamSynchronize(s.st));   // jobs and P are reused by the next group
   }
   return RFF_OK;
 }
