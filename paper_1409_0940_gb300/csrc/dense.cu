@@ -389,8 +389,13 @@ __global__ void __launch_bounds__(256) k_gram_tile(const float* __restrict__ Z, 
 // (bs = min(64, s - kcol)) in shared memory, write L back (upper part zeroed) and
 // the inverse of L into inv (64 x 64, zero padded).  info = column+1 of the first
 // non-positive pivot (the pivot is replaced by 1 so the factorisation finishes).
-
-
+// Step c of the right-looking factorisation also takes step c of the forward substitution
+// L X = I (X = L^-1, built in place of the identity: row c scaled by 1 / L_cc, then
+// X_rq -= L_rc X_cq for r > c, q <= c), so the inverse needs no sweep of its own.  The
+// trailing update walks only the pairs (r, q), c < q <= r, in an order where step c's pairs
+// are a prefix of one table (pair (r, q) at r'(r'+1)/2 + q', r' = 63 - q, q' = 63 - r): no lane
+// of a warp idles on this part's narrow FP64 pipe.  Every element sees the same operations in
+// the same order as the column-by-column forms of both sweeps.
 __global__ void __launch_bounds__(256) k_potrf_diag(const DiagJob* __restrict__ jobs, int kcol) {
   const DiagJob jb = jobs[blockIdx.x];
   if (kcol >= jb.s) return;
@@ -399,12 +404,15 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const DiagJob* __restrict__ 
   __shared__ double Li[64][65];
   __shared__ double rinv[64];   // reciprocals of the pivots (one FP64 division each: this part's
                                 // FP64 division is a long sequence on its 1/64-rate pipe)
+  __shared__ uint16_t pairs[63 * 64 / 2];   // (r' << 8) | q', 0 <= q' <= r' < 63
   __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
   for (int t = tid; t < 64 * 64; t += 256) {
     const int r = t / 64, c = t % 64;
     L[r][c] = (r < bs && c < bs) ? jb.A[(int64_t)(kcol + r) * jb.ld + kcol + c] : (r == c ? 1.0 : 0.0);
+    Li[r][c] = r == c ? 1.0 : 0.0;
+    if (r < 63 && c <= r) pairs[r * (r + 1) / 2 + c] = (uint16_t)((r << 8) | c);
   }
   __syncthreads();
   for (int c = 0; c < bs; ++c) {
@@ -419,33 +427,29 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const DiagJob* __restrict__ 
     }
     __syncthreads();
     const double ri = rinv[c];
-    for (int r = c + 1 + tid; r < bs; r += 256) L[r][c] *= ri;
+    if (tid < 64) {
+      if (c + 1 + tid < 64) L[c + 1 + tid][c] *= ri;
+    } else if (tid < 128) {
+      if (tid - 64 <= c) Li[c][tid - 64] *= ri;
+    }
     __syncthreads();
-    const int w = bs - c - 1;
-    for (int t = tid; t < w * w; t += 256) {
-      const int r = c + 1 + t / w, q = c + 1 + t % w;
-      if (q <= r) L[r][q] -= L[r][c] * L[q][c];
+    const int w = 63 - c, cw = c + 1;
+    for (int p = tid; p < w * (w + 1) / 2; p += 256) {
+      const uint32_t v = pairs[p];
+      const int r = 63 - (int)(v & 0xffu), q = 63 - (int)(v >> 8);
+      L[r][q] -= L[r][c] * L[q][c];
+    }
+    for (int t = tid; t < w * cw; t += 256) {
+      const int r = c + 1 + t / cw, q = t % cw;
+      Li[r][q] -= L[r][c] * Li[c][q];
     }
     __syncthreads();
   }
-  // inverse of the lower-triangular L, one column per thread
-  if (tid < 64) {
-    const int q = tid;
-    for (int r = 0; r < 64; ++r) {
-      double v = 0.0;
-      if (r >= q && r < bs) {
-        double sacc = (r == q) ? 1.0 : 0.0;
-        for (int t = q; t < r; ++t) sacc -= L[r][t] * Li[t][q];
-        v = sacc * rinv[r];
-      }
-      Li[r][q] = v;
-    }
-  }
-  __syncthreads();
   for (int t = tid; t < 64 * 64; t += 256) {
     const int r = t / 64, c = t % 64;
-    if (r < bs && c < bs) jb.A[(int64_t)(kcol + r) * jb.ld + kcol + c] = (c <= r) ? L[r][c] : 0.0;
-    jb.inv[t] = Li[r][c];
+    const bool in = r < bs && c < bs;
+    if (in) jb.A[(int64_t)(kcol + r) * jb.ld + kcol + c] = (c <= r) ? L[r][c] : 0.0;
+    jb.inv[t] = in ? Li[r][c] : 0.0;
   }
   if (tid == 0 && bad && jb.info && *jb.info == 0) *jb.info = bad;
 }
