@@ -5,18 +5,22 @@
 //
 // Every update of the factorisation is D = beta C + alpha A B^T with K <= 64, A (M x K) and
 // B (N x K) given by rows.  Each row of an operand is scaled by a power of two 2^e (e: the
-// smallest with every |x| < 2^e in the row) and cut into S = 7 slices of 7 bits,
-//   x = 2^e sum_s a_s 2^(-7(s+1)) + r,   a_s integers, |a_s| <= 127,  0 <= |r| < 2^(e-49),
-// (the 49 leading bits of the row's fixed-point form, sign and magnitude), each a_s exact in
-// FP16.  The product of slices s and t summed over K = 64 is an integer below 64 * 127^2 <
-// 2^20, and the sum over the c + 1 pairs with s + t = c stays below 7 * 2^20 < 2^23: the
-// tensor cores' FP32 accumulator holds every partial sum exactly, whatever the order or the
-// rounding of its additions.  One TMEM accumulator per c = 0..6 takes the 28 pairs with
-// s + t <= 6 (the dropped pairs weigh at most 2^-49 of max|A_r| max|B_c| K together with the
-// slicing remainders).  The epilogue adds the seven exact integers with their weights
-// 2^(-7c) in double-float (TwoSum), scales the pair by 2^(e_A + e_B - 14) through the
-// exponent field and adds it to C in FP64: two FP64 additions per element, the only work
-// done on this part's FP64 pipe (1/64 of the FP32 rate).
+// smallest with every |x| < 2^e in the row) and cut into S = 6 slices of 8 bits,
+//   x = 2^e sum_s a_s 2^(-8(s+1)) + r,   a_s integers, |a_s| <= 255,  0 <= |r| < 2^(e-48),
+// (the 48 leading bits of the row's fixed-point form, sign and magnitude), each a_s exact in
+// FP16.  The product of slices s and t summed over K = 64 is an integer of at most
+// 64 * 255^2 = 4,161,600; one TMEM accumulator per c = 0..5 takes the 21 pairs with s + t = c.
+// For c <= 3 (at most 4 pairs) every partial sum stays within 4 * 4,161,600 < 2^24: the
+// tensor cores' FP32 accumulator holds it exactly, whatever the order or the rounding of its
+// additions.  The accumulators of c = 4, 5 (weights 2^-32, 2^-40) may pass 2^24 and lose at
+// most one unit per product instruction (K = 16 each, 44 in all), below 2^-49 of
+// max|A_r| max|B_c| K; the dropped pairs (s + t >= 6) and the slicing remainders weigh about
+// 2^-45 of it together.  The epilogue adds the six integers with their weights 2^(-8c) in
+// double-float (TwoSum), scales the pair by 2^(e_A + e_B - 16) through the exponent field and
+// adds it to C in FP64: two FP64 additions per element, the only work done on this part's
+// FP64 pipe (1/64 of the FP32 rate).  Six slices of 8 bits take 84 product instructions per
+// 128 x 32 tile where seven of 7 bits (the same accuracy) would take 112: at N = 32 the tensor
+// cores' instruction issue, not their arithmetic, bounds the kernel.
 //
 // The 64 x 64 diagonal blocks are factored and inverted in FP64 (k_potrf_diag); the
 // structure of the factorisation and of the inverse (forward sweep L Y = I, backward sweep
@@ -38,8 +42,9 @@ namespace {
 
 using namespace tc5;
 
-constexpr int OZ_S = 7;                    // slices per operand row
-constexpr int OZ_BITS = 7;                 // bits per slice
+constexpr int OZ_S = 6;                    // slices per operand row
+constexpr int OZ_BITS = 8;                 // bits per slice
+constexpr int OZ_FBITS = OZ_S * OZ_BITS;   // bits of a row's fixed-point form
 constexpr int OZ_K = 64;                   // K of every update
 constexpr int OZ_BM = 128, OZ_BN = 32;     // output tile (rows of A, columns of B)
 constexpr int OZ_ITEM_COLS = 512;          // columns of one work item (16 tiles)
@@ -47,7 +52,7 @@ constexpr int OZ_ITEMS_PER_CTA = 2;        // work items a CTA takes in turn (at
 constexpr uint32_t OZ_ATILE = OZ_BM * OZ_K * 2;                // 16 KB: one slice of a 128-row block
 constexpr uint32_t OZ_BTILE = OZ_BN * OZ_K * 2;                // 4 KB: one slice of a 32-column tile
 constexpr uint32_t OZ_ACOLS = OZ_S * OZ_BN;                    // TMEM columns of one accumulator set
-constexpr uint32_t OZ_TILES = OZ_S * OZ_ATILE + 2 * OZ_S * OZ_BTILE;   // 168 KB
+constexpr uint32_t OZ_TILES = OZ_S * OZ_ATILE + 2 * OZ_S * OZ_BTILE;   // 144 KB
 constexpr int OZ_BAD = 1 << 20;            // exponent recorded for a row holding an Inf or a NaN
 constexpr int ERR_OZ = 16;
 constexpr int OZ_EPI_WARPS = 16;          // four per TMEM lane quarter, 8 columns each
@@ -96,17 +101,17 @@ struct OzShared {
   int abort_flag;
 };
 
-// the 49-bit fixed-point magnitude of x (bits b, biased exponent e) in units of 2^(e_row - 49),
-// e_row = emax - 1022 the row's exponent: floor(|x| 2^(49 - e_row))
+// the 48-bit fixed-point magnitude of x (bits b, biased exponent e) in units of 2^(e_row - 48),
+// e_row = emax - 1022 the row's exponent: floor(|x| 2^(48 - e_row))
 __device__ __forceinline__ uint64_t oz_fixed(uint64_t b, int e, int emax) {
   if (e == 0 || e == 0x7ff || emax == 0x7ff) return 0;   // zero or subnormal; Inf/NaN rows are flagged
   const uint64_t m = (b & ((1ull << 52) - 1)) | (1ull << 52);
-  const int sh = 4 + emax - e;
+  const int sh = (53 - OZ_FBITS) + emax - e;
   return sh >= 64 ? 0ull : m >> sh;
 }
 
 __device__ __forceinline__ __half oz_digit(uint64_t F, int sh, uint64_t b) {
-  int v = (int)((F >> sh) & 127u);
+  int v = (int)((F >> sh) & ((1u << OZ_BITS) - 1u));
   if (b >> 63) v = -v;
   return __int2half_rn(v);
 }
@@ -168,18 +173,17 @@ __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, OzShared&
   }
 }
 
-// sum over c of g[c] 2^(-7c) as a double-float (hi, lo), |lo| <= ulp(hi) / 2.  Every term is
-// an exact FP32 number.  The three smallest (c = 4..6, below 2^-5 in units of the leading
-// integer's weight) are summed in plain FP32 (one rounding, below 2^-29 of those units); the
-// four leading ones are added by TwoSum, whose rounding errors are recovered in lo.  Against the
-// bound max|A_r| max|B_c| K (about 2^20 units) the pair is accurate to about 2^-46.
+// sum over c of g[c] 2^(-8c) as a double-float (hi, lo), |lo| <= ulp(hi) / 2.  Every term is
+// an FP32 number.  The two smallest (c = 4, 5, below 2^-8 in units of the leading integer's
+// weight) are summed in plain FP32 (one rounding, below 2^-32 of those units); the four leading
+// ones are added by TwoSum, whose rounding errors are recovered in lo.  Against the bound
+// max|A_r| max|B_c| K (about 2^22 units) the pair is accurate to about 2^-46.
 __device__ __forceinline__ void oz_combine(const uint32_t (&g)[OZ_S][4], int j, float& hi, float& lo) {
-  hi = __fmaf_rn(__uint_as_float(g[6][j]), 0x1p-42f,
-                 __fmaf_rn(__uint_as_float(g[5][j]), 0x1p-35f, __fmul_rn(__uint_as_float(g[4][j]), 0x1p-28f)));
+  hi = __fmaf_rn(__uint_as_float(g[5][j]), 0x1p-40f, __fmul_rn(__uint_as_float(g[4][j]), 0x1p-32f));
   lo = 0.f;
 #pragma unroll
   for (int c = 3; c >= 0; --c) {
-    const float w = c == 0 ? 1.f : c == 1 ? 0x1p-7f : c == 2 ? 0x1p-14f : 0x1p-21f;
+    const float w = c == 0 ? 1.f : c == 1 ? 0x1p-8f : c == 2 ? 0x1p-16f : 0x1p-24f;
     const float tv = __fmul_rn(__uint_as_float(g[c][j]), w);
     const float s = __fadd_rn(tv, hi);
     const float bb = __fsub_rn(s, tv);
@@ -192,10 +196,10 @@ __device__ __forceinline__ void oz_combine(const uint32_t (&g)[OZ_S][4], int j, 
   hi = s;
 }
 
-// Each CTA (one per SM at a time: the slices fill shared memory) takes a few work items in turn.  Per item warp 0 copies the seven A
-// slices of the row block once and the seven B slices of each 32-column tile into a double
-// buffer (TMA, 128-byte swizzle); one thread of warp 1 issues the 28 x 4 products of a tile
-// into one of two TMEM accumulator sets (seven 128 x 32 accumulators each); warps 2..17 read a
+// Each CTA (one per SM at a time: the slices fill shared memory) takes a few work items in turn.  Per item warp 0 copies the six A
+// slices of the row block once and the six B slices of each 32-column tile into a double
+// buffer (TMA, 128-byte swizzle); one thread of warp 1 issues the 21 x 4 products of a tile
+// into one of two TMEM accumulator sets (six 128 x 32 accumulators each); warps 2..17 read a
 // finished set, update their 32 rows x 8 columns of D and free it, while the next tile's
 // copies and products run.  Every wait is bounded: on a timeout the CTA records an error
 // code, stops issuing, lets its copies and products in flight finish (bounded), frees TMEM and
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_rows(const __grid_constant
             break;
           }
           fence_after();
-          // 112 products, fully unrolled: a product is only ~16 tensor cycles at N = 32, so the
+          // 84 products, fully unrolled: a product is only ~16 tensor cycles at N = 32, so the
           // issuing thread adds compile-time offsets to two base descriptors (the start address
           // field is the byte address / 16: offsets inside shared memory never carry out of it)
           const uint32_t acc = tmem + st * OZ_ACOLS;
