@@ -1260,7 +1260,9 @@ rff_status setup_factors(rff_admm_t h) {
       CK(launch_set_diag(Qb, fd, fd, 1.0, s.st));
       jobs.push_back(MatJob{Hb, fd, (int)fd, Qb, fd, info + bb});
     }
-    CK(factor_and_invert_f64(jobs, true, fscr, s.st, true));
+    // Q is stored to 24 bits (FP32, or three BF16 pieces): updates that keep 40 bits of every
+    // operand leave it within cond(H) 2^-40 (about 2e-9 at cond 2.3e3), far inside that
+    CK(factor_and_invert_f64(jobs, true, fscr, s.st, true, 40));
     for (int64_t bb = 0; bb < nb; ++bb) {
       const int64_t blk = b0 + bb;
       const int64_t fd = s.outer ? s.row_size[blk / s.C] : s.col_size[blk % s.C];

@@ -584,10 +584,10 @@ size_t factor_scratch_bytes(int njobs, int smax) {
 }
 
 cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st,
-                                  bool double_float) {
+                                  bool double_float, int oz_bits) {
   const int nj = (int)jobs.size();
   if (nj == 0) return cudaSuccess;
-  if (!use_double_float_updates()) return factor_and_invert_oz(jobs, invert, dev_scratch, st);
+  if (!use_double_float_updates()) return factor_and_invert_oz(jobs, invert, dev_scratch, st, oz_bits);
   int smax = 0;
   for (const auto& j : jobs) smax = std::max(smax, j.s);
   const int nb = (int)ceil_div(smax, 64);

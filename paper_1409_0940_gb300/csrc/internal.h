@@ -175,15 +175,17 @@ struct MatJob {    // host description of one matrix to factor (and invert)
 };
 size_t factor_scratch_bytes(int njobs, int smax);
 // blocked Cholesky (and inverse); double_float selects the double-float GEMM for the block
-// updates (the 64 x 64 diagonal factorisations stay FP64)
+// updates under RFF_FACTOR=df (the 64 x 64 diagonal factorisations stay FP64); oz_bits: the
+// leading bits of every update operand the tensor-core updates keep (48 or 40)
 cudaError_t factor_and_invert_f64(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st,
-                                  bool double_float = false);
+                                  bool double_float = false, int oz_bits = 48);
 cudaError_t launch_mirror_lower(double* Q, int64_t ld, int64_t s, cudaStream_t st);
 
 // ozaki.cu: the same factorisation with the block updates on the tensor cores (error-free
 // slices of the FP64 operands); factor_and_invert_f64 calls it unless RFF_FACTOR=df
 size_t oz_factor_scratch_bytes(int njobs, int smax);
-cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st);
+cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st,
+                                 int bits);
 
 // elementwise.cu
 // dst[p][c] = src[map[p] * lds + c] (c < w), zero for c >= w or map[p] < 0; map null = identity

@@ -22,6 +22,11 @@
 // 128 x 32 tile where seven of 7 bits (the same accuracy) would take 112: at N = 32 the tensor
 // cores' instruction issue, not their arithmetic, bounds the kernel.
 //
+// S = 6 (48 bits) serves the public Cholesky factorisation.  The solver's set-up stores the
+// inverse to 24 bits (FP32, or three BF16 pieces) and takes S = 5: 40 bits, 15 pairs (60
+// product instructions per tile), the accumulator of c = 4 the only one that may round; the
+// inverse then stays within about cond(H) 2^-40 of its FP64 value.
+//
 // The 64 x 64 diagonal blocks are factored and inverted in FP64 (k_potrf_diag); the
 // structure of the factorisation and of the inverse (forward sweep L Y = I, backward sweep
 // L^T Q = Y over the block lower triangle, mirrored at the end) is that of the double-float
@@ -42,17 +47,17 @@ namespace {
 
 using namespace tc5;
 
-constexpr int OZ_S = 6;                    // slices per operand row
+constexpr int OZ_SMAX = 6;                 // slices per operand row (S), at most
 constexpr int OZ_BITS = 8;                 // bits per slice
-constexpr int OZ_FBITS = OZ_S * OZ_BITS;   // bits of a row's fixed-point form
 constexpr int OZ_K = 64;                   // K of every update
 constexpr int OZ_BM = 128, OZ_BN = 32;     // output tile (rows of A, columns of B)
 constexpr int OZ_ITEM_COLS = 512;          // columns of one work item (16 tiles)
 constexpr int OZ_ITEMS_PER_CTA = 2;        // work items a CTA takes in turn (at least one CTA per SM)
 constexpr uint32_t OZ_ATILE = OZ_BM * OZ_K * 2;                // 16 KB: one slice of a 128-row block
 constexpr uint32_t OZ_BTILE = OZ_BN * OZ_K * 2;                // 4 KB: one slice of a 32-column tile
-constexpr uint32_t OZ_ACOLS = OZ_S * OZ_BN;                    // TMEM columns of one accumulator set
-constexpr uint32_t OZ_TILES = OZ_S * OZ_ATILE + 2 * OZ_S * OZ_BTILE;   // 144 KB
+// TMEM columns of one accumulator set, and the shared-memory tiles (144 KB at S = 6)
+__host__ __device__ constexpr uint32_t oz_acols(int S) { return (uint32_t)S * OZ_BN; }
+__host__ __device__ constexpr uint32_t oz_tiles(int S) { return (uint32_t)S * OZ_ATILE + 2u * S * OZ_BTILE; }
 constexpr int OZ_BAD = 1 << 20;            // exponent recorded for a row holding an Inf or a NaN
 constexpr int ERR_OZ = 16;
 constexpr int OZ_EPI_WARPS = 16;          // four per TMEM lane quarter, 8 columns each
@@ -63,7 +68,7 @@ struct OzSliceJob {
   int64_t ld;
   int rows, kdim;
   int trans;          // 0: x[r][k] = src[r ld + k];  1: x[r][k] = src[k ld + r]
-  __half* dst;        // OZ_S x rpad x 64: slice s of row r at (s rpad + r) 64
+  __half* dst;        // S x rpad x 64: slice s of row r at (s rpad + r) 64
   int32_t* exps;      // rpad
 };
 
@@ -101,12 +106,12 @@ struct OzShared {
   int abort_flag;
 };
 
-// the 48-bit fixed-point magnitude of x (bits b, biased exponent e) in units of 2^(e_row - 48),
-// e_row = emax - 1022 the row's exponent: floor(|x| 2^(48 - e_row))
-__device__ __forceinline__ uint64_t oz_fixed(uint64_t b, int e, int emax) {
+// the fbits-bit fixed-point magnitude of x (bits b, biased exponent e) in units of
+// 2^(e_row - fbits), e_row = emax - 1022 the row's exponent: floor(|x| 2^(fbits - e_row))
+__device__ __forceinline__ uint64_t oz_fixed(uint64_t b, int e, int emax, int fbits) {
   if (e == 0 || e == 0x7ff || emax == 0x7ff) return 0;   // zero or subnormal; Inf/NaN rows are flagged
   const uint64_t m = (b & ((1ull << 52) - 1)) | (1ull << 52);
-  const int sh = (53 - OZ_FBITS) + emax - e;
+  const int sh = (53 - fbits) + emax - e;
   return sh >= 64 ? 0ull : m >> sh;
 }
 
@@ -116,6 +121,7 @@ __device__ __forceinline__ __half oz_digit(uint64_t F, int sh, uint64_t b) {
   return __int2half_rn(v);
 }
 
+template <int S>
 __global__ void __launch_bounds__(256) k_oz_slice(const OzSliceJob* __restrict__ jobs, int rpad) {
   const OzSliceJob J = jobs[blockIdx.z];
   const int r0 = blockIdx.x * 32;
@@ -144,13 +150,13 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSliceJob* __restrict__
     const uint64_t b1 = (uint64_t)__double_as_longlong(t[r][lane + 32]);
     const int e0 = (int)((b0 >> 52) & 0x7ff), e1 = (int)((b1 >> 52) & 0x7ff);
     const int emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(e0, e1));
-    const uint64_t F0 = oz_fixed(b0, e0, emax), F1 = oz_fixed(b1, e1, emax);
+    const uint64_t F0 = oz_fixed(b0, e0, emax, S * OZ_BITS), F1 = oz_fixed(b1, e1, emax, S * OZ_BITS);
     const int64_t row = r0 + r;
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-      const int sh = OZ_BITS * (OZ_S - 1 - s);
+    for (int s = 0; s < S; ++s) {
+      const int sh = OZ_BITS * (S - 1 - s);
       const int64_t o = ((int64_t)s * rpad + row) * 64;
-      if (RFF_SPAN(o, 64, (int64_t)OZ_S * rpad * 64)) {
+      if (RFF_SPAN(o, 64, (int64_t)S * rpad * 64)) {
         J.dst[o + lane] = oz_digit(F0, sh, b0);
         J.dst[o + lane + 32] = oz_digit(F1, sh, b1);
       }
@@ -174,12 +180,16 @@ __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, OzShared&
 }
 
 // sum over c of g[c] 2^(-8c) as a double-float (hi, lo), |lo| <= ulp(hi) / 2.  Every term is
-// an FP32 number.  The two smallest (c = 4, 5, below 2^-8 in units of the leading integer's
-// weight) are summed in plain FP32 (one rounding, below 2^-32 of those units); the four leading
-// ones are added by TwoSum, whose rounding errors are recovered in lo.  Against the bound
+// an FP32 number.  Those of c >= 4 (below 2^-8 in units of the leading integer's weight) are
+// summed in plain FP32 (one rounding each, below 2^-32 of those units); the four leading ones
+// are added by TwoSum, whose rounding errors are recovered in lo.  Against the bound
 // max|A_r| max|B_c| K (about 2^22 units) the pair is accurate to about 2^-46.
-__device__ __forceinline__ void oz_combine(const uint32_t (&g)[OZ_S][4], int j, float& hi, float& lo) {
-  hi = __fmaf_rn(__uint_as_float(g[5][j]), 0x1p-40f, __fmul_rn(__uint_as_float(g[4][j]), 0x1p-32f));
+template <int S>
+__device__ __forceinline__ void oz_combine(const uint32_t (&g)[S][4], int j, float& hi, float& lo) {
+  static_assert(S >= 5, "the four leading weights are summed by TwoSum");
+  hi = 0.f;
+#pragma unroll
+  for (int c = S - 1; c >= 4; --c) hi = __fmaf_rn(__uint_as_float(g[c][j]), __int_as_float((127 - 8 * c) << 23), hi);
   lo = 0.f;
 #pragma unroll
   for (int c = 3; c >= 0; --c) {
@@ -204,12 +214,13 @@ __device__ __forceinline__ void oz_combine(const uint32_t (&g)[OZ_S][4], int j, 
 // copies and products run.  Every wait is bounded: on a timeout the CTA records an error
 // code, stops issuing, lets its copies and products in flight finish (bounded), frees TMEM and
 // returns.
+template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_rows(const __grid_constant__ OzArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-  OzShared& sh = *reinterpret_cast<OzShared*>(base + OZ_TILES);
+  OzShared& sh = *reinterpret_cast<OzShared*>(base + oz_tiles(S));
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const uint32_t sa = smem_u32(base), sb = sa + OZ_S * OZ_ATILE;
+  const uint32_t sa = smem_u32(base), sb = sa + S * OZ_ATILE;
   const uint32_t bar_a_full = smem_u32(&sh.a_full), bar_a_empty = smem_u32(&sh.a_empty);
   const uint32_t bar_b_full = smem_u32(&sh.b_full[0]), bar_b_empty = smem_u32(&sh.b_empty[0]);
   const uint32_t bar_acc_full = smem_u32(&sh.acc_full[0]), bar_acc_empty = smem_u32(&sh.acc_empty[0]);
@@ -245,9 +256,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_rows(const __grid_constant
           break;
         }
         ++ni;
-        mbar_expect_tx(bar_a_full, OZ_S * OZ_ATILE);
+        mbar_expect_tx(bar_a_full, S * OZ_ATILE);
 #pragma unroll 1
-        for (int s = 0; s < OZ_S; ++s)
+        for (int s = 0; s < S; ++s)
           tma_load_2d(sa + s * OZ_ATILE, &a.tA, 0, J.a_row + s * a.rpad + w.m0, bar_a_full);
         for (int n0 = w.n0; n0 < w.n1; n0 += OZ_BN, ++it) {
           const uint32_t st = it & 1;
@@ -255,10 +266,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_rows(const __grid_constant
             ok = false;
             break;
           }
-          mbar_expect_tx(bar_b_full + 8 * st, OZ_S * OZ_BTILE);
+          mbar_expect_tx(bar_b_full + 8 * st, S * OZ_BTILE);
 #pragma unroll 1
-          for (int s = 0; s < OZ_S; ++s)
-            tma_load_2d(sb + (st * OZ_S + s) * OZ_BTILE, &a.tB, 0, J.b_row + s * a.rpad + n0, bar_b_full + 8 * st);
+          for (int s = 0; s < S; ++s)
+            tma_load_2d(sb + (st * S + s) * OZ_BTILE, &a.tB, 0, J.b_row + s * a.rpad + n0, bar_b_full + 8 * st);
         }
       }
       if (!ok) {   // copies still in flight land before the CTA may exit (bounded)
@@ -293,12 +304,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_rows(const __grid_constant
           // 84 products, fully unrolled: a product is only ~16 tensor cycles at N = 32, so the
           // issuing thread adds compile-time offsets to two base descriptors (the start address
           // field is the byte address / 16: offsets inside shared memory never carry out of it)
-          const uint32_t acc = tmem + st * OZ_ACOLS;
-          const uint64_t da0 = sw128_desc(sa), db0 = sw128_desc(sb + st * OZ_S * OZ_BTILE);
+          const uint32_t acc = tmem + st * oz_acols(S);
+          const uint64_t da0 = sw128_desc(sa), db0 = sw128_desc(sb + st * S * OZ_BTILE);
 #pragma unroll
-          for (int s = 0; s < OZ_S; ++s)
+          for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int t = 0; t + s < OZ_S; ++t)
+            for (int t = 0; t + s < S; ++t)
 #pragma unroll
               for (int kk = 0; kk < OZ_K / 16; ++kk)
                 mma_bf16(acc + (uint32_t)((s + t) * OZ_BN), da0 + (uint64_t)((s * OZ_ATILE + kk * 32) >> 4),
@@ -377,16 +388,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_rows(const __grid_constant
         const bool vec = wmask == 0xffu && (reinterpret_cast<uintptr_t>(drow) & 15) == 0;
 #pragma unroll
         for (int q = 0; q < 8; q += 4) {   // two rounds of four columns
-          uint32_t g[OZ_S][4];
+          uint32_t g[S][4];
 #pragma unroll
-          for (int c = 0; c < OZ_S; ++c)
-            tmem_ld4(tmem + lane_base + st * OZ_ACOLS + (uint32_t)(c * OZ_BN + col8 * 8 + q), g[c]);
+          for (int c = 0; c < S; ++c)
+            tmem_ld4(tmem + lane_base + st * oz_acols(S) + (uint32_t)(c * OZ_BN + col8 * 8 + q), g[c]);
           tmem_wait_ld();
           double v[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             float hi, lo;
-            oz_combine(g, j, hi, lo);
+            oz_combine<S>(g, j, hi, lo);
             if (a.neg) {
               hi = -hi;
               lo = -lo;
@@ -425,13 +436,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_rows(const __grid_constant
   if (warp == 1) tmem_dealloc<1>(tmem, 512);
 }
 
-constexpr size_t OZ_SMEM_BYTES = 1024 + OZ_TILES + 64;
+constexpr size_t oz_smem_bytes(int S) { return 1024 + oz_tiles(S) + 64; }
 
+template <int S>
 cudaError_t oz_rows_attr() {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_oz_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM_BYTES);
+    attr = cudaFuncSetAttribute(k_oz_rows<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes(S));
   });
   return attr;
 }
@@ -498,8 +510,8 @@ OzLayout oz_layout(int nj, int smax) {
   };
   L.inv = take((size_t)nj * L.nb * 4096 * sizeof(double));
   L.djobs = take((size_t)nj * L.nb * sizeof(DiagJob));
-  L.sa = take((size_t)nj * OZ_S * L.rpad * 64 * 2);
-  L.sb = take((size_t)nj * OZ_S * L.rpad * 64 * 2);
+  L.sa = take((size_t)nj * OZ_SMAX * L.rpad * 64 * 2);
+  L.sb = take((size_t)nj * OZ_SMAX * L.rpad * 64 * 2);
   L.ea = take((size_t)nj * L.rpad * 4);
   L.eb = take((size_t)nj * L.rpad * 4);
   L.sjobs = take((size_t)OZ_NPHASE * L.nb * 2 * nj * sizeof(OzSliceJob));
@@ -521,11 +533,8 @@ int sm_count() {
   return n;
 }
 
-}  // namespace
-
-size_t oz_factor_scratch_bytes(int njobs, int smax) { return oz_layout(njobs, smax).total; }
-
-cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st) {
+template <int S>
+cudaError_t factor_and_invert_sliced(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st) {
   const int nj = (int)jobs.size();
   if (nj == 0) return cudaSuccess;
   int smax = 0;
@@ -544,7 +553,7 @@ cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, v
   OzJob* gjobs = reinterpret_cast<OzJob*>(p + L.gjobs);
   OzItem* ditems = reinterpret_cast<OzItem*>(p + L.items);
   cudaError_t e;
-  if ((e = oz_rows_attr()) != cudaSuccess) return e;
+  if ((e = oz_rows_attr<S>()) != cudaSuccess) return e;
 
   std::vector<DiagJob> hd((size_t)nj * nb);
   for (int k = 0; k < nb; ++k)
@@ -573,11 +582,11 @@ cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, v
       const double* Ikk = inv + ((size_t)b * nb + k) * 4096;
       double* Lp = J.A + (c0 + 64) * J.ld + c0;   // L panel below the diagonal block
       double* Qk = J.Q ? J.Q + c0 * J.ldq : nullptr;
-      __half* da = sa + (size_t)b * OZ_S * rpad * 64;
-      __half* db = sb + (size_t)b * OZ_S * rpad * 64;
+      __half* da = sa + (size_t)b * S * rpad * 64;
+      __half* db = sb + (size_t)b * S * rpad * 64;
       int32_t* xa = ea + (size_t)b * rpad;
       int32_t* xb = eb + (size_t)b * rpad;
-      const int arow = b * OZ_S * rpad;
+      const int arow = b * S * rpad;
       auto slice = [&](int ph, const double* srcA, int64_t ldA, int rowsA, int transA, const double* srcB,
                        int64_t ldB, int rowsB, int transB) {
         sj(ph, k, 0, b) = OzSliceJob{srcA, ldA, rowsA, bs, transA, da, xa};
@@ -635,7 +644,7 @@ cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, v
 
   OzArgs a;
   memset(&a, 0, sizeof(a));
-  const int64_t map_rows = (int64_t)nj * OZ_S * rpad;
+  const int64_t map_rows = (int64_t)nj * S * rpad;
   if ((e = tc_make_map_bf16(&a.tA, sa, 64, map_rows, 64, OZ_BM, 64)) != cudaSuccess) return e;
   if ((e = tc_make_map_bf16(&a.tB, sb, 64, map_rows, 64, OZ_BN, 64)) != cudaSuccess) return e;
   a.rpad = rpad;
@@ -651,7 +660,7 @@ cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, v
     if (i1 <= i0) return cudaSuccess;
     const int rows = (int)round_up(std::max(rowsA, rowsB), OZ_BM);
     dim3 sg((unsigned)(std::min(rows, rpad) / 32), 1, (unsigned)(2 * nj));
-    k_oz_slice<<<sg, 256, 0, st>>>(sjobs + ((size_t)ph * nb + k) * 2 * nj, rpad);
+    k_oz_slice<S><<<sg, 256, 0, st>>>(sjobs + ((size_t)ph * nb + k) * 2 * nj, rpad);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     a.jobs = gjobs + ((size_t)ph * nb + k) * nj;
@@ -664,7 +673,7 @@ cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, v
     // kernels (a server's scoring on a high-priority stream) start only when one finishes
     const int64_t ni = i1 - i0;
     const int64_t grid = std::min<int64_t>(ni, std::max<int64_t>(nsm, ceil_div(ni, OZ_ITEMS_PER_CTA)));
-    k_oz_rows<<<(unsigned)grid, OZ_THREADS, OZ_SMEM_BYTES, st>>>(a);
+    k_oz_rows<S><<<(unsigned)grid, OZ_THREADS, oz_smem_bytes(S), st>>>(a);
     return cudaGetLastError();
   };
   for (int k = 0; k < nb; ++k) {
@@ -687,6 +696,19 @@ cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, v
   for (const auto& J : jobs)
     if (J.Q && (e = launch_mirror_lower(J.Q, J.ldq, J.s, st)) != cudaSuccess) return e;
   return cudaSuccess;
+}
+
+}  // namespace
+
+size_t oz_factor_scratch_bytes(int njobs, int smax) { return oz_layout(njobs, smax).total; }
+
+cudaError_t factor_and_invert_oz(const std::vector<MatJob>& jobs, bool invert, void* dev_scratch, cudaStream_t st,
+                                 int bits) {
+  switch (bits) {
+    case 48: return factor_and_invert_sliced<6>(jobs, invert, dev_scratch, st);
+    case 40: return factor_and_invert_sliced<5>(jobs, invert, dev_scratch, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 RFF_CHECK_UNIT(ozaki)
