@@ -378,7 +378,73 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
   const int64_t jstride = a.nslots * mp;
   const float inv_c1 = 1.f / (float)(a.C + 1);
   const float cfrac = (float)a.C * inv_c1;
-  for (int r = warp; r < EX_ROWS; r += 8) {
+  // elementwise losses: the tile's 32 x m_pad elements as 16-byte items, two items per thread
+  // with all their loads (O, nu, Y and the C blocks of O') issued before any use, so that
+  // enough bytes are in flight to keep HBM busy; the arithmetic per element and its order are
+  // those of the row form below
+  if constexpr (!row_loss(LOSS)) {
+    const int n4 = EX_ROWS * mp / 4;
+    const int64_t tb = p0 * mp;
+    constexpr int NB = 2;
+#pragma unroll 1
+    for (int i0 = threadIdx.x; i0 < n4; i0 += NB * 256) {
+      float4 Ov[NB], nuv[NB], yv[NB], Sv[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int e4 = i0 + u * 256;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        Ov[u] = nuv[u] = yv[u] = Sv[u] = z;
+        if (e4 < n4) {
+          Ov[u] = *reinterpret_cast<const float4*>(a.O + tb + 4 * e4);
+          nuv[u] = *reinterpret_cast<const float4*>(a.nu + tb + 4 * e4);
+          yv[u] = __ldg(reinterpret_cast<const float4*>(a.Y + tb + 4 * e4));
+        }
+      }
+#pragma unroll 4
+      for (int j = 0; j < a.C; ++j) {
+        const float* opj = a.Op + j * jstride + tb;
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int e4 = i0 + u * 256;
+          if (e4 < n4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(opj + 4 * e4));
+            Sv[u].x += v.x;
+            Sv[u].y += v.y;
+            Sv[u].z += v.z;
+            Sv[u].w += v.w;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int e4 = i0 + u * 256;
+        if (e4 >= n4) continue;
+        const int r = (4 * e4) / mp, k0 = (4 * e4) % mp;
+        const bool ok = a.row_ok[p0 + r] >= 0;
+        float S[4] = {Sv[u].x, Sv[u].y, Sv[u].z, Sv[u].w}, O[4] = {Ov[u].x, Ov[u].y, Ov[u].z, Ov[u].w};
+        float nu[4] = {nuv[u].x, nuv[u].y, nuv[u].z, nuv[u].w}, y[4] = {yv[u].x, yv[u].y, yv[u].z, yv[u].w};
+        float ob[4], tm[4], on[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const bool live = ok && k0 + c < a.m;
+          const float Delta = O[c] - S[c];
+          const float Obar = S[c] * inv_c1 + cfrac * O[c];
+          const float nun = nu[c] + (O[c] - Obar);
+          ob[c] = live ? Obar : 0.f;
+          nu[c] = live ? nun : 0.f;
+          if (live) numax = fmaxf(numax, fabsf(nun));
+          tm[c] = live ? Delta * inv_c1 + nun : 0.f;
+          on[c] = live ? prox_scalar(LOSS, Obar - nun, y[c], a.t_loss, a.newton) : 0.f;
+          if (live) omax = fmaxf(omax, fabsf(on[c]));
+        }
+        *reinterpret_cast<float4*>(a.Obar + tb + 4 * e4) = make_float4(ob[0], ob[1], ob[2], ob[3]);
+        *reinterpret_cast<float4*>(a.nu + tb + 4 * e4) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+        *reinterpret_cast<float4*>(a.O + tb + 4 * e4) = make_float4(on[0], on[1], on[2], on[3]);
+        *reinterpret_cast<float4*>(term + 4 * e4) = make_float4(tm[0], tm[1], tm[2], tm[3]);
+      }
+    }
+  }
+  for (int r = warp; row_loss(LOSS) && r < EX_ROWS; r += 8) {
     const int64_t p = p0 + r;
     const bool ok = a.row_ok[p] >= 0;
     const int64_t base = p * mp;
