@@ -283,8 +283,7 @@ rff_status rff_admm_predict_labels(rff_admm_t h, const float* Xq, int64_t q, int
  * split path (the queries in FP32, their FP16 hi/lo split, the padded scores); a larger
  * q returns RFF_EINVAL with the limit in the error text -- score in smaller batches.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- * once per device, that device current); make that first call before any stream
- * capture begins.
+ * once per device, that device current).
  * All calls share the array and it keeps the previous call's contents (the call clears
  * what must start at zero): calls that overlap on the GPU -- two handles or threads
  * scoring at the same time -- race on it.
