@@ -1081,6 +1081,7 @@ rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t
     v.out_elems = (int64_t)GRAM_GROUP * tc_gram_tiles(smax) * 128 * 256;
     v.out_scale = 1.f / (zs * zs);
     v.two_acc = 1;
+    v.persistent = 1;
     v.st = s.st;
     CK(split_gemm(v));
     CK(launch_gram_reduce(P, (int)(g1 - g0), (int)nt, dtiles, sj, H, sj, s.st));
@@ -1375,7 +1376,7 @@ SgView qgemm_view(const rff_admm_s& s) {
   v.two_acc = 1;
   v.bmask = s.act();
   v.accumulate = 1;   // W'_ij += Q_ij rhs_ij (the incremental projection)
-  v.st = s.st;
+  v.st = s.st;   // one job per CTA: the hardware hands the 3.4 waves of jobs to whichever SM is free
   return v;
 }
 

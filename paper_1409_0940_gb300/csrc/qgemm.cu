@@ -47,6 +47,9 @@ struct QArgs {
   int mpad, ns;
   uint32_t stage_bytes, tmem_cols;
   uint32_t acc_b;            // column of the second accumulator (the small products), 0 = one accumulator
+  uint32_t nbuf;             // accumulator sets in TMEM (2: the next job's products overlap the epilogue)
+  uint32_t buf_cols;         // TMEM columns of one set
+  int njobs;
   const SgJob* jobs;
   float* out;
   int64_t out_elems;
@@ -61,7 +64,7 @@ struct QArgs {
 
 struct QShared {
   uint64_t full[QMAXS], empty[QMAXS];
-  uint64_t acc_full, mma_done;
+  uint64_t acc_full[2], acc_empty[2], mma_done;
   uint32_t tmem;
   int abort_flag;
 };
@@ -84,18 +87,24 @@ __device__ __forceinline__ bool qwait(uint32_t bar, uint32_t parity, QShared& sh
 __host__ __device__ constexpr int prod_a(int p) { return p == 2 || p == 4 ? 1 : p == 5 ? 2 : 0; }
 __host__ __device__ constexpr int prod_b(int p) { return p == 1 || p == 4 ? 1 : p == 3 ? 2 : 0; }
 
+// A job is skipped by every role alike when it has no K chunks or its block is inactive.
+__device__ __forceinline__ bool q_skip(const SgJob& j, const QArgs& a) {
+  return j.nk <= 0 || (a.bmask && !a.bmask[j.blk]);
+}
+
+// Each CTA takes the jobs blockIdx.x, blockIdx.x + gridDim.x, ... (one job per CTA when the
+// grid covers the table).  The copies run ahead through the ring across jobs; a job's products
+// go to accumulator set (its count) mod nbuf, which the writing warps free after reading it.
 template <int NA, int NB, int F16>
 __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArgs a) {
   constexpr int NPROD = (NA == 3 && NB == 3) ? 6 : 3;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   QShared& sh = *reinterpret_cast<QShared*>(base + a.ns * a.stage_bytes);
-  const SgJob job = a.jobs[blockIdx.x];
-  if (a.bmask && !a.bmask[job.blk]) return;   // inactive block: its outputs keep their values
-  const int nk = job.nk;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const uint32_t bar_full = smem_u32(&sh.full[0]), bar_empty = smem_u32(&sh.empty[0]);
-  const uint32_t bar_acc = smem_u32(&sh.acc_full), bar_done = smem_u32(&sh.mma_done);
+  const uint32_t bar_accf = smem_u32(&sh.acc_full[0]), bar_acce = smem_u32(&sh.acc_empty[0]);
+  const uint32_t bar_done = smem_u32(&sh.mma_done);
   const uint32_t mb = (uint32_t)a.mpad * (QKC * 2);   // one B tile: m_pad rows x 64 bytes
   if (threadIdx.x == 0) {
     sh.abort_flag = 0;
@@ -103,7 +112,10 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
       mbar_init(bar_full + 8 * i, 1);
       mbar_init(bar_empty + 8 * i, 1);
     }
-    mbar_init(bar_acc, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar_accf + 8 * i, 1);
+      mbar_init(bar_acce + 8 * i, 4);   // one arrival per writing warp
+    }
     mbar_init(bar_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -120,20 +132,28 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
 
   if (warp == 0) {
     if (lane == 0) {
-      uint32_t issued = 0;
-      for (int kc = 0; kc < nk; ++kc) {
-        const int st = kc % a.ns;
-        const uint32_t use = kc / a.ns;
-        if (use > 0 && !qwait(bar_empty + 8 * st, (use - 1) & 1, sh, a)) break;
-        const uint32_t fb = bar_full + 8 * st;
-        mbar_expect_tx(fb, a.stage_bytes);
-        const uint32_t dst = smem_u32(base + st * a.stage_bytes);
+      uint32_t issued = 0;   // ring stages filled, over all of this CTA's jobs
+      bool ok = true;
+      for (int jx = blockIdx.x; ok && jx < a.njobs; jx += gridDim.x) {
+        const SgJob job = a.jobs[jx];
+        if (q_skip(job, a)) continue;
+        for (int kc = 0; kc < job.nk; ++kc) {
+          const int st = issued % a.ns;
+          const uint32_t use = issued / a.ns;
+          if (use > 0 && !qwait(bar_empty + 8 * st, (use - 1) & 1, sh, a)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = bar_full + 8 * st;
+          mbar_expect_tx(fb, a.stage_bytes);
+          const uint32_t dst = smem_u32(base + st * a.stage_bytes);
 #pragma unroll
-        for (int s = 0; s < NA; ++s) tma_load_2d(dst + s * QATILE, &a.tA[s], job.a_k0 + kc * QKC, job.a_row, fb);
+          for (int s = 0; s < NA; ++s) tma_load_2d(dst + s * QATILE, &a.tA[s], job.a_k0 + kc * QKC, job.a_row, fb);
 #pragma unroll
-        for (int s = 0; s < NB; ++s)
-          tma_load_2d(dst + NA * QATILE + s * mb, &a.tB[s], job.b_k0 + kc * QKC, job.b_row, fb);
-        ++issued;
+          for (int s = 0; s < NB; ++s)
+            tma_load_2d(dst + NA * QATILE + s * mb, &a.tB[s], job.b_k0 + kc * QKC, job.b_row, fb);
+          ++issued;
+        }
       }
       // copies in flight finish before the CTA may exit (bounded)
       for (uint32_t u = issued > (uint32_t)a.ns ? issued - a.ns : 0; u < issued; ++u) {
@@ -147,49 +167,68 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
     if (lane == 0) {
       const uint32_t idesc = F16 ? idesc_f16(128, a.mpad) : idesc_bf16(128, a.mpad);
       bool ok = true;
-      for (int kc = 0; kc < nk; ++kc) {
-        const int st = kc % a.ns;
-        if (!qwait(bar_full + 8 * st, (kc / a.ns) & 1, sh, a)) {
+      uint32_t used = 0, done_jobs = 0;   // ring stages consumed, jobs multiplied
+      for (int jx = blockIdx.x; ok && jx < a.njobs; jx += gridDim.x) {
+        const SgJob job = a.jobs[jx];
+        if (q_skip(job, a)) continue;
+        const uint32_t buf = done_jobs % a.nbuf, round = done_jobs / a.nbuf;
+        if (round > 0 && !qwait(bar_acce + 8 * buf, (round - 1) & 1, sh, a)) {
           ok = false;
           break;
         }
         fence_after();
-        const uint32_t sa = smem_u32(base + st * a.stage_bytes);
-        const uint32_t sb = sa + NA * QATILE;
+        const uint32_t acc = tmem + buf * a.buf_cols;
+        for (int kc = 0; kc < job.nk; ++kc, ++used) {
+          const int st = used % a.ns;
+          if (!qwait(bar_full + 8 * st, (used / a.ns) & 1, sh, a)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sa = smem_u32(base + st * a.stage_bytes);
+          const uint32_t sb = sa + NA * QATILE;
 #pragma unroll
-        for (int kk = 0; kk < QKC / 16; ++kk) {
+          for (int kk = 0; kk < QKC / 16; ++kk) {
 #pragma unroll
-          for (int p = 0; p < NPROD; ++p) {
-            const uint64_t da = smem_desc(sa + prod_a(p) * QATILE + kk * 32, 512, 4);
-            const uint64_t db = smem_desc(sb + prod_b(p) * mb + kk * 32, 512, 4);
-            if (a.acc_b) {
-              // hi.hi alone in the first accumulator, the smaller products in the second
-              const uint32_t d = p == 0 ? tmem : tmem + a.acc_b;
-              mma_bf16(d, da, db, idesc, (kc > 0 || kk > 0 || p > 1) ? 1u : 0u);
-            } else {
-              mma_bf16(tmem, da, db, idesc, (kc > 0 || kk > 0 || p > 0) ? 1u : 0u);
+            for (int p = 0; p < NPROD; ++p) {
+              const uint64_t da = smem_desc(sa + prod_a(p) * QATILE + kk * 32, 512, 4);
+              const uint64_t db = smem_desc(sb + prod_b(p) * mb + kk * 32, 512, 4);
+              if (a.acc_b) {
+                // hi.hi alone in the first accumulator, the smaller products in the second
+                const uint32_t d = p == 0 ? acc : acc + a.acc_b;
+                mma_bf16(d, da, db, idesc, (kc > 0 || kk > 0 || p > 1) ? 1u : 0u);
+              } else {
+                mma_bf16(acc, da, db, idesc, (kc > 0 || kk > 0 || p > 0) ? 1u : 0u);
+              }
             }
           }
+          mma_commit(bar_empty + 8 * st);
         }
-        mma_commit(bar_empty + 8 * st);
+        if (!ok) break;
+        mma_commit(bar_accf + 8 * buf);
+        ++done_jobs;
       }
-      if (ok && nk > 0) mma_commit(bar_acc);
       mma_commit(bar_done);
       qwait(bar_done, 0, sh, a);
     }
   } else {
-    // epilogue: lanes = rows of the A tile, m_pad columns
+    // epilogue: lanes = rows of the A tile, m_pad columns, 8 per TMEM read
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
-    int ok = 0;
-    if (lane == 0) ok = (nk > 0 && qwait(bar_acc, 0, sh, a)) ? 1 : 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (ok) {
+    uint32_t done_jobs = 0;
+    float mx = 0.f;
+    for (int jx = blockIdx.x; jx < a.njobs; jx += gridDim.x) {
+      const SgJob job = a.jobs[jx];
+      if (q_skip(job, a)) continue;
+      const uint32_t buf = done_jobs % a.nbuf, round = done_jobs / a.nbuf;
+      int ok = 0;
+      if (lane == 0) ok = qwait(bar_accf + 8 * buf, round & 1, sh, a) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
       fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+      const uint32_t taddr = tmem + buf * a.buf_cols + ((uint32_t)(quarter * 32) << 16);
       float* orow_p = a.out + job.out + (int64_t)row * a.mpad;
       const float sc = a.out_scale * (a.b_amax ? f16_inv_scale(__uint_as_float(*a.b_amax)) : 1.f);
-      float mx = 0.f;
       for (int c = 0; c < a.mpad; c += 8) {
         uint32_t r8[8], s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         tmem_ld8(taddr + c, r8);
@@ -212,11 +251,15 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
           dst[1] = make_float4(x[4], x[5], x[6], x[7]);
         }
       }
-      if (a.amax) {
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_acce + 8 * buf);   // the set is free for the job after next
+      ++done_jobs;
+    }
+    if (a.amax) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0 && mx > 0.f) atomicMax(a.amax, __float_as_uint(mx));
-      }
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0 && mx > 0.f) atomicMax(a.amax, __float_as_uint(mx));
     }
   }
   fence_before();
@@ -289,6 +332,17 @@ __global__ void k_split3_q(const double* __restrict__ Q, int s, int64_t ldq, int
   q3[o] = l;
 }
 
+int qsm_count() {
+  static int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+      v = 0;
+    return v > 0 ? v : 1;
+  }();
+  return n;
+}
+
 template <int NA, int NB, int F16>
 cudaError_t set_smem_attr() {
   static std::once_flag once;
@@ -344,6 +398,7 @@ cudaError_t split_gemm(const SgView& v) {
     a.tmem_cols *= 2;
   }
   a.jobs = v.jobs;
+  a.njobs = v.njobs;
   a.out = v.out;
   a.out_elems = v.out_elems;
   a.out_scale = v.out_scale;
@@ -357,11 +412,31 @@ cudaError_t split_gemm(const SgView& v) {
   const size_t smem = 1024 + (size_t)a.ns * a.stage_bytes + 256;
   if (v.na == 3) {
     if ((e = set_smem_attr<3, 3, 0>()) != cudaSuccess) return e;
-    k_split_gemm<3, 3, 0><<<(unsigned)v.njobs, QNT, smem, v.st>>>(a);
   } else {
     if ((e = set_smem_attr<2, 2, 1>()) != cudaSuccess) return e;
-    k_split_gemm<2, 2, 1><<<(unsigned)v.njobs, QNT, smem, v.st>>>(a);
   }
+  // one job per CTA, or (persistent) at most as many CTAs as fit on the device at once, each
+  // taking every grid-th job; two accumulator sets when the tensor memory of the CTAs that
+  // share an SM holds them
+  a.buf_cols = a.tmem_cols;
+  a.nbuf = 1;
+  int64_t grid = v.njobs;
+  if (v.persistent) {
+    int per_sm = 0;
+    e = v.na == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_split_gemm<3, 3, 0>, QNT, smem)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_split_gemm<2, 2, 1>, QNT, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+    grid = std::min<int64_t>(v.njobs, (int64_t)qsm_count() * per_sm);
+    if (2u * a.tmem_cols * (uint32_t)per_sm <= 512u) {
+      a.nbuf = 2;
+      a.tmem_cols *= 2;
+    }
+  }
+  if (v.na == 3)
+    k_split_gemm<3, 3, 0><<<(unsigned)grid, QNT, smem, v.st>>>(a);
+  else
+    k_split_gemm<2, 2, 1><<<(unsigned)grid, QNT, smem, v.st>>>(a);
   return cudaGetLastError();
 }
 

@@ -97,6 +97,7 @@ struct SgView {
   int two_acc;                         // 1: hi.hi products in their own TMEM accumulator (twice the columns)
   const uint8_t* bmask;                // device, R x C: a job of an inactive block does nothing; or null
   int accumulate;                      // 1: out += the product (amax of the sum)
+  int persistent;                      // 1: CTAs that stay resident and take jobs in turn
   cudaStream_t st;
 };
 cudaError_t split_gemm(const SgView& v);
