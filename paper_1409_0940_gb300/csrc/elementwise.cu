@@ -355,11 +355,10 @@ __global__ void k_prox_reg(int reg, const float* __restrict__ V, const float* __
 constexpr int EX_ROWS = 32;
 
 template <int LOSS>
-__global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
+__global__ void __launch_bounds__(256, row_loss(LOSS) ? 3 : 4) k_exchange(RowEpiArgs a) {
   extern __shared__ float ex_smem[];
   const int mp = a.mpad;
-  float* term = ex_smem;                         // [32][mpad]
-  float* tile = ex_smem + EX_ROWS * mp;          // [32][mpad + 1] (split path)
+  float* tile = ex_smem;   // U of the 32 rows, [32][mpad + 1] (zero where not live)
   const bool split = a.VThi != nullptr;
   float vscale = 1.f;
   if (split) {
@@ -440,7 +439,8 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
         *reinterpret_cast<float4*>(a.Obar + tb + 4 * e4) = make_float4(ob[0], ob[1], ob[2], ob[3]);
         *reinterpret_cast<float4*>(a.nu + tb + 4 * e4) = make_float4(nu[0], nu[1], nu[2], nu[3]);
         *reinterpret_cast<float4*>(a.O + tb + 4 * e4) = make_float4(on[0], on[1], on[2], on[3]);
-        *reinterpret_cast<float4*>(term + 4 * e4) = make_float4(tm[0], tm[1], tm[2], tm[3]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tile[r * (mp + 1) + k0 + c] = tm[c];
       }
     }
   }
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
       a.Obar[base + k] = live ? Obar : 0.f;
       a.nu[base + k] = live ? nu : 0.f;
       if (live) numax = fmaxf(numax, fabsf(nu));
-      term[r * mp + k] = live ? Delta * inv_c1 + nu : 0.f;
+      tile[r * (mp + 1) + k] = live ? Delta * inv_c1 + nu : 0.f;
       if (live) w_in[q] = Obar - nu;
       else y[q] = 0.f;
     }
@@ -514,22 +514,13 @@ __global__ void __launch_bounds__(256) k_exchange(RowEpiArgs a) {
     }
   }
   __syncthreads();
-  // phase 2: U_i = term, once (block 0 of the V buffers): row-major FP32, or transposed and
-  // split into the scaled FP16 pair through the shared-memory tile
+  // phase 2: U_i, once (block 0 of the V buffers): row-major FP32, or transposed and split
+  // into the scaled FP16 pair from the shared-memory tile
   if (!split) {
     float* v = a.V32 + p0 * mp;
-    for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
-      const bool live = a.row_ok[p0 + e / mp] >= 0 && e % mp < a.m;
-      v[e] = live ? term[e] : 0.f;
-    }
+    for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) v[e] = tile[(e / mp) * (mp + 1) + e % mp];
     return;
   }
-  for (int e = threadIdx.x; e < EX_ROWS * mp; e += 256) {
-    const int r = e / mp, k = e % mp;
-    const bool live = a.row_ok[p0 + r] >= 0 && k < a.m;
-    tile[r * (mp + 1) + k] = live ? term[e] : 0.f;
-  }
-  __syncthreads();
   // lanes over the 32 rows, warps over columns: U^T[c][p0 + lane]
   for (int c = warp; c < mp; c += 8) {
     __half hi, lo;
@@ -876,12 +867,12 @@ cudaError_t launch_row_epilogue(const RowEpiArgs& a, cudaStream_t st) {
   if (a.mpad > 32 * MAXPL || a.nslots % EX_ROWS) return cudaErrorInvalidValue;
   const bool split = a.VThi && a.VTlo && a.amax;
   if (!a.V32 && !split) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)EX_ROWS * (split ? 2 * a.mpad + 1 : a.mpad) * sizeof(float);
+  const size_t smem = (size_t)EX_ROWS * (a.mpad + 1) * sizeof(float);
   const unsigned grid = (unsigned)(a.nslots / EX_ROWS);
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    const int mx = EX_ROWS * (2 * 32 * MAXPL + 1) * (int)sizeof(float);
+    const int mx = EX_ROWS * (32 * MAXPL + 1) * (int)sizeof(float);
     attr = cudaFuncSetAttribute(k_exchange<LOSS_SQUARED>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_exchange<LOSS_HINGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
