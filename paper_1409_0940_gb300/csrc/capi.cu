@@ -1082,6 +1082,7 @@ rff_status tc_gram_accumulate(rff_admm_t h, const float* Zc, int64_t nr, int64_t
     v.out_scale = 1.f / (zs * zs);
     v.two_acc = 1;
     v.persistent = 1;
+    v.kc = 64;   // K = kn, a multiple of 512
     v.st = s.st;
     CK(split_gemm(v));
     CK(launch_gram_reduce(P, (int)(g1 - g0), (int)nt, dtiles, sj, H, sj, s.st));
@@ -1376,7 +1377,8 @@ SgView qgemm_view(const rff_admm_s& s) {
   v.two_acc = 1;
   v.bmask = s.act();
   v.accumulate = 1;   // W'_ij += Q_ij rhs_ij (the incremental projection)
-  v.st = s.st;   // one job per CTA: the hardware hands the 3.4 waves of jobs to whichever SM is free
+  v.kc = 64;          // the split inverses are zero past s_j columns
+  v.st = s.st;        // one job per CTA: the hardware hands the 3.4 waves of jobs to whichever SM is free
   return v;
 }
 

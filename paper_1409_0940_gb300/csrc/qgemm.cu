@@ -36,8 +36,7 @@ namespace {
 
 using namespace tc5;
 
-constexpr int QKC = 32;                      // K elements per ring stage
-constexpr uint32_t QATILE = 128 * QKC * 2;   // 8 KB: 128 rows x 64 bytes
+constexpr int QKC = 32;                      // K elements of a job's chunk count (SgJob::nk)
 constexpr int QMAXS = 8;
 constexpr int QNT = 192;
 constexpr int ERR_Q = 8;
@@ -95,9 +94,15 @@ __device__ __forceinline__ bool q_skip(const SgJob& j, const QArgs& a) {
 // Each CTA takes the jobs blockIdx.x, blockIdx.x + gridDim.x, ... (one job per CTA when the
 // grid covers the table).  The copies run ahead through the ring across jobs; a job's products
 // go to accumulator set (its count) mod nbuf, which the writing warps free after reading it.
-template <int NA, int NB, int F16>
+// KC: K elements per ring stage, 32 (64-byte rows, 64-byte swizzle) or 64 (128-byte rows and
+// swizzle: fewer shared-memory wavefronts per product, half as many stages); a job's nk counts
+// chunks of 32, so with KC = 64 an odd count reads 32 more K columns, which the caller keeps
+// zero in A (or beyond the tensor, where the copy fills zeros).
+template <int NA, int NB, int F16, int KC>
 __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArgs a) {
   constexpr int NPROD = (NA == 3 && NB == 3) ? 6 : 3;
+  constexpr uint32_t ATILE = 128 * KC * 2;                  // one 128-row A term
+  constexpr uint32_t SBO = 8 * KC * 2, LAYOUT = KC == 64 ? 2 : 4;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   QShared& sh = *reinterpret_cast<QShared*>(base + a.ns * a.stage_bytes);
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
   const uint32_t bar_full = smem_u32(&sh.full[0]), bar_empty = smem_u32(&sh.empty[0]);
   const uint32_t bar_accf = smem_u32(&sh.acc_full[0]), bar_acce = smem_u32(&sh.acc_empty[0]);
   const uint32_t bar_done = smem_u32(&sh.mma_done);
-  const uint32_t mb = (uint32_t)a.mpad * (QKC * 2);   // one B tile: m_pad rows x 64 bytes
+  const uint32_t mb = (uint32_t)a.mpad * (KC * 2);   // one B term: m_pad rows
   if (threadIdx.x == 0) {
     sh.abort_flag = 0;
     for (int i = 0; i < a.ns; ++i) {
@@ -137,7 +142,8 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
       for (int jx = blockIdx.x; ok && jx < a.njobs; jx += gridDim.x) {
         const SgJob job = a.jobs[jx];
         if (q_skip(job, a)) continue;
-        for (int kc = 0; kc < job.nk; ++kc) {
+        const int nkc = KC == 64 ? (job.nk + 1) >> 1 : job.nk;
+        for (int kc = 0; kc < nkc; ++kc) {
           const int st = issued % a.ns;
           const uint32_t use = issued / a.ns;
           if (use > 0 && !qwait(bar_empty + 8 * st, (use - 1) & 1, sh, a)) {
@@ -148,10 +154,10 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
           mbar_expect_tx(fb, a.stage_bytes);
           const uint32_t dst = smem_u32(base + st * a.stage_bytes);
 #pragma unroll
-          for (int s = 0; s < NA; ++s) tma_load_2d(dst + s * QATILE, &a.tA[s], job.a_k0 + kc * QKC, job.a_row, fb);
+          for (int s = 0; s < NA; ++s) tma_load_2d(dst + s * ATILE, &a.tA[s], job.a_k0 + kc * KC, job.a_row, fb);
 #pragma unroll
           for (int s = 0; s < NB; ++s)
-            tma_load_2d(dst + NA * QATILE + s * mb, &a.tB[s], job.b_k0 + kc * QKC, job.b_row, fb);
+            tma_load_2d(dst + NA * ATILE + s * mb, &a.tB[s], job.b_k0 + kc * KC, job.b_row, fb);
           ++issued;
         }
       }
@@ -178,7 +184,8 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
         }
         fence_after();
         const uint32_t acc = tmem + buf * a.buf_cols;
-        for (int kc = 0; kc < job.nk; ++kc, ++used) {
+        const int nkc = KC == 64 ? (job.nk + 1) >> 1 : job.nk;
+        for (int kc = 0; kc < nkc; ++kc, ++used) {
           const int st = used % a.ns;
           if (!qwait(bar_full + 8 * st, (used / a.ns) & 1, sh, a)) {
             ok = false;
@@ -186,13 +193,13 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
           }
           fence_after();
           const uint32_t sa = smem_u32(base + st * a.stage_bytes);
-          const uint32_t sb = sa + NA * QATILE;
+          const uint32_t sb = sa + NA * ATILE;
 #pragma unroll
-          for (int kk = 0; kk < QKC / 16; ++kk) {
+          for (int kk = 0; kk < KC / 16; ++kk) {
 #pragma unroll
             for (int p = 0; p < NPROD; ++p) {
-              const uint64_t da = smem_desc(sa + prod_a(p) * QATILE + kk * 32, 512, 4);
-              const uint64_t db = smem_desc(sb + prod_b(p) * mb + kk * 32, 512, 4);
+              const uint64_t da = smem_desc(sa + prod_a(p) * ATILE + kk * 32, SBO, LAYOUT);
+              const uint64_t db = smem_desc(sb + prod_b(p) * mb + kk * 32, SBO, LAYOUT);
               if (a.acc_b) {
                 // hi.hi alone in the first accumulator, the smaller products in the second
                 const uint32_t d = p == 0 ? acc : acc + a.acc_b;
@@ -343,12 +350,12 @@ int qsm_count() {
   return n;
 }
 
-template <int NA, int NB, int F16>
+template <int NA, int NB, int F16, int KC>
 cudaError_t set_smem_attr() {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_split_gemm<NA, NB, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr = cudaFuncSetAttribute(k_split_gemm<NA, NB, F16, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 1024 + 216 * 1024 + 256);
   });
   return attr;
@@ -379,14 +386,16 @@ cudaError_t split_gemm(const SgView& v) {
   QArgs a;
   memset(&a, 0, sizeof(a));
   cudaError_t e;
+  const size_t budget = std::min<size_t>(v.smem_budget ? v.smem_budget : 216 * 1024, 216 * 1024);
+  // 64-element stages only where two of them fit (m_pad = 256 with three terms does not)
+  const int kc = (v.kc == 64 && 2 * (size_t)(v.na * 128 + v.nb * v.mpad) * 64 * 2 <= budget) ? 64 : 32;
   for (int s = 0; s < v.na; ++s)
-    if ((e = tc_make_map_bf16(&a.tA[s], v.A[s], v.a_cols, v.a_rows, v.a_cols, 128, QKC)) != cudaSuccess) return e;
+    if ((e = tc_make_map_bf16(&a.tA[s], v.A[s], v.a_cols, v.a_rows, v.a_cols, 128, kc)) != cudaSuccess) return e;
   for (int s = 0; s < v.nb; ++s)
-    if ((e = tc_make_map_bf16(&a.tB[s], v.B[s], v.b_cols, v.b_rows, v.b_cols, v.mpad, QKC)) != cudaSuccess)
+    if ((e = tc_make_map_bf16(&a.tB[s], v.B[s], v.b_cols, v.b_rows, v.b_cols, v.mpad, kc)) != cudaSuccess)
       return e;
   a.mpad = v.mpad;
-  a.stage_bytes = v.na * QATILE + v.nb * (uint32_t)v.mpad * QKC * 2;
-  const size_t budget = std::min<size_t>(v.smem_budget ? v.smem_budget : 216 * 1024, 216 * 1024);
+  a.stage_bytes = (uint32_t)(v.na * 128 + v.nb * v.mpad) * kc * 2;
   a.ns = (int)std::min<size_t>(QMAXS, budget / a.stage_bytes);
   if (a.ns < 2) a.ns = 2;
   a.tmem_cols = v.mpad <= 32 ? 32 : v.mpad <= 64 ? 64 : v.mpad <= 128 ? 128 : 256;
@@ -410,11 +419,16 @@ cudaError_t split_gemm(const SgView& v) {
   if (!a.err) return cudaErrorMemoryAllocation;
   a.timeout_cycles = 4000000000LL;   // about two seconds at the boost clock
   const size_t smem = 1024 + (size_t)a.ns * a.stage_bytes + 256;
-  if (v.na == 3) {
-    if ((e = set_smem_attr<3, 3, 0>()) != cudaSuccess) return e;
-  } else {
-    if ((e = set_smem_attr<2, 2, 1>()) != cudaSuccess) return e;
-  }
+  // the four instances: BF16 three-term or FP16 two-term operands, 32- or 64-element stages
+  auto kern = [&]() -> const void* {
+    if (v.na == 3) return kc == 64 ? (const void*)k_split_gemm<3, 3, 0, 64> : (const void*)k_split_gemm<3, 3, 0, 32>;
+    return kc == 64 ? (const void*)k_split_gemm<2, 2, 1, 64> : (const void*)k_split_gemm<2, 2, 1, 32>;
+  };
+  if (v.na == 3)
+    e = kc == 64 ? set_smem_attr<3, 3, 0, 64>() : set_smem_attr<3, 3, 0, 32>();
+  else
+    e = kc == 64 ? set_smem_attr<2, 2, 1, 64>() : set_smem_attr<2, 2, 1, 32>();
+  if (e != cudaSuccess) return e;
   // one job per CTA, or (persistent) at most as many CTAs as fit on the device at once, each
   // taking every grid-th job; two accumulator sets when the tensor memory of the CTAs that
   // share an SM holds them
@@ -423,8 +437,7 @@ cudaError_t split_gemm(const SgView& v) {
   int64_t grid = v.njobs;
   if (v.persistent) {
     int per_sm = 0;
-    e = v.na == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_split_gemm<3, 3, 0>, QNT, smem)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_split_gemm<2, 2, 1>, QNT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern(), QNT, smem);
     if (e != cudaSuccess) return e;
     per_sm = std::max(per_sm, 1);
     grid = std::min<int64_t>(v.njobs, (int64_t)qsm_count() * per_sm);
@@ -433,10 +446,13 @@ cudaError_t split_gemm(const SgView& v) {
       a.tmem_cols *= 2;
     }
   }
-  if (v.na == 3)
-    k_split_gemm<3, 3, 0><<<(unsigned)grid, QNT, smem, v.st>>>(a);
-  else
-    k_split_gemm<2, 2, 1><<<(unsigned)grid, QNT, smem, v.st>>>(a);
+  if (v.na == 3) {
+    if (kc == 64) k_split_gemm<3, 3, 0, 64><<<(unsigned)grid, QNT, smem, v.st>>>(a);
+    else k_split_gemm<3, 3, 0, 32><<<(unsigned)grid, QNT, smem, v.st>>>(a);
+  } else {
+    if (kc == 64) k_split_gemm<2, 2, 1, 64><<<(unsigned)grid, QNT, smem, v.st>>>(a);
+    else k_split_gemm<2, 2, 1, 32><<<(unsigned)grid, QNT, smem, v.st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -98,6 +98,8 @@ struct SgView {
   const uint8_t* bmask;                // device, R x C: a job of an inactive block does nothing; or null
   int accumulate;                      // 1: out += the product (amax of the sum)
   int persistent;                      // 1: CTAs that stay resident and take jobs in turn
+  int kc;                              // K per ring stage: 32 (0 = default) or 64 (128-byte swizzle; an
+                                       // odd nk then reads 32 more K columns, zero in A or past its end)
   cudaStream_t st;
 };
 cudaError_t split_gemm(const SgView& v);
