@@ -432,7 +432,7 @@ void compute_geometry(rff_admm_s& s, int64_t n, int64_t d) {
 // Split-path Gram on the tensor cores (Gram form): per row chunk of Z, Z^T as a scaled FP16
 // hi/lo pair and 128 x 256 tiles of Z^T Z over 512-row pieces of K, GRAM_GROUP pieces per
 // launch, their partial tiles summed into H in FP64.
-constexpr int GRAM_KCH = 512, GRAM_GROUP = 8;
+constexpr int GRAM_KCH = 512, GRAM_GROUP = 16;
 
 int64_t tc_gram_tiles(int64_t smax, std::vector<int2>* out = nullptr) {
   const int64_t spad = round_up(smax, 256);

@@ -995,7 +995,7 @@ cudaError_t launch_finite_check(const float* x, int64_t n, int pm1, int* flag, c
 // Four consecutive columns per thread: the pieces' float4 loads are all issued before the
 // sums (which keep the pieces' order), and H is updated by two double2 read-modify-writes
 // where the address is 16-byte aligned (H itself may start on an 8-byte boundary).
-constexpr int GRAM_PIECES_MAX = 8;
+constexpr int GRAM_PIECES_MAX = 16;
 
 __global__ void k_gram_reduce(const float* __restrict__ P, int nchunk, int ntiles, const int2* __restrict__ tiles,
                               int64_t s, double* __restrict__ H, int64_t ldh) {

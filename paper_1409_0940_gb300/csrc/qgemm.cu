@@ -329,10 +329,27 @@ __global__ void k_split3_q(const double* __restrict__ Q, int s, int64_t ldq, int
   if (t >= (int64_t)s * s) return;
   const int64_t r = t / s, c = t % s;
   const double x = Q[t];
-  const __nv_bfloat16 h = __double2bfloat16(x);
-  const double rem = x - (double)__bfloat162float(h);
-  const __nv_bfloat16 m = __double2bfloat16(rem);
-  const __nv_bfloat16 l = __double2bfloat16(rem - (double)__bfloat162float(m));
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  __nv_bfloat16 h, m, l;
+  if (E >= 1023 - 64 && E <= 1023 + 64) {   // 2^-64 <= |x| < 2^65: every power below is a normal FP32
+    // x = t + rs: t its leading 24 bits as an FP32 number and rs the remaining 29 (both exact,
+    // built by integer instructions: this part's FP64 pipe runs at 1/64 of the FP32 rate);
+    // then h = bf16(t), and m, l the BF16 terms of (t - h) + rs, whose FP32 rounding lies
+    // below 2^-32 |x|
+    const uint32_t sgn = (uint32_t)(b >> 32) & 0x80000000u;
+    const float t32 = __uint_as_float(sgn | ((uint32_t)(E - 1023 + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+    const float r32 = __uint2float_rn((uint32_t)(b & 0x1fffffffu)) * __uint_as_float((uint32_t)(E - 1075 + 127) << 23);
+    h = __float2bfloat16_rn(t32);
+    const float rem = __fadd_rn(__fsub_rn(t32, __bfloat162float(h)), sgn ? -r32 : r32);
+    m = __float2bfloat16_rn(rem);
+    l = __float2bfloat16_rn(__fsub_rn(rem, __bfloat162float(m)));
+  } else {   // zero, tiny, huge or not finite: the FP64 route
+    h = __double2bfloat16(x);
+    const double rem = x - (double)__bfloat162float(h);
+    m = __double2bfloat16(rem);
+    l = __double2bfloat16(rem - (double)__bfloat162float(m));
+  }
   const int64_t o = (qrow + r) * ldq + c;
   q1[o] = h;
   q2[o] = m;
