@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
       for (int jx = blockIdx.x; ok && jx < a.njobs; jx += gridDim.x) {
         const SgJob job = a.jobs[jx];
         if (q_skip(job, a)) continue;
-        const int nkc = KC == 64 ? (job.nk + 1) >> 1 : job.nk;
+        const int nkc = (job.nk * QKC + KC - 1) / KC;   // stages of KC elements
         for (int kc = 0; kc < nkc; ++kc) {
           const int st = issued % a.ns;
           const uint32_t use = issued / a.ns;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
         }
         fence_after();
         const uint32_t acc = tmem + buf * a.buf_cols;
-        const int nkc = KC == 64 ? (job.nk + 1) >> 1 : job.nk;
+        const int nkc = (job.nk * QKC + KC - 1) / KC;   // stages of KC elements
         for (int kc = 0; kc < nkc; ++kc, ++used) {
           const int st = used % a.ns;
           if (!qwait(bar_full + 8 * st, (used / a.ns) & 1, sh, a)) {
