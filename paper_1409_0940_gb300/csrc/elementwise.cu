@@ -615,24 +615,56 @@ __global__ void k_transpose_f32(const float* __restrict__ src, int64_t rows, int
   }
 }
 
-// Wbar = (W + sum_i W'_i)/(R+1);  mu += W - Wbar;  mu'_i += W'_i - Wbar
+// Double-float arithmetic on the FP32 pipes (this part's FP64 pipe runs at 1/64 of the FP32
+// rate): Knuth's TwoSum and Dekker's Fast2Sum, every operation rounded on its own.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return FF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_fast(float a, float b) {   // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add_f(FF x, float y) {
+  const FF t = ff_two_sum(x.hi, y);
+  return ff_fast(t.hi, __fadd_rn(t.lo, x.lo));
+}
+// x / c for a small positive integer c (exact in FP32): the remainder x.hi - q c is exact
+// through the FMA
+__device__ __forceinline__ FF ff_div_int(FF x, float c) {
+  const float q1 = __fdiv_rn(x.hi, c);
+  const float r = __fadd_rn(__fmaf_rn(-q1, c, x.hi), x.lo);
+  return ff_fast(q1, __fdiv_rn(r, c));
+}
+// RN32(y + x - m) for a pair m: (y + x) as a pair, minus m, rounded once at the end
+__device__ __forceinline__ float ff_round_sum(float y, float x, FF m) {
+  FF t = ff_two_sum(y, x);
+  t = ff_add_f(t, -m.hi);
+  t = ff_add_f(t, -m.lo);
+  return __fadd_rn(t.hi, t.lo);
+}
+
 // Wbar = (W + sum_i W'_ij)/(R+1), mu += W - Wbar, mu'_ij += W'_ij - Wbar.  The average and
-// the dual updates are formed in FP64 from the FP32 operands (converted exactly), and each
-// result is rounded once: the duals add up W - Wbar over the iterations, and an FP32 average
-// would hand them its rounding every time (an error that grows with the iteration count).
+// the dual updates are formed in double-float arithmetic from the FP32 operands (about 2^-47
+// relative), and each result is rounded to FP32 once: the duals add up W - Wbar over the
+// iterations, and an FP32 average would hand them its rounding every time (an error that
+// grows with the iteration count).
 __global__ void k_avg_dual(const float* __restrict__ W, const float* __restrict__ What, int R, int64_t nfe,
                            float* __restrict__ Wbar, float* __restrict__ mu, float* __restrict__ muij) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= nfe) return;
-  const double w = f32_to_f64_scaled(W[e], 0);
-  double s = w;
-  for (int i = 0; i < R; ++i) s += f32_to_f64_scaled(What[(int64_t)i * nfe + e], 0);
-  const double wb = s * (1.0 / (double)(R + 1));
-  Wbar[e] = (float)wb;
-  mu[e] = (float)(f32_to_f64_scaled(mu[e], 0) + (w - wb));
+  const float w = W[e];
+  FF s{w, 0.f};
+  for (int i = 0; i < R; ++i) s = ff_add_f(s, What[(int64_t)i * nfe + e]);
+  const FF wb = ff_div_int(s, (float)(R + 1));
+  Wbar[e] = __fadd_rn(wb.hi, wb.lo);
+  mu[e] = ff_round_sum(mu[e], w, wb);
   for (int i = 0; i < R; ++i) {
     const int64_t t = (int64_t)i * nfe + e;
-    muij[t] = (float)(f32_to_f64_scaled(muij[t], 0) + (f32_to_f64_scaled(What[t], 0) - wb));
+    muij[t] = ff_round_sum(muij[t], What[t], wb);
   }
 }
 
