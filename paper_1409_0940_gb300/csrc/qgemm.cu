@@ -17,9 +17,9 @@
 // right-hand side), and the two chained products of the cached-Z precision
 // (pass 1: A = Z^T, B = V^T; pass 2: A = Z, B = W'^T; eq. (gpWij), (gpOij)).
 //
-// A TMA ring of 32-element K chunks (64-byte swizzle) feeds the tiles of each
-// chunk.  Warp 0 issues the copies, one thread of warp 1 the MMAs, warps 2..5
-// write the result.  Waits are bounded as in the regeneration kernel: on a timeout
+// A TMA ring of 32-element K chunks (64-byte swizzle), or 64-element ones (128-byte
+// swizzle), feeds the tiles of each chunk.  Warp 0 issues the copies, one thread of warp 1
+// the MMAs, warps 2..9 write the result.  Waits are bounded as in the regeneration kernel: on a timeout
 // the CTA records an error code, waits (bounded) for its copies and products in
 // flight, frees TMEM and returns.
 #include <algorithm>
@@ -38,7 +38,8 @@ using namespace tc5;
 
 constexpr int QKC = 32;                      // K elements of a job's chunk count (SgJob::nk)
 constexpr int QMAXS = 8;
-constexpr int QNT = 192;
+constexpr int QEPI = 8;                      // writing warps: two per TMEM lane quarter, half the columns each
+constexpr int QNT = 64 + 32 * QEPI;
 constexpr int ERR_Q = 8;
 
 struct QArgs {
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(bar_accf + 8 * i, 1);
-      mbar_init(bar_acce + 8 * i, 4);   // one arrival per writing warp
+      mbar_init(bar_acce + 8 * i, QEPI);   // one arrival per writing warp
     }
     mbar_init(bar_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -219,8 +220,10 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
       qwait(bar_done, 0, sh, a);
     }
   } else {
-    // epilogue: lanes = rows of the A tile, m_pad columns, 8 per TMEM read
+    // epilogue: lanes = rows of the A tile; warps 2..5 take the first m_pad/2 columns, warps
+    // 6..9 the rest, 8 per TMEM read
     const int quarter = warp & 3;
+    const int c_begin = ((warp - 2) >> 2) * (a.mpad / 2), c_end = c_begin + a.mpad / 2;
     const int row = quarter * 32 + lane;
     uint32_t done_jobs = 0;
     float mx = 0.f;
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(QNT) k_split_gemm(const __grid_constant__ QArg
       const uint32_t taddr = tmem + buf * a.buf_cols + ((uint32_t)(quarter * 32) << 16);
       float* orow_p = a.out + job.out + (int64_t)row * a.mpad;
       const float sc = a.out_scale * (a.b_amax ? f16_inv_scale(__uint_as_float(*a.b_amax)) : 1.f);
-      for (int c = 0; c < a.mpad; c += 8) {
+      for (int c = c_begin; c < c_end; c += 8) {
         uint32_t r8[8], s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         tmem_ld8(taddr + c, r8);
         if (a.acc_b) tmem_ld8(taddr + a.acc_b + c, s8);
