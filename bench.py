@@ -141,7 +141,7 @@ def pads(w):
     return -(-w["m"] // 16) * 16, -(-w["d"] // 64) * 64   # m_pad, d_pad (the slot layout's padding)
 
 
-def survey_flops_per_pass(w):
+def algorithmic_flops_per_pass(w):
     """Algorithmic tensor work of one regeneration pass, as the roofline counts it: the
     three split products of X.G at the data's own d (3 x 2 n d D) and one chained product
     at m_pad (2 n D m_pad)."""
@@ -334,7 +334,7 @@ def run_ours(args, rank, world):
     per_launch_ms = prof[ph] / max(prof["iters"], 1)
     executed = exec_pass / (per_launch_ms * 1e-3) / 1e12
     if args.prec == "split_bf16":
-        achieved = survey_flops_per_pass(w) * act / (per_launch_ms * 1e-3) / 1e12
+        achieved = algorithmic_flops_per_pass(w) * act / (per_launch_ms * 1e-3) / 1e12
         traffic = TRAFFIC_200K.get(ph[3:]) if not args.n and act == 1.0 else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sus, "unit": "TFLOP/s",
                 "frac": achieved / bf16_sus, "traffic": traffic, "kernel": "k_regen_tc " + ph[3:],
@@ -530,7 +530,7 @@ def run_large(args, steps=3):
     _, _, bf16_sus, src = peaks()
     ph = "ms_pass2" if prof["ms_pass2"] >= prof["ms_pass1"] else "ms_pass1"
     per_launch_ms = prof[ph] / max(prof["iters"], 1)
-    achieved = survey_flops_per_pass(w) / (per_launch_ms * 1e-3) / 1e12
+    achieved = algorithmic_flops_per_pass(w) / (per_launch_ms * 1e-3) / 1e12
     _, exec_pass = flops_per_iter(w, "split_bf16")
     executed = exec_pass / (per_launch_ms * 1e-3) / 1e12
     out = {"metric": METRIC, "value": steps / (ms * 1e-3), "unit": "iter/s", "steps": steps, "warmup": 1,
