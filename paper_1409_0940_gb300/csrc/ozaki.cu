@@ -470,24 +470,50 @@ OzShape oz_shape(int ph, int k, int s) {
   }
 }
 
+int sm_count() {
+  static int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+      v = 0;
+    return v > 0 ? v : 1;
+  }();
+  return n;
+}
+
 // work items of one product: per 128-row block, its columns (those on or left of the block
-// diagonal when lower) in pieces of OZ_ITEM_COLS
+// diagonal when lower) in pieces of `cols`
 template <typename F>
-void oz_items(const OzShape& sh, F&& emit) {
+void oz_items(const OzShape& sh, int cols, F&& emit) {
   for (int m0 = 0; m0 < sh.M; m0 += OZ_BM) {
     const int nlim = sh.lower ? std::min(sh.N, (m0 / 64 + 2) * 64) : sh.N;
     const int nend = (int)round_up(nlim, OZ_BN);
-    for (int n0 = 0; n0 < nend; n0 += OZ_ITEM_COLS) emit(m0, n0, std::min(n0 + OZ_ITEM_COLS, nend));
+    for (int n0 = 0; n0 < nend; n0 += cols) emit(m0, n0, std::min(n0 + cols, nend));
   }
 }
 
-int64_t oz_items_per_job(int smax, bool invert) {
+// columns of one work item: OZ_ITEM_COLS, narrower (down to one 32-column tile) where the nj
+// matrices of a batch would give fewer items than there are SMs -- the small products of a
+// step (the panel, the diagonal block rows of both sweeps), which otherwise leave most SMs idle
+int oz_item_cols(const OzShape& sh, int nj) {
+  auto count = [&](int cols) {
+    int64_t n = 0;
+    oz_items(sh, cols, [&](int, int, int) { ++n; });
+    return n * nj;
+  };
+  int w = OZ_ITEM_COLS;
+  while (w > OZ_BN && count(w) < sm_count()) w /= 2;
+  return w;
+}
+
+int64_t oz_items_per_job(int smax, bool invert, int nj) {
   const int nb = (int)ceil_div(smax, 64);
   int64_t n = 0;
   for (int k = 0; k < nb; ++k)
     for (int ph = 0; ph < OZ_NPHASE; ++ph) {
       if (!invert && ph >= OZ_FA) break;
-      oz_items(oz_shape(ph, k, smax), [&](int, int, int) { ++n; });
+      const OzShape sh = oz_shape(ph, k, smax);
+      oz_items(sh, oz_item_cols(sh, nj), [&](int, int, int) { ++n; });
     }
   return n;
 }
@@ -517,20 +543,9 @@ OzLayout oz_layout(int nj, int smax) {
   L.sjobs = take((size_t)OZ_NPHASE * L.nb * 2 * nj * sizeof(OzSliceJob));
   L.gjobs = take((size_t)OZ_NPHASE * L.nb * nj * sizeof(OzJob));
   // every job's items are at most those of a matrix of order smax
-  L.items = take((size_t)nj * oz_items_per_job(smax, true) * sizeof(OzItem));
+  L.items = take((size_t)nj * oz_items_per_job(smax, true, nj) * sizeof(OzItem));
   L.total = p + 1024;   // the caller's pointer is aligned up to 1 KB first
   return L;
-}
-
-int sm_count() {
-  static int n = [] {
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess)
-      v = 0;
-    return v > 0 ? v : 1;
-  }();
-  return n;
 }
 
 template <int S>
@@ -622,10 +637,11 @@ cudaError_t factor_and_invert_sliced(const std::vector<MatJob>& jobs, bool inver
   for (int ph = 0; ph < OZ_NPHASE; ++ph)
     for (int k = 0; k < nb; ++k) {
       item_at[(size_t)ph * nb + k] = (int64_t)hi.size();
+      const int cols = oz_item_cols(oz_shape(ph, k, smax), nj);   // the same width for every matrix
       for (int b = 0; b < nj; ++b) {
         const OzJob& g = gj(ph, k, b);
         if (g.M <= 0 || g.N <= 0) continue;
-        oz_items(OzShape{g.M, g.N, ph == OZ_TRAIL || ph == OZ_BB}, [&](int m0, int n0, int n1) {
+        oz_items(OzShape{g.M, g.N, ph == OZ_TRAIL || ph == OZ_BB}, cols, [&](int m0, int n0, int n1) {
           hi.push_back(OzItem{b, m0, n0, n1});
         });
       }
