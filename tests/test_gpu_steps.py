@@ -156,7 +156,7 @@ def test_prox_reg_matches_oracle(rff, reg):
 
 
 # ----------------------------------------------------------------- Cholesky
-@pytest.mark.parametrize("s", [1, 5, 63, 64, 65, 200, 513, 1100])
+@pytest.mark.parametrize("s", [1, 5, 63, 64, 65, 200, 513, 1100, 2048])
 def test_cholesky_f64_matches_numpy(rff, s):
     rng = np.random.default_rng(s)
     batch = 3
